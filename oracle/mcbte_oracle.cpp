@@ -1,0 +1,800 @@
+// MCBTE oracle: plain, slow, FP64 scalar reference for the deviational
+// energy-based Monte Carlo solution of the linearised phonon BTE.
+//
+// TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+// bench's CPU-baseline leg may load this library.  It shares no code,
+// header or table generator with the CUDA library.
+//
+// What it follows (sections / equations of arXiv:2104.03573):
+//   - per-bin heat capacity C_i = D_i dE/dT(omega_i) d_omega_i           Eq. BE_derivative, Eq. Nbin
+//   - source energies E_i and E_eff = E_tot / N                           Eq. dev_tot, Eq. source_energy
+//   - source choice from the cumulative source energy                     Sec. 3.2 (Initialization)
+//   - emission: initial condition (bin ~ C|dT|, isotropic)                Eqs. Nbin, cumul_freq, angle_gen
+//               isothermal wall (bin ~ C v, Lambertian)                   Eqs. iso_flux, wall_dir
+//               control-gradient body source (bin ~ C v, Lambertian)      Eqs. grad_flux, grad_flux_sim
+//   - straight flights, exponential relaxation clock x = -Lambda ln R    Eqs. advection_eq, time_to_scat
+//   - remaining clock kept across boundary hits                           Sec. 3.3 case (iii)
+//   - relaxation: bin redrawn ~ C/tau, isotropic, sign kept               Eq. n_scatt, Sec. 3.5.2
+//   - adiabatic wall: specular with probability d, else Lambertian        Eq. specular, Sec. 3.5.3
+//   - isothermal wall absorbs; periodic wall translates                   Secs. 3.5.4, 3.5.5 (Eq. periodic_lin_final)
+//   - termination: absorbed, t > t_max, or N_scat_max relaxations         Sec. 3.5.6
+//   - steady track-length tallies                                         Eqs. steady_estimate, temp_steady, flux_x_steady
+//   - transient snapshot tallies                                          Eq. sampling, Sec. 3.4
+//   - likelihood-ratio scores for d/d(log tau_i) and d/dp (no counterpart in the paper; derived
+//     from the exponential law of Eq. time_to_scat and the discrete draws of Eq. n_scatt / Eq. specular)
+//
+// The random numbers are Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11,
+// "Parallel random numbers: as easy as 1, 2, 3"), implemented here from
+// that published definition.  Counter = (particle id, batch index, event
+// index, sub-block); key = (seed low, seed high).  Which word feeds which
+// draw is a fixed contract (listed at each use below).
+//
+// Internal units: length nm, time ps, velocity nm/ps.
+//
+// Compile with -O2 -ffp-contract=off (no fused multiply-add), so every
+// floating-point operation is the one written.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+namespace {
+
+const double kHbar = 1.054571817e-34;   // J s
+const double kBoltz = 1.380649e-23;     // J / K
+const double kTwoPi = 6.283185307179586;
+const double k2m32 = 2.3283064365386963e-10;   // 2^-32
+const double k2m53 = 1.1102230246251565e-16;   // 2^-53
+
+// ---------------------------------------------------------------- Philox4x32-10
+void philox4x32_10(const uint32_t ctr[4], uint32_t k0, uint32_t k1, uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// Real-valued maps of random words.
+inline double oc32(uint32_t w) { return ((double)w + 1.0) * k2m32; }    // (0, 1]
+inline double co32(uint32_t w) { return (double)w * k2m32; }            // [0, 1)
+inline double mid32(uint32_t w) { return ((double)w + 0.5) * k2m32; }   // (0, 1)
+inline double oc53(uint32_t lo, uint32_t hi) {                          // (0, 1], 53 bits
+  uint64_t m = ((uint64_t)hi << 21) ^ (uint64_t)(lo >> 11);
+  return ((double)m + 1.0) * k2m53;
+}
+
+// ---------------------------------------------------------------- tables
+struct Alias {
+  std::vector<double> prob;
+  std::vector<uint64_t> thr;
+  std::vector<int32_t> alias;
+};
+
+// Walker's alias method, built with Vose's two work lists (stacks filled in
+// increasing bin order, popped from the back).  The sampled law is the pmf
+// w_i / sum(w).
+Alias build_alias(const std::vector<double>& w) {
+  const int n = (int)w.size();
+  double W = 0.0;
+  for (int i = 0; i < n; ++i) W += w[i];
+  std::vector<double> p(n);
+  for (int i = 0; i < n; ++i) p[i] = (w[i] * (double)n) / W;
+  std::vector<int> small, large;
+  for (int i = 0; i < n; ++i) {
+    if (p[i] < 1.0) small.push_back(i); else large.push_back(i);
+  }
+  Alias a;
+  a.prob.assign(n, 1.0);
+  a.alias.assign(n, 0);
+  for (int i = 0; i < n; ++i) a.alias[i] = i;
+  while (!small.empty() && !large.empty()) {
+    int l = small.back(); small.pop_back();
+    int g = large.back(); large.pop_back();
+    a.prob[l] = p[l];
+    a.alias[l] = g;
+    p[g] = (p[g] + p[l]) - 1.0;
+    if (p[g] < 1.0) small.push_back(g); else large.push_back(g);
+  }
+  // leftovers keep prob 1 and alias = self
+  a.thr.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double q = a.prob[i];
+    a.thr[i] = (q >= 1.0) ? UINT64_MAX : (uint64_t)(q * 18446744073709551616.0);
+  }
+  return a;
+}
+
+// Draw a bin: column from one word (exact integer multiply-high), then keep
+// the column iff the 64-bit threshold word is below its threshold.
+inline int alias_draw(const Alias& a, int n, uint32_t wcol, uint32_t thr_lo, uint32_t thr_hi) {
+  int col = (int)(((uint64_t)wcol * (uint64_t)n) >> 32);
+  uint64_t r = ((uint64_t)thr_hi << 32) | (uint64_t)thr_lo;
+  return (r < a.thr[col]) ? col : a.alias[col];
+}
+
+// dE/dT of the Bose-Einstein mode energy hbar*omega*f_eq at temperature T:
+// k_B (x/2)^2 / sinh^2(x/2), x = hbar omega / (k_B T)   (Eq. BE_derivative, read as
+// the derivative of hbar*omega/(exp(x)-1)).
+double dEdT(double omega, double T) {
+  double x = (kHbar * omega) / (kBoltz * T);
+  double h = 0.5 * x;
+  double s = std::sinh(h);
+  return kBoltz * (h * h) / (s * s);
+}
+
+}  // namespace
+
+extern "C" {
+
+typedef struct {
+  // material (SI)
+  int n_bins;
+  const double* omega;
+  const double* v;
+  const double* tau;
+  const double* C;        // format 2, or NULL
+  const double* D;        // format 1, or NULL
+  const double* domega;   // format 1
+  double T_lin;
+  // geometry (SI)
+  double L[3];
+  int face_type[6];       // 0 isothermal, 1 adiabatic, 2 periodic
+  double face_T[6];
+  double face_p[6];
+  double T_eq;
+  double grad_T[3];
+  int pore;
+  double pore_c[2];
+  double pore_r;
+  double pore_p;
+  int gauss;
+  double gauss_c[3];
+  double gauss_sigma;
+  double gauss_dT;
+  // run
+  uint64_t seed;
+  uint32_t batch_index;
+  int transient;
+  uint64_t n_particles;   // N that defines E_eff
+  uint64_t pid_begin;
+  uint64_t pid_end;
+  int n_scat_max;         // 0 = unlimited
+  uint64_t max_events;
+  int n_cells;
+  int cell_axis;
+  int tally_axis;
+  double t_max;           // s
+  int n_times;
+  const double* t_meas;   // s
+  int grid[3];
+  int want_grad;
+  int n_dirs;
+  const double* dirs;     // [n_dirs][n_bins]
+  int n_threads;
+} or_params;
+
+enum {
+  OR_SUMX = 0, OR_SUMX2, OR_EVENTS, OR_TRUNC, OR_ABSORBED, OR_SIGNED_ABS, OR_SIGNED_EMIT,
+  OR_RSUM, OR_GP, OR_GP2, OR_ETOT, OR_CTOT, OR_VSOLID, OR_MAXEV, OR_NSCAL = 16
+};
+
+typedef struct {
+  double* T_sum;        // [n_cells]            sum s * l_c / v           (ps)
+  double* Q_sum;        // [n_cells][3]         sum s * l_c * u_b         (nm)
+  double* qbin_sum;     // [n_bins]             sum s * l * u_tally       (nm)
+  double* snap;         // [n_times][cells][4]  sum s, sum s v u_{x,y,z}  (-, nm/ps)
+  uint32_t* events_pp;  // [pid_end - pid_begin]
+  double* X_pp;         // [pid_end - pid_begin]  per-particle sum s l u_tally (nm)
+  double* G;            // [n_bins]  sum over particles of the sparse LR part
+  double* dir_sum;      // [n_dirs]
+  double* dir_sum2;     // [n_dirs]
+  double scal[16];
+} or_out;
+
+}  // extern "C"
+
+namespace {
+
+struct Tables {
+  int n = 0;
+  std::vector<double> C, v_nm, lam_nm, inv_v, pi_relax;
+  double C_tot = 0, sum_Cv = 0, sum_Ct = 0;
+  Alias emit, init, relax;
+};
+
+int build_tables(const or_params* P, Tables& t) {
+  const int n = P->n_bins;
+  if (n < 1) return 1;
+  t.n = n;
+  t.C.resize(n);
+  for (int i = 0; i < n; ++i) {
+    if (P->C) t.C[i] = P->C[i];
+    else t.C[i] = (P->D[i] * dEdT(P->omega[i], P->T_lin)) * P->domega[i];
+  }
+  std::vector<double> w_emit(n), w_init(n), w_relax(n);
+  for (int i = 0; i < n; ++i) {
+    w_emit[i] = t.C[i] * P->v[i];
+    w_init[i] = t.C[i];
+    w_relax[i] = t.C[i] / P->tau[i];
+  }
+  t.C_tot = 0; t.sum_Cv = 0; t.sum_Ct = 0;
+  for (int i = 0; i < n; ++i) {
+    t.C_tot += t.C[i];
+    t.sum_Cv += w_emit[i];
+    t.sum_Ct += w_relax[i];
+  }
+  t.emit = build_alias(w_emit);
+  t.init = build_alias(w_init);
+  t.relax = build_alias(w_relax);
+  t.v_nm.resize(n); t.lam_nm.resize(n); t.inv_v.resize(n); t.pi_relax.resize(n);
+  for (int i = 0; i < n; ++i) {
+    t.v_nm[i] = P->v[i] * 1e-3;
+    double tau_ps = P->tau[i] * 1e12;
+    t.lam_nm[i] = t.v_nm[i] * tau_ps;
+    t.inv_v[i] = 1.0 / t.v_nm[i];
+    t.pi_relax[i] = w_relax[i] / t.sum_Ct;
+  }
+  return 0;
+}
+
+const int kFaceAxis[6] = {1, 0, 1, 0, 2, 2};
+const int kFaceIsMax[6] = {0, 1, 1, 0, 0, 1};
+const int kAxisMinFace[3] = {3, 0, 4};
+const int kAxisMaxFace[3] = {1, 2, 5};
+
+struct Geo {
+  double L[3];
+  int type[6];
+  double Tb[6];
+  uint64_t pthr[6];
+  bool pore;
+  double cx, cy, r, r2, p_pore;
+  uint64_t pthr_pore;
+  double V_solid_m3;
+};
+
+uint64_t spec_threshold(double p) {
+  if (p <= 0.0) return 0;
+  if (p >= 1.0) return (uint64_t)1 << 32;
+  return (uint64_t)(p * 4294967296.0);
+}
+
+struct Source {
+  int kind;   // 0 face, 1 body, 2 gauss
+  int face;
+  double E;
+};
+
+struct Setup {
+  Geo g;
+  std::vector<Source> src;
+  std::vector<uint64_t> src_thr;
+  double E_tot = 0;
+  int grad_axis = -1;
+  double grad_sign = 0;
+  double t_max_ps = 0;
+  std::vector<double> t_meas_ps;
+  double gauss_c[3], gauss_sigma;
+  double dpi_dirs[64];
+};
+
+int setup(const or_params* P, const Tables& t, Setup& S) {
+  Geo& g = S.g;
+  for (int a = 0; a < 3; ++a) g.L[a] = P->L[a] * 1e9;
+  for (int f = 0; f < 6; ++f) {
+    g.type[f] = P->face_type[f];
+    g.Tb[f] = P->face_T[f];
+    g.pthr[f] = spec_threshold(P->face_p[f]);
+  }
+  g.pore = P->pore != 0;
+  g.cx = P->pore_c[0] * 1e9;
+  g.cy = P->pore_c[1] * 1e9;
+  g.r = P->pore_r * 1e9;
+  g.r2 = g.r * g.r;
+  g.p_pore = P->pore_p;
+  g.pthr_pore = spec_threshold(P->pore_p);
+  double V = P->L[0] * P->L[1] * P->L[2];
+  if (g.pore) V = V - (3.141592653589793 * (P->pore_r * P->pore_r)) * P->L[2];
+  g.V_solid_m3 = V;
+  // sources, in order: isothermal faces by ID, body, initial condition
+  const double time_factor = P->transient ? P->t_max : 1.0;
+  for (int f = 0; f < 6; ++f) {
+    if (g.type[f] != 0) continue;
+    double dT = P->face_T[f] - P->T_eq;
+    if (dT == 0.0) continue;
+    int a = kFaceAxis[f];
+    double A = P->L[(a + 1) % 3] * P->L[(a + 2) % 3];
+    double E = ((0.25 * A) * t.sum_Cv) * std::fabs(dT);
+    S.src.push_back({0, f, E * time_factor});
+  }
+  int nz = 0;
+  for (int a = 0; a < 3; ++a) if (P->grad_T[a] != 0.0) { nz++; S.grad_axis = a; }
+  if (nz > 1) return 2;
+  if (nz == 1) {
+    if (P->transient) return 2;
+    double gmag = std::fabs(P->grad_T[S.grad_axis]);
+    S.grad_sign = P->grad_T[S.grad_axis] > 0 ? 1.0 : -1.0;
+    double E = ((0.5 * V) * gmag) * t.sum_Cv;
+    S.src.push_back({1, -1, E});
+  }
+  if (P->gauss) {
+    double s = P->gauss_sigma;
+    double E = (((t.C_tot * std::fabs(P->gauss_dT)) * 15.749609945722419) * ((s * s) * s)) * 0.5;
+    S.src.push_back({2, -1, E});
+    for (int a = 0; a < 3; ++a) S.gauss_c[a] = P->gauss_c[a] * 1e9;
+    S.gauss_sigma = s * 1e9;
+  }
+  if (S.src.empty()) return 3;
+  double run = 0;
+  for (auto& s : S.src) run += s.E;
+  S.E_tot = run;
+  double acc = 0;
+  for (size_t k = 0; k < S.src.size(); ++k) {
+    acc += S.src[k].E;
+    if (k + 1 == S.src.size()) S.src_thr.push_back((uint64_t)1 << 32);
+    else S.src_thr.push_back((uint64_t)((acc / S.E_tot) * 4294967296.0));
+  }
+  S.t_max_ps = P->t_max * 1e12;
+  for (int m = 0; m < P->n_times; ++m) S.t_meas_ps.push_back(P->t_meas[m] * 1e12);
+  if (P->want_grad) {
+    if (P->n_dirs > 64) return 4;
+    for (int k = 0; k < P->n_dirs; ++k) {
+      double acc2 = 0;
+      for (int i = 0; i < t.n; ++i) acc2 += P->dirs[(size_t)k * t.n + i] * t.pi_relax[i];
+      S.dpi_dirs[k] = acc2;
+    }
+  }
+  return 0;
+}
+
+// First boundary along the ray: the faces met in the direction of travel and
+// the pore cylinder.  Ties go to the lowest paper boundary ID (faces 1..6,
+// pore 7).  Returns the distance (nm) and the face index (0..5, or 6).
+inline void first_hit(const Geo& g, const double x[3], const double u[3], double* dist, int* face) {
+  double best = INFINITY;
+  int bf = -1;
+  for (int a = 0; a < 3; ++a) {
+    double d;
+    int f;
+    if (u[a] > 0.0) { d = (g.L[a] - x[a]) / u[a]; f = kAxisMaxFace[a]; }
+    else if (u[a] < 0.0) { d = (0.0 - x[a]) / u[a]; f = kAxisMinFace[a]; }
+    else continue;
+    if (d < 0.0) d = 0.0;
+    if (d < best || (d == best && f < bf)) { best = d; bf = f; }
+  }
+  if (g.pore) {
+    double dx = x[0] - g.cx, dy = x[1] - g.cy;
+    double a = u[0] * u[0] + u[1] * u[1];
+    double b = dx * u[0] + dy * u[1];
+    if (a > 0.0 && b < 0.0) {
+      double c = (dx * dx + dy * dy) - g.r2;
+      double disc = b * b - a * c;
+      if (disc >= 0.0) {
+        double d = c / (std::sqrt(disc) - b);
+        if (d < 0.0) d = 0.0;
+        if (d < best) { best = d; bf = 6; }
+      }
+    }
+  }
+  *dist = best;
+  *face = bf;
+}
+
+// Direction with polar cosine mu about +/- axis a; the other two axes, in
+// cyclic order a+1, a+2, take s cos(phi), s sin(phi).
+inline void dir_about_axis(double u[3], int a, double sgn, double mu, uint32_t wphi) {
+  double s = std::sqrt(std::max(0.0, 1.0 - mu * mu));
+  double phi = kTwoPi * co32(wphi);
+  u[a] = sgn * mu;
+  u[(a + 1) % 3] = s * std::cos(phi);
+  u[(a + 2) % 3] = s * std::sin(phi);
+}
+
+struct Partial {
+  std::vector<double> T, Q, qbin, snap, G, dsum, dsum2;
+  double scal[OR_NSCAL] = {0};
+};
+
+struct Period { int bin; double A, B; };
+
+void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p0, uint64_t p1,
+                 Partial& out, or_out* O) {
+  const Geo& g = S.g;
+  const int n = t.n;
+  const uint32_t k0 = (uint32_t)P->seed, k1 = (uint32_t)(P->seed >> 32);
+  const int ta = P->tally_axis;
+  const bool cells = P->n_cells > 0 && !P->transient;
+  const double h_cell = cells ? g.L[P->cell_axis] / (double)P->n_cells : 0.0;
+  const int nx = P->grid[0], ny = P->grid[1], nzg = P->grid[2];
+  const int ncell_t = nx * ny * nzg;
+  std::vector<Period> periods;
+  for (uint64_t pid = p0; pid < p1; ++pid) {
+    uint32_t ctr[4] = {(uint32_t)pid, P->batch_index, 0u, 0u};
+    uint32_t w[4], w1[4], w2[4], w3[4];
+    // ---- emission (event 0)
+    ctr[3] = 0; philox4x32_10(ctr, k0, k1, w);
+    ctr[3] = 1; philox4x32_10(ctr, k0, k1, w1);
+    ctr[3] = 2; philox4x32_10(ctr, k0, k1, w2);
+    int k = 0;
+    while ((uint64_t)w[0] >= S.src_thr[k]) ++k;
+    const Source& src = S.src[k];
+    double x[3], u[3];
+    int bin;
+    double s;
+    double t_now = 0.0;
+    if (src.kind == 0) {
+      int f = src.face, a = kFaceAxis[f];
+      bin = alias_draw(t.emit, n, w[1], w[2], w[3]);
+      s = (g.Tb[f] > P->T_eq) ? 1.0 : -1.0;
+      double mu = std::sqrt(oc32(w1[0]));
+      dir_about_axis(u, a, kFaceIsMax[f] ? -1.0 : 1.0, mu, w1[1]);
+      if (P->transient) t_now = co32(w2[1]) * S.t_max_ps;
+      ctr[3] = 3; philox4x32_10(ctr, k0, k1, w3);
+      x[a] = kFaceIsMax[f] ? g.L[a] : 0.0;
+      x[(a + 1) % 3] = mid32(w3[0]) * g.L[(a + 1) % 3];
+      x[(a + 2) % 3] = mid32(w3[1]) * g.L[(a + 2) % 3];
+    } else if (src.kind == 1) {
+      bin = alias_draw(t.emit, n, w[1], w[2], w[3]);
+      s = (w2[0] < 0x80000000u) ? 1.0 : -1.0;
+      // positive particles travel down the control gradient, negative ones up it
+      double dsgn = (s > 0.0) ? -S.grad_sign : S.grad_sign;
+      double mu = std::sqrt(oc32(w1[0]));
+      dir_about_axis(u, S.grad_axis, dsgn, mu, w1[1]);
+      int attempt = 0;
+      for (;;) {
+        ctr[3] = 3u + (uint32_t)attempt; philox4x32_10(ctr, k0, k1, w3);
+        x[0] = mid32(w3[0]) * g.L[0];
+        x[1] = mid32(w3[1]) * g.L[1];
+        x[2] = mid32(w3[2]) * g.L[2];
+        if (!g.pore) break;
+        double dx = x[0] - g.cx, dy = x[1] - g.cy;
+        if (dx * dx + dy * dy >= g.r2) break;
+        if (++attempt >= 64) break;   // unreachable for porosities the API accepts
+      }
+    } else {
+      bin = alias_draw(t.init, n, w[1], w[2], w[3]);
+      s = (P->gauss_dT > 0.0) ? 1.0 : -1.0;
+      double mu = 1.0 - 2.0 * oc32(w1[0]);
+      dir_about_axis(u, 2, 1.0, mu, w1[1]);
+      ctr[3] = 3; philox4x32_10(ctr, k0, k1, w3);
+      double m1 = std::sqrt(-2.0 * std::log(oc32(w3[0])));
+      double m2 = std::sqrt(-2.0 * std::log(oc32(w3[2])));
+      double a1 = kTwoPi * co32(w3[1]);
+      double a2 = kTwoPi * co32(w3[3]);
+      double nrm[3] = {m1 * std::cos(a1), m1 * std::sin(a1), m2 * std::cos(a2)};
+      for (int a = 0; a < 3; ++a) {
+        double c = S.gauss_c[a] + S.gauss_sigma * nrm[a];
+        if (c < 0.0) c = -c;
+        if (c > g.L[a]) c = 2.0 * g.L[a] - c;
+        if (c < 0.0) c = 0.0;
+        if (c > g.L[a]) c = g.L[a];
+        x[a] = c;
+      }
+    }
+    double d_rel = t.lam_nm[bin] * (-std::log(oc53(w1[2], w1[3])));
+    out.scal[OR_SIGNED_EMIT] += s;
+    uint32_t e = 0;
+    int n_relax = 0;
+    double X = 0.0;
+    bool truncated = false;
+    // adjoint bookkeeping
+    periods.clear();
+    if (P->want_grad) periods.push_back({bin, 0.0, 0.0});
+    int n_res = 0;
+    double sum_x_res = 0.0;
+    double PA = 0.0, PB = 0.0;
+    size_t mi = 0;
+    if (P->transient) {
+      while (mi < S.t_meas_ps.size() && S.t_meas_ps[mi] < t_now) ++mi;
+    }
+    for (;;) {
+      if ((uint64_t)e + 1 >= P->max_events) { truncated = true; break; }
+      double db;
+      int face;
+      first_hit(g, x, u, &db, &face);
+      const double v = t.v_nm[bin];
+      bool final_seg = false;
+      bool relax;
+      double seg;
+      if (P->transient) {
+        double d_end = (S.t_max_ps - t_now) * v;
+        if (d_end <= d_rel && d_end <= db) { final_seg = true; seg = d_end; relax = false; }
+        else if (d_rel < db) { seg = d_rel; relax = true; }
+        else { seg = db; relax = false; }
+      } else {
+        if (d_rel < db) { seg = d_rel; relax = true; }
+        else { seg = db; relax = false; }
+      }
+      // ---- tallies of this flight
+      if (P->transient) {
+        double t_end = t_now + seg / v;
+        while (mi < S.t_meas_ps.size() &&
+               (S.t_meas_ps[mi] < t_end || (final_seg && S.t_meas_ps[mi] <= t_end))) {
+          double dist = v * (S.t_meas_ps[mi] - t_now);
+          double pm[3];
+          for (int a = 0; a < 3; ++a) pm[a] = x[a] + dist * u[a];
+          int ix = (int)std::floor(pm[0] / (g.L[0] / (double)nx));
+          int iy = (int)std::floor(pm[1] / (g.L[1] / (double)ny));
+          int iz = (int)std::floor(pm[2] / (g.L[2] / (double)nzg));
+          ix = std::min(std::max(ix, 0), nx - 1);
+          iy = std::min(std::max(iy, 0), ny - 1);
+          iz = std::min(std::max(iz, 0), nzg - 1);
+          size_t c = ((size_t)mi * ncell_t + ((size_t)iz * ny + iy) * nx + ix) * 4;
+          out.snap[c + 0] += s;
+          out.snap[c + 1] += (s * v) * u[0];
+          out.snap[c + 2] += (s * v) * u[1];
+          out.snap[c + 3] += (s * v) * u[2];
+          ++mi;
+        }
+        t_now = t_end;
+      } else {
+        double contrib = (s * seg) * u[ta];
+        double Xb = X;
+        X += contrib;
+        if (P->n_bins > 0 && O->qbin_sum) out.qbin[bin] += contrib;
+        if (cells) {
+          int ca = P->cell_axis;
+          double z0 = x[ca];
+          double z1 = z0 + seg * u[ca];
+          double inv_v = t.inv_v[bin];
+          if (u[ca] == 0.0) {
+            int c = (int)std::floor(z0 / h_cell);
+            c = std::min(std::max(c, 0), P->n_cells - 1);
+            out.T[c] += (s * seg) * inv_v;
+            for (int b = 0; b < 3; ++b) out.Q[(size_t)c * 3 + b] += (s * seg) * u[b];
+          } else {
+            double zlo = std::min(z0, z1), zhi = std::max(z0, z1);
+            int clo = std::min(std::max((int)std::floor(zlo / h_cell), 0), P->n_cells - 1);
+            int chi = std::min(std::max((int)std::floor(zhi / h_cell), 0), P->n_cells - 1);
+            double au = std::fabs(u[ca]);
+            for (int c = clo; c <= chi; ++c) {
+              double lo = std::max(zlo, c * h_cell);
+              double hi = std::min(zhi, (c + 1) * h_cell);
+              if (c == P->n_cells - 1) hi = zhi;
+              if (c == 0) lo = zlo;
+              double ov = hi - lo;
+              if (ov <= 0.0) continue;
+              double l = ov / au;
+              out.T[c] += (s * l) * inv_v;
+              for (int b = 0; b < 3; ++b) out.Q[(size_t)c * 3 + b] += (s * l) * u[b];
+            }
+          }
+        }
+        if (P->want_grad) {
+          double score = seg / t.lam_nm[bin];
+          if (relax) score = score - 1.0;
+          Period& pr = periods.back();
+          pr.A += score;
+          pr.B += score * Xb;
+        }
+      }
+      // ---- move
+      for (int a = 0; a < 3; ++a) x[a] = x[a] + seg * u[a];
+      if (final_seg) break;
+      ++e;
+      if (relax) {
+        ++n_relax;
+        if (P->n_scat_max > 0 && n_relax >= P->n_scat_max) break;
+        ctr[2] = e;
+        ctr[3] = 0; philox4x32_10(ctr, k0, k1, w);
+        ctr[3] = 1; philox4x32_10(ctr, k0, k1, w1);
+        bin = alias_draw(t.relax, n, w[0], w[1], w1[0]);
+        dir_about_axis(u, 2, 1.0, 1.0 - 2.0 * oc32(w[2]), w[3]);
+        d_rel = t.lam_nm[bin] * (-std::log(oc53(w1[1], w1[2])));
+        if (P->want_grad) {
+          periods.push_back({bin, -1.0, -X});
+          ++n_res;
+          sum_x_res += X;
+        }
+        continue;
+      }
+      d_rel = d_rel - seg;
+      if (face < 6) {
+        int a = kFaceAxis[face];
+        x[a] = kFaceIsMax[face] ? g.L[a] : 0.0;
+        int ty = g.type[face];
+        if (ty == 0) {
+          out.scal[OR_ABSORBED] += 1.0;
+          out.scal[OR_SIGNED_ABS] += s;
+          break;
+        } else if (ty == 2) {
+          x[a] = kFaceIsMax[face] ? 0.0 : g.L[a];
+        } else {
+          ctr[2] = e;
+          ctr[3] = 0; philox4x32_10(ctr, k0, k1, w);
+          if ((uint64_t)w[0] < g.pthr[face]) {
+            u[a] = -u[a];
+          } else {
+            dir_about_axis(u, a, kFaceIsMax[face] ? -1.0 : 1.0, std::sqrt(oc32(w[2])), w[3]);
+          }
+        }
+      } else {
+        // pore wall: outward normal of the cylinder points into the solid
+        double nx0 = x[0] - g.cx, ny0 = x[1] - g.cy;
+        double len = std::sqrt(nx0 * nx0 + ny0 * ny0);
+        nx0 = nx0 / len;
+        ny0 = ny0 / len;
+        ctr[2] = e;
+        ctr[3] = 0; philox4x32_10(ctr, k0, k1, w);
+        bool spec = (uint64_t)w[0] < g.pthr_pore;
+        if (P->want_grad) {
+          double sc = spec ? 1.0 / g.p_pore : -1.0 / (1.0 - g.p_pore);
+          PA += sc;
+          PB += sc * X;
+        }
+        if (spec) {
+          double un = u[0] * nx0 + u[1] * ny0;
+          u[0] = u[0] - (2.0 * un) * nx0;
+          u[1] = u[1] - (2.0 * un) * ny0;
+        } else {
+          double mu = std::sqrt(oc32(w[2]));
+          double sn = std::sqrt(std::max(0.0, 1.0 - mu * mu));
+          double phi = kTwoPi * co32(w[3]);
+          double sc = sn * std::cos(phi);
+          u[0] = mu * nx0 - sc * ny0;
+          u[1] = mu * ny0 + sc * nx0;
+          u[2] = sn * std::sin(phi);
+        }
+      }
+    }
+    const uint64_t nev = (uint64_t)e + 1;
+    out.scal[OR_EVENTS] += (double)nev;
+    if ((double)nev > out.scal[OR_MAXEV]) out.scal[OR_MAXEV] = (double)nev;
+    if (truncated) out.scal[OR_TRUNC] += 1.0;
+    out.scal[OR_SUMX] += X;
+    out.scal[OR_SUMX2] += X * X;
+    if (O->events_pp) O->events_pp[pid - P->pid_begin] = (uint32_t)std::min<uint64_t>(nev, 0xFFFFFFFFu);
+    if (O->X_pp) O->X_pp[pid - P->pid_begin] = X;
+    if (P->want_grad) {
+      for (const Period& pr : periods) out.G[pr.bin] += pr.A * X - pr.B;
+      double R = (double)n_res * X - sum_x_res;
+      out.scal[OR_RSUM] += R;
+      double gp = PA * X - PB;
+      out.scal[OR_GP] += gp;
+      out.scal[OR_GP2] += gp * gp;
+      for (int kd = 0; kd < P->n_dirs; ++kd) {
+        const double* d = P->dirs + (size_t)kd * n;
+        double val = 0.0;
+        for (const Period& pr : periods) val += (pr.A * X - pr.B) * d[pr.bin];
+        val += R * S.dpi_dirs[kd];
+        out.dsum[kd] += val;
+        out.dsum2[kd] += val * val;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+void or_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  philox4x32_10(ctr, key[0], key[1], out);
+}
+
+double or_dEdT(double omega, double T) { return dEdT(omega, T); }
+
+// Alias table of arbitrary weights (for the table tests).
+void or_alias(int n, const double* w, double* prob, uint64_t* thr, int32_t* alias) {
+  std::vector<double> ww(w, w + n);
+  Alias a = build_alias(ww);
+  for (int i = 0; i < n; ++i) { prob[i] = a.prob[i]; thr[i] = a.thr[i]; alias[i] = a.alias[i]; }
+}
+
+int or_alias_draw(int n, const uint64_t* thr, const int32_t* alias, uint32_t wcol, uint32_t lo, uint32_t hi) {
+  Alias a;
+  a.thr.assign(thr, thr + n);
+  a.alias.assign(alias, alias + n);
+  return alias_draw(a, n, wcol, lo, hi);
+}
+
+// Material tables: C[n]; for table k in (emit ~ C v, init ~ C, relax ~ C/tau):
+// prob[k*n+i], thr[k*n+i], alias[k*n+i]; sums = (C_tot, sum C v, sum C/tau).
+int or_tables(const or_params* P, double* C, double* prob, uint64_t* thr, int32_t* alias, double* sums) {
+  Tables t;
+  if (build_tables(P, t)) return 1;
+  const int n = t.n;
+  const Alias* al[3] = {&t.emit, &t.init, &t.relax};
+  for (int i = 0; i < n; ++i) C[i] = t.C[i];
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < n; ++i) {
+      prob[k * n + i] = al[k]->prob[i];
+      thr[k * n + i] = al[k]->thr[i];
+      alias[k * n + i] = al[k]->alias[i];
+    }
+  sums[0] = t.C_tot; sums[1] = t.sum_Cv; sums[2] = t.sum_Ct;
+  return 0;
+}
+
+// Geometry probe for the unit tests: x, u in nm.
+int or_first_hit(const or_params* P, const double x[3], const double u[3], double* dist, int* face) {
+  Tables t;
+  Setup S;
+  Geo& g = S.g;
+  for (int a = 0; a < 3; ++a) g.L[a] = P->L[a] * 1e9;
+  g.pore = P->pore != 0;
+  g.cx = P->pore_c[0] * 1e9; g.cy = P->pore_c[1] * 1e9; g.r = P->pore_r * 1e9; g.r2 = g.r * g.r;
+  first_hit(g, x, u, dist, face);
+  return 0;
+}
+
+// Source energies: out[0] = E_tot, out[1] = V_solid, out[2..] = E per source.
+int or_sources(const or_params* P, double* out, int* n_src) {
+  Tables t;
+  if (build_tables(P, t)) return 1;
+  Setup S;
+  int rc = setup(P, t, S);
+  if (rc) return 10 + rc;
+  out[0] = S.E_tot;
+  out[1] = S.g.V_solid_m3;
+  for (size_t k = 0; k < S.src.size(); ++k) out[2 + k] = S.src[k].E;
+  *n_src = (int)S.src.size();
+  return 0;
+}
+
+int or_run(const or_params* P, or_out* O) {
+  Tables t;
+  if (build_tables(P, t)) return 1;
+  Setup S;
+  int rc = setup(P, t, S);
+  if (rc) return 10 + rc;
+  if (P->transient && (P->grid[0] < 1 || P->grid[1] < 1 || P->grid[2] < 1)) return 20;
+  if (P->want_grad && P->transient) return 21;
+  const uint64_t total = P->pid_end - P->pid_begin;
+  int nt = P->n_threads > 0 ? P->n_threads : (int)std::thread::hardware_concurrency();
+  if (nt < 1) nt = 1;
+  if ((uint64_t)nt > total) nt = (int)std::max<uint64_t>(1, total);
+  const size_t ncell_t = (size_t)P->grid[0] * P->grid[1] * P->grid[2];
+  std::vector<Partial> parts(nt);
+  for (auto& p : parts) {
+    if (!P->transient && P->n_cells > 0) { p.T.assign(P->n_cells, 0.0); p.Q.assign((size_t)P->n_cells * 3, 0.0); }
+    if (O->qbin_sum) p.qbin.assign(P->n_bins, 0.0);
+    if (P->transient) p.snap.assign((size_t)P->n_times * ncell_t * 4, 0.0);
+    if (P->want_grad) { p.G.assign(P->n_bins, 0.0); p.dsum.assign(P->n_dirs, 0.0); p.dsum2.assign(P->n_dirs, 0.0); }
+  }
+  std::vector<std::thread> th;
+  for (int i = 0; i < nt; ++i) {
+    uint64_t a = P->pid_begin + total * (uint64_t)i / (uint64_t)nt;
+    uint64_t b = P->pid_begin + total * (uint64_t)(i + 1) / (uint64_t)nt;
+    th.emplace_back([&, a, b, i]() { trace_range(P, t, S, a, b, parts[i], O); });
+  }
+  for (auto& x : th) x.join();
+  for (int k = 0; k < OR_NSCAL; ++k) O->scal[k] = 0.0;
+  for (int i = 0; i < nt; ++i) {
+    const Partial& p = parts[i];
+    for (int k = 0; k < OR_NSCAL; ++k) {
+      if (k == OR_MAXEV) O->scal[k] = std::max(O->scal[k], p.scal[k]);
+      else O->scal[k] += p.scal[k];
+    }
+    if (O->T_sum) for (size_t c = 0; c < p.T.size(); ++c) O->T_sum[c] += p.T[c];
+    if (O->Q_sum) for (size_t c = 0; c < p.Q.size(); ++c) O->Q_sum[c] += p.Q[c];
+    if (O->qbin_sum) for (size_t c = 0; c < p.qbin.size(); ++c) O->qbin_sum[c] += p.qbin[c];
+    if (O->snap) for (size_t c = 0; c < p.snap.size(); ++c) O->snap[c] += p.snap[c];
+    if (O->G) for (size_t c = 0; c < p.G.size(); ++c) O->G[c] += p.G[c];
+    if (O->dir_sum) for (size_t c = 0; c < p.dsum.size(); ++c) { O->dir_sum[c] += p.dsum[c]; O->dir_sum2[c] += p.dsum2[c]; }
+  }
+  O->scal[OR_ETOT] = S.E_tot;
+  O->scal[OR_CTOT] = t.C_tot;
+  O->scal[OR_VSOLID] = S.g.V_solid_m3;
+  (void)nt;
+  return 0;
+}
+
+}  // extern "C"

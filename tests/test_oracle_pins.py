@@ -1,0 +1,386 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: each test checks it against a
+published value (Philox known answers), a closed form or an independent
+deterministic solve (exponential-integral Nystrom, discrete ordinates,
+kinetic theory, Fuchs-Sondheimer, the paper's ballistic Eq. Analytical_T),
+an exact invariant (signed-energy and transient energy conservation,
+partition invariance) or brute force on tiny inputs (alias tables, ray
+hits).  Statistical checks use batch means over disjoint particle ranges.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import closed_forms as cf
+from inputs import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+KB = 1.380649e-23
+HBAR = 1.054571817e-34
+
+
+def _batches(fn, n, nb=8):
+    """Run fn(pid_begin, pid_end) over nb disjoint ranges; return mean and SE
+    of the per-batch results (each scaled to the full N)."""
+    vals = []
+    for b in range(nb):
+        a, e = n * b // nb, n * (b + 1) // nb
+        vals.append(fn(a, e))
+    v = np.array(vals)
+    return v.mean(axis=0), v.std(axis=0, ddof=1) / math.sqrt(nb)
+
+
+# ------------------------------------------------------------------ RNG
+def test_philox_known_answers():
+    rows = []
+    with open(os.path.join(HERE, "golden", "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            rows.append([int(x, 16) for x in line.split()])
+    assert len(rows) == 3
+    for r in rows:
+        out = oracle.philox(r[0:4], r[4:6])
+        assert out.tolist() == r[6:10]
+
+
+def test_philox_counter_sensitivity():
+    # every counter word and key word changes every output word (avalanche)
+    base = oracle.philox([1, 2, 3, 4], [5, 6])
+    for i in range(6):
+        c = [1, 2, 3, 4, 5, 6]
+        c[i] ^= 1
+        o = oracle.philox(c[:4], c[4:])
+        assert all(int(a) != int(b) for a, b in zip(o, base))
+
+
+# ------------------------------------------------------------------ tables
+def _exact_alias_law(thr, al):
+    n = len(thr)
+    P = [Fraction(0)] * n
+    two64 = 2 ** 64
+    for j in range(n):
+        keep = Fraction(int(thr[j]), two64) if int(thr[j]) != two64 - 1 else Fraction(1)
+        if int(al[j]) == j:
+            keep = Fraction(1)
+        P[j] += keep / n
+        P[int(al[j])] += (1 - keep) / n
+    return P
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_alias_reproduces_pmf_exactly(seed):
+    rng = np.random.default_rng(seed)
+    n = 257
+    w = rng.exponential(size=n) ** 4
+    w[5] = 0.0
+    w[17] = 1e-30
+    prob, thr, al = oracle.alias_table(w)
+    P = _exact_alias_law(thr, al)
+    target = w / w.sum()
+    err = max(abs(float(P[i]) - target[i]) for i in range(n))
+    assert err <= 1e-15
+    assert sum(P) == 1
+
+
+def test_alias_draw_brute_force_tiny():
+    # n = 3: enumerate the column word on a grid and the threshold word's
+    # top bits; the empirical law converges to w / sum(w)
+    w = np.array([0.2, 0.5, 0.3])
+    prob, thr, al = oracle.alias_table(w)
+    counts = np.zeros(3)
+    grid = 600
+    for a in range(grid):
+        wcol = int((a + 0.5) / grid * 2 ** 32)
+        for b in range(grid):
+            hi = int((b + 0.5) / grid * 2 ** 32)
+            counts[oracle.alias_draw(thr, al, wcol, 0, hi)] += 1
+    assert np.allclose(counts / counts.sum(), w / w.sum(), atol=2e-3)
+
+
+def test_dEdT_derivative_and_classical_limit():
+    T = 300.0
+    for w in [1e11, 1e12, 1e13, 5e13, 1e14]:
+        e = lambda TT: HBAR * w / math.expm1(HBAR * w / (KB * TT))
+        h = 1e-3
+        num = (e(T + h) - e(T - h)) / (2 * h)
+        assert oracle.dEdT(w, T) == pytest.approx(num, rel=1e-7)
+    assert oracle.dEdT(1e6, 300.0) == pytest.approx(KB, rel=1e-12)
+
+
+def test_heat_capacity_classical_limit_per_bin():
+    # C_i = D_i dE/dT(omega_i) d_omega_i and dE/dT -> k_B as hbar omega / k_B T -> 0
+    m = W.bvk_holland(T=300.0)
+    m.T_lin = 1.0e7
+    tb = oracle.tables(m)
+    ratio = tb["C"] / (m.D * m.domega)
+    assert np.allclose(ratio, KB, rtol=1e-8, atol=0)
+    m.T_lin = 300.0
+    tb3 = oracle.tables(m)
+    x = HBAR * m.omega / (KB * 300.0)
+    assert np.allclose(tb3["C"] / (m.D * m.domega), KB * x * x * np.exp(x) / np.expm1(x) ** 2, rtol=1e-12)
+
+
+def test_dos_integral_per_branch():
+    # Eq. DOS with the 3-D normalisation: int D d omega = k_max^3 / (6 pi^2)
+    # (midpoint bins converge as sqrt(h) at the van Hove edge, so a fine grid)
+    m = W.bvk_holland(n_per_branch=1_000_000)
+    kmax = 2 * math.pi / W.SI_LATTICE_A
+    n = 1_000_000
+    for b in range(3):
+        s = np.sum(m.D[b * n:(b + 1) * n] * m.domega[b * n:(b + 1) * n])
+        assert s == pytest.approx(kmax ** 3 / (6 * math.pi ** 2), rel=2e-3)
+
+
+def test_format2_heat_capacity_passthrough():
+    m = W.gray(6000.0, 100e-9, C=1.234e6)
+    tb = oracle.tables(m)
+    assert tb["C"][0] == 1.234e6
+
+
+# ------------------------------------------------------------------ geometry
+def test_first_hit_box_faces_and_ties():
+    g = W.adiabatic_box((100e-9, 100e-9, 50e-9))
+    d, f = oracle.first_hit(g, [50, 50, 25], [0, 0, 1])
+    assert (d, f) == (25.0, 5)                  # z = Lz is paper ID 6
+    d, f = oracle.first_hit(g, [50, 50, 25], [0, -1, 0])
+    assert (d, f) == (50.0, 0)                  # y = 0 is paper ID 1
+    s = 1 / math.sqrt(2)
+    d, f = oracle.first_hit(g, [50, 50, 25], [s, s, 0])   # corner x=Lx, y=Ly tie
+    assert f == 1 and d == pytest.approx(50 * math.sqrt(2))
+    d, f = oracle.first_hit(g, [0, 50, 25], [1, 0, 0])    # on face x=0, moving in
+    assert (d, f) == (100.0, 1)
+
+
+def test_first_hit_pore_cylinder():
+    g = W.pore_lattice(100e-9, 0.25, 200e-9)
+    r = g.pore_r * 1e9
+    d, f = oracle.first_hit(g, [10, 50, 100], [1, 0, 0])
+    assert f == 6 and d == pytest.approx(40 - r, rel=1e-14)
+    # tangent-missing ray passes above the pore
+    d, f = oracle.first_hit(g, [10, 50 + r + 1e-6, 100], [1, 0, 0])
+    assert f == 1
+    # on the pore wall moving outward: no pore hit
+    d, f = oracle.first_hit(g, [50 - r, 50, 100], [-1, 0, 0])
+    assert f == 3
+    # oblique: compare with the quadratic root
+    x = np.array([5.0, 20.0, 3.0]); u = np.array([0.6, 0.64, 0.48])
+    d, f = oracle.first_hit(g, x, u)
+    a = u[0] ** 2 + u[1] ** 2; b = (x[0] - 50) * u[0] + (x[1] - 50) * u[1]
+    c = (x[0] - 50) ** 2 + (x[1] - 50) ** 2 - r * r
+    assert f == 6 and d == pytest.approx((-b - math.sqrt(b * b - a * c)) / a, rel=1e-12)
+
+
+def test_solid_volume_and_source_energies():
+    g = W.pore_lattice(100e-9, 0.25, 200e-9)
+    m = W.gray(6000.0, 100e-9, C=1e6)
+    s = oracle.sources(m, g)
+    assert s["V_solid"] == pytest.approx(100e-9 * 100e-9 * 200e-9 * 0.75, rel=1e-12)
+    # body source rate (V/2)|grad T| sum C v  (Eq. grad_flux integrated over both signs)
+    assert s["E_tot"] == pytest.approx(0.5 * s["V_solid"] * 1e6 * 1e6 * 6000.0, rel=1e-12)
+    sl = W.slab_z(100e-9, 300.5, 299.5)
+    s2 = oracle.sources(m, sl)
+    A = 100e-9 * 100e-9
+    # isothermal wall: A/4 sum C v |dT|  (Eq. iso_flux)
+    assert s2["E"] == pytest.approx([0.25 * A * 6e9 * 0.5] * 2, rel=1e-12)
+
+
+# ------------------------------------------------------------------ closed forms
+def test_gray_slab_closed_forms_agree_and_limits():
+    psi_ny = cf.gray_slab_psi(1.0)
+    _, _, psi_do = cf.gray_slab_ordinates(1.0, 16, 200, 1e-11)
+    assert psi_ny == pytest.approx(psi_do, abs=2e-5)
+    assert cf.gray_slab_psi(1e-3) == pytest.approx(1.0, abs=2e-3)
+    t = 20.0
+    assert cf.gray_slab_psi(t) == pytest.approx(4.0 / (3.0 * t + 4.0), rel=0.02)
+
+
+def test_fs_limits():
+    assert cf.fs_suppression(1e4)[0] == pytest.approx(1.0 - 3.0 / (8.0 * 1e4), rel=1e-6)
+    assert cf.fs_suppression(1e-4)[0] == pytest.approx(0.75e-4 * math.log(1e4) + 0.75e-4 * (1.5 - 0.5772156649), rel=0.05)
+    assert cf.fs_suppression(0.5, p=1.0 - 1e-12)[0] == pytest.approx(1.0, abs=1e-6)
+
+
+# ------------------------------------------------------------------ Monte Carlo vs closed forms
+def test_gray_slab_flux_and_temperature():
+    wl = W.gray_slab_c1(n=100_000)
+    mat, g, run = wl.material, wl.geometries[0], wl.run
+    r = oracle.run_steady(mat, g, run)
+    psi = cf.gray_slab_psi(1.0)
+    q_exact = psi * 1e6 * 6000.0 * 1.0 / 4.0
+    assert abs(r["q_mean"] - q_exact) < 3.5 * r["q_se"]
+    # temperature profile vs the Nystrom solution, cell averages, batch-mean SE
+    def f(a, e):
+        rr = oracle.run_steady(mat, g, run, pid_begin=a, pid_end=e)
+        return rr["T"] * (run.n / (e - a))
+    Tm, Tse = _batches(f, run.n)
+    t, phi, _ = cf.gray_slab_nystrom(1.0, 801)
+    edges = np.linspace(0, 1.0, 51)
+    Tex = np.array([np.mean(np.interp(np.linspace(a, b, 41), t, phi)) - 0.5 for a, b in zip(edges[:-1], edges[1:])])
+    z = (Tm - Tex) / Tse
+    assert np.max(np.abs(z)) < 4.5
+    assert np.mean(z ** 2) < 2.0
+
+
+def test_signed_energy_conservation_slab():
+    wl = W.gray_slab_c1(n=20_000)
+    r = oracle.run_steady(wl.material, wl.geometries[0], wl.run)
+    sc = r["scal"]
+    assert sc[oracle.ABSORBED] == wl.run.n
+    assert sc[oracle.SIGNED_ABS] == sc[oracle.SIGNED_EMIT]
+
+
+def test_kinetic_limit_gray():
+    m = W.gray(6000.0, 100e-9, C=1e6)
+    g = W.film(1e-6)
+    g.face_type = [W.PERIODIC] * 6
+    run = W.SteadyRun(n=400_000, seed=11, tally_axis=1, n_scat_max=3)
+    r = oracle.run_steady(m, g, run)
+    k = cf.kinetic_kappa([1e6], [6000.0], [100e-9 / 6000.0])
+    assert abs(r["kappa"] - k) < 3.5 * r["kappa_se"]
+    assert r["kappa_se"] < 0.01 * k
+
+
+def test_kinetic_limit_bvk():
+    m = W.bvk_holland()
+    tb = oracle.tables(m)
+    g = W.film(1e-6)
+    g.face_type = [W.PERIODIC] * 6
+    run = W.SteadyRun(n=1_000_000, seed=12, tally_axis=1, n_scat_max=2)
+    r = oracle.run_steady(m, g, run)
+    k = cf.kinetic_kappa(tb["C"], m.v, m.tau)
+    assert k == pytest.approx(130.69, abs=0.01)
+    assert abs(r["kappa"] - k) < 3.5 * r["kappa_se"]
+
+
+@pytest.mark.parametrize("d", [10e-9, 100e-9, 1e-6])
+def test_fuchs_sondheimer_films_bvk(d):
+    m = W.bvk_holland()
+    tb = oracle.tables(m)
+    run = W.SteadyRun(n=300_000, seed=13, tally_axis=1, n_scat_max=10, max_events=10 ** 8)
+    r = oracle.run_steady(m, W.film(d), run)
+    fs = cf.fuchs_sondheimer(tb["C"], m.v, m.tau, d)
+    assert r["truncated"] == 0
+    assert abs(r["kappa"] - fs) < 3.5 * r["kappa_se"]
+
+
+def test_fuchs_sondheimer_partially_specular_gray():
+    m = W.gray(6000.0, 300e-9, C=1e6)
+    run = W.SteadyRun(n=400_000, seed=14, tally_axis=1, n_scat_max=4)
+    r = oracle.run_steady(m, W.film(100e-9, p=0.5), run)
+    fs = cf.fuchs_sondheimer([1e6], [6000.0], [300e-9 / 6000.0], 100e-9, p=0.5)
+    assert abs(r["kappa"] - fs) < 3.5 * r["kappa_se"]
+
+
+def test_partition_invariance():
+    wl = W.gray_slab_c1(n=10_000)
+    mat, g, run = wl.material, wl.geometries[0], wl.run
+    full = oracle.run_steady(mat, g, run, per_particle=True)
+    a = oracle.run_steady(mat, g, run, pid_begin=0, pid_end=4000, per_particle=True)
+    b = oracle.run_steady(mat, g, run, pid_begin=4000, pid_end=10_000, per_particle=True)
+    assert np.array_equal(full["events_pp"], np.concatenate([a["events_pp"], b["events_pp"]]))
+    assert np.array_equal(full["X_pp"], np.concatenate([a["X_pp"], b["X_pp"]]))
+    assert np.allclose(full["raw_T"], a["raw_T"] + b["raw_T"], rtol=1e-12, atol=1e-9)
+
+
+def test_ballistic_transient_matches_eq_analytical_T():
+    wl = W.ballistic_transient_e1(n=400_000, nz=30)
+    mat, g, run = wl.material, wl.geometries[0], wl.run
+
+    def f(a, e):
+        rr = oracle.run_transient(mat, g, run, pid_begin=a, pid_end=e)
+        return rr["tally"][:, :, 0, 0, 0] * (run.n / (e - a))
+    Tm, Tse = _batches(f, run.n)
+    L = 3e-6
+    zc = (np.arange(30) + 0.5) * L / 30
+    for m, t in enumerate(run.t_meas):
+        fine = np.linspace(0, L, 30 * 50 + 1)
+        ex = cf.ballistic_transient(fine, t, L, 12360.0, 3.0, -3.0)
+        exc = np.array([ex[i * 50:(i + 1) * 50 + 1].mean() for i in range(30)])
+        ok = Tse[m] > 0
+        z = (Tm[m][ok] - exc[ok]) / Tse[m][ok]
+        assert np.max(np.abs(z)) < 5.0, (t, z)
+        assert np.all(np.abs(Tm[m][~ok] - exc[~ok]) < 1e-12)
+
+
+def test_transient_energy_conservation():
+    wl = W.transient_box_c3(n=4000, grid=(8, 8, 4), n_times=20)
+    mat, g, run = wl.material, wl.geometries[0], wl.run
+    r = oracle.run_transient(mat, g, run)
+    Ttot = r["tally"][..., 0].sum(axis=(1, 2, 3)) * r["C_tot"] * r["V_cell"]
+    assert np.allclose(Ttot, r["E_tot"], rtol=1e-12)
+
+
+@pytest.mark.slow
+def test_transient_gray_long_time_fourier():
+    # short mean free path: late-time profile follows the heat equation with
+    # alpha = v Lambda / 3 (Gaussian centred on the adiabatic top face)
+    m = W.gray(6000.0, 5e-9, C=1e6)
+    g = W.adiabatic_box((2e-6, 2e-6, 1e-6))
+    g.gauss, g.gauss_c, g.gauss_sigma, g.gauss_dT = True, (1e-6, 1e-6, 1e-6), 100e-9, 1.0
+    t = np.array([0.5e-9, 1.0e-9])
+    run = W.TransientRun(n=100_000, seed=21, t_max=float(t[-1]), t_meas=t, grid=(20, 20, 10))
+    r = oracle.run_transient(m, g, run)
+    alpha = 6000.0 * 5e-9 / 3.0
+    # compare the energy-weighted mean square radius (exact for the heat equation)
+    xc = (np.arange(20) + 0.5) * 1e-7
+    zc = (np.arange(10) + 0.5) * 1e-7
+    Z, Y, X = np.meshgrid(zc, xc, xc, indexing="ij")
+    r2 = (X - 1e-6) ** 2 + (Y - 1e-6) ** 2
+    for k, tk in enumerate(t):
+        T = r["tally"][k, ..., 0]
+        m_r2 = (T * r2).sum() / T.sum()
+        s2 = 100e-9 ** 2 + 2 * alpha * tk
+        expect = 2 * s2 + 2 * (1e-7 ** 2) / 12      # two lateral axes, + cell-binning variance
+        assert m_r2 == pytest.approx(expect, rel=0.06)
+
+
+# ------------------------------------------------------------------ gradient
+def _small_bvk():
+    return W.bvk_holland(n_per_branch=8)
+
+
+@pytest.mark.slow
+def test_lr_gradient_matches_crn_finite_difference_tau():
+    m = _small_bvk()
+    n = m.n_bins
+    g = W.pore_lattice(100e-9, 0.25, 200e-9)
+    run = W.SteadyRun(n=200_000, seed=31, tally_axis=1, n_scat_max=4, max_events=10 ** 7)
+    rng = np.random.default_rng(3)
+    dirs = np.vstack([rng.choice([-1.0, 1.0], size=n), np.eye(n)[n - 2], np.eye(n)[3]])
+    r = oracle.run_steady(m, g, run, grad=True, dirs=dirs)
+    # per-direction LR value must equal the projection of the full gradient
+    assert np.allclose(r["dkappa_dir"], dirs @ r["dkappa_dlogtau"], rtol=1e-9, atol=1e-12)
+    h = 1e-2
+    for k in range(dirs.shape[0]):
+        rp = oracle.run_steady(m.scaled_tau(h * dirs[k]), g, run, per_particle=True)
+        rm = oracle.run_steady(m.scaled_tau(-h * dirs[k]), g, run, per_particle=True)
+        fd = (rp["kappa"] - rm["kappa"]) / (2 * h)
+        dpp = (rp["X_pp"] - rm["X_pp"]) / (2 * h)
+        fd_se = abs(rp["kappa"] / rp["X_pp"].sum()) * dpp.std(ddof=1) * math.sqrt(run.n)
+        se = math.hypot(fd_se, r["dkappa_dir_se"][k])
+        assert abs(r["dkappa_dir"][k] - fd) < 4.0 * se, (k, r["dkappa_dir"][k], fd, se)
+
+
+@pytest.mark.slow
+def test_lr_gradient_matches_crn_finite_difference_specularity():
+    m = W.gray(6000.0, 200e-9, C=1e6)
+    run = W.SteadyRun(n=200_000, seed=32, tally_axis=1, n_scat_max=4, max_events=10 ** 7)
+    p0, h = 0.5, 1e-2
+    g = W.pore_lattice(100e-9, 0.25, 200e-9, p_pore=p0)
+    r = oracle.run_steady(m, g, run, grad=True)
+    gp = W.pore_lattice(100e-9, 0.25, 200e-9, p_pore=p0 + h)
+    gm = W.pore_lattice(100e-9, 0.25, 200e-9, p_pore=p0 - h)
+    rp = oracle.run_steady(m, gp, run, per_particle=True)
+    rm = oracle.run_steady(m, gm, run, per_particle=True)
+    fd = (rp["kappa"] - rm["kappa"]) / (2 * h)
+    dpp = (rp["X_pp"] - rm["X_pp"]) / (2 * h)
+    fd_se = abs(rp["kappa"] / rp["X_pp"].sum()) * dpp.std(ddof=1) * math.sqrt(run.n)
+    se = math.hypot(fd_se, r["dkappa_dp_se"])
+    assert r["dkappa_dp"] > 0           # specular pores conduct better
+    assert abs(r["dkappa_dp"] - fd) < 4.0 * se
