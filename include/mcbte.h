@@ -1,0 +1,260 @@
+/*
+ * mcbte.h -- C ABI of the GB300 deviational Monte Carlo solver for the
+ * linearised phonon Boltzmann transport equation (arXiv:2104.03573, MCBTE).
+ *
+ * The library traces independent signed deviational energy particles
+ * (Sec. 3, Eq. deviational_approx): emission from isothermal walls, an
+ * initial condition or a control-gradient body source, straight flights,
+ * exponential relaxation clocks, relaxation resampling ~ C/tau, adiabatic /
+ * isothermal / periodic boundaries and steady track-length or transient
+ * snapshot tallies.  All tracing, table building, source setup and
+ * finalisation run in CUDA kernels on one GPU (sm_103a).
+ *
+ * Conventions for every call:
+ *   - Return an mcbte_status; 0 is success.  No call exits, traps or prints.
+ *   - mcbte_last_error() gives a message for the last failure of the calling
+ *     host thread.
+ *   - Handles are opaque, owned by the library, released by *_destroy.
+ *   - Descriptor arrays (material columns, wall data, t_meas, n_particles)
+ *     are HOST memory, read during the call and not retained.
+ *   - Output buffers are owned by the caller.  They are all device memory
+ *     (on_host = 0; results are written asynchronously on `stream`) or all
+ *     host memory (on_host = 1; the call copies results back and
+ *     synchronises `stream` before returning).
+ *   - `stream` is a cudaStream_t; NULL is the legacy default stream.
+ *   - Units at the boundary are SI (m, s, K, W).
+ */
+#ifndef MCBTE_H
+#define MCBTE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* mcbte_stream; /* == cudaStream_t */
+
+typedef enum {
+  MCBTE_OK = 0,
+  MCBTE_ERR_INVALID_ARG = 1,   /* a descriptor or parameter is out of range  */
+  MCBTE_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed */
+  MCBTE_ERR_OOM = 3,           /* device allocation failed                   */
+  MCBTE_ERR_TIMEOUT = 4,       /* the run hit its wall-clock budget          */
+  MCBTE_WARN_TRUNCATED = 5,    /* some particles hit max_events (results are
+                                  written; the truncated count is in stats)  */
+  MCBTE_ERR_WORKSPACE = 6      /* caller workspace smaller than required     */
+} mcbte_status;
+
+/* Message of the last failure on this host thread; returns its length.
+ * Writes at most n bytes including the terminating NUL. */
+int mcbte_last_error(char* buf, size_t n);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int mcbte_version(void);
+
+/* ------------------------------------------------------------------ material
+ * Per-bin material table of the paper's mat_data.txt (Sec. 4.1): format 1
+ * (omega, DOS D, V_g, d_omega, tau) or format 2 (omega, V_g, tau, C).
+ * Create copies the columns to the device and builds, in FP64 on the GPU:
+ *   C_i = D_i * dE/dT(omega_i, T_lin) * d_omega_i   (Eq. BE_derivative, Eq. Nbin)
+ *         with dE/dT = k_B (x/2)^2 / sinh^2(x/2), x = hbar omega / (k_B T)
+ *   alias tables (Walker / Vose) for bins ~ C v (wall and body emission,
+ *   Eqs. iso_flux, grad_flux_sim), ~ C (initial condition, Eq. Nbin) and
+ *   ~ C / tau (relaxation resampling, Eq. n_scatt).
+ * Errors: n_bins < 1, any v <= 0 or tau <= 0, C < 0 (or D, d_omega < 0),
+ * sum C == 0, T_lin <= 0 when D is given -> MCBTE_ERR_INVALID_ARG.
+ * The call synchronises the device work it launches (legacy stream). */
+typedef struct {
+  int n_bins;
+  const double* omega;   /* [n_bins] rad/s                                  */
+  const double* v;       /* [n_bins] m/s, group velocity magnitude          */
+  const double* tau;     /* [n_bins] s, relaxation time                     */
+  const double* C;       /* [n_bins] J/(m^3 K), format 2; or NULL           */
+  const double* D;       /* [n_bins] s/(rad m^3), format 1 (used if C NULL) */
+  const double* domega;  /* [n_bins] rad/s, format 1                        */
+  double T_lin;          /* K, linearisation temperature (Sec. 4.4)         */
+} mcbte_material_desc;
+
+typedef struct mcbte_material mcbte_material;
+
+mcbte_status mcbte_material_create(const mcbte_material_desc* desc, mcbte_material** out);
+void mcbte_material_destroy(mcbte_material* m);
+int mcbte_material_n_bins(const mcbte_material* m);
+
+/* Copy the FP64 tables back to HOST buffers (any may be NULL):
+ * C[n]; for table k in {0: ~C v, 1: ~C, 2: ~C/tau}: prob[k*n+i] (Vose
+ * probability), thr[k*n+i] (64-bit keep threshold), alias[k*n+i];
+ * sums[3] = (sum C, sum C v, sum C/tau). Synchronous. */
+mcbte_status mcbte_material_tables(const mcbte_material* m, double* C, double* prob,
+                                   uint64_t* thr, int32_t* alias, double* sums);
+
+/* ------------------------------------------------------------------ geometry
+ * Axis-aligned box [0,Lx]x[0,Ly]x[0,Lz], one corner at the origin (Sec. 4.2),
+ * six faces in the paper's Boundary_prop.txt ID order (Sec. 4.3):
+ *   index 0..5 = ID 1..6 = y=0, x=Lx, y=Ly, x=0, z=0, z=Lz.
+ * Face types: isothermal (absorbing, emits at T_b; Sec. 3.5.4), adiabatic
+ * with specularity p (Eq. specular, Sec. 3.5.3), periodic (translation by
+ * the box length, spatially varying control, Eq. periodic_lin_final).
+ * Optional cylindrical pore parallel to z at (cx, cy) with radius r and
+ * specularity p_pore (boundary ID 7).  grad_T is the uniform control
+ * gradient of Sec. 2.5 (Eq. lin_spatial); it adds the body source of
+ * Eq. grad_flux.  At most one component may be non-zero.  gauss adds an
+ * initial-condition source dT exp(-|x-c|^2 / 2 sigma^2) (transient only).
+ * Errors: L <= 0, periodic faces not paired on an axis, p outside [0,1],
+ * pore not inside the cell (r >= min(Lx,Ly)/2 or centre off), more than one
+ * gradient component -> MCBTE_ERR_INVALID_ARG. */
+enum { MCBTE_FACE_ISOTHERMAL = 0, MCBTE_FACE_ADIABATIC = 1, MCBTE_FACE_PERIODIC = 2 };
+
+typedef struct {
+  double L[3];           /* m                                               */
+  int face_type[6];
+  double face_T[6];      /* K, isothermal faces                             */
+  double face_p[6];      /* specularity in [0,1], adiabatic faces           */
+  double T_eq;           /* K, control temperature                          */
+  double grad_T[3];      /* K/m                                             */
+  int pore;              /* 0 / 1                                           */
+  double pore_c[2];      /* m                                               */
+  double pore_r;         /* m                                               */
+  double pore_p;         /* specularity of the pore wall                    */
+  int gauss;             /* 0 / 1                                           */
+  double gauss_c[3];     /* m                                               */
+  double gauss_sigma;    /* m                                               */
+  double gauss_dT;       /* K                                               */
+} mcbte_geometry_desc;
+
+typedef struct mcbte_geometry mcbte_geometry;
+
+mcbte_status mcbte_geometry_create(const mcbte_geometry_desc* desc, mcbte_geometry** out);
+void mcbte_geometry_destroy(mcbte_geometry* g);
+
+/* ------------------------------------------------------------------ runs */
+enum { MCBTE_FP64_PLAIN = 0,      /* one thread per particle, FP64 throughout  */
+       MCBTE_FP32_TRACE = 1 };    /* persistent FP32 tracer, FP64 tallies      */
+
+/* stats[] layout of every run (per geometry for steady runs) */
+enum {
+  MCBTE_STAT_KAPPA = 0,       /* W/m/K, -q_mean / (dT/dx) along tally_axis (solid volume)  */
+  MCBTE_STAT_KAPPA_SE,        /* standard error of kappa                                  */
+  MCBTE_STAT_Q_MEAN,          /* W/m^2, mean flux along tally_axis over the solid (Eq. flux_x_steady) */
+  MCBTE_STAT_Q_SE,
+  MCBTE_STAT_SUMX,            /* sum_p X_p, X_p = sum s l_axis of particle p (nm)           */
+  MCBTE_STAT_SUMX2,
+  MCBTE_STAT_EVENTS,          /* emission + relaxations + boundary interactions           */
+  MCBTE_STAT_TRUNCATED,       /* particles stopped by max_events or the time budget       */
+  MCBTE_STAT_E_TOT,           /* W (steady) or J (transient): total deviational source     */
+  MCBTE_STAT_MAX_EVENTS,      /* largest per-particle event count                         */
+  MCBTE_STAT_KAPPA_CELL,      /* kappa normalised by the full cell volume                 */
+  MCBTE_STAT_SIGNED_EMITTED,  /* sum of emitted signs                                     */
+  MCBTE_STAT_SIGNED_ABSORBED, /* sum of signs absorbed at isothermal walls                */
+  MCBTE_STAT_STATUS,          /* 0 ok, 4 timeout, 5 truncated                              */
+  MCBTE_STAT_N,               /* particles traced                                         */
+  MCBTE_STAT_ABSORBED,        /* particles absorbed at isothermal walls                   */
+  MCBTE_NSTATS = 16
+};
+
+typedef struct {
+  const uint64_t* n_particles; /* HOST [n_geoms], each in [1, 2^32)                      */
+  uint64_t seed;               /* Philox key                                             */
+  int precision;               /* MCBTE_FP64_PLAIN or MCBTE_FP32_TRACE                    */
+  int n_scat_max;              /* terminate after this many relaxations; 0 = unlimited    */
+  uint64_t max_events;         /* per-particle event guard (0 = 2^32-1)                   */
+  int n_cells;                 /* cells of the 1-D track-length grid (0 = none)           */
+  int cell_axis;               /* 0,1,2 */
+  int tally_axis;              /* axis of q_mean, kappa, X_p and q_bin                    */
+  int per_bin;                 /* 1: frequency-resolved flux q_bin                       */
+  int threads_per_block;       /* 0 = default                                            */
+  int blocks_per_sm;           /* 0 = default                                            */
+  double time_budget_s;        /* 0 = 120 s; the kernel stops and reports TIMEOUT        */
+} mcbte_steady_params;
+
+typedef struct {
+  double* T;            /* [n_geoms][n_cells]     K, T - T_eq (Eq. temp_steady) or NULL  */
+  double* q;            /* [n_geoms][n_cells][3]  W/m^2 (Eq. flux_x_steady) or NULL      */
+  double* q_bin;        /* [n_geoms][n_bins]      W/m^2 per bin along tally_axis or NULL  */
+  double* stats;        /* [n_geoms][MCBTE_NSTATS] (required)                            */
+  uint32_t* events_pp;  /* [sum n_particles] per-particle event counts, or NULL          */
+  double* X_pp;         /* [sum n_particles] per-particle X_p (nm), or NULL              */
+  int on_host;          /* 0: device pointers, 1: host pointers                          */
+} mcbte_steady_out;
+
+/* Device scratch a run needs.  Pass a buffer at least this large (256-byte
+ * aligned) to the run, or NULL to let the run allocate (cudaMallocAsync on
+ * `stream`) and free it. */
+mcbte_status mcbte_steady_workspace_size(const mcbte_material* m, const mcbte_geometry* const* geoms,
+                                         int n_geoms, const mcbte_steady_params* p, int want_grad,
+                                         int n_dirs, size_t* bytes);
+
+/* Steady-state run over n_geoms geometries (1..128) in one launch (the
+ * steady estimator of Eq. steady_estimate with track-length tallies,
+ * Eqs. temp_steady and flux_x_steady).  Particle k of geometry g draws from
+ * Philox4x32-10 with counter (k, g, event, sub-block) and key = seed, so
+ * results do not depend on the launch shape or on how a run is split.
+ * With device outputs the call is asynchronous; its status lands in
+ * stats[MCBTE_STAT_STATUS].  With host outputs it returns TIMEOUT /
+ * TRUNCATED itself. */
+mcbte_status mcbte_run_steady(const mcbte_material* m, const mcbte_geometry* const* geoms, int n_geoms,
+                              const mcbte_steady_params* p, const mcbte_steady_out* out,
+                              void* workspace, size_t workspace_bytes, mcbte_stream stream);
+
+typedef struct {
+  uint64_t n_particles;        /* [1, 2^32) */
+  uint64_t seed;
+  int precision;
+  uint64_t max_events;
+  double t_max;                /* s, end of the simulated interval (Sec. 3.5.6)          */
+  int n_times;                 /* measurement times (Sec. 3.4)                           */
+  const double* t_meas;        /* HOST [n_times] s, ascending, in (0, t_max]             */
+  int grid[3];                 /* nx, ny, nz detector cells over the box                 */
+  int threads_per_block;
+  int blocks_per_sm;
+  double time_budget_s;
+} mcbte_transient_params;
+
+typedef struct {
+  double* tally;        /* [n_times][nz][ny][nx][4]: T - T_eq (K), q_x, q_y, q_z (W/m^2), Eq. sampling */
+  double* stats;        /* [MCBTE_NSTATS]                                                */
+  uint32_t* events_pp;  /* [n_particles] or NULL                                         */
+  int on_host;
+} mcbte_transient_out;
+
+mcbte_status mcbte_transient_workspace_size(const mcbte_material* m, const mcbte_geometry* g,
+                                            const mcbte_transient_params* p, size_t* bytes);
+
+/* Transient run (Sec. 3.2-3.5): wall sources emit at t0 = R t_max, the
+ * initial condition at t0 = 0; at each t_meas inside a particle's life its
+ * cell receives s E_eff / (C V_cell) and s E_eff V_g / V_cell (Eq. sampling).
+ * Body sources are not allowed (MCBTE_ERR_INVALID_ARG). */
+mcbte_status mcbte_run_transient(const mcbte_material* m, const mcbte_geometry* g,
+                                 const mcbte_transient_params* p, const mcbte_transient_out* out,
+                                 void* workspace, size_t workspace_bytes, mcbte_stream stream);
+
+typedef struct {
+  double* dkappa_dlogtau;  /* [n_bins] d kappa / d log tau_i                              */
+  double* dkappa_dp;       /* [2] value and standard error of d kappa / d p_pore; NaN
+                              when the geometry has no pore or p_pore is 0 or 1           */
+  const double* dirs;      /* [n_dirs][n_bins] probe directions in log-tau space, or NULL */
+  int n_dirs;              /* 0..16                                                        */
+  double* dkappa_dir;      /* [n_dirs][2] value and SE of d kappa along each direction     */
+  int on_host;             /* must equal the forward outputs' on_host                     */
+} mcbte_grad_out;
+
+/* Steady run of one geometry that also returns the likelihood-ratio
+ * (score-function) gradient of kappa with respect to per-bin log tau scale
+ * factors and the pore specularity.  The scores follow from the laws the
+ * paper samples: the exponential relaxation distance of Eq. time_to_scat
+ * (relaxation-ended flight: -1 + l / Lambda; censored flight: l / Lambda),
+ * the resampling law ~ C/tau of Eq. n_scatt (-delta_ij + pi_j) and the
+ * specular / diffuse draw of Sec. 3.5.3 (1/p, -1/(1-p)); each score
+ * multiplies the tally still to come.  The paper itself has no gradient.
+ * Requires 1 <= n_scat_max <= 64. */
+mcbte_status mcbte_grad(const mcbte_material* m, const mcbte_geometry* g, const mcbte_steady_params* p,
+                        const mcbte_steady_out* fwd, const mcbte_grad_out* grad,
+                        void* workspace, size_t workspace_bytes, mcbte_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCBTE_H */

@@ -91,6 +91,9 @@ def lib():
         L.or_philox.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         L.or_dEdT.argtypes = [C.c_double, C.c_double]
         L.or_dEdT.restype = C.c_double
+        L.or_log.argtypes = [C.c_double]
+        L.or_log.restype = C.c_double
+        L.or_sincos2pi.argtypes = [C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.or_alias.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.or_alias_draw.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32]
         L.or_alias_draw.restype = C.c_int
@@ -158,6 +161,16 @@ def philox(ctr: Sequence[int], key: Sequence[int]) -> np.ndarray:
 
 def dEdT(omega: float, T: float) -> float:
     return lib().or_dEdT(float(omega), float(T))
+
+
+def series_log(x: float) -> float:
+    return lib().or_log(float(x))
+
+
+def series_sincos2pi(r: float):
+    s, c = C.c_double(0), C.c_double(0)
+    lib().or_sincos2pi(float(r), C.byref(s), C.byref(c))
+    return s.value, c.value
 
 
 def alias_table(w: np.ndarray):

@@ -45,7 +45,6 @@ namespace {
 
 const double kHbar = 1.054571817e-34;   // J s
 const double kBoltz = 1.380649e-23;     // J / K
-const double kTwoPi = 6.283185307179586;
 const double k2m32 = 2.3283064365386963e-10;   // 2^-32
 const double k2m53 = 1.1102230246251565e-16;   // 2^-53
 
@@ -78,6 +77,67 @@ inline double mid32(uint32_t w) { return ((double)w + 0.5) * k2m32; }   // (0, 1
 inline double oc53(uint32_t lo, uint32_t hi) {                          // (0, 1], 53 bits
   uint64_t m = ((uint64_t)hi << 21) ^ (uint64_t)(lo >> 11);
   return ((double)m + 1.0) * k2m53;
+}
+
+// ---------------------------------------------------------------- elementary functions
+// The transcendental functions of the tracer are evaluated by fixed
+// published series with a fixed operation order, so that any IEEE-754
+// double implementation without fused multiply-add produces the same bits
+// (a library log / sin / cos may differ by an ulp between platforms, and
+// diffuse reflection off a convex pore amplifies such differences).
+//
+// ln x (x > 0, normal): x = m 2^e with m in [sqrt(2)/2, sqrt(2)];
+// ln x = e ln 2 + 2 atanh(z), z = (m - 1)/(m + 1), |z| < 0.172, atanh by its
+// Taylor series z + z^3/3 + ... + z^25/25 (Abramowitz & Stegun 4.1.27 /
+// 4.6.22), nested from the highest term.
+double series_log(double x) {
+  uint64_t b;
+  std::memcpy(&b, &x, sizeof(b));
+  int e = (int)((b >> 52) & 0x7ffu) - 1023;
+  uint64_t mb = (b & 0x000fffffffffffffull) | 0x3ff0000000000000ull;
+  double m;
+  std::memcpy(&m, &mb, sizeof(m));
+  if (m > 1.4142135623730951) {
+    m = m * 0.5;
+    e = e + 1;
+  }
+  const double z = (m - 1.0) / (m + 1.0);
+  const double z2 = z * z;
+  const double p = 0.3333333333333333 + z2 * (0.2 + z2 * (0.14285714285714285 + z2 * (0.1111111111111111 +
+                   z2 * (0.09090909090909091 + z2 * (0.07692307692307693 + z2 * (0.06666666666666667 +
+                   z2 * (0.058823529411764705 + z2 * (0.05263157894736842 + z2 * (0.047619047619047616 +
+                   z2 * (0.043478260869565216 + z2 * 0.04))))))))));
+  const double lm = 2.0 * (z + z * (z2 * p));
+  return (double)e * 0.6931471805599453 + lm;
+}
+
+// cos(2 pi r), sin(2 pi r) for r in [0, 1): octant k = floor(8 r), the
+// remainder mapped to theta in [0, pi/4] (reflected on odd octants), Taylor
+// series of sin and cos at theta (terms to theta^15 / theta^16), then the
+// octant symmetries of the unit circle.
+void series_sincos2pi(double r, double* sn, double* cs) {
+  const double t = r * 8.0;
+  const int k = (int)t;
+  double f = t - (double)k;
+  if (k & 1) f = 1.0 - f;
+  const double th = f * 0.7853981633974483;
+  const double t2 = th * th;
+  const double S = th * (1.0 + t2 * (-0.16666666666666666 + t2 * (0.008333333333333333 + t2 * (-0.0001984126984126984 +
+                   t2 * (2.7557319223985893e-06 + t2 * (-2.505210838544172e-08 + t2 * (1.6059043836821613e-10 +
+                   t2 * -7.647163731819816e-13)))))));
+  const double Cc = 1.0 + t2 * (-0.5 + t2 * (0.041666666666666664 + t2 * (-0.001388888888888889 +
+                    t2 * (2.48015873015873e-05 + t2 * (-2.755731922398589e-07 + t2 * (2.08767569878681e-09 +
+                    t2 * (-1.1470745597729725e-11 + t2 * 4.779477332387385e-14)))))));
+  switch (k & 7) {
+    case 0: *cs = Cc; *sn = S; break;
+    case 1: *cs = S; *sn = Cc; break;
+    case 2: *cs = -S; *sn = Cc; break;
+    case 3: *cs = -Cc; *sn = S; break;
+    case 4: *cs = -Cc; *sn = -S; break;
+    case 5: *cs = -S; *sn = -Cc; break;
+    case 6: *cs = S; *sn = -Cc; break;
+    default: *cs = Cc; *sn = -S; break;
+  }
 }
 
 // ---------------------------------------------------------------- tables
@@ -401,10 +461,11 @@ inline void first_hit(const Geo& g, const double x[3], const double u[3], double
 // cyclic order a+1, a+2, take s cos(phi), s sin(phi).
 inline void dir_about_axis(double u[3], int a, double sgn, double mu, uint32_t wphi) {
   double s = std::sqrt(std::max(0.0, 1.0 - mu * mu));
-  double phi = kTwoPi * co32(wphi);
+  double sn, cs;
+  series_sincos2pi(co32(wphi), &sn, &cs);
   u[a] = sgn * mu;
-  u[(a + 1) % 3] = s * std::cos(phi);
-  u[(a + 2) % 3] = s * std::sin(phi);
+  u[(a + 1) % 3] = s * cs;
+  u[(a + 2) % 3] = s * sn;
 }
 
 struct Partial {
@@ -474,11 +535,12 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
       double mu = 1.0 - 2.0 * oc32(w1[0]);
       dir_about_axis(u, 2, 1.0, mu, w1[1]);
       ctr[3] = 3; philox4x32_10(ctr, k0, k1, w3);
-      double m1 = std::sqrt(-2.0 * std::log(oc32(w3[0])));
-      double m2 = std::sqrt(-2.0 * std::log(oc32(w3[2])));
-      double a1 = kTwoPi * co32(w3[1]);
-      double a2 = kTwoPi * co32(w3[3]);
-      double nrm[3] = {m1 * std::cos(a1), m1 * std::sin(a1), m2 * std::cos(a2)};
+      double m1 = std::sqrt(-2.0 * series_log(oc32(w3[0])));
+      double m2 = std::sqrt(-2.0 * series_log(oc32(w3[2])));
+      double s1, c1, s2, c2;
+      series_sincos2pi(co32(w3[1]), &s1, &c1);
+      series_sincos2pi(co32(w3[3]), &s2, &c2);
+      double nrm[3] = {m1 * c1, m1 * s1, m2 * c2};
       for (int a = 0; a < 3; ++a) {
         double c = S.gauss_c[a] + S.gauss_sigma * nrm[a];
         if (c < 0.0) c = -c;
@@ -488,7 +550,7 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
         x[a] = c;
       }
     }
-    double d_rel = t.lam_nm[bin] * (-std::log(oc53(w1[2], w1[3])));
+    double d_rel = t.lam_nm[bin] * (-series_log(oc53(w1[2], w1[3])));
     out.scal[OR_SIGNED_EMIT] += s;
     uint32_t e = 0;
     int n_relax = 0;
@@ -597,7 +659,7 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
         ctr[3] = 1; philox4x32_10(ctr, k0, k1, w1);
         bin = alias_draw(t.relax, n, w[0], w[1], w1[0]);
         dir_about_axis(u, 2, 1.0, 1.0 - 2.0 * oc32(w[2]), w[3]);
-        d_rel = t.lam_nm[bin] * (-std::log(oc53(w1[1], w1[2])));
+        d_rel = t.lam_nm[bin] * (-series_log(oc53(w1[1], w1[2])));
         if (P->want_grad) {
           periods.push_back({bin, -1.0, -X});
           ++n_res;
@@ -646,11 +708,12 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
         } else {
           double mu = std::sqrt(oc32(w[2]));
           double sn = std::sqrt(std::max(0.0, 1.0 - mu * mu));
-          double phi = kTwoPi * co32(w[3]);
-          double sc = sn * std::cos(phi);
+          double sphi, cphi;
+          series_sincos2pi(co32(w[3]), &sphi, &cphi);
+          double sc = sn * cphi;
           u[0] = mu * nx0 - sc * ny0;
           u[1] = mu * ny0 + sc * nx0;
-          u[2] = sn * std::sin(phi);
+          u[2] = sn * sphi;
         }
       }
     }
@@ -690,6 +753,10 @@ void or_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
 }
 
 double or_dEdT(double omega, double T) { return dEdT(omega, T); }
+
+double or_log(double x) { return series_log(x); }
+
+void or_sincos2pi(double r, double* s, double* c) { series_sincos2pi(r, s, c); }
 
 // Alias table of arbitrary weights (for the table tests).
 void or_alias(int n, const double* w, double* prob, uint64_t* thr, int32_t* alias) {

@@ -1,0 +1,690 @@
+// C ABI of the MCBTE GB300 library: handle management, argument checks,
+// workspace layout and the launch sequence of every run.  No numerical step
+// of the method runs here; this file only validates, lays out memory and
+// launches kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+
+using namespace mcbte;
+
+namespace {
+
+thread_local std::string g_err;
+
+mcbte_status fail(mcbte_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+mcbte_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? MCBTE_ERR_OOM : MCBTE_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(call)                                 \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+// Bump allocator over one device buffer (256-byte aligned pieces).
+struct Carve {
+  size_t off = 0;
+  char* base = nullptr;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+}  // namespace
+
+struct mcbte_material {
+  int n;
+  void* block;
+  MatView view;
+  MatBuild b;
+};
+
+struct mcbte_geometry {
+  mcbte_geometry_desc host;
+  mcbte_geometry_desc* dev;
+};
+
+extern "C" {
+
+int mcbte_last_error(char* buf, size_t n) {
+  if (buf && n > 0) {
+    size_t k = g_err.size() < n - 1 ? g_err.size() : n - 1;
+    std::memcpy(buf, g_err.data(), k);
+    buf[k] = '\0';
+  }
+  return (int)g_err.size();
+}
+
+int mcbte_version(void) { return 10000; }
+
+// ------------------------------------------------------------------ material
+mcbte_status mcbte_material_create(const mcbte_material_desc* d, mcbte_material** out) {
+  if (!d || !out) return fail(MCBTE_ERR_INVALID_ARG, "material_create: null argument");
+  *out = nullptr;
+  const int n = d->n_bins;
+  if (n < 1 || n > (1 << 24)) return fail(MCBTE_ERR_INVALID_ARG, "material_create: n_bins out of range");
+  if (!d->omega || !d->v || !d->tau) return fail(MCBTE_ERR_INVALID_ARG, "material_create: omega, v, tau required");
+  const bool fmt2 = d->C != nullptr;
+  if (!fmt2 && (!d->D || !d->domega))
+    return fail(MCBTE_ERR_INVALID_ARG, "material_create: give C (format 2) or D and domega (format 1)");
+  if (!fmt2 && !finite_pos(d->T_lin)) return fail(MCBTE_ERR_INVALID_ARG, "material_create: T_lin must be > 0");
+  for (int i = 0; i < n; ++i) {
+    if (!finite_pos(d->v[i])) return fail(MCBTE_ERR_INVALID_ARG, "material_create: v must be > 0");
+    if (!finite_pos(d->tau[i])) return fail(MCBTE_ERR_INVALID_ARG, "material_create: tau must be > 0");
+    if (!std::isfinite(d->omega[i]) || d->omega[i] <= 0.0)
+      return fail(MCBTE_ERR_INVALID_ARG, "material_create: omega must be > 0");
+    if (fmt2 && !(std::isfinite(d->C[i]) && d->C[i] >= 0.0))
+      return fail(MCBTE_ERR_INVALID_ARG, "material_create: C must be >= 0");
+    if (!fmt2 && !(std::isfinite(d->D[i]) && d->D[i] >= 0.0 && std::isfinite(d->domega[i]) && d->domega[i] >= 0.0))
+      return fail(MCBTE_ERR_INVALID_ARG, "material_create: D and domega must be >= 0");
+  }
+  Carve c;
+  auto layout = [&](MatBuild& b) {
+    b.n = n;
+    double* omega = c.take<double>(n);
+    double* v = c.take<double>(n);
+    double* tau = c.take<double>(n);
+    double* Cin = c.take<double>(n);
+    double* D = c.take<double>(n);
+    double* dw = c.take<double>(n);
+    b.omega = omega; b.v = v; b.tau = tau;
+    b.C_in = fmt2 ? Cin : nullptr;
+    b.D = D; b.domega = dw;
+    b.T_lin = d->T_lin;
+    b.C = c.take<double>(n);
+    b.w_emit = c.take<double>(n);
+    b.w_init = c.take<double>(n);
+    b.w_relax = c.take<double>(n);
+    b.v_nm = c.take<double>(n);
+    b.inv_v = c.take<double>(n);
+    b.lam = c.take<double>(n);
+    b.pi = c.take<double>(n);
+    b.sums = c.take<double>(4);
+    b.prob = c.take<double>(3 * (size_t)n);
+    b.thr = c.take<uint64_t>(3 * (size_t)n);
+    b.alias = c.take<int32_t>(3 * (size_t)n);
+    b.rec = c.take<uint4>(3 * (size_t)n);
+    b.binf = c.take<float4>(n);
+    b.scratch_p = c.take<double>(3 * (size_t)n);
+    b.scratch_small = c.take<int>(3 * (size_t)n);
+    b.scratch_large = c.take<int>(3 * (size_t)n);
+  };
+  MatBuild probe{};
+  layout(probe);
+  const size_t bytes = c.off;
+  void* block = nullptr;
+  CUDA_TRY(cudaMalloc(&block, bytes));
+  c.off = 0;
+  c.base = static_cast<char*>(block);
+  MatBuild b{};
+  layout(b);
+  auto cleanup = [&]() { cudaFree(block); };
+  const size_t nb = (size_t)n * sizeof(double);
+  cudaError_t e = cudaMemcpy((void*)b.omega, d->omega, nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy((void*)b.v, d->v, nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy((void*)b.tau, d->tau, nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && fmt2) e = cudaMemcpy((void*)b.C_in, d->C, nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !fmt2) e = cudaMemcpy((void*)b.D, d->D, nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !fmt2) e = cudaMemcpy((void*)b.domega, d->domega, nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_material_build(b, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+  double sums[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(sums, b.sums, 3 * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "material_create");
+  }
+  if (!(sums[0] > 0.0) || !(sums[2] > 0.0)) {
+    cleanup();
+    return fail(MCBTE_ERR_INVALID_ARG, "material_create: total heat capacity is zero");
+  }
+  mcbte_material* m = new mcbte_material();
+  m->n = n;
+  m->block = block;
+  m->b = b;
+  MatView& v = m->view;
+  v.n = n;
+  v.rec_emit = b.rec;
+  v.rec_init = b.rec + n;
+  v.rec_relax = b.rec + 2 * (size_t)n;
+  v.binf = b.binf;
+  v.v_d = b.v_nm;
+  v.inv_v_d = b.inv_v;
+  v.lam_d = b.lam;
+  v.pi = b.pi;
+  v.sums = b.sums;
+  *out = m;
+  return MCBTE_OK;
+}
+
+void mcbte_material_destroy(mcbte_material* m) {
+  if (!m) return;
+  cudaFree(m->block);
+  delete m;
+}
+
+int mcbte_material_n_bins(const mcbte_material* m) { return m ? m->n : 0; }
+
+mcbte_status mcbte_material_tables(const mcbte_material* m, double* C, double* prob, uint64_t* thr, int32_t* alias,
+                                   double* sums) {
+  if (!m) return fail(MCBTE_ERR_INVALID_ARG, "material_tables: null material");
+  const size_t n = (size_t)m->n;
+  if (C) CUDA_TRY(cudaMemcpy(C, m->b.C, n * sizeof(double), cudaMemcpyDeviceToHost));
+  if (prob) CUDA_TRY(cudaMemcpy(prob, m->b.prob, 3 * n * sizeof(double), cudaMemcpyDeviceToHost));
+  if (thr) CUDA_TRY(cudaMemcpy(thr, m->b.thr, 3 * n * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  if (alias) CUDA_TRY(cudaMemcpy(alias, m->b.alias, 3 * n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (sums) CUDA_TRY(cudaMemcpy(sums, m->b.sums, 3 * sizeof(double), cudaMemcpyDeviceToHost));
+  return MCBTE_OK;
+}
+
+// ------------------------------------------------------------------ geometry
+mcbte_status mcbte_geometry_create(const mcbte_geometry_desc* d, mcbte_geometry** out) {
+  if (!d || !out) return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: null argument");
+  *out = nullptr;
+  for (int a = 0; a < 3; ++a)
+    if (!finite_pos(d->L[a])) return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: L must be > 0");
+  for (int f = 0; f < 6; ++f) {
+    if (d->face_type[f] < 0 || d->face_type[f] > 2) return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: face type");
+    if (d->face_type[f] == MCBTE_FACE_ADIABATIC && !(d->face_p[f] >= 0.0 && d->face_p[f] <= 1.0))
+      return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: specularity outside [0,1]");
+    if (d->face_type[f] == MCBTE_FACE_ISOTHERMAL && !finite_pos(d->face_T[f]))
+      return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: isothermal T_b must be > 0");
+  }
+  const int lo[3] = {3, 0, 4}, hi[3] = {1, 2, 5};
+  for (int a = 0; a < 3; ++a) {
+    const bool pl = d->face_type[lo[a]] == MCBTE_FACE_PERIODIC, ph = d->face_type[hi[a]] == MCBTE_FACE_PERIODIC;
+    if (pl != ph) return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: periodic faces must come in pairs");
+  }
+  if (!finite_pos(d->T_eq)) return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: T_eq must be > 0");
+  int ng = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (!std::isfinite(d->grad_T[a])) return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: grad_T not finite");
+    if (d->grad_T[a] != 0.0) ++ng;
+  }
+  if (ng > 1) return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: at most one grad_T component");
+  if (d->pore) {
+    const double r = d->pore_r, cx = d->pore_c[0], cy = d->pore_c[1];
+    if (!finite_pos(r) || !(cx - r > 0.0) || !(cx + r < d->L[0]) || !(cy - r > 0.0) || !(cy + r < d->L[1]))
+      return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: pore must lie strictly inside the cell");
+    if (!(d->pore_p >= 0.0 && d->pore_p <= 1.0))
+      return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: pore specularity outside [0,1]");
+    if (3.141592653589793 * r * r > 0.9 * d->L[0] * d->L[1])
+      return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: porosity above 0.9");
+  }
+  if (d->gauss && !finite_pos(d->gauss_sigma))
+    return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: gauss_sigma must be > 0");
+  mcbte_geometry_desc* dev = nullptr;
+  CUDA_TRY(cudaMalloc(&dev, sizeof(mcbte_geometry_desc)));
+  cudaError_t e = cudaMemcpy(dev, d, sizeof(mcbte_geometry_desc), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(dev);
+    return cuda_fail(e, "geometry_create");
+  }
+  mcbte_geometry* g = new mcbte_geometry();
+  g->host = *d;
+  g->dev = dev;
+  *out = g;
+  return MCBTE_OK;
+}
+
+void mcbte_geometry_destroy(mcbte_geometry* g) {
+  if (!g) return;
+  cudaFree(g->dev);
+  delete g;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ steady runs
+namespace {
+
+bool has_isothermal_source(const mcbte_geometry_desc& d) {
+  for (int f = 0; f < 6; ++f)
+    if (d.face_type[f] == MCBTE_FACE_ISOTHERMAL && d.face_T[f] != d.T_eq) return true;
+  return false;
+}
+
+bool has_gradient(const mcbte_geometry_desc& d) {
+  return d.grad_T[0] != 0.0 || d.grad_T[1] != 0.0 || d.grad_T[2] != 0.0;
+}
+
+struct SteadyWs {
+  GeoRun* geos;
+  uint64_t* offs;
+  char* zero_begin;
+  double* cellP;
+  double* cellD;
+  double* qbin;
+  double* dsc;
+  unsigned long long* cnt;
+  double* G;
+  double* dsum;
+  unsigned long long* work;
+  int* flags;
+  unsigned long long* t0;
+  char* zero_end;
+  double* dirs;
+  double* dpi;
+  // host-output staging
+  double *T, *q, *q_bin, *stats;
+  uint32_t* events_pp;
+  double* X_pp;
+  double *dk, *dkp, *dkdir;
+  size_t bytes;
+};
+
+SteadyWs layout_steady(char* base, int G, int n, int nc, uint64_t total, bool grad, int nd, bool host_out,
+                       bool want_ev, bool want_x, bool want_T, bool want_q, bool want_qbin) {
+  Carve c;
+  c.base = base;
+  SteadyWs w{};
+  w.geos = c.take<GeoRun>(G);
+  w.offs = c.take<uint64_t>(G + 1);
+  c.off = (c.off + 255) & ~(size_t)255;
+  w.zero_begin = base ? base + c.off : nullptr;
+  w.cellP = nc > 0 ? c.take<double>((size_t)G * nc * 4) : nullptr;
+  w.cellD = nc > 0 ? c.take<double>((size_t)G * (nc + 1) * 4) : nullptr;
+  w.qbin = c.take<double>((size_t)G * n);
+  w.dsc = c.take<double>((size_t)G * 8);
+  w.cnt = c.take<unsigned long long>((size_t)G * 4);
+  w.G = grad ? c.take<double>(n) : nullptr;
+  w.dsum = grad ? c.take<double>(2 * (size_t)(nd > 0 ? nd : 1)) : nullptr;
+  w.work = c.take<unsigned long long>(1);
+  w.flags = c.take<int>(2);
+  w.t0 = c.take<unsigned long long>(1);
+  c.off = (c.off + 255) & ~(size_t)255;
+  w.zero_end = base ? base + c.off : nullptr;
+  w.dirs = (grad && nd > 0) ? c.take<double>((size_t)nd * n) : nullptr;
+  w.dpi = (grad && nd > 0) ? c.take<double>(nd) : nullptr;
+  if (host_out) {
+    w.T = (want_T && nc > 0) ? c.take<double>((size_t)G * nc) : nullptr;
+    w.q = (want_q && nc > 0) ? c.take<double>((size_t)G * nc * 3) : nullptr;
+    w.q_bin = want_qbin ? c.take<double>((size_t)G * n) : nullptr;
+    w.stats = c.take<double>((size_t)G * MCBTE_NSTATS);
+    w.events_pp = want_ev ? c.take<uint32_t>(total) : nullptr;
+    w.X_pp = want_x ? c.take<double>(total) : nullptr;
+    w.dk = grad ? c.take<double>(n) : nullptr;
+    w.dkp = grad ? c.take<double>(2) : nullptr;
+    w.dkdir = (grad && nd > 0) ? c.take<double>(2 * (size_t)nd) : nullptr;
+  }
+  w.bytes = c.off + 256;
+  return w;
+}
+
+mcbte_status check_steady(const mcbte_material* m, const mcbte_geometry* const* geoms, int G,
+                          const mcbte_steady_params* p, uint64_t* total) {
+  if (!m || !geoms || !p) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: null argument");
+  if (G < 1 || G > kMaxGeoms) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: n_geoms must be in [1, 128]");
+  if (!p->n_particles) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: n_particles required");
+  if (p->precision != MCBTE_FP64_PLAIN && p->precision != MCBTE_FP32_TRACE)
+    return fail(MCBTE_ERR_INVALID_ARG, "run_steady: precision");
+  if (p->n_cells < 0 || p->n_cells > 4096) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: n_cells in [0, 4096]");
+  if (p->cell_axis < 0 || p->cell_axis > 2 || p->tally_axis < 0 || p->tally_axis > 2)
+    return fail(MCBTE_ERR_INVALID_ARG, "run_steady: axis must be 0, 1 or 2");
+  if (p->n_scat_max < 0) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: n_scat_max < 0");
+  if (p->threads_per_block < 0 || p->threads_per_block > 512 || (p->threads_per_block % 32) != 0)
+    return fail(MCBTE_ERR_INVALID_ARG, "run_steady: threads_per_block must be a multiple of 32 up to 512");
+  uint64_t t = 0;
+  for (int g = 0; g < G; ++g) {
+    if (!geoms[g]) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: null geometry");
+    const uint64_t ng = p->n_particles[g];
+    if (ng < 1 || ng >= (1ull << 32)) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: n_particles in [1, 2^32)");
+    t += ng;
+    const mcbte_geometry_desc& d = geoms[g]->host;
+    if (d.gauss) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: an initial condition needs a transient run");
+    if (!has_isothermal_source(d) && !has_gradient(d))
+      return fail(MCBTE_ERR_INVALID_ARG, "run_steady: geometry has no source (no isothermal wall off T_eq, no grad_T)");
+  }
+  if (t >= (1ull << 40)) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: too many particles");
+  *total = t;
+  return MCBTE_OK;
+}
+
+mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* geoms, int G,
+                         const mcbte_steady_params* p, const mcbte_steady_out* out, const mcbte_grad_out* gout,
+                         void* workspace, size_t ws_bytes, cudaStream_t s) {
+  uint64_t total = 0;
+  mcbte_status st = check_steady(m, geoms, G, p, &total);
+  if (st != MCBTE_OK) return st;
+  if (!out || !out->stats) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: out->stats required");
+  const bool grad = gout != nullptr;
+  const int n = m->n;
+  const int nc = p->n_cells;
+  const int nd = grad ? gout->n_dirs : 0;
+  if (grad) {
+    if (G != 1) return fail(MCBTE_ERR_INVALID_ARG, "grad: one geometry");
+    if (p->n_scat_max < 1 || p->n_scat_max > kMaxPeriods - 1)
+      return fail(MCBTE_ERR_INVALID_ARG, "grad: n_scat_max must be in [1, 64]");
+    if (nd < 0 || nd > kMaxDirs || (nd > 0 && !gout->dirs))
+      return fail(MCBTE_ERR_INVALID_ARG, "grad: n_dirs in [0, 16] with dirs");
+    if (!gout->dkappa_dlogtau || !gout->dkappa_dp || (nd > 0 && !gout->dkappa_dir))
+      return fail(MCBTE_ERR_INVALID_ARG, "grad: output pointers required");
+    if (gout->on_host != out->on_host) return fail(MCBTE_ERR_INVALID_ARG, "grad: on_host must match");
+  }
+  const bool host_out = out->on_host != 0;
+  SteadyWs w = layout_steady(nullptr, G, n, nc, total, grad, nd, host_out, out->events_pp, out->X_pp, out->T, out->q,
+                             out->q_bin);
+  const size_t need = w.bytes;
+  char* base = static_cast<char*>(workspace);
+  bool own = false;
+  if (!base) {
+    CUDA_TRY(cudaMallocAsync((void**)&base, need, s));
+    own = true;
+  } else if (ws_bytes < need) {
+    return fail(MCBTE_ERR_WORKSPACE, "run_steady: workspace too small");
+  }
+  char* aligned = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(base) + 255) & ~(uintptr_t)255);
+  w = layout_steady(aligned, G, n, nc, total, grad, nd, host_out, out->events_pp, out->X_pp, out->T, out->q,
+                    out->q_bin);
+  auto release = [&]() {
+    if (own) cudaFreeAsync(base, s);
+  };
+#define RUN_TRY(call)                      \
+  do {                                     \
+    cudaError_t e_ = (call);               \
+    if (e_ != cudaSuccess) {               \
+      release();                           \
+      return cuda_fail(e_, #call);         \
+    }                                      \
+  } while (0)
+  RUN_TRY(cudaMemsetAsync(w.zero_begin, 0, (size_t)(w.zero_end - w.zero_begin), s));
+  SetupArgs a;
+  std::memset(&a, 0, sizeof(a));
+  for (int g = 0; g < G; ++g) {
+    a.desc[g] = geoms[g]->dev;
+    a.n[g] = p->n_particles[g];
+  }
+  RUN_TRY(launch_setup(a, G, m->view, 0, 0.0, p->tally_axis, w.geos, w.offs, w.t0, s));
+  RunCfg C{};
+  C.k0 = (uint32_t)p->seed;
+  C.k1 = (uint32_t)(p->seed >> 32);
+  C.n_scat_max = p->n_scat_max;
+  C.max_events = (p->max_events == 0 || p->max_events > 0xFFFFFFFFull) ? 0xFFFFFFFFu : (uint32_t)p->max_events;
+  C.n_cells = nc;
+  C.cell_axis = p->cell_axis;
+  C.tally_axis = p->tally_axis;
+  C.per_bin = p->per_bin ? 1 : 0;
+  C.n_geoms = G;
+  C.total = total;
+  C.t0 = w.t0;
+  C.budget_ns = (uint64_t)((p->time_budget_s > 0 ? p->time_budget_s : 120.0) * 1e9);
+  Acc A{};
+  A.cellP = w.cellP;
+  A.cellD = w.cellD;
+  A.qbin = w.qbin;
+  A.dsc = w.dsc;
+  A.cnt = w.cnt;
+  A.G = w.G;
+  A.dsum = w.dsum;
+  A.work = w.work;
+  A.flags = w.flags;
+  A.events_pp = host_out ? w.events_pp : out->events_pp;
+  A.X_pp = host_out ? w.X_pp : out->X_pp;
+  if (grad && nd > 0) {
+    RUN_TRY(cudaMemcpyAsync(w.dirs, gout->dirs, (size_t)nd * n * sizeof(double),
+                            host_out ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    RUN_TRY(launch_dirs_dot_pi(w.dirs, nd, m->view, w.dpi, s));
+    C.n_dirs = nd;
+    C.dirs = w.dirs;
+    C.dpi = w.dpi;
+  }
+  RUN_TRY(launch_steady(p->precision, grad, w.geos, w.offs, m->view, C, A, p->threads_per_block, p->blocks_per_sm, s));
+  SteadyOutDev O{};
+  O.T = host_out ? w.T : out->T;
+  O.q = host_out ? w.q : out->q;
+  O.q_bin = host_out ? w.q_bin : out->q_bin;
+  O.stats = host_out ? w.stats : out->stats;
+  if (grad) {
+    O.dk = host_out ? w.dk : gout->dkappa_dlogtau;
+    O.dkp = host_out ? w.dkp : gout->dkappa_dp;
+    O.dkdir = host_out ? w.dkdir : gout->dkappa_dir;
+  }
+  RUN_TRY(launch_finalize_steady(w.geos, m->view, C, A, O, grad, w.flags, s));
+  mcbte_status result = MCBTE_OK;
+  if (host_out) {
+    auto d2h = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+      if (!dst || !src || bytes == 0) return cudaSuccess;
+      return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+    };
+    RUN_TRY(d2h(out->T, w.T, (size_t)G * nc * sizeof(double)));
+    RUN_TRY(d2h(out->q, w.q, (size_t)G * nc * 3 * sizeof(double)));
+    RUN_TRY(d2h(out->q_bin, w.q_bin, (size_t)G * n * sizeof(double)));
+    RUN_TRY(d2h(out->stats, w.stats, (size_t)G * MCBTE_NSTATS * sizeof(double)));
+    RUN_TRY(d2h(out->events_pp, w.events_pp, total * sizeof(uint32_t)));
+    RUN_TRY(d2h(out->X_pp, w.X_pp, total * sizeof(double)));
+    if (grad) {
+      RUN_TRY(d2h(gout->dkappa_dlogtau, w.dk, (size_t)n * sizeof(double)));
+      RUN_TRY(d2h(gout->dkappa_dp, w.dkp, 2 * sizeof(double)));
+      if (nd > 0) RUN_TRY(d2h(gout->dkappa_dir, w.dkdir, 2 * (size_t)nd * sizeof(double)));
+    }
+    release();
+    own = false;
+    RUN_TRY(cudaStreamSynchronize(s));
+    for (int g = 0; g < G; ++g) {
+      const double code = out->stats[(size_t)g * MCBTE_NSTATS + MCBTE_STAT_STATUS];
+      if (code == (double)MCBTE_ERR_TIMEOUT) result = fail(MCBTE_ERR_TIMEOUT, "run: time budget exceeded");
+      else if (code == (double)MCBTE_WARN_TRUNCATED && result == MCBTE_OK)
+        result = fail(MCBTE_WARN_TRUNCATED, "run: some particles reached max_events");
+    }
+  } else {
+    release();
+  }
+#undef RUN_TRY
+  return result;
+}
+
+}  // namespace
+
+extern "C" {
+
+mcbte_status mcbte_steady_workspace_size(const mcbte_material* m, const mcbte_geometry* const* geoms, int n_geoms,
+                                         const mcbte_steady_params* p, int want_grad, int n_dirs, size_t* bytes) {
+  uint64_t total = 0;
+  mcbte_status st = check_steady(m, geoms, n_geoms, p, &total);
+  if (st != MCBTE_OK) return st;
+  if (!bytes) return fail(MCBTE_ERR_INVALID_ARG, "workspace_size: null bytes");
+  SteadyWs w = layout_steady(nullptr, n_geoms, m->n, p->n_cells, total, want_grad != 0, n_dirs, false, false, false,
+                             false, false, false);
+  *bytes = w.bytes;
+  return MCBTE_OK;
+}
+
+mcbte_status mcbte_run_steady(const mcbte_material* m, const mcbte_geometry* const* geoms, int n_geoms,
+                              const mcbte_steady_params* p, const mcbte_steady_out* out, void* workspace,
+                              size_t workspace_bytes, mcbte_stream stream) {
+  return steady_impl(m, geoms, n_geoms, p, out, nullptr, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+mcbte_status mcbte_grad(const mcbte_material* m, const mcbte_geometry* g, const mcbte_steady_params* p,
+                        const mcbte_steady_out* fwd, const mcbte_grad_out* grad, void* workspace,
+                        size_t workspace_bytes, mcbte_stream stream) {
+  if (!grad) return fail(MCBTE_ERR_INVALID_ARG, "grad: null grad output");
+  const mcbte_geometry* gs[1] = {g};
+  return steady_impl(m, gs, 1, p, fwd, grad, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ transient runs
+namespace {
+
+struct TransientWs {
+  GeoRun* geos;
+  uint64_t* offs;
+  char* zero_begin;
+  double* dsc;
+  unsigned long long* cnt;
+  unsigned long long* work;
+  int* flags;
+  unsigned long long* t0;
+  char* zero_end;
+  double* t_meas_ps;
+  double* snap;     // only when outputs are on the host
+  double* stats;
+  uint32_t* events_pp;
+  size_t bytes;
+};
+
+TransientWs layout_transient(char* base, size_t snap_len, int n_times, bool host_out, bool want_ev, uint64_t total) {
+  Carve c;
+  c.base = base;
+  TransientWs w{};
+  w.geos = c.take<GeoRun>(1);
+  w.offs = c.take<uint64_t>(2);
+  c.off = (c.off + 255) & ~(size_t)255;
+  w.zero_begin = base ? base + c.off : nullptr;
+  w.dsc = c.take<double>(8);
+  w.cnt = c.take<unsigned long long>(4);
+  w.work = c.take<unsigned long long>(1);
+  w.flags = c.take<int>(2);
+  w.t0 = c.take<unsigned long long>(1);
+  c.off = (c.off + 255) & ~(size_t)255;
+  w.zero_end = base ? base + c.off : nullptr;
+  w.t_meas_ps = c.take<double>(n_times);
+  if (host_out) {
+    w.snap = c.take<double>(snap_len);
+    w.stats = c.take<double>(MCBTE_NSTATS);
+    w.events_pp = want_ev ? c.take<uint32_t>(total) : nullptr;
+  }
+  w.bytes = c.off + 256;
+  return w;
+}
+
+mcbte_status check_transient(const mcbte_material* m, const mcbte_geometry* g, const mcbte_transient_params* p) {
+  if (!m || !g || !p) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: null argument");
+  if (p->n_particles < 1 || p->n_particles >= (1ull << 32))
+    return fail(MCBTE_ERR_INVALID_ARG, "run_transient: n_particles in [1, 2^32)");
+  if (p->precision != MCBTE_FP64_PLAIN && p->precision != MCBTE_FP32_TRACE)
+    return fail(MCBTE_ERR_INVALID_ARG, "run_transient: precision");
+  if (!finite_pos(p->t_max)) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: t_max must be > 0");
+  if (p->n_times < 1 || !p->t_meas) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: t_meas required");
+  for (int k = 0; k < p->n_times; ++k) {
+    if (!(p->t_meas[k] > 0.0 && p->t_meas[k] <= p->t_max)) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: t_meas in (0, t_max]");
+    if (k > 0 && !(p->t_meas[k] > p->t_meas[k - 1])) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: t_meas ascending");
+  }
+  for (int a = 0; a < 3; ++a)
+    if (p->grid[a] < 1 || p->grid[a] > 4096) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: grid in [1, 4096]");
+  if (p->threads_per_block < 0 || p->threads_per_block > 512 || (p->threads_per_block % 32) != 0)
+    return fail(MCBTE_ERR_INVALID_ARG, "run_transient: threads_per_block must be a multiple of 32 up to 512");
+  const mcbte_geometry_desc& d = g->host;
+  if (has_gradient(d)) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: body (gradient) sources are steady only");
+  if (!d.gauss && !has_isothermal_source(d)) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: no source");
+  return MCBTE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mcbte_status mcbte_transient_workspace_size(const mcbte_material* m, const mcbte_geometry* g,
+                                            const mcbte_transient_params* p, size_t* bytes) {
+  mcbte_status st = check_transient(m, g, p);
+  if (st != MCBTE_OK) return st;
+  if (!bytes) return fail(MCBTE_ERR_INVALID_ARG, "workspace_size: null bytes");
+  *bytes = layout_transient(nullptr, 0, p->n_times, false, false, 0).bytes;
+  return MCBTE_OK;
+}
+
+mcbte_status mcbte_run_transient(const mcbte_material* m, const mcbte_geometry* g, const mcbte_transient_params* p,
+                                 const mcbte_transient_out* out, void* workspace, size_t workspace_bytes,
+                                 mcbte_stream stream) {
+  mcbte_status st = check_transient(m, g, p);
+  if (st != MCBTE_OK) return st;
+  if (!out || !out->tally || !out->stats) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: tally and stats required");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ncell = (size_t)p->grid[0] * p->grid[1] * p->grid[2];
+  const size_t snap_len = (size_t)p->n_times * ncell * 4;
+  const bool host_out = out->on_host != 0;
+  TransientWs w = layout_transient(nullptr, snap_len, p->n_times, host_out, out->events_pp, p->n_particles);
+  char* base = static_cast<char*>(workspace);
+  bool own = false;
+  if (!base) {
+    CUDA_TRY(cudaMallocAsync((void**)&base, w.bytes, s));
+    own = true;
+  } else if (workspace_bytes < w.bytes) {
+    return fail(MCBTE_ERR_WORKSPACE, "run_transient: workspace too small");
+  }
+  char* aligned = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(base) + 255) & ~(uintptr_t)255);
+  w = layout_transient(aligned, snap_len, p->n_times, host_out, out->events_pp, p->n_particles);
+  auto release = [&]() {
+    if (own) cudaFreeAsync(base, s);
+  };
+#define RUN_TRY(call)              \
+  do {                             \
+    cudaError_t e_ = (call);       \
+    if (e_ != cudaSuccess) {       \
+      release();                   \
+      return cuda_fail(e_, #call); \
+    }                              \
+  } while (0)
+  double* snap = host_out ? w.snap : out->tally;
+  RUN_TRY(cudaMemsetAsync(w.zero_begin, 0, (size_t)(w.zero_end - w.zero_begin), s));
+  RUN_TRY(cudaMemsetAsync(snap, 0, snap_len * sizeof(double), s));
+  std::vector<double> tm(p->n_times);
+  for (int k = 0; k < p->n_times; ++k) tm[k] = p->t_meas[k] * 1e12;
+  RUN_TRY(cudaMemcpyAsync(w.t_meas_ps, tm.data(), tm.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  SetupArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.desc[0] = g->dev;
+  a.n[0] = p->n_particles;
+  RUN_TRY(launch_setup(a, 1, m->view, 1, p->t_max, 2, w.geos, w.offs, w.t0, s));
+  RunCfg C{};
+  C.k0 = (uint32_t)p->seed;
+  C.k1 = (uint32_t)(p->seed >> 32);
+  C.n_scat_max = 0;
+  C.max_events = (p->max_events == 0 || p->max_events > 0xFFFFFFFFull) ? 0xFFFFFFFFu : (uint32_t)p->max_events;
+  C.n_geoms = 1;
+  C.total = p->n_particles;
+  C.t0 = w.t0;
+  C.budget_ns = (uint64_t)((p->time_budget_s > 0 ? p->time_budget_s : 120.0) * 1e9);
+  C.t_max_ps = p->t_max * 1e12;
+  C.n_times = p->n_times;
+  C.t_meas_ps = w.t_meas_ps;
+  for (int k = 0; k < 3; ++k) C.grid[k] = p->grid[k];
+  Acc A{};
+  A.dsc = w.dsc;
+  A.cnt = w.cnt;
+  A.work = w.work;
+  A.flags = w.flags;
+  A.snap = snap;
+  A.events_pp = host_out ? w.events_pp : out->events_pp;
+  RUN_TRY(launch_transient(p->precision, w.geos, m->view, C, A, p->threads_per_block, p->blocks_per_sm, s));
+  double* stats = host_out ? w.stats : out->stats;
+  RUN_TRY(launch_finalize_transient(w.geos, m->view, C, A, snap, stats, ncell, s));
+  mcbte_status result = MCBTE_OK;
+  if (host_out) {
+    RUN_TRY(cudaMemcpyAsync(out->tally, snap, snap_len * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RUN_TRY(cudaMemcpyAsync(out->stats, stats, MCBTE_NSTATS * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (out->events_pp)
+      RUN_TRY(cudaMemcpyAsync(out->events_pp, w.events_pp, p->n_particles * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    release();
+    own = false;
+    RUN_TRY(cudaStreamSynchronize(s));
+    const double code = out->stats[MCBTE_STAT_STATUS];
+    if (code == (double)MCBTE_ERR_TIMEOUT) result = fail(MCBTE_ERR_TIMEOUT, "run: time budget exceeded");
+    else if (code == (double)MCBTE_WARN_TRUNCATED) result = fail(MCBTE_WARN_TRUNCATED, "run: some particles reached max_events");
+  } else {
+    release();
+  }
+#undef RUN_TRY
+  return result;
+}
+
+}  // extern "C"

@@ -1,0 +1,264 @@
+// Device-side building blocks of the MCBTE GB300 library: Philox4x32-10,
+// random-word maps, per-run geometry records, ray / face / pore hits and
+// direction sampling.  Everything here is templated on the tracing real
+// type R (double for the FP64 path, float for the FP32 path).
+//
+// Internal units: length nm, time ps, velocity nm/ps.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/mcbte.h"
+
+namespace mcbte {
+
+constexpr int kMaxGeoms = 128;
+constexpr int kMaxSources = 8;
+constexpr int kMaxDirs = 16;
+constexpr int kMaxPeriods = 65;
+
+// ------------------------------------------------------------------ per-run records
+// Geometry as the tracer sees it, derived on the device by the setup kernel
+// from the caller's SI descriptor (lengths in nm, specularities as 32-bit
+// integer thresholds, isothermal faces and sources resolved).
+struct GeoRun {
+  double L[3];
+  double cx, cy, r2;
+  float Lf[3];
+  float cxf, cyf, r2f;
+  uint64_t pthr[6];
+  uint64_t pthr_pore;
+  int type[6];
+  int pore;
+  int n_src;
+  int src_kind[kMaxSources];   // 0 isothermal face, 1 body (control gradient), 2 initial Gaussian
+  int src_face[kMaxSources];
+  uint64_t src_thr[kMaxSources];
+  double face_sign[6];         // sign of T_b - T_eq of isothermal faces
+  int grad_axis;
+  double grad_sign;
+  double gauss_c[3];
+  double gauss_sigma;
+  double gauss_sign;
+  double p_pore;
+  double E_tot;                // W (steady) or J (transient)
+  double V_solid;              // m^3
+  double V_box;                // m^3
+  double kappa_grad;           // K/m that defines kappa along the tally axis
+  uint64_t n;                  // particles of this geometry
+  uint64_t offset;             // first flattened particle index
+};
+
+// Material as the tracer sees it (device pointers).
+struct MatView {
+  int n;
+  const uint4* rec_emit;    // alias records ~ C v   {thr_lo, thr_hi, alias, 0}
+  const uint4* rec_init;    // alias records ~ C
+  const uint4* rec_relax;   // alias records ~ C / tau
+  const float4* binf;       // {v (nm/ps), 1/v (ps/nm), Lambda (nm), 0}
+  const double* v_d;        // nm/ps
+  const double* inv_v_d;    // ps/nm
+  const double* lam_d;      // nm
+  const double* pi;         // relaxation pmf (C/tau) / sum(C/tau)
+  const double* sums;       // [3] sum C, sum C v, sum C / tau  (SI)
+};
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw (SC'11): ten rounds of two 32x32->64 products
+// with multipliers 0xD2511F53 / 0xCD9E8D57, Weyl key schedule
+// 0x9E3779B9 / 0xBB67AE85.
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// ------------------------------------------------------------------ FP64 elementary functions
+// Fixed-order series (no library transcendental), so the FP64 tracer is a
+// deterministic function of its random words on any IEEE-754 double
+// arithmetic without fused multiply-add (this translation unit is built
+// with --fmad=false).
+//
+// ln x: x = m 2^e, m folded into [sqrt(2)/2, sqrt(2)], ln x = e ln 2 +
+// 2 atanh((m-1)/(m+1)); atanh by its Taylor series through z^25
+// (Abramowitz & Stegun 4.1.27), Horner from the highest coefficient.
+__device__ __forceinline__ double series_log(double x) {
+  const long long bits = __double_as_longlong(x);
+  int ex = (int)((bits >> 52) & 0x7ffll) - 1023;
+  double m = __longlong_as_double((bits & 0x000fffffffffffffll) | 0x3ff0000000000000ll);
+  if (m > 1.4142135623730951) {
+    m = m * 0.5;
+    ex = ex + 1;
+  }
+  const double z = (m - 1.0) / (m + 1.0);
+  const double z2 = z * z;
+  // 1/(2k+1) for k = 12 down to 1
+  const double inv_odd[12] = {0.04, 0.043478260869565216, 0.047619047619047616, 0.05263157894736842,
+                              0.058823529411764705, 0.06666666666666667, 0.07692307692307693, 0.09090909090909091,
+                              0.1111111111111111, 0.14285714285714285, 0.2, 0.3333333333333333};
+  double p = inv_odd[0];
+#pragma unroll
+  for (int k = 1; k < 12; ++k) p = inv_odd[k] + z2 * p;
+  const double lm = 2.0 * (z + z * (z2 * p));
+  return (double)ex * 0.6931471805599453 + lm;
+}
+
+// cos(2 pi r), sin(2 pi r), r in [0, 1): octant reduction to theta in
+// [0, pi/4], Taylor polynomials of sin (to theta^15) and cos (to theta^16)
+// by Horner from the highest coefficient, then the octant symmetries.
+__device__ __forceinline__ void series_sincos2pi(double r, double* sn, double* cs) {
+  const double t = r * 8.0;
+  const int oct = (int)t;
+  double f = t - (double)oct;
+  if (oct & 1) f = 1.0 - f;
+  const double th = f * 0.7853981633974483;
+  const double t2 = th * th;
+  const double sc[8] = {-7.647163731819816e-13, 1.6059043836821613e-10, -2.505210838544172e-08,
+                        2.7557319223985893e-06, -0.0001984126984126984, 0.008333333333333333,
+                        -0.16666666666666666, 1.0};
+  const double cc[9] = {4.779477332387385e-14, -1.1470745597729725e-11, 2.08767569878681e-09,
+                        -2.755731922398589e-07, 2.48015873015873e-05, -0.001388888888888889,
+                        0.041666666666666664, -0.5, 1.0};
+  double ps = sc[0];
+#pragma unroll
+  for (int k = 1; k < 8; ++k) ps = sc[k] + t2 * ps;
+  double pc = cc[0];
+#pragma unroll
+  for (int k = 1; k < 9; ++k) pc = cc[k] + t2 * pc;
+  const double S = th * ps;
+  const double C = pc;
+  switch (oct & 7) {
+    case 0: *cs = C; *sn = S; break;
+    case 1: *cs = S; *sn = C; break;
+    case 2: *cs = -S; *sn = C; break;
+    case 3: *cs = -C; *sn = S; break;
+    case 4: *cs = -C; *sn = -S; break;
+    case 5: *cs = -S; *sn = -C; break;
+    case 6: *cs = S; *sn = -C; break;
+    default: *cs = C; *sn = -S; break;
+  }
+}
+
+// ------------------------------------------------------------------ real maps
+template <typename R> struct Num;
+
+template <> struct Num<double> {
+  static __device__ __forceinline__ double oc(uint32_t w) { return ((double)w + 1.0) * 2.3283064365386963e-10; }
+  static __device__ __forceinline__ double co(uint32_t w) { return (double)w * 2.3283064365386963e-10; }
+  static __device__ __forceinline__ double mid(uint32_t w) { return ((double)w + 0.5) * 2.3283064365386963e-10; }
+  static __device__ __forceinline__ double oc53(uint32_t lo, uint32_t hi) {
+    const uint64_t m = ((uint64_t)hi << 21) ^ (uint64_t)(lo >> 11);
+    return ((double)m + 1.0) * 1.1102230246251565e-16;
+  }
+  static __device__ __forceinline__ double log_(double x) { return series_log(x); }
+  static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+  static __device__ __forceinline__ void sincos2pi(double r, double* s, double* c) { series_sincos2pi(r, s, c); }
+  static __device__ __forceinline__ double fmax_(double a, double b) { return fmax(a, b); }
+  static __device__ __forceinline__ double big() { return 1.0e300; }
+};
+
+template <> struct Num<float> {
+  static __device__ __forceinline__ float oc(uint32_t w) { return (float)((w >> 8) + 1u) * 5.9604644775390625e-8f; }
+  static __device__ __forceinline__ float co(uint32_t w) { return (float)(w >> 8) * 5.9604644775390625e-8f; }
+  static __device__ __forceinline__ float mid(uint32_t w) { return ((float)(w >> 8) + 0.5f) * 5.9604644775390625e-8f; }
+  static __device__ __forceinline__ float oc53(uint32_t lo, uint32_t hi) {
+    (void)lo;
+    return (float)((hi >> 8) + 1u) * 5.9604644775390625e-8f;
+  }
+  static __device__ __forceinline__ float log_(float x) { return __logf(x); }
+  static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+  static __device__ __forceinline__ void sincos2pi(float r, float* s, float* c) {
+    __sincosf(6.28318530717958647f * r, s, c);
+  }
+  static __device__ __forceinline__ float fmax_(float a, float b) { return fmaxf(a, b); }
+  static __device__ __forceinline__ float big() { return 3.0e38f; }
+};
+
+// Alias draw: column = floor(w * n / 2^32) (exact), keep the column iff the
+// 64-bit word (hi:lo) is below its threshold, else take its alias.
+__device__ __forceinline__ int alias_draw(const uint4* rec, int n, uint32_t wcol, uint32_t lo, uint32_t hi) {
+  const int col = (int)(((uint64_t)wcol * (uint64_t)n) >> 32);
+  const uint4 a = rec[col];
+  const uint64_t thr = ((uint64_t)a.y << 32) | (uint64_t)a.x;
+  const uint64_t r = ((uint64_t)hi << 32) | (uint64_t)lo;
+  return (r < thr) ? col : (int)a.z;
+}
+
+// Face index (paper ID - 1) -> axis and side.
+__device__ __forceinline__ int face_axis(int f) { return (f == 1 || f == 3) ? 0 : ((f == 0 || f == 2) ? 1 : 2); }
+__device__ __forceinline__ int face_is_max(int f) { return (f == 1 || f == 2 || f == 5) ? 1 : 0; }
+__device__ __forceinline__ int axis_min_face(int a) { return a == 0 ? 3 : (a == 1 ? 0 : 4); }
+__device__ __forceinline__ int axis_max_face(int a) { return a == 0 ? 1 : (a == 1 ? 2 : 5); }
+
+template <typename R> __device__ __forceinline__ R geo_L(const GeoRun& g, int a);
+template <> __device__ __forceinline__ double geo_L<double>(const GeoRun& g, int a) { return g.L[a]; }
+template <> __device__ __forceinline__ float geo_L<float>(const GeoRun& g, int a) { return g.Lf[a]; }
+
+// Direction with polar cosine mu about sgn * axis a; axes a+1, a+2 (cyclic)
+// take s cos(phi), s sin(phi), phi = 2 pi co(wphi).
+template <typename R>
+__device__ __forceinline__ void dir_about_axis(R u[3], int a, R sgn, R mu, uint32_t wphi) {
+  const R s = Num<R>::sqrt_(Num<R>::fmax_(R(0), R(1) - mu * mu));
+  R sn, cs;
+  Num<R>::sincos2pi(Num<R>::co(wphi), &sn, &cs);
+  const int a1 = (a == 2) ? 0 : a + 1;
+  const int a2 = (a == 0) ? 2 : (a == 1 ? 0 : 1);
+  u[a] = sgn * mu;
+  u[a1] = s * cs;
+  u[a2] = s * sn;
+}
+
+// First boundary along the ray (faces in the direction of travel, then the
+// pore cylinder); ties go to the lowest paper boundary ID.
+template <typename R>
+__device__ __forceinline__ void first_hit(const GeoRun& g, const R x[3], const R u[3], R* dist, int* face) {
+  R best = Num<R>::big();
+  int bf = 7;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    R d;
+    int f;
+    const R La = geo_L<R>(g, a);
+    if (u[a] > R(0)) { d = (La - x[a]) / u[a]; f = axis_max_face(a); }
+    else if (u[a] < R(0)) { d = (R(0) - x[a]) / u[a]; f = axis_min_face(a); }
+    else continue;
+    if (d < R(0)) d = R(0);
+    if (d < best || (d == best && f < bf)) { best = d; bf = f; }
+  }
+  if (g.pore) {
+    const R cx = sizeof(R) == 8 ? (R)g.cx : (R)g.cxf;
+    const R cy = sizeof(R) == 8 ? (R)g.cy : (R)g.cyf;
+    const R r2 = sizeof(R) == 8 ? (R)g.r2 : (R)g.r2f;
+    const R dx = x[0] - cx, dy = x[1] - cy;
+    const R a = u[0] * u[0] + u[1] * u[1];
+    const R b = dx * u[0] + dy * u[1];
+    if (a > R(0) && b < R(0)) {
+      const R c = (dx * dx + dy * dy) - r2;
+      const R disc = b * b - a * c;
+      if (disc >= R(0)) {
+        R d = c / (Num<R>::sqrt_(disc) - b);
+        if (d < R(0)) d = R(0);
+        if (d < best) { best = d; bf = 6; }
+      }
+    }
+  }
+  *dist = best;
+  *face = bf;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+}  // namespace mcbte

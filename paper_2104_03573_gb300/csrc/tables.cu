@@ -1,0 +1,105 @@
+// Material table build (FP64, on the GPU).
+//
+// Per bin: C_i = D_i dE/dT(omega_i) d_omega_i (Eq. BE_derivative read as the
+// derivative of the Bose-Einstein mode energy, Eq. Nbin), or C_i given
+// (format 2); emission weights C v (Eqs. iso_flux, grad_flux_sim), C
+// (Eq. Nbin) and relaxation weights C / tau (Eq. n_scatt); unit conversion
+// to nm / ps.  Then one thread per table builds Walker's alias table with
+// Vose's two work lists (filled in increasing bin order, popped from the
+// back), so the table is a deterministic function of the weights.
+#include "launch.h"
+
+namespace mcbte {
+
+namespace {
+
+__device__ __forceinline__ double dEdT(double omega, double T) {
+  const double kHbar = 1.054571817e-34;
+  const double kBoltz = 1.380649e-23;
+  const double x = (kHbar * omega) / (kBoltz * T);
+  const double h = 0.5 * x;
+  const double s = sinh(h);
+  return kBoltz * (h * h) / (s * s);
+}
+
+__global__ void k_bins(MatBuild b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= b.n) return;
+  double C;
+  if (b.C_in) C = b.C_in[i];
+  else C = (b.D[i] * dEdT(b.omega[i], b.T_lin)) * b.domega[i];
+  b.C[i] = C;
+  b.w_emit[i] = C * b.v[i];
+  b.w_init[i] = C;
+  b.w_relax[i] = C / b.tau[i];
+  const double v_nm = b.v[i] * 1e-3;
+  const double tau_ps = b.tau[i] * 1e12;
+  const double lam = v_nm * tau_ps;
+  const double inv_v = 1.0 / v_nm;
+  b.v_nm[i] = v_nm;
+  b.lam[i] = lam;
+  b.inv_v[i] = inv_v;
+  b.binf[i] = make_float4((float)v_nm, (float)inv_v, (float)lam, 0.0f);
+}
+
+// blockIdx.x = 0..2 builds alias table k (weights C v, C, C / tau);
+// blockIdx.x = 3 forms the sums and the relaxation pmf.  One thread each.
+__global__ void k_alias(MatBuild b) {
+  if (threadIdx.x != 0) return;
+  const int n = b.n;
+  const int k = blockIdx.x;
+  if (k == 3) {
+    double ct = 0.0, cv = 0.0, cr = 0.0;
+    for (int i = 0; i < n; ++i) {
+      ct += b.C[i];
+      cv += b.w_emit[i];
+      cr += b.w_relax[i];
+    }
+    b.sums[0] = ct;
+    b.sums[1] = cv;
+    b.sums[2] = cr;
+    for (int i = 0; i < n; ++i) b.pi[i] = b.w_relax[i] / cr;
+    return;
+  }
+  const double* w = (k == 0) ? b.w_emit : (k == 1 ? b.w_init : b.w_relax);
+  double* p = b.scratch_p + (size_t)k * n;
+  int* small = b.scratch_small + (size_t)k * n;
+  int* large = b.scratch_large + (size_t)k * n;
+  double* prob = b.prob + (size_t)k * n;
+  int32_t* alias = b.alias + (size_t)k * n;
+  double W = 0.0;
+  for (int i = 0; i < n; ++i) W += w[i];
+  int ns = 0, nl = 0;
+  for (int i = 0; i < n; ++i) {
+    p[i] = (w[i] * (double)n) / W;
+    prob[i] = 1.0;
+    alias[i] = i;
+    if (p[i] < 1.0) small[ns++] = i; else large[nl++] = i;
+  }
+  while (ns > 0 && nl > 0) {
+    const int l = small[--ns];
+    const int g = large[--nl];
+    prob[l] = p[l];
+    alias[l] = g;
+    p[g] = (p[g] + p[l]) - 1.0;
+    if (p[g] < 1.0) small[ns++] = g; else large[nl++] = g;
+  }
+  uint64_t* thr = b.thr + (size_t)k * n;
+  uint4* rec = b.rec + (size_t)k * n;
+  for (int i = 0; i < n; ++i) {
+    const double q = prob[i];
+    const uint64_t t = (q >= 1.0) ? UINT64_MAX : (uint64_t)(q * 18446744073709551616.0);
+    thr[i] = t;
+    rec[i] = make_uint4((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)alias[i], 0u);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_material_build(const MatBuild& b, cudaStream_t s) {
+  k_bins<<<(b.n + 255) / 256, 256, 0, s>>>(b);
+  k_alias<<<4, 32, 0, s>>>(b);
+  return cudaGetLastError();
+}
+
+}  // namespace mcbte

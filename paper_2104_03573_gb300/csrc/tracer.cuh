@@ -1,0 +1,451 @@
+// Particle emission and the event step of the deviational tracer, shared by
+// the FP64 plain kernels and the FP32 persistent kernels.
+//
+// Event contract (identical for every precision; the random words are the
+// same, only their real-valued maps differ in width):
+//   counter = (particle id within its geometry, geometry index, event index, sub-block)
+//   key     = (seed low, seed high)
+//   emission (event 0): sub 0 {source, alias column, alias threshold lo, hi}
+//                       sub 1 {direction mu, phi, flight -ln R lo, hi}
+//                       sub 2 {body sign, emission time}
+//                       sub 3+k {position attempt k; Gaussian: Box-Muller words}
+//   relaxation event  : sub 0 {alias column, threshold lo, mu, phi}
+//                       sub 1 {threshold hi, flight -ln R lo, hi}
+//   adiabatic / pore  : sub 0 {specular test, -, mu, phi}
+//   isothermal / periodic walls draw nothing.
+#pragma once
+
+#include "mcbte_device.cuh"
+
+namespace mcbte {
+
+enum { MODE_STEADY = 0, MODE_TRANSIENT = 1, MODE_GRAD = 2 };
+
+struct RunCfg {
+  uint32_t k0, k1;
+  int n_scat_max;
+  uint32_t max_events;
+  int n_cells, cell_axis, tally_axis, per_bin;
+  int n_geoms;
+  uint64_t total;
+  const unsigned long long* t0;   // device timestamp (ns) written by the setup kernel
+  uint64_t budget_ns;             // wall-clock budget of the tracing kernel
+  // gradient
+  int n_dirs;
+  const double* dirs;    // [n_dirs][n_bins]
+  const double* dpi;     // [n_dirs] dirs . pi
+  // transient
+  double t_max_ps;
+  int n_times;
+  const double* t_meas_ps;
+  int grid[3];
+};
+
+// Raw accumulators of a run (device, FP64 unless noted).
+struct Acc {
+  double* cellP;              // [G][nc][4]   per-cell direct / partial-cell sums
+  double* cellD;              // [G][nc+1][4] difference array of full-cell sums
+  double* qbin;               // [G][n_bins]
+  double* dsc;                // [G][8]: sumX, sumX2, signed emitted, signed absorbed, R, Gp, Gp^2, absorbed
+  unsigned long long* cnt;    // [G][4]: events, truncated, max events, traced
+  double* G;                  // [n_bins] sparse part of the LR gradient
+  double* dsum;               // [n_dirs][2]
+  double* snap;               // [n_times][cells][4] transient
+  uint32_t* events_pp;        // [total] or null
+  double* X_pp;               // [total] or null
+  unsigned long long* work;   // [1] persistent work counter
+  int* flags;                 // [1] bit 0: time budget hit
+};
+
+template <typename R>
+struct Particle {
+  R x[3], u[3];
+  R d_rel;          // remaining relaxation distance (nm)
+  R v, inv_v, lam;  // current bin
+  R t;              // ps (transient)
+  R s;              // sign
+  int bin;
+  uint32_t e;
+  int n_relax;
+  uint32_t pid;
+  int g;
+  int mi;           // next measurement index (transient)
+  double X;         // sum s l u_tally (nm)
+  double Xper;      // X at the start of the current relaxation period
+};
+
+template <typename R>
+__device__ __forceinline__ void load_bin(Particle<R>& p, const MatView& M, const float4* binf) {
+  if (sizeof(R) == 8) {
+    p.v = (R)M.v_d[p.bin];
+    p.inv_v = (R)M.inv_v_d[p.bin];
+    p.lam = (R)M.lam_d[p.bin];
+  } else {
+    const float4 b = binf[p.bin];
+    p.v = (R)b.x;
+    p.inv_v = (R)b.y;
+    p.lam = (R)b.z;
+  }
+}
+
+// Emission of particle (pid, g) at event 0 (Sec. 3.2: source by cumulative
+// energy; Secs. 3.2.1-3.2.3: position, bin, sign, direction).
+template <typename R>
+__device__ __forceinline__ void emit(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_emit,
+                                     const uint4* rec_init, const float4* binf, uint32_t k0, uint32_t k1,
+                                     bool transient, R t_max_ps) {
+  uint4 ctr = make_uint4(p.pid, (uint32_t)p.g, 0u, 0u);
+  const uint4 w0 = philox(ctr, k0, k1);
+  ctr.w = 1u;
+  const uint4 w1 = philox(ctr, k0, k1);
+  ctr.w = 2u;
+  const uint4 w2 = philox(ctr, k0, k1);
+  int k = 0;
+  while ((uint64_t)w0.x >= g.src_thr[k]) ++k;
+  const int kind = g.src_kind[k];
+  p.t = R(0);
+  if (kind == 0) {
+    const int f = g.src_face[k];
+    const int a = face_axis(f);
+    const int mx = face_is_max(f);
+    p.bin = alias_draw(rec_emit, M.n, w0.y, w0.z, w0.w);
+    p.s = (R)g.face_sign[f];
+    const R mu = Num<R>::sqrt_(Num<R>::oc(w1.x));
+    dir_about_axis<R>(p.u, a, mx ? R(-1) : R(1), mu, w1.y);
+    if (transient) p.t = Num<R>::co(w2.y) * t_max_ps;
+    ctr.w = 3u;
+    const uint4 w3 = philox(ctr, k0, k1);
+    const int a1 = (a == 2) ? 0 : a + 1;
+    const int a2 = (a == 0) ? 2 : (a == 1 ? 0 : 1);
+    p.x[a] = mx ? geo_L<R>(g, a) : R(0);
+    p.x[a1] = Num<R>::mid(w3.x) * geo_L<R>(g, a1);
+    p.x[a2] = Num<R>::mid(w3.y) * geo_L<R>(g, a2);
+  } else if (kind == 1) {
+    p.bin = alias_draw(rec_emit, M.n, w0.y, w0.z, w0.w);
+    p.s = (w2.x < 0x80000000u) ? R(1) : R(-1);
+    // positive particles travel down the control gradient, negative ones up it
+    const R dsgn = (p.s > R(0)) ? (R)(-g.grad_sign) : (R)g.grad_sign;
+    const R mu = Num<R>::sqrt_(Num<R>::oc(w1.x));
+    dir_about_axis<R>(p.u, g.grad_axis, dsgn, mu, w1.y);
+    const R cx = sizeof(R) == 8 ? (R)g.cx : (R)g.cxf;
+    const R cy = sizeof(R) == 8 ? (R)g.cy : (R)g.cyf;
+    const R r2 = sizeof(R) == 8 ? (R)g.r2 : (R)g.r2f;
+    for (uint32_t attempt = 0;; ++attempt) {
+      ctr.w = 3u + attempt;
+      const uint4 w3 = philox(ctr, k0, k1);
+      p.x[0] = Num<R>::mid(w3.x) * geo_L<R>(g, 0);
+      p.x[1] = Num<R>::mid(w3.y) * geo_L<R>(g, 1);
+      p.x[2] = Num<R>::mid(w3.z) * geo_L<R>(g, 2);
+      if (!g.pore) break;
+      const R dx = p.x[0] - cx, dy = p.x[1] - cy;
+      if (dx * dx + dy * dy >= r2) break;
+      if (attempt + 1 >= 64u) break;
+    }
+  } else {
+    p.bin = alias_draw(rec_init, M.n, w0.y, w0.z, w0.w);
+    p.s = (R)g.gauss_sign;
+    dir_about_axis<R>(p.u, 2, R(1), R(1) - R(2) * Num<R>::oc(w1.x), w1.y);
+    ctr.w = 3u;
+    const uint4 w3 = philox(ctr, k0, k1);
+    const R m1 = Num<R>::sqrt_(R(-2) * Num<R>::log_(Num<R>::oc(w3.x)));
+    const R m2 = Num<R>::sqrt_(R(-2) * Num<R>::log_(Num<R>::oc(w3.z)));
+    R s1, c1, s2, c2;
+    Num<R>::sincos2pi(Num<R>::co(w3.y), &s1, &c1);
+    Num<R>::sincos2pi(Num<R>::co(w3.w), &s2, &c2);
+    const R nrm[3] = {m1 * c1, m1 * s1, m2 * c2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const R La = geo_L<R>(g, a);
+      R c = (R)g.gauss_c[a] + (R)g.gauss_sigma * nrm[a];
+      if (c < R(0)) c = -c;
+      if (c > La) c = R(2) * La - c;
+      if (c < R(0)) c = R(0);
+      if (c > La) c = La;
+      p.x[a] = c;
+    }
+  }
+  load_bin(p, M, binf);
+  p.d_rel = p.lam * (-Num<R>::log_(Num<R>::oc53(w1.z, w1.w)));
+  p.e = 0u;
+  p.n_relax = 0;
+  p.X = 0.0;
+  p.Xper = 0.0;
+}
+
+// Plain per-cell track-length tally: every cell the segment crosses gets its
+// own path length (global FP64 atomics).
+template <typename R>
+__device__ __forceinline__ void cells_plain(double* P, int nc, int ca, R h, const R x[3], const R u[3], R seg, R s,
+                                            R inv_v) {
+  const R z0 = x[ca];
+  const R z1 = z0 + seg * u[ca];
+  if (u[ca] == R(0)) {
+    int c = (int)floor((double)(z0 / h));
+    c = min(max(c, 0), nc - 1);
+    atomicAdd(&P[c * 4 + 0], (double)((s * seg) * inv_v));
+#pragma unroll
+    for (int b = 0; b < 3; ++b) atomicAdd(&P[c * 4 + 1 + b], (double)((s * seg) * u[b]));
+    return;
+  }
+  const R zlo = z0 < z1 ? z0 : z1;
+  const R zhi = z0 < z1 ? z1 : z0;
+  const int clo = min(max((int)floor((double)(zlo / h)), 0), nc - 1);
+  const int chi = min(max((int)floor((double)(zhi / h)), 0), nc - 1);
+  const R au = u[ca] < R(0) ? -u[ca] : u[ca];
+  for (int c = clo; c <= chi; ++c) {
+    R lo = zlo > (R)c * h ? zlo : (R)c * h;
+    const R ch = (R)(c + 1) * h;
+    R hi = zhi < ch ? zhi : ch;
+    if (c == nc - 1) hi = zhi;
+    if (c == 0) lo = zlo;
+    const R ov = hi - lo;
+    if (ov <= R(0)) continue;
+    const R l = ov / au;
+    atomicAdd(&P[c * 4 + 0], (double)((s * l) * inv_v));
+#pragma unroll
+    for (int b = 0; b < 3; ++b) atomicAdd(&P[c * 4 + 1 + b], (double)((s * l) * u[b]));
+  }
+}
+
+// Difference-array track-length tally: the (up to) two partial end cells go
+// to P, the run of full cells in between is one +/- pair in D; the final
+// per-cell value is P[c] + sum_{c' <= c} D[c'].  At most 4 x 4 adds per
+// segment, whatever the number of cells crossed.
+template <typename R>
+__device__ __forceinline__ void cells_diff(double* P, double* D, int nc, int ca, R h, R inv_h, const R x[3],
+                                           const R u[3], R seg, R s, R inv_v) {
+  const R z0 = x[ca];
+  const R uz = u[ca];
+  if (uz == R(0)) {
+    int c = min(max((int)(z0 * inv_h), 0), nc - 1);
+    const R sl = s * seg;
+    atomicAdd(&P[c * 4 + 0], (double)(sl * inv_v));
+    atomicAdd(&P[c * 4 + 1], (double)(sl * u[0]));
+    atomicAdd(&P[c * 4 + 2], (double)(sl * u[1]));
+    atomicAdd(&P[c * 4 + 3], (double)(sl * u[2]));
+    return;
+  }
+  const R z1 = z0 + seg * uz;
+  const R zlo = z0 < z1 ? z0 : z1;
+  const R zhi = z0 < z1 ? z1 : z0;
+  const int clo = min(max((int)(zlo * inv_h), 0), nc - 1);
+  const int chi = min(max((int)(zhi * inv_h), 0), nc - 1);
+  const R k = s / (uz < R(0) ? -uz : uz);      // per unit of axial length
+  const R f0 = k * inv_v, f1 = k * u[0], f2 = k * u[1], f3 = k * u[2];
+  if (clo == chi) {
+    const R dz = zhi - zlo;
+    atomicAdd(&P[clo * 4 + 0], (double)(f0 * dz));
+    atomicAdd(&P[clo * 4 + 1], (double)(f1 * dz));
+    atomicAdd(&P[clo * 4 + 2], (double)(f2 * dz));
+    atomicAdd(&P[clo * 4 + 3], (double)(f3 * dz));
+    return;
+  }
+  const R dlo = (R)(clo + 1) * h - zlo;
+  const R dhi = zhi - (R)chi * h;
+  atomicAdd(&P[clo * 4 + 0], (double)(f0 * dlo));
+  atomicAdd(&P[clo * 4 + 1], (double)(f1 * dlo));
+  atomicAdd(&P[clo * 4 + 2], (double)(f2 * dlo));
+  atomicAdd(&P[clo * 4 + 3], (double)(f3 * dlo));
+  atomicAdd(&P[chi * 4 + 0], (double)(f0 * dhi));
+  atomicAdd(&P[chi * 4 + 1], (double)(f1 * dhi));
+  atomicAdd(&P[chi * 4 + 2], (double)(f2 * dhi));
+  atomicAdd(&P[chi * 4 + 3], (double)(f3 * dhi));
+  if (chi > clo + 1) {
+    const double g0 = (double)(f0 * h), g1 = (double)(f1 * h), g2 = (double)(f2 * h), g3 = (double)(f3 * h);
+    atomicAdd(&D[(clo + 1) * 4 + 0], g0);
+    atomicAdd(&D[(clo + 1) * 4 + 1], g1);
+    atomicAdd(&D[(clo + 1) * 4 + 2], g2);
+    atomicAdd(&D[(clo + 1) * 4 + 3], g3);
+    atomicAdd(&D[chi * 4 + 0], -g0);
+    atomicAdd(&D[chi * 4 + 1], -g1);
+    atomicAdd(&D[chi * 4 + 2], -g2);
+    atomicAdd(&D[chi * 4 + 3], -g3);
+  }
+}
+
+// Likelihood-ratio bookkeeping of one particle (steady gradient runs).
+struct GradState {
+  int np;
+  int bin[kMaxPeriods];
+  double A[kMaxPeriods];
+  double B[kMaxPeriods];
+  int n_res;
+  double sum_x_res;
+  double PA, PB;
+};
+
+// Outcome of one event step.
+enum { STEP_ALIVE = 0, STEP_ABSORBED = 1, STEP_DONE = 2, STEP_TRUNCATED = 3 };
+
+// The event that ends a flight (Sec. 3.3 cases i/iii; Secs. 3.5.2-3.5.6):
+// relaxation (bin redrawn ~ C/tau, isotropic direction, new clock, sign
+// kept), or the boundary `face` (isothermal: absorbed; periodic: translated
+// to the opposite face; adiabatic / pore: specular with probability p, else
+// Lambertian about the inward normal).  The particle has already moved.
+template <typename R, bool GRAD>
+__device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_relax,
+                                           const float4* binf, const RunCfg& C, bool relax, int face, R seg,
+                                           double* qb, GradState* gs) {
+  ++p.e;
+  uint4 ctr = make_uint4(p.pid, (uint32_t)p.g, p.e, 0u);
+  if (relax) {
+    ++p.n_relax;
+    if (C.n_scat_max > 0 && p.n_relax >= C.n_scat_max) return STEP_DONE;
+    // the relaxation period in this bin is over: frequency-resolved flux
+    if (qb) {
+      atomicAdd(&qb[p.bin], p.X - p.Xper);
+      p.Xper = p.X;
+    }
+    const uint4 w = philox(ctr, C.k0, C.k1);
+    ctr.w = 1u;
+    const uint4 w1 = philox(ctr, C.k0, C.k1);
+    p.bin = alias_draw(rec_relax, M.n, w.x, w.y, w1.x);
+    dir_about_axis<R>(p.u, 2, R(1), R(1) - R(2) * Num<R>::oc(w.z), w.w);
+    load_bin(p, M, binf);
+    p.d_rel = p.lam * (-Num<R>::log_(Num<R>::oc53(w1.y, w1.z)));
+    if (GRAD) {
+      if (gs->np < kMaxPeriods) {
+        gs->bin[gs->np] = p.bin;
+        gs->A[gs->np] = -1.0;
+        gs->B[gs->np] = -p.X;
+        gs->np++;
+      }
+      gs->n_res++;
+      gs->sum_x_res += p.X;
+    }
+    return STEP_ALIVE;
+  }
+  p.d_rel = p.d_rel - seg;
+  if (face < 6) {
+    const int a = face_axis(face);
+    const int mx = face_is_max(face);
+    const R La = geo_L<R>(g, a);
+    p.x[a] = mx ? La : R(0);
+    const int ty = g.type[face];
+    if (ty == MCBTE_FACE_ISOTHERMAL) return STEP_ABSORBED;
+    if (ty == MCBTE_FACE_PERIODIC) {
+      p.x[a] = mx ? R(0) : La;
+      return STEP_ALIVE;
+    }
+    const uint4 w = philox(ctr, C.k0, C.k1);
+    if ((uint64_t)w.x < g.pthr[face]) {
+      p.u[a] = -p.u[a];
+    } else {
+      dir_about_axis<R>(p.u, a, mx ? R(-1) : R(1), Num<R>::sqrt_(Num<R>::oc(w.z)), w.w);
+    }
+    return STEP_ALIVE;
+  }
+  // pore wall: the cylinder's outward normal points into the solid
+  const R cx = sizeof(R) == 8 ? (R)g.cx : (R)g.cxf;
+  const R cy = sizeof(R) == 8 ? (R)g.cy : (R)g.cyf;
+  R nx = p.x[0] - cx, ny = p.x[1] - cy;
+  const R len = Num<R>::sqrt_(nx * nx + ny * ny);
+  nx = nx / len;
+  ny = ny / len;
+  const uint4 w = philox(ctr, C.k0, C.k1);
+  const bool spec = (uint64_t)w.x < g.pthr_pore;
+  if (GRAD) {
+    const double sc = spec ? 1.0 / g.p_pore : -1.0 / (1.0 - g.p_pore);
+    gs->PA += sc;
+    gs->PB += sc * p.X;
+  }
+  if (spec) {
+    const R un = p.u[0] * nx + p.u[1] * ny;
+    p.u[0] = p.u[0] - (R(2) * un) * nx;
+    p.u[1] = p.u[1] - (R(2) * un) * ny;
+  } else {
+    const R mu = Num<R>::sqrt_(Num<R>::oc(w.z));
+    const R sn = Num<R>::sqrt_(Num<R>::fmax_(R(0), R(1) - mu * mu));
+    R sphi, cphi;
+    Num<R>::sincos2pi(Num<R>::co(w.w), &sphi, &cphi);
+    const R sc = sn * cphi;
+    p.u[0] = mu * nx - sc * ny;
+    p.u[1] = mu * ny + sc * nx;
+    p.u[2] = sn * sphi;
+  }
+  return STEP_ALIVE;
+}
+
+// One flight + event of a steady (or gradient) particle: first hit vs the
+// remaining relaxation distance (boundary wins ties, Sec. 3.3 case iii),
+// track-length tallies of the flight (Eqs. temp_steady, flux_x_steady), then
+// the event.  CELLS: 0 none, 1 plain per-cell, 2 difference array.
+template <typename R, int CELLS, bool GRAD>
+__device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_relax,
+                                           const float4* binf, const RunCfg& C, double* cP, double* cD, R h,
+                                           R inv_h, double* qb, GradState* gs) {
+  if (p.e + 1u >= C.max_events) return STEP_TRUNCATED;
+  R db;
+  int face;
+  first_hit<R>(g, p.x, p.u, &db, &face);
+  const bool relax = p.d_rel < db;
+  const R seg = relax ? p.d_rel : db;
+  const int ta = C.tally_axis;
+  const R contrib = (p.s * seg) * p.u[ta];
+  const double Xb = p.X;
+  p.X += (double)contrib;
+  if (CELLS == 1) cells_plain<R>(cP, C.n_cells, C.cell_axis, h, p.x, p.u, seg, p.s, p.inv_v);
+  if (CELLS == 2) cells_diff<R>(cP, cD, C.n_cells, C.cell_axis, h, inv_h, p.x, p.u, seg, p.s, p.inv_v);
+  if (GRAD) {
+    double score = (double)(seg / p.lam);
+    if (relax) score = score - 1.0;
+    gs->A[gs->np - 1] += score;
+    gs->B[gs->np - 1] += score * Xb;
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
+  return apply_event<R, GRAD>(p, g, M, rec_relax, binf, C, relax, face, seg, qb, gs);
+}
+
+// One flight + event of a transient particle: the flight also ends at
+// t_max (Sec. 3.5.6); every measurement time t_m inside the flight's
+// interval [t, t_end) (closed at t_max) adds the particle's snapshot to its
+// detector cell (Eq. sampling, Sec. 3.4).
+template <typename R>
+__device__ __forceinline__ int step_transient(Particle<R>& p, const GeoRun& g, const MatView& M,
+                                              const uint4* rec_relax, const float4* binf, const RunCfg& C,
+                                              double* snap) {
+  if (p.e + 1u >= C.max_events) return STEP_TRUNCATED;
+  R db;
+  int face;
+  first_hit<R>(g, p.x, p.u, &db, &face);
+  const R v = p.v;
+  const R tmax = (R)C.t_max_ps;
+  const R d_end = (tmax - p.t) * v;
+  bool fin = false, relax = false;
+  R seg;
+  if (d_end <= p.d_rel && d_end <= db) { fin = true; seg = d_end; }
+  else if (p.d_rel < db) { relax = true; seg = p.d_rel; }
+  else { seg = db; }
+  const R t_end = (sizeof(R) == 8) ? p.t + seg / v : p.t + seg * p.inv_v;
+  const int nx = C.grid[0], ny = C.grid[1], nz = C.grid[2];
+  const size_t ncell = (size_t)nx * ny * nz;
+  while (p.mi < C.n_times) {
+    const R tm = (R)C.t_meas_ps[p.mi];
+    if (!(tm < t_end || (fin && tm <= t_end))) break;
+    const R dist = v * (tm - p.t);
+    R pm[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) pm[a] = p.x[a] + dist * p.u[a];
+    int ix = (int)floor((double)(pm[0] / (geo_L<R>(g, 0) / (R)nx)));
+    int iy = (int)floor((double)(pm[1] / (geo_L<R>(g, 1) / (R)ny)));
+    int iz = (int)floor((double)(pm[2] / (geo_L<R>(g, 2) / (R)nz)));
+    ix = min(max(ix, 0), nx - 1);
+    iy = min(max(iy, 0), ny - 1);
+    iz = min(max(iz, 0), nz - 1);
+    const size_t c = ((size_t)p.mi * ncell + ((size_t)iz * ny + iy) * nx + ix) * 4;
+    const R sv = p.s * v;
+    atomicAdd(&snap[c + 0], (double)p.s);
+    atomicAdd(&snap[c + 1], (double)(sv * p.u[0]));
+    atomicAdd(&snap[c + 2], (double)(sv * p.u[1]));
+    atomicAdd(&snap[c + 3], (double)(sv * p.u[2]));
+    ++p.mi;
+  }
+  p.t = t_end;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
+  if (fin) return STEP_DONE;
+  return apply_event<R, false>(p, g, M, rec_relax, binf, C, relax, face, seg, nullptr, nullptr);
+}
+
+}  // namespace mcbte

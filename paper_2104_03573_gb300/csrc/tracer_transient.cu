@@ -1,0 +1,199 @@
+// Transient tracing (Secs. 3.2-3.5): wall sources emit at t0 = R t_max, the
+// initial condition at t0 = 0 (Sec. 3.2); every measurement time inside a
+// particle's life adds its snapshot to the detector grid (Eq. sampling).
+// FP64 plain kernel (one thread per particle) and persistent FP32 kernel
+// (per-lane refill, alias tables in shared memory, FP64 L2 atomics into the
+// [time][cell][T, qx, qy, qz] tally, which is far larger than shared memory).
+#include "launch.h"
+
+#ifndef MCBTE_F64
+#define MCBTE_F64 0
+#endif
+#ifndef MCBTE_F32
+#define MCBTE_F32 0
+#endif
+
+namespace mcbte {
+
+namespace {
+
+template <typename R>
+__device__ __forceinline__ void transient_start(Particle<R>& p, const RunCfg& C) {
+  p.mi = 0;
+  while (p.mi < C.n_times && (R)C.t_meas_ps[p.mi] < p.t) ++p.mi;
+}
+
+template <typename R>
+__device__ __forceinline__ void transient_finish(const Particle<R>& p, int out, uint64_t idx, const Acc& A) {
+  const unsigned long long nev = (unsigned long long)p.e + 1ull;
+  atomicAdd(&A.cnt[0], nev);
+  if (out == STEP_TRUNCATED) atomicAdd(&A.cnt[1], 1ull);
+  atomicMax(&A.cnt[2], nev);
+  atomicAdd(&A.cnt[3], 1ull);
+  atomicAdd(&A.dsc[2], (double)p.s);
+  if (out == STEP_ABSORBED) {
+    atomicAdd(&A.dsc[3], (double)p.s);
+    atomicAdd(&A.dsc[7], 1.0);
+  }
+  if (A.events_pp) A.events_pp[idx] = (uint32_t)nev;
+}
+
+#if MCBTE_F64
+__global__ void __launch_bounds__(256) k_transient_fp64(const GeoRun* __restrict__ geos, MatView M, RunCfg C, Acc A) {
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= C.total) return;
+  const GeoRun& G = geos[0];
+  const uint64_t deadline = *C.t0 + C.budget_ns;
+  Particle<double> p;
+  p.pid = (uint32_t)idx;
+  p.g = 0;
+  emit<double>(p, G, M, M.rec_emit, M.rec_init, nullptr, C.k0, C.k1, true, C.t_max_ps);
+  transient_start(p, C);
+  int out;
+  for (;;) {
+    out = step_transient<double>(p, G, M, M.rec_relax, nullptr, C, A.snap);
+    if (out != STEP_ALIVE) break;
+    if ((p.e & 1023u) == 0u && globaltimer_ns() > deadline) {
+      atomicOr(A.flags, 1);
+      out = STEP_TRUNCATED;
+      break;
+    }
+  }
+  transient_finish(p, out, idx, A);
+}
+
+#endif  // MCBTE_F64
+#if MCBTE_F32
+__global__ void __launch_bounds__(512) k_transient_f32(const GeoRun* __restrict__ geos, MatView M, RunCfg C, Acc A,
+                                                       SmemPlan S) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned char* sp = smem;
+  const int n = M.n;
+  const uint4* relax = M.rec_relax;
+  const float4* binf = M.binf;
+  if (S.relax_in_smem) {
+    uint4* t = reinterpret_cast<uint4*>(sp);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) t[i] = M.rec_relax[i];
+    relax = t;
+    sp += (size_t)n * sizeof(uint4);
+  }
+  if (S.binf_in_smem) {
+    float4* t = reinterpret_cast<float4*>(sp);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) t[i] = M.binf[i];
+    binf = t;
+  }
+  __syncthreads();
+  const GeoRun& G = geos[0];
+  const uint64_t deadline = *C.t0 + C.budget_ns;
+  const unsigned lane = threadIdx.x & 31u;
+  Particle<float> p;
+  bool alive = false;
+  uint64_t idx = 0;
+  for (;;) {
+    const unsigned act = __activemask();
+    const unsigned need = __ballot_sync(act, !alive);
+    if (need) {
+      const int leader = __ffs(need) - 1;
+      unsigned long long base = 0;
+      if ((int)lane == leader) base = atomicAdd(A.work, (unsigned long long)__popc(need));
+      base = __shfl_sync(act, base, leader);
+      if (!alive) {
+        idx = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
+        if (idx >= C.total) break;
+        if (*(volatile int*)A.flags & 1) break;
+        p.pid = (uint32_t)idx;
+        p.g = 0;
+        emit<float>(p, G, M, M.rec_emit, M.rec_init, binf, C.k0, C.k1, true, (float)C.t_max_ps);
+        transient_start(p, C);
+        alive = true;
+      }
+    }
+    int out = step_transient<float>(p, G, M, relax, binf, C, A.snap);
+    if (out == STEP_ALIVE && (p.e & 255u) == 0u && globaltimer_ns() > deadline) {
+      atomicOr(A.flags, 1);
+      out = STEP_TRUNCATED;
+    }
+    if (out != STEP_ALIVE) {
+      transient_finish(p, out, idx, A);
+      alive = false;
+    }
+  }
+}
+
+#endif  // MCBTE_F32
+#if MCBTE_F64
+// Scale the raw snapshot sums: T = s E_eff / (C V_cell), q = s E_eff V_g / V_cell.
+__global__ void k_finalize_transient(const GeoRun* geos, MatView M, RunCfg C, Acc A, double* tally, double* stats,
+                                     size_t n_cells_total) {
+  const GeoRun& G = geos[0];
+  const double E_eff = G.E_tot / (double)G.n;
+  const double Vc = G.V_box / (double)((size_t)C.grid[0] * C.grid[1] * C.grid[2]);
+  const double kT = E_eff / (M.sums[0] * Vc);
+  const double kq = E_eff / Vc;
+  const size_t total = (size_t)C.n_times * n_cells_total;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const double* r = A.snap + i * 4;
+    double* o = tally + i * 4;
+    const double a0 = r[0], a1 = r[1], a2 = r[2], a3 = r[3];
+    o[0] = kT * a0;
+    o[1] = (kq * a1) * 1e3;
+    o[2] = (kq * a2) * 1e3;
+    o[3] = (kq * a3) * 1e3;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int k = 0; k < MCBTE_NSTATS; ++k) stats[k] = 0.0;
+    stats[MCBTE_STAT_EVENTS] = (double)A.cnt[0];
+    stats[MCBTE_STAT_TRUNCATED] = (double)A.cnt[1];
+    stats[MCBTE_STAT_MAX_EVENTS] = (double)A.cnt[2];
+    stats[MCBTE_STAT_N] = (double)A.cnt[3];
+    stats[MCBTE_STAT_E_TOT] = G.E_tot;
+    stats[MCBTE_STAT_SIGNED_EMITTED] = A.dsc[2];
+    stats[MCBTE_STAT_SIGNED_ABSORBED] = A.dsc[3];
+    stats[MCBTE_STAT_ABSORBED] = A.dsc[7];
+    stats[MCBTE_STAT_STATUS] = (A.flags[0] & 1) ? (double)MCBTE_ERR_TIMEOUT
+                                                : (A.cnt[1] ? (double)MCBTE_WARN_TRUNCATED : 0.0);
+  }
+}
+
+#endif  // MCBTE_F64
+}  // namespace
+
+#if MCBTE_F64
+cudaError_t launch_transient(int precision, const GeoRun* geos, const MatView& M, const RunCfg& C, const Acc& A,
+                             int threads, int bps, cudaStream_t s) {
+  if (precision == MCBTE_FP64_PLAIN) {
+    const uint64_t blocks = (C.total + 255) / 256;
+    k_transient_fp64<<<(unsigned)blocks, 256, 0, s>>>(geos, M, C, A);
+    return cudaGetLastError();
+  }
+  return launch_transient_f32(geos, M, C, A, threads > 0 ? threads : 256, bps, s);
+}
+
+#endif  // MCBTE_F64
+#if MCBTE_F32
+cudaError_t launch_transient_f32(const GeoRun* geos, const MatView& M, const RunCfg& C, const Acc& A, int threads,
+                                 int bps, cudaStream_t s) {
+  const SmemPlan S = plan_smem_f32(M.n, 1, 0, 0, 200 * 1024);
+  const int t = threads;
+  cudaError_t e = cudaFuncSetAttribute(k_transient_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.bytes);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transient_f32, t, S.bytes);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  const int b = (bps > 0 && bps < occ) ? bps : occ;
+  k_transient_f32<<<sm_count() * b, t, S.bytes, s>>>(geos, M, C, A, S);
+  return cudaGetLastError();
+}
+
+#endif  // MCBTE_F32
+#if MCBTE_F64
+cudaError_t launch_finalize_transient(const GeoRun* geos, const MatView& M, const RunCfg& C, const Acc& A,
+                                      double* tally, double* stats, size_t n_cells_total, cudaStream_t s) {
+  k_finalize_transient<<<sm_count() * 4, 256, 0, s>>>(geos, M, C, A, tally, stats, n_cells_total);
+  return cudaGetLastError();
+}
+
+#endif  // MCBTE_F64
+
+}  // namespace mcbte

@@ -59,6 +59,29 @@ def test_philox_counter_sensitivity():
         assert all(int(a) != int(b) for a, b in zip(o, base))
 
 
+# ------------------------------------------------------------------ elementary functions
+def test_series_log_accuracy():
+    rng = np.random.default_rng(1)
+    xs = np.concatenate([rng.uniform(0, 1, 4000), 2.0 ** -rng.uniform(0, 53, 4000),
+                         [1.0, 0.5, 2 ** -53, 2 ** -32, 1 - 2 ** -53, 0.7071067811865476, 1.4142135623730951 / 2]])
+    xs = xs[xs > 0]
+    for x in xs:
+        got = oracle.series_log(x)
+        ref = math.log(x)
+        assert abs(got - ref) <= 4 * np.spacing(abs(ref)) + 1e-300, (x, got, ref)
+    assert oracle.series_log(1.0) == 0.0
+
+
+def test_series_sincos2pi_accuracy():
+    rng = np.random.default_rng(2)
+    rs = np.concatenate([rng.uniform(0, 1, 5000), np.arange(16) / 16.0, [1 - 2 ** -32]])
+    for r in rs:
+        s, c = oracle.series_sincos2pi(r)
+        a = 2 * math.pi * r
+        assert abs(s - math.sin(a)) < 1e-15 and abs(c - math.cos(a)) < 1e-15, (r, s, c)
+        assert abs(s * s + c * c - 1.0) < 1e-15
+
+
 # ------------------------------------------------------------------ tables
 def _exact_alias_law(thr, al):
     n = len(thr)
