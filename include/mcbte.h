@@ -167,6 +167,8 @@ typedef struct {
   int threads_per_block;       /* 0 = default                                            */
   int blocks_per_sm;           /* 0 = default                                            */
   double time_budget_s;        /* 0 = 120 s; the kernel stops and reports TIMEOUT        */
+  void* trace_event_start;     /* optional cudaEvent_t recorded on `stream` just before   */
+  void* trace_event_stop;      /* and just after the tracing kernel (NULL = none)         */
 } mcbte_steady_params;
 
 typedef struct {
@@ -210,6 +212,8 @@ typedef struct {
   int threads_per_block;
   int blocks_per_sm;
   double time_budget_s;
+  void* trace_event_start;     /* optional cudaEvent_t pair around the tracing kernel     */
+  void* trace_event_stop;
 } mcbte_transient_params;
 
 typedef struct {

@@ -189,9 +189,10 @@ def gray_slab_c1(n: int = 100_000) -> Workload:
 
 
 def si_slab_c2(n: int = 10_000_000, material: Optional[Material] = None) -> Workload:
-    """Silicon-like cross-plane film L=1 um, 3000 bins, per-bin flux tallies."""
+    """Silicon-like cross-plane film L=1 um (a 1 um cube, periodic x, y),
+    3000 bins, per-bin flux tallies."""
     return Workload("si_slab_L1um_3000bins", material or bvk_holland(),
-                    [slab_z(1e-6, 300.5, 299.5)],
+                    [slab_z(1e-6, 300.5, 299.5, lateral=1e-6)],
                     SteadyRun(n=n, seed=1002, n_cells=50, cell_axis=2, tally_axis=2,
                               per_bin=True))
 

@@ -42,7 +42,8 @@ class SteadyParams(C.Structure):
     _fields_ = [("n_particles", C.c_void_p), ("seed", C.c_uint64), ("precision", C.c_int),
                 ("n_scat_max", C.c_int), ("max_events", C.c_uint64), ("n_cells", C.c_int),
                 ("cell_axis", C.c_int), ("tally_axis", C.c_int), ("per_bin", C.c_int),
-                ("threads_per_block", C.c_int), ("blocks_per_sm", C.c_int), ("time_budget_s", C.c_double)]
+                ("threads_per_block", C.c_int), ("blocks_per_sm", C.c_int), ("time_budget_s", C.c_double),
+                ("trace_event_start", C.c_void_p), ("trace_event_stop", C.c_void_p)]
 
 
 class SteadyOut(C.Structure):
@@ -54,7 +55,8 @@ class TransientParams(C.Structure):
     _fields_ = [("n_particles", C.c_uint64), ("seed", C.c_uint64), ("precision", C.c_int),
                 ("max_events", C.c_uint64), ("t_max", C.c_double), ("n_times", C.c_int),
                 ("t_meas", C.c_void_p), ("grid", C.c_int * 3), ("threads_per_block", C.c_int),
-                ("blocks_per_sm", C.c_int), ("time_budget_s", C.c_double)]
+                ("blocks_per_sm", C.c_int), ("time_budget_s", C.c_double),
+                ("trace_event_start", C.c_void_p), ("trace_event_stop", C.c_void_p)]
 
 
 class TransientOut(C.Structure):

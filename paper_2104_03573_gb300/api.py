@@ -119,6 +119,13 @@ class SteadyConfig:
     threads_per_block: int = 0
     blocks_per_sm: int = 0
     time_budget_s: float = 0.0
+    trace_events: Optional[tuple] = None     # (start, stop) torch.cuda.Event around the trace kernel
+
+
+def _event_handles(pair):
+    if not pair:
+        return None, None
+    return pair[0].cuda_event, pair[1].cuda_event
 
 
 def steady_params(cfg: SteadyConfig, n_particles: np.ndarray) -> "L.SteadyParams":
@@ -135,6 +142,7 @@ def steady_params(cfg: SteadyConfig, n_particles: np.ndarray) -> "L.SteadyParams
     p.threads_per_block = int(cfg.threads_per_block)
     p.blocks_per_sm = int(cfg.blocks_per_sm)
     p.time_budget_s = float(cfg.time_budget_s)
+    p.trace_event_start, p.trace_event_stop = _event_handles(cfg.trace_events)
     return p
 
 
@@ -227,6 +235,7 @@ class TransientConfig:
     threads_per_block: int = 0
     blocks_per_sm: int = 0
     time_budget_s: float = 0.0
+    trace_events: Optional[tuple] = None
 
 
 class TransientOutputs:
@@ -258,6 +267,7 @@ def transient_params(cfg: TransientConfig, n_particles: int, t_meas: np.ndarray)
     p.threads_per_block = int(cfg.threads_per_block)
     p.blocks_per_sm = int(cfg.blocks_per_sm)
     p.time_budget_s = float(cfg.time_budget_s)
+    p.trace_event_start, p.trace_event_stop = _event_handles(cfg.trace_events)
     return p
 
 

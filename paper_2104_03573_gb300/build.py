@@ -24,6 +24,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # (source, extra flags, fused multiply-add allowed)
 UNITS = [
     ("tables.cu", [], False),
+    ("setup.cu", [], False),
     ("api.cu", [], False),
     ("tracer_steady.cu", ["-DMCBTE_F64=1"], False),
     ("tracer_steady.cu", ["-DMCBTE_F32=1"], True),

@@ -272,6 +272,9 @@ struct SteadyWs {
   double* cellP;
   double* cellD;
   double* qbin;
+  long long* cellPq;
+  long long* cellDq;
+  long long* qbinq;
   double* dsc;
   unsigned long long* cnt;
   double* G;
@@ -302,6 +305,9 @@ SteadyWs layout_steady(char* base, int G, int n, int nc, uint64_t total, bool gr
   w.cellP = nc > 0 ? c.take<double>((size_t)G * nc * 4) : nullptr;
   w.cellD = nc > 0 ? c.take<double>((size_t)G * (nc + 1) * 4) : nullptr;
   w.qbin = c.take<double>((size_t)G * n);
+  w.cellPq = nc > 0 ? c.take<long long>((size_t)G * nc * 4) : nullptr;
+  w.cellDq = nc > 0 ? c.take<long long>((size_t)G * (nc + 1) * 4) : nullptr;
+  w.qbinq = c.take<long long>((size_t)G * n);
   w.dsc = c.take<double>((size_t)G * 8);
   w.cnt = c.take<unsigned long long>((size_t)G * 4);
   w.G = grad ? c.take<double>(n) : nullptr;
@@ -339,8 +345,9 @@ mcbte_status check_steady(const mcbte_material* m, const mcbte_geometry* const* 
   if (p->cell_axis < 0 || p->cell_axis > 2 || p->tally_axis < 0 || p->tally_axis > 2)
     return fail(MCBTE_ERR_INVALID_ARG, "run_steady: axis must be 0, 1 or 2");
   if (p->n_scat_max < 0) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: n_scat_max < 0");
-  if (p->threads_per_block < 0 || p->threads_per_block > 512 || (p->threads_per_block % 32) != 0)
-    return fail(MCBTE_ERR_INVALID_ARG, "run_steady: threads_per_block must be a multiple of 32 up to 512");
+  if (p->threads_per_block != 0 && p->threads_per_block != 256 && p->threads_per_block != 512 &&
+      p->threads_per_block != 768 && p->threads_per_block != 1024)
+    return fail(MCBTE_ERR_INVALID_ARG, "run_steady: threads_per_block must be 0, 256, 512, 768 or 1024");
   uint64_t t = 0;
   for (int g = 0; g < G; ++g) {
     if (!geoms[g]) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: null geometry");
@@ -429,6 +436,9 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   A.cellP = w.cellP;
   A.cellD = w.cellD;
   A.qbin = w.qbin;
+  A.cellPq = w.cellPq;
+  A.cellDq = w.cellDq;
+  A.qbinq = w.qbinq;
   A.dsc = w.dsc;
   A.cnt = w.cnt;
   A.G = w.G;
@@ -445,7 +455,9 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
     C.dirs = w.dirs;
     C.dpi = w.dpi;
   }
+  if (p->trace_event_start) RUN_TRY(cudaEventRecord((cudaEvent_t)p->trace_event_start, s));
   RUN_TRY(launch_steady(p->precision, grad, w.geos, w.offs, m->view, C, A, p->threads_per_block, p->blocks_per_sm, s));
+  if (p->trace_event_stop) RUN_TRY(cudaEventRecord((cudaEvent_t)p->trace_event_stop, s));
   SteadyOutDev O{};
   O.T = host_out ? w.T : out->T;
   O.q = host_out ? w.q : out->q;
@@ -665,7 +677,9 @@ mcbte_status mcbte_run_transient(const mcbte_material* m, const mcbte_geometry* 
   A.flags = w.flags;
   A.snap = snap;
   A.events_pp = host_out ? w.events_pp : out->events_pp;
+  if (p->trace_event_start) RUN_TRY(cudaEventRecord((cudaEvent_t)p->trace_event_start, s));
   RUN_TRY(launch_transient(p->precision, w.geos, m->view, C, A, p->threads_per_block, p->blocks_per_sm, s));
+  if (p->trace_event_stop) RUN_TRY(cudaEventRecord((cudaEvent_t)p->trace_event_stop, s));
   double* stats = host_out ? w.stats : out->stats;
   RUN_TRY(launch_finalize_transient(w.geos, m->view, C, A, snap, stats, ncell, s));
   mcbte_status result = MCBTE_OK;

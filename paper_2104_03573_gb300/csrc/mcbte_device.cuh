@@ -203,6 +203,26 @@ template <typename R> __device__ __forceinline__ R geo_L(const GeoRun& g, int a)
 template <> __device__ __forceinline__ double geo_L<double>(const GeoRun& g, int a) { return g.L[a]; }
 template <> __device__ __forceinline__ float geo_L<float>(const GeoRun& g, int a) { return g.Lf[a]; }
 
+// Component a of a 3-vector, and assignment to it, by selects: a runtime
+// index into a register array would force the array into local memory.
+template <typename R>
+__device__ __forceinline__ R sel3(const R v[3], int a) {
+  return a == 0 ? v[0] : (a == 1 ? v[1] : v[2]);
+}
+template <typename R>
+__device__ __forceinline__ void put3(R v[3], int a, R val) {
+  v[0] = a == 0 ? val : v[0];
+  v[1] = a == 1 ? val : v[1];
+  v[2] = a == 2 ? val : v[2];
+}
+// v[a] = A, v[a+1] = B, v[a+2] = C (indices cyclic).
+template <typename R>
+__device__ __forceinline__ void put3_cyclic(R v[3], int a, R A, R B, R C) {
+  v[0] = a == 0 ? A : (a == 1 ? C : B);
+  v[1] = a == 0 ? B : (a == 1 ? A : C);
+  v[2] = a == 0 ? C : (a == 1 ? B : A);
+}
+
 // Direction with polar cosine mu about sgn * axis a; axes a+1, a+2 (cyclic)
 // take s cos(phi), s sin(phi), phi = 2 pi co(wphi).
 template <typename R>
@@ -210,11 +230,7 @@ __device__ __forceinline__ void dir_about_axis(R u[3], int a, R sgn, R mu, uint3
   const R s = Num<R>::sqrt_(Num<R>::fmax_(R(0), R(1) - mu * mu));
   R sn, cs;
   Num<R>::sincos2pi(Num<R>::co(wphi), &sn, &cs);
-  const int a1 = (a == 2) ? 0 : a + 1;
-  const int a2 = (a == 0) ? 2 : (a == 1 ? 0 : 1);
-  u[a] = sgn * mu;
-  u[a1] = s * cs;
-  u[a2] = s * sn;
+  put3_cyclic<R>(u, a, sgn * mu, s * cs, s * sn);
 }
 
 // First boundary along the ray (faces in the direction of travel, then the

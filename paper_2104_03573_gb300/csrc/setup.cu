@@ -1,0 +1,136 @@
+// Per-run setup kernel (FP64): the tracer's geometry records, the source
+// list with its energies and the cumulative source thresholds.
+#include "launch.h"
+
+namespace mcbte {
+
+namespace {
+
+__device__ __forceinline__ uint64_t spec_threshold(double p) {
+  if (p <= 0.0) return 0ull;
+  if (p >= 1.0) return 1ull << 32;
+  return (uint64_t)(p * 4294967296.0);
+}
+
+// One thread per geometry: derive the tracer's geometry record and the
+// source list with E_i (Eq. dev_tot / Eq. source_energy, Sec. 3.1):
+//   isothermal wall  E = (A/4) sum C v |T_b - T_eq|           (Eq. iso_flux)
+//   control gradient E = (V/2) |grad T| sum C v                (Eq. grad_flux over both signs)
+//   initial Gaussian E = C_tot |dT| (2 pi)^{3/2} sigma^3 / 2  (Eq. Nbin; half inside the box)
+// (x t_max for transient wall sources), then the cumulative source
+// thresholds used with one 32-bit word (Sec. 3.2).
+__global__ void k_setup(SetupArgs a, int G, MatView M, int transient, double t_max_s, int ta, GeoRun* geos,
+                        uint64_t* offs, unsigned long long* t0) {
+  const int gi = threadIdx.x;
+  if (gi == 0) {
+    *t0 = globaltimer_ns();
+    uint64_t acc = 0;
+    for (int k = 0; k < G; ++k) {
+      offs[k] = acc;
+      acc += a.n[k];
+    }
+    offs[G] = acc;
+  }
+  if (gi >= G) return;
+  const mcbte_geometry_desc& d = *a.desc[gi];
+  GeoRun r;
+  const double C_tot = M.sums[0];
+  const double sum_Cv = M.sums[1];
+  for (int k = 0; k < 3; ++k) {
+    r.L[k] = d.L[k] * 1e9;
+    r.Lf[k] = (float)r.L[k];
+  }
+  for (int f = 0; f < 6; ++f) {
+    r.type[f] = d.face_type[f];
+    r.pthr[f] = spec_threshold(d.face_p[f]);
+    r.face_sign[f] = (d.face_T[f] > d.T_eq) ? 1.0 : -1.0;
+  }
+  r.pore = d.pore;
+  r.cx = d.pore_c[0] * 1e9;
+  r.cy = d.pore_c[1] * 1e9;
+  const double rr = d.pore_r * 1e9;
+  r.r2 = rr * rr;
+  r.cxf = (float)r.cx;
+  r.cyf = (float)r.cy;
+  r.r2f = (float)r.r2;
+  r.p_pore = d.pore_p;
+  r.pthr_pore = spec_threshold(d.pore_p);
+  double V = d.L[0] * d.L[1] * d.L[2];
+  r.V_box = V;
+  if (d.pore) V = V - (3.141592653589793 * (d.pore_r * d.pore_r)) * d.L[2];
+  r.V_solid = V;
+  const double tf = transient ? t_max_s : 1.0;
+  int ns = 0;
+  double E[kMaxSources];
+  for (int f = 0; f < 6; ++f) {
+    if (d.face_type[f] != MCBTE_FACE_ISOTHERMAL) continue;
+    const double dT = d.face_T[f] - d.T_eq;
+    if (dT == 0.0) continue;
+    const int ax = face_axis(f);
+    const double A = d.L[(ax + 1) % 3] * d.L[(ax + 2) % 3];
+    E[ns] = (((0.25 * A) * sum_Cv) * fabs(dT)) * tf;
+    r.src_kind[ns] = 0;
+    r.src_face[ns] = f;
+    ++ns;
+  }
+  r.grad_axis = 0;
+  r.grad_sign = 0.0;
+  for (int k = 0; k < 3; ++k)
+    if (d.grad_T[k] != 0.0) {
+      r.grad_axis = k;
+      r.grad_sign = d.grad_T[k] > 0.0 ? 1.0 : -1.0;
+    }
+  if (r.grad_sign != 0.0) {
+    E[ns] = ((0.5 * V) * fabs(d.grad_T[r.grad_axis])) * sum_Cv;
+    r.src_kind[ns] = 1;
+    r.src_face[ns] = -1;
+    ++ns;
+  }
+  for (int k = 0; k < 3; ++k) r.gauss_c[k] = d.gauss_c[k] * 1e9;
+  r.gauss_sigma = d.gauss_sigma * 1e9;
+  r.gauss_sign = d.gauss_dT > 0.0 ? 1.0 : -1.0;
+  if (d.gauss) {
+    const double s = d.gauss_sigma;
+    E[ns] = (((C_tot * fabs(d.gauss_dT)) * 15.749609945722419) * ((s * s) * s)) * 0.5;
+    r.src_kind[ns] = 2;
+    r.src_face[ns] = -1;
+    ++ns;
+  }
+  r.n_src = ns;
+  double Et = 0.0;
+  for (int k = 0; k < ns; ++k) Et += E[k];
+  r.E_tot = Et;
+  double acc = 0.0;
+  for (int k = 0; k < ns; ++k) {
+    acc += E[k];
+    r.src_thr[k] = (k + 1 == ns) ? (1ull << 32) : (uint64_t)((acc / Et) * 4294967296.0);
+  }
+  for (int k = ns; k < kMaxSources; ++k) {
+    r.src_thr[k] = 1ull << 32;
+    r.src_kind[k] = 0;
+    r.src_face[k] = 0;
+  }
+  // dT/dx defining kappa along the tally axis
+  double kg = d.grad_T[ta];
+  if (kg == 0.0) {
+    const int lo = axis_min_face(ta), hi = axis_max_face(ta);
+    if (d.face_type[lo] == MCBTE_FACE_ISOTHERMAL && d.face_type[hi] == MCBTE_FACE_ISOTHERMAL)
+      kg = (d.face_T[hi] - d.face_T[lo]) / d.L[ta];
+    else
+      kg = __longlong_as_double(0x7ff8000000000000ll);
+  }
+  r.kappa_grad = kg;
+  r.n = a.n[gi];
+  r.offset = 0;
+  geos[gi] = r;
+}
+
+}  // namespace
+
+cudaError_t launch_setup(const SetupArgs& a, int n_geoms, const MatView& M, int transient, double t_max_s,
+                         int tally_axis, GeoRun* geos, uint64_t* offs, unsigned long long* t0, cudaStream_t s) {
+  k_setup<<<1, kMaxGeoms, 0, s>>>(a, n_geoms, M, transient, t_max_s, tally_axis, geos, offs, t0);
+  return cudaGetLastError();
+}
+
+}  // namespace mcbte

@@ -19,7 +19,11 @@
 
 namespace mcbte {
 
-enum { MODE_STEADY = 0, MODE_TRANSIENT = 1, MODE_GRAD = 2 };
+// Fixed-point unit of the FP32 path's tallies: 2^-20 nm (lengths) and
+// 2^-20 ps (times).  64-bit integer sums are exact and independent of the
+// order of the atomic adds.
+constexpr float kFx = 1048576.0f;
+constexpr double kFxInv = 9.5367431640625e-07;
 
 struct RunCfg {
   uint32_t k0, k1;
@@ -41,11 +45,14 @@ struct RunCfg {
   int grid[3];
 };
 
-// Raw accumulators of a run (device, FP64 unless noted).
+// Raw accumulators of a run (device).
 struct Acc {
-  double* cellP;              // [G][nc][4]   per-cell direct / partial-cell sums
-  double* cellD;              // [G][nc+1][4] difference array of full-cell sums
-  double* qbin;               // [G][n_bins]
+  double* cellP;              // [G][nc][4]   per-cell direct / partial-cell sums (FP64 path)
+  double* cellD;              // [G][nc+1][4] difference array of full-cell sums (FP64 path)
+  double* qbin;               // [G][n_bins]  (FP64 path)
+  long long* cellPq;          // [G][nc][4]   fixed-point counterparts (FP32 path)
+  long long* cellDq;          // [G][nc+1][4]
+  long long* qbinq;           // [G][n_bins]
   double* dsc;                // [G][8]: sumX, sumX2, signed emitted, signed absorbed, R, Gp, Gp^2, absorbed
   unsigned long long* cnt;    // [G][4]: events, truncated, max events, traced
   double* G;                  // [n_bins] sparse part of the LR gradient
@@ -70,8 +77,10 @@ struct Particle {
   uint32_t pid;
   int g;
   int mi;           // next measurement index (transient)
-  double X;         // sum s l u_tally (nm)
+  double X;         // sum s l u_tally (nm), FP64 path
   double Xper;      // X at the start of the current relaxation period
+  long long Xq;     // the same in fixed point, FP32 path
+  long long Xqper;
 };
 
 template <typename R>
@@ -117,9 +126,8 @@ __device__ __forceinline__ void emit(Particle<R>& p, const GeoRun& g, const MatV
     const uint4 w3 = philox(ctr, k0, k1);
     const int a1 = (a == 2) ? 0 : a + 1;
     const int a2 = (a == 0) ? 2 : (a == 1 ? 0 : 1);
-    p.x[a] = mx ? geo_L<R>(g, a) : R(0);
-    p.x[a1] = Num<R>::mid(w3.x) * geo_L<R>(g, a1);
-    p.x[a2] = Num<R>::mid(w3.y) * geo_L<R>(g, a2);
+    put3_cyclic<R>(p.x, a, mx ? geo_L<R>(g, a) : R(0), Num<R>::mid(w3.x) * geo_L<R>(g, a1),
+                   Num<R>::mid(w3.y) * geo_L<R>(g, a2));
   } else if (kind == 1) {
     p.bin = alias_draw(rec_emit, M.n, w0.y, w0.z, w0.w);
     p.s = (w2.x < 0x80000000u) ? R(1) : R(-1);
@@ -170,98 +178,130 @@ __device__ __forceinline__ void emit(Particle<R>& p, const GeoRun& g, const MatV
   p.n_relax = 0;
   p.X = 0.0;
   p.Xper = 0.0;
+  p.Xq = 0;
+  p.Xqper = 0;
 }
 
-// Plain per-cell track-length tally: every cell the segment crosses gets its
-// own path length (global FP64 atomics).
-template <typename R>
-__device__ __forceinline__ void cells_plain(double* P, int nc, int ca, R h, const R x[3], const R u[3], R seg, R s,
-                                            R inv_v) {
-  const R z0 = x[ca];
-  const R z1 = z0 + seg * u[ca];
-  if (u[ca] == R(0)) {
-    int c = (int)floor((double)(z0 / h));
-    c = min(max(c, 0), nc - 1);
-    atomicAdd(&P[c * 4 + 0], (double)((s * seg) * inv_v));
+// ------------------------------------------------------------------ tally policies
+// FP64 plain path: every cell the segment crosses gets its own path length,
+// added with global FP64 atomics (the plain definition of the track-length
+// estimator, Eqs. temp_steady and flux_x_steady).
+struct TallyPlain {
+  double* cP;      // [nc][4] of this particle's geometry, or null
+  double* qb;      // [n_bins], or null
+  int nc, ca, ta;
+  double h;
+
+  __device__ __forceinline__ double X(const Particle<double>& p) const { return p.X; }
+
+  __device__ __forceinline__ void segment(Particle<double>& p, double seg) const {
+    const double contrib = (p.s * seg) * sel3(p.u, ta);
+    p.X += contrib;
+    if (!cP) return;
+    const double z0 = sel3(p.x, ca);
+    const double uc = sel3(p.u, ca);
+    const double z1 = z0 + seg * uc;
+    if (uc == 0.0) {
+      int c = (int)floor(z0 / h);
+      c = min(max(c, 0), nc - 1);
+      atomicAdd(&cP[c * 4 + 0], (p.s * seg) * p.inv_v);
 #pragma unroll
-    for (int b = 0; b < 3; ++b) atomicAdd(&P[c * 4 + 1 + b], (double)((s * seg) * u[b]));
-    return;
-  }
-  const R zlo = z0 < z1 ? z0 : z1;
-  const R zhi = z0 < z1 ? z1 : z0;
-  const int clo = min(max((int)floor((double)(zlo / h)), 0), nc - 1);
-  const int chi = min(max((int)floor((double)(zhi / h)), 0), nc - 1);
-  const R au = u[ca] < R(0) ? -u[ca] : u[ca];
-  for (int c = clo; c <= chi; ++c) {
-    R lo = zlo > (R)c * h ? zlo : (R)c * h;
-    const R ch = (R)(c + 1) * h;
-    R hi = zhi < ch ? zhi : ch;
-    if (c == nc - 1) hi = zhi;
-    if (c == 0) lo = zlo;
-    const R ov = hi - lo;
-    if (ov <= R(0)) continue;
-    const R l = ov / au;
-    atomicAdd(&P[c * 4 + 0], (double)((s * l) * inv_v));
+      for (int b = 0; b < 3; ++b) atomicAdd(&cP[c * 4 + 1 + b], (p.s * seg) * p.u[b]);
+      return;
+    }
+    const double zlo = z0 < z1 ? z0 : z1;
+    const double zhi = z0 < z1 ? z1 : z0;
+    const int clo = min(max((int)floor(zlo / h), 0), nc - 1);
+    const int chi = min(max((int)floor(zhi / h), 0), nc - 1);
+    const double au = fabs(uc);
+    for (int c = clo; c <= chi; ++c) {
+      double lo = fmax(zlo, c * h);
+      double hi = fmin(zhi, (c + 1) * h);
+      if (c == nc - 1) hi = zhi;
+      if (c == 0) lo = zlo;
+      const double ov = hi - lo;
+      if (ov <= 0.0) continue;
+      const double l = ov / au;
+      atomicAdd(&cP[c * 4 + 0], (p.s * l) * p.inv_v);
 #pragma unroll
-    for (int b = 0; b < 3; ++b) atomicAdd(&P[c * 4 + 1 + b], (double)((s * l) * u[b]));
+      for (int b = 0; b < 3; ++b) atomicAdd(&cP[c * 4 + 1 + b], (p.s * l) * p.u[b]);
+    }
   }
+
+  __device__ __forceinline__ void period_end(Particle<double>& p) const {
+    if (qb) {
+      atomicAdd(&qb[p.bin], p.X - p.Xper);
+      p.Xper = p.X;
+    }
+  }
+};
+
+__device__ __forceinline__ void fx_add4(long long* a, float f0, float f1, float f2, float f3, float d) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(a + 0), (unsigned long long)__float2ll_rn(f0 * d * kFx));
+  atomicAdd(reinterpret_cast<unsigned long long*>(a + 1), (unsigned long long)__float2ll_rn(f1 * d * kFx));
+  atomicAdd(reinterpret_cast<unsigned long long*>(a + 2), (unsigned long long)__float2ll_rn(f2 * d * kFx));
+  atomicAdd(reinterpret_cast<unsigned long long*>(a + 3), (unsigned long long)__float2ll_rn(f3 * d * kFx));
 }
 
-// Difference-array track-length tally: the (up to) two partial end cells go
-// to P, the run of full cells in between is one +/- pair in D; the final
-// per-cell value is P[c] + sum_{c' <= c} D[c'].  At most 4 x 4 adds per
-// segment, whatever the number of cells crossed.
-template <typename R>
-__device__ __forceinline__ void cells_diff(double* P, double* D, int nc, int ca, R h, R inv_h, const R x[3],
-                                           const R u[3], R seg, R s, R inv_v) {
-  const R z0 = x[ca];
-  const R uz = u[ca];
-  if (uz == R(0)) {
-    int c = min(max((int)(z0 * inv_h), 0), nc - 1);
-    const R sl = s * seg;
-    atomicAdd(&P[c * 4 + 0], (double)(sl * inv_v));
-    atomicAdd(&P[c * 4 + 1], (double)(sl * u[0]));
-    atomicAdd(&P[c * 4 + 2], (double)(sl * u[1]));
-    atomicAdd(&P[c * 4 + 3], (double)(sl * u[2]));
-    return;
+// FP32 path: fixed-point tallies.  Cells use a difference array: the (up to)
+// two partial end cells go to P, the run of full cells in between is one
+// +/- pair in D, and the per-cell value is P[c] + sum_{c' <= c} D[c'];
+// at most 4 x 4 integer atomics per segment whatever the number of cells
+// crossed.  The frequency-resolved flux is added once per relaxation
+// period (the bin is constant over a period).
+struct TallyFx {
+  long long* cP;   // [nc][4] (shared memory or global), or null
+  long long* cD;   // [nc+1][4]
+  long long* qb;   // [n_bins], or null
+  int nc, ca, ta;
+  float h, inv_h;
+
+  __device__ __forceinline__ double X(const Particle<float>& p) const { return (double)p.Xq * kFxInv; }
+
+  __device__ __forceinline__ void segment(Particle<float>& p, float seg) const {
+    const float contrib = (p.s * seg) * sel3(p.u, ta);
+    p.Xq += __float2ll_rn(contrib * kFx);
+    if (!cP) return;
+    const float z0 = sel3(p.x, ca);
+    const float uz = sel3(p.u, ca);
+    if (uz == 0.0f) {
+      const int c = min(max((int)(z0 * inv_h), 0), nc - 1);
+      const float sl = p.s * seg;
+      fx_add4(cP + c * 4, sl * p.inv_v, sl * p.u[0], sl * p.u[1], sl * p.u[2], 1.0f);
+      return;
+    }
+    const float z1 = z0 + seg * uz;
+    const float zlo = fminf(z0, z1);
+    const float zhi = fmaxf(z0, z1);
+    const int clo = min(max((int)(zlo * inv_h), 0), nc - 1);
+    const int chi = min(max((int)(zhi * inv_h), 0), nc - 1);
+    const float k = p.s / fabsf(uz);      // per unit of axial length
+    const float f0 = k * p.inv_v, f1 = k * p.u[0], f2 = k * p.u[1], f3 = k * p.u[2];
+    if (clo == chi) {
+      fx_add4(cP + clo * 4, f0, f1, f2, f3, zhi - zlo);
+      return;
+    }
+    fx_add4(cP + clo * 4, f0, f1, f2, f3, (float)(clo + 1) * h - zlo);
+    fx_add4(cP + chi * 4, f0, f1, f2, f3, zhi - (float)chi * h);
+    if (chi > clo + 1) {
+      fx_add4(cD + (clo + 1) * 4, f0, f1, f2, f3, h);
+      fx_add4(cD + chi * 4, f0, f1, f2, f3, -h);
+    }
   }
-  const R z1 = z0 + seg * uz;
-  const R zlo = z0 < z1 ? z0 : z1;
-  const R zhi = z0 < z1 ? z1 : z0;
-  const int clo = min(max((int)(zlo * inv_h), 0), nc - 1);
-  const int chi = min(max((int)(zhi * inv_h), 0), nc - 1);
-  const R k = s / (uz < R(0) ? -uz : uz);      // per unit of axial length
-  const R f0 = k * inv_v, f1 = k * u[0], f2 = k * u[1], f3 = k * u[2];
-  if (clo == chi) {
-    const R dz = zhi - zlo;
-    atomicAdd(&P[clo * 4 + 0], (double)(f0 * dz));
-    atomicAdd(&P[clo * 4 + 1], (double)(f1 * dz));
-    atomicAdd(&P[clo * 4 + 2], (double)(f2 * dz));
-    atomicAdd(&P[clo * 4 + 3], (double)(f3 * dz));
-    return;
+
+  __device__ __forceinline__ void period_end(Particle<float>& p) const {
+    if (qb) {
+      atomicAdd(reinterpret_cast<unsigned long long*>(qb + p.bin), (unsigned long long)(p.Xq - p.Xqper));
+      p.Xqper = p.Xq;
+    }
   }
-  const R dlo = (R)(clo + 1) * h - zlo;
-  const R dhi = zhi - (R)chi * h;
-  atomicAdd(&P[clo * 4 + 0], (double)(f0 * dlo));
-  atomicAdd(&P[clo * 4 + 1], (double)(f1 * dlo));
-  atomicAdd(&P[clo * 4 + 2], (double)(f2 * dlo));
-  atomicAdd(&P[clo * 4 + 3], (double)(f3 * dlo));
-  atomicAdd(&P[chi * 4 + 0], (double)(f0 * dhi));
-  atomicAdd(&P[chi * 4 + 1], (double)(f1 * dhi));
-  atomicAdd(&P[chi * 4 + 2], (double)(f2 * dhi));
-  atomicAdd(&P[chi * 4 + 3], (double)(f3 * dhi));
-  if (chi > clo + 1) {
-    const double g0 = (double)(f0 * h), g1 = (double)(f1 * h), g2 = (double)(f2 * h), g3 = (double)(f3 * h);
-    atomicAdd(&D[(clo + 1) * 4 + 0], g0);
-    atomicAdd(&D[(clo + 1) * 4 + 1], g1);
-    atomicAdd(&D[(clo + 1) * 4 + 2], g2);
-    atomicAdd(&D[(clo + 1) * 4 + 3], g3);
-    atomicAdd(&D[chi * 4 + 0], -g0);
-    atomicAdd(&D[chi * 4 + 1], -g1);
-    atomicAdd(&D[chi * 4 + 2], -g2);
-    atomicAdd(&D[chi * 4 + 3], -g3);
-  }
-}
+};
+
+// No steady tallies (transient runs).
+struct TallyNone {
+  template <typename R>
+  __device__ __forceinline__ void period_end(Particle<R>&) const {}
+};
 
 // Likelihood-ratio bookkeeping of one particle (steady gradient runs).
 struct GradState {
@@ -282,20 +322,18 @@ enum { STEP_ALIVE = 0, STEP_ABSORBED = 1, STEP_DONE = 2, STEP_TRUNCATED = 3 };
 // kept), or the boundary `face` (isothermal: absorbed; periodic: translated
 // to the opposite face; adiabatic / pore: specular with probability p, else
 // Lambertian about the inward normal).  The particle has already moved.
-template <typename R, bool GRAD>
+// `Xnow` is the particle's tally so far (gradient bookkeeping only).
+template <typename R, bool GRAD, class Tally>
 __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_relax,
                                            const float4* binf, const RunCfg& C, bool relax, int face, R seg,
-                                           double* qb, GradState* gs) {
+                                           const Tally& T, GradState* gs, double Xnow) {
   ++p.e;
   uint4 ctr = make_uint4(p.pid, (uint32_t)p.g, p.e, 0u);
   if (relax) {
     ++p.n_relax;
     if (C.n_scat_max > 0 && p.n_relax >= C.n_scat_max) return STEP_DONE;
     // the relaxation period in this bin is over: frequency-resolved flux
-    if (qb) {
-      atomicAdd(&qb[p.bin], p.X - p.Xper);
-      p.Xper = p.X;
-    }
+    T.period_end(p);
     const uint4 w = philox(ctr, C.k0, C.k1);
     ctr.w = 1u;
     const uint4 w1 = philox(ctr, C.k0, C.k1);
@@ -307,11 +345,11 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
       if (gs->np < kMaxPeriods) {
         gs->bin[gs->np] = p.bin;
         gs->A[gs->np] = -1.0;
-        gs->B[gs->np] = -p.X;
+        gs->B[gs->np] = -Xnow;
         gs->np++;
       }
       gs->n_res++;
-      gs->sum_x_res += p.X;
+      gs->sum_x_res += Xnow;
     }
     return STEP_ALIVE;
   }
@@ -320,16 +358,19 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
     const int a = face_axis(face);
     const int mx = face_is_max(face);
     const R La = geo_L<R>(g, a);
-    p.x[a] = mx ? La : R(0);
     const int ty = g.type[face];
-    if (ty == MCBTE_FACE_ISOTHERMAL) return STEP_ABSORBED;
+    if (ty == MCBTE_FACE_ISOTHERMAL) {
+      put3<R>(p.x, a, mx ? La : R(0));
+      return STEP_ABSORBED;
+    }
     if (ty == MCBTE_FACE_PERIODIC) {
-      p.x[a] = mx ? R(0) : La;
+      put3<R>(p.x, a, mx ? R(0) : La);
       return STEP_ALIVE;
     }
+    put3<R>(p.x, a, mx ? La : R(0));
     const uint4 w = philox(ctr, C.k0, C.k1);
     if ((uint64_t)w.x < g.pthr[face]) {
-      p.u[a] = -p.u[a];
+      put3<R>(p.u, a, -sel3(p.u, a));
     } else {
       dir_about_axis<R>(p.u, a, mx ? R(-1) : R(1), Num<R>::sqrt_(Num<R>::oc(w.z)), w.w);
     }
@@ -347,7 +388,7 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
   if (GRAD) {
     const double sc = spec ? 1.0 / g.p_pore : -1.0 / (1.0 - g.p_pore);
     gs->PA += sc;
-    gs->PB += sc * p.X;
+    gs->PB += sc * Xnow;
   }
   if (spec) {
     const R un = p.u[0] * nx + p.u[1] * ny;
@@ -369,23 +410,19 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
 // One flight + event of a steady (or gradient) particle: first hit vs the
 // remaining relaxation distance (boundary wins ties, Sec. 3.3 case iii),
 // track-length tallies of the flight (Eqs. temp_steady, flux_x_steady), then
-// the event.  CELLS: 0 none, 1 plain per-cell, 2 difference array.
-template <typename R, int CELLS, bool GRAD>
+// the event.
+template <typename R, bool GRAD, class Tally>
 __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_relax,
-                                           const float4* binf, const RunCfg& C, double* cP, double* cD, R h,
-                                           R inv_h, double* qb, GradState* gs) {
+                                           const float4* binf, const RunCfg& C, const Tally& T, GradState* gs) {
   if (p.e + 1u >= C.max_events) return STEP_TRUNCATED;
   R db;
   int face;
   first_hit<R>(g, p.x, p.u, &db, &face);
   const bool relax = p.d_rel < db;
   const R seg = relax ? p.d_rel : db;
-  const int ta = C.tally_axis;
-  const R contrib = (p.s * seg) * p.u[ta];
-  const double Xb = p.X;
-  p.X += (double)contrib;
-  if (CELLS == 1) cells_plain<R>(cP, C.n_cells, C.cell_axis, h, p.x, p.u, seg, p.s, p.inv_v);
-  if (CELLS == 2) cells_diff<R>(cP, cD, C.n_cells, C.cell_axis, h, inv_h, p.x, p.u, seg, p.s, p.inv_v);
+  double Xb = 0.0;
+  if (GRAD) Xb = T.X(p);
+  T.segment(p, seg);
   if (GRAD) {
     double score = (double)(seg / p.lam);
     if (relax) score = score - 1.0;
@@ -394,7 +431,8 @@ __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, cons
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
-  return apply_event<R, GRAD>(p, g, M, rec_relax, binf, C, relax, face, seg, qb, gs);
+  return apply_event<R, GRAD, Tally>(p, g, M, rec_relax, binf, C, relax, face, seg, T, gs,
+                                     GRAD ? T.X(p) : 0.0);
 }
 
 // One flight + event of a transient particle: the flight also ends at
@@ -445,7 +483,7 @@ __device__ __forceinline__ int step_transient(Particle<R>& p, const GeoRun& g, c
 #pragma unroll
   for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
   if (fin) return STEP_DONE;
-  return apply_event<R, false>(p, g, M, rec_relax, binf, C, relax, face, seg, nullptr, nullptr);
+  return apply_event<R, false, TallyNone>(p, g, M, rec_relax, binf, C, relax, face, seg, TallyNone(), nullptr, 0.0);
 }
 
 }  // namespace mcbte
