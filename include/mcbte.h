@@ -200,6 +200,26 @@ mcbte_status mcbte_run_steady(const mcbte_material* m, const mcbte_geometry* con
                               const mcbte_steady_params* p, const mcbte_steady_out* out,
                               void* workspace, size_t workspace_bytes, mcbte_stream stream);
 
+/* Steady run that allocates no device memory.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc (code
+ * under an allocation-free contract, a fixed device-memory budget, or a
+ * process that must not grow device memory after start-up).  Same inputs,
+ * results and asynchronous behaviour as mcbte_run_steady with device
+ * outputs, but the run's scratch is a fixed 8 MiB device array inside this
+ * library, held on every GPU that loads it until the process exits.
+ *   - out->on_host must be 0 (outputs are the caller's device buffers).
+ *   - Runs needing more than 8 MiB of scratch (many geometries x bins x
+ *     cells) return MCBTE_ERR_WORKSPACE with the size needed.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call shares the one array, which keeps the last call's contents
+ *     (each call clears what must start at zero): calls whose GPU work
+ *     overlaps, on any streams or host threads, race and corrupt each
+ *     other's results.  Serialise them. */
+mcbte_status mcbte_run_steady_noalloc(const mcbte_material* m, const mcbte_geometry* const* geoms, int n_geoms,
+                                      const mcbte_steady_params* p, const mcbte_steady_out* out,
+                                      mcbte_stream stream);
+
 typedef struct {
   uint64_t n_particles;        /* [1, 2^32) */
   uint64_t seed;

@@ -201,6 +201,20 @@ def run_steady(material: Material, geoms: Sequence[Geometry], n_particles, cfg: 
     return out
 
 
+def run_steady_noalloc(material: Material, geoms: Sequence[Geometry], n_particles, cfg: SteadyConfig,
+                       out: SteadyOutputs, stream=None) -> SteadyOutputs:
+    """``mcbte_run_steady_noalloc``: the steady run for callers that cannot
+    allocate device memory.  `out` must already hold the device outputs; the
+    library uses its fixed internal scratch and allocates nothing.  Calls
+    whose GPU work overlaps race on that scratch."""
+    n = np.ascontiguousarray(np.asarray(n_particles, dtype=np.uint64))
+    p = steady_params(cfg, n)
+    o = out.struct()
+    L.check(L.load().mcbte_run_steady_noalloc(material.handle, _handles(geoms), len(geoms), C.byref(p), C.byref(o),
+                                              _stream_ptr(stream)))
+    return out
+
+
 def run_steady_host(material: Material, geoms: Sequence[Geometry], n_particles, cfg: SteadyConfig) -> Dict:
     """``mcbte_run_steady`` with host (numpy) outputs: the library copies
     results back and synchronises before returning."""

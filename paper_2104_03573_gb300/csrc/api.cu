@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -699,6 +700,62 @@ mcbte_status mcbte_run_transient(const mcbte_material* m, const mcbte_geometry* 
   }
 #undef RUN_TRY
   return result;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ steady run without device allocation
+// For callers that cannot call cudaMalloc: code running where the CUDA
+// allocator is off limits (inside another library's allocation-free region,
+// a real-time or pre-allocated memory budget, a host process that must not
+// grow device memory after start-up).  The run's scratch lives in a fixed
+// device array that every GPU loading this library holds until the process
+// exits; outputs are still the caller's device buffers.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;   // 8 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+
+}  // namespace
+
+extern "C" {
+
+mcbte_status mcbte_run_steady_noalloc(const mcbte_material* m, const mcbte_geometry* const* geoms, int n_geoms,
+                                      const mcbte_steady_params* p, const mcbte_steady_out* out,
+                                      mcbte_stream stream) {
+  if (!out) return fail(MCBTE_ERR_INVALID_ARG, "run_steady_noalloc: null outputs");
+  if (out->on_host) return fail(MCBTE_ERR_INVALID_ARG, "run_steady_noalloc: outputs must be device memory");
+  uint64_t total = 0;
+  mcbte_status st = check_steady(m, geoms, n_geoms, p, &total);
+  if (st != MCBTE_OK) return st;
+  const SteadyWs w = layout_steady(nullptr, n_geoms, m->n, p->n_cells, total, false, 0, false, false, false, false,
+                                   false, false);
+  if (w.bytes > kNoAllocScratchBytes)
+    return fail(MCBTE_ERR_WORKSPACE, "run_steady_noalloc: this run needs " + std::to_string(w.bytes) +
+                                         " bytes of scratch, above the fixed " +
+                                         std::to_string(kNoAllocScratchBytes) + " bytes");
+  int dev = -1;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(MCBTE_ERR_INVALID_ARG, "run_steady_noalloc: device ordinal");
+  void* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      // the array's name is a host-side stand-in; its device address comes
+      // from the runtime, once per device, with that device current
+      void* ptr = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "run_steady_noalloc: cudaGetSymbolAddress");
+      g_noalloc_addr[dev] = ptr;
+    }
+    scratch = g_noalloc_addr[dev];
+  }
+  return steady_impl(m, geoms, n_geoms, p, out, nullptr, scratch, kNoAllocScratchBytes, (cudaStream_t)stream);
 }
 
 }  // extern "C"
