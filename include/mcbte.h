@@ -169,6 +169,12 @@ typedef struct {
   double time_budget_s;        /* 0 = 120 s; the kernel stops and reports TIMEOUT        */
   void* trace_event_start;     /* optional cudaEvent_t recorded on `stream` just before   */
   void* trace_event_stop;      /* and just after the tracing kernel (NULL = none)         */
+  const uint64_t* seed_device; /* optional DEVICE pointer: if set, the tracing kernel reads
+                                  the Philox key from it when it starts (a captured CUDA
+                                  graph then draws a new sample per replay after the caller
+                                  updates it); `seed` is ignored                          */
+  int refill_threshold;        /* FP32 tracer: a warp refills its finished lanes once at
+                                  least this many are idle (0 or 1 = at once, up to 32)   */
 } mcbte_steady_params;
 
 typedef struct {

@@ -120,6 +120,8 @@ class SteadyConfig:
     blocks_per_sm: int = 0
     time_budget_s: float = 0.0
     trace_events: Optional[tuple] = None     # (start, stop) torch.cuda.Event around the trace kernel
+    seed_device: Optional[object] = None     # int64 device tensor holding the Philox key
+    refill_threshold: int = 0
 
 
 def _event_handles(pair):
@@ -143,6 +145,8 @@ def steady_params(cfg: SteadyConfig, n_particles: np.ndarray) -> "L.SteadyParams
     p.blocks_per_sm = int(cfg.blocks_per_sm)
     p.time_budget_s = float(cfg.time_budget_s)
     p.trace_event_start, p.trace_event_stop = _event_handles(cfg.trace_events)
+    p.seed_device = None if cfg.seed_device is None else cfg.seed_device.data_ptr()
+    p.refill_threshold = int(cfg.refill_threshold)
     return p
 
 

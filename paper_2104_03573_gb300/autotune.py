@@ -1,0 +1,76 @@
+"""Launch-shape autotuner of the persistent FP32 tracer.
+
+For a given material / geometry batch / run configuration it times a
+reduced-size run for each candidate (block size, blocks per SM, warp refill
+threshold) and keeps the fastest by particle-events per second.  Results
+are cached per process by the features that decide the kernel variant and
+its load balance.  The physics does not depend on the choice: every
+particle's random stream is keyed by its own id, so any launch shape
+produces the same per-particle trajectories.
+"""
+from __future__ import annotations
+
+from dataclasses import replace
+from typing import Dict, Iterable, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import _lib as L
+from . import api
+
+_CACHE: Dict[tuple, dict] = {}
+
+DEFAULT_CANDIDATES: Tuple[Tuple[int, int, int], ...] = (
+    (512, 0, 1), (768, 0, 1), (1024, 0, 1), (768, 0, 4), (768, 0, 16), (256, 0, 1),
+)
+
+
+def _key(material: api.Material, geoms: Sequence[api.Geometry], n_particles, cfg: api.SteadyConfig) -> tuple:
+    n = np.asarray(n_particles, dtype=np.int64)
+    return (material.n_bins, len(geoms), int(cfg.n_cells), bool(cfg.per_bin), int(cfg.n_scat_max),
+            int(cfg.tally_axis), int(np.log2(max(1, int(n.sum())))))
+
+
+def tune(material: api.Material, geoms: Sequence[api.Geometry], n_particles, cfg: api.SteadyConfig, *,
+         fraction: float = 0.05, min_particles: int = 20_000, repeats: int = 2,
+         candidates: Optional[Iterable[Tuple[int, int, int]]] = None, verbose: bool = False) -> api.SteadyConfig:
+    """Return `cfg` with the fastest (threads_per_block, blocks_per_sm,
+    refill_threshold) for this workload (FP32 path only)."""
+    import torch
+    if cfg.precision != L.FP32_TRACE:
+        return cfg
+    key = _key(material, geoms, n_particles, cfg)
+    if key in _CACHE:
+        return replace(cfg, **_CACHE[key])
+    n = np.asarray(n_particles, dtype=np.int64)
+    sample = np.maximum(1, np.maximum((n * fraction).astype(np.int64), min(min_particles, int(n.max())) // len(n)))
+    best, best_rate = None, -1.0
+    results = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for threads, bps, refill in (candidates or DEFAULT_CANDIDATES):
+        c = replace(cfg, threads_per_block=threads, blocks_per_sm=bps, refill_threshold=refill, trace_events=None,
+                    seed_device=None)
+        out = api.SteadyOutputs(len(geoms), material.n_bins, c.n_cells, c.per_bin)
+        api.run_steady(material, geoms, sample, c, out=out)        # warm-up / first-launch costs
+        times = []
+        for _ in range(repeats):
+            e0.record()
+            api.run_steady(material, geoms, sample, c, out=out)
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        events = float(out.stats[:, L.STAT_EVENTS].sum().item())
+        rate = events / min(times)
+        results.append(((threads, bps, refill), rate))
+        if rate > best_rate:
+            best, best_rate = (threads, bps, refill), rate
+    if verbose:
+        for cand, rate in results:
+            print(f"autotune {cand}: {rate:.3e} events/s")
+    choice = {"threads_per_block": best[0], "blocks_per_sm": best[1], "refill_threshold": best[2]}
+    _CACHE[key] = choice
+    return replace(cfg, **choice)
+
+
+def clear_cache() -> None:
+    _CACHE.clear()

@@ -346,6 +346,8 @@ mcbte_status check_steady(const mcbte_material* m, const mcbte_geometry* const* 
   if (p->cell_axis < 0 || p->cell_axis > 2 || p->tally_axis < 0 || p->tally_axis > 2)
     return fail(MCBTE_ERR_INVALID_ARG, "run_steady: axis must be 0, 1 or 2");
   if (p->n_scat_max < 0) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: n_scat_max < 0");
+  if (p->refill_threshold < 0 || p->refill_threshold > 32)
+    return fail(MCBTE_ERR_INVALID_ARG, "run_steady: refill_threshold in [0, 32]");
   if (p->threads_per_block != 0 && p->threads_per_block != 256 && p->threads_per_block != 512 &&
       p->threads_per_block != 768 && p->threads_per_block != 1024)
     return fail(MCBTE_ERR_INVALID_ARG, "run_steady: threads_per_block must be 0, 256, 512, 768 or 1024");
@@ -433,6 +435,8 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   C.total = total;
   C.t0 = w.t0;
   C.budget_ns = (uint64_t)((p->time_budget_s > 0 ? p->time_budget_s : 120.0) * 1e9);
+  C.seed_dev = reinterpret_cast<const unsigned long long*>(p->seed_device);
+  C.refill_min = p->refill_threshold;
   Acc A{};
   A.cellP = w.cellP;
   A.cellD = w.cellD;

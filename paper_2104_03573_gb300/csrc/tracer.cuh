@@ -34,6 +34,8 @@ struct RunCfg {
   uint64_t total;
   const unsigned long long* t0;   // device timestamp (ns) written by the setup kernel
   uint64_t budget_ns;             // wall-clock budget of the tracing kernel
+  const unsigned long long* seed_dev;   // optional device-resident Philox key (overrides k0, k1)
+  int refill_min;                 // FP32 tracer: refill a warp once this many lanes are idle
   // gradient
   int n_dirs;
   const double* dirs;    // [n_dirs][n_bins]
@@ -314,6 +316,15 @@ struct GradState {
   double PA, PB;
 };
 
+// Philox key of the run: the host seed, or the device-resident one.
+__device__ __forceinline__ uint2 run_key(const RunCfg& C) {
+  if (C.seed_dev) {
+    const unsigned long long s = *C.seed_dev;
+    return make_uint2((uint32_t)s, (uint32_t)(s >> 32));
+  }
+  return make_uint2(C.k0, C.k1);
+}
+
 // Outcome of one event step.
 enum { STEP_ALIVE = 0, STEP_ABSORBED = 1, STEP_DONE = 2, STEP_TRUNCATED = 3 };
 
@@ -325,8 +336,8 @@ enum { STEP_ALIVE = 0, STEP_ABSORBED = 1, STEP_DONE = 2, STEP_TRUNCATED = 3 };
 // `Xnow` is the particle's tally so far (gradient bookkeeping only).
 template <typename R, bool GRAD, class Tally>
 __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_relax,
-                                           const float4* binf, const RunCfg& C, bool relax, int face, R seg,
-                                           const Tally& T, GradState* gs, double Xnow) {
+                                           const float4* binf, const RunCfg& C, uint32_t k0, uint32_t k1,
+                                           bool relax, int face, R seg, const Tally& T, GradState* gs, double Xnow) {
   ++p.e;
   uint4 ctr = make_uint4(p.pid, (uint32_t)p.g, p.e, 0u);
   if (relax) {
@@ -334,9 +345,9 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
     if (C.n_scat_max > 0 && p.n_relax >= C.n_scat_max) return STEP_DONE;
     // the relaxation period in this bin is over: frequency-resolved flux
     T.period_end(p);
-    const uint4 w = philox(ctr, C.k0, C.k1);
+    const uint4 w = philox(ctr, k0, k1);
     ctr.w = 1u;
-    const uint4 w1 = philox(ctr, C.k0, C.k1);
+    const uint4 w1 = philox(ctr, k0, k1);
     p.bin = alias_draw(rec_relax, M.n, w.x, w.y, w1.x);
     dir_about_axis<R>(p.u, 2, R(1), R(1) - R(2) * Num<R>::oc(w.z), w.w);
     load_bin(p, M, binf);
@@ -368,7 +379,7 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
       return STEP_ALIVE;
     }
     put3<R>(p.x, a, mx ? La : R(0));
-    const uint4 w = philox(ctr, C.k0, C.k1);
+    const uint4 w = philox(ctr, k0, k1);
     if ((uint64_t)w.x < g.pthr[face]) {
       put3<R>(p.u, a, -sel3(p.u, a));
     } else {
@@ -383,7 +394,7 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
   const R len = Num<R>::sqrt_(nx * nx + ny * ny);
   nx = nx / len;
   ny = ny / len;
-  const uint4 w = philox(ctr, C.k0, C.k1);
+  const uint4 w = philox(ctr, k0, k1);
   const bool spec = (uint64_t)w.x < g.pthr_pore;
   if (GRAD) {
     const double sc = spec ? 1.0 / g.p_pore : -1.0 / (1.0 - g.p_pore);
@@ -413,7 +424,8 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
 // the event.
 template <typename R, bool GRAD, class Tally>
 __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_relax,
-                                           const float4* binf, const RunCfg& C, const Tally& T, GradState* gs) {
+                                           const float4* binf, const RunCfg& C, uint32_t k0, uint32_t k1,
+                                           const Tally& T, GradState* gs) {
   if (p.e + 1u >= C.max_events) return STEP_TRUNCATED;
   R db;
   int face;
@@ -431,7 +443,7 @@ __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, cons
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
-  return apply_event<R, GRAD, Tally>(p, g, M, rec_relax, binf, C, relax, face, seg, T, gs,
+  return apply_event<R, GRAD, Tally>(p, g, M, rec_relax, binf, C, k0, k1, relax, face, seg, T, gs,
                                      GRAD ? T.X(p) : 0.0);
 }
 
@@ -442,7 +454,7 @@ __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, cons
 template <typename R>
 __device__ __forceinline__ int step_transient(Particle<R>& p, const GeoRun& g, const MatView& M,
                                               const uint4* rec_relax, const float4* binf, const RunCfg& C,
-                                              double* snap) {
+                                              uint32_t k0, uint32_t k1, double* snap) {
   if (p.e + 1u >= C.max_events) return STEP_TRUNCATED;
   R db;
   int face;
@@ -483,7 +495,8 @@ __device__ __forceinline__ int step_transient(Particle<R>& p, const GeoRun& g, c
 #pragma unroll
   for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
   if (fin) return STEP_DONE;
-  return apply_event<R, false, TallyNone>(p, g, M, rec_relax, binf, C, relax, face, seg, TallyNone(), nullptr, 0.0);
+  return apply_event<R, false, TallyNone>(p, g, M, rec_relax, binf, C, k0, k1, relax, face, seg, TallyNone(), nullptr,
+                                          0.0);
 }
 
 }  // namespace mcbte

@@ -75,7 +75,8 @@ __global__ void __launch_bounds__(256) k_steady_fp64(const GeoRun* __restrict__ 
   Particle<double> p;
   p.pid = (uint32_t)(idx - offs[g]);
   p.g = g;
-  emit<double>(p, G, M, M.rec_emit, M.rec_init, nullptr, C.k0, C.k1, false, 0.0);
+  const uint2 key = run_key(C);
+  emit<double>(p, G, M, M.rec_emit, M.rec_init, nullptr, key.x, key.y, false, 0.0);
   GradState gs;
   if (GRAD) grad_init(&gs, p);
   TallyPlain T;
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(256) k_steady_fp64(const GeoRun* __restrict__ 
   T.h = CELLS ? G.L[C.cell_axis] / (double)C.n_cells : 1.0;
   int out;
   for (;;) {
-    out = step_steady<double, GRAD, TallyPlain>(p, G, M, M.rec_relax, nullptr, C, T, &gs);
+    out = step_steady<double, GRAD, TallyPlain>(p, G, M, M.rec_relax, nullptr, C, key.x, key.y, T, &gs);
     if (out != STEP_ALIVE) break;
     if ((p.e & 1023u) == 0u && globaltimer_ns() > deadline) {
       atomicOr(A.flags, 1);
@@ -181,10 +182,13 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
   bool alive = false;
   uint64_t idx = 0;
   const GeoRun* G = geos;
+  const uint2 key = run_key(C);
+  const int refill_min = C.refill_min > 1 ? C.refill_min : 1;
   for (;;) {
     const unsigned act = __activemask();
     const unsigned need = __ballot_sync(act, !alive);
-    if (need) {
+    // refill once enough lanes are idle (or all of them are)
+    if (need && (__popc(need) >= refill_min || need == act)) {
       const int leader = __ffs(need) - 1;
       unsigned long long base = 0;
       if ((int)lane == leader) base = atomicAdd(A.work, (unsigned long long)__popc(need));
@@ -197,7 +201,7 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
         G = &geos[g];
         p.pid = (uint32_t)(idx - offs[g]);
         p.g = g;
-        emit<float>(p, *G, M, M.rec_emit, M.rec_init, binf, C.k0, C.k1, false, 0.0f);
+        emit<float>(p, *G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, false, 0.0f);
         if (GRAD) grad_init(&gs, p);
         if (CELLS) {
           T.cP = S.cells_in_smem ? s_cP : A.cellPq + (size_t)g * nc * 4;
@@ -209,7 +213,8 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
         alive = true;
       }
     }
-    int out = step_steady<float, GRAD, TallyFx>(p, *G, M, relax, binf, C, T, &gs);
+    if (!alive) continue;
+    int out = step_steady<float, GRAD, TallyFx>(p, *G, M, relax, binf, C, key.x, key.y, T, &gs);
     if (out == STEP_ALIVE && (p.e & 255u) == 0u && globaltimer_ns() > deadline) {
       atomicOr(A.flags, 1);
       out = STEP_TRUNCATED;

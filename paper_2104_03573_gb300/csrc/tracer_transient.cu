@@ -47,11 +47,12 @@ __global__ void __launch_bounds__(256) k_transient_fp64(const GeoRun* __restrict
   Particle<double> p;
   p.pid = (uint32_t)idx;
   p.g = 0;
-  emit<double>(p, G, M, M.rec_emit, M.rec_init, nullptr, C.k0, C.k1, true, C.t_max_ps);
+  const uint2 key = run_key(C);
+  emit<double>(p, G, M, M.rec_emit, M.rec_init, nullptr, key.x, key.y, true, C.t_max_ps);
   transient_start(p, C);
   int out;
   for (;;) {
-    out = step_transient<double>(p, G, M, M.rec_relax, nullptr, C, A.snap);
+    out = step_transient<double>(p, G, M, M.rec_relax, nullptr, C, key.x, key.y, A.snap);
     if (out != STEP_ALIVE) break;
     if ((p.e & 1023u) == 0u && globaltimer_ns() > deadline) {
       atomicOr(A.flags, 1);
@@ -86,6 +87,7 @@ __global__ void __launch_bounds__(512) k_transient_f32(const GeoRun* __restrict_
   const GeoRun& G = geos[0];
   const uint64_t deadline = *C.t0 + C.budget_ns;
   const unsigned lane = threadIdx.x & 31u;
+  const uint2 key = run_key(C);
   Particle<float> p;
   bool alive = false;
   uint64_t idx = 0;
@@ -103,12 +105,12 @@ __global__ void __launch_bounds__(512) k_transient_f32(const GeoRun* __restrict_
         if (*(volatile int*)A.flags & 1) break;
         p.pid = (uint32_t)idx;
         p.g = 0;
-        emit<float>(p, G, M, M.rec_emit, M.rec_init, binf, C.k0, C.k1, true, (float)C.t_max_ps);
+        emit<float>(p, G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, true, (float)C.t_max_ps);
         transient_start(p, C);
         alive = true;
       }
     }
-    int out = step_transient<float>(p, G, M, relax, binf, C, A.snap);
+    int out = step_transient<float>(p, G, M, relax, binf, C, key.x, key.y, A.snap);
     if (out == STEP_ALIVE && (p.e & 255u) == 0u && globaltimer_ns() > deadline) {
       atomicOr(A.flags, 1);
       out = STEP_TRUNCATED;

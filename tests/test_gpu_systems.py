@@ -1,0 +1,162 @@
+"""Batching, CUDA-graph replay, autotuning and the autograd adjoint.
+
+* launch-shape independence: every particle's random stream is keyed by its
+  own id, and the FP32 path accumulates its tallies in 64-bit fixed point,
+  so per-particle results and all tallies are bit-identical for every block
+  size and refill threshold;
+* a captured CUDA graph of a batched multi-geometry run reproduces a direct
+  run with the same key, and a new key gives a new sample;
+* the torch.autograd.Function backward equals ``mcbte_grad`` and agrees with
+  central finite differences under common random numbers.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from inputs import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2104_03573_gb300 import _lib as L  # noqa: E402
+from paper_2104_03573_gb300 import api, autograd, autotune, batch  # noqa: E402
+from oracle import closed_forms as cf  # noqa: E402
+import oracle  # noqa: E402
+
+
+def _run(M, Gs, ns, cfg, per_particle=False):
+    out = api.run_steady(M, Gs, ns, cfg, per_particle=per_particle)
+    torch.cuda.synchronize()
+    return out
+
+
+def test_fp32_results_independent_of_launch_shape():
+    wl = W.si_slab_c2(n=60_000)
+    mat, geo, run = wl.material, wl.geometries[0], wl.run
+    M, G = api.Material(mat), api.Geometry(geo)
+    base = None
+    for threads, refill in ((256, 1), (512, 1), (768, 8), (1024, 32)):
+        cfg = api.SteadyConfig(seed=run.seed, precision=L.FP32_TRACE, n_cells=run.n_cells, tally_axis=2,
+                               per_bin=True, threads_per_block=threads, refill_threshold=refill)
+        o = _run(M, [G], [run.n], cfg, per_particle=True)
+        cur = {k: getattr(o, k).cpu().numpy() for k in ("events_pp", "X_pp", "T", "q", "q_bin")}
+        if base is None:
+            base = cur
+            continue
+        for k in cur:
+            assert np.array_equal(cur[k], base[k]), (threads, refill, k)
+
+
+def test_graph_batch_replays_and_matches_direct_run():
+    wl = W.film_batch_c4(n_films=8)
+    mat, run = wl.material, wl.run
+    M = api.Material(mat)
+    Gs = [api.Geometry(g) for g in wl.geometries]
+    ns = [3000, 100, 4500, 1, 800, 2500, 60, 1200]
+    cfg = api.SteadyConfig(seed=77, precision=L.FP32_TRACE, tally_axis=1, per_bin=True, n_scat_max=10,
+                           max_events=5_000_000)
+    gb = batch.GraphBatch(M, Gs, ns, cfg, tune=False)
+    a = gb.replay(seed=123)
+    torch.cuda.synchronize()
+    sa = a.stats.clone(); qa = a.q_bin.clone()
+    gb.replay(seed=124)
+    torch.cuda.synchronize()
+    sb = gb.out.stats.clone()
+    gb.replay(seed=123)
+    torch.cuda.synchronize()
+    assert torch.equal(gb.out.q_bin, qa)
+    assert torch.allclose(gb.out.stats, sa, rtol=1e-12, atol=0)
+    assert not torch.equal(sb[:, L.STAT_SUMX], sa[:, L.STAT_SUMX])
+    direct = _run(M, Gs, ns, api.SteadyConfig(seed=123, precision=L.FP32_TRACE, tally_axis=1, per_bin=True,
+                                              n_scat_max=10, max_events=5_000_000))
+    assert torch.equal(direct.q_bin, qa)
+    assert torch.allclose(direct.stats, sa, rtol=1e-12, atol=0)
+    assert (sa[:, L.STAT_N].cpu().numpy() == np.array(ns)).all()
+
+
+def test_autotune_returns_a_valid_shape_with_the_same_physics():
+    wl = W.si_slab_c2(n=200_000)
+    mat, geo, run = wl.material, wl.geometries[0], wl.run
+    M, G = api.Material(mat), api.Geometry(geo)
+    cfg = api.SteadyConfig(seed=run.seed, precision=L.FP32_TRACE, n_cells=run.n_cells, tally_axis=2, per_bin=True)
+    autotune.clear_cache()
+    tuned = autotune.tune(M, [G], [run.n], cfg)
+    assert tuned.threads_per_block in (256, 512, 768, 1024)
+    a = _run(M, [G], [run.n], cfg)
+    b = _run(M, [G], [run.n], tuned)
+    assert torch.equal(a.T, b.T) and torch.equal(a.q_bin, b.q_bin)
+    assert autotune.tune(M, [G], [run.n], cfg) == tuned       # cached
+
+
+def test_films_batched_kappa_vs_fuchs_sondheimer():
+    wl = W.film_batch_c4(scale=0.05)
+    mat, run = wl.material, wl.run
+    tb = oracle.tables(mat)
+    M = api.Material(mat)
+    Gs = [api.Geometry(g) for g in wl.geometries]
+    cfg = api.SteadyConfig(seed=1004, precision=L.FP32_TRACE, tally_axis=1, per_bin=True, n_scat_max=10,
+                           max_events=200_000_000, time_budget_s=300)
+    o = _run(M, Gs, wl.n_per_geom, cfg)
+    st = o.stats.cpu().numpy()
+    z = []
+    for f, g in enumerate(wl.geometries):
+        fs = cf.fuchs_sondheimer(tb["C"], mat.v, mat.tau, g.L[2])
+        z.append((st[f, L.STAT_KAPPA] - fs) / st[f, L.STAT_KAPPA_SE])
+    z = np.array(z)
+    assert st[:, L.STAT_TRUNCATED].sum() == 0
+    assert np.max(np.abs(z)) < 4.5, z
+    assert np.mean(z ** 2) < 2.0, np.mean(z ** 2)
+
+
+def test_autograd_backward_equals_library_gradient():
+    mat = W.bvk_holland(n_per_branch=8)
+    geo = W.pore_lattice(100e-9, 0.25, 200e-9, p_pore=0.3)
+    cfg = api.SteadyConfig(seed=5, precision=L.FP32_TRACE, tally_axis=1, per_bin=False, n_scat_max=6,
+                           max_events=5_000_000)
+    s = torch.zeros(mat.n_bins, dtype=torch.float64, requires_grad=True)
+    p = torch.tensor(0.3, dtype=torch.float64, requires_grad=True)
+    k = autograd.kappa(s, p, mat, geo, 100_000, cfg)
+    k.backward()
+    _, go = api.grad(api.Material(mat), api.Geometry(geo), 100_000, cfg)
+    torch.cuda.synchronize()
+    assert torch.allclose(s.grad, go.dkappa_dlogtau.cpu(), rtol=1e-12, atol=0)
+    assert p.grad.item() == pytest.approx(go.dkappa_dp[0].item(), rel=1e-12)
+
+
+def _kappa_pp(mat, geo, cfg, n):
+    o = _run(api.Material(mat), [api.Geometry(geo)], [n], cfg, per_particle=True)
+    st = o.stats[0].cpu().numpy()
+    X = o.X_pp.cpu().numpy()
+    return st[L.STAT_KAPPA], st[L.STAT_KAPPA] / X.sum() * X
+
+
+def test_autograd_gradient_matches_crn_central_differences():
+    mat = W.bvk_holland(n_per_branch=8)
+    geo = W.pore_lattice(100e-9, 0.25, 200e-9, p_pore=0.3)
+    n = 1_000_000
+    cfg = api.SteadyConfig(seed=11, precision=L.FP32_TRACE, tally_axis=1, n_scat_max=4, max_events=5_000_000)
+    rng = np.random.default_rng(4)
+    dirs = np.vstack([rng.choice([-1.0, 1.0], size=mat.n_bins), np.eye(mat.n_bins)[mat.n_bins - 3]])
+    _, go = api.grad(api.Material(mat), api.Geometry(geo), n, cfg, dirs=dirs)
+    torch.cuda.synchronize()
+    lr = go.dkappa_dir[:2].cpu().numpy()
+    h = 1e-2
+    for k in range(2):
+        kp, xp = _kappa_pp(mat.scaled_tau(h * dirs[k]), geo, cfg, n)
+        km, xm = _kappa_pp(mat.scaled_tau(-h * dirs[k]), geo, cfg, n)
+        fd = (kp - km) / (2 * h)
+        fd_se = ((xp - xm) / (2 * h)).std(ddof=1) * math.sqrt(n)
+        se = math.hypot(fd_se, lr[k, 1])
+        assert abs(lr[k, 0] - fd) < 4 * se, (k, lr[k], fd, fd_se)
+    # pore specularity
+    gp = go.dkappa_dp.cpu().numpy()
+    from dataclasses import replace
+    kp, xp = _kappa_pp(mat, replace(geo, pore_p=0.3 + h), cfg, n)
+    km, xm = _kappa_pp(mat, replace(geo, pore_p=0.3 - h), cfg, n)
+    fd = (kp - km) / (2 * h)
+    fd_se = ((xp - xm) / (2 * h)).std(ddof=1) * math.sqrt(n)
+    assert abs(gp[0] - fd) < 4 * math.hypot(gp[1], fd_se), (gp, fd, fd_se)
