@@ -137,7 +137,13 @@ def run_ours(args):
     kv0, kv1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     cfg = api.SteadyConfig(seed=seed, precision=L.FP32_TRACE, n_cells=run.n_cells, cell_axis=2, tally_axis=2,
                            per_bin=True, threads_per_block=args.threads, blocks_per_sm=args.blocks_per_sm,
-                           trace_events=(kv0, kv1))
+                           refill_threshold=args.refill, trace_events=(kv0, kv1))
+    if args.threads == 0 and not args.no_autotune:
+        from paper_2104_03573_gb300 import autotune
+        from dataclasses import replace
+        cfg = replace(autotune.tune(M, [G], [run.n], replace(cfg, trace_events=None)), trace_events=(kv0, kv1))
+    launch_shape = {"threads_per_block": cfg.threads_per_block, "blocks_per_sm": cfg.blocks_per_sm,
+                    "refill_threshold": cfg.refill_threshold}
     ws_bytes = api.steady_workspace_size(M, [G], [run.n], cfg)
     workspace = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     out = api.SteadyOutputs(1, M.n_bins, run.n_cells, True)
@@ -261,7 +267,7 @@ def run_ours(args):
                    "Holland tau at 300 K, walls 300+-0.5 K, 50 cells + per-bin flux; FP32 tracing, FP64 tallies",
                    "n_particles_per_gpu": run.n, "parallelism": f"independent samples x{ws}",
                    "l2": "256 MiB buffer zeroed between timed steps (outside the per-step CUDA events)",
-                   "seed": run.seed},
+                   "seed": run.seed, "launch": launch_shape},
         "s_to_1pct_se_kappa": t_1pct, "kappa_eff": kappa, "kappa_se": float(np.mean(kses)),
         "events_per_step": ev_step, "wall_s": wall_max,
         "fp64_plain": fp64,
@@ -347,6 +353,8 @@ def main():
     ap.add_argument("--fp64-particles", type=int, default=10_000_000)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--refill", type=int, default=0)
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

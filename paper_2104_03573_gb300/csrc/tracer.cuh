@@ -238,11 +238,29 @@ struct TallyPlain {
   }
 };
 
+// Out-of-line 64-bit conversion for the rare contributions beyond 2^31
+// fixed-point units (kept out of line so the common path never issues it).
+static __device__ __noinline__ long long fx_wide(float s) { return __float2ll_rn(s); }
+
+// v in fixed point (units of 2^-20), rounded to nearest; the common case
+// fits a 32-bit conversion, larger values take the 64-bit one.
+__device__ __forceinline__ long long fx(float v) {
+  const float s = v * kFx;
+  if (fabsf(s) < 2.0e9f) return (long long)__float2int_rn(s);
+  return fx_wide(s);
+}
+
+// Integer add to a tally that lives in shared or global memory (a generic
+// atomic: the hardware resolves the address space).
+__device__ __forceinline__ void red_s64(long long* a, long long v) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(a), (unsigned long long)v);
+}
+
 __device__ __forceinline__ void fx_add4(long long* a, float f0, float f1, float f2, float f3, float d) {
-  atomicAdd(reinterpret_cast<unsigned long long*>(a + 0), (unsigned long long)__float2ll_rn(f0 * d * kFx));
-  atomicAdd(reinterpret_cast<unsigned long long*>(a + 1), (unsigned long long)__float2ll_rn(f1 * d * kFx));
-  atomicAdd(reinterpret_cast<unsigned long long*>(a + 2), (unsigned long long)__float2ll_rn(f2 * d * kFx));
-  atomicAdd(reinterpret_cast<unsigned long long*>(a + 3), (unsigned long long)__float2ll_rn(f3 * d * kFx));
+  red_s64(a + 0, fx(f0 * d));
+  red_s64(a + 1, fx(f1 * d));
+  red_s64(a + 2, fx(f2 * d));
+  red_s64(a + 3, fx(f3 * d));
 }
 
 // FP32 path: fixed-point tallies.  Cells use a difference array: the (up to)
@@ -262,7 +280,7 @@ struct TallyFx {
 
   __device__ __forceinline__ void segment(Particle<float>& p, float seg) const {
     const float contrib = (p.s * seg) * sel3(p.u, ta);
-    p.Xq += __float2ll_rn(contrib * kFx);
+    p.Xq += fx(contrib);
     if (!cP) return;
     const float z0 = sel3(p.x, ca);
     const float uz = sel3(p.u, ca);
@@ -293,7 +311,7 @@ struct TallyFx {
 
   __device__ __forceinline__ void period_end(Particle<float>& p) const {
     if (qb) {
-      atomicAdd(reinterpret_cast<unsigned long long*>(qb + p.bin), (unsigned long long)(p.Xq - p.Xqper));
+      red_s64(qb + p.bin, p.Xq - p.Xqper);
       p.Xqper = p.Xq;
     }
   }

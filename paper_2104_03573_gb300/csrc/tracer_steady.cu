@@ -117,7 +117,40 @@ __global__ void __launch_bounds__(256) k_steady_fp64(const GeoRun* __restrict__ 
 
 #if MCBTE_F32
 // ------------------------------------------------------------------ FP32 persistent
-constexpr int kSmemGeos = 16;   // per-block particle accounting for up to 16 geometries
+// Per-thread book-keeping of finished particles (integer / fixed-point
+// fields, few registers), flushed to the geometry's global accumulators when
+// the thread moves to another geometry and at exit.
+struct ThreadAcct {
+  int g;
+  unsigned traced, trunc, absorbed, maxev;
+  int s_emit, s_abs;
+  unsigned long long ev;
+  long long sxq;      // sum of X in units of 2^-20 nm (exact)
+  double sx2;
+
+  __device__ __forceinline__ void reset(int gg) {
+    g = gg;
+    traced = trunc = absorbed = maxev = 0u;
+    s_emit = s_abs = 0;
+    ev = 0ull;
+    sxq = 0;
+    sx2 = 0.0;
+  }
+  __device__ __forceinline__ void flush(const Acc& A) const {
+    if (g < 0 || traced == 0u) return;
+    atomicAdd(&A.cnt[g * 4 + 0], ev);
+    if (trunc) atomicAdd(&A.cnt[g * 4 + 1], (unsigned long long)trunc);
+    atomicMax(&A.cnt[g * 4 + 2], (unsigned long long)maxev);
+    atomicAdd(&A.cnt[g * 4 + 3], (unsigned long long)traced);
+    atomicAdd(&A.dsc[g * 8 + 0], (double)sxq * kFxInv);
+    atomicAdd(&A.dsc[g * 8 + 1], sx2);
+    atomicAdd(&A.dsc[g * 8 + 2], (double)s_emit);
+    if (absorbed) {
+      atomicAdd(&A.dsc[g * 8 + 3], (double)s_abs);
+      atomicAdd(&A.dsc[g * 8 + 7], (double)absorbed);
+    }
+  }
+};
 
 // Every lane owns one particle at a time.  When its particle terminates the
 // lane refills from a global work counter; the refills of a warp are
@@ -129,13 +162,6 @@ template <bool CELLS, bool GRAD, int TPB>
 __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict__ geos,
                                                        const uint64_t* __restrict__ offs, MatView M, RunCfg C,
                                                        Acc A, SmemPlan S) {
-  __shared__ unsigned long long s_cnt[kSmemGeos][4];
-  __shared__ double s_dsc[kSmemGeos][8];
-  const bool acc_smem = C.n_geoms <= kSmemGeos;
-  for (int i = threadIdx.x; i < kSmemGeos * 4; i += blockDim.x) (&s_cnt[0][0])[i] = 0ull;
-  for (int i = threadIdx.x; i < kSmemGeos * 8; i += blockDim.x) (&s_dsc[0][0])[i] = 0.0;
-  unsigned long long* cnt_base = acc_smem ? &s_cnt[0][0] : A.cnt;
-  double* dsc_base = acc_smem ? &s_dsc[0][0] : A.dsc;
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* sp = smem;
   const int n = M.n;
@@ -173,6 +199,8 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
   const uint64_t deadline = *C.t0 + C.budget_ns;
   Particle<float> p;
   GradState gs;
+  ThreadAcct acct;
+  acct.reset(-1);
   TallyFx T;
   T.nc = nc;
   T.ca = C.cell_axis;
@@ -198,6 +226,10 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
         if (idx >= C.total) break;
         if (*(volatile int*)A.flags & 1) break;
         const int g = find_geom(offs, C.n_geoms, idx);
+        if (g != acct.g) {
+          acct.flush(A);
+          acct.reset(g);
+        }
         G = &geos[g];
         p.pid = (uint32_t)(idx - offs[g]);
         p.g = g;
@@ -222,39 +254,27 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
     if (out != STEP_ALIVE) {
       T.period_end(p);
       const double X = T.X(p);
-      const unsigned long long nev = (unsigned long long)p.e + 1ull;
-      unsigned long long* cn = cnt_base + p.g * 4;
-      double* ds = dsc_base + p.g * 8;
-      atomicAdd(cn + 0, nev);
-      if (out == STEP_TRUNCATED) atomicAdd(cn + 1, 1ull);
-      atomicMax(cn + 2, nev);
-      atomicAdd(cn + 3, 1ull);
-      atomicAdd(ds + 0, X);
-      atomicAdd(ds + 1, X * X);
-      atomicAdd(ds + 2, (double)p.s);
+      const unsigned nev = p.e + 1u;
+      acct.ev += nev;
+      acct.trunc += (out == STEP_TRUNCATED) ? 1u : 0u;
+      acct.maxev = nev > acct.maxev ? nev : acct.maxev;
+      acct.traced += 1u;
+      acct.sxq += p.Xq;
+      acct.sx2 += X * X;
+      const int sgn = p.s > 0.0f ? 1 : -1;
+      acct.s_emit += sgn;
       if (out == STEP_ABSORBED) {
-        atomicAdd(ds + 3, (double)p.s);
-        atomicAdd(ds + 7, 1.0);
+        acct.s_abs += sgn;
+        acct.absorbed += 1u;
       }
-      if (A.events_pp) A.events_pp[idx] = (uint32_t)nev;
+      if (A.events_pp) A.events_pp[idx] = nev;
       if (A.X_pp) A.X_pp[idx] = X;
       if (GRAD) grad_finish(&gs, X, p.g, C, A, M);
       alive = false;
     }
   }
+  acct.flush(A);
   __syncthreads();
-  if (acc_smem) {
-    for (int i = threadIdx.x; i < C.n_geoms * 4; i += blockDim.x) {
-      const unsigned long long v = (&s_cnt[0][0])[i];
-      if (v == 0ull) continue;
-      if ((i & 3) == 2) atomicMax(&A.cnt[i], v);
-      else atomicAdd(&A.cnt[i], v);
-    }
-    for (int i = threadIdx.x; i < C.n_geoms * 8; i += blockDim.x) {
-      const double v = (&s_dsc[0][0])[i];
-      if (v != 0.0) atomicAdd(&A.dsc[i], v);
-    }
-  }
   if (S.qbin_in_smem) {
     for (int i = threadIdx.x; i < n; i += blockDim.x)
       if (s_qbin[i] != 0) atomicAdd(reinterpret_cast<unsigned long long*>(&A.qbinq[i]), (unsigned long long)s_qbin[i]);
