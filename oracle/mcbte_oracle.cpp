@@ -27,7 +27,9 @@
 // "Parallel random numbers: as easy as 1, 2, 3"), implemented here from
 // that published definition.  Counter = (particle id, batch index, event
 // index, sub-block); key = (seed low, seed high).  Which word feeds which
-// draw is a fixed contract (listed at each use below).
+// draw is a fixed contract (listed at each use below); an emission uses
+// sub-blocks 0 and 1 exactly as a relaxation does for the bin, direction
+// and flight draws.
 //
 // Internal units: length nm, time ps, velocity nm/ps.
 //
@@ -489,12 +491,14 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
   for (uint64_t pid = p0; pid < p1; ++pid) {
     uint32_t ctr[4] = {(uint32_t)pid, P->batch_index, 0u, 0u};
     uint32_t w[4], w1[4], w2[4], w3[4];
-    // ---- emission (event 0)
+    // ---- emission (event 0): sub-blocks 0 and 1 carry the bin, direction
+    // and flight words exactly as a relaxation event does; sub 1 word 3
+    // picks the source; sub 2 carries the position and the sign / emission time.
     ctr[3] = 0; philox4x32_10(ctr, k0, k1, w);
     ctr[3] = 1; philox4x32_10(ctr, k0, k1, w1);
     ctr[3] = 2; philox4x32_10(ctr, k0, k1, w2);
     int k = 0;
-    while ((uint64_t)w[0] >= S.src_thr[k]) ++k;
+    while ((uint64_t)w1[3] >= S.src_thr[k]) ++k;
     const Source& src = S.src[k];
     double x[3], u[3];
     int bin;
@@ -502,38 +506,41 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
     double t_now = 0.0;
     if (src.kind == 0) {
       int f = src.face, a = kFaceAxis[f];
-      bin = alias_draw(t.emit, n, w[1], w[2], w[3]);
+      bin = alias_draw(t.emit, n, w[0], w[1], w1[0]);
       s = (g.Tb[f] > P->T_eq) ? 1.0 : -1.0;
-      double mu = std::sqrt(oc32(w1[0]));
-      dir_about_axis(u, a, kFaceIsMax[f] ? -1.0 : 1.0, mu, w1[1]);
-      if (P->transient) t_now = co32(w2[1]) * S.t_max_ps;
-      ctr[3] = 3; philox4x32_10(ctr, k0, k1, w3);
+      double mu = std::sqrt(oc32(w[2]));
+      dir_about_axis(u, a, kFaceIsMax[f] ? -1.0 : 1.0, mu, w[3]);
+      if (P->transient) t_now = co32(w2[3]) * S.t_max_ps;
       x[a] = kFaceIsMax[f] ? g.L[a] : 0.0;
-      x[(a + 1) % 3] = mid32(w3[0]) * g.L[(a + 1) % 3];
-      x[(a + 2) % 3] = mid32(w3[1]) * g.L[(a + 2) % 3];
+      x[(a + 1) % 3] = mid32(w2[0]) * g.L[(a + 1) % 3];
+      x[(a + 2) % 3] = mid32(w2[1]) * g.L[(a + 2) % 3];
     } else if (src.kind == 1) {
-      bin = alias_draw(t.emit, n, w[1], w[2], w[3]);
-      s = (w2[0] < 0x80000000u) ? 1.0 : -1.0;
+      bin = alias_draw(t.emit, n, w[0], w[1], w1[0]);
+      s = (w2[3] < 0x80000000u) ? 1.0 : -1.0;
       // positive particles travel down the control gradient, negative ones up it
       double dsgn = (s > 0.0) ? -S.grad_sign : S.grad_sign;
-      double mu = std::sqrt(oc32(w1[0]));
-      dir_about_axis(u, S.grad_axis, dsgn, mu, w1[1]);
-      int attempt = 0;
-      for (;;) {
-        ctr[3] = 3u + (uint32_t)attempt; philox4x32_10(ctr, k0, k1, w3);
+      double mu = std::sqrt(oc32(w[2]));
+      dir_about_axis(u, S.grad_axis, dsgn, mu, w[3]);
+      // uniform position in the solid: attempt 0 uses sub 2, attempt j sub 2 + j
+      for (int j = 0;; ++j) {
+        if (j > 0) {
+          ctr[3] = 2u + (uint32_t)j; philox4x32_10(ctr, k0, k1, w3);
+        } else {
+          for (int q = 0; q < 4; ++q) w3[q] = w2[q];
+        }
         x[0] = mid32(w3[0]) * g.L[0];
         x[1] = mid32(w3[1]) * g.L[1];
         x[2] = mid32(w3[2]) * g.L[2];
         if (!g.pore) break;
         double dx = x[0] - g.cx, dy = x[1] - g.cy;
         if (dx * dx + dy * dy >= g.r2) break;
-        if (++attempt >= 64) break;   // unreachable for porosities the API accepts
+        if (j + 1 >= 64) break;   // unreachable for porosities the API accepts
       }
     } else {
-      bin = alias_draw(t.init, n, w[1], w[2], w[3]);
+      bin = alias_draw(t.init, n, w[0], w[1], w1[0]);
       s = (P->gauss_dT > 0.0) ? 1.0 : -1.0;
-      double mu = 1.0 - 2.0 * oc32(w1[0]);
-      dir_about_axis(u, 2, 1.0, mu, w1[1]);
+      double mu = 1.0 - 2.0 * oc32(w[2]);
+      dir_about_axis(u, 2, 1.0, mu, w[3]);
       ctr[3] = 3; philox4x32_10(ctr, k0, k1, w3);
       double m1 = std::sqrt(-2.0 * series_log(oc32(w3[0])));
       double m2 = std::sqrt(-2.0 * series_log(oc32(w3[2])));
@@ -550,7 +557,7 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
         x[a] = c;
       }
     }
-    double d_rel = t.lam_nm[bin] * (-series_log(oc53(w1[2], w1[3])));
+    double d_rel = t.lam_nm[bin] * (-series_log(oc53(w1[1], w1[2])));
     out.scal[OR_SIGNED_EMIT] += s;
     uint32_t e = 0;
     int n_relax = 0;

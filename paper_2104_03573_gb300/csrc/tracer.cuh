@@ -99,62 +99,81 @@ __device__ __forceinline__ void load_bin(Particle<R>& p, const MatView& M, const
   }
 }
 
-// Emission of particle (pid, g) at event 0 (Sec. 3.2: source by cumulative
-// energy; Secs. 3.2.1-3.2.3: position, bin, sign, direction).
+// Shared resampling step of emissions and relaxations: bin from an alias
+// table (~C v or ~C at emission, Eqs. iso_flux / grad_flux_sim / Nbin;
+// ~C/tau at relaxation, Eq. n_scatt), direction with polar cosine
+// mu = sqrt(R) about a face normal or the gradient (Lambertian, Eq. wall_dir)
+// or mu = 1 - 2R (isotropic, Eq. angle_gen), new relaxation distance
+// Lambda (-ln R) (Eq. time_to_scat).  w, w1 are the event's sub-blocks 0 and 1.
 template <typename R>
-__device__ __forceinline__ void emit(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_emit,
-                                     const uint4* rec_init, const float4* binf, uint32_t k0, uint32_t k1,
-                                     bool transient, R t_max_ps) {
-  uint4 ctr = make_uint4(p.pid, (uint32_t)p.g, 0u, 0u);
-  const uint4 w0 = philox(ctr, k0, k1);
-  ctr.w = 1u;
-  const uint4 w1 = philox(ctr, k0, k1);
-  ctr.w = 2u;
+__device__ __forceinline__ void resample(Particle<R>& p, const MatView& M, const uint4* rec, const float4* binf,
+                                         uint4 w, uint4 w1, bool lambert, int axis, R sgn) {
+  p.bin = alias_draw(rec, M.n, w.x, w.y, w1.x);
+  const R mu = lambert ? Num<R>::sqrt_(Num<R>::oc(w.z)) : R(1) - R(2) * Num<R>::oc(w.z);
+  dir_about_axis<R>(p.u, axis, sgn, mu, w.w);
+  load_bin(p, M, binf);
+  p.d_rel = p.lam * (-Num<R>::log_(Num<R>::oc53(w1.y, w1.z)));
+}
+
+// Emission-only part of event 0 (Sec. 3.2: source by cumulative energy,
+// sub 1 word 3; Secs. 3.2.1-3.2.3: sign, emission time, position from sub 2,
+// further body-position attempts from sub 2 + j, Box-Muller from sub 3).
+// Returns the direction law for resample(): table (0 ~C v, 1 ~C), Lambertian
+// or isotropic, axis and sign.
+template <typename R>
+__device__ __forceinline__ void emit_prologue(Particle<R>& p, const GeoRun& g, uint32_t k0, uint32_t k1,
+                                              bool transient, R t_max_ps, uint4 w1, int* table, bool* lambert,
+                                              int* axis, R* sgn) {
+  uint4 ctr = make_uint4(p.pid, (uint32_t)p.g, 0u, 2u);
   const uint4 w2 = philox(ctr, k0, k1);
   int k = 0;
-  while ((uint64_t)w0.x >= g.src_thr[k]) ++k;
+  while ((uint64_t)w1.w >= g.src_thr[k]) ++k;
   const int kind = g.src_kind[k];
   p.t = R(0);
   if (kind == 0) {
     const int f = g.src_face[k];
     const int a = face_axis(f);
     const int mx = face_is_max(f);
-    p.bin = alias_draw(rec_emit, M.n, w0.y, w0.z, w0.w);
     p.s = (R)g.face_sign[f];
-    const R mu = Num<R>::sqrt_(Num<R>::oc(w1.x));
-    dir_about_axis<R>(p.u, a, mx ? R(-1) : R(1), mu, w1.y);
-    if (transient) p.t = Num<R>::co(w2.y) * t_max_ps;
-    ctr.w = 3u;
-    const uint4 w3 = philox(ctr, k0, k1);
+    *table = 0;
+    *lambert = true;
+    *axis = a;
+    *sgn = mx ? R(-1) : R(1);
+    if (transient) p.t = Num<R>::co(w2.w) * t_max_ps;
     const int a1 = (a == 2) ? 0 : a + 1;
     const int a2 = (a == 0) ? 2 : (a == 1 ? 0 : 1);
-    put3_cyclic<R>(p.x, a, mx ? geo_L<R>(g, a) : R(0), Num<R>::mid(w3.x) * geo_L<R>(g, a1),
-                   Num<R>::mid(w3.y) * geo_L<R>(g, a2));
+    put3_cyclic<R>(p.x, a, mx ? geo_L<R>(g, a) : R(0), Num<R>::mid(w2.x) * geo_L<R>(g, a1),
+                   Num<R>::mid(w2.y) * geo_L<R>(g, a2));
   } else if (kind == 1) {
-    p.bin = alias_draw(rec_emit, M.n, w0.y, w0.z, w0.w);
-    p.s = (w2.x < 0x80000000u) ? R(1) : R(-1);
+    p.s = (w2.w < 0x80000000u) ? R(1) : R(-1);
+    *table = 0;
+    *lambert = true;
+    *axis = g.grad_axis;
     // positive particles travel down the control gradient, negative ones up it
-    const R dsgn = (p.s > R(0)) ? (R)(-g.grad_sign) : (R)g.grad_sign;
-    const R mu = Num<R>::sqrt_(Num<R>::oc(w1.x));
-    dir_about_axis<R>(p.u, g.grad_axis, dsgn, mu, w1.y);
+    *sgn = (p.s > R(0)) ? (R)(-g.grad_sign) : (R)g.grad_sign;
     const R cx = sizeof(R) == 8 ? (R)g.cx : (R)g.cxf;
     const R cy = sizeof(R) == 8 ? (R)g.cy : (R)g.cyf;
     const R r2 = sizeof(R) == 8 ? (R)g.r2 : (R)g.r2f;
-    for (uint32_t attempt = 0;; ++attempt) {
-      ctr.w = 3u + attempt;
-      const uint4 w3 = philox(ctr, k0, k1);
+    uint4 w3 = w2;
+    for (uint32_t j = 0;; ++j) {
+      if (j > 0) {
+        ctr.w = 2u + j;
+        w3 = philox(ctr, k0, k1);
+      }
       p.x[0] = Num<R>::mid(w3.x) * geo_L<R>(g, 0);
       p.x[1] = Num<R>::mid(w3.y) * geo_L<R>(g, 1);
       p.x[2] = Num<R>::mid(w3.z) * geo_L<R>(g, 2);
       if (!g.pore) break;
       const R dx = p.x[0] - cx, dy = p.x[1] - cy;
       if (dx * dx + dy * dy >= r2) break;
-      if (attempt + 1 >= 64u) break;
+      if (j + 1 >= 64u) break;
     }
   } else {
-    p.bin = alias_draw(rec_init, M.n, w0.y, w0.z, w0.w);
     p.s = (R)g.gauss_sign;
-    dir_about_axis<R>(p.u, 2, R(1), R(1) - R(2) * Num<R>::oc(w1.x), w1.y);
+    *table = 1;
+    *lambert = false;
+    *axis = 2;
+    *sgn = R(1);
     ctr.w = 3u;
     const uint4 w3 = philox(ctr, k0, k1);
     const R m1 = Num<R>::sqrt_(R(-2) * Num<R>::log_(Num<R>::oc(w3.x)));
@@ -174,14 +193,42 @@ __device__ __forceinline__ void emit(Particle<R>& p, const GeoRun& g, const MatV
       p.x[a] = c;
     }
   }
-  load_bin(p, M, binf);
-  p.d_rel = p.lam * (-Num<R>::log_(Num<R>::oc53(w1.z, w1.w)));
+}
+
+__device__ __forceinline__ void particle_reset_counters(Particle<float>& p) {
   p.e = 0u;
   p.n_relax = 0;
   p.X = 0.0;
   p.Xper = 0.0;
   p.Xq = 0;
   p.Xqper = 0;
+}
+__device__ __forceinline__ void particle_reset_counters(Particle<double>& p) {
+  p.e = 0u;
+  p.n_relax = 0;
+  p.X = 0.0;
+  p.Xper = 0.0;
+  p.Xq = 0;
+  p.Xqper = 0;
+}
+
+// Emission of particle (pid, g) at event 0: the emission prologue, then the
+// shared resampling step with the source's bin law and direction law.
+template <typename R>
+__device__ __forceinline__ void emit(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_emit,
+                                     const uint4* rec_init, const float4* binf, uint32_t k0, uint32_t k1,
+                                     bool transient, R t_max_ps) {
+  uint4 ctr = make_uint4(p.pid, (uint32_t)p.g, 0u, 0u);
+  const uint4 w = philox(ctr, k0, k1);
+  ctr.w = 1u;
+  const uint4 w1 = philox(ctr, k0, k1);
+  int table;
+  bool lambert;
+  int axis;
+  R sgn;
+  emit_prologue<R>(p, g, k0, k1, transient, t_max_ps, w1, &table, &lambert, &axis, &sgn);
+  resample<R>(p, M, table ? rec_init : rec_emit, binf, w, w1, lambert, axis, sgn);
+  particle_reset_counters(p);
 }
 
 // ------------------------------------------------------------------ tally policies
@@ -344,7 +391,8 @@ __device__ __forceinline__ uint2 run_key(const RunCfg& C) {
 }
 
 // Outcome of one event step.
-enum { STEP_ALIVE = 0, STEP_ABSORBED = 1, STEP_DONE = 2, STEP_TRUNCATED = 3 };
+// STEP_RESAMPLE: a relaxation whose resampling the caller performs.
+enum { STEP_ALIVE = 0, STEP_ABSORBED = 1, STEP_DONE = 2, STEP_TRUNCATED = 3, STEP_RESAMPLE = 4 };
 
 // The event that ends a flight (Sec. 3.3 cases i/iii; Secs. 3.5.2-3.5.6):
 // relaxation (bin redrawn ~ C/tau, isotropic direction, new clock, sign
@@ -352,7 +400,7 @@ enum { STEP_ALIVE = 0, STEP_ABSORBED = 1, STEP_DONE = 2, STEP_TRUNCATED = 3 };
 // to the opposite face; adiabatic / pore: specular with probability p, else
 // Lambertian about the inward normal).  The particle has already moved.
 // `Xnow` is the particle's tally so far (gradient bookkeeping only).
-template <typename R, bool GRAD, class Tally>
+template <typename R, bool GRAD, class Tally, bool SPLIT = false>
 __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_relax,
                                            const float4* binf, const RunCfg& C, uint32_t k0, uint32_t k1,
                                            bool relax, int face, R seg, const Tally& T, GradState* gs, double Xnow) {
@@ -363,13 +411,11 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
     if (C.n_scat_max > 0 && p.n_relax >= C.n_scat_max) return STEP_DONE;
     // the relaxation period in this bin is over: frequency-resolved flux
     T.period_end(p);
+    if (SPLIT) return STEP_RESAMPLE;
     const uint4 w = philox(ctr, k0, k1);
     ctr.w = 1u;
     const uint4 w1 = philox(ctr, k0, k1);
-    p.bin = alias_draw(rec_relax, M.n, w.x, w.y, w1.x);
-    dir_about_axis<R>(p.u, 2, R(1), R(1) - R(2) * Num<R>::oc(w.z), w.w);
-    load_bin(p, M, binf);
-    p.d_rel = p.lam * (-Num<R>::log_(Num<R>::oc53(w1.y, w1.z)));
+    resample<R>(p, M, rec_relax, binf, w, w1, false, 2, R(1));
     if (GRAD) {
       if (gs->np < kMaxPeriods) {
         gs->bin[gs->np] = p.bin;
@@ -440,7 +486,7 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
 // remaining relaxation distance (boundary wins ties, Sec. 3.3 case iii),
 // track-length tallies of the flight (Eqs. temp_steady, flux_x_steady), then
 // the event.
-template <typename R, bool GRAD, class Tally>
+template <typename R, bool GRAD, class Tally, bool SPLIT = false>
 __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_relax,
                                            const float4* binf, const RunCfg& C, uint32_t k0, uint32_t k1,
                                            const Tally& T, GradState* gs) {
@@ -461,8 +507,8 @@ __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, cons
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
-  return apply_event<R, GRAD, Tally>(p, g, M, rec_relax, binf, C, k0, k1, relax, face, seg, T, gs,
-                                     GRAD ? T.X(p) : 0.0);
+  return apply_event<R, GRAD, Tally, SPLIT>(p, g, M, rec_relax, binf, C, k0, k1, relax, face, seg, T, gs,
+                                            GRAD ? T.X(p) : 0.0);
 }
 
 // One flight + event of a transient particle: the flight also ends at

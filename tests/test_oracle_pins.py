@@ -241,7 +241,7 @@ def test_gray_slab_flux_and_temperature():
     def f(a, e):
         rr = oracle.run_steady(mat, g, run, pid_begin=a, pid_end=e)
         return rr["T"] * (run.n / (e - a))
-    Tm, Tse = _batches(f, run.n)
+    Tm, Tse = _batches(f, run.n, nb=32)
     t, phi, _ = cf.gray_slab_nystrom(1.0, 801)
     edges = np.linspace(0, 1.0, 51)
     Tex = np.array([np.mean(np.interp(np.linspace(a, b, 41), t, phi)) - 0.5 for a, b in zip(edges[:-1], edges[1:])])
@@ -311,24 +311,43 @@ def test_partition_invariance():
     assert np.allclose(full["raw_T"], a["raw_T"] + b["raw_T"], rtol=1e-12, atol=1e-9)
 
 
+def _ballistic_cell_average(t, L, v, dT, nz):
+    """Exact cell averages of Eq. Analytical_T (one wall at z = 0, the other
+    by symmetry)."""
+    h = L / nz
+    out = np.zeros(nz)
+    for side, d in ((0, dT[0]), (1, dT[1])):
+        for i in range(nz):
+            a, b = (i * h, (i + 1) * h) if side == 0 else (L - (i + 1) * h, L - i * h)
+            f = v * t
+            hi = min(b, f)
+            if hi > a:      # integral of 0.5 (1 - z/f) over [a, hi]
+                out[i] += 0.5 * d * ((hi - a) - (hi * hi - a * a) / (2 * f)) / h
+    return out
+
+
 def test_ballistic_transient_matches_eq_analytical_T():
-    wl = W.ballistic_transient_e1(n=400_000, nz=30)
+    wl = W.ballistic_transient_e1(n=1_000_000, nz=30)
     mat, g, run = wl.material, wl.geometries[0], wl.run
 
     def f(a, e):
         rr = oracle.run_transient(mat, g, run, pid_begin=a, pid_end=e)
         return rr["tally"][:, :, 0, 0, 0] * (run.n / (e - a))
-    Tm, Tse = _batches(f, run.n)
-    L = 3e-6
-    zc = (np.arange(30) + 0.5) * L / 30
+    # 32 batches: batch-mean z-scores are t-distributed with 31 degrees of freedom
+    Tm, Tse = _batches(f, run.n, nb=32)
+    L, v = 3e-6, 12360.0
+    # temperature one particle adds to a cell: E_eff / (C V_cell)
+    quantum = (2 * 0.25 * v * 3.0 * run.t_max) / (run.n * L / 30)
     for m, t in enumerate(run.t_meas):
-        fine = np.linspace(0, L, 30 * 50 + 1)
-        ex = cf.ballistic_transient(fine, t, L, 12360.0, 3.0, -3.0)
-        exc = np.array([ex[i * 50:(i + 1) * 50 + 1].mean() for i in range(30)])
-        ok = Tse[m] > 0
-        z = (Tm[m][ok] - exc[ok]) / Tse[m][ok]
+        exc = _ballistic_cell_average(t, L, v, (3.0, -3.0), 30)
+        # cells with enough particles for normal statistics: z-test; cells near
+        # the ballistic fronts (a handful of particles): absolute bound
+        many = np.abs(exc) / quantum > 100
+        z = (Tm[m][many] - exc[many]) / Tse[m][many]
         assert np.max(np.abs(z)) < 5.0, (t, z)
-        assert np.all(np.abs(Tm[m][~ok] - exc[~ok]) < 1e-12)
+        few = ~many
+        if few.any():
+            assert np.max(np.abs(Tm[m][few] - exc[few])) < 0.03, (t, np.max(np.abs(Tm[m][few] - exc[few])))
 
 
 def test_transient_energy_conservation():
