@@ -1,32 +1,41 @@
 #!/usr/bin/env python3
 """Benchmark of the deviational Monte Carlo phonon-BTE hot path on GB300.
 
-Workload (default): steady cross-plane silicon-like film, L = 1 um, BvK
-dispersion with 3 x 1000 bins and Holland relaxation times at 300 K, walls at
-300 +/- 0.5 K, 1e7 deviational particles, 50 track-length cells and the
-frequency-resolved flux (3000 bins).  One step = one full run of the hot
-path: run setup, tracing of all 1e7 particles, finalisation.
+Default workload (`si_slab`): steady cross-plane silicon-like film, L = 1 um
+(a 1 um cube, periodic x, y), BvK dispersion with 3 x 1000 bins and Holland
+relaxation times at 300 K, walls at 300 +/- 0.5 K, 1e7 deviational
+particles, 50 track-length cells and the frequency-resolved flux.  One step
+= one full run of the hot path: run setup, tracing of all particles,
+finalisation.  Our arm times the persistent FP32 tracer (FP64-exact
+fixed-point tallies) and reports particle-events/s plus seconds to a 1 %
+standard error on kappa_eff (t_step * (SE_rel / 0.01)^2), with the plain FP64
+tracer timed beside it on the same inputs.
 
-Our arm times the persistent FP32 tracer (FP64 tallies) and reports
-particle-events/s plus seconds to a 1 % standard error on kappa_eff
-(t_run * (SE_rel / 0.01)^2), with the plain FP64 tracer timed beside it on
-the same inputs.  ``--impl reference`` times the FP64 CPU oracle on the host
-cores on a bounded sample of the same workload.
+Other workloads (`--workload`), same line format:
+  transient_box  2x2x1 um diffuse box, +1 K Gaussian hot spot, 1e8 particles,
+                 64x64x32 cells x 200 snapshot times (FP64 L2 atomics)
+  film_batch     64 films 10 nm..10 um in one persistent launch replayed as
+                 a CUDA graph, 1.4e8 particles in total
+  pore_grad      nanoporous film, 5e7 particles, forward + likelihood-ratio
+                 gradient over 3000 log-tau scales and the pore specularity
 
-Multi-GPU (torchrun): every rank traces its own independent 1e7-particle
-sample (seed offset by rank): weak scaling, no collective on the data path.
+`--impl reference` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.  Multi-GPU (torchrun): every rank traces its own
+independent sample (seed offset by rank): weak scaling, no collective on the
+data path.
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
-import math
 import os
 import statistics
 import subprocess
 import sys
 import tempfile
 import time
+from dataclasses import replace
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -36,22 +45,21 @@ from inputs import workloads as W  # noqa: E402
 
 METRIC = "particle-events/s and s to 1% std-err kappa_eff, batched FP32 vs plain FP64, 1 GB300"
 UNIT = "particle-events/s"
-WORKLOAD = "si_slab_L1um_3000bins"
+WORKLOADS = {"si_slab": "si_slab_L1um_3000bins", "transient_box": "transient_box_2x2x1um_gauss",
+             "film_batch": "film_batch_64_10nm_10um", "pore_grad": "pore_film_W100nm_phi0.25_t200nm_grad"}
 # Algorithmic thread-instructions per event of the tracer (one Philox4x32-10
 # call, log + sqrt + sincos, six-plane first hit, alias draw, state update and
 # tallies); the issue-rate roofline is SMs x 4 x 32 lanes x f_clk / this.
 INSTR_PER_EVENT = 200.0
-# DRAM bytes per launch of the FP32 tracing kernel on this workload, from the
-# ncu capture summarised in profiles/ (None until a capture of the current
-# kernel exists).
+# DRAM bytes per launch of the FP32 steady tracing kernel on the default
+# workload, from the ncu capture summarised in profiles/ (None until a capture
+# of the current kernel exists).
 TRACE_DRAM_BYTES_PER_LAUNCH = None
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    lrank = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, lrank
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
 def _peaks():
@@ -66,9 +74,7 @@ class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
     def __init__(self, index: int):
-        self.index = index
-        self.proc = None
-        self.path = None
+        self.index, self.proc, self.path = index, None, None
 
     def start(self):
         try:
@@ -78,7 +84,7 @@ class ClockSampler:
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -100,20 +106,198 @@ class ClockSampler:
         os.unlink(self.path)
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows]
         reasons = set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
             for k, nm in enumerate(names):
                 if r[5 + k].lower().startswith("active"):
                     reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "samples": len(rows),
-                "reasons": sorted(reasons)}
+        return {"sm_mhz": statistics.median(float(r[1]) for r in rows), "sm_max_mhz": float(rows[0][2]),
+                "samples": len(rows), "reasons": sorted(reasons)}
 
 
 def _material_bytes(mat) -> int:
     cols = [mat.omega, mat.v, mat.tau] + ([mat.C] if mat.C is not None else [mat.D, mat.domega])
     return sum(int(c.nbytes) for c in cols)
+
+
+class Timer:
+    """Per-step CUDA events around a step and, recorded by the library on the
+    launch stream, around its tracing kernel."""
+
+    def __init__(self):
+        import torch
+        self.torch = torch
+        E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+        self.s0, self.s1, self.k0, self.k1 = E(), E(), E(), E()
+        self.flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+
+    def run(self, step, steps):
+        stream = self.torch.cuda.current_stream()
+        step_ms, kern_ms, results = [], [], []
+        for _ in range(steps):
+            self.flush.zero_()                      # L2 flush between timed steps
+            # torch only times events it recorded itself: record the kernel
+            # events here; the library re-records them on the same stream just
+            # before and after the tracing kernel, elapsed_time uses the latest.
+            self.k0.record(stream)
+            self.k1.record(stream)
+            self.s0.record(stream)
+            r = step()
+            self.s1.record(stream)
+            self.s1.synchronize()
+            step_ms.append(self.s0.elapsed_time(self.s1))
+            kern_ms.append(self.k0.elapsed_time(self.k1))
+            results.append(r())
+        return step_ms, kern_ms, results
+
+
+def _workload_setup(name, args, seed_offset):
+    """Build (material, geometries, step factory, description, counters)."""
+    from paper_2104_03573_gb300 import api, _lib as L, batch, autotune
+    import torch
+    tm = Timer()
+    ev = (tm.k0, tm.k1)
+    if name == "si_slab":
+        wl = W.si_slab_c2(n=args.n_particles or 10_000_000)
+        mat, geo, run = wl.material, wl.geometries[0], wl.run
+        M, G = api.Material(mat), api.Geometry(geo)
+        cfg = api.SteadyConfig(seed=run.seed + seed_offset, precision=L.FP32_TRACE, n_cells=run.n_cells,
+                               cell_axis=2, tally_axis=2, per_bin=True, threads_per_block=args.threads,
+                               blocks_per_sm=args.blocks_per_sm, refill_threshold=args.refill)
+        if args.threads == 0 and not args.no_autotune:
+            cfg = autotune.tune(M, [G], [run.n], cfg)
+        cfg = replace(cfg, trace_events=ev)
+        ws = torch.empty(api.steady_workspace_size(M, [G], [run.n], cfg), dtype=torch.uint8, device="cuda")
+        out = api.SteadyOutputs(1, M.n_bins, run.n_cells, True)
+
+        def step():
+            api.run_steady(M, [G], [run.n], cfg, out=out, workspace=ws)
+            return lambda: out.stats.cpu().numpy()
+
+        def fp64(n64):
+            c = replace(cfg, precision=L.FP64_PLAIN, threads_per_block=0, refill_threshold=0)
+            o = api.SteadyOutputs(1, M.n_bins, run.n_cells, True)
+            return lambda: (api.run_steady(M, [G], [n64], c, out=o), (lambda: o.stats.cpu().numpy()))[1]
+
+        def e2e():
+            Mh, Gh = api.Material(mat), api.Geometry(geo)
+            res = api.run_steady_host(Mh, [Gh], [run.n], replace(cfg, trace_events=None))
+            return res["stats"]
+        d2h = 8 * (run.n_cells + 3 * run.n_cells + M.n_bins + L.NSTATS)
+        h2d = _material_bytes(mat) + ctypes.sizeof(L.GeometryDesc) + 8
+        desc = ("steady cross-plane Si-like film L=1um (1um cube, periodic x,y), BvK 3x1000 bins + Holland tau "
+                "at 300 K, walls 300+-0.5 K, 50 cells + per-bin flux; FP32 tracing, fixed-point FP64-exact tallies")
+        launches = 3
+        shape = {"threads_per_block": cfg.threads_per_block, "refill_threshold": cfg.refill_threshold}
+        return dict(mat=mat, geo=geo, run=run, n=run.n, step=step, fp64=fp64, e2e=e2e, d2h=d2h, h2d=h2d, desc=desc,
+                    launches=launches, timer=tm, kernel="k_steady_f32", shape=shape, kappa=True, kind="steady")
+    if name == "pore_grad":
+        wl = W.pore_film_c5(n=args.n_particles or 50_000_000)
+        mat, geo, run = wl.material, wl.geometries[0], wl.run
+        M, G = api.Material(mat), api.Geometry(geo)
+        cfg = api.SteadyConfig(seed=run.seed + seed_offset, precision=L.FP32_TRACE, tally_axis=1, per_bin=True,
+                               n_scat_max=10, max_events=10 ** 9, threads_per_block=args.threads or 768,
+                               refill_threshold=args.refill or 4, trace_events=ev, time_budget_s=300)
+        fwd = api.SteadyOutputs(1, M.n_bins, 0, True)
+        go = api.GradOutputs(M.n_bins)
+
+        def step():
+            api.grad(M, G, run.n, cfg, fwd=fwd, gout=go)
+            return lambda: fwd.stats.cpu().numpy()
+
+        def fp64(n64):
+            c = replace(cfg, precision=L.FP64_PLAIN)
+            f2, g2 = api.SteadyOutputs(1, M.n_bins, 0, True), api.GradOutputs(M.n_bins)
+            return lambda: (api.grad(M, G, n64, c, fwd=f2, gout=g2), (lambda: f2.stats.cpu().numpy()))[1]
+
+        def e2e():
+            import torch as t
+            Mh, Gh = api.Material(mat), api.Geometry(geo)
+            f3, g3 = api.grad(Mh, Gh, run.n, replace(cfg, trace_events=None))
+            return f3.stats.cpu().numpy(), g3.dkappa_dlogtau.cpu().numpy()
+        desc = ("nanoporous film: 100 nm cell, cylindrical pore porosity 0.25, 200 nm thick, diffuse walls, "
+                "grad_T -1e6 K/m along y, N_scat_max 10; forward + LR gradient (3000 log-tau + pore p)")
+        return dict(mat=mat, geo=geo, run=run, n=run.n, step=step, fp64=fp64, e2e=e2e,
+                    d2h=8 * (M.n_bins * 2 + 2 + L.NSTATS), h2d=_material_bytes(mat) + ctypes.sizeof(L.GeometryDesc) + 8,
+                    desc=desc, launches=3, timer=tm, kernel="k_steady_f32 (grad)",
+                    shape={"threads_per_block": cfg.threads_per_block, "refill_threshold": cfg.refill_threshold},
+                    kappa=True, kind="grad")
+    if name == "film_batch":
+        scale = (args.n_particles / 1.4e8) if args.n_particles else 1.0
+        wl = W.film_batch_c4(scale=scale)
+        mat, run = wl.material, wl.run
+        M = api.Material(mat)
+        Gs = [api.Geometry(g) for g in wl.geometries]
+        cfg = api.SteadyConfig(seed=run.seed + seed_offset, precision=L.FP32_TRACE, tally_axis=1, per_bin=True,
+                               n_scat_max=10, max_events=10 ** 9, threads_per_block=args.threads,
+                               refill_threshold=args.refill, trace_events=ev, time_budget_s=300)
+        gb = batch.GraphBatch(M, Gs, wl.n_per_geom, cfg, tune=(args.threads == 0 and not args.no_autotune))
+
+        def step():
+            gb.replay()
+            return lambda: gb.out.stats.cpu().numpy()
+
+        def fp64(n64):
+            fr = n64 / sum(wl.n_per_geom)
+            ns = [max(1, int(x * fr)) for x in wl.n_per_geom]
+            c = replace(cfg, precision=L.FP64_PLAIN, trace_events=ev)
+            o = api.SteadyOutputs(len(Gs), M.n_bins, 0, True)
+            return lambda: (api.run_steady(M, Gs, ns, c, out=o), (lambda: o.stats.cpu().numpy()))[1]
+
+        def e2e():
+            Mh = api.Material(mat)
+            Gh = [api.Geometry(g) for g in wl.geometries]
+            res = api.run_steady_host(Mh, Gh, wl.n_per_geom, replace(gb.cfg, trace_events=None, seed_device=None))
+            return res["stats"]
+        desc = ("64 in-plane films d = 10 nm * 1000^(f/63), 100x100 nm cell, periodic x,y, diffuse z, grad_T -1e6 K/m, "
+                "N_f = 1e5*100^u_f, N_scat_max 10; one persistent launch replayed as a CUDA graph")
+        return dict(mat=mat, geo=None, run=run, n=int(sum(wl.n_per_geom)), step=step, fp64=fp64, e2e=e2e,
+                    d2h=8 * 64 * (M.n_bins + L.NSTATS),
+                    h2d=_material_bytes(mat) + 64 * (ctypes.sizeof(L.GeometryDesc) + 8), desc=desc, launches=3,
+                    timer=tm, kernel="k_steady_f32 (64 geometries, graph)",
+                    shape={"threads_per_block": gb.cfg.threads_per_block, "refill_threshold": gb.cfg.refill_threshold},
+                    kappa=True, kind="batch")
+    if name == "transient_box":
+        wl = W.transient_box_c3(n=args.n_particles or 100_000_000)
+        mat, geo, run = wl.material, wl.geometries[0], wl.run
+        M, G = api.Material(mat), api.Geometry(geo)
+        cfg = api.TransientConfig(seed=run.seed + seed_offset, t_max=run.t_max, t_meas=run.t_meas, grid=run.grid,
+                                  precision=L.FP32_TRACE, threads_per_block=args.threads if args.threads in (0, 256, 512) else 0,
+                                  trace_events=ev, time_budget_s=300)
+        out = api.TransientOutputs(len(run.t_meas), run.grid, run.n)
+
+        def step():
+            api.run_transient(M, G, run.n, cfg, out=out)
+            return lambda: out.stats.cpu().numpy()[None, :]
+
+        def fp64(n64):
+            c = replace(cfg, precision=L.FP64_PLAIN)
+            o = api.TransientOutputs(len(run.t_meas), run.grid, n64)
+            return lambda: (api.run_transient(M, G, n64, c, out=o), (lambda: o.stats.cpu().numpy()[None, :]))[1]
+
+        def e2e():
+            import numpy as np
+            from paper_2104_03573_gb300 import _lib as LL
+            Mh, Gh = api.Material(mat), api.Geometry(geo)
+            nx, ny, nz = run.grid
+            tally = np.zeros((len(run.t_meas), nz, ny, nx, 4))
+            st = np.zeros(LL.NSTATS)
+            tmv = np.ascontiguousarray(run.t_meas, dtype=np.float64)
+            p = api.transient_params(replace(cfg, trace_events=None), run.n, tmv)
+            o = LL.TransientOut()
+            o.tally, o.stats, o.on_host = tally.ctypes.data, st.ctypes.data, 1
+            LL.check(LL.load().mcbte_run_transient(Mh.handle, Gh.handle, ctypes.byref(p), ctypes.byref(o), None, 0,
+                                                   None), allow=(LL.OK, LL.WARN_TRUNCATED))
+            return st[None, :]
+        nt = len(run.t_meas) * run.grid[0] * run.grid[1] * run.grid[2] * 4 * 8
+        desc = ("transient 2x2x1 um diffuse adiabatic box, +1 K Gaussian sigma 100 nm at the top-face centre, "
+                "64x64x32 cells x 200 snapshots (10 ps), FP32 flights, FP64 L2-atomic snapshot tallies")
+        return dict(mat=mat, geo=geo, run=run, n=run.n, step=step, fp64=fp64, e2e=e2e, d2h=nt + 8 * L.NSTATS,
+                    h2d=_material_bytes(mat) + ctypes.sizeof(L.GeometryDesc) + 8 * len(run.t_meas), desc=desc,
+                    launches=3, timer=tm, kernel="k_transient_f32", shape={"threads_per_block": cfg.threads_per_block},
+                    kappa=False, kind="transient")
+    raise ValueError(name)
 
 
 def run_ours(args):
@@ -126,159 +310,106 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", lrank))
-    from paper_2104_03573_gb300 import build, api, _lib as L
+    from paper_2104_03573_gb300 import build, _lib as L
     build.build()
-    wl = W.si_slab_c2(n=args.n_particles)
-    mat, geo, run = wl.material, wl.geometries[0], wl.run
-    M = api.Material(mat)
-    G = api.Geometry(geo)
-    seed = run.seed + 1_000_003 * rank
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    kv0, kv1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    cfg = api.SteadyConfig(seed=seed, precision=L.FP32_TRACE, n_cells=run.n_cells, cell_axis=2, tally_axis=2,
-                           per_bin=True, threads_per_block=args.threads, blocks_per_sm=args.blocks_per_sm,
-                           refill_threshold=args.refill, trace_events=(kv0, kv1))
-    if args.threads == 0 and not args.no_autotune:
-        from paper_2104_03573_gb300 import autotune
-        from dataclasses import replace
-        cfg = replace(autotune.tune(M, [G], [run.n], replace(cfg, trace_events=None)), trace_events=(kv0, kv1))
-    launch_shape = {"threads_per_block": cfg.threads_per_block, "blocks_per_sm": cfg.blocks_per_sm,
-                    "refill_threshold": cfg.refill_threshold}
-    ws_bytes = api.steady_workspace_size(M, [G], [run.n], cfg)
-    workspace = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
-    out = api.SteadyOutputs(1, M.n_bins, run.n_cells, True)
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB L2
-    stream = torch.cuda.current_stream()
-
-    def step():
-        api.run_steady(M, [G], [run.n], cfg, out=out, workspace=workspace, stream=stream)
-
+    wk = _workload_setup(args.workload, args, 1_000_003 * rank)
+    tm = wk["timer"]
     for _ in range(args.warmup):
-        step()
+        wk["step"]()()
     torch.cuda.synchronize()
     sampler = ClockSampler(lrank)
     sampler.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms, kern_ms, events, kappas, kses = [], [], [], [], []
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        flush.zero_()                                   # L2 flush between timed steps
-        # torch only times events it has recorded itself: record the kernel
-        # events once here; the library re-records them on the same stream
-        # just before and after the tracing kernel, and elapsed_time uses the
-        # latest records.
-        kv0.record(stream)
-        kv1.record(stream)
-        ev0.record(stream)
-        step()
-        ev1.record(stream)
-        ev1.synchronize()
-        step_ms.append(ev0.elapsed_time(ev1))
-        kern_ms.append(kv0.elapsed_time(kv1))
-        st = out.stats[0].cpu().numpy()
-        events.append(st[L.STAT_EVENTS])
-        kappas.append(st[L.STAT_KAPPA])
-        kses.append(st[L.STAT_KAPPA_SE])
-        assert st[L.STAT_STATUS] == 0, f"run status {st[L.STAT_STATUS]}"
+    step_ms, kern_ms, stats = tm.run(wk["step"], args.steps)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     wall = time.perf_counter() - t0
     clocks = sampler.stop()
-
-    t_step = sum(step_ms) / len(step_ms) / 1e3            # s, device time of one step on this rank
-    ev_step = float(np.mean(events))
+    for st in stats:
+        assert np.all(st[:, L.STAT_STATUS] == 0), f"run status {st[:, L.STAT_STATUS]}"
+    t_step = sum(step_ms) / len(step_ms) / 1e3
+    ev_step = float(np.mean([st[:, L.STAT_EVENTS].sum() for st in stats]))
     tot = torch.tensor([ev_step * args.steps, t_step * args.steps, wall], dtype=torch.float64, device="cuda")
     if dist:
         s = tot.clone()
         dist.all_reduce(s[0:1], op=dist.ReduceOp.SUM)
         dist.all_reduce(s[1:3], op=dist.ReduceOp.MAX)
         tot = s
-    total_events, t_max_ranks, wall_max = (float(x) for x in tot.cpu())
-    value = total_events / t_max_ranks
-    kappa = float(np.mean(kappas))
-    se_rel = float(np.mean(kses)) / kappa
-    t_1pct = t_step * (se_rel / 0.01) ** 2
-
+    total_events, t_ranks, wall_max = (float(x) for x in tot.cpu())
+    value = total_events / t_ranks
+    st = stats[-1]
+    kappa = kse = t_1pct = None
+    if wk["kappa"]:
+        k = st[:, L.STAT_KAPPA]
+        se = st[:, L.STAT_KAPPA_SE]
+        kappa, kse = float(k[0]), float(se[0])
+        t_1pct = float(t_step * np.max((se / np.abs(k) / 0.01) ** 2))
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
 
-    # plain FP64 tracer on the same inputs (one timed run after one warm-up)
     fp64 = None
     if not args.no_fp64:
-        c64 = api.SteadyConfig(seed=seed, precision=L.FP64_PLAIN, n_cells=run.n_cells, cell_axis=2, tally_axis=2,
-                               per_bin=True, trace_events=(kv0, kv1))
-        o64 = api.SteadyOutputs(1, M.n_bins, run.n_cells, True)
-        n64 = args.fp64_particles
-        api.run_steady(M, [G], [n64], c64, out=o64)
+        n64 = args.fp64_particles or (10_000_000 if args.workload == "si_slab" else 2_000_000)
+        f = wk["fp64"](n64)
+        f()()                                           # warm-up
         torch.cuda.synchronize()
-        flush.zero_()
-        kv0.record(stream)
-        kv1.record(stream)
-        ev0.record(stream)
-        api.run_steady(M, [G], [n64], c64, out=o64, stream=stream)
-        ev1.record(stream)
-        ev1.synchronize()
-        t64 = ev0.elapsed_time(ev1) / 1e3
-        s64 = o64.stats[0].cpu().numpy()
-        se64 = s64[L.STAT_KAPPA_SE] / s64[L.STAT_KAPPA]
-        fp64 = {"value": s64[L.STAT_EVENTS] / t64, "unit": UNIT, "n_particles": n64, "s_per_run": t64,
-                "kappa": s64[L.STAT_KAPPA], "kappa_se": s64[L.STAT_KAPPA_SE],
-                "s_to_1pct_se": t64 * (se64 / 0.01) ** 2}
+        s_ms, _, st64 = tm.run(f, 1)
+        t64 = s_ms[0] / 1e3
+        s64 = st64[0]
+        fp64 = {"value": float(s64[:, L.STAT_EVENTS].sum() / t64), "unit": UNIT, "n_particles": n64, "s_per_run": t64}
+        if wk["kappa"]:
+            se64 = s64[:, L.STAT_KAPPA_SE] / np.abs(s64[:, L.STAT_KAPPA])
+            fp64.update({"kappa": float(s64[0, L.STAT_KAPPA]), "kappa_se": float(s64[0, L.STAT_KAPPA_SE]),
+                         "s_to_1pct_se": float(t64 * np.max((se64 / 0.01) ** 2))})
 
     # end-to-end through the public API with host buffers: material upload and
-    # table build, run with host outputs (copies back, synchronises), release
-    e2e_times = []
-    n_e2e = max(1, min(args.steps, 3))
+    # table build, geometry upload, run with host outputs (copies back and
+    # synchronises), release
+    e2e_times, n_e2e = [], max(1, min(args.steps, 3))
+    ev_e2e = None
     for k in range(n_e2e + 1):
+        torch.cuda.synchronize()
         t_a = time.perf_counter()
-        Mh = api.Material(mat)
-        Gh = api.Geometry(geo)
-        res = api.run_steady_host(Mh, [Gh], [run.n], cfg_host(api, L, run, seed))
-        del Mh, Gh
+        r = wk["e2e"]()
         t_b = time.perf_counter()
         if k > 0:
             e2e_times.append(t_b - t_a)
-        ev_e2e = res["stats"][0][L.STAT_EVENTS]
+        ev_e2e = float(np.asarray(r[0] if isinstance(r, tuple) else r)[:, L.STAT_EVENTS].sum())
     t_e2e = sum(e2e_times) / len(e2e_times)
-    import ctypes
-    # material columns + geometry descriptor + the n_particles word
-    h2d = _material_bytes(mat) + ctypes.sizeof(L.GeometryDesc) + 8
-    d2h = 8 * (run.n_cells + 3 * run.n_cells + M.n_bins + L.NSTATS)
 
     peaks, peak_kind = _peaks()
-    props = torch.cuda.get_device_properties(lrank)
-    n_sm = props.multi_processor_count
+    n_sm = torch.cuda.get_device_properties(lrank).multi_processor_count
     f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     peak_tinst = n_sm * 4 * 32 * f_max / 1e12
     t_kern = sum(kern_ms) / len(kern_ms) / 1e3
     achieved = ev_step * INSTR_PER_EVENT / t_kern / 1e12
-
-    cpu = cpu_baseline(mat, geo, run, args) if (ws == 1 and not args.no_cpu) else None
+    cpu = cpu_baseline(wk, args) if (ws == 1 and not args.no_cpu) else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "description": "steady cross-plane Si-like film L=1um, BvK 3x1000 bins + "
-                   "Holland tau at 300 K, walls 300+-0.5 K, 50 cells + per-bin flux; FP32 tracing, FP64 tallies",
-                   "n_particles_per_gpu": run.n, "parallelism": f"independent samples x{ws}",
+        "config": {"workload": WORKLOADS[args.workload], "description": wk["desc"], "n_particles_per_gpu": wk["n"],
+                   "parallelism": f"independent samples x{ws}",
                    "l2": "256 MiB buffer zeroed between timed steps (outside the per-step CUDA events)",
-                   "seed": run.seed, "launch": launch_shape},
-        "s_to_1pct_se_kappa": t_1pct, "kappa_eff": kappa, "kappa_se": float(np.mean(kses)),
+                   "seed": wk["run"].seed, "launch": wk["shape"]},
+        "s_to_1pct_se_kappa": t_1pct, "kappa_eff": kappa, "kappa_se": kse,
         "events_per_step": ev_step, "wall_s": wall_max,
         "fp64_plain": fp64,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
-                     "frac": achieved / peak_tinst, "traffic": TRACE_DRAM_BYTES_PER_LAUNCH,
-                     "kernel": "k_steady_f32", "kernel_ms": t_kern * 1e3,
+                     "frac": achieved / peak_tinst,
+                     "traffic": TRACE_DRAM_BYTES_PER_LAUNCH if args.workload == "si_slab" else None,
+                     "kernel": wk["kernel"], "kernel_ms": t_kern * 1e3,
                      "peak_basis": f"{n_sm} SMs x 4 x 32 lanes x {f_max / 1e6:.0f} MHz ({peak_kind} sm_max_mhz); "
                                    f"{INSTR_PER_EVENT:.0f} algorithmic thread-instructions per event"},
-        "e2e": {"value": ev_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "s_per_step": t_e2e},
-        "gpu_launches": 3 * args.steps,
+        "e2e": {"value": ev_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(wk["h2d"]),
+                "d2h_bytes_per_step": int(wk["d2h"]), "s_per_step": t_e2e},
+        "gpu_launches": wk["launches"] * args.steps,
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
@@ -287,31 +418,54 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def cfg_host(api, L, run, seed):
-    return api.SteadyConfig(seed=seed, precision=L.FP32_TRACE, n_cells=run.n_cells, cell_axis=2, tally_axis=2,
-                            per_bin=True)
-
-
-def cpu_baseline(mat, geo, run, args, target_s: float = None):
+def cpu_baseline(wk, args, target_s=None):
     """The oracle, as it stands, on the host cores: a bounded sample of the
     same workload sized to about `target_s` seconds of CPU work."""
     import oracle
     target_s = target_s or args.cpu_seconds
-    probe = W.SteadyRun(n=100_000, seed=run.seed, n_cells=run.n_cells, cell_axis=2, tally_axis=2, per_bin=True)
+    run, mat = wk["run"], wk["mat"]
+    kind = wk["kind"]
+    if kind == "transient":
+        def go(n):
+            r = W.TransientRun(n=n, seed=run.seed, t_max=run.t_max, t_meas=run.t_meas, grid=run.grid)
+            return oracle.run_transient(mat, wk["geo"], r, n_threads=4)
+        probe_n = 5_000
+        cores = 4
+    elif kind == "batch":
+        wl = W.film_batch_c4()
+        geos = wl.geometries
+
+        def go(n):
+            tot_ev, res = 0.0, None
+            per = max(1, n // 8)
+            for f in range(0, 64, 8):
+                r = oracle.run_steady(mat, geos[f], replace(run, max_events=10 ** 9), n_total=per, batch_index=f)
+                tot_ev += r["events"]
+                res = r
+            res = dict(res)
+            res["events"] = tot_ev
+            return res
+        probe_n = 8_000
+        cores = os.cpu_count()
+    else:
+        def go(n):
+            r = replace(run, n=n)
+            return oracle.run_steady(mat, wk["geo"], r, grad=(kind == "grad"))
+        probe_n = 50_000
+        cores = os.cpu_count()
     t0 = time.perf_counter()
-    r0 = oracle.run_steady(mat, geo, probe)
+    r0 = go(probe_n)
     dt0 = time.perf_counter() - t0
-    rate = r0["events"] / dt0
-    ev_per_p = r0["events"] / probe.n
-    n = int(min(run.n, max(100_000, target_s * rate / ev_per_p)))
-    sample = W.SteadyRun(n=n, seed=run.seed, n_cells=run.n_cells, cell_axis=2, tally_axis=2, per_bin=True)
+    n = int(min(wk["n"], max(probe_n, probe_n * target_s / max(dt0, 1e-3))))
     t0 = time.perf_counter()
-    r = oracle.run_steady(mat, geo, sample)
+    r = go(n)
     dt = time.perf_counter() - t0
-    se_rel = r["kappa_se"] / r["kappa"]
-    return {"value": r["events"] / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n} of {run.n} particles of the same workload ({r['events']:.3g} events, {dt:.1f} s)",
-            "s_to_1pct_se_kappa": dt * (se_rel / 0.01) ** 2, "kappa_eff": r["kappa"]}
+    out = {"value": r["events"] / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{n} of {wk['n']} particles of the same workload ({r['events']:.3g} events, {dt:.1f} s)"}
+    if "kappa" in r and wk["kappa"] and kind != "batch":
+        out["s_to_1pct_se_kappa"] = dt * (r["kappa_se"] / abs(r["kappa"]) / 0.01) ** 2
+        out["kappa_eff"] = r["kappa"]
+    return out
 
 
 def run_reference(args):
@@ -319,23 +473,22 @@ def run_reference(args):
     if rank != 0:
         return
     mat = W.bvk_holland()
-    wl = W.si_slab_c2(n=args.n_particles, material=mat)
-    geo, run = wl.geometries[0], wl.run
-    import oracle
+    wl = W.si_slab_c2(n=args.n_particles or 10_000_000, material=mat)
+    wk = {"run": wl.run, "mat": mat, "geo": wl.geometries[0], "kind": "steady", "n": wl.run.n, "kappa": True}
     per = max(2.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        cpu_baseline(mat, geo, run, args, target_s=per)
+        cpu_baseline(wk, args, target_s=per)
     res = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        res.append(cpu_baseline(mat, geo, run, args, target_s=per))
+        res.append(cpu_baseline(wk, args, target_s=per))
     wall = time.perf_counter() - t0
     value = statistics.mean(r["value"] for r in res)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": wall / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOAD, "n_particles_per_gpu": run.n, "seed": run.seed},
+        "config": {"workload": WORKLOADS["si_slab"], "n_particles_per_gpu": wl.run.n, "seed": wl.run.seed},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                          "sample": res[-1]["sample"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -349,8 +502,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n-particles", type=int, default=10_000_000)
-    ap.add_argument("--fp64-particles", type=int, default=10_000_000)
+    ap.add_argument("--workload", default="si_slab", choices=sorted(WORKLOADS))
+    ap.add_argument("--n-particles", type=int, default=0)
+    ap.add_argument("--fp64-particles", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--refill", type=int, default=0)

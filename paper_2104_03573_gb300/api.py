@@ -127,6 +127,9 @@ class SteadyConfig:
 def _event_handles(pair):
     if not pair:
         return None, None
+    for e in pair:
+        if not e.cuda_event:
+            e.record()          # torch creates the CUDA event at its first record
     return pair[0].cuda_event, pair[1].cuda_event
 
 

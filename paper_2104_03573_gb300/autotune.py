@@ -21,7 +21,7 @@ from . import api
 _CACHE: Dict[tuple, dict] = {}
 
 DEFAULT_CANDIDATES: Tuple[Tuple[int, int, int], ...] = (
-    (512, 0, 1), (768, 0, 1), (1024, 0, 1), (768, 0, 4), (768, 0, 16), (256, 0, 1),
+    (1024, 0, 4), (1024, 0, 8), (1024, 0, 1), (768, 0, 4), (768, 0, 1), (512, 0, 4), (256, 0, 1),
 )
 
 
@@ -32,10 +32,12 @@ def _key(material: api.Material, geoms: Sequence[api.Geometry], n_particles, cfg
 
 
 def tune(material: api.Material, geoms: Sequence[api.Geometry], n_particles, cfg: api.SteadyConfig, *,
-         fraction: float = 0.05, min_particles: int = 20_000, repeats: int = 2,
+         fraction: float = 0.25, min_particles: int = 20_000, repeats: int = 2,
          candidates: Optional[Iterable[Tuple[int, int, int]]] = None, verbose: bool = False) -> api.SteadyConfig:
     """Return `cfg` with the fastest (threads_per_block, blocks_per_sm,
-    refill_threshold) for this workload (FP32 path only)."""
+    refill_threshold) for this workload (FP32 path only).  The sample must
+    hold tens of particles per resident lane, or the drain tail of the
+    persistent launch, not its steady state, decides the ranking."""
     import torch
     if cfg.precision != L.FP32_TRACE:
         return cfg

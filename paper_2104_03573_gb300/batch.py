@@ -27,9 +27,11 @@ class GraphBatch:
         self.geoms = list(geoms)
         self.n = np.ascontiguousarray(np.asarray(n_particles, dtype=np.uint64))
         if tune and cfg.precision == L.FP32_TRACE:
-            cfg = autotune.tune(material, self.geoms, self.n, cfg)
+            cfg = replace(autotune.tune(material, self.geoms, self.n, replace(cfg, trace_events=None)),
+                          trace_events=cfg.trace_events)
         self.seed = torch.tensor([int(cfg.seed)], dtype=torch.int64, device="cuda")
-        self.cfg = replace(cfg, seed_device=self.seed, trace_events=None)
+        # trace events, if given, become event-record nodes of the graph
+        self.cfg = replace(cfg, seed_device=self.seed)
         ws = api.steady_workspace_size(material, self.geoms, self.n, self.cfg)
         self.workspace = torch.empty(ws, dtype=torch.uint8, device="cuda")
         self.out = api.SteadyOutputs(len(self.geoms), material.n_bins, cfg.n_cells, cfg.per_bin)

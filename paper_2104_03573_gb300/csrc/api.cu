@@ -22,6 +22,18 @@ mcbte_status fail(mcbte_status s, const std::string& msg) {
   return s;
 }
 
+// Caller-owned timing event around the trace kernel. Inside a stream capture
+// it becomes an external event-record node, so that it fires at every replay
+// of the graph; outside a capture it is a plain record.
+cudaError_t record_trace_event(void* ev, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const cudaError_t e = cudaStreamIsCapturing(s, &cs);
+  if (e != cudaSuccess) return e;
+  if (cs == cudaStreamCaptureStatusActive)
+    return cudaEventRecordWithFlags((cudaEvent_t)ev, s, cudaEventRecordExternal);
+  return cudaEventRecord((cudaEvent_t)ev, s);
+}
+
 mcbte_status cuda_fail(cudaError_t e, const char* what) {
   return fail(e == cudaErrorMemoryAllocation ? MCBTE_ERR_OOM : MCBTE_ERR_CUDA,
               std::string(what) + ": " + cudaGetErrorString(e));
@@ -460,9 +472,9 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
     C.dirs = w.dirs;
     C.dpi = w.dpi;
   }
-  if (p->trace_event_start) RUN_TRY(cudaEventRecord((cudaEvent_t)p->trace_event_start, s));
+  if (p->trace_event_start) RUN_TRY(record_trace_event(p->trace_event_start, s));
   RUN_TRY(launch_steady(p->precision, grad, w.geos, w.offs, m->view, C, A, p->threads_per_block, p->blocks_per_sm, s));
-  if (p->trace_event_stop) RUN_TRY(cudaEventRecord((cudaEvent_t)p->trace_event_stop, s));
+  if (p->trace_event_stop) RUN_TRY(record_trace_event(p->trace_event_stop, s));
   SteadyOutDev O{};
   O.T = host_out ? w.T : out->T;
   O.q = host_out ? w.q : out->q;
@@ -682,11 +694,11 @@ mcbte_status mcbte_run_transient(const mcbte_material* m, const mcbte_geometry* 
   A.flags = w.flags;
   A.snap = snap;
   A.events_pp = host_out ? w.events_pp : out->events_pp;
-  if (p->trace_event_start) RUN_TRY(cudaEventRecord((cudaEvent_t)p->trace_event_start, s));
+  if (p->trace_event_start) RUN_TRY(record_trace_event(p->trace_event_start, s));
   RUN_TRY(launch_transient(p->precision, w.geos, m->view, C, A, p->threads_per_block, p->blocks_per_sm, s));
-  if (p->trace_event_stop) RUN_TRY(cudaEventRecord((cudaEvent_t)p->trace_event_stop, s));
+  if (p->trace_event_stop) RUN_TRY(record_trace_event(p->trace_event_stop, s));
   double* stats = host_out ? w.stats : out->stats;
-  RUN_TRY(launch_finalize_transient(w.geos, m->view, C, A, snap, stats, ncell, s));
+  RUN_TRY(launch_finalize_transient(w.geos, m->view, C, A, snap, stats, ncell, p->precision == MCBTE_FP32_TRACE, s));
   mcbte_status result = MCBTE_OK;
   if (host_out) {
     RUN_TRY(cudaMemcpyAsync(out->tally, snap, snap_len * sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -56,7 +56,8 @@ cudaError_t launch_transient(int precision, const GeoRun* geos, const MatView& M
                              int threads, int blocks_per_sm, cudaStream_t s);
 
 cudaError_t launch_finalize_transient(const GeoRun* geos, const MatView& M, const RunCfg& C, const Acc& A,
-                                      double* tally, double* stats, size_t n_cells_total, cudaStream_t s);
+                                      double* tally, double* stats, size_t n_cells_total, bool fixed,
+                                      cudaStream_t s);
 
 // Material table build (FP64): per-bin kernel + one thread per alias table.
 struct MatBuild {

@@ -243,10 +243,10 @@ struct TallyPlain {
 
   __device__ __forceinline__ double X(const Particle<double>& p) const { return p.X; }
 
-  __device__ __forceinline__ void segment(Particle<double>& p, double seg) const {
+  __device__ __forceinline__ double segment(Particle<double>& p, double seg) const {
     const double contrib = (p.s * seg) * sel3(p.u, ta);
     p.X += contrib;
-    if (!cP) return;
+    if (!cP) return contrib;
     const double z0 = sel3(p.x, ca);
     const double uc = sel3(p.u, ca);
     const double z1 = z0 + seg * uc;
@@ -256,7 +256,7 @@ struct TallyPlain {
       atomicAdd(&cP[c * 4 + 0], (p.s * seg) * p.inv_v);
 #pragma unroll
       for (int b = 0; b < 3; ++b) atomicAdd(&cP[c * 4 + 1 + b], (p.s * seg) * p.u[b]);
-      return;
+      return contrib;
     }
     const double zlo = z0 < z1 ? z0 : z1;
     const double zhi = z0 < z1 ? z1 : z0;
@@ -275,6 +275,7 @@ struct TallyPlain {
 #pragma unroll
       for (int b = 0; b < 3; ++b) atomicAdd(&cP[c * 4 + 1 + b], (p.s * l) * p.u[b]);
     }
+    return contrib;
   }
 
   __device__ __forceinline__ void period_end(Particle<double>& p) const {
@@ -325,17 +326,17 @@ struct TallyFx {
 
   __device__ __forceinline__ double X(const Particle<float>& p) const { return (double)p.Xq * kFxInv; }
 
-  __device__ __forceinline__ void segment(Particle<float>& p, float seg) const {
+  __device__ __forceinline__ float segment(Particle<float>& p, float seg) const {
     const float contrib = (p.s * seg) * sel3(p.u, ta);
     p.Xq += fx(contrib);
-    if (!cP) return;
+    if (!cP) return contrib;
     const float z0 = sel3(p.x, ca);
     const float uz = sel3(p.u, ca);
     if (uz == 0.0f) {
       const int c = min(max((int)(z0 * inv_h), 0), nc - 1);
       const float sl = p.s * seg;
       fx_add4(cP + c * 4, sl * p.inv_v, sl * p.u[0], sl * p.u[1], sl * p.u[2], 1.0f);
-      return;
+      return contrib;
     }
     const float z1 = z0 + seg * uz;
     const float zlo = fminf(z0, z1);
@@ -346,7 +347,7 @@ struct TallyFx {
     const float f0 = k * p.inv_v, f1 = k * p.u[0], f2 = k * p.u[1], f3 = k * p.u[2];
     if (clo == chi) {
       fx_add4(cP + clo * 4, f0, f1, f2, f3, zhi - zlo);
-      return;
+      return contrib;
     }
     fx_add4(cP + clo * 4, f0, f1, f2, f3, (float)(clo + 1) * h - zlo);
     fx_add4(cP + chi * 4, f0, f1, f2, f3, zhi - (float)chi * h);
@@ -354,6 +355,7 @@ struct TallyFx {
       fx_add4(cD + (clo + 1) * 4, f0, f1, f2, f3, h);
       fx_add4(cD + chi * 4, f0, f1, f2, f3, -h);
     }
+    return contrib;
   }
 
   __device__ __forceinline__ void period_end(Particle<float>& p) const {
@@ -370,8 +372,35 @@ struct TallyNone {
   __device__ __forceinline__ void period_end(Particle<R>&) const {}
 };
 
-// Likelihood-ratio bookkeeping of one particle (steady gradient runs).
-struct GradState {
+// ------------------------------------------------------------------ likelihood-ratio policies
+// Scores of the sampled laws (no gradient in the paper; derived from them):
+//   flight ended by relaxation   -1 + l / Lambda   (density of Eq. time_to_scat)
+//   flight ended by a boundary        l / Lambda   (survival)
+//   resampling into bin i        -delta_ij + pi_j  (law ~ C/tau of Eq. n_scatt)
+//   specular / diffuse pore hit   1/p, -1/(1-p)    (Sec. 3.5.3)
+// Each score multiplies the tally still to come (causal form).  Per particle
+// and relaxation period k (bin b_k): G[b_k] += A_k X - B_k with A_k the sum
+// of its scores and B_k the sum of score x tally-so-far; the dense pi_j part
+// is R pi_j with R = n_res X - sum of X at each resampling.
+
+struct GradOff {
+  static constexpr bool on = false;
+  __device__ __forceinline__ void init(int) {}
+  template <typename C>
+  __device__ __forceinline__ void flight(bool, double, double, C) {}
+  __device__ __forceinline__ void resampled(int, double) {}
+  __device__ __forceinline__ void pore_hit(bool, double, double) {}
+  __device__ __forceinline__ int periods() const { return 0; }
+  __device__ __forceinline__ int period_bin(int) const { return 0; }
+  __device__ __forceinline__ double period_value(int, double) const { return 0.0; }
+  __device__ __forceinline__ double resample_term(double) const { return 0.0; }
+  __device__ __forceinline__ double spec_term(double) const { return 0.0; }
+};
+
+// FP64 path: the per-segment form, kept operation for operation with the
+// CPU implementation of the same scores.
+struct GradList {
+  static constexpr bool on = true;
   int np;
   int bin[kMaxPeriods];
   double A[kMaxPeriods];
@@ -379,6 +408,98 @@ struct GradState {
   int n_res;
   double sum_x_res;
   double PA, PB;
+
+  __device__ __forceinline__ void init(int b) {
+    np = 1;
+    bin[0] = b;
+    A[0] = 0.0;
+    B[0] = 0.0;
+    n_res = 0;
+    sum_x_res = 0.0;
+    PA = 0.0;
+    PB = 0.0;
+  }
+  // ratio = l / Lambda of the flight; Xb = tally before it
+  __device__ __forceinline__ void flight(bool relax, double ratio, double Xb, double) {
+    double score = ratio;
+    if (relax) score = score - 1.0;
+    A[np - 1] += score;
+    B[np - 1] += score * Xb;
+  }
+  __device__ __forceinline__ void resampled(int b, double Xnow) {
+    if (np < kMaxPeriods) {
+      bin[np] = b;
+      A[np] = -1.0;
+      B[np] = -Xnow;
+      np++;
+    }
+    n_res++;
+    sum_x_res += Xnow;
+  }
+  __device__ __forceinline__ void pore_hit(bool spec, double p, double Xnow) {
+    const double sc = spec ? 1.0 / p : -1.0 / (1.0 - p);
+    PA += sc;
+    PB += sc * Xnow;
+  }
+  __device__ __forceinline__ double period_value(int k, double X) const { return A[k] * X - B[k]; }
+  __device__ __forceinline__ int periods() const { return np; }
+  __device__ __forceinline__ int period_bin(int k) const { return bin[k]; }
+  __device__ __forceinline__ double resample_term(double X) const { return (double)n_res * X - sum_x_res; }
+  __device__ __forceinline__ double spec_term(double X) const { return PA * X - PB; }
+};
+
+// FP32 path: the current period lives in registers as (a, d) with
+// d = a X - b, which a flight with tally increment c advances by a c (after
+// adding its score to a); completed periods are written once each.  The
+// specularity score uses the same form, so its value needs no list.
+struct GradFast {
+  static constexpr bool on = true;
+  int np;
+  int bin[kMaxPeriods];
+  float A[kMaxPeriods];
+  double B[kMaxPeriods];
+  int bin_cur;
+  float a, d;
+  float pa, pd;
+  int n_res;
+  double sum_x_res;
+
+  __device__ __forceinline__ void init(int b) {
+    np = 0;
+    bin_cur = b;
+    a = d = pa = pd = 0.0f;
+    n_res = 0;
+    sum_x_res = 0.0;
+  }
+  __device__ __forceinline__ void flight(bool relax, double ratio, double, float c) {
+    a += (float)ratio - (relax ? 1.0f : 0.0f);
+    d = fmaf(a, c, d);
+    pd = fmaf(pa, c, pd);
+  }
+  __device__ __forceinline__ void resampled(int b, double Xnow) {
+    if (np < kMaxPeriods) {
+      bin[np] = bin_cur;
+      A[np] = a;
+      B[np] = (double)a * Xnow - (double)d;
+      np++;
+    }
+    bin_cur = b;
+    a = -1.0f;
+    d = 0.0f;
+    n_res++;
+    sum_x_res += Xnow;
+  }
+  __device__ __forceinline__ void pore_hit(bool spec, double p, double) {
+    pa += spec ? (float)(1.0 / p) : (float)(-1.0 / (1.0 - p));
+  }
+  // periods 0..np-1 are completed; index np is the current one
+  __device__ __forceinline__ double period_value(int k, double X) const {
+    return k < np ? (double)A[k] * X - B[k] : (double)d;
+  }
+  __device__ __forceinline__ int periods() const { return np + 1; }
+  __device__ __forceinline__ int period_bin(int k) const { return k < np ? bin[k] : bin_cur; }
+  __device__ __forceinline__ double resample_term(double X) const { return (double)n_res * X - sum_x_res; }
+  __device__ __forceinline__ double spec_term(double) const { return (double)pd; }
 };
 
 // Philox key of the run: the host seed, or the device-resident one.
@@ -400,10 +521,10 @@ enum { STEP_ALIVE = 0, STEP_ABSORBED = 1, STEP_DONE = 2, STEP_TRUNCATED = 3, STE
 // to the opposite face; adiabatic / pore: specular with probability p, else
 // Lambertian about the inward normal).  The particle has already moved.
 // `Xnow` is the particle's tally so far (gradient bookkeeping only).
-template <typename R, bool GRAD, class Tally, bool SPLIT = false>
+template <typename R, class Grad, class Tally, bool SPLIT = false>
 __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_relax,
                                            const float4* binf, const RunCfg& C, uint32_t k0, uint32_t k1,
-                                           bool relax, int face, R seg, const Tally& T, GradState* gs, double Xnow) {
+                                           bool relax, int face, R seg, const Tally& T, Grad& gr, double Xnow) {
   ++p.e;
   uint4 ctr = make_uint4(p.pid, (uint32_t)p.g, p.e, 0u);
   if (relax) {
@@ -416,16 +537,7 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
     ctr.w = 1u;
     const uint4 w1 = philox(ctr, k0, k1);
     resample<R>(p, M, rec_relax, binf, w, w1, false, 2, R(1));
-    if (GRAD) {
-      if (gs->np < kMaxPeriods) {
-        gs->bin[gs->np] = p.bin;
-        gs->A[gs->np] = -1.0;
-        gs->B[gs->np] = -Xnow;
-        gs->np++;
-      }
-      gs->n_res++;
-      gs->sum_x_res += Xnow;
-    }
+    if (Grad::on) gr.resampled(p.bin, Xnow);
     return STEP_ALIVE;
   }
   p.d_rel = p.d_rel - seg;
@@ -460,11 +572,7 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
   ny = ny / len;
   const uint4 w = philox(ctr, k0, k1);
   const bool spec = (uint64_t)w.x < g.pthr_pore;
-  if (GRAD) {
-    const double sc = spec ? 1.0 / g.p_pore : -1.0 / (1.0 - g.p_pore);
-    gs->PA += sc;
-    gs->PB += sc * Xnow;
-  }
+  if (Grad::on) gr.pore_hit(spec, g.p_pore, Xnow);
   if (spec) {
     const R un = p.u[0] * nx + p.u[1] * ny;
     p.u[0] = p.u[0] - (R(2) * un) * nx;
@@ -486,10 +594,10 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
 // remaining relaxation distance (boundary wins ties, Sec. 3.3 case iii),
 // track-length tallies of the flight (Eqs. temp_steady, flux_x_steady), then
 // the event.
-template <typename R, bool GRAD, class Tally, bool SPLIT = false>
+template <typename R, class Grad, class Tally, bool SPLIT = false>
 __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_relax,
                                            const float4* binf, const RunCfg& C, uint32_t k0, uint32_t k1,
-                                           const Tally& T, GradState* gs) {
+                                           const Tally& T, Grad& gr) {
   if (p.e + 1u >= C.max_events) return STEP_TRUNCATED;
   R db;
   int face;
@@ -497,18 +605,13 @@ __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, cons
   const bool relax = p.d_rel < db;
   const R seg = relax ? p.d_rel : db;
   double Xb = 0.0;
-  if (GRAD) Xb = T.X(p);
-  T.segment(p, seg);
-  if (GRAD) {
-    double score = (double)(seg / p.lam);
-    if (relax) score = score - 1.0;
-    gs->A[gs->np - 1] += score;
-    gs->B[gs->np - 1] += score * Xb;
-  }
+  if (Grad::on) Xb = T.X(p);
+  const auto c = T.segment(p, seg);
+  if (Grad::on) gr.flight(relax, (double)(seg / p.lam), Xb, c);
 #pragma unroll
   for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
-  return apply_event<R, GRAD, Tally, SPLIT>(p, g, M, rec_relax, binf, C, k0, k1, relax, face, seg, T, gs,
-                                            GRAD ? T.X(p) : 0.0);
+  return apply_event<R, Grad, Tally, SPLIT>(p, g, M, rec_relax, binf, C, k0, k1, relax, face, seg, T, gr,
+                                            Grad::on ? T.X(p) : 0.0);
 }
 
 // One flight + event of a transient particle: the flight also ends at
@@ -549,18 +652,28 @@ __device__ __forceinline__ int step_transient(Particle<R>& p, const GeoRun& g, c
     iz = min(max(iz, 0), nz - 1);
     const size_t c = ((size_t)p.mi * ncell + ((size_t)iz * ny + iy) * nx + ix) * 4;
     const R sv = p.s * v;
-    atomicAdd(&snap[c + 0], (double)p.s);
-    atomicAdd(&snap[c + 1], (double)(sv * p.u[0]));
-    atomicAdd(&snap[c + 2], (double)(sv * p.u[1]));
-    atomicAdd(&snap[c + 3], (double)(sv * p.u[2]));
+    if (sizeof(R) == 8) {
+      atomicAdd(&snap[c + 0], (double)p.s);
+      atomicAdd(&snap[c + 1], (double)(sv * p.u[0]));
+      atomicAdd(&snap[c + 2], (double)(sv * p.u[1]));
+      atomicAdd(&snap[c + 3], (double)(sv * p.u[2]));
+    } else {
+      // FP32 path: the signed count exactly, the flux in 2^-20 nm/ps units
+      long long* q = reinterpret_cast<long long*>(snap) + c;
+      red_s64(q + 0, p.s > R(0) ? 1ll : -1ll);
+      red_s64(q + 1, fx((float)(sv * p.u[0])));
+      red_s64(q + 2, fx((float)(sv * p.u[1])));
+      red_s64(q + 3, fx((float)(sv * p.u[2])));
+    }
     ++p.mi;
   }
   p.t = t_end;
 #pragma unroll
   for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
   if (fin) return STEP_DONE;
-  return apply_event<R, false, TallyNone>(p, g, M, rec_relax, binf, C, k0, k1, relax, face, seg, TallyNone(), nullptr,
-                                          0.0);
+  GradOff off;
+  return apply_event<R, GradOff, TallyNone>(p, g, M, rec_relax, binf, C, k0, k1, relax, face, seg, TallyNone(), off,
+                                            0.0);
 }
 
 }  // namespace mcbte

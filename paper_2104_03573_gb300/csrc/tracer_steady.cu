@@ -28,39 +28,33 @@ __device__ __forceinline__ int find_geom(const uint64_t* offs, int G, uint64_t i
   return lo;
 }
 
-template <typename R>
-__device__ __forceinline__ void grad_init(GradState* gs, const Particle<R>& p) {
-  gs->np = 1;
-  gs->bin[0] = p.bin;
-  gs->A[0] = 0.0;
-  gs->B[0] = 0.0;
-  gs->n_res = 0;
-  gs->sum_x_res = 0.0;
-  gs->PA = 0.0;
-  gs->PB = 0.0;
-}
-
-// Likelihood-ratio contributions of a finished particle with tally X:
-// sum over its relaxation periods of (A X - B) into G[bin], the dense
-// resampling term R = n_res X - sum X_at_resample, the specularity score and
-// the probe directions.
-__device__ __forceinline__ void grad_finish(const GradState* gs, double X, int g, const RunCfg& C, const Acc& A,
+// Likelihood-ratio contributions of a finished particle with tally X: every
+// relaxation period's value into G[bin], the dense resampling term R, the
+// specularity score and the probe directions.
+template <class Grad>
+__device__ __forceinline__ void grad_finish(const Grad& gr, double X, int g, const RunCfg& C, const Acc& A,
                                             const MatView& M) {
-  for (int k = 0; k < gs->np; ++k) atomicAdd(&A.G[gs->bin[k]], gs->A[k] * X - gs->B[k]);
-  const double Rv = (double)gs->n_res * X - gs->sum_x_res;
+  const int np = gr.periods();
+  for (int k = 0; k < np; ++k) atomicAdd(&A.G[gr.period_bin(k)], gr.period_value(k, X));
+  const double Rv = gr.resample_term(X);
   atomicAdd(&A.dsc[g * 8 + 4], Rv);
-  const double gp = gs->PA * X - gs->PB;
+  const double gp = gr.spec_term(X);
   atomicAdd(&A.dsc[g * 8 + 5], gp);
   atomicAdd(&A.dsc[g * 8 + 6], gp * gp);
   for (int kd = 0; kd < C.n_dirs; ++kd) {
     const double* dd = C.dirs + (size_t)kd * M.n;
     double val = 0.0;
-    for (int k = 0; k < gs->np; ++k) val += (gs->A[k] * X - gs->B[k]) * dd[gs->bin[k]];
+    for (int k = 0; k < np; ++k) val += gr.period_value(k, X) * dd[gr.period_bin(k)];
     val += Rv * C.dpi[kd];
     atomicAdd(&A.dsum[kd * 2 + 0], val);
     atomicAdd(&A.dsum[kd * 2 + 1], val * val);
   }
 }
+
+template <bool GRAD, class On>
+struct GradPick { using type = On; };
+template <class On>
+struct GradPick<false, On> { using type = GradOff; };
 
 #if MCBTE_F64
 // ------------------------------------------------------------------ FP64 plain
@@ -77,8 +71,8 @@ __global__ void __launch_bounds__(256) k_steady_fp64(const GeoRun* __restrict__ 
   p.g = g;
   const uint2 key = run_key(C);
   emit<double>(p, G, M, M.rec_emit, M.rec_init, nullptr, key.x, key.y, false, 0.0);
-  GradState gs;
-  if (GRAD) grad_init(&gs, p);
+  typename GradPick<GRAD, GradList>::type gr;
+  if (GRAD) gr.init(p.bin);
   TallyPlain T;
   T.cP = CELLS ? A.cellP + (size_t)g * C.n_cells * 4 : nullptr;
   T.qb = C.per_bin ? A.qbin + (size_t)g * M.n : nullptr;
@@ -88,7 +82,8 @@ __global__ void __launch_bounds__(256) k_steady_fp64(const GeoRun* __restrict__ 
   T.h = CELLS ? G.L[C.cell_axis] / (double)C.n_cells : 1.0;
   int out;
   for (;;) {
-    out = step_steady<double, GRAD, TallyPlain>(p, G, M, M.rec_relax, nullptr, C, key.x, key.y, T, &gs);
+    out = step_steady<double, typename GradPick<GRAD, GradList>::type, TallyPlain>(p, G, M, M.rec_relax, nullptr, C,
+                                                                                 key.x, key.y, T, gr);
     if (out != STEP_ALIVE) break;
     if ((p.e & 1023u) == 0u && globaltimer_ns() > deadline) {
       atomicOr(A.flags, 1);
@@ -111,7 +106,7 @@ __global__ void __launch_bounds__(256) k_steady_fp64(const GeoRun* __restrict__ 
   }
   if (A.events_pp) A.events_pp[idx] = (uint32_t)nev;
   if (A.X_pp) A.X_pp[idx] = p.X;
-  if (GRAD) grad_finish(&gs, p.X, g, C, A, M);
+  if (GRAD) grad_finish(gr, p.X, g, C, A, M);
 }
 #endif  // MCBTE_F64
 
@@ -198,7 +193,7 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
   const unsigned lane = threadIdx.x & 31u;
   const uint64_t deadline = *C.t0 + C.budget_ns;
   Particle<float> p;
-  GradState gs;
+  typename GradPick<GRAD, GradFast>::type gr;
   ThreadAcct acct;
   acct.reset(-1);
   TallyFx T;
@@ -234,7 +229,7 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
         p.pid = (uint32_t)(idx - offs[g]);
         p.g = g;
         emit<float>(p, *G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, false, 0.0f);
-        if (GRAD) grad_init(&gs, p);
+        if (GRAD) gr.init(p.bin);
         if (CELLS) {
           T.cP = S.cells_in_smem ? s_cP : A.cellPq + (size_t)g * nc * 4;
           T.cD = S.cells_in_smem ? s_cD : A.cellDq + (size_t)g * (nc + 1) * 4;
@@ -246,7 +241,8 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
       }
     }
     if (!alive) continue;
-    int out = step_steady<float, GRAD, TallyFx>(p, *G, M, relax, binf, C, key.x, key.y, T, &gs);
+    int out = step_steady<float, typename GradPick<GRAD, GradFast>::type, TallyFx>(p, *G, M, relax, binf, C, key.x,
+                                                                                  key.y, T, gr);
     if (out == STEP_ALIVE && (p.e & 255u) == 0u && globaltimer_ns() > deadline) {
       atomicOr(A.flags, 1);
       out = STEP_TRUNCATED;
@@ -269,7 +265,7 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
       }
       if (A.events_pp) A.events_pp[idx] = nev;
       if (A.X_pp) A.X_pp[idx] = X;
-      if (GRAD) grad_finish(&gs, X, p.g, C, A, M);
+      if (GRAD) grad_finish(gr, X, p.g, C, A, M);
       alive = false;
     }
   }

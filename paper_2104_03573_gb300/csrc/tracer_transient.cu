@@ -125,8 +125,10 @@ __global__ void __launch_bounds__(512) k_transient_f32(const GeoRun* __restrict_
 #endif  // MCBTE_F32
 #if MCBTE_F64
 // Scale the raw snapshot sums: T = s E_eff / (C V_cell), q = s E_eff V_g / V_cell.
+// `fixed`: the sums are the FP32 path's integers (signed count; flux in
+// 2^-20 nm/ps units), converted here in place.
 __global__ void k_finalize_transient(const GeoRun* geos, MatView M, RunCfg C, Acc A, double* tally, double* stats,
-                                     size_t n_cells_total) {
+                                     size_t n_cells_total, int fixed) {
   const GeoRun& G = geos[0];
   const double E_eff = G.E_tot / (double)G.n;
   const double Vc = G.V_box / (double)((size_t)C.grid[0] * C.grid[1] * C.grid[2]);
@@ -136,7 +138,19 @@ __global__ void k_finalize_transient(const GeoRun* geos, MatView M, RunCfg C, Ac
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
     const double* r = A.snap + i * 4;
     double* o = tally + i * 4;
-    const double a0 = r[0], a1 = r[1], a2 = r[2], a3 = r[3];
+    double a0, a1, a2, a3;
+    if (fixed) {
+      const long long* q = reinterpret_cast<const long long*>(r);
+      a0 = (double)q[0];
+      a1 = (double)q[1] * kFxInv;
+      a2 = (double)q[2] * kFxInv;
+      a3 = (double)q[3] * kFxInv;
+    } else {
+      a0 = r[0];
+      a1 = r[1];
+      a2 = r[2];
+      a3 = r[3];
+    }
     o[0] = kT * a0;
     o[1] = (kq * a1) * 1e3;
     o[2] = (kq * a2) * 1e3;
@@ -191,8 +205,9 @@ cudaError_t launch_transient_f32(const GeoRun* geos, const MatView& M, const Run
 #endif  // MCBTE_F32
 #if MCBTE_F64
 cudaError_t launch_finalize_transient(const GeoRun* geos, const MatView& M, const RunCfg& C, const Acc& A,
-                                      double* tally, double* stats, size_t n_cells_total, cudaStream_t s) {
-  k_finalize_transient<<<sm_count() * 4, 256, 0, s>>>(geos, M, C, A, tally, stats, n_cells_total);
+                                      double* tally, double* stats, size_t n_cells_total, bool fixed,
+                                      cudaStream_t s) {
+  k_finalize_transient<<<sm_count() * 4, 256, 0, s>>>(geos, M, C, A, tally, stats, n_cells_total, fixed ? 1 : 0);
   return cudaGetLastError();
 }
 

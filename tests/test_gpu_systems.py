@@ -160,3 +160,61 @@ def test_autograd_gradient_matches_crn_central_differences():
     fd = (kp - km) / (2 * h)
     fd_se = ((xp - xm) / (2 * h)).std(ddof=1) * math.sqrt(n)
     assert abs(gp[0] - fd) < 4 * math.hypot(gp[1], fd_se), (gp, fd, fd_se)
+
+
+def _timing_events(record=True):
+    evs = tuple(torch.cuda.Event(enable_timing=True) for _ in range(2))
+    if record:               # torch only reports elapsed time for events it recorded itself
+        for e in evs:
+            e.record()
+        torch.cuda.synchronize()
+    return evs
+
+
+def _outer_ms(fn):
+    a, b = _timing_events(record=False)
+    a.record()
+    fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def test_trace_events_time_the_kernel_eagerly_and_in_graph_replays():
+    wl = W.film_batch_c4(n_films=4)
+    M = api.Material(wl.material)
+    Gs = [api.Geometry(g) for g in wl.geometries]
+    ns = [20_000] * len(Gs)
+    evs = _timing_events()
+    cfg = api.SteadyConfig(seed=5, precision=L.FP32_TRACE, tally_axis=1, per_bin=True, n_scat_max=10,
+                           max_events=5_000_000, trace_events=evs)
+    out = api.run_steady(M, Gs, ns, cfg)
+    torch.cuda.synchronize()
+    t_eager = evs[0].elapsed_time(evs[1])
+    assert t_eager > 0.0
+    assert (out.stats[:, L.STAT_N].cpu().numpy() == np.array(ns)).all()
+
+    # events never recorded before the capture: the library must still get
+    # real handles, and every replay must re-record the pair around the kernel
+    gevs = _timing_events(record=False)
+    gb = batch.GraphBatch(M, Gs, ns, replace_cfg(cfg, trace_events=gevs), tune=False)
+    for seed in (11, 12):
+        for e in gevs:
+            e.record()
+        step = _outer_ms(lambda: gb.replay(seed=seed))
+        t = gevs[0].elapsed_time(gevs[1])
+        assert 0.5 * step < t <= step, (t, step)
+
+    wt = W.transient_box_c3(n=200_000)
+    tevs = _timing_events()
+    tr = wt.run
+    tcfg = api.TransientConfig(seed=tr.seed, precision=L.FP32_TRACE, t_max=tr.t_max, t_meas=tr.t_meas,
+                               grid=tr.grid, trace_events=tevs)
+    api.run_transient(api.Material(wt.material), api.Geometry(wt.geometries[0]), tr.n, tcfg)
+    torch.cuda.synchronize()
+    assert tevs[0].elapsed_time(tevs[1]) > 0.0
+
+
+def replace_cfg(cfg, **kw):
+    from dataclasses import replace
+    return replace(cfg, **kw)
