@@ -36,6 +36,10 @@ extern "C" {
 
 typedef struct CUstream_st* mcbte_stream; /* == cudaStream_t */
 
+/* Largest number of transient measurement times: the FP32 tracer keeps them
+ * in shared memory (4 bytes each). */
+#define MCBTE_MAX_TIMES 16384
+
 typedef enum {
   MCBTE_OK = 0,
   MCBTE_ERR_INVALID_ARG = 1,   /* a descriptor or parameter is out of range  */
@@ -44,7 +48,9 @@ typedef enum {
   MCBTE_ERR_TIMEOUT = 4,       /* the run hit its wall-clock budget          */
   MCBTE_WARN_TRUNCATED = 5,    /* some particles hit max_events (results are
                                   written; the truncated count is in stats)  */
-  MCBTE_ERR_WORKSPACE = 6      /* caller workspace smaller than required     */
+  MCBTE_ERR_WORKSPACE = 6,     /* caller workspace smaller than required     */
+  MCBTE_ERR_REPLAY = 7         /* FP32 gradient pass did not reproduce a
+                                  particle of the forward pass (internal)    */
 } mcbte_status;
 
 /* Message of the last failure on this host thread; returns its length.
@@ -232,10 +238,10 @@ typedef struct {
   int precision;
   uint64_t max_events;
   double t_max;                /* s, end of the simulated interval (Sec. 3.5.6)          */
-  int n_times;                 /* measurement times (Sec. 3.4)                           */
+  int n_times;                 /* measurement times (Sec. 3.4), 1..MCBTE_MAX_TIMES       */
   const double* t_meas;        /* HOST [n_times] s, ascending, in (0, t_max]             */
   int grid[3];                 /* nx, ny, nz detector cells over the box                 */
-  int threads_per_block;
+  int threads_per_block;        /* 0 (default 512), 256, 512, 768 or 1024 (FP32 path)     */
   int blocks_per_sm;
   double time_budget_s;
   void* trace_event_start;     /* optional cudaEvent_t pair around the tracing kernel     */
@@ -278,7 +284,13 @@ typedef struct {
  * the resampling law ~ C/tau of Eq. n_scatt (-delta_ij + pi_j) and the
  * specular / diffuse draw of Sec. 3.5.3 (1/p, -1/(1-p)); each score
  * multiplies the tally still to come.  The paper itself has no gradient.
- * Requires 1 <= n_scat_max <= 64. */
+ * FP64_PLAIN keeps each particle's relaxation periods and requires
+ * 1 <= n_scat_max <= 64.  FP32_TRACE runs two passes: the forward run, which
+ * records every particle's final tally, then a pass that replays the same
+ * particles (same random words) and adds each period's term as it closes;
+ * it requires n_scat_max >= 1, needs 8 more workspace bytes per particle,
+ * and returns MCBTE_ERR_REPLAY in the status statistic should a replayed
+ * tally differ from the recorded one. */
 mcbte_status mcbte_grad(const mcbte_material* m, const mcbte_geometry* g, const mcbte_steady_params* p,
                         const mcbte_steady_out* fwd, const mcbte_grad_out* grad,
                         void* workspace, size_t workspace_bytes, mcbte_stream stream);

@@ -9,7 +9,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmcbte.so")
 
-OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, WARN_TRUNCATED, ERR_WORKSPACE = range(7)
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, WARN_TRUNCATED, ERR_WORKSPACE, ERR_REPLAY = range(8)
 FACE_ISOTHERMAL, FACE_ADIABATIC, FACE_PERIODIC = 0, 1, 2
 FP64_PLAIN, FP32_TRACE = 0, 1
 (STAT_KAPPA, STAT_KAPPA_SE, STAT_Q_MEAN, STAT_Q_SE, STAT_SUMX, STAT_SUMX2, STAT_EVENTS, STAT_TRUNCATED,

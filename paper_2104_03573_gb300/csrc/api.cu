@@ -291,6 +291,7 @@ struct SteadyWs {
   double* dsc;
   unsigned long long* cnt;
   double* G;
+  long long* Gq;
   double* dsum;
   unsigned long long* work;
   int* flags;
@@ -303,11 +304,12 @@ struct SteadyWs {
   uint32_t* events_pp;
   double* X_pp;
   double *dk, *dkp, *dkdir;
+  double* xrep;   // FP32 gradient: final tally of every particle (forward -> replay)
   size_t bytes;
 };
 
-SteadyWs layout_steady(char* base, int G, int n, int nc, uint64_t total, bool grad, int nd, bool host_out,
-                       bool want_ev, bool want_x, bool want_T, bool want_q, bool want_qbin) {
+SteadyWs layout_steady(char* base, int G, int n, int nc, uint64_t total, bool grad, bool replay, int nd,
+                       bool host_out, bool want_ev, bool want_x, bool want_T, bool want_q, bool want_qbin) {
   Carve c;
   c.base = base;
   SteadyWs w{};
@@ -324,6 +326,7 @@ SteadyWs layout_steady(char* base, int G, int n, int nc, uint64_t total, bool gr
   w.dsc = c.take<double>((size_t)G * 8);
   w.cnt = c.take<unsigned long long>((size_t)G * 4);
   w.G = grad ? c.take<double>(n) : nullptr;
+  w.Gq = grad ? c.take<long long>(n) : nullptr;
   w.dsum = grad ? c.take<double>(2 * (size_t)(nd > 0 ? nd : 1)) : nullptr;
   w.work = c.take<unsigned long long>(1);
   w.flags = c.take<int>(2);
@@ -332,6 +335,7 @@ SteadyWs layout_steady(char* base, int G, int n, int nc, uint64_t total, bool gr
   w.zero_end = base ? base + c.off : nullptr;
   w.dirs = (grad && nd > 0) ? c.take<double>((size_t)nd * n) : nullptr;
   w.dpi = (grad && nd > 0) ? c.take<double>(nd) : nullptr;
+  w.xrep = replay ? c.take<double>(total) : nullptr;
   if (host_out) {
     w.T = (want_T && nc > 0) ? c.take<double>((size_t)G * nc) : nullptr;
     w.q = (want_q && nc > 0) ? c.take<double>((size_t)G * nc * 3) : nullptr;
@@ -392,8 +396,9 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   const int nd = grad ? gout->n_dirs : 0;
   if (grad) {
     if (G != 1) return fail(MCBTE_ERR_INVALID_ARG, "grad: one geometry");
-    if (p->n_scat_max < 1 || p->n_scat_max > kMaxPeriods - 1)
-      return fail(MCBTE_ERR_INVALID_ARG, "grad: n_scat_max must be in [1, 64]");
+    if (p->n_scat_max < 1) return fail(MCBTE_ERR_INVALID_ARG, "grad: n_scat_max must be >= 1");
+    if (p->precision == MCBTE_FP64_PLAIN && p->n_scat_max > kMaxPeriods - 1)
+      return fail(MCBTE_ERR_INVALID_ARG, "grad: FP64 n_scat_max must be in [1, 64]");
     if (nd < 0 || nd > kMaxDirs || (nd > 0 && !gout->dirs))
       return fail(MCBTE_ERR_INVALID_ARG, "grad: n_dirs in [0, 16] with dirs");
     if (!gout->dkappa_dlogtau || !gout->dkappa_dp || (nd > 0 && !gout->dkappa_dir))
@@ -401,8 +406,9 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
     if (gout->on_host != out->on_host) return fail(MCBTE_ERR_INVALID_ARG, "grad: on_host must match");
   }
   const bool host_out = out->on_host != 0;
-  SteadyWs w = layout_steady(nullptr, G, n, nc, total, grad, nd, host_out, out->events_pp, out->X_pp, out->T, out->q,
-                             out->q_bin);
+  const bool replay = grad && p->precision == MCBTE_FP32_TRACE;
+  SteadyWs w = layout_steady(nullptr, G, n, nc, total, grad, replay, nd, host_out, out->events_pp, out->X_pp, out->T,
+                             out->q, out->q_bin);
   const size_t need = w.bytes;
   char* base = static_cast<char*>(workspace);
   bool own = false;
@@ -413,7 +419,7 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
     return fail(MCBTE_ERR_WORKSPACE, "run_steady: workspace too small");
   }
   char* aligned = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(base) + 255) & ~(uintptr_t)255);
-  w = layout_steady(aligned, G, n, nc, total, grad, nd, host_out, out->events_pp, out->X_pp, out->T, out->q,
+  w = layout_steady(aligned, G, n, nc, total, grad, replay, nd, host_out, out->events_pp, out->X_pp, out->T, out->q,
                     out->q_bin);
   auto release = [&]() {
     if (own) cudaFreeAsync(base, s);
@@ -459,6 +465,7 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   A.dsc = w.dsc;
   A.cnt = w.cnt;
   A.G = w.G;
+  A.Gq = w.Gq;
   A.dsum = w.dsum;
   A.work = w.work;
   A.flags = w.flags;
@@ -473,7 +480,24 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
     C.dpi = w.dpi;
   }
   if (p->trace_event_start) RUN_TRY(record_trace_event(p->trace_event_start, s));
-  RUN_TRY(launch_steady(p->precision, grad, w.geos, w.offs, m->view, C, A, p->threads_per_block, p->blocks_per_sm, s));
+  if (replay) {
+    // forward pass (all tallies, every particle's final X), then the
+    // gradient pass over the same particles
+    Acc A1 = A;
+    A1.X_pp = w.xrep;
+    RUN_TRY(launch_steady(p->precision, false, w.geos, w.offs, m->view, C, A1, p->threads_per_block,
+                          p->blocks_per_sm, s));
+    RUN_TRY(cudaMemsetAsync(w.work, 0, sizeof(unsigned long long), s));
+    Acc A2 = A;
+    A2.X_pp = w.xrep;
+    A2.events_pp = nullptr;
+    RUN_TRY(launch_steady(p->precision, true, w.geos, w.offs, m->view, C, A2, p->threads_per_block,
+                          p->blocks_per_sm, s));
+    if (A.X_pp) RUN_TRY(cudaMemcpyAsync(A.X_pp, w.xrep, total * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else {
+    RUN_TRY(launch_steady(p->precision, grad, w.geos, w.offs, m->view, C, A, p->threads_per_block, p->blocks_per_sm,
+                          s));
+  }
   if (p->trace_event_stop) RUN_TRY(record_trace_event(p->trace_event_stop, s));
   SteadyOutDev O{};
   O.T = host_out ? w.T : out->T;
@@ -529,8 +553,9 @@ mcbte_status mcbte_steady_workspace_size(const mcbte_material* m, const mcbte_ge
   mcbte_status st = check_steady(m, geoms, n_geoms, p, &total);
   if (st != MCBTE_OK) return st;
   if (!bytes) return fail(MCBTE_ERR_INVALID_ARG, "workspace_size: null bytes");
-  SteadyWs w = layout_steady(nullptr, n_geoms, m->n, p->n_cells, total, want_grad != 0, n_dirs, false, false, false,
-                             false, false, false);
+  SteadyWs w = layout_steady(nullptr, n_geoms, m->n, p->n_cells, total, want_grad != 0,
+                             want_grad != 0 && p->precision == MCBTE_FP32_TRACE, n_dirs, false, false, false, false,
+                             false, false);
   *bytes = w.bytes;
   return MCBTE_OK;
 }
@@ -604,14 +629,16 @@ mcbte_status check_transient(const mcbte_material* m, const mcbte_geometry* g, c
     return fail(MCBTE_ERR_INVALID_ARG, "run_transient: precision");
   if (!finite_pos(p->t_max)) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: t_max must be > 0");
   if (p->n_times < 1 || !p->t_meas) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: t_meas required");
+  if (p->n_times > MCBTE_MAX_TIMES) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: n_times above MCBTE_MAX_TIMES");
   for (int k = 0; k < p->n_times; ++k) {
     if (!(p->t_meas[k] > 0.0 && p->t_meas[k] <= p->t_max)) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: t_meas in (0, t_max]");
     if (k > 0 && !(p->t_meas[k] > p->t_meas[k - 1])) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: t_meas ascending");
   }
   for (int a = 0; a < 3; ++a)
     if (p->grid[a] < 1 || p->grid[a] > 4096) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: grid in [1, 4096]");
-  if (p->threads_per_block < 0 || p->threads_per_block > 512 || (p->threads_per_block % 32) != 0)
-    return fail(MCBTE_ERR_INVALID_ARG, "run_transient: threads_per_block must be a multiple of 32 up to 512");
+  if (p->threads_per_block != 0 && p->threads_per_block != 256 && p->threads_per_block != 512 &&
+      p->threads_per_block != 768 && p->threads_per_block != 1024)
+    return fail(MCBTE_ERR_INVALID_ARG, "run_transient: threads_per_block must be 0, 256, 512, 768 or 1024");
   const mcbte_geometry_desc& d = g->host;
   if (has_gradient(d)) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: body (gradient) sources are steady only");
   if (!d.gauss && !has_isothermal_source(d)) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: no source");
@@ -749,8 +776,8 @@ mcbte_status mcbte_run_steady_noalloc(const mcbte_material* m, const mcbte_geome
   uint64_t total = 0;
   mcbte_status st = check_steady(m, geoms, n_geoms, p, &total);
   if (st != MCBTE_OK) return st;
-  const SteadyWs w = layout_steady(nullptr, n_geoms, m->n, p->n_cells, total, false, 0, false, false, false, false,
-                                   false, false);
+  const SteadyWs w = layout_steady(nullptr, n_geoms, m->n, p->n_cells, total, false, false, 0, false, false, false,
+                                   false, false, false);
   if (w.bytes > kNoAllocScratchBytes)
     return fail(MCBTE_ERR_WORKSPACE, "run_steady_noalloc: this run needs " + std::to_string(w.bytes) +
                                          " bytes of scratch, above the fixed " +

@@ -57,7 +57,8 @@ struct Acc {
   long long* qbinq;           // [G][n_bins]
   double* dsc;                // [G][8]: sumX, sumX2, signed emitted, signed absorbed, R, Gp, Gp^2, absorbed
   unsigned long long* cnt;    // [G][4]: events, truncated, max events, traced
-  double* G;                  // [n_bins] sparse part of the LR gradient
+  double* G;                  // [n_bins] sparse part of the LR gradient (FP64 path)
+  long long* Gq;              // [n_bins] its fixed-point counterpart (FP32 gradient pass)
   double* dsum;               // [n_dirs][2]
   double* snap;               // [n_times][cells][4] transient
   uint32_t* events_pp;        // [total] or null
@@ -448,41 +449,44 @@ struct GradList {
   __device__ __forceinline__ double spec_term(double X) const { return PA * X - PB; }
 };
 
-// FP32 path: the current period lives in registers as (a, d) with
-// d = a X - b, which a flight with tally increment c advances by a c (after
-// adding its score to a); completed periods are written once each.  The
-// specularity score uses the same form, so its value needs no list.
-struct GradFast {
+// FP32 path, second pass.  The forward pass stored every particle's final
+// tally X_f; this pass traces the same particle again (same random words,
+// same fixed-point tally, so the same trajectory) and adds each relaxation
+// period's term A_k X_f - B_k = a (X_f - X_end) + d to the gradient the moment
+// the period closes.  Nothing is stored per period: a is the period's score
+// sum, d the running sum of (score so far) x (segment tally) (FP32 registers).
+struct GradReplay {
   static constexpr bool on = true;
-  int np;
-  int bin[kMaxPeriods];
-  float A[kMaxPeriods];
-  double B[kMaxPeriods];
+  double Xf;
+  long long* G;         // [n_bins] gradient accumulator (global, 2^-20 fixed point: order-free sums)
   int bin_cur;
   float a, d;
   float pa, pd;
   int n_res;
   double sum_x_res;
+  int n_dirs, n_bins;
+  const double* dirs;
+  double dv[kMaxDirs];  // per direction: sum over closed periods of value x dirs[bin]
 
   __device__ __forceinline__ void init(int b) {
-    np = 0;
     bin_cur = b;
     a = d = pa = pd = 0.0f;
     n_res = 0;
     sum_x_res = 0.0;
+    for (int k = 0; k < n_dirs; ++k) dv[k] = 0.0;
   }
   __device__ __forceinline__ void flight(bool relax, double ratio, double, float c) {
     a += (float)ratio - (relax ? 1.0f : 0.0f);
     d = fmaf(a, c, d);
     pd = fmaf(pa, c, pd);
   }
+  __device__ __forceinline__ void close_period(double Xnow) {
+    const double val = (double)a * (Xf - Xnow) + (double)d;
+    red_s64(&G[bin_cur], __double2ll_rn(val * kFx));
+    for (int k = 0; k < n_dirs; ++k) dv[k] += val * dirs[(size_t)k * n_bins + bin_cur];
+  }
   __device__ __forceinline__ void resampled(int b, double Xnow) {
-    if (np < kMaxPeriods) {
-      bin[np] = bin_cur;
-      A[np] = a;
-      B[np] = (double)a * Xnow - (double)d;
-      np++;
-    }
+    close_period(Xnow);
     bin_cur = b;
     a = -1.0f;
     d = 0.0f;
@@ -492,12 +496,6 @@ struct GradFast {
   __device__ __forceinline__ void pore_hit(bool spec, double p, double) {
     pa += spec ? (float)(1.0 / p) : (float)(-1.0 / (1.0 - p));
   }
-  // periods 0..np-1 are completed; index np is the current one
-  __device__ __forceinline__ double period_value(int k, double X) const {
-    return k < np ? (double)A[k] * X - B[k] : (double)d;
-  }
-  __device__ __forceinline__ int periods() const { return np + 1; }
-  __device__ __forceinline__ int period_bin(int k) const { return k < np ? bin[k] : bin_cur; }
   __device__ __forceinline__ double resample_term(double X) const { return (double)n_res * X - sum_x_res; }
   __device__ __forceinline__ double spec_term(double) const { return (double)pd; }
 };
@@ -618,10 +616,14 @@ __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, cons
 // t_max (Sec. 3.5.6); every measurement time t_m inside the flight's
 // interval [t, t_end) (closed at t_max) adds the particle's snapshot to its
 // detector cell (Eq. sampling, Sec. 3.4).
+// `tmeas`: the measurement times in ps (FP64 path: the global array; FP32
+// path: a float copy in shared memory).  `cinv`: cells per nm along x, y, z
+// (FP32 path only; the FP64 path divides by the cell size, the CPU reference form).
 template <typename R>
 __device__ __forceinline__ int step_transient(Particle<R>& p, const GeoRun& g, const MatView& M,
                                               const uint4* rec_relax, const float4* binf, const RunCfg& C,
-                                              uint32_t k0, uint32_t k1, double* snap) {
+                                              uint32_t k0, uint32_t k1, double* snap, const R* tmeas,
+                                              const R* cinv) {
   if (p.e + 1u >= C.max_events) return STEP_TRUNCATED;
   R db;
   int face;
@@ -638,15 +640,22 @@ __device__ __forceinline__ int step_transient(Particle<R>& p, const GeoRun& g, c
   const int nx = C.grid[0], ny = C.grid[1], nz = C.grid[2];
   const size_t ncell = (size_t)nx * ny * nz;
   while (p.mi < C.n_times) {
-    const R tm = (R)C.t_meas_ps[p.mi];
+    const R tm = tmeas[p.mi];
     if (!(tm < t_end || (fin && tm <= t_end))) break;
     const R dist = v * (tm - p.t);
     R pm[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) pm[a] = p.x[a] + dist * p.u[a];
-    int ix = (int)floor((double)(pm[0] / (geo_L<R>(g, 0) / (R)nx)));
-    int iy = (int)floor((double)(pm[1] / (geo_L<R>(g, 1) / (R)ny)));
-    int iz = (int)floor((double)(pm[2] / (geo_L<R>(g, 2) / (R)nz)));
+    int ix, iy, iz;
+    if constexpr (sizeof(R) == 8) {
+      ix = (int)floor(pm[0] / (geo_L<R>(g, 0) / (R)nx));
+      iy = (int)floor(pm[1] / (geo_L<R>(g, 1) / (R)ny));
+      iz = (int)floor(pm[2] / (geo_L<R>(g, 2) / (R)nz));
+    } else {
+      ix = (int)floorf(pm[0] * cinv[0]);
+      iy = (int)floorf(pm[1] * cinv[1]);
+      iz = (int)floorf(pm[2] * cinv[2]);
+    }
     ix = min(max(ix, 0), nx - 1);
     iy = min(max(iy, 0), ny - 1);
     iz = min(max(iz, 0), nz - 1);

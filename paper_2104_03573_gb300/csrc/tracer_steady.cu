@@ -147,12 +147,31 @@ struct ThreadAcct {
   }
 };
 
+// Gradient pass: the open period closes at the particle's end (X = X_f),
+// then the resampling and specularity terms and the directional values.
+__device__ __forceinline__ void grad_finish_replay(GradReplay& gr, double X, int g, const RunCfg& C, const Acc& A) {
+  gr.close_period(X);
+  const double Rv = gr.resample_term(X);
+  atomicAdd(&A.dsc[g * 8 + 4], Rv);
+  const double gp = gr.spec_term(X);
+  atomicAdd(&A.dsc[g * 8 + 5], gp);
+  atomicAdd(&A.dsc[g * 8 + 6], gp * gp);
+  for (int kd = 0; kd < C.n_dirs; ++kd) {
+    const double val = gr.dv[kd] + Rv * C.dpi[kd];
+    atomicAdd(&A.dsum[kd * 2 + 0], val);
+    atomicAdd(&A.dsum[kd * 2 + 1], val * val);
+  }
+}
+
 // Every lane owns one particle at a time.  When its particle terminates the
 // lane refills from a global work counter; the refills of a warp are
 // aggregated into one atomicAdd (ballot of the empty lanes, leader adds the
 // popcount, lanes take consecutive indices).  Lanes therefore never idle
 // while work remains, whatever the event-count spread between particles.
 // TPB is the block size the kernel is compiled for (register budget).
+// GRAD: the gradient pass, which replays the forward pass's particles with
+// their final tallies read from A.X_pp; it writes the gradient accumulators
+// only, and flags (bit 2) any particle whose replayed tally differs.
 template <bool CELLS, bool GRAD, int TPB>
 __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict__ geos,
                                                        const uint64_t* __restrict__ offs, MatView M, RunCfg C,
@@ -193,7 +212,13 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
   const unsigned lane = threadIdx.x & 31u;
   const uint64_t deadline = *C.t0 + C.budget_ns;
   Particle<float> p;
-  typename GradPick<GRAD, GradFast>::type gr;
+  typename GradPick<GRAD, GradReplay>::type gr;
+  if constexpr (GRAD) {
+    gr.G = A.Gq;
+    gr.n_dirs = C.n_dirs;
+    gr.n_bins = n;
+    gr.dirs = C.dirs;
+  }
   ThreadAcct acct;
   acct.reset(-1);
   TallyFx T;
@@ -229,25 +254,35 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
         p.pid = (uint32_t)(idx - offs[g]);
         p.g = g;
         emit<float>(p, *G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, false, 0.0f);
-        if (GRAD) gr.init(p.bin);
+        if constexpr (GRAD) {
+          gr.init(p.bin);
+          gr.Xf = A.X_pp[idx];
+        }
         if (CELLS) {
           T.cP = S.cells_in_smem ? s_cP : A.cellPq + (size_t)g * nc * 4;
           T.cD = S.cells_in_smem ? s_cD : A.cellDq + (size_t)g * (nc + 1) * 4;
           T.h = G->Lf[C.cell_axis] / (float)nc;
           T.inv_h = (float)nc / G->Lf[C.cell_axis];
         }
-        T.qb = C.per_bin ? (S.qbin_in_smem ? s_qbin : A.qbinq + (size_t)g * n) : nullptr;
+        T.qb = (C.per_bin && !GRAD) ? (S.qbin_in_smem ? s_qbin : A.qbinq + (size_t)g * n) : nullptr;
         alive = true;
       }
     }
     if (!alive) continue;
-    int out = step_steady<float, typename GradPick<GRAD, GradFast>::type, TallyFx>(p, *G, M, relax, binf, C, key.x,
+    int out = step_steady<float, typename GradPick<GRAD, GradReplay>::type, TallyFx>(p, *G, M, relax, binf, C, key.x,
                                                                                   key.y, T, gr);
     if (out == STEP_ALIVE && (p.e & 255u) == 0u && globaltimer_ns() > deadline) {
       atomicOr(A.flags, 1);
       out = STEP_TRUNCATED;
     }
-    if (out != STEP_ALIVE) {
+    if (GRAD && out != STEP_ALIVE) {
+      const double X = T.X(p);
+      if constexpr (GRAD) {
+        if (X != gr.Xf) atomicOr(A.flags, 4);
+        grad_finish_replay(gr, X, p.g, C, A);
+      }
+      alive = false;
+    } else if (out != STEP_ALIVE) {
       T.period_end(p);
       const double X = T.X(p);
       const unsigned nev = p.e + 1u;
@@ -265,11 +300,10 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
       }
       if (A.events_pp) A.events_pp[idx] = nev;
       if (A.X_pp) A.X_pp[idx] = X;
-      if (GRAD) grad_finish(gr, X, p.g, C, A, M);
       alive = false;
     }
   }
-  acct.flush(A);
+  if (!GRAD) acct.flush(A);
   __syncthreads();
   if (S.qbin_in_smem) {
     for (int i = threadIdx.x; i < n; i += blockDim.x)
@@ -349,15 +383,16 @@ __global__ void k_finalize_steady(const GeoRun* geos, MatView M, RunCfg C, Acc A
     st[MCBTE_STAT_KAPPA_CELL] = (-q_mean / G.kappa_grad) * (G.V_solid / G.V_box);
     st[MCBTE_STAT_SIGNED_EMITTED] = A.dsc[g * 8 + 2];
     st[MCBTE_STAT_SIGNED_ABSORBED] = A.dsc[g * 8 + 3];
-    st[MCBTE_STAT_STATUS] = (flags[0] & 1) ? (double)MCBTE_ERR_TIMEOUT
-                                           : (A.cnt[g * 4 + 1] ? (double)MCBTE_WARN_TRUNCATED : 0.0);
+    st[MCBTE_STAT_STATUS] = (flags[0] & 4)   ? (double)MCBTE_ERR_REPLAY
+                            : (flags[0] & 1) ? (double)MCBTE_ERR_TIMEOUT
+                                             : (A.cnt[g * 4 + 1] ? (double)MCBTE_WARN_TRUNCATED : 0.0);
     st[MCBTE_STAT_N] = nt;
     st[MCBTE_STAT_ABSORBED] = A.dsc[g * 8 + 7];
   }
   if (grad && g == 0) {
     const double scale = -(E_eff / G.V_solid) * 1e-9 / G.kappa_grad;
     const double Rs = A.dsc[4];
-    for (int i = threadIdx.x; i < n; i += blockDim.x) O.dk[i] = scale * (A.G[i] + Rs * M.pi[i]);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) O.dk[i] = scale * ((A.G[i] + (double)A.Gq[i] * kFxInv) + Rs * M.pi[i]);
     if (threadIdx.x == 0) {
       const double nt = (double)A.cnt[3];
       const double gm = A.dsc[5] / nt;
@@ -397,7 +432,7 @@ cudaError_t launch_f64(const GeoRun* geos, const uint64_t* offs, const MatView& 
 template <bool CELLS, bool GRAD, int TPB>
 cudaError_t launch_f32_tpb(const GeoRun* geos, const uint64_t* offs, const MatView& M, const RunCfg& C,
                            const Acc& A, int bps, cudaStream_t s) {
-  const SmemPlan S = plan_smem_f32(M.n, C.n_geoms, C.n_cells, C.per_bin, 200 * 1024);
+  const SmemPlan S = plan_smem_f32(M.n, C.n_geoms, GRAD ? 0 : C.n_cells, GRAD ? 0 : C.per_bin, 200 * 1024);
   auto kern = k_steady_f32<CELLS, GRAD, TPB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.bytes);
   if (e != cudaSuccess) return e;
@@ -487,9 +522,8 @@ cudaError_t launch_dirs_dot_pi(const double* dirs, int n_dirs, const MatView& M,
 #if MCBTE_F32
 cudaError_t launch_steady_f32(bool grad, bool cells, const GeoRun* geos, const uint64_t* offs, const MatView& M,
                               const RunCfg& C, const Acc& A, int threads, int bps, cudaStream_t s) {
-  if (grad)
-    return cells ? launch_f32<true, true>(geos, offs, M, C, A, threads, bps, s)
-                 : launch_f32<false, true>(geos, offs, M, C, A, threads, bps, s);
+  // the gradient pass keeps no cell or per-bin tallies
+  if (grad) return launch_f32<false, true>(geos, offs, M, C, A, threads, bps, s);
   return cells ? launch_f32<true, false>(geos, offs, M, C, A, threads, bps, s)
                : launch_f32<false, false>(geos, offs, M, C, A, threads, bps, s);
 }

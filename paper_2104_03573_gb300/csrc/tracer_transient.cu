@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) k_transient_fp64(const GeoRun* __restrict
   transient_start(p, C);
   int out;
   for (;;) {
-    out = step_transient<double>(p, G, M, M.rec_relax, nullptr, C, key.x, key.y, A.snap);
+    out = step_transient<double>(p, G, M, M.rec_relax, nullptr, C, key.x, key.y, A.snap, C.t_meas_ps, nullptr);
     if (out != STEP_ALIVE) break;
     if ((p.e & 1023u) == 0u && globaltimer_ns() > deadline) {
       atomicOr(A.flags, 1);
@@ -65,26 +65,35 @@ __global__ void __launch_bounds__(256) k_transient_fp64(const GeoRun* __restrict
 
 #endif  // MCBTE_F64
 #if MCBTE_F32
-__global__ void __launch_bounds__(512) k_transient_f32(const GeoRun* __restrict__ geos, MatView M, RunCfg C, Acc A,
-                                                       SmemPlan S) {
+// Shared memory: the measurement times as float (always), then the relaxation
+// alias records and per-bin constants where the plan has room.
+template <int TPB>
+__global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restrict__ geos, MatView M, RunCfg C,
+                                                          Acc A, SmemPlan S) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* sp = smem;
   const int n = M.n;
   const uint4* relax = M.rec_relax;
   const float4* binf = M.binf;
+  float* tmeas = reinterpret_cast<float*>(sp);
+  for (int i = threadIdx.x; i < C.n_times; i += TPB) tmeas[i] = (float)C.t_meas_ps[i];
+  sp += ((size_t)C.n_times * sizeof(float) + 15) & ~(size_t)15;
   if (S.relax_in_smem) {
     uint4* t = reinterpret_cast<uint4*>(sp);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) t[i] = M.rec_relax[i];
+    for (int i = threadIdx.x; i < n; i += TPB) t[i] = M.rec_relax[i];
     relax = t;
     sp += (size_t)n * sizeof(uint4);
   }
   if (S.binf_in_smem) {
     float4* t = reinterpret_cast<float4*>(sp);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) t[i] = M.binf[i];
+    for (int i = threadIdx.x; i < n; i += TPB) t[i] = M.binf[i];
     binf = t;
   }
   __syncthreads();
   const GeoRun& G = geos[0];
+  float cinv[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) cinv[a] = (float)((double)C.grid[a] / G.L[a]);
   const uint64_t deadline = *C.t0 + C.budget_ns;
   const unsigned lane = threadIdx.x & 31u;
   const uint2 key = run_key(C);
@@ -110,7 +119,7 @@ __global__ void __launch_bounds__(512) k_transient_f32(const GeoRun* __restrict_
         alive = true;
       }
     }
-    int out = step_transient<float>(p, G, M, relax, binf, C, key.x, key.y, A.snap);
+    int out = step_transient<float>(p, G, M, relax, binf, C, key.x, key.y, A.snap, tmeas, cinv);
     if (out == STEP_ALIVE && (p.e & 255u) == 0u && globaltimer_ns() > deadline) {
       atomicOr(A.flags, 1);
       out = STEP_TRUNCATED;
@@ -182,24 +191,40 @@ cudaError_t launch_transient(int precision, const GeoRun* geos, const MatView& M
     k_transient_fp64<<<(unsigned)blocks, 256, 0, s>>>(geos, M, C, A);
     return cudaGetLastError();
   }
-  return launch_transient_f32(geos, M, C, A, threads > 0 ? threads : 256, bps, s);
+  return launch_transient_f32(geos, M, C, A, threads > 0 ? threads : 512, bps, s);
 }
 
 #endif  // MCBTE_F64
 #if MCBTE_F32
-cudaError_t launch_transient_f32(const GeoRun* geos, const MatView& M, const RunCfg& C, const Acc& A, int threads,
-                                 int bps, cudaStream_t s) {
-  const SmemPlan S = plan_smem_f32(M.n, 1, 0, 0, 200 * 1024);
-  const int t = threads;
-  cudaError_t e = cudaFuncSetAttribute(k_transient_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.bytes);
+namespace {
+template <int TPB>
+cudaError_t launch_transient_tpb(const GeoRun* geos, const MatView& M, const RunCfg& C, const Acc& A, int bps,
+                                 cudaStream_t s) {
+  const size_t tm_bytes = ((size_t)C.n_times * sizeof(float) + 15) & ~(size_t)15;
+  SmemPlan S = plan_smem_f32(M.n, 1, 0, 0, 200 * 1024 - tm_bytes);
+  S.bytes += tm_bytes;
+  auto kern = k_transient_f32<TPB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.bytes);
   if (e != cudaSuccess) return e;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transient_f32, t, S.bytes);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TPB, S.bytes);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   const int b = (bps > 0 && bps < occ) ? bps : occ;
-  k_transient_f32<<<sm_count() * b, t, S.bytes, s>>>(geos, M, C, A, S);
+  kern<<<sm_count() * b, TPB, S.bytes, s>>>(geos, M, C, A, S);
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_transient_f32(const GeoRun* geos, const MatView& M, const RunCfg& C, const Acc& A, int threads,
+                                 int bps, cudaStream_t s) {
+  switch (threads) {
+    case 256: return launch_transient_tpb<256>(geos, M, C, A, bps, s);
+    case 512: return launch_transient_tpb<512>(geos, M, C, A, bps, s);
+    case 768: return launch_transient_tpb<768>(geos, M, C, A, bps, s);
+    case 1024: return launch_transient_tpb<1024>(geos, M, C, A, bps, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 #endif  // MCBTE_F32

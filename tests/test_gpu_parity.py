@@ -324,6 +324,7 @@ def test_fp32_gradient_directional_vs_oracle():
                            max_events=run.max_events, tally_axis=run.tally_axis, per_bin=True)
     fwd, go = api.grad(M, G, run.n, cfg, dirs=dirs)
     torch.cuda.synchronize()
+    assert fwd.stats[0, L.STAT_STATUS].item() == 0      # no replay mismatch, no truncation
     run.seed = 801
     ref = oracle.run_steady(mat, g, run, grad=True, dirs=dirs)
     gd = go.dkappa_dir[:2].cpu().numpy()
