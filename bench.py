@@ -263,7 +263,7 @@ def _workload_setup(name, args, seed_offset):
         mat, geo, run = wl.material, wl.geometries[0], wl.run
         M, G = api.Material(mat), api.Geometry(geo)
         cfg = api.TransientConfig(seed=run.seed + seed_offset, t_max=run.t_max, t_meas=run.t_meas, grid=run.grid,
-                                  precision=L.FP32_TRACE, threads_per_block=args.threads if args.threads in (0, 256, 512) else 0,
+                                  precision=L.FP32_TRACE, threads_per_block=args.threads if args.threads in (0, 256, 512, 768, 1024) else 0,
                                   trace_events=ev, time_budget_s=300)
         out = api.TransientOutputs(len(run.t_meas), run.grid, run.n)
 

@@ -510,8 +510,7 @@ __device__ __forceinline__ uint2 run_key(const RunCfg& C) {
 }
 
 // Outcome of one event step.
-// STEP_RESAMPLE: a relaxation whose resampling the caller performs.
-enum { STEP_ALIVE = 0, STEP_ABSORBED = 1, STEP_DONE = 2, STEP_TRUNCATED = 3, STEP_RESAMPLE = 4 };
+enum { STEP_ALIVE = 0, STEP_ABSORBED = 1, STEP_DONE = 2, STEP_TRUNCATED = 3 };
 
 // The event that ends a flight (Sec. 3.3 cases i/iii; Secs. 3.5.2-3.5.6):
 // relaxation (bin redrawn ~ C/tau, isotropic direction, new clock, sign
@@ -519,7 +518,7 @@ enum { STEP_ALIVE = 0, STEP_ABSORBED = 1, STEP_DONE = 2, STEP_TRUNCATED = 3, STE
 // to the opposite face; adiabatic / pore: specular with probability p, else
 // Lambertian about the inward normal).  The particle has already moved.
 // `Xnow` is the particle's tally so far (gradient bookkeeping only).
-template <typename R, class Grad, class Tally, bool SPLIT = false>
+template <typename R, class Grad, class Tally>
 __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_relax,
                                            const float4* binf, const RunCfg& C, uint32_t k0, uint32_t k1,
                                            bool relax, int face, R seg, const Tally& T, Grad& gr, double Xnow) {
@@ -530,7 +529,6 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
     if (C.n_scat_max > 0 && p.n_relax >= C.n_scat_max) return STEP_DONE;
     // the relaxation period in this bin is over: frequency-resolved flux
     T.period_end(p);
-    if (SPLIT) return STEP_RESAMPLE;
     const uint4 w = philox(ctr, k0, k1);
     ctr.w = 1u;
     const uint4 w1 = philox(ctr, k0, k1);
@@ -592,7 +590,7 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
 // remaining relaxation distance (boundary wins ties, Sec. 3.3 case iii),
 // track-length tallies of the flight (Eqs. temp_steady, flux_x_steady), then
 // the event.
-template <typename R, class Grad, class Tally, bool SPLIT = false>
+template <typename R, class Grad, class Tally>
 __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_relax,
                                            const float4* binf, const RunCfg& C, uint32_t k0, uint32_t k1,
                                            const Tally& T, Grad& gr) {
@@ -608,7 +606,7 @@ __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, cons
   if (Grad::on) gr.flight(relax, (double)(seg / p.lam), Xb, c);
 #pragma unroll
   for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
-  return apply_event<R, Grad, Tally, SPLIT>(p, g, M, rec_relax, binf, C, k0, k1, relax, face, seg, T, gr,
+  return apply_event<R, Grad, Tally>(p, g, M, rec_relax, binf, C, k0, k1, relax, face, seg, T, gr,
                                             Grad::on ? T.X(p) : 0.0);
 }
 

@@ -228,23 +228,30 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
   T.cP = T.cD = T.qb = nullptr;
   T.h = T.inv_h = 1.0f;
   bool alive = false;
+  bool drained = false;   // no work left for this lane: it idles in the loop until its warp is drained
   uint64_t idx = 0;
   const GeoRun* G = geos;
   const uint2 key = run_key(C);
   const int refill_min = C.refill_min > 1 ? C.refill_min : 1;
+  // All 32 lanes stay in the loop until every lane of the warp is drained, so
+  // the warp-wide votes below reconverge the warp at every event step.
+  constexpr unsigned kAll = 0xffffffffu;
   for (;;) {
-    const unsigned act = __activemask();
-    const unsigned need = __ballot_sync(act, !alive);
-    // refill once enough lanes are idle (or all of them are)
-    if (need && (__popc(need) >= refill_min || need == act)) {
+    if (__all_sync(kAll, drained)) break;
+    const unsigned need = __ballot_sync(kAll, !alive && !drained);
+    const unsigned live = __ballot_sync(kAll, alive);
+    // refill once enough lanes are idle (or no lane is busy)
+    if (need && (__popc(need) >= refill_min || live == 0u)) {
       const int leader = __ffs(need) - 1;
       unsigned long long base = 0;
       if ((int)lane == leader) base = atomicAdd(A.work, (unsigned long long)__popc(need));
-      base = __shfl_sync(act, base, leader);
-      if (!alive) {
+      base = __shfl_sync(kAll, base, leader);
+      if (!alive && !drained) {
         idx = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
-        if (idx >= C.total) break;
-        if (*(volatile int*)A.flags & 1) break;
+        if (idx >= C.total || (*(volatile int*)A.flags & 1)) {
+          drained = true;
+          continue;
+        }
         const int g = find_geom(offs, C.n_geoms, idx);
         if (g != acct.g) {
           acct.flush(A);

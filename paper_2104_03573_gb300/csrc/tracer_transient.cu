@@ -99,19 +99,23 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
   const uint2 key = run_key(C);
   Particle<float> p;
   bool alive = false;
+  bool drained = false;   // as in the steady tracer: idle lanes stay until the warp is drained
   uint64_t idx = 0;
+  constexpr unsigned kAll = 0xffffffffu;
   for (;;) {
-    const unsigned act = __activemask();
-    const unsigned need = __ballot_sync(act, !alive);
+    if (__all_sync(kAll, drained)) break;
+    const unsigned need = __ballot_sync(kAll, !alive && !drained);
     if (need) {
       const int leader = __ffs(need) - 1;
       unsigned long long base = 0;
       if ((int)lane == leader) base = atomicAdd(A.work, (unsigned long long)__popc(need));
-      base = __shfl_sync(act, base, leader);
-      if (!alive) {
+      base = __shfl_sync(kAll, base, leader);
+      if (!alive && !drained) {
         idx = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
-        if (idx >= C.total) break;
-        if (*(volatile int*)A.flags & 1) break;
+        if (idx >= C.total || (*(volatile int*)A.flags & 1)) {
+          drained = true;
+          continue;
+        }
         p.pid = (uint32_t)idx;
         p.g = 0;
         emit<float>(p, G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, true, (float)C.t_max_ps);
@@ -119,6 +123,7 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
         alive = true;
       }
     }
+    if (!alive) continue;
     int out = step_transient<float>(p, G, M, relax, binf, C, key.x, key.y, A.snap, tmeas, cinv);
     if (out == STEP_ALIVE && (p.e & 255u) == 0u && globaltimer_ns() > deadline) {
       atomicOr(A.flags, 1);
