@@ -312,7 +312,8 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", lrank))
     from paper_2104_03573_gb300 import build, _lib as L
     build.build()
-    wk = _workload_setup(args.workload, args, 1_000_003 * rank)
+    from paper_2104_03573_gb300 import shard
+    wk = _workload_setup(args.workload, args, shard.rank_key(0, rank))
     tm = wk["timer"]
     for _ in range(args.warmup):
         wk["step"]()()
@@ -333,13 +334,12 @@ def run_ours(args):
         assert np.all(st[:, L.STAT_STATUS] == 0), f"run status {st[:, L.STAT_STATUS]}"
     t_step = sum(step_ms) / len(step_ms) / 1e3
     ev_step = float(np.mean([st[:, L.STAT_EVENTS].sum() for st in stats]))
-    tot = torch.tensor([ev_step * args.steps, t_step * args.steps, wall], dtype=torch.float64, device="cuda")
+    total_events, t_ranks, wall_max = ev_step * args.steps, t_step * args.steps, wall
     if dist:
-        s = tot.clone()
-        dist.all_reduce(s[0:1], op=dist.ReduceOp.SUM)
-        dist.all_reduce(s[1:3], op=dist.ReduceOp.MAX)
-        tot = s
-    total_events, t_ranks, wall_max = (float(x) for x in tot.cpu())
+        # weak scaling: every rank's events count, the slowest rank sets the time
+        total_events = shard.sum_over_ranks(total_events)
+        t_ranks = shard.max_over_ranks(t_ranks)
+        wall_max = shard.max_over_ranks(wall_max)
     value = total_events / t_ranks
     st = stats[-1]
     kappa = kse = t_1pct = None
@@ -347,6 +347,9 @@ def run_ours(args):
         k = st[:, L.STAT_KAPPA]
         se = st[:, L.STAT_KAPPA_SE]
         kappa, kse = float(k[0]), float(se[0])
+        if dist:                                        # pooled over the ranks' independent samples
+            pooled = shard.allreduce_steady_stats(st[0])
+            kappa, kse = pooled["kappa"], pooled["kappa_se"]
         t_1pct = float(t_step * np.max((se / np.abs(k) / 0.01) ** 2))
     if rank != 0:
         if dist:
