@@ -241,11 +241,14 @@ typedef struct {
   int n_times;                 /* measurement times (Sec. 3.4), 1..MCBTE_MAX_TIMES       */
   const double* t_meas;        /* HOST [n_times] s, ascending, in (0, t_max]             */
   int grid[3];                 /* nx, ny, nz detector cells over the box                 */
-  int threads_per_block;        /* 0 (default 512), 256, 512, 768 or 1024 (FP32 path)     */
+  int threads_per_block;        /* 0 (default 1024), 256, 512, 768 or 1024 (FP32 path)    */
   int blocks_per_sm;
   double time_budget_s;
   void* trace_event_start;     /* optional cudaEvent_t pair around the tracing kernel     */
   void* trace_event_stop;
+  int window_times;            /* FP32 path: measurement times per time window; 0 picks the
+                                  largest window whose tally slice fits a third of the L2;
+                                  >= n_times traces in one pass (no state buffer)           */
 } mcbte_transient_params;
 
 typedef struct {

@@ -257,6 +257,7 @@ class TransientConfig:
     blocks_per_sm: int = 0
     time_budget_s: float = 0.0
     trace_events: Optional[tuple] = None
+    window_times: int = 0                    # measurement times per time window (0: sized to the L2)
 
 
 class TransientOutputs:
@@ -289,6 +290,7 @@ def transient_params(cfg: TransientConfig, n_particles: int, t_meas: np.ndarray)
     p.blocks_per_sm = int(cfg.blocks_per_sm)
     p.time_budget_s = float(cfg.time_budget_s)
     p.trace_event_start, p.trace_event_stop = _event_handles(cfg.trace_events)
+    p.window_times = int(cfg.window_times)
     return p
 
 

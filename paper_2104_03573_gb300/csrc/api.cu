@@ -593,10 +593,31 @@ struct TransientWs {
   double* snap;     // only when outputs are on the host
   double* stats;
   uint32_t* events_pp;
+  uint4* tstate;    // FP32 time windows: particle state between windows
   size_t bytes;
 };
 
-TransientWs layout_transient(char* base, size_t snap_len, int n_times, bool host_out, bool want_ev, uint64_t total) {
+// FP32 transient time windows: measurement times per window.  Automatic
+// choice: the largest window whose [times][cells][4] x 8-byte slice of the
+// snapshot tally fits a third of the L2, so the snapshot atomics of a window
+// hit in L2 instead of read-modify-writing HBM.
+int transient_window_times(const mcbte_transient_params* p) {
+  if (p->precision != MCBTE_FP32_TRACE) return p->n_times;
+  int wt = p->window_times;
+  if (wt <= 0) {
+    int dev = 0, l2 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess ||
+        l2 <= 0)
+      l2 = 96 << 20;
+    const size_t slice = (size_t)p->grid[0] * p->grid[1] * p->grid[2] * 4 * sizeof(long long);
+    const size_t fit = ((size_t)l2 / 3) / slice;
+    wt = fit < 1 ? 1 : (fit > (size_t)p->n_times ? p->n_times : (int)fit);
+  }
+  return wt < p->n_times ? wt : p->n_times;
+}
+
+TransientWs layout_transient(char* base, size_t snap_len, int n_times, bool host_out, bool want_ev, uint64_t total,
+                             bool windows) {
   Carve c;
   c.base = base;
   TransientWs w{};
@@ -612,6 +633,7 @@ TransientWs layout_transient(char* base, size_t snap_len, int n_times, bool host
   c.off = (c.off + 255) & ~(size_t)255;
   w.zero_end = base ? base + c.off : nullptr;
   w.t_meas_ps = c.take<double>(n_times);
+  w.tstate = windows ? c.take<uint4>(3 * total) : nullptr;
   if (host_out) {
     w.snap = c.take<double>(snap_len);
     w.stats = c.take<double>(MCBTE_NSTATS);
@@ -654,7 +676,8 @@ mcbte_status mcbte_transient_workspace_size(const mcbte_material* m, const mcbte
   mcbte_status st = check_transient(m, g, p);
   if (st != MCBTE_OK) return st;
   if (!bytes) return fail(MCBTE_ERR_INVALID_ARG, "workspace_size: null bytes");
-  *bytes = layout_transient(nullptr, 0, p->n_times, false, false, 0).bytes;
+  *bytes = layout_transient(nullptr, 0, p->n_times, false, false, p->n_particles,
+                            transient_window_times(p) < p->n_times).bytes;
   return MCBTE_OK;
 }
 
@@ -668,7 +691,9 @@ mcbte_status mcbte_run_transient(const mcbte_material* m, const mcbte_geometry* 
   const size_t ncell = (size_t)p->grid[0] * p->grid[1] * p->grid[2];
   const size_t snap_len = (size_t)p->n_times * ncell * 4;
   const bool host_out = out->on_host != 0;
-  TransientWs w = layout_transient(nullptr, snap_len, p->n_times, host_out, out->events_pp, p->n_particles);
+  const int wt = transient_window_times(p);
+  const int n_win = (p->n_times + wt - 1) / wt;
+  TransientWs w = layout_transient(nullptr, snap_len, p->n_times, host_out, out->events_pp, p->n_particles, n_win > 1);
   char* base = static_cast<char*>(workspace);
   bool own = false;
   if (!base) {
@@ -678,7 +703,7 @@ mcbte_status mcbte_run_transient(const mcbte_material* m, const mcbte_geometry* 
     return fail(MCBTE_ERR_WORKSPACE, "run_transient: workspace too small");
   }
   char* aligned = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(base) + 255) & ~(uintptr_t)255);
-  w = layout_transient(aligned, snap_len, p->n_times, host_out, out->events_pp, p->n_particles);
+  w = layout_transient(aligned, snap_len, p->n_times, host_out, out->events_pp, p->n_particles, n_win > 1);
   auto release = [&]() {
     if (own) cudaFreeAsync(base, s);
   };
@@ -721,8 +746,16 @@ mcbte_status mcbte_run_transient(const mcbte_material* m, const mcbte_geometry* 
   A.flags = w.flags;
   A.snap = snap;
   A.events_pp = host_out ? w.events_pp : out->events_pp;
+  A.tstate = w.tstate;
   if (p->trace_event_start) RUN_TRY(record_trace_event(p->trace_event_start, s));
-  RUN_TRY(launch_transient(p->precision, w.geos, m->view, C, A, p->threads_per_block, p->blocks_per_sm, s));
+  // one launch per time window (a single one unless the FP32 tally exceeds the L2 budget)
+  for (int k = 0; k < n_win; ++k) {
+    C.win_first = k == 0;
+    C.win_last = k == n_win - 1;
+    C.win_end = (k + 1) * wt < p->n_times ? (k + 1) * wt : p->n_times;
+    if (k > 0) RUN_TRY(cudaMemsetAsync(w.work, 0, sizeof(unsigned long long), s));
+    RUN_TRY(launch_transient(p->precision, w.geos, m->view, C, A, p->threads_per_block, p->blocks_per_sm, s));
+  }
   if (p->trace_event_stop) RUN_TRY(record_trace_event(p->trace_event_stop, s));
   double* stats = host_out ? w.stats : out->stats;
   RUN_TRY(launch_finalize_transient(w.geos, m->view, C, A, snap, stats, ncell, p->precision == MCBTE_FP32_TRACE, s));

@@ -45,6 +45,9 @@ struct RunCfg {
   int n_times;
   const double* t_meas_ps;
   int grid[3];
+  // FP32 transient time windows: this launch takes the snapshots with index
+  // < win_end; the first window emits, later ones resume saved particles
+  int win_first, win_last, win_end;
 };
 
 // Raw accumulators of a run (device).
@@ -61,6 +64,7 @@ struct Acc {
   long long* Gq;              // [n_bins] its fixed-point counterpart (FP32 gradient pass)
   double* dsum;               // [n_dirs][2]
   double* snap;               // [n_times][cells][4] transient
+  uint4* tstate;              // [total][3] particle state between transient time windows, or null
   uint32_t* events_pp;        // [total] or null
   double* X_pp;               // [total] or null
   unsigned long long* work;   // [1] persistent work counter
@@ -665,12 +669,21 @@ __device__ __forceinline__ int step_transient(Particle<R>& p, const GeoRun& g, c
       atomicAdd(&snap[c + 2], (double)(sv * p.u[1]));
       atomicAdd(&snap[c + 3], (double)(sv * p.u[2]));
     } else {
-      // FP32 path: the signed count exactly, the flux in 2^-20 nm/ps units
+      // FP32 path: the signed count exactly, the flux in 2^-20 nm/ps units;
+      // |s v u_a| <= v (1 + rounding), so for v below 2^10 nm/ps every
+      // component is below 2^30 in fixed point and the 32-bit conversion
+      // gives the value fx gives, without its range test
       long long* q = reinterpret_cast<long long*>(snap) + c;
       red_s64(q + 0, p.s > R(0) ? 1ll : -1ll);
-      red_s64(q + 1, fx((float)(sv * p.u[0])));
-      red_s64(q + 2, fx((float)(sv * p.u[1])));
-      red_s64(q + 3, fx((float)(sv * p.u[2])));
+      if ((float)v < 1024.0f) {
+        red_s64(q + 1, (long long)__float2int_rn((float)(sv * p.u[0]) * kFx));
+        red_s64(q + 2, (long long)__float2int_rn((float)(sv * p.u[1]) * kFx));
+        red_s64(q + 3, (long long)__float2int_rn((float)(sv * p.u[2]) * kFx));
+      } else {
+        red_s64(q + 1, fx((float)(sv * p.u[0])));
+        red_s64(q + 2, fx((float)(sv * p.u[1])));
+        red_s64(q + 3, fx((float)(sv * p.u[2])));
+      }
     }
     ++p.mi;
   }

@@ -65,6 +65,52 @@ __global__ void __launch_bounds__(256) k_transient_fp64(const GeoRun* __restrict
 
 #endif  // MCBTE_F64
 #if MCBTE_F32
+// Particle state between time windows, 48 bytes: {x, t}, {u, d_rel},
+// {event index, bin | sign bit, next measurement index, relaxations | live bit}.
+// Streaming (evict-first) accesses keep the window's tally slice in L2.
+constexpr uint32_t kLive = 0x80000000u;
+
+__device__ __forceinline__ void save_state(uint4* st, uint64_t idx, const Particle<float>& p) {
+  uint4* q = st + idx * 3;
+  __stcs(q + 0, make_uint4(__float_as_uint(p.x[0]), __float_as_uint(p.x[1]), __float_as_uint(p.x[2]),
+                           __float_as_uint(p.t)));
+  __stcs(q + 1, make_uint4(__float_as_uint(p.u[0]), __float_as_uint(p.u[1]), __float_as_uint(p.u[2]),
+                           __float_as_uint(p.d_rel)));
+  __stcs(q + 2, make_uint4(p.e, (uint32_t)p.bin | (p.s < 0.0f ? 0x80000000u : 0u), (uint32_t)p.mi,
+                           (uint32_t)p.n_relax | kLive));
+}
+
+__device__ __forceinline__ void mark_done(uint4* st, uint64_t idx) { __stcs(st + idx * 3 + 2, make_uint4(0, 0, 0, 0)); }
+
+// false: the particle ended in an earlier window, or it has nothing to
+// sample before `win_end` (then its saved state stays as it is)
+__device__ __forceinline__ bool load_state(const uint4* st, uint64_t idx, Particle<float>& p, const MatView& M,
+                                           const float4* binf, const RunCfg& C) {
+  const uint4* q = st + idx * 3;
+  const uint4 c = __ldcs(q + 2);
+  if (!(c.w & kLive)) return false;
+  if (!C.win_last && (int)c.z >= C.win_end) return false;
+  const uint4 a = __ldcs(q + 0);
+  const uint4 b = __ldcs(q + 1);
+  p.x[0] = __uint_as_float(a.x);
+  p.x[1] = __uint_as_float(a.y);
+  p.x[2] = __uint_as_float(a.z);
+  p.t = __uint_as_float(a.w);
+  p.u[0] = __uint_as_float(b.x);
+  p.u[1] = __uint_as_float(b.y);
+  p.u[2] = __uint_as_float(b.z);
+  p.d_rel = __uint_as_float(b.w);
+  p.e = c.x;
+  p.bin = (int)(c.y & 0x7fffffffu);
+  p.s = (c.y & 0x80000000u) ? -1.0f : 1.0f;
+  p.mi = (int)c.z;
+  p.n_relax = (int)(c.w & ~kLive);
+  p.pid = (uint32_t)idx;
+  p.g = 0;
+  load_bin(p, M, binf);
+  return true;
+}
+
 // Shared memory: the measurement times as float (always), then the relaxation
 // alias records and per-bin constants where the plan has room.
 template <int TPB>
@@ -116,10 +162,18 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
           drained = true;
           continue;
         }
-        p.pid = (uint32_t)idx;
-        p.g = 0;
-        emit<float>(p, G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, true, (float)C.t_max_ps);
-        transient_start(p, C);
+        if (C.win_first) {
+          p.pid = (uint32_t)idx;
+          p.g = 0;
+          emit<float>(p, G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, true, (float)C.t_max_ps);
+          transient_start(p, C);
+          if (!C.win_last && p.mi >= C.win_end) {   // emitted after this window's last snapshot
+            save_state(A.tstate, idx, p);
+            continue;
+          }
+        } else if (!load_state(A.tstate, idx, p, M, binf, C)) {
+          continue;
+        }
         alive = true;
       }
     }
@@ -131,6 +185,11 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
     }
     if (out != STEP_ALIVE) {
       transient_finish(p, out, idx, A);
+      if (!C.win_last) mark_done(A.tstate, idx);
+      alive = false;
+    } else if (!C.win_last && p.mi >= C.win_end) {
+      // this window's snapshots are taken: park the particle at its event
+      save_state(A.tstate, idx, p);
       alive = false;
     }
   }
@@ -196,7 +255,7 @@ cudaError_t launch_transient(int precision, const GeoRun* geos, const MatView& M
     k_transient_fp64<<<(unsigned)blocks, 256, 0, s>>>(geos, M, C, A);
     return cudaGetLastError();
   }
-  return launch_transient_f32(geos, M, C, A, threads > 0 ? threads : 512, bps, s);
+  return launch_transient_f32(geos, M, C, A, threads > 0 ? threads : 1024, bps, s);
 }
 
 #endif  // MCBTE_F64
