@@ -593,7 +593,9 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
       }
       // ---- tallies of this flight
       if (P->transient) {
-        double t_end = t_now + seg / v;
+        // the flight ended by t_max ends at t_max exactly (its length was
+        // derived from t_max; dividing it by v again could land an ulp short)
+        double t_end = final_seg ? S.t_max_ps : t_now + seg / v;
         while (mi < S.t_meas_ps.size() &&
                (S.t_meas_ps[mi] < t_end || (final_seg && S.t_meas_ps[mi] <= t_end))) {
           double dist = v * (S.t_meas_ps[mi] - t_now);

@@ -638,7 +638,9 @@ __device__ __forceinline__ int step_transient(Particle<R>& p, const GeoRun& g, c
   if (d_end <= p.d_rel && d_end <= db) { fin = true; seg = d_end; }
   else if (p.d_rel < db) { relax = true; seg = p.d_rel; }
   else { seg = db; }
-  const R t_end = (sizeof(R) == 8) ? p.t + seg / v : p.t + seg * p.inv_v;
+  // the flight ended by t_max ends at t_max exactly (Sec. 3.5.6), so a
+  // measurement at t_max samples every particle still alive
+  const R t_end = fin ? tmax : ((sizeof(R) == 8) ? p.t + seg / v : p.t + seg * p.inv_v);
   const int nx = C.grid[0], ny = C.grid[1], nz = C.grid[2];
   const size_t ncell = (size_t)nx * ny * nz;
   while (p.mi < C.n_times) {
