@@ -54,7 +54,7 @@ INSTR_PER_EVENT = 200.0
 # DRAM bytes per launch of the FP32 steady tracing kernel on the default
 # workload, from the ncu capture summarised in profiles/ (None until a capture
 # of the current kernel exists).
-TRACE_DRAM_BYTES_PER_LAUNCH = None
+TRACE_DRAM_BYTES_PER_LAUNCH = 1_344_256 + 200_704
 
 
 def _dist():
@@ -245,10 +245,17 @@ def _workload_setup(name, args, seed_offset):
             o = api.SteadyOutputs(len(Gs), M.n_bins, 0, True)
             return lambda: (api.run_steady(M, Gs, ns, c, out=o), (lambda: o.stats.cpu().numpy()))[1]
 
+        e2e_k = [0]
+
         def e2e():
+            # the graph replays take keys seed+1, seed+2, ...: end-to-end run k takes
+            # the key of timed step k (run 0 is untimed), so both see the same samples
             Mh = api.Material(mat)
             Gh = [api.Geometry(g) for g in wl.geometries]
-            res = api.run_steady_host(Mh, Gh, wl.n_per_geom, replace(gb.cfg, trace_events=None, seed_device=None))
+            key = gb.cfg.seed + args.warmup + e2e_k[0]
+            e2e_k[0] += 1
+            res = api.run_steady_host(Mh, Gh, wl.n_per_geom, replace(gb.cfg, seed=key, trace_events=None,
+                                                                        seed_device=None))
             return res["stats"]
         desc = ("64 in-plane films d = 10 nm * 1000^(f/63), 100x100 nm cell, periodic x,y, diffuse z, grad_T -1e6 K/m, "
                 "N_f = 1e5*100^u_f, N_scat_max 10; one persistent launch replayed as a CUDA graph")

@@ -70,6 +70,10 @@ __global__ void __launch_bounds__(256) k_steady_fp64(const GeoRun* __restrict__ 
   p.pid = (uint32_t)(idx - offs[g]);
   p.g = g;
   const uint2 key = run_key(C);
+  if (globaltimer_ns() > deadline) {   // over budget before this particle started
+    atomicOr(A.flags, 1);
+    return;
+  }
   emit<double>(p, G, M, M.rec_emit, M.rec_init, nullptr, key.x, key.y, false, 0.0);
   typename GradPick<GRAD, GradList>::type gr;
   if (GRAD) gr.init(p.bin);
@@ -244,7 +248,14 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
     if (need && (__popc(need) >= refill_min || live == 0u)) {
       const int leader = __ffs(need) - 1;
       unsigned long long base = 0;
-      if ((int)lane == leader) base = atomicAdd(A.work, (unsigned long long)__popc(need));
+      if ((int)lane == leader) {
+        base = atomicAdd(A.work, (unsigned long long)__popc(need));
+        // the time budget is also checked each time the handed-out count
+        // crosses a multiple of 4096 (particles shorter than the per-event
+        // check interval would otherwise never look)
+        if (((base + (unsigned long long)__popc(need)) >> 12) != (base >> 12) && globaltimer_ns() > deadline)
+          atomicOr(A.flags, 1);
+      }
       base = __shfl_sync(kAll, base, leader);
       if (!alive && !drained) {
         idx = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));

@@ -1,0 +1,171 @@
+"""Parity at the full workload sizes the bench times, in the launch
+configurations it uses: the CPU reference traces the whole 1e7-particle slab
+(16 host cores, a few seconds) or samples of particles one by one, and
+properties that hold at any size (exact count conservation, invariance of
+the integer tallies under time windows, the gradient against common-random-
+number central differences) cover the rest."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import oracle
+from inputs import workloads as W
+from gpu_helpers import rel_close
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2104_03573_gb300 import _lib as L  # noqa: E402
+from paper_2104_03573_gb300 import api, batch  # noqa: E402
+
+RTOL = 1e-9
+
+
+def _ranges(n, k, width, seed):
+    """k runs of `width` consecutive particle ids spread over [0, n), plus both ends."""
+    rng = np.random.default_rng(seed)
+    starts = np.unique(np.concatenate([[0, n - width], rng.integers(0, n - width, size=k)]))
+    return [(int(s), int(s) + width) for s in starts]
+
+
+def _oracle_sample(mat, geom, run, n_total, ranges, batch_index=0):
+    ev, X = [], []
+    for a, b in ranges:
+        r = oracle.run_steady(mat, geom, run, pid_begin=a, pid_end=b, n_total=n_total, batch_index=batch_index,
+                              per_particle=True, n_threads=1)
+        ev.append(r["events_pp"])
+        X.append(r["X_pp"])
+    return np.concatenate(ev), np.concatenate(X)
+
+
+def _take(arr, ranges):
+    return np.concatenate([arr[a:b] for a, b in ranges])
+
+
+def test_si_slab_full_size_fp64_tallies_and_fp32_kappa():
+    wl = W.si_slab_c2()                                   # 1e7 particles, 50 cells + per-bin flux
+    mat, geo, run = wl.material, wl.geometries[0], wl.run
+    ref = oracle.run_steady(mat, geo, run)                # all particles, all host cores
+    M, G = api.Material(mat), api.Geometry(geo)
+    base = dict(seed=run.seed, n_cells=run.n_cells, cell_axis=run.cell_axis, tally_axis=run.tally_axis,
+                per_bin=True, max_events=run.max_events)
+    f64 = api.run_steady(M, [G], [run.n], api.SteadyConfig(precision=L.FP64_PLAIN, **base))
+    torch.cuda.synchronize()
+    for k, ours in (("T", f64.T[0]), ("q", f64.q[0]), ("q_bin", f64.q_bin[0])):
+        ok, err = rel_close(ours.cpu().numpy(), ref[k], RTOL)
+        assert ok, (k, err)
+    st = f64.stats[0].cpu().numpy()
+    assert st[L.STAT_EVENTS] == ref["events"]
+    assert st[L.STAT_KAPPA] == pytest.approx(ref["kappa"], rel=RTOL)
+    # FP32 tracer in the bench's launch shapes, same random words
+    for threads, refill in ((1024, 4), (768, 4)):
+        o = api.run_steady(M, [G], [run.n], api.SteadyConfig(precision=L.FP32_TRACE, threads_per_block=threads,
+                                                             refill_threshold=refill, **base))
+        torch.cuda.synchronize()
+        s32 = o.stats[0].cpu().numpy()
+        assert s32[L.STAT_STATUS] == 0 and s32[L.STAT_N] == run.n
+        se = np.hypot(s32[L.STAT_KAPPA_SE], ref["kappa_se"])
+        assert abs(s32[L.STAT_KAPPA] - ref["kappa"]) < min(3 * se, 0.005 * ref["kappa"])
+
+
+def test_si_slab_full_size_sampled_particles():
+    wl = W.si_slab_c2()
+    mat, geo, run = wl.material, wl.geometries[0], wl.run
+    M, G = api.Material(mat), api.Geometry(geo)
+    o = api.run_steady(M, [G], [run.n], api.SteadyConfig(seed=run.seed, precision=L.FP64_PLAIN, n_cells=run.n_cells,
+                                                         tally_axis=run.tally_axis, per_bin=True,
+                                                         max_events=run.max_events), per_particle=True)
+    torch.cuda.synchronize()
+    ranges = _ranges(run.n, 24, 16, 11)
+    ev, X = _oracle_sample(mat, geo, run, run.n, ranges)
+    assert np.array_equal(_take(o.events_pp.cpu().numpy().astype(np.uint32), ranges), ev)
+    ok, err = rel_close(_take(o.X_pp.cpu().numpy(), ranges), X, RTOL)
+    assert ok, err
+
+
+def test_transient_box_full_size_counts_and_windows():
+    wl = W.transient_box_c3()                             # 1e8 particles, 64x64x32 cells x 200 times
+    mat, geo, run = wl.material, wl.geometries[0], wl.run
+    M, G = api.Material(mat), api.Geometry(geo)
+    out = api.TransientOutputs(len(run.t_meas), run.grid, run.n)
+    outs = []
+    for wt in (0, len(run.t_meas)):                       # the bench's windows, then one pass
+        cfg = api.TransientConfig(seed=run.seed, t_max=run.t_max, t_meas=run.t_meas, grid=run.grid,
+                                  precision=L.FP32_TRACE, window_times=wt)
+        api.run_transient(M, G, run.n, cfg, out=out)
+        torch.cuda.synchronize()
+        st = out.stats.cpu().numpy()
+        assert st[L.STAT_STATUS] == 0 and st[L.STAT_N] == run.n
+        outs.append((out.tally.clone(), st))
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert outs[0][1][L.STAT_EVENTS] == outs[1][1][L.STAT_EVENTS]
+    # every particle is inside the adiabatic box at every measurement time and
+    # every sign is +: each snapshot's temperature field sums to N quanta of
+    # E_eff / (C_tot V_cell) (Eq. sampling)
+    ncell = run.grid[0] * run.grid[1] * run.grid[2]
+    v_cell = float(np.prod(geo.L)) / ncell
+    quantum = (outs[0][1][L.STAT_E_TOT] / run.n) / (M.tables()["C_tot"] * v_cell)
+    per_time = (outs[0][0][..., 0].sum(dim=(1, 2, 3)) / quantum).cpu().numpy()
+    np.testing.assert_allclose(per_time, run.n, rtol=1e-9)
+
+
+def test_film_batch_full_size_sampled_particles_and_fp32_batch():
+    wl = W.film_batch_c4()                                # 64 films, ~1.4e8 particles
+    mat, run = wl.material, wl.run
+    ns = list(wl.n_per_geom)
+    M = api.Material(mat)
+    Gs = [api.Geometry(g) for g in wl.geometries]
+    base = dict(tally_axis=run.tally_axis, per_bin=True, n_scat_max=run.n_scat_max, max_events=10 ** 9,
+                time_budget_s=300)
+    f64 = api.run_steady(M, Gs, ns, api.SteadyConfig(seed=run.seed, precision=L.FP64_PLAIN, **base),
+                         per_particle=True)
+    torch.cuda.synchronize()
+    st64 = f64.stats.cpu().numpy()
+    assert np.all(st64[:, L.STAT_STATUS] == 0)
+    ev_all = f64.events_pp.cpu().numpy().astype(np.uint32)
+    X_all = f64.X_pp.cpu().numpy()
+    off = np.concatenate([[0], np.cumsum(ns)])
+    for f in (0, 1, 9, 21, 40, 63):
+        rr = _ranges(ns[f], 3, 8, 100 + f)
+        ev, X = _oracle_sample(mat, wl.geometries[f], run, ns[f], rr, batch_index=f)
+        glob = [(a + off[f], b + off[f]) for a, b in rr]
+        assert np.array_equal(_take(ev_all, glob), ev), f
+        ok, err = rel_close(_take(X_all, glob), X, RTOL)
+        assert ok, (f, err)
+    # FP32: the bench's batched launch (CUDA graph, device-resident key)
+    gb = batch.GraphBatch(M, Gs, ns, api.SteadyConfig(seed=run.seed, precision=L.FP32_TRACE, **base), tune=True)
+    o = gb.replay(seed=run.seed)
+    torch.cuda.synchronize()
+    st = o.stats.cpu().numpy()
+    assert np.all(st[:, L.STAT_STATUS] == 0)
+    assert np.array_equal(st[:, L.STAT_N], np.array(ns, dtype=np.float64))
+    z = (st[:, L.STAT_KAPPA] - st64[:, L.STAT_KAPPA]) / np.hypot(st[:, L.STAT_KAPPA_SE], st64[:, L.STAT_KAPPA_SE])
+    assert np.all(np.abs(z) < 3.0), z
+
+
+def test_pore_grad_full_size_replay_and_crn_differences():
+    wl = W.pore_film_c5()                                 # 5e7 particles
+    mat, geo, run = wl.material, wl.geometries[0], wl.run
+    M, G = api.Material(mat), api.Geometry(geo)
+    cfg = api.SteadyConfig(seed=run.seed, precision=L.FP32_TRACE, tally_axis=run.tally_axis, per_bin=True,
+                           n_scat_max=run.n_scat_max, max_events=10 ** 9, threads_per_block=768,
+                           refill_threshold=4, time_budget_s=300)
+    ones = np.ones((1, mat.n_bins))
+    fwd, go = api.grad(M, G, run.n, cfg, dirs=ones)
+    torch.cuda.synchronize()
+    assert fwd.stats[0, L.STAT_STATUS].item() == 0       # every replayed particle reproduced its tally
+    d, d_se = go.dkappa_dir[0].cpu().numpy()
+    # common random numbers: kappa(tau e^{+h}) - kappa(tau e^{-h}) over 2h
+    h = 0.05
+    ks = []
+    for sgn in (1.0, -1.0):
+        m2 = replace(mat, tau=mat.tau * np.exp(sgn * h))
+        o = api.run_steady(api.Material(m2), [G], [run.n], cfg)
+        torch.cuda.synchronize()
+        ks.append(o.stats[0, L.STAT_KAPPA].item())
+    fd = (ks[0] - ks[1]) / (2 * h)
+    assert abs(d - fd) < 4 * d_se + 0.01 * abs(fd), (d, d_se, fd)

@@ -7,6 +7,8 @@ sums and libm's log / sin / cos may differ by an ulp).  FP32 mode: every
 compared tally within 3 combined standard errors of the oracle on
 independent seeds, kappa within 0.5 %.
 """
+from dataclasses import replace
+
 import numpy as np
 import pytest
 
@@ -179,6 +181,29 @@ def test_max_events_truncation_reported():
     assert gg["stats"][0][L.STAT_TRUNCATED] == ref["truncated"] > 0
     assert np.array_equal(gg["events_pp"], ref["events_pp"])
     assert gg["events_pp"].max() == 50
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_time_budget_stops_the_run_and_leaves_the_device_usable(precision):
+    # the budget is a device-timer check between events, not a wait: a run
+    # that exceeds it stops refilling, reports TIMEOUT, and the next run works
+    prec = L.FP32_TRACE if precision == "fp32" else L.FP64_PLAIN
+    wl = W.si_slab_c2(n=4_000_000)
+    mat, g, run = wl.material, wl.geometries[0], wl.run
+    M, G = api.Material(mat), api.Geometry(g)
+    cfg = api.SteadyConfig(seed=5, precision=prec, n_cells=run.n_cells, tally_axis=run.tally_axis,
+                           time_budget_s=2e-5)
+    out = api.run_steady(M, [G], [run.n], cfg)
+    torch.cuda.synchronize()
+    st = out.stats[0].cpu().numpy()
+    assert st[L.STAT_STATUS] == L.ERR_TIMEOUT
+    assert st[L.STAT_N] < run.n
+    with pytest.raises(L.MCBTEError) as e:           # host outputs: the status comes back as an error
+        api.run_steady_host(M, [G], [run.n], cfg)
+    assert e.value.status == L.ERR_TIMEOUT
+    ok = api.run_steady(M, [G], [20_000], replace(cfg, time_budget_s=0.0))
+    torch.cuda.synchronize()
+    assert ok.stats[0, L.STAT_STATUS].item() == 0 and ok.stats[0, L.STAT_N].item() == 20_000
 
 
 def test_host_output_path_matches_device_path():
