@@ -164,7 +164,8 @@ def _workload_setup(name, args, seed_offset):
         M, G = api.Material(mat), api.Geometry(geo)
         cfg = api.SteadyConfig(seed=run.seed + seed_offset, precision=L.FP32_TRACE, n_cells=run.n_cells,
                                cell_axis=2, tally_axis=2, per_bin=True, threads_per_block=args.threads,
-                               blocks_per_sm=args.blocks_per_sm, refill_threshold=args.refill)
+                               blocks_per_sm=args.blocks_per_sm, refill_threshold=args.refill,
+                               cell_flux_axis=True)
         if args.threads == 0 and not args.no_autotune:
             cfg = autotune.tune(M, [G], [run.n], cfg)
         cfg = replace(cfg, trace_events=ev)
@@ -187,7 +188,7 @@ def _workload_setup(name, args, seed_offset):
         d2h = 8 * (run.n_cells + 3 * run.n_cells + M.n_bins + L.NSTATS)
         h2d = _material_bytes(mat) + ctypes.sizeof(L.GeometryDesc) + 8
         desc = ("steady cross-plane Si-like film L=1um (1um cube, periodic x,y), BvK 3x1000 bins + Holland tau "
-                "at 300 K, walls 300+-0.5 K, 50 cells + per-bin flux; FP32 tracing, fixed-point FP64-exact tallies")
+                "at 300 K, walls 300+-0.5 K, 50 cells x {T, q_z} + per-bin q_z; FP32 tracing, fixed-point FP64-exact tallies")
         launches = 3
         shape = {"threads_per_block": cfg.threads_per_block, "refill_threshold": cfg.refill_threshold}
         return dict(mat=mat, geo=geo, run=run, n=run.n, step=step, fp64=fp64, e2e=e2e, d2h=d2h, h2d=h2d, desc=desc,

@@ -181,6 +181,10 @@ typedef struct {
                                   updates it); `seed` is ignored                          */
   int refill_threshold;        /* FP32 tracer: a warp refills its finished lanes once at
                                   least this many are idle (0 or 1 = at once, up to 32)   */
+  int cell_flux_axis;          /* FP32 tracer, cell tallies: 0 = T and q_x, q_y, q_z;
+                                  1 = T and the flux along tally_axis only (the other two
+                                  components are returned as 0; Eq. flux_x_steady needs
+                                  only that one)                                          */
 } mcbte_steady_params;
 
 typedef struct {

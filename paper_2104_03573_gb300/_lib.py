@@ -44,7 +44,7 @@ class SteadyParams(C.Structure):
                 ("cell_axis", C.c_int), ("tally_axis", C.c_int), ("per_bin", C.c_int),
                 ("threads_per_block", C.c_int), ("blocks_per_sm", C.c_int), ("time_budget_s", C.c_double),
                 ("trace_event_start", C.c_void_p), ("trace_event_stop", C.c_void_p),
-                ("seed_device", C.c_void_p), ("refill_threshold", C.c_int)]
+                ("seed_device", C.c_void_p), ("refill_threshold", C.c_int), ("cell_flux_axis", C.c_int)]
 
 
 class SteadyOut(C.Structure):

@@ -122,6 +122,7 @@ class SteadyConfig:
     trace_events: Optional[tuple] = None     # (start, stop) torch.cuda.Event around the trace kernel
     seed_device: Optional[object] = None     # int64 device tensor holding the Philox key
     refill_threshold: int = 0
+    cell_flux_axis: bool = False             # FP32 cell tallies: T and the tally-axis flux only
 
 
 def _event_handles(pair):
@@ -150,6 +151,7 @@ def steady_params(cfg: SteadyConfig, n_particles: np.ndarray) -> "L.SteadyParams
     p.trace_event_start, p.trace_event_stop = _event_handles(cfg.trace_events)
     p.seed_device = None if cfg.seed_device is None else cfg.seed_device.data_ptr()
     p.refill_threshold = int(cfg.refill_threshold)
+    p.cell_flux_axis = int(bool(cfg.cell_flux_axis))
     return p
 
 

@@ -455,6 +455,7 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   C.budget_ns = (uint64_t)((p->time_budget_s > 0 ? p->time_budget_s : 120.0) * 1e9);
   C.seed_dev = reinterpret_cast<const unsigned long long*>(p->seed_device);
   C.refill_min = p->refill_threshold;
+  C.cell_flux_axis = p->cell_flux_axis ? 1 : 0;
   Acc A{};
   A.cellP = w.cellP;
   A.cellD = w.cellD;

@@ -45,6 +45,7 @@ struct RunCfg {
   int n_times;
   const double* t_meas_ps;
   int grid[3];
+  int cell_flux_axis;   // FP32 cell tallies: T and the tally-axis flux only
   // FP32 transient time windows: this launch takes the snapshots with index
   // < win_end; the first window emits, later ones resume saved particles
   int win_first, win_last, win_end;
@@ -309,11 +310,34 @@ __device__ __forceinline__ void red_s64(long long* a, long long v) {
   atomicAdd(reinterpret_cast<unsigned long long*>(a), (unsigned long long)v);
 }
 
+// Adds f_i * d to a[i] (i < 4) in fixed point; one range test for the
+// group (values below 2e9 in fixed point take the 32-bit conversion, as fx).
 __device__ __forceinline__ void fx_add4(long long* a, float f0, float f1, float f2, float f3, float d) {
-  red_s64(a + 0, fx(f0 * d));
-  red_s64(a + 1, fx(f1 * d));
-  red_s64(a + 2, fx(f2 * d));
-  red_s64(a + 3, fx(f3 * d));
+  const float v0 = (f0 * d) * kFx, v1 = (f1 * d) * kFx, v2 = (f2 * d) * kFx, v3 = (f3 * d) * kFx;
+  if (fmaxf(fmaxf(fabsf(v0), fabsf(v1)), fmaxf(fabsf(v2), fabsf(v3))) < 2.0e9f) {
+    red_s64(a + 0, (long long)__float2int_rn(v0));
+    red_s64(a + 1, (long long)__float2int_rn(v1));
+    red_s64(a + 2, (long long)__float2int_rn(v2));
+    red_s64(a + 3, (long long)__float2int_rn(v3));
+  } else {
+    red_s64(a + 0, fx_wide(v0));
+    red_s64(a + 1, fx_wide(v1));
+    red_s64(a + 2, fx_wide(v2));
+    red_s64(a + 3, fx_wide(v3));
+  }
+}
+
+// The same for {a[0], a[1 + ax]} only (cell tallies of T and the flux along
+// one axis).
+__device__ __forceinline__ void fx_add2(long long* a, int ax, float f0, float fa, float d) {
+  const float v0 = (f0 * d) * kFx, va = (fa * d) * kFx;
+  if (fmaxf(fabsf(v0), fabsf(va)) < 2.0e9f) {
+    red_s64(a, (long long)__float2int_rn(v0));
+    red_s64(a + 1 + ax, (long long)__float2int_rn(va));
+  } else {
+    red_s64(a, fx_wide(v0));
+    red_s64(a + 1 + ax, fx_wide(va));
+  }
 }
 
 // FP32 path: fixed-point tallies.  Cells use a difference array: the (up to)
@@ -321,8 +345,10 @@ __device__ __forceinline__ void fx_add4(long long* a, float f0, float f1, float 
 // +/- pair in D, and the per-cell value is P[c] + sum_{c' <= c} D[c'];
 // at most 4 x 4 integer atomics per segment whatever the number of cells
 // crossed.  The frequency-resolved flux is added once per relaxation
-// period (the bin is constant over a period).
-struct TallyFx {
+// period (the bin is constant over a period).  NQ = 4: cells tally T and
+// q_x, q_y, q_z; NQ = 2: T and the flux along the tally axis only.
+template <int NQ = 4>
+struct TallyFxT {
   long long* cP;   // [nc][4] (shared memory or global), or null
   long long* cD;   // [nc+1][4]
   long long* qb;   // [n_bins], or null
@@ -340,7 +366,7 @@ struct TallyFx {
     if (uz == 0.0f) {
       const int c = min(max((int)(z0 * inv_h), 0), nc - 1);
       const float sl = p.s * seg;
-      fx_add4(cP + c * 4, sl * p.inv_v, sl * p.u[0], sl * p.u[1], sl * p.u[2], 1.0f);
+      add(cP + c * 4, sl * p.inv_v, sl * p.u[0], sl * p.u[1], sl * p.u[2], 1.0f);
       return contrib;
     }
     const float z1 = z0 + seg * uz;
@@ -351,16 +377,21 @@ struct TallyFx {
     const float k = p.s / fabsf(uz);      // per unit of axial length
     const float f0 = k * p.inv_v, f1 = k * p.u[0], f2 = k * p.u[1], f3 = k * p.u[2];
     if (clo == chi) {
-      fx_add4(cP + clo * 4, f0, f1, f2, f3, zhi - zlo);
+      add(cP + clo * 4, f0, f1, f2, f3, zhi - zlo);
       return contrib;
     }
-    fx_add4(cP + clo * 4, f0, f1, f2, f3, (float)(clo + 1) * h - zlo);
-    fx_add4(cP + chi * 4, f0, f1, f2, f3, zhi - (float)chi * h);
+    add(cP + clo * 4, f0, f1, f2, f3, (float)(clo + 1) * h - zlo);
+    add(cP + chi * 4, f0, f1, f2, f3, zhi - (float)chi * h);
     if (chi > clo + 1) {
-      fx_add4(cD + (clo + 1) * 4, f0, f1, f2, f3, h);
-      fx_add4(cD + chi * 4, f0, f1, f2, f3, -h);
+      add(cD + (clo + 1) * 4, f0, f1, f2, f3, h);
+      add(cD + chi * 4, f0, f1, f2, f3, -h);
     }
     return contrib;
+  }
+
+  __device__ __forceinline__ void add(long long* a, float f0, float f1, float f2, float f3, float d) const {
+    if constexpr (NQ == 4) fx_add4(a, f0, f1, f2, f3, d);
+    else fx_add2(a, ta, f0, ta == 0 ? f1 : (ta == 1 ? f2 : f3), d);
   }
 
   __device__ __forceinline__ void period_end(Particle<float>& p) const {
@@ -370,6 +401,7 @@ struct TallyFx {
     }
   }
 };
+using TallyFx = TallyFxT<4>;
 
 // No steady tallies (transient runs).
 struct TallyNone {

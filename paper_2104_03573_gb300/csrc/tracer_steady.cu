@@ -176,7 +176,9 @@ __device__ __forceinline__ void grad_finish_replay(GradReplay& gr, double X, int
 // GRAD: the gradient pass, which replays the forward pass's particles with
 // their final tallies read from A.X_pp; it writes the gradient accumulators
 // only, and flags (bit 2) any particle whose replayed tally differs.
-template <bool CELLS, bool GRAD, int TPB>
+// CELLS: 0 no cell tallies, 1 T and three flux components, 2 T and the
+// tally-axis flux only.
+template <int CELLS, bool GRAD, int TPB>
 __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict__ geos,
                                                        const uint64_t* __restrict__ offs, MatView M, RunCfg C,
                                                        Acc A, SmemPlan S) {
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
   }
   ThreadAcct acct;
   acct.reset(-1);
-  TallyFx T;
+  TallyFxT<CELLS == 2 ? 2 : 4> T;
   T.nc = nc;
   T.ca = C.cell_axis;
   T.ta = C.tally_axis;
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
       }
     }
     if (!alive) continue;
-    int out = step_steady<float, typename GradPick<GRAD, GradReplay>::type, TallyFx>(p, *G, M, relax, binf, C, key.x,
+    int out = step_steady<float, typename GradPick<GRAD, GradReplay>::type, decltype(T)>(p, *G, M, relax, binf, C, key.x,
                                                                                   key.y, T, gr);
     if (out == STEP_ALIVE && (p.e & 255u) == 0u && globaltimer_ns() > deadline) {
       atomicOr(A.flags, 1);
@@ -447,7 +449,7 @@ cudaError_t launch_f64(const GeoRun* geos, const uint64_t* offs, const MatView& 
 #endif  // MCBTE_F64
 
 #if MCBTE_F32
-template <bool CELLS, bool GRAD, int TPB>
+template <int CELLS, bool GRAD, int TPB>
 cudaError_t launch_f32_tpb(const GeoRun* geos, const uint64_t* offs, const MatView& M, const RunCfg& C,
                            const Acc& A, int bps, cudaStream_t s) {
   const SmemPlan S = plan_smem_f32(M.n, C.n_geoms, GRAD ? 0 : C.n_cells, GRAD ? 0 : C.per_bin, 200 * 1024);
@@ -463,7 +465,7 @@ cudaError_t launch_f32_tpb(const GeoRun* geos, const uint64_t* offs, const MatVi
   return cudaGetLastError();
 }
 
-template <bool CELLS, bool GRAD>
+template <int CELLS, bool GRAD>
 cudaError_t launch_f32(const GeoRun* geos, const uint64_t* offs, const MatView& M, const RunCfg& C, const Acc& A,
                        int threads, int bps, cudaStream_t s) {
   switch (threads) {
@@ -541,9 +543,10 @@ cudaError_t launch_dirs_dot_pi(const double* dirs, int n_dirs, const MatView& M,
 cudaError_t launch_steady_f32(bool grad, bool cells, const GeoRun* geos, const uint64_t* offs, const MatView& M,
                               const RunCfg& C, const Acc& A, int threads, int bps, cudaStream_t s) {
   // the gradient pass keeps no cell or per-bin tallies
-  if (grad) return launch_f32<false, true>(geos, offs, M, C, A, threads, bps, s);
-  return cells ? launch_f32<true, false>(geos, offs, M, C, A, threads, bps, s)
-               : launch_f32<false, false>(geos, offs, M, C, A, threads, bps, s);
+  if (grad) return launch_f32<0, true>(geos, offs, M, C, A, threads, bps, s);
+  if (!cells) return launch_f32<0, false>(geos, offs, M, C, A, threads, bps, s);
+  return C.cell_flux_axis ? launch_f32<2, false>(geos, offs, M, C, A, threads, bps, s)
+                          : launch_f32<1, false>(geos, offs, M, C, A, threads, bps, s);
 }
 #endif  // MCBTE_F32
 

@@ -266,3 +266,18 @@ def test_fp32_transient_time_windows_change_nothing(case):
         for k in (L.STAT_EVENTS, L.STAT_N, L.STAT_MAX_EVENTS, L.STAT_TRUNCATED):
             assert o.stats[k].item() == base.stats[k].item()
     assert base.stats[L.STAT_N].item() == r.n
+
+
+def test_fp32_axis_only_cell_tallies_equal_the_full_ones():
+    wl = W.si_slab_c2(n=200_000)
+    mat, geo, run = wl.material, wl.geometries[0], wl.run
+    M, G = api.Material(mat), api.Geometry(geo)
+    cfg = api.SteadyConfig(seed=41, precision=L.FP32_TRACE, n_cells=run.n_cells, cell_axis=2, tally_axis=2,
+                           per_bin=True)
+    full = _run(M, [G], [run.n], cfg)
+    axis = _run(M, [G], [run.n], replace_cfg(cfg, cell_flux_axis=True))
+    assert torch.equal(axis.T, full.T)
+    assert torch.equal(axis.q[..., 2], full.q[..., 2])
+    assert torch.count_nonzero(axis.q[..., :2]) == 0
+    assert torch.equal(axis.q_bin, full.q_bin)
+    assert torch.equal(axis.stats[:, L.STAT_SUMX], full.stats[:, L.STAT_SUMX])
