@@ -42,6 +42,7 @@ class Material:
     C: Optional[np.ndarray] = None       # J/(m^3 K), per-bin heat capacity (format 2)
     T_lin: float = 300.0
     name: str = ""
+    tau_imp: Optional[np.ndarray] = None  # s, optional two-phonon (impurity) relaxation times
 
     @property
     def n_bins(self) -> int:

@@ -39,6 +39,7 @@ class _Params(C.Structure):
     _fields_ = [
         ("n_bins", C.c_int), ("omega", C.c_void_p), ("v", C.c_void_p), ("tau", C.c_void_p),
         ("C", C.c_void_p), ("D", C.c_void_p), ("domega", C.c_void_p), ("T_lin", C.c_double),
+        ("tau_imp", C.c_void_p),
         ("L", C.c_double * 3), ("face_type", C.c_int * 6), ("face_T", C.c_double * 6),
         ("face_p", C.c_double * 6), ("T_eq", C.c_double), ("grad_T", C.c_double * 3),
         ("pore", C.c_int), ("pore_c", C.c_double * 2), ("pore_r", C.c_double), ("pore_p", C.c_double),
@@ -131,6 +132,8 @@ def _params(material, geom, keep: _Keep, **kw) -> _Params:
         P.D = _ptr(keep.add(_f64(material.D)))
         P.domega = _ptr(keep.add(_f64(material.domega)))
     P.T_lin = material.T_lin
+    if getattr(material, "tau_imp", None) is not None:
+        P.tau_imp = _ptr(keep.add(_f64(material.tau_imp)))
     if geom is not None:
         P.L[:] = [float(x) for x in geom.L]
         P.face_type[:] = [int(x) for x in geom.face_type]

@@ -38,6 +38,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <limits>
 #include <cstdint>
 #include <cstring>
 #include <thread>
@@ -215,6 +216,7 @@ typedef struct {
   const double* D;        // format 1, or NULL
   const double* domega;   // format 1
   double T_lin;
+  const double* tau_imp;  // optional two-phonon (impurity) relaxation times, or NULL (Sec. 3.3, Sec. 4.1)
   // geometry (SI)
   double L[3];
   int face_type[6];       // 0 isothermal, 1 adiabatic, 2 periodic
@@ -277,6 +279,8 @@ namespace {
 struct Tables {
   int n = 0;
   std::vector<double> C, v_nm, lam_nm, inv_v, pi_relax;
+  bool imp = false;              // a two-phonon clock is present
+  std::vector<double> lam2_nm;   // v tau_imp (nm); +inf for bins without impurity scattering
   double C_tot = 0, sum_Cv = 0, sum_Ct = 0;
   Alias emit, init, relax;
 };
@@ -313,6 +317,11 @@ int build_tables(const or_params* P, Tables& t) {
     t.inv_v[i] = 1.0 / t.v_nm[i];
     t.pi_relax[i] = w_relax[i] / t.sum_Ct;
   }
+  t.imp = P->tau_imp != nullptr;
+  t.lam2_nm.assign(n, std::numeric_limits<double>::infinity());
+  if (t.imp)
+    for (int i = 0; i < n; ++i)
+      if (std::isfinite(P->tau_imp[i])) t.lam2_nm[i] = t.v_nm[i] * (P->tau_imp[i] * 1e12);
   return 0;
 }
 
@@ -558,6 +567,16 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
       }
     }
     double d_rel = t.lam_nm[bin] * (-series_log(oc53(w1[1], w1[2])));
+    // two-phonon clock (Sec. 3.3): its own exponential distance, drawn from
+    // sub-block 256 of the event that (re)starts it
+    auto draw_d2 = [&](uint32_t ev) -> double {
+      if (!t.imp || !std::isfinite(t.lam2_nm[bin])) return std::numeric_limits<double>::infinity();
+      uint32_t c4[4] = {(uint32_t)pid, P->batch_index, ev, 256u};
+      uint32_t w4[4];
+      philox4x32_10(c4, k0, k1, w4);
+      return t.lam2_nm[bin] * (-series_log(oc53(w4[0], w4[1])));
+    };
+    double d2 = draw_d2(0);
     out.scal[OR_SIGNED_EMIT] += s;
     uint32_t e = 0;
     int n_relax = 0;
@@ -580,16 +599,21 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
       first_hit(g, x, u, &db, &face);
       const double v = t.v_nm[bin];
       bool final_seg = false;
-      bool relax;
+      bool relax;           // three-phonon relaxation ends the flight
+      bool relax2 = false;  // two-phonon (impurity) scattering ends the flight
       double seg;
-      if (P->transient) {
-        double d_end = (S.t_max_ps - t_now) * v;
-        if (d_end <= d_rel && d_end <= db) { final_seg = true; seg = d_end; relax = false; }
-        else if (d_rel < db) { seg = d_rel; relax = true; }
-        else { seg = db; relax = false; }
+      // the flight ends at the nearest of: t_max (transient), the three-phonon
+      // clock, the two-phonon clock, the boundary; the boundary wins ties, and
+      // the three-phonon clock wins a tie with the two-phonon one
+      if (P->transient && (S.t_max_ps - t_now) * v <= d_rel && (S.t_max_ps - t_now) * v <= db &&
+          (S.t_max_ps - t_now) * v <= d2) {
+        final_seg = true; seg = (S.t_max_ps - t_now) * v; relax = false;
+      } else if (d_rel < db && d_rel <= d2) {
+        seg = d_rel; relax = true;
+      } else if (d2 < db) {
+        seg = d2; relax = false; relax2 = true;
       } else {
-        if (d_rel < db) { seg = d_rel; relax = true; }
-        else { seg = db; relax = false; }
+        seg = db; relax = false;
       }
       // ---- tallies of this flight
       if (P->transient) {
@@ -669,6 +693,7 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
         bin = alias_draw(t.relax, n, w[0], w[1], w1[0]);
         dir_about_axis(u, 2, 1.0, 1.0 - 2.0 * oc32(w[2]), w[3]);
         d_rel = t.lam_nm[bin] * (-series_log(oc53(w1[1], w1[2])));
+        d2 = draw_d2(e);
         if (P->want_grad) {
           periods.push_back({bin, -1.0, -X});
           ++n_res;
@@ -677,6 +702,15 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
         continue;
       }
       d_rel = d_rel - seg;
+      if (relax2) {
+        // same mode, new isotropic direction (Sec. 3.5.1), new two-phonon clock
+        ctr[2] = e;
+        ctr[3] = 0; philox4x32_10(ctr, k0, k1, w);
+        dir_about_axis(u, 2, 1.0, 1.0 - 2.0 * oc32(w[2]), w[3]);
+        d2 = draw_d2(e);
+        continue;
+      }
+      d2 = d2 - seg;
       if (face < 6) {
         int a = kFaceAxis[face];
         x[a] = kFaceIsMax[face] ? g.L[a] : 0.0;

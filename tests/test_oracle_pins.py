@@ -281,6 +281,63 @@ def test_kinetic_limit_bvk():
     assert abs(r["kappa"] - k) < 3.5 * r["kappa_se"]
 
 
+# ------------------------------------------------------------------ two-phonon clock (Sec. 3.3)
+def _with_imp(m, tau_imp):
+    from dataclasses import replace
+    return replace(m, tau_imp=np.asarray(tau_imp, dtype=np.float64))
+
+
+def test_two_phonon_clock_gray_slab_equals_combined_mean_free_path():
+    # gray medium: the three-phonon redraw keeps the only bin, so both
+    # processes just randomise the direction; the slab then sees one process
+    # with 1/Lambda = 1/Lambda_3 + 1/Lambda_2 (here Lambda_3 = 200 nm,
+    # Lambda_2 = 200 nm: Kn = 1 as in the one-process closed form)
+    wl = W.gray_slab_c1(n=100_000)
+    g, run = wl.geometries[0], wl.run
+    m = _with_imp(W.gray(6000.0, 200e-9, C=1e6), [200e-9 / 6000.0])
+    r = oracle.run_steady(m, g, run)
+    q_exact = cf.gray_slab_psi(1.0) * 1e6 * 6000.0 * 1.0 / 4.0
+    assert abs(r["q_mean"] - q_exact) < 3.5 * r["q_se"]
+    # the flux differs from the three-phonon process alone (Kn = 2)
+    assert abs(cf.gray_slab_psi(2.0) - cf.gray_slab_psi(1.0)) * 1e6 * 6000.0 / 4.0 > 8 * r["q_se"]
+
+
+def test_two_phonon_clock_kinetic_limit_bvk():
+    # bulk limit with the paper's impurity law tau_imp^-1 = 2e-44 omega^4:
+    # kappa = 1/3 sum C v^2 (1/tau + 1/tau_imp)^-1 (no Matthiessen rule in the
+    # tracer; the combined rate emerges from the two clocks)
+    m0 = W.bvk_holland()
+    tau_imp = 1.0 / (2e-44 * m0.omega ** 4)
+    m = _with_imp(m0, tau_imp)
+    tb = oracle.tables(m)
+    g = W.film(1e-6)
+    g.face_type = [W.PERIODIC] * 6
+    run = W.SteadyRun(n=1_000_000, seed=14, tally_axis=1, n_scat_max=2)
+    r = oracle.run_steady(m, g, run)
+    k = cf.kinetic_kappa(tb["C"], m.v, 1.0 / (1.0 / m.tau + 1.0 / tau_imp))
+    k3 = cf.kinetic_kappa(tb["C"], m.v, m.tau)
+    assert k < 0.9 * k3
+    assert abs(r["kappa"] - k) < 3.5 * r["kappa_se"]
+
+
+def test_two_phonon_events_do_not_count_toward_n_scat_max():
+    # gray, a box far larger than the mean free path (no wraps), N_scat^max = 1:
+    # the number of two-phonon events before the first three-phonon one is
+    # geometric with mean tau / tau_imp = 4, so a particle has on average
+    # 1 (emission) + 4 + 1 (the terminating relaxation) = 6 events
+    m = _with_imp(W.gray(6000.0, 100e-9, C=1e6), [25e-9 / 6000.0])
+    g = W.film(1e-3, W=1e-3)
+    g.face_type = [W.PERIODIC] * 6
+    run = W.SteadyRun(n=40_000, seed=15, tally_axis=1, n_scat_max=1)
+    r = oracle.run_steady(m, g, run, per_particle=True)
+    ev = r["events_pp"].astype(np.float64)
+    assert abs(ev.mean() - 6.0) < 4 * math.sqrt(20.0 / ev.size)
+    assert ev.min() == 2
+    # geometric law: P(k two-phonon events) = 0.8^k 0.2
+    frac0 = np.mean(ev == 2)
+    assert abs(frac0 - 0.2) < 4 * math.sqrt(0.2 * 0.8 / ev.size)
+
+
 @pytest.mark.parametrize("d", [10e-9, 100e-9, 1e-6])
 def test_fuchs_sondheimer_films_bvk(d):
     m = W.bvk_holland()
