@@ -45,7 +45,8 @@ from inputs import workloads as W  # noqa: E402
 
 METRIC = "particle-events/s and s to 1% std-err kappa_eff, batched FP32 vs plain FP64, 1 GB300"
 UNIT = "particle-events/s"
-WORKLOADS = {"si_slab": "si_slab_L1um_3000bins", "transient_box": "transient_box_2x2x1um_gauss",
+WORKLOADS = {"si_slab": "si_slab_L1um_3000bins", "si_slab_imp": "si_slab_L1um_3000bins_two_phonon_clock",
+             "transient_box": "transient_box_2x2x1um_gauss",
              "film_batch": "film_batch_64_10nm_10um", "pore_grad": "pore_film_W100nm_phi0.25_t200nm_grad"}
 # Algorithmic thread-instructions per event of the tracer (one Philox4x32-10
 # call, log + sqrt + sincos, six-plane first hit, alias draw, state update and
@@ -158,9 +159,11 @@ def _workload_setup(name, args, seed_offset):
     import torch
     tm = Timer()
     ev = (tm.k0, tm.k1)
-    if name == "si_slab":
+    if name in ("si_slab", "si_slab_imp"):
         wl = W.si_slab_c2(n=args.n_particles or 10_000_000)
         mat, geo, run = wl.material, wl.geometries[0], wl.run
+        if name == "si_slab_imp":        # separate impurity clock, tau_imp^-1 = 2e-44 omega^4 (s^-1)
+            mat = replace(mat, tau_imp=1.0 / (2e-44 * mat.omega ** 4))
         M, G = api.Material(mat), api.Geometry(geo)
         cfg = api.SteadyConfig(seed=run.seed + seed_offset, precision=L.FP32_TRACE, n_cells=run.n_cells,
                                cell_axis=2, tally_axis=2, per_bin=True, threads_per_block=args.threads,
@@ -188,7 +191,8 @@ def _workload_setup(name, args, seed_offset):
         d2h = 8 * (run.n_cells + 3 * run.n_cells + M.n_bins + L.NSTATS)
         h2d = _material_bytes(mat) + ctypes.sizeof(L.GeometryDesc) + 8
         desc = ("steady cross-plane Si-like film L=1um (1um cube, periodic x,y), BvK 3x1000 bins + Holland tau "
-                "at 300 K, walls 300+-0.5 K, 50 cells x {T, q_z} + per-bin q_z; FP32 tracing, fixed-point FP64-exact tallies")
+                "at 300 K, walls 300+-0.5 K, 50 cells x {T, q_z} + per-bin q_z; FP32 tracing, fixed-point FP64-exact tallies"
+                + ("; separate two-phonon clock, tau_imp^-1 = 2e-44 omega^4" if name == "si_slab_imp" else ""))
         launches = 3
         shape = {"threads_per_block": cfg.threads_per_block, "refill_threshold": cfg.refill_threshold}
         return dict(mat=mat, geo=geo, run=run, n=run.n, step=step, fp64=fp64, e2e=e2e, d2h=d2h, h2d=h2d, desc=desc,

@@ -81,6 +81,13 @@ typedef struct {
   const double* D;       /* [n_bins] s/(rad m^3), format 1 (used if C NULL) */
   const double* domega;  /* [n_bins] rad/s, format 1                        */
   double T_lin;          /* K, linearisation temperature (Sec. 4.4)         */
+  const double* tau_imp; /* [n_bins] s, optional two-phonon (impurity)
+                            relaxation times (the optional last column of
+                            Sec. 4.1), or NULL; each > 0, +inf for none.
+                            With it, two- and three-phonon scattering keep
+                            separate clocks (Sec. 3.3): a two-phonon event
+                            redraws the direction only; only three-phonon
+                            events count toward n_scat_max             */
 } mcbte_material_desc;
 
 typedef struct mcbte_material mcbte_material;

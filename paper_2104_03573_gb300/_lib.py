@@ -27,7 +27,8 @@ EXPORTS = [
 
 class MaterialDesc(C.Structure):
     _fields_ = [("n_bins", C.c_int), ("omega", C.c_void_p), ("v", C.c_void_p), ("tau", C.c_void_p),
-                ("C", C.c_void_p), ("D", C.c_void_p), ("domega", C.c_void_p), ("T_lin", C.c_double)]
+                ("C", C.c_void_p), ("D", C.c_void_p), ("domega", C.c_void_p), ("T_lin", C.c_double),
+                ("tau_imp", C.c_void_p)]
 
 
 class GeometryDesc(C.Structure):

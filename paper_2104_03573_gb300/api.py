@@ -38,6 +38,10 @@ class Material:
             self._keep += [D, dw]
             d.D, d.domega = D.ctypes.data, dw.ctypes.data
         d.T_lin = float(m.T_lin)
+        if getattr(m, "tau_imp", None) is not None:
+            ti = _f64(m.tau_imp)
+            self._keep.append(ti)
+            d.tau_imp = ti.ctypes.data
         h = C.c_void_p()
         L.check(lib.mcbte_material_create(C.byref(d), C.byref(h)))
         self.handle = h

@@ -107,6 +107,8 @@ mcbte_status mcbte_material_create(const mcbte_material_desc* d, mcbte_material*
       return fail(MCBTE_ERR_INVALID_ARG, "material_create: C must be >= 0");
     if (!fmt2 && !(std::isfinite(d->D[i]) && d->D[i] >= 0.0 && std::isfinite(d->domega[i]) && d->domega[i] >= 0.0))
       return fail(MCBTE_ERR_INVALID_ARG, "material_create: D and domega must be >= 0");
+    if (d->tau_imp && !(d->tau_imp[i] > 0.0))
+      return fail(MCBTE_ERR_INVALID_ARG, "material_create: tau_imp must be > 0 (+inf: no two-phonon scattering)");
   }
   Carve c;
   auto layout = [&](MatBuild& b) {
@@ -129,6 +131,9 @@ mcbte_status mcbte_material_create(const mcbte_material_desc* d, mcbte_material*
     b.inv_v = c.take<double>(n);
     b.lam = c.take<double>(n);
     b.pi = c.take<double>(n);
+    b.lam2 = c.take<double>(n);
+    double* ti = c.take<double>(n);
+    b.tau_imp = d->tau_imp ? ti : nullptr;
     b.sums = c.take<double>(4);
     b.prob = c.take<double>(3 * (size_t)n);
     b.thr = c.take<uint64_t>(3 * (size_t)n);
@@ -153,6 +158,7 @@ mcbte_status mcbte_material_create(const mcbte_material_desc* d, mcbte_material*
   cudaError_t e = cudaMemcpy((void*)b.omega, d->omega, nb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy((void*)b.v, d->v, nb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy((void*)b.tau, d->tau, nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && d->tau_imp) e = cudaMemcpy((void*)b.tau_imp, d->tau_imp, nb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && fmt2) e = cudaMemcpy((void*)b.C_in, d->C, nb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !fmt2) e = cudaMemcpy((void*)b.D, d->D, nb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !fmt2) e = cudaMemcpy((void*)b.domega, d->domega, nb, cudaMemcpyHostToDevice);
@@ -183,6 +189,8 @@ mcbte_status mcbte_material_create(const mcbte_material_desc* d, mcbte_material*
   v.lam_d = b.lam;
   v.pi = b.pi;
   v.sums = b.sums;
+  v.lam2_d = b.lam2;
+  v.imp = d->tau_imp ? 1 : 0;
   *out = m;
   return MCBTE_OK;
 }

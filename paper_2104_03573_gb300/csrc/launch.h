@@ -63,8 +63,10 @@ cudaError_t launch_finalize_transient(const GeoRun* geos, const MatView& M, cons
 struct MatBuild {
   int n;
   const double *omega, *v, *tau, *C_in, *D, *domega;
+  const double* tau_imp;   // optional two-phonon relaxation times (s), or null
   double T_lin;
   double *C, *w_emit, *w_init, *w_relax, *v_nm, *inv_v, *lam, *pi, *sums;
+  double* lam2;            // [n] v tau_imp (nm), +inf without a two-phonon clock
   double* prob;        // [3][n]
   uint64_t* thr;       // [3][n]
   int32_t* alias;      // [3][n]

@@ -56,12 +56,14 @@ struct MatView {
   const uint4* rec_emit;    // alias records ~ C v   {thr_lo, thr_hi, alias, 0}
   const uint4* rec_init;    // alias records ~ C
   const uint4* rec_relax;   // alias records ~ C / tau
-  const float4* binf;       // {v (nm/ps), 1/v (ps/nm), Lambda (nm), 0}
+  const float4* binf;       // {v (nm/ps), 1/v (ps/nm), Lambda (nm), Lambda_2 (nm, +inf: none)}
   const double* v_d;        // nm/ps
   const double* inv_v_d;    // ps/nm
   const double* lam_d;      // nm
   const double* pi;         // relaxation pmf (C/tau) / sum(C/tau)
   const double* sums;       // [3] sum C, sum C v, sum C / tau  (SI)
+  const double* lam2_d;     // nm, two-phonon mean free path v tau_imp (+inf: none)
+  int imp;                  // a two-phonon clock is present (Sec. 3.3)
 };
 
 // ------------------------------------------------------------------ Philox4x32-10
@@ -164,6 +166,7 @@ template <> struct Num<double> {
   static __device__ __forceinline__ void sincos2pi(double r, double* s, double* c) { series_sincos2pi(r, s, c); }
   static __device__ __forceinline__ double fmax_(double a, double b) { return fmax(a, b); }
   static __device__ __forceinline__ double big() { return 1.0e300; }
+  static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
 };
 
 template <> struct Num<float> {
@@ -181,6 +184,7 @@ template <> struct Num<float> {
   }
   static __device__ __forceinline__ float fmax_(float a, float b) { return fmaxf(a, b); }
   static __device__ __forceinline__ float big() { return 3.0e38f; }
+  static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
 };
 
 // Alias draw: column = floor(w * n / 2^32) (exact), keep the column iff the

@@ -36,10 +36,14 @@ __global__ void k_bins(MatBuild b) {
   const double tau_ps = b.tau[i] * 1e12;
   const double lam = v_nm * tau_ps;
   const double inv_v = 1.0 / v_nm;
+  // two-phonon mean free path (Sec. 3.3); +inf where the bin has none
+  double lam2 = __longlong_as_double(0x7ff0000000000000ll);
+  if (b.tau_imp && isfinite(b.tau_imp[i])) lam2 = v_nm * (b.tau_imp[i] * 1e12);
   b.v_nm[i] = v_nm;
   b.lam[i] = lam;
   b.inv_v[i] = inv_v;
-  b.binf[i] = make_float4((float)v_nm, (float)inv_v, (float)lam, 0.0f);
+  b.lam2[i] = lam2;
+  b.binf[i] = make_float4((float)v_nm, (float)inv_v, (float)lam, (float)lam2);
 }
 
 // blockIdx.x = 0..2 builds alias table k (weights C v, C, C / tau);

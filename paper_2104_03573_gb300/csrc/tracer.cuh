@@ -75,7 +75,8 @@ struct Acc {
 template <typename R>
 struct Particle {
   R x[3], u[3];
-  R d_rel;          // remaining relaxation distance (nm)
+  R d_rel;          // remaining relaxation distance (nm), three-phonon clock
+  R d2;             // remaining two-phonon distance (nm), +inf without that clock
   R v, inv_v, lam;  // current bin
   R t;              // ps (transient)
   R s;              // sign
@@ -103,6 +104,19 @@ __device__ __forceinline__ void load_bin(Particle<R>& p, const MatView& M, const
     p.inv_v = (R)b.y;
     p.lam = (R)b.z;
   }
+}
+
+// Two-phonon clock (Sec. 3.3): a new exponential distance with the current
+// bin's mean free path v tau_imp, from sub-block 256 of the particle's
+// current event; +inf without impurity scattering.
+template <typename R>
+__device__ __forceinline__ R draw_d2(const Particle<R>& p, const MatView& M, const float4* binf, uint32_t k0,
+                                     uint32_t k1) {
+  if (!M.imp) return Num<R>::inf();
+  const R lam2 = sizeof(R) == 8 ? (R)M.lam2_d[p.bin] : (R)binf[p.bin].w;
+  if (isinf(lam2)) return Num<R>::inf();
+  const uint4 w = philox(make_uint4(p.pid, (uint32_t)p.g, p.e, 256u), k0, k1);
+  return lam2 * (-Num<R>::log_(Num<R>::oc53(w.x, w.y)));
 }
 
 // Shared resampling step of emissions and relaxations: bin from an alias
@@ -220,7 +234,8 @@ __device__ __forceinline__ void particle_reset_counters(Particle<double>& p) {
 
 // Emission of particle (pid, g) at event 0: the emission prologue, then the
 // shared resampling step with the source's bin law and direction law.
-template <typename R>
+// IMP: the material may have a two-phonon clock (else d2 is never drawn).
+template <typename R, bool IMP = true>
 __device__ __forceinline__ void emit(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_emit,
                                      const uint4* rec_init, const float4* binf, uint32_t k0, uint32_t k1,
                                      bool transient, R t_max_ps) {
@@ -235,6 +250,7 @@ __device__ __forceinline__ void emit(Particle<R>& p, const GeoRun& g, const MatV
   emit_prologue<R>(p, g, k0, k1, transient, t_max_ps, w1, &table, &lambert, &axis, &sgn);
   resample<R>(p, M, table ? rec_init : rec_emit, binf, w, w1, lambert, axis, sgn);
   particle_reset_counters(p);
+  if constexpr (IMP) p.d2 = draw_d2(p, M, binf, k0, k1);
 }
 
 // ------------------------------------------------------------------ tally policies
@@ -374,7 +390,7 @@ struct TallyFxT {
     const float zhi = fmaxf(z0, z1);
     const int clo = min(max((int)(zlo * inv_h), 0), nc - 1);
     const int chi = min(max((int)(zhi * inv_h), 0), nc - 1);
-    const float k = p.s / fabsf(uz);      // per unit of axial length
+    const float k = copysignf(__frcp_rn(fabsf(uz)), p.s);   // s / |u_z| exactly (s = +-1): per unit axial length
     const float f0 = k * p.inv_v, f1 = k * p.u[0], f2 = k * p.u[1], f3 = k * p.u[2];
     if (clo == chi) {
       add(cP + clo * 4, f0, f1, f2, f3, zhi - zlo);
@@ -554,10 +570,11 @@ enum { STEP_ALIVE = 0, STEP_ABSORBED = 1, STEP_DONE = 2, STEP_TRUNCATED = 3 };
 // to the opposite face; adiabatic / pore: specular with probability p, else
 // Lambertian about the inward normal).  The particle has already moved.
 // `Xnow` is the particle's tally so far (gradient bookkeeping only).
-template <typename R, class Grad, class Tally>
+template <typename R, class Grad, class Tally, bool IMP = true>
 __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_relax,
                                            const float4* binf, const RunCfg& C, uint32_t k0, uint32_t k1,
-                                           bool relax, int face, R seg, const Tally& T, Grad& gr, double Xnow) {
+                                           bool relax, bool relax2, int face, R seg, const Tally& T, Grad& gr,
+                                           double Xnow) {
   ++p.e;
   uint4 ctr = make_uint4(p.pid, (uint32_t)p.g, p.e, 0u);
   if (relax) {
@@ -569,10 +586,22 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
     ctr.w = 1u;
     const uint4 w1 = philox(ctr, k0, k1);
     resample<R>(p, M, rec_relax, binf, w, w1, false, 2, R(1));
+    if constexpr (IMP) p.d2 = draw_d2(p, M, binf, k0, k1);   // both clocks restart in the new mode (Sec. 3.3 (i))
     if (Grad::on) gr.resampled(p.bin, Xnow);
     return STEP_ALIVE;
   }
   p.d_rel = p.d_rel - seg;
+  if constexpr (IMP) {
+    if (relax2) {
+      // two-phonon scattering (Sec. 3.5.1, Sec. 3.3 (ii)): same mode, new
+      // isotropic direction, new two-phonon clock; the three-phonon clock runs on
+      const uint4 w = philox(ctr, k0, k1);
+      dir_about_axis<R>(p.u, 2, R(1), R(1) - R(2) * Num<R>::oc(w.z), w.w);
+      p.d2 = draw_d2(p, M, binf, k0, k1);
+      return STEP_ALIVE;
+    }
+    p.d2 = p.d2 - seg;
+  }
   if (face < 6) {
     const int a = face_axis(face);
     const int mx = face_is_max(face);
@@ -626,7 +655,7 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
 // remaining relaxation distance (boundary wins ties, Sec. 3.3 case iii),
 // track-length tallies of the flight (Eqs. temp_steady, flux_x_steady), then
 // the event.
-template <typename R, class Grad, class Tally>
+template <typename R, class Grad, class Tally, bool IMP = true>
 __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_relax,
                                            const float4* binf, const RunCfg& C, uint32_t k0, uint32_t k1,
                                            const Tally& T, Grad& gr) {
@@ -634,15 +663,18 @@ __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, cons
   R db;
   int face;
   first_hit<R>(g, p.x, p.u, &db, &face);
-  const bool relax = p.d_rel < db;
-  const R seg = relax ? p.d_rel : db;
+  // nearest of the two scattering clocks and the boundary (Sec. 3.3): the
+  // boundary wins ties, the three-phonon clock wins a tie with the two-phonon one
+  const bool relax = IMP ? (p.d_rel < db && p.d_rel <= p.d2) : p.d_rel < db;
+  const bool relax2 = IMP && !relax && p.d2 < db;
+  const R seg = relax ? p.d_rel : (relax2 ? p.d2 : db);
   double Xb = 0.0;
   if (Grad::on) Xb = T.X(p);
   const auto c = T.segment(p, seg);
   if (Grad::on) gr.flight(relax, (double)(seg / p.lam), Xb, c);
 #pragma unroll
   for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
-  return apply_event<R, Grad, Tally>(p, g, M, rec_relax, binf, C, k0, k1, relax, face, seg, T, gr,
+  return apply_event<R, Grad, Tally, IMP>(p, g, M, rec_relax, binf, C, k0, k1, relax, relax2, face, seg, T, gr,
                                             Grad::on ? T.X(p) : 0.0);
 }
 
@@ -653,7 +685,7 @@ __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, cons
 // `tmeas`: the measurement times in ps (FP64 path: the global array; FP32
 // path: a float copy in shared memory).  `cinv`: cells per nm along x, y, z
 // (FP32 path only; the FP64 path divides by the cell size, the CPU reference form).
-template <typename R>
+template <typename R, bool IMP = true>
 __device__ __forceinline__ int step_transient(Particle<R>& p, const GeoRun& g, const MatView& M,
                                               const uint4* rec_relax, const float4* binf, const RunCfg& C,
                                               uint32_t k0, uint32_t k1, double* snap, const R* tmeas,
@@ -665,10 +697,11 @@ __device__ __forceinline__ int step_transient(Particle<R>& p, const GeoRun& g, c
   const R v = p.v;
   const R tmax = (R)C.t_max_ps;
   const R d_end = (tmax - p.t) * v;
-  bool fin = false, relax = false;
+  bool fin = false, relax = false, relax2 = false;
   R seg;
-  if (d_end <= p.d_rel && d_end <= db) { fin = true; seg = d_end; }
-  else if (p.d_rel < db) { relax = true; seg = p.d_rel; }
+  if (d_end <= p.d_rel && d_end <= db && (!IMP || d_end <= p.d2)) { fin = true; seg = d_end; }
+  else if (p.d_rel < db && (!IMP || p.d_rel <= p.d2)) { relax = true; seg = p.d_rel; }
+  else if (IMP && p.d2 < db) { relax2 = true; seg = p.d2; }
   else { seg = db; }
   // the flight ended by t_max ends at t_max exactly (Sec. 3.5.6), so a
   // measurement at t_max samples every particle still alive
@@ -726,7 +759,7 @@ __device__ __forceinline__ int step_transient(Particle<R>& p, const GeoRun& g, c
   for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
   if (fin) return STEP_DONE;
   GradOff off;
-  return apply_event<R, GradOff, TallyNone>(p, g, M, rec_relax, binf, C, k0, k1, relax, face, seg, TallyNone(), off,
+  return apply_event<R, GradOff, TallyNone, IMP>(p, g, M, rec_relax, binf, C, k0, k1, relax, relax2, face, seg, TallyNone(), off,
                                             0.0);
 }
 

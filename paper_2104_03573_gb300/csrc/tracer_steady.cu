@@ -178,7 +178,7 @@ __device__ __forceinline__ void grad_finish_replay(GradReplay& gr, double X, int
 // only, and flags (bit 2) any particle whose replayed tally differs.
 // CELLS: 0 no cell tallies, 1 T and three flux components, 2 T and the
 // tally-axis flux only.
-template <int CELLS, bool GRAD, int TPB>
+template <int CELLS, bool GRAD, int TPB, bool IMP>
 __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict__ geos,
                                                        const uint64_t* __restrict__ offs, MatView M, RunCfg C,
                                                        Acc A, SmemPlan S) {
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
         G = &geos[g];
         p.pid = (uint32_t)(idx - offs[g]);
         p.g = g;
-        emit<float>(p, *G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, false, 0.0f);
+        emit<float, IMP>(p, *G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, false, 0.0f);
         if constexpr (GRAD) {
           gr.init(p.bin);
           gr.Xf = A.X_pp[idx];
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
       }
     }
     if (!alive) continue;
-    int out = step_steady<float, typename GradPick<GRAD, GradReplay>::type, decltype(T)>(p, *G, M, relax, binf, C, key.x,
+    int out = step_steady<float, typename GradPick<GRAD, GradReplay>::type, decltype(T), IMP>(p, *G, M, relax, binf, C, key.x,
                                                                                   key.y, T, gr);
     if (out == STEP_ALIVE && (p.e & 255u) == 0u && globaltimer_ns() > deadline) {
       atomicOr(A.flags, 1);
@@ -449,11 +449,11 @@ cudaError_t launch_f64(const GeoRun* geos, const uint64_t* offs, const MatView& 
 #endif  // MCBTE_F64
 
 #if MCBTE_F32
-template <int CELLS, bool GRAD, int TPB>
+template <int CELLS, bool GRAD, int TPB, bool IMP>
 cudaError_t launch_f32_tpb(const GeoRun* geos, const uint64_t* offs, const MatView& M, const RunCfg& C,
                            const Acc& A, int bps, cudaStream_t s) {
   const SmemPlan S = plan_smem_f32(M.n, C.n_geoms, GRAD ? 0 : C.n_cells, GRAD ? 0 : C.per_bin, 200 * 1024);
-  auto kern = k_steady_f32<CELLS, GRAD, TPB>;
+  auto kern = k_steady_f32<CELLS, GRAD, TPB, IMP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.bytes);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -465,16 +465,24 @@ cudaError_t launch_f32_tpb(const GeoRun* geos, const uint64_t* offs, const MatVi
   return cudaGetLastError();
 }
 
+template <int CELLS, bool GRAD, bool IMP>
+cudaError_t launch_f32_imp(const GeoRun* geos, const uint64_t* offs, const MatView& M, const RunCfg& C, const Acc& A,
+                           int threads, int bps, cudaStream_t s) {
+  switch (threads) {
+    case 256: return launch_f32_tpb<CELLS, GRAD, 256, IMP>(geos, offs, M, C, A, bps, s);
+    case 512: return launch_f32_tpb<CELLS, GRAD, 512, IMP>(geos, offs, M, C, A, bps, s);
+    case 768: return launch_f32_tpb<CELLS, GRAD, 768, IMP>(geos, offs, M, C, A, bps, s);
+    case 1024: return launch_f32_tpb<CELLS, GRAD, 1024, IMP>(geos, offs, M, C, A, bps, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// The two-phonon clock is compiled in only for materials that have one.
 template <int CELLS, bool GRAD>
 cudaError_t launch_f32(const GeoRun* geos, const uint64_t* offs, const MatView& M, const RunCfg& C, const Acc& A,
                        int threads, int bps, cudaStream_t s) {
-  switch (threads) {
-    case 256: return launch_f32_tpb<CELLS, GRAD, 256>(geos, offs, M, C, A, bps, s);
-    case 512: return launch_f32_tpb<CELLS, GRAD, 512>(geos, offs, M, C, A, bps, s);
-    case 768: return launch_f32_tpb<CELLS, GRAD, 768>(geos, offs, M, C, A, bps, s);
-    case 1024: return launch_f32_tpb<CELLS, GRAD, 1024>(geos, offs, M, C, A, bps, s);
-    default: return cudaErrorInvalidValue;
-  }
+  return M.imp ? launch_f32_imp<CELLS, GRAD, true>(geos, offs, M, C, A, threads, bps, s)
+               : launch_f32_imp<CELLS, GRAD, false>(geos, offs, M, C, A, threads, bps, s);
 }
 #endif  // MCBTE_F32
 
@@ -482,17 +490,11 @@ cudaError_t launch_f32(const GeoRun* geos, const uint64_t* offs, const MatView& 
 
 #if MCBTE_F64
 SmemPlan plan_smem_f32(int n_bins, int n_geoms, int n_cells, int per_bin, size_t budget) {
+  // By use per event: the relaxation alias records and the per-bin
+  // constants (every relaxation), the cell tallies (every flight), the
+  // per-bin flux (every relaxation period); each is placed while room remains.
   SmemPlan S{0, 0, 0, 0, 0};
   size_t used = 0;
-  const size_t cells = (size_t)(n_cells * 4 + (n_cells + 1) * 4) * sizeof(long long);
-  if (n_cells > 0 && n_geoms == 1 && cells <= 16 * 1024) {
-    S.cells_in_smem = 1;
-    used += cells;
-  }
-  if (per_bin && n_geoms == 1 && used + (size_t)n_bins * 8 <= budget / 3) {
-    S.qbin_in_smem = 1;
-    used += (size_t)n_bins * 8;
-  }
   if (used + (size_t)n_bins * 16 <= budget) {
     S.relax_in_smem = 1;
     used += (size_t)n_bins * 16;
@@ -500,6 +502,15 @@ SmemPlan plan_smem_f32(int n_bins, int n_geoms, int n_cells, int per_bin, size_t
   if (used + (size_t)n_bins * 16 <= budget) {
     S.binf_in_smem = 1;
     used += (size_t)n_bins * 16;
+  }
+  const size_t cells = (size_t)(n_cells * 4 + (n_cells + 1) * 4) * sizeof(long long);
+  if (n_cells > 0 && n_geoms == 1 && used + cells <= budget) {
+    S.cells_in_smem = 1;
+    used += cells;
+  }
+  if (per_bin && n_geoms == 1 && used + (size_t)n_bins * 8 <= budget) {
+    S.qbin_in_smem = 1;
+    used += (size_t)n_bins * 8;
   }
   S.bytes = used;
   return S;

@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(256) k_transient_fp64(const GeoRun* __restrict
 #endif  // MCBTE_F64
 #if MCBTE_F32
 // Particle state between time windows, 48 bytes: {x, t}, {u, d_rel},
-// {event index, bin | sign bit, next measurement index, relaxations | live bit}.
+// {event index, bin | sign bit, next measurement index | live bit, d2}
+// (transient runs have no N_scat^max, so the relaxation count is not kept).
 // Streaming (evict-first) accesses keep the window's tally slice in L2.
 constexpr uint32_t kLive = 0x80000000u;
 
@@ -80,8 +81,8 @@ __device__ __forceinline__ void save_state(uint4* st, uint64_t idx, const Partic
                            __float_as_uint(p.t)));
   __stcs(q + 1, make_uint4(__float_as_uint(p.u[0]), __float_as_uint(p.u[1]), __float_as_uint(p.u[2]),
                            __float_as_uint(p.d_rel)));
-  __stcs(q + 2, make_uint4(p.e, (uint32_t)p.bin | (p.s < 0.0f ? 0x80000000u : 0u), (uint32_t)p.mi,
-                           (uint32_t)p.n_relax | kLive));
+  __stcs(q + 2, make_uint4(p.e, (uint32_t)p.bin | (p.s < 0.0f ? 0x80000000u : 0u), (uint32_t)p.mi | kLive,
+                           __float_as_uint(p.d2)));
 }
 
 __device__ __forceinline__ void mark_done(uint4* st, uint64_t idx) { __stcs(st + idx * 3 + 2, make_uint4(0, 0, 0, 0)); }
@@ -92,8 +93,8 @@ __device__ __forceinline__ bool load_state(const uint4* st, uint64_t idx, Partic
                                            const float4* binf, const RunCfg& C) {
   const uint4* q = st + idx * 3;
   const uint4 c = __ldcs(q + 2);
-  if (!(c.w & kLive)) return false;
-  if (!C.win_last && (int)c.z >= C.win_end) return false;
+  if (!(c.z & kLive)) return false;
+  if (!C.win_last && (int)(c.z & ~kLive) >= C.win_end) return false;
   const uint4 a = __ldcs(q + 0);
   const uint4 b = __ldcs(q + 1);
   p.x[0] = __uint_as_float(a.x);
@@ -107,8 +108,9 @@ __device__ __forceinline__ bool load_state(const uint4* st, uint64_t idx, Partic
   p.e = c.x;
   p.bin = (int)(c.y & 0x7fffffffu);
   p.s = (c.y & 0x80000000u) ? -1.0f : 1.0f;
-  p.mi = (int)c.z;
-  p.n_relax = (int)(c.w & ~kLive);
+  p.mi = (int)(c.z & ~kLive);
+  p.d2 = __uint_as_float(c.w);
+  p.n_relax = 0;
   p.pid = (uint32_t)idx;
   p.g = 0;
   load_bin(p, M, binf);
@@ -117,7 +119,7 @@ __device__ __forceinline__ bool load_state(const uint4* st, uint64_t idx, Partic
 
 // Shared memory: the measurement times as float (always), then the relaxation
 // alias records and per-bin constants where the plan has room.
-template <int TPB>
+template <int TPB, bool IMP>
 __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restrict__ geos, MatView M, RunCfg C,
                                                           Acc A, SmemPlan S) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
         if (C.win_first) {
           p.pid = (uint32_t)idx;
           p.g = 0;
-          emit<float>(p, G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, true, (float)C.t_max_ps);
+          emit<float, IMP>(p, G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, true, (float)C.t_max_ps);
           transient_start(p, C);
           if (!C.win_last && p.mi >= C.win_end) {   // emitted after this window's last snapshot
             save_state(A.tstate, idx, p);
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
       }
     }
     if (!alive) continue;
-    int out = step_transient<float>(p, G, M, relax, binf, C, key.x, key.y, A.snap, tmeas, cinv);
+    int out = step_transient<float, IMP>(p, G, M, relax, binf, C, key.x, key.y, A.snap, tmeas, cinv);
     if (out == STEP_ALIVE && (p.e & 255u) == 0u && globaltimer_ns() > deadline) {
       atomicOr(A.flags, 1);
       out = STEP_TRUNCATED;
@@ -272,13 +274,13 @@ cudaError_t launch_transient(int precision, const GeoRun* geos, const MatView& M
 #endif  // MCBTE_F64
 #if MCBTE_F32
 namespace {
-template <int TPB>
+template <int TPB, bool IMP>
 cudaError_t launch_transient_tpb(const GeoRun* geos, const MatView& M, const RunCfg& C, const Acc& A, int bps,
                                  cudaStream_t s) {
   const size_t tm_bytes = ((size_t)C.n_times * sizeof(float) + 15) & ~(size_t)15;
   SmemPlan S = plan_smem_f32(M.n, 1, 0, 0, 200 * 1024 - tm_bytes);
   S.bytes += tm_bytes;
-  auto kern = k_transient_f32<TPB>;
+  auto kern = k_transient_f32<TPB, IMP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.bytes);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -293,11 +295,16 @@ cudaError_t launch_transient_tpb(const GeoRun* geos, const MatView& M, const Run
 
 cudaError_t launch_transient_f32(const GeoRun* geos, const MatView& M, const RunCfg& C, const Acc& A, int threads,
                                  int bps, cudaStream_t s) {
+  const bool imp = M.imp != 0;   // the two-phonon clock is compiled in only when present
   switch (threads) {
-    case 256: return launch_transient_tpb<256>(geos, M, C, A, bps, s);
-    case 512: return launch_transient_tpb<512>(geos, M, C, A, bps, s);
-    case 768: return launch_transient_tpb<768>(geos, M, C, A, bps, s);
-    case 1024: return launch_transient_tpb<1024>(geos, M, C, A, bps, s);
+    case 256: return imp ? launch_transient_tpb<256, true>(geos, M, C, A, bps, s)
+                         : launch_transient_tpb<256, false>(geos, M, C, A, bps, s);
+    case 512: return imp ? launch_transient_tpb<512, true>(geos, M, C, A, bps, s)
+                         : launch_transient_tpb<512, false>(geos, M, C, A, bps, s);
+    case 768: return imp ? launch_transient_tpb<768, true>(geos, M, C, A, bps, s)
+                         : launch_transient_tpb<768, false>(geos, M, C, A, bps, s);
+    case 1024: return imp ? launch_transient_tpb<1024, true>(geos, M, C, A, bps, s)
+                          : launch_transient_tpb<1024, false>(geos, M, C, A, bps, s);
     default: return cudaErrorInvalidValue;
   }
 }

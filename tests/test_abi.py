@@ -83,6 +83,16 @@ def test_material_validation_rejects_before_cuda(lib):
     d.n_bins = n
     d.C = None
     assert lib.mcbte_material_create(C.byref(d), C.byref(h)) == _lib.ERR_INVALID_ARG
+    # two-phonon times must be > 0 (+inf allowed)
+    v[1] = 1.5e3
+    d.C = Cc.ctypes.data
+    bad_imp = np.array([1e-12, np.inf, 0.0])
+    d.tau_imp = bad_imp.ctypes.data
+    assert lib.mcbte_material_create(C.byref(d), C.byref(h)) == _lib.ERR_INVALID_ARG
+    bad_imp[2] = -1.0
+    assert lib.mcbte_material_create(C.byref(d), C.byref(h)) == _lib.ERR_INVALID_ARG
+    bad_imp[2] = np.nan
+    assert lib.mcbte_material_create(C.byref(d), C.byref(h)) == _lib.ERR_INVALID_ARG
 
 
 def test_null_arguments_rejected(lib):

@@ -89,6 +89,63 @@ def test_fp64_bvk_slab_per_bin():
                  "q_bin": gg["q_bin"][0]}, ref, tallies=("T", "q", "q_bin"))
 
 
+def _with_imp(m, law=lambda w: 1.0 / (2e-44 * w ** 4)):
+    return replace(m, tau_imp=np.asarray(law(np.asarray(m.omega, dtype=np.float64)), dtype=np.float64))
+
+
+def test_fp64_two_phonon_clock_slab_per_particle():
+    # separate two- and three-phonon clocks (Sec. 3.3) with the paper's
+    # impurity law; a few bins without impurity scattering (+inf)
+    wl = W.si_slab_c2(n=20_000)
+    g, run = wl.geometries[0], wl.run
+    mat = _with_imp(wl.material)
+    mat.tau_imp[::97] = np.inf
+    gg = gpu_steady(mat, [g], [run.n], run, L.FP64_PLAIN, per_particle=True)
+    ref = oracle.run_steady(mat, g, run, per_particle=True)
+    _check_fp64({"events_pp": gg["events_pp"], "X_pp": gg["X_pp"], "T": gg["T"][0], "q": gg["q"][0],
+                 "q_bin": gg["q_bin"][0]}, ref, tallies=("T", "q", "q_bin"))
+    plain = oracle.run_steady(wl.material, g, run, per_particle=True)
+    assert ref["events"] > 1.05 * plain["events"]          # the clock adds events
+
+
+def test_fp64_two_phonon_clock_transient_and_gradient():
+    wl = W.transient_box_c3(n=3000, grid=(16, 16, 8), n_times=20)
+    g, run = wl.geometries[0], wl.run
+    mat = _with_imp(wl.material)
+    gg = gpu_transient(mat, g, run, L.FP64_PLAIN, per_particle=True)
+    ref = oracle.run_transient(mat, g, run, per_particle=True)
+    assert np.array_equal(gg["events_pp"], ref["events_pp"])
+    ok, err = rel_close(gg["tally"], ref["tally"], RTOL)
+    assert ok, err
+    # gradient: flights ended by the two-phonon clock are censored for tau
+    wp = W.pore_film_c5(n=3000, p_pore=0.3)
+    gp, rp = wp.geometries[0], wp.run
+    rp.max_events = 2_000_000
+    mp = _with_imp(wp.material)
+    cfg = api.SteadyConfig(seed=rp.seed, precision=L.FP64_PLAIN, n_scat_max=rp.n_scat_max,
+                           max_events=rp.max_events, tally_axis=rp.tally_axis, per_bin=True)
+    fwd, go = api.grad(api.Material(mp), api.Geometry(gp), rp.n, cfg)
+    torch.cuda.synchronize()
+    rg = oracle.run_steady(mp, gp, rp, grad=True)
+    ok, err = rel_close(go.dkappa_dlogtau.cpu().numpy(), rg["dkappa_dlogtau"], RTOL)
+    assert ok, err
+    assert fwd.stats[0, L.STAT_KAPPA].item() == pytest.approx(rg["kappa"], rel=RTOL)
+
+
+def test_fp32_two_phonon_clock_kappa_vs_oracle():
+    wl = W.pore_film_c5(n=300_000)
+    g, run = wl.geometries[0], wl.run
+    mat = _with_imp(wl.material)
+    run.max_events = 10 ** 8
+    gg = gpu_steady(mat, [g], [run.n], run, L.FP32_TRACE, seed=901)
+    ref = oracle.run_steady(mat, g, run)
+    k, se = gg["stats"][0][L.STAT_KAPPA], gg["stats"][0][L.STAT_KAPPA_SE]
+    assert gg["stats"][0][L.STAT_STATUS] == 0
+    assert abs(k - ref["kappa"]) < 3.5 * np.hypot(se, ref["kappa_se"])
+    plain = oracle.run_steady(wl.material, g, run)
+    assert ref["kappa"] < plain["kappa"] - 5 * np.hypot(ref["kappa_se"], plain["kappa_se"])
+
+
 def test_fp64_film_batch_geometry_index_streams():
     wl = W.film_batch_c4(n_films=6)
     mat = wl.material

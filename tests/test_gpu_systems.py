@@ -239,12 +239,15 @@ def test_fp32_gradient_forward_equals_plain_run_and_is_reproducible():
     assert torch.equal(g1.dkappa_dlogtau, g2.dkappa_dlogtau)
 
 
-@pytest.mark.parametrize("case", ["gauss_box", "walls"])
+@pytest.mark.parametrize("case", ["gauss_box", "walls", "two_phonon"])
 def test_fp32_transient_time_windows_change_nothing(case):
     # windows hold whole flights and park particles at events, so any window
     # size reproduces the one-pass trajectories and integer tallies exactly
-    if case == "gauss_box":
+    if case in ("gauss_box", "two_phonon"):
         wl = W.transient_box_c3(n=300_000, grid=(16, 16, 8), n_times=23)
+        if case == "two_phonon":       # the parked state carries the two-phonon clock
+            from dataclasses import replace
+            wl.material = replace(wl.material, tau_imp=1.0 / (2e-44 * wl.material.omega ** 4))
     else:       # wall sources emit at t0 = R t_max; particles are absorbed mid-window
         wl = W.ballistic_transient_e1(n=300_000)
         wl.material.tau[:] = 20e-12
