@@ -43,6 +43,7 @@ class Material:
     T_lin: float = 300.0
     name: str = ""
     tau_imp: Optional[np.ndarray] = None  # s, optional two-phonon (impurity) relaxation times
+    spec_bin: Optional[np.ndarray] = None  # optional per-bin specularity d(omega) in [0, 1]
 
     @property
     def n_bins(self) -> int:
@@ -105,6 +106,12 @@ class Geometry:
     gauss_c: Sequence[float] = (0.0, 0.0, 0.0)
     gauss_sigma: float = 0.0
     gauss_dT: float = 0.0
+    # internal boundaries (Sec. 4.2): segments (x1, y1, x2, y2) in m in the x-y
+    # plane through the thickness, unit normals (nx, ny) into the solid, and
+    # specularities (< 0: the material's per-bin specularity)
+    inner: Sequence[Sequence[float]] = ()
+    inner_n: Sequence[Sequence[float]] = ()
+    inner_p: Sequence[float] = ()
 
 
 def slab_z(L: float, T_hot: float, T_cold: float, T_eq: float = 300.0,
@@ -142,6 +149,19 @@ def pore_lattice(W: float, porosity: float, thickness: float, p_pore: float = 0.
     g.pore_c = (0.5 * W, 0.5 * W)
     g.pore_r = W * math.sqrt(porosity / math.pi)
     g.pore_p = p_pore
+    return g
+
+
+def nanomesh(W: float = 34e-9, pore: float = 11e-9, thickness: float = 22e-9, p_pore: float = 0.0,
+             p_faces: float = 0.0, grad_y: float = -1.0e6, T_eq: float = 300.0) -> Geometry:
+    """Square-pore nanomesh unit cell of Sec. 5.5: W x W, periodic in x and y,
+    a square pore of side `pore` at the centre through the thickness, given as
+    four internal walls with normals pointing away from the pore."""
+    g = film(thickness, W=W, p=p_faces, grad_y=grad_y, T_eq=T_eq)
+    a, b = 0.5 * (W - pore), 0.5 * (W + pore)
+    g.inner = [(a, a, b, a), (b, a, b, b), (b, b, a, b), (a, b, a, a)]
+    g.inner_n = [(0.0, -1.0), (1.0, 0.0), (0.0, 1.0), (-1.0, 0.0)]
+    g.inner_p = [p_pore] * 4
     return g
 
 

@@ -39,12 +39,14 @@ class _Params(C.Structure):
     _fields_ = [
         ("n_bins", C.c_int), ("omega", C.c_void_p), ("v", C.c_void_p), ("tau", C.c_void_p),
         ("C", C.c_void_p), ("D", C.c_void_p), ("domega", C.c_void_p), ("T_lin", C.c_double),
-        ("tau_imp", C.c_void_p),
+        ("tau_imp", C.c_void_p), ("spec_bin", C.c_void_p),
         ("L", C.c_double * 3), ("face_type", C.c_int * 6), ("face_T", C.c_double * 6),
         ("face_p", C.c_double * 6), ("T_eq", C.c_double), ("grad_T", C.c_double * 3),
         ("pore", C.c_int), ("pore_c", C.c_double * 2), ("pore_r", C.c_double), ("pore_p", C.c_double),
         ("gauss", C.c_int), ("gauss_c", C.c_double * 3), ("gauss_sigma", C.c_double),
         ("gauss_dT", C.c_double),
+        ("n_inner", C.c_int), ("inner", (C.c_double * 4) * 16), ("inner_n", (C.c_double * 2) * 16),
+        ("inner_p", C.c_double * 16),
         ("seed", C.c_uint64), ("batch_index", C.c_uint32), ("transient", C.c_int),
         ("n_particles", C.c_uint64), ("pid_begin", C.c_uint64), ("pid_end", C.c_uint64),
         ("n_scat_max", C.c_int), ("max_events", C.c_uint64),
@@ -121,6 +123,17 @@ class _Keep:
         return a
 
 
+def _set_inner(P, geom) -> None:
+    inner = list(getattr(geom, "inner", ()) or ())
+    if len(inner) > 16:
+        raise ValueError("at most 16 internal boundaries")
+    P.n_inner = len(inner)
+    for k, seg in enumerate(inner):
+        P.inner[k][:] = [float(c) for c in seg]
+        P.inner_n[k][:] = [float(c) for c in geom.inner_n[k]]
+        P.inner_p[k] = float(geom.inner_p[k])
+
+
 def _params(material, geom, keep: _Keep, **kw) -> _Params:
     P = _Params()
     P.n_bins = material.n_bins
@@ -134,6 +147,8 @@ def _params(material, geom, keep: _Keep, **kw) -> _Params:
     P.T_lin = material.T_lin
     if getattr(material, "tau_imp", None) is not None:
         P.tau_imp = _ptr(keep.add(_f64(material.tau_imp)))
+    if getattr(material, "spec_bin", None) is not None:
+        P.spec_bin = _ptr(keep.add(_f64(material.spec_bin)))
     if geom is not None:
         P.L[:] = [float(x) for x in geom.L]
         P.face_type[:] = [int(x) for x in geom.face_type]
@@ -149,6 +164,7 @@ def _params(material, geom, keep: _Keep, **kw) -> _Params:
         P.gauss_c[:] = [float(x) for x in geom.gauss_c]
         P.gauss_sigma = geom.gauss_sigma
         P.gauss_dT = geom.gauss_dT
+        _set_inner(P, geom)
     for k, val in kw.items():
         setattr(P, k, val)
     return P
@@ -221,6 +237,17 @@ def first_hit(geom, x_nm, u):
     d = C.c_double(0); f = C.c_int(0)
     lib().or_first_hit(C.byref(P), x.ctypes.data, uu.ctypes.data, C.byref(d), C.byref(f))
     return d.value, f.value
+
+
+def in_hole(geom, x_nm: float, y_nm: float) -> bool:
+    """True if (x, y) in nm lies inside a hole bounded by the internal walls."""
+    keep = _Keep()
+    from inputs.workloads import gray
+    P = _params(gray(1.0, 1.0), geom, keep)
+    f = lib().or_in_hole
+    f.argtypes = [C.c_void_p, C.c_double, C.c_double]
+    f.restype = C.c_int
+    return bool(f(C.byref(P), float(x_nm), float(y_nm)))
 
 
 def _kappa_gradient(geom, axis: int) -> float:

@@ -217,6 +217,7 @@ typedef struct {
   const double* domega;   // format 1
   double T_lin;
   const double* tau_imp;  // optional two-phonon (impurity) relaxation times, or NULL (Sec. 3.3, Sec. 4.1)
+  const double* spec_bin; // optional per-bin specularity d(omega) in [0, 1] (Sec. 3.5.3), or NULL
   // geometry (SI)
   double L[3];
   int face_type[6];       // 0 isothermal, 1 adiabatic, 2 periodic
@@ -232,6 +233,12 @@ typedef struct {
   double gauss_c[3];
   double gauss_sigma;
   double gauss_dT;
+  // internal boundaries (Sec. 4.2): segments in the x-y plane through the
+  // thickness, normal pointing into the solid, specularity (< 0: per bin)
+  int n_inner;
+  double inner[16][4];    // x1, y1, x2, y2 (m)
+  double inner_n[16][2];
+  double inner_p[16];
   // run
   uint64_t seed;
   uint32_t batch_index;
@@ -276,11 +283,18 @@ typedef struct {
 
 namespace {
 
+uint64_t spec_threshold(double p) {
+  if (p <= 0.0) return 0;
+  if (p >= 1.0) return (uint64_t)1 << 32;
+  return (uint64_t)(p * 4294967296.0);
+}
+
 struct Tables {
   int n = 0;
   std::vector<double> C, v_nm, lam_nm, inv_v, pi_relax;
   bool imp = false;              // a two-phonon clock is present
   std::vector<double> lam2_nm;   // v tau_imp (nm); +inf for bins without impurity scattering
+  std::vector<uint64_t> spec_thr_bin;  // per-bin specular thresholds (empty without d(omega))
   double C_tot = 0, sum_Cv = 0, sum_Ct = 0;
   Alias emit, init, relax;
 };
@@ -317,6 +331,10 @@ int build_tables(const or_params* P, Tables& t) {
     t.inv_v[i] = 1.0 / t.v_nm[i];
     t.pi_relax[i] = w_relax[i] / t.sum_Ct;
   }
+  if (P->spec_bin) {
+    t.spec_thr_bin.resize(n);
+    for (int i = 0; i < n; ++i) t.spec_thr_bin[i] = spec_threshold(P->spec_bin[i]);
+  }
   t.imp = P->tau_imp != nullptr;
   t.lam2_nm.assign(n, std::numeric_limits<double>::infinity());
   if (t.imp)
@@ -338,14 +356,28 @@ struct Geo {
   bool pore;
   double cx, cy, r, r2, p_pore;
   uint64_t pthr_pore;
+  bool fbin[6];             // outer face uses the per-bin specularity
+  int n_inner;
+  double sx1[16], sy1[16], sx2[16], sy2[16], snx[16], sny[16];   // nm
+  uint64_t sthr[16];
+  bool sbin[16];
   double V_solid_m3;
 };
 
-uint64_t spec_threshold(double p) {
-  if (p <= 0.0) return 0;
-  if (p >= 1.0) return (uint64_t)1 << 32;
-  return (uint64_t)(p * 4294967296.0);
+// Inside a hole bounded by the internal segments: even-odd count of the
+// segments crossed by the ray from (x, y) towards +x.
+inline bool in_hole(const Geo& g, double x, double y) {
+  bool c = false;
+  for (int k = 0; k < g.n_inner; ++k) {
+    const double y1 = g.sy1[k], y2 = g.sy2[k];
+    if ((y1 > y) != (y2 > y)) {
+      const double xc = g.sx1[k] + ((y - y1) * (g.sx2[k] - g.sx1[k])) / (y2 - y1);
+      if (x < xc) c = !c;
+    }
+  }
+  return c;
 }
+
 
 struct Source {
   int kind;   // 0 face, 1 body, 2 gauss
@@ -372,7 +404,27 @@ int setup(const or_params* P, const Tables& t, Setup& S) {
   for (int f = 0; f < 6; ++f) {
     g.type[f] = P->face_type[f];
     g.Tb[f] = P->face_T[f];
+    g.fbin[f] = P->face_p[f] < 0.0;
     g.pthr[f] = spec_threshold(P->face_p[f]);
+  }
+  g.n_inner = P->n_inner;
+  double hole_area = 0.0;   // m^2: segments oriented with the solid on their right
+  for (int k = 0; k < g.n_inner; ++k) {
+    double x1 = P->inner[k][0], y1 = P->inner[k][1], x2 = P->inner[k][2], y2 = P->inner[k][3];
+    const double nx = P->inner_n[k][0], ny = P->inner_n[k][1];
+    if ((y2 - y1) * nx - (x2 - x1) * ny < 0.0) {
+      std::swap(x1, x2);
+      std::swap(y1, y2);
+    }
+    hole_area += 0.5 * (x1 * y2 - x2 * y1);
+    g.sx1[k] = x1 * 1e9; g.sy1[k] = y1 * 1e9; g.sx2[k] = x2 * 1e9; g.sy2[k] = y2 * 1e9;
+    g.snx[k] = nx; g.sny[k] = ny;
+    g.sbin[k] = P->inner_p[k] < 0.0;
+    g.sthr[k] = spec_threshold(P->inner_p[k]);
+  }
+  if (P->spec_bin == nullptr) {   // a per-bin specularity needs the material's d(omega)
+    for (int f = 0; f < 6; ++f) if (g.fbin[f] && g.type[f] == 1) return 5;
+    for (int k = 0; k < g.n_inner; ++k) if (g.sbin[k]) return 5;
   }
   g.pore = P->pore != 0;
   g.cx = P->pore_c[0] * 1e9;
@@ -383,6 +435,7 @@ int setup(const or_params* P, const Tables& t, Setup& S) {
   g.pthr_pore = spec_threshold(P->pore_p);
   double V = P->L[0] * P->L[1] * P->L[2];
   if (g.pore) V = V - (3.141592653589793 * (P->pore_r * P->pore_r)) * P->L[2];
+  if (g.n_inner > 0) V = V - hole_area * P->L[2];
   g.V_solid_m3 = V;
   // sources, in order: isothermal faces by ID, body, initial condition
   const double time_factor = P->transient ? P->t_max : 1.0;
@@ -464,6 +517,21 @@ inline void first_hit(const Geo& g, const double x[3], const double u[3], double
       }
     }
   }
+  // internal walls (IDs 8, 9, ...): only approached from the solid side
+  for (int k = 0; k < g.n_inner; ++k) {
+    const double un = u[0] * g.snx[k] + u[1] * g.sny[k];
+    if (!(un < 0.0)) continue;
+    // behind the wall's line (beyond the hole): not this wall; on it within
+    // rounding (after a hit the particle is projected onto the line): d = 0
+    const double dn = (x[0] - g.sx1[k]) * g.snx[k] + (x[1] - g.sy1[k]) * g.sny[k];
+    if (dn < -1e-9) continue;
+    double d = dn / (-un);
+    if (d < 0.0) d = 0.0;
+    const double tx = g.sx2[k] - g.sx1[k], ty = g.sy2[k] - g.sy1[k];
+    const double hs = ((x[0] + d * u[0]) - g.sx1[k]) * tx + ((x[1] + d * u[1]) - g.sy1[k]) * ty;
+    if (hs < 0.0 || hs > tx * tx + ty * ty) continue;
+    if (d < best) { best = d; bf = 7 + k; }
+  }
   *dist = best;
   *face = bf;
 }
@@ -540,9 +608,13 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
         x[0] = mid32(w3[0]) * g.L[0];
         x[1] = mid32(w3[1]) * g.L[1];
         x[2] = mid32(w3[2]) * g.L[2];
-        if (!g.pore) break;
-        double dx = x[0] - g.cx, dy = x[1] - g.cy;
-        if (dx * dx + dy * dy >= g.r2) break;
+        bool inside = false;
+        if (g.pore) {
+          double dx = x[0] - g.cx, dy = x[1] - g.cy;
+          inside = dx * dx + dy * dy < g.r2;
+        }
+        if (!inside && g.n_inner > 0) inside = in_hole(g, x[0], x[1]);
+        if (!inside) break;
         if (j + 1 >= 64) break;   // unreachable for porosities the API accepts
       }
     } else {
@@ -724,11 +796,34 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
         } else {
           ctr[2] = e;
           ctr[3] = 0; philox4x32_10(ctr, k0, k1, w);
-          if ((uint64_t)w[0] < g.pthr[face]) {
+          if ((uint64_t)w[0] < (g.fbin[face] ? t.spec_thr_bin[bin] : g.pthr[face])) {
             u[a] = -u[a];
           } else {
             dir_about_axis(u, a, kFaceIsMax[face] ? -1.0 : 1.0, std::sqrt(oc32(w[2])), w[3]);
           }
+        }
+      } else if (face >= 7) {
+        // internal wall: onto its line, then specular or Lambertian about its normal
+        const int k = face - 7;
+        const double nx0 = g.snx[k], ny0 = g.sny[k];
+        const double dn = (x[0] - g.sx1[k]) * nx0 + (x[1] - g.sy1[k]) * ny0;
+        x[0] = x[0] - dn * nx0;
+        x[1] = x[1] - dn * ny0;
+        ctr[2] = e;
+        ctr[3] = 0; philox4x32_10(ctr, k0, k1, w);
+        if ((uint64_t)w[0] < (g.sbin[k] ? t.spec_thr_bin[bin] : g.sthr[k])) {
+          double un = u[0] * nx0 + u[1] * ny0;
+          u[0] = u[0] - (2.0 * un) * nx0;
+          u[1] = u[1] - (2.0 * un) * ny0;
+        } else {
+          double mu = std::sqrt(oc32(w[2]));
+          double sn = std::sqrt(std::max(0.0, 1.0 - mu * mu));
+          double sphi, cphi;
+          series_sincos2pi(co32(w[3]), &sphi, &cphi);
+          double sc = sn * cphi;
+          u[0] = mu * nx0 - sc * ny0;
+          u[1] = mu * ny0 + sc * nx0;
+          u[2] = sn * sphi;
         }
       } else {
         // pore wall: outward normal of the cylinder points into the solid
@@ -841,8 +936,25 @@ int or_first_hit(const or_params* P, const double x[3], const double u[3], doubl
   for (int a = 0; a < 3; ++a) g.L[a] = P->L[a] * 1e9;
   g.pore = P->pore != 0;
   g.cx = P->pore_c[0] * 1e9; g.cy = P->pore_c[1] * 1e9; g.r = P->pore_r * 1e9; g.r2 = g.r * g.r;
+  g.n_inner = P->n_inner;
+  for (int k = 0; k < g.n_inner; ++k) {
+    g.sx1[k] = P->inner[k][0] * 1e9; g.sy1[k] = P->inner[k][1] * 1e9;
+    g.sx2[k] = P->inner[k][2] * 1e9; g.sy2[k] = P->inner[k][3] * 1e9;
+    g.snx[k] = P->inner_n[k][0]; g.sny[k] = P->inner_n[k][1];
+  }
   first_hit(g, x, u, dist, face);
   return 0;
+}
+
+// 1 if (x, y) (nm) lies inside a hole bounded by the internal segments.
+int or_in_hole(const or_params* P, double x, double y) {
+  Geo g;
+  g.n_inner = P->n_inner;
+  for (int k = 0; k < g.n_inner; ++k) {
+    g.sx1[k] = P->inner[k][0] * 1e9; g.sy1[k] = P->inner[k][1] * 1e9;
+    g.sx2[k] = P->inner[k][2] * 1e9; g.sy2[k] = P->inner[k][3] * 1e9;
+  }
+  return in_hole(g, x, y) ? 1 : 0;
 }
 
 // Source energies: out[0] = E_tot, out[1] = V_solid, out[2..] = E per source.

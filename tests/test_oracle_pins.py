@@ -338,6 +338,108 @@ def test_two_phonon_events_do_not_count_toward_n_scat_max():
     assert abs(frac0 - 0.2) < 4 * math.sqrt(0.2 * 0.8 / ev.size)
 
 
+# ------------------------------------------------------------------ internal walls, d(omega) (Secs. 3.5.3, 4.2)
+def _golden(name):
+    vals = {}
+    for line in open(os.path.join(HERE, "golden", name)):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            vals[k] = float(v)
+    return vals
+
+
+def test_nanomesh_solid_volume_matches_paper():
+    gv = _golden("nanomesh_volume.txt")
+    g = W.nanomesh(W=gv["W_m"], pore=gv["pore_m"], thickness=gv["thickness_m"])
+    src = oracle.sources(W.gray(6000.0, 100e-9), g)
+    assert src["V_solid"] == pytest.approx(gv["V_m3_printed"], abs=0.005e-23)
+    assert src["V_solid"] == pytest.approx(22e-9 * (34e-9 ** 2 - 11e-9 ** 2), rel=1e-12)
+    # the body source scales with the solid volume (Eq. grad_flux_sim)
+    src0 = oracle.sources(W.gray(6000.0, 100e-9), W.film(gv["thickness_m"], W=gv["W_m"]))
+    assert src["E_tot"] / src0["E_tot"] == pytest.approx(src["V_solid"] / src0["V_solid"], rel=1e-12)
+
+
+def test_in_hole_even_odd_rule():
+    g = W.nanomesh()            # hole [11.5, 22.5]^2 nm
+    assert oracle.in_hole(g, 17.0, 17.0) and oracle.in_hole(g, 11.6, 22.4)
+    assert not oracle.in_hole(g, 11.4, 17.0) and not oracle.in_hole(g, 30.0, 5.0)
+    # two holes side by side
+    g2 = W.film(20e-9, W=100e-9)
+    sq = lambda x0, y0, a: [(x0, y0, x0 + a, y0), (x0 + a, y0, x0 + a, y0 + a), (x0 + a, y0 + a, x0, y0 + a),
+                            (x0, y0 + a, x0, y0)]
+    g2.inner = sq(10e-9, 10e-9, 20e-9) + sq(60e-9, 10e-9, 20e-9)
+    g2.inner_n = [(0, -1), (1, 0), (0, 1), (-1, 0)] * 2
+    g2.inner_p = [0.0] * 8
+    pts = [(20, 20, True), (70, 20, True), (45, 20, False), (20, 50, False), (75, 29.9, True)]
+    for x, y, inside in pts:
+        assert oracle.in_hole(g2, x, y) == inside, (x, y)
+    src = oracle.sources(W.gray(6000.0, 100e-9), g2)
+    assert src["V_solid"] == pytest.approx(20e-9 * (100e-9 ** 2 - 2 * 20e-9 ** 2), rel=1e-12)
+
+
+def test_first_hit_internal_walls_brute_force():
+    # march each ray in small steps until it enters the hole or leaves the
+    # cell, then bisect: the first event's distance must match first_hit
+    g = W.nanomesh()
+    L = np.array(g.L) * 1e9
+    rng = np.random.default_rng(21)
+    checked = 0
+    while checked < 300:
+        x = rng.uniform(0, 1, 3) * L
+        if oracle.in_hole(g, x[0], x[1]):
+            continue
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        d, f = oracle.first_hit(g, x, u)
+        bad = lambda t: (oracle.in_hole(g, *(x + t * u)[:2]) or np.any(x + t * u < 0) or np.any(x + t * u > L))
+        t0, step = 0.0, 0.05
+        while not bad(t0 + step):
+            t0 += step
+        lo, hi = t0, t0 + step
+        for _ in range(40):
+            mid = 0.5 * (lo + hi)
+            lo, hi = (lo, mid) if bad(mid) else (mid, hi)
+        assert d == pytest.approx(hi, abs=1e-6), (x, u, d, hi, f)
+        p = x + d * u
+        if f >= 7:                      # internal wall: the hit point lies on that wall
+            x1, y1, x2, y2 = np.array(g.inner[f - 7]) * 1e9
+            assert abs((p[0] - x1) * g.inner_n[f - 7][0] + (p[1] - y1) * g.inner_n[f - 7][1]) < 1e-9
+        checked += 1
+
+
+def test_per_bin_specularity_equal_to_face_value_is_identical():
+    m = W.gray(6000.0, 300e-9, C=1e6)
+    run = W.SteadyRun(n=3000, seed=31, tally_axis=1, n_scat_max=5)
+    g_face = W.film(50e-9, p=0.4)
+    g_bin = W.film(50e-9, p=0.4)
+    g_bin.face_p = [(-1.0 if t == W.ADIABATIC else 0.0) for t in g_bin.face_type]
+    from dataclasses import replace
+    mb = replace(m, spec_bin=np.array([0.4]))
+    a = oracle.run_steady(m, g_face, run, per_particle=True)
+    b = oracle.run_steady(mb, g_bin, run, per_particle=True)
+    assert np.array_equal(a["events_pp"], b["events_pp"])
+    assert np.array_equal(a["X_pp"], b["X_pp"])
+
+
+def test_frequency_dependent_specularity_fuchs_sondheimer():
+    # each mode sees its own wall specularity: kappa = sum_i 1/3 C_i v_i^2
+    # tau_i S(d / Lambda_i, p_i); two modes, specular (S = 1) and diffuse
+    from dataclasses import replace
+    v = np.array([6000.0, 6000.0])
+    lam = np.array([100e-9, 300e-9])
+    m = W.Material(omega=np.array([1e13, 2e13]), v=v, tau=lam / v, C=np.array([1e6, 1e6]),
+                   spec_bin=np.array([1.0, 0.0]), name="two-mode")
+    d = 100e-9
+    g = W.film(d)
+    g.face_p = [(-1.0 if t == W.ADIABATIC else 0.0) for t in g.face_type]
+    run = W.SteadyRun(n=400_000, seed=32, tally_axis=1, n_scat_max=10, max_events=10 ** 7)
+    r = oracle.run_steady(m, g, run)
+    k = sum(cf.fuchs_sondheimer([m.C[i]], [v[i]], [m.tau[i]], d, p=float(m.spec_bin[i])) for i in range(2))
+    assert abs(r["kappa"] - k) < 3.5 * r["kappa_se"]
+    k_diffuse = cf.fuchs_sondheimer(m.C, v, m.tau, d, p=0.0)
+    assert k - k_diffuse > 6 * r["kappa_se"]
+
+
 @pytest.mark.parametrize("d", [10e-9, 100e-9, 1e-6])
 def test_fuchs_sondheimer_films_bvk(d):
     m = W.bvk_holland()
