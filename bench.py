@@ -47,6 +47,7 @@ METRIC = "particle-events/s and s to 1% std-err kappa_eff, batched FP32 vs plain
 UNIT = "particle-events/s"
 WORKLOADS = {"si_slab": "si_slab_L1um_3000bins", "si_slab_imp": "si_slab_L1um_3000bins_two_phonon_clock",
              "transient_box": "transient_box_2x2x1um_gauss",
+             "nanomesh": "nanomesh_W34nm_pore11nm_t22nm_timp",
              "film_batch": "film_batch_64_10nm_10um", "pore_grad": "pore_film_W100nm_phi0.25_t200nm_grad"}
 # Algorithmic thread-instructions per event of the tracer (one Philox4x32-10
 # call, log + sqrt + sincos, six-plane first hit, alias draw, state update and
@@ -197,6 +198,43 @@ def _workload_setup(name, args, seed_offset):
         shape = {"threads_per_block": cfg.threads_per_block, "refill_threshold": cfg.refill_threshold}
         return dict(mat=mat, geo=geo, run=run, n=run.n, step=step, fp64=fp64, e2e=e2e, d2h=d2h, h2d=h2d, desc=desc,
                     launches=launches, timer=tm, kernel="k_steady_f32", shape=shape, kappa=True, kind="steady")
+    if name == "nanomesh":
+        # the paper's nanomesh (Sec. 5.5): N = 1e6, N_scat^max = 10, square pore
+        # as four internal walls, diffuse walls, tau_imp^-1 = 2e-44 omega^4
+        n = args.n_particles or 1_000_000
+        base = W.bvk_holland()
+        mat = replace(base, tau_imp=1.0 / (2e-44 * base.omega ** 4))
+        geo = W.nanomesh()
+        run = W.SteadyRun(n=n, seed=1006 + seed_offset, tally_axis=1, per_bin=True, n_scat_max=10)
+        M, G = api.Material(mat), api.Geometry(geo)
+        cfg = api.SteadyConfig(seed=run.seed, precision=L.FP32_TRACE, tally_axis=1, per_bin=True, n_scat_max=10,
+                               max_events=10 ** 9, threads_per_block=args.threads, refill_threshold=args.refill,
+                               time_budget_s=300)
+        if args.threads == 0 and not args.no_autotune:
+            cfg = autotune.tune(M, [G], [n], cfg)
+        cfg = replace(cfg, trace_events=ev)
+        out = api.SteadyOutputs(1, M.n_bins, 0, True)
+
+        def step():
+            api.run_steady(M, [G], [n], cfg, out=out)
+            return lambda: out.stats.cpu().numpy()
+
+        def fp64(n64):
+            c = replace(cfg, precision=L.FP64_PLAIN, threads_per_block=0, refill_threshold=0)
+            o = api.SteadyOutputs(1, M.n_bins, 0, True)
+            return lambda: (api.run_steady(M, [G], [n64], c, out=o), (lambda: o.stats.cpu().numpy()))[1]
+
+        def e2e():
+            Mh, Gh = api.Material(mat), api.Geometry(geo)
+            return api.run_steady_host(Mh, [Gh], [n], replace(cfg, trace_events=None))["stats"]
+        desc = ("Si nanomesh unit cell 34 nm, 11 nm square pore (four internal walls) through a 22 nm film, "
+                "diffuse walls, periodic x,y, grad_T -1e6 K/m along y, BvK 3x1000 bins + Holland tau, "
+                "separate impurity clock tau_imp^-1 = 2e-44 omega^4, N_scat_max 10")
+        return dict(mat=mat, geo=geo, run=run, n=n, step=step, fp64=fp64, e2e=e2e,
+                    d2h=8 * (M.n_bins + L.NSTATS), h2d=_material_bytes(mat) + ctypes.sizeof(L.GeometryDesc) + 8,
+                    desc=desc, launches=3, timer=tm, kernel="k_steady_f32 (nanomesh)",
+                    shape={"threads_per_block": cfg.threads_per_block, "refill_threshold": cfg.refill_threshold},
+                    kappa=True, kind="steady")
     if name == "pore_grad":
         wl = W.pore_film_c5(n=args.n_particles or 50_000_000)
         mat, geo, run = wl.material, wl.geometries[0], wl.run

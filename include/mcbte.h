@@ -81,6 +81,9 @@ typedef struct {
   const double* D;       /* [n_bins] s/(rad m^3), format 1 (used if C NULL) */
   const double* domega;  /* [n_bins] rad/s, format 1                        */
   double T_lin;          /* K, linearisation temperature (Sec. 4.4)         */
+  const double* spec_bin; /* [n_bins] optional per-bin specularity d(omega) in
+                            [0, 1] (Sec. 3.5.3), used by faces and walls whose
+                            specularity is given as < 0; or NULL          */
   const double* tau_imp; /* [n_bins] s, optional two-phonon (impurity)
                             relaxation times (the optional last column of
                             Sec. 4.1), or NULL; each > 0, +inf for none.
@@ -115,10 +118,21 @@ mcbte_status mcbte_material_tables(const mcbte_material* m, double* C, double* p
  * gradient of Sec. 2.5 (Eq. lin_spatial); it adds the body source of
  * Eq. grad_flux.  At most one component may be non-zero.  gauss adds an
  * initial-condition source dT exp(-|x-c|^2 / 2 sigma^2) (transient only).
- * Errors: L <= 0, periodic faces not paired on an axis, p outside [0,1],
+ * Internal walls (Sec. 4.2, In_bnd.txt): up to MCBTE_MAX_INNER adiabatic
+ * segments (x1, y1, x2, y2) in the x-y plane running through the thickness,
+ * each with a unit normal (nx, ny) pointing into the solid and a specularity
+ * (IDs after the cylinder).  They bound holes (the regions they enclose,
+ * even-odd rule), which body sources avoid and the solid volume excludes; a
+ * wall is met only from its solid side.  A specularity below 0 on an
+ * adiabatic face or wall selects the material's per-bin d(omega)
+ * (mcbte_material_desc.spec_bin; the run fails with MCBTE_ERR_INVALID_ARG if
+ * the material has none).
+ * Errors: L <= 0, periodic faces not paired on an axis, p above 1,
  * pore not inside the cell (r >= min(Lx,Ly)/2 or centre off), more than one
- * gradient component -> MCBTE_ERR_INVALID_ARG. */
+ * gradient component, walls outside the box or normals not of unit length
+ * -> MCBTE_ERR_INVALID_ARG. */
 enum { MCBTE_FACE_ISOTHERMAL = 0, MCBTE_FACE_ADIABATIC = 1, MCBTE_FACE_PERIODIC = 2 };
+#define MCBTE_MAX_INNER 16
 
 typedef struct {
   double L[3];           /* m                                               */
@@ -135,6 +149,10 @@ typedef struct {
   double gauss_c[3];     /* m                                               */
   double gauss_sigma;    /* m                                               */
   double gauss_dT;       /* K                                               */
+  int n_inner;           /* internal walls, 0..MCBTE_MAX_INNER              */
+  double inner[MCBTE_MAX_INNER][4];    /* x1, y1, x2, y2 (m)               */
+  double inner_n[MCBTE_MAX_INNER][2];  /* unit normal into the solid       */
+  double inner_p[MCBTE_MAX_INNER];     /* specularity; < 0: per bin        */
 } mcbte_geometry_desc;
 
 typedef struct mcbte_geometry mcbte_geometry;

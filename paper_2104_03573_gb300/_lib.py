@@ -28,7 +28,7 @@ EXPORTS = [
 class MaterialDesc(C.Structure):
     _fields_ = [("n_bins", C.c_int), ("omega", C.c_void_p), ("v", C.c_void_p), ("tau", C.c_void_p),
                 ("C", C.c_void_p), ("D", C.c_void_p), ("domega", C.c_void_p), ("T_lin", C.c_double),
-                ("tau_imp", C.c_void_p)]
+                ("spec_bin", C.c_void_p), ("tau_imp", C.c_void_p)]
 
 
 class GeometryDesc(C.Structure):
@@ -36,7 +36,8 @@ class GeometryDesc(C.Structure):
                 ("face_p", C.c_double * 6), ("T_eq", C.c_double), ("grad_T", C.c_double * 3),
                 ("pore", C.c_int), ("pore_c", C.c_double * 2), ("pore_r", C.c_double), ("pore_p", C.c_double),
                 ("gauss", C.c_int), ("gauss_c", C.c_double * 3), ("gauss_sigma", C.c_double),
-                ("gauss_dT", C.c_double)]
+                ("gauss_dT", C.c_double), ("n_inner", C.c_int), ("inner", (C.c_double * 4) * 16),
+                ("inner_n", (C.c_double * 2) * 16), ("inner_p", C.c_double * 16)]
 
 
 class SteadyParams(C.Structure):

@@ -42,6 +42,10 @@ class Material:
             ti = _f64(m.tau_imp)
             self._keep.append(ti)
             d.tau_imp = ti.ctypes.data
+        if getattr(m, "spec_bin", None) is not None:
+            sb = _f64(m.spec_bin)
+            self._keep.append(sb)
+            d.spec_bin = sb.ctypes.data
         h = C.c_void_p()
         L.check(lib.mcbte_material_create(C.byref(d), C.byref(h)))
         self.handle = h
@@ -80,6 +84,12 @@ def geometry_desc(g) -> "L.GeometryDesc":
     d.gauss_c[:] = [float(x) for x in g.gauss_c]
     d.gauss_sigma = float(g.gauss_sigma)
     d.gauss_dT = float(g.gauss_dT)
+    inner = list(getattr(g, "inner", ()) or ())
+    d.n_inner = len(inner)
+    for k, seg in enumerate(inner[:16]):
+        d.inner[k][:] = [float(c) for c in seg]
+        d.inner_n[k][:] = [float(c) for c in g.inner_n[k]]
+        d.inner_p[k] = float(g.inner_p[k])
     return d
 
 

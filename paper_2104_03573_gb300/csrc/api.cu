@@ -109,6 +109,8 @@ mcbte_status mcbte_material_create(const mcbte_material_desc* d, mcbte_material*
       return fail(MCBTE_ERR_INVALID_ARG, "material_create: D and domega must be >= 0");
     if (d->tau_imp && !(d->tau_imp[i] > 0.0))
       return fail(MCBTE_ERR_INVALID_ARG, "material_create: tau_imp must be > 0 (+inf: no two-phonon scattering)");
+    if (d->spec_bin && !(d->spec_bin[i] >= 0.0 && d->spec_bin[i] <= 1.0))
+      return fail(MCBTE_ERR_INVALID_ARG, "material_create: spec_bin must be in [0, 1]");
   }
   Carve c;
   auto layout = [&](MatBuild& b) {
@@ -134,6 +136,9 @@ mcbte_status mcbte_material_create(const mcbte_material_desc* d, mcbte_material*
     b.lam2 = c.take<double>(n);
     double* ti = c.take<double>(n);
     b.tau_imp = d->tau_imp ? ti : nullptr;
+    double* sb = c.take<double>(n);
+    b.spec_bin = d->spec_bin ? sb : nullptr;
+    b.spec_thr = c.take<uint64_t>(n);
     b.sums = c.take<double>(4);
     b.prob = c.take<double>(3 * (size_t)n);
     b.thr = c.take<uint64_t>(3 * (size_t)n);
@@ -159,6 +164,7 @@ mcbte_status mcbte_material_create(const mcbte_material_desc* d, mcbte_material*
   if (e == cudaSuccess) e = cudaMemcpy((void*)b.v, d->v, nb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy((void*)b.tau, d->tau, nb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && d->tau_imp) e = cudaMemcpy((void*)b.tau_imp, d->tau_imp, nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && d->spec_bin) e = cudaMemcpy((void*)b.spec_bin, d->spec_bin, nb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && fmt2) e = cudaMemcpy((void*)b.C_in, d->C, nb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !fmt2) e = cudaMemcpy((void*)b.D, d->D, nb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !fmt2) e = cudaMemcpy((void*)b.domega, d->domega, nb, cudaMemcpyHostToDevice);
@@ -191,6 +197,7 @@ mcbte_status mcbte_material_create(const mcbte_material_desc* d, mcbte_material*
   v.sums = b.sums;
   v.lam2_d = b.lam2;
   v.imp = d->tau_imp ? 1 : 0;
+  v.spec_thr = d->spec_bin ? b.spec_thr : nullptr;
   *out = m;
   return MCBTE_OK;
 }
@@ -223,8 +230,8 @@ mcbte_status mcbte_geometry_create(const mcbte_geometry_desc* d, mcbte_geometry*
     if (!finite_pos(d->L[a])) return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: L must be > 0");
   for (int f = 0; f < 6; ++f) {
     if (d->face_type[f] < 0 || d->face_type[f] > 2) return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: face type");
-    if (d->face_type[f] == MCBTE_FACE_ADIABATIC && !(d->face_p[f] >= 0.0 && d->face_p[f] <= 1.0))
-      return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: specularity outside [0,1]");
+    if (d->face_type[f] == MCBTE_FACE_ADIABATIC && !(d->face_p[f] <= 1.0))   // < 0: per-bin d(omega)
+      return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: specularity above 1");
     if (d->face_type[f] == MCBTE_FACE_ISOTHERMAL && !finite_pos(d->face_T[f]))
       return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: isothermal T_b must be > 0");
   }
@@ -251,6 +258,18 @@ mcbte_status mcbte_geometry_create(const mcbte_geometry_desc* d, mcbte_geometry*
   }
   if (d->gauss && !finite_pos(d->gauss_sigma))
     return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: gauss_sigma must be > 0");
+  if (d->n_inner < 0 || d->n_inner > MCBTE_MAX_INNER)
+    return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: n_inner in [0, MCBTE_MAX_INNER]");
+  for (int k = 0; k < d->n_inner; ++k) {
+    const double* s4 = d->inner[k];
+    for (int c = 0; c < 4; ++c)
+      if (!(std::isfinite(s4[c]) && s4[c] >= 0.0 && s4[c] <= d->L[c & 1]))
+        return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: internal walls must lie in the cell");
+    if (s4[0] == s4[2] && s4[1] == s4[3]) return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: empty internal wall");
+    const double nn = d->inner_n[k][0] * d->inner_n[k][0] + d->inner_n[k][1] * d->inner_n[k][1];
+    if (!(std::fabs(nn - 1.0) < 1e-9)) return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: wall normals must be unit");
+    if (!(d->inner_p[k] <= 1.0)) return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: wall specularity above 1");
+  }
   mcbte_geometry_desc* dev = nullptr;
   CUDA_TRY(cudaMalloc(&dev, sizeof(mcbte_geometry_desc)));
   cudaError_t e = cudaMemcpy(dev, d, sizeof(mcbte_geometry_desc), cudaMemcpyHostToDevice);
@@ -279,6 +298,15 @@ namespace {
 bool has_isothermal_source(const mcbte_geometry_desc& d) {
   for (int f = 0; f < 6; ++f)
     if (d.face_type[f] == MCBTE_FACE_ISOTHERMAL && d.face_T[f] != d.T_eq) return true;
+  return false;
+}
+
+// A face or internal wall that takes the material's per-bin specularity.
+bool uses_spec_bin(const mcbte_geometry_desc& d) {
+  for (int f = 0; f < 6; ++f)
+    if (d.face_type[f] == MCBTE_FACE_ADIABATIC && d.face_p[f] < 0.0) return true;
+  for (int k = 0; k < d.n_inner; ++k)
+    if (d.inner_p[k] < 0.0) return true;
   return false;
 }
 
@@ -385,6 +413,8 @@ mcbte_status check_steady(const mcbte_material* m, const mcbte_geometry* const* 
     if (d.gauss) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: an initial condition needs a transient run");
     if (!has_isothermal_source(d) && !has_gradient(d))
       return fail(MCBTE_ERR_INVALID_ARG, "run_steady: geometry has no source (no isothermal wall off T_eq, no grad_T)");
+    if (uses_spec_bin(d) && !m->view.spec_thr)
+      return fail(MCBTE_ERR_INVALID_ARG, "run_steady: a per-bin specularity needs the material's spec_bin");
   }
   if (t >= (1ull << 40)) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: too many particles");
   *total = t;
@@ -672,6 +702,8 @@ mcbte_status check_transient(const mcbte_material* m, const mcbte_geometry* g, c
     return fail(MCBTE_ERR_INVALID_ARG, "run_transient: threads_per_block must be 0, 256, 512, 768 or 1024");
   const mcbte_geometry_desc& d = g->host;
   if (has_gradient(d)) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: body (gradient) sources are steady only");
+  if (uses_spec_bin(d) && !m->view.spec_thr)
+    return fail(MCBTE_ERR_INVALID_ARG, "run_transient: a per-bin specularity needs the material's spec_bin");
   if (!d.gauss && !has_isothermal_source(d)) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: no source");
   return MCBTE_OK;
 }

@@ -64,6 +64,8 @@ struct MatBuild {
   int n;
   const double *omega, *v, *tau, *C_in, *D, *domega;
   const double* tau_imp;   // optional two-phonon relaxation times (s), or null
+  const double* spec_bin;  // optional per-bin specularity, or null
+  uint64_t* spec_thr;      // [n] its thresholds (when given)
   double T_lin;
   double *C, *w_emit, *w_init, *w_relax, *v_nm, *inv_v, *lam, *pi, *sums;
   double* lam2;            // [n] v tau_imp (nm), +inf without a two-phonon clock

@@ -17,6 +17,15 @@ constexpr int kMaxGeoms = 128;
 constexpr int kMaxSources = 8;
 constexpr int kMaxDirs = 16;
 constexpr int kMaxPeriods = 65;
+constexpr int kMaxInner = MCBTE_MAX_INNER;
+
+// Specular threshold of a reflection probability p on a 32-bit word:
+// specular iff word < floor(p 2^32) (p = 1: always).
+__host__ __device__ __forceinline__ uint64_t spec_threshold(double p) {
+  if (p <= 0.0) return 0ull;
+  if (p >= 1.0) return 1ull << 32;
+  return (uint64_t)(p * 4294967296.0);
+}
 
 // ------------------------------------------------------------------ per-run records
 // Geometry as the tracer sees it, derived on the device by the setup kernel
@@ -31,6 +40,13 @@ struct GeoRun {
   uint64_t pthr_pore;
   int type[6];
   int pore;
+  // internal walls (Sec. 4.2), nm, oriented as given; normal into the solid
+  int n_inner;
+  int fbin;                    // bit f: face f takes the per-bin specularity
+  int sbin;                    // bit k: wall k takes the per-bin specularity
+  double sx1[kMaxInner], sy1[kMaxInner], sx2[kMaxInner], sy2[kMaxInner], snx[kMaxInner], sny[kMaxInner];
+  float sx1f[kMaxInner], sy1f[kMaxInner], sx2f[kMaxInner], sy2f[kMaxInner], snxf[kMaxInner], snyf[kMaxInner];
+  uint64_t sthr[kMaxInner];
   int n_src;
   int src_kind[kMaxSources];   // 0 isothermal face, 1 body (control gradient), 2 initial Gaussian
   int src_face[kMaxSources];
@@ -64,6 +80,7 @@ struct MatView {
   const double* sums;       // [3] sum C, sum C v, sum C / tau  (SI)
   const double* lam2_d;     // nm, two-phonon mean free path v tau_imp (+inf: none)
   int imp;                  // a two-phonon clock is present (Sec. 3.3)
+  const uint64_t* spec_thr; // per-bin specular thresholds floor(d(omega) 2^32), or null
 };
 
 // ------------------------------------------------------------------ Philox4x32-10
@@ -271,8 +288,46 @@ __device__ __forceinline__ void first_hit(const GeoRun& g, const R x[3], const R
       }
     }
   }
+  // internal walls (faces 7, 8, ...), met only from their solid side; a
+  // particle behind a wall's line by more than rounding is beyond the hole
+  const R tol = sizeof(R) == 8 ? R(1e-9) : R(1e-4);
+  for (int k = 0; k < g.n_inner; ++k) {
+    const R nx = sizeof(R) == 8 ? (R)g.snx[k] : (R)g.snxf[k];
+    const R ny = sizeof(R) == 8 ? (R)g.sny[k] : (R)g.snyf[k];
+    const R un = u[0] * nx + u[1] * ny;
+    if (!(un < R(0))) continue;
+    const R x1 = sizeof(R) == 8 ? (R)g.sx1[k] : (R)g.sx1f[k];
+    const R y1 = sizeof(R) == 8 ? (R)g.sy1[k] : (R)g.sy1f[k];
+    const R dn = (x[0] - x1) * nx + (x[1] - y1) * ny;
+    if (dn < -tol) continue;
+    R d = dn / (-un);
+    if (d < R(0)) d = R(0);
+    const R tx = (sizeof(R) == 8 ? (R)g.sx2[k] : (R)g.sx2f[k]) - x1;
+    const R ty = (sizeof(R) == 8 ? (R)g.sy2[k] : (R)g.sy2f[k]) - y1;
+    const R hs = ((x[0] + d * u[0]) - x1) * tx + ((x[1] + d * u[1]) - y1) * ty;
+    if (hs < R(0) || hs > tx * tx + ty * ty) continue;
+    if (d < best) { best = d; bf = 7 + k; }
+  }
   *dist = best;
   *face = bf;
+}
+
+// Inside a hole bounded by the internal walls: even-odd count of the walls
+// crossed by the ray from (x, y) towards +x.
+template <typename R>
+__device__ __forceinline__ bool in_hole(const GeoRun& g, R x, R y) {
+  bool c = false;
+  for (int k = 0; k < g.n_inner; ++k) {
+    const R y1 = sizeof(R) == 8 ? (R)g.sy1[k] : (R)g.sy1f[k];
+    const R y2 = sizeof(R) == 8 ? (R)g.sy2[k] : (R)g.sy2f[k];
+    if ((y1 > y) != (y2 > y)) {
+      const R x1 = sizeof(R) == 8 ? (R)g.sx1[k] : (R)g.sx1f[k];
+      const R x2 = sizeof(R) == 8 ? (R)g.sx2[k] : (R)g.sx2f[k];
+      const R xc = x1 + ((y - y1) * (x2 - x1)) / (y2 - y1);
+      if (x < xc) c = !c;
+    }
+  }
+  return c;
 }
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {

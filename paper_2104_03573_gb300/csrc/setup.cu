@@ -6,12 +6,6 @@ namespace mcbte {
 
 namespace {
 
-__device__ __forceinline__ uint64_t spec_threshold(double p) {
-  if (p <= 0.0) return 0ull;
-  if (p >= 1.0) return 1ull << 32;
-  return (uint64_t)(p * 4294967296.0);
-}
-
 // One thread per geometry: derive the tracer's geometry record and the
 // source list with E_i (Eq. dev_tot / Eq. source_energy, Sec. 3.1):
 //   isothermal wall  E = (A/4) sum C v |T_b - T_eq|           (Eq. iso_flux)
@@ -40,10 +34,33 @@ __global__ void k_setup(SetupArgs a, int G, MatView M, int transient, double t_m
     r.L[k] = d.L[k] * 1e9;
     r.Lf[k] = (float)r.L[k];
   }
+  r.fbin = 0;
   for (int f = 0; f < 6; ++f) {
     r.type[f] = d.face_type[f];
     r.pthr[f] = spec_threshold(d.face_p[f]);
     r.face_sign[f] = (d.face_T[f] > d.T_eq) ? 1.0 : -1.0;
+    if (d.face_p[f] < 0.0) r.fbin |= 1 << f;
+  }
+  // internal walls: oriented with the solid on their right (normal = (dy, -dx)
+  // direction), so the shoelace sum over them is the holes' area
+  r.n_inner = d.n_inner;
+  r.sbin = 0;
+  double hole_area = 0.0;
+  for (int k = 0; k < d.n_inner; ++k) {
+    double x1 = d.inner[k][0], y1 = d.inner[k][1], x2 = d.inner[k][2], y2 = d.inner[k][3];
+    const double nx = d.inner_n[k][0], ny = d.inner_n[k][1];
+    if ((y2 - y1) * nx - (x2 - x1) * ny < 0.0) {
+      const double tx = x1, ty = y1;
+      x1 = x2; y1 = y2; x2 = tx; y2 = ty;
+    }
+    hole_area += 0.5 * (x1 * y2 - x2 * y1);
+    r.sx1[k] = x1 * 1e9; r.sy1[k] = y1 * 1e9; r.sx2[k] = x2 * 1e9; r.sy2[k] = y2 * 1e9;
+    r.snx[k] = nx; r.sny[k] = ny;
+    r.sx1f[k] = (float)r.sx1[k]; r.sy1f[k] = (float)r.sy1[k];
+    r.sx2f[k] = (float)r.sx2[k]; r.sy2f[k] = (float)r.sy2[k];
+    r.snxf[k] = (float)nx; r.snyf[k] = (float)ny;
+    r.sthr[k] = spec_threshold(d.inner_p[k]);
+    if (d.inner_p[k] < 0.0) r.sbin |= 1 << k;
   }
   r.pore = d.pore;
   r.cx = d.pore_c[0] * 1e9;
@@ -58,6 +75,7 @@ __global__ void k_setup(SetupArgs a, int G, MatView M, int transient, double t_m
   double V = d.L[0] * d.L[1] * d.L[2];
   r.V_box = V;
   if (d.pore) V = V - (3.141592653589793 * (d.pore_r * d.pore_r)) * d.L[2];
+  if (d.n_inner > 0) V = V - hole_area * d.L[2];
   r.V_solid = V;
   const double tf = transient ? t_max_s : 1.0;
   int ns = 0;

@@ -43,6 +43,7 @@ __global__ void k_bins(MatBuild b) {
   b.lam[i] = lam;
   b.inv_v[i] = inv_v;
   b.lam2[i] = lam2;
+  if (b.spec_bin) b.spec_thr[i] = spec_threshold(b.spec_bin[i]);
   b.binf[i] = make_float4((float)v_nm, (float)inv_v, (float)lam, (float)lam2);
 }
 

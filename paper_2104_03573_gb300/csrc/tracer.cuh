@@ -183,9 +183,13 @@ __device__ __forceinline__ void emit_prologue(Particle<R>& p, const GeoRun& g, u
       p.x[0] = Num<R>::mid(w3.x) * geo_L<R>(g, 0);
       p.x[1] = Num<R>::mid(w3.y) * geo_L<R>(g, 1);
       p.x[2] = Num<R>::mid(w3.z) * geo_L<R>(g, 2);
-      if (!g.pore) break;
-      const R dx = p.x[0] - cx, dy = p.x[1] - cy;
-      if (dx * dx + dy * dy >= r2) break;
+      bool inside = false;
+      if (g.pore) {
+        const R dx = p.x[0] - cx, dy = p.x[1] - cy;
+        inside = dx * dx + dy * dy < r2;
+      }
+      if (!inside && g.n_inner > 0) inside = in_hole<R>(g, p.x[0], p.x[1]);
+      if (!inside) break;
       if (j + 1 >= 64u) break;
     }
   } else {
@@ -617,23 +621,38 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
     }
     put3<R>(p.x, a, mx ? La : R(0));
     const uint4 w = philox(ctr, k0, k1);
-    if ((uint64_t)w.x < g.pthr[face]) {
+    if ((uint64_t)w.x < (((g.fbin >> face) & 1) ? M.spec_thr[p.bin] : g.pthr[face])) {
       put3<R>(p.u, a, -sel3(p.u, a));
     } else {
       dir_about_axis<R>(p.u, a, mx ? R(-1) : R(1), Num<R>::sqrt_(Num<R>::oc(w.z)), w.w);
     }
     return STEP_ALIVE;
   }
-  // pore wall: the cylinder's outward normal points into the solid
-  const R cx = sizeof(R) == 8 ? (R)g.cx : (R)g.cxf;
-  const R cy = sizeof(R) == 8 ? (R)g.cy : (R)g.cyf;
-  R nx = p.x[0] - cx, ny = p.x[1] - cy;
-  const R len = Num<R>::sqrt_(nx * nx + ny * ny);
-  nx = nx / len;
-  ny = ny / len;
+  R nx, ny;
+  bool spec;
   const uint4 w = philox(ctr, k0, k1);
-  const bool spec = (uint64_t)w.x < g.pthr_pore;
-  if (Grad::on) gr.pore_hit(spec, g.p_pore, Xnow);
+  if (face >= 7) {
+    // internal wall (Sec. 4.2): onto its line, then reflect about its normal
+    const int k = face - 7;
+    nx = sizeof(R) == 8 ? (R)g.snx[k] : (R)g.snxf[k];
+    ny = sizeof(R) == 8 ? (R)g.sny[k] : (R)g.snyf[k];
+    const R dn = (p.x[0] - (sizeof(R) == 8 ? (R)g.sx1[k] : (R)g.sx1f[k])) * nx +
+                 (p.x[1] - (sizeof(R) == 8 ? (R)g.sy1[k] : (R)g.sy1f[k])) * ny;
+    p.x[0] = p.x[0] - dn * nx;
+    p.x[1] = p.x[1] - dn * ny;
+    spec = (uint64_t)w.x < (((g.sbin >> k) & 1) ? M.spec_thr[p.bin] : g.sthr[k]);
+  } else {
+    // pore wall: the cylinder's outward normal points into the solid
+    const R cx = sizeof(R) == 8 ? (R)g.cx : (R)g.cxf;
+    const R cy = sizeof(R) == 8 ? (R)g.cy : (R)g.cyf;
+    nx = p.x[0] - cx;
+    ny = p.x[1] - cy;
+    const R len = Num<R>::sqrt_(nx * nx + ny * ny);
+    nx = nx / len;
+    ny = ny / len;
+    spec = (uint64_t)w.x < g.pthr_pore;
+    if (Grad::on) gr.pore_hit(spec, g.p_pore, Xnow);
+  }
   if (spec) {
     const R un = p.u[0] * nx + p.u[1] * ny;
     p.u[0] = p.u[0] - (R(2) * un) * nx;

@@ -68,6 +68,29 @@ def test_geometry_validation_rejects_before_cuda(lib):
     assert lib.mcbte_geometry_create(C.byref(api.geometry_desc(g3)), C.byref(h)) == _lib.ERR_INVALID_ARG
 
 
+def test_internal_wall_validation_rejects_before_cuda(lib):
+    from paper_2104_03573_gb300 import _lib, api
+    from inputs import workloads as W
+    h = C.c_void_p()
+    for mutate in ("outside", "normal", "spec", "count", "empty"):
+        g = W.nanomesh()
+        if mutate == "outside":
+            g.inner = [list(s) for s in g.inner]
+            g.inner[0][2] = 40e-9
+        elif mutate == "normal":
+            g.inner_n = [list(n) for n in g.inner_n]
+            g.inner_n[1] = [0.9, 0.0]
+        elif mutate == "spec":
+            g.inner_p = [0.0, 1.5, 0.0, 0.0]
+        elif mutate == "empty":
+            g.inner = [list(s) for s in g.inner]
+            g.inner[2] = [g.inner[2][0], g.inner[2][1], g.inner[2][0], g.inner[2][1]]
+        d = api.geometry_desc(g)
+        if mutate == "count":
+            d.n_inner = 17
+        assert lib.mcbte_geometry_create(C.byref(d), C.byref(h)) == _lib.ERR_INVALID_ARG, mutate
+
+
 def test_material_validation_rejects_before_cuda(lib):
     from paper_2104_03573_gb300 import _lib
     n = 3

@@ -146,6 +146,43 @@ def test_fp32_two_phonon_clock_kappa_vs_oracle():
     assert ref["kappa"] < plain["kappa"] - 5 * np.hypot(ref["kappa_se"], plain["kappa_se"])
 
 
+def _nanomesh_case(n, spec_low=False):
+    # the paper's nanomesh (Sec. 5.5): 34 nm cell, 11 nm square pore through a
+    # 22 nm film, diffuse walls, tau_imp^-1 = 2e-44 omega^4, N_scat^max = 10;
+    # spec_low: modes up to 2 THz reflect specularly from every wall
+    m = _with_imp(W.bvk_holland())
+    g = W.nanomesh()
+    if spec_low:
+        m = replace(m, spec_bin=(m.omega / (2 * np.pi) <= 2e12).astype(np.float64))
+        g.inner_p = [-1.0] * 4
+        g.face_p = [(-1.0 if t == W.ADIABATIC else 0.0) for t in g.face_type]
+    run = W.SteadyRun(n=n, seed=1006, tally_axis=1, per_bin=True, n_scat_max=10, max_events=10 ** 8)
+    return m, g, run
+
+
+@pytest.mark.parametrize("spec_low", [False, True])
+def test_fp64_nanomesh_internal_walls_per_particle(spec_low):
+    m, g, run = _nanomesh_case(3000, spec_low)
+    gg = gpu_steady(m, [g], [run.n], run, L.FP64_PLAIN, per_particle=True)
+    ref = oracle.run_steady(m, g, run, per_particle=True)
+    _check_fp64({"events_pp": gg["events_pp"], "X_pp": gg["X_pp"], "q_bin": gg["q_bin"][0]}, ref,
+                tallies=("q_bin",))
+    assert gg["stats"][0][L.STAT_KAPPA] == pytest.approx(ref["kappa"], rel=RTOL)
+
+
+def test_fp32_nanomesh_kappa_vs_oracle():
+    m, g, run = _nanomesh_case(200_000)
+    gg = gpu_steady(m, [g], [run.n], run, L.FP32_TRACE, seed=902)
+    ref = oracle.run_steady(m, g, run)
+    s = gg["stats"][0]
+    assert s[L.STAT_STATUS] == 0
+    assert abs(s[L.STAT_KAPPA] - ref["kappa"]) < 3.5 * np.hypot(s[L.STAT_KAPPA_SE], ref["kappa_se"])
+    ms, gs, _ = _nanomesh_case(200_000, spec_low=True)
+    gsp = gpu_steady(ms, [gs], [run.n], run, L.FP32_TRACE, seed=903)
+    assert gsp["stats"][0][L.STAT_KAPPA] > s[L.STAT_KAPPA] + 4 * np.hypot(gsp["stats"][0][L.STAT_KAPPA_SE],
+                                                                           s[L.STAT_KAPPA_SE])
+
+
 def test_fp64_film_batch_geometry_index_streams():
     wl = W.film_batch_c4(n_films=6)
     mat = wl.material
