@@ -239,6 +239,17 @@ def first_hit(geom, x_nm, u):
     return d.value, f.value
 
 
+def dir_about_vector(gv, sgn: float, mu: float, wphi: int) -> np.ndarray:
+    """Body-particle direction with polar cosine mu about sgn * gv (unit)."""
+    g = _f64(gv)
+    u = np.zeros(3)
+    f = lib().or_dir_about_vector
+    f.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_uint32, C.c_void_p]
+    f.restype = C.c_int
+    f(g.ctypes.data, float(sgn), float(mu), int(wphi), u.ctypes.data)
+    return u
+
+
 def in_hole(geom, x_nm: float, y_nm: float) -> bool:
     """True if (x, y) in nm lies inside a hole bounded by the internal walls."""
     keep = _Keep()

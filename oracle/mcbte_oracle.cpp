@@ -392,6 +392,8 @@ struct Setup {
   double E_tot = 0;
   int grad_axis = -1;
   double grad_sign = 0;
+  bool grad_general = false;   // more than one gradient component: Lambertian about gvec
+  double gvec[3] = {0, 0, 0};  // grad T / |grad T|
   double t_max_ps = 0;
   std::vector<double> t_meas_ps;
   double gauss_c[3], gauss_sigma;
@@ -450,11 +452,20 @@ int setup(const or_params* P, const Tables& t, Setup& S) {
   }
   int nz = 0;
   for (int a = 0; a < 3; ++a) if (P->grad_T[a] != 0.0) { nz++; S.grad_axis = a; }
-  if (nz > 1) return 2;
   if (nz == 1) {
     if (P->transient) return 2;
     double gmag = std::fabs(P->grad_T[S.grad_axis]);
     S.grad_sign = P->grad_T[S.grad_axis] > 0 ? 1.0 : -1.0;
+    double E = ((0.5 * V) * gmag) * t.sum_Cv;
+    S.src.push_back({1, -1, E});
+  } else if (nz > 1) {
+    // a control gradient in any direction: the same body source with |grad T|,
+    // particles Lambertian about -/+ grad T / |grad T| (Sec. 3.2.3)
+    if (P->transient) return 2;
+    double gmag = std::sqrt((P->grad_T[0] * P->grad_T[0] + P->grad_T[1] * P->grad_T[1]) + P->grad_T[2] * P->grad_T[2]);
+    S.grad_general = true;
+    S.grad_sign = 1.0;
+    for (int a = 0; a < 3; ++a) S.gvec[a] = P->grad_T[a] / gmag;
     double E = ((0.5 * V) * gmag) * t.sum_Cv;
     S.src.push_back({1, -1, E});
   }
@@ -547,6 +558,23 @@ inline void dir_about_axis(double u[3], int a, double sgn, double mu, uint32_t w
   u[(a + 2) % 3] = s * sn;
 }
 
+// Direction with polar cosine mu about sgn * gv (a unit vector): the
+// orthonormal frame {b1, b2, n} of n = sgn gv by the branchless construction
+// of Duff et al., "Building an Orthonormal Basis, Revisited" (JCGT 6(1),
+// 2017); u = mu n + s cos(phi) b1 + s sin(phi) b2, phi = 2 pi co(wphi).
+inline void dir_about_vector(double u[3], const double gv[3], double sgn, double mu, uint32_t wphi) {
+  const double n[3] = {sgn * gv[0], sgn * gv[1], sgn * gv[2]};
+  const double sg = n[2] >= 0.0 ? 1.0 : -1.0;
+  const double a = -1.0 / (sg + n[2]);
+  const double b = (n[0] * n[1]) * a;
+  const double b1[3] = {1.0 + ((sg * n[0]) * n[0]) * a, sg * b, -sg * n[0]};
+  const double b2[3] = {b, sg + (n[1] * n[1]) * a, -n[1]};
+  double s = std::sqrt(std::max(0.0, 1.0 - mu * mu));
+  double sn, cs;
+  series_sincos2pi(co32(wphi), &sn, &cs);
+  for (int k = 0; k < 3; ++k) u[k] = (mu * n[k] + (s * cs) * b1[k]) + (s * sn) * b2[k];
+}
+
 struct Partial {
   std::vector<double> T, Q, qbin, snap, G, dsum, dsum2;
   double scal[OR_NSCAL] = {0};
@@ -597,7 +625,8 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
       // positive particles travel down the control gradient, negative ones up it
       double dsgn = (s > 0.0) ? -S.grad_sign : S.grad_sign;
       double mu = std::sqrt(oc32(w[2]));
-      dir_about_axis(u, S.grad_axis, dsgn, mu, w[3]);
+      if (S.grad_general) dir_about_vector(u, S.gvec, dsgn, mu, w[3]);
+      else dir_about_axis(u, S.grad_axis, dsgn, mu, w[3]);
       // uniform position in the solid: attempt 0 uses sub 2, attempt j sub 2 + j
       for (int j = 0;; ++j) {
         if (j > 0) {
@@ -943,6 +972,12 @@ int or_first_hit(const or_params* P, const double x[3], const double u[3], doubl
     g.snx[k] = P->inner_n[k][0]; g.sny[k] = P->inner_n[k][1];
   }
   first_hit(g, x, u, dist, face);
+  return 0;
+}
+
+// The direction of a body particle about sgn * gv (pins of the frame).
+int or_dir_about_vector(const double gv[3], double sgn, double mu, uint32_t wphi, double u[3]) {
+  dir_about_vector(u, gv, sgn, mu, wphi);
   return 0;
 }
 

@@ -440,6 +440,56 @@ def test_frequency_dependent_specularity_fuchs_sondheimer():
     assert k - k_diffuse > 6 * r["kappa_se"]
 
 
+# ------------------------------------------------------------------ control gradient in any direction (Sec. 3.2.3)
+def test_dir_about_vector_is_an_orthonormal_frame():
+    rng = np.random.default_rng(41)
+    for _ in range(200):
+        gv = rng.normal(size=3)
+        if _ % 7 == 0:
+            gv = np.array([1e-3, 2e-3, -1.0])          # near the frame's -z branch point
+        gv /= np.linalg.norm(gv)
+        sgn = 1.0 if _ % 2 else -1.0
+        mu = rng.uniform(0, 1)
+        us = [oracle.dir_about_vector(gv, sgn, mu, w) for w in (0, 1 << 30, 1 << 31, 3 << 30)]
+        for u in us:
+            assert np.linalg.norm(u) == pytest.approx(1.0, abs=1e-12)
+            assert float(u @ (sgn * gv)) == pytest.approx(mu, abs=1e-12)
+        # quarter turns in phi are quarter turns about the axis
+        tang = [u - mu * sgn * gv for u in us]
+        if mu < 0.999:
+            r2 = 1 - mu * mu
+            for a, b in zip(tang, tang[1:] + tang[:1]):
+                assert float(a @ b) == pytest.approx(0.0, abs=1e-9)
+                assert float(np.cross(a, b) @ (sgn * gv)) == pytest.approx(r2, abs=1e-9)
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_kinetic_limit_diagonal_gradient(axis):
+    # bulk medium, control gradient along (1, 1, 0)/sqrt 2: q = -kappa grad T,
+    # so kappa measured along x or along y is the kinetic value
+    m = W.gray(6000.0, 100e-9, C=1e6)
+    g = W.film(1e-6)
+    g.face_type = [W.PERIODIC] * 6
+    g.grad_T = (-1e6 / math.sqrt(2), -1e6 / math.sqrt(2), 0.0)
+    run = W.SteadyRun(n=400_000, seed=42 + axis, tally_axis=axis, n_scat_max=3)
+    r = oracle.run_steady(m, g, run)
+    k = cf.kinetic_kappa([1e6], [6000.0], [100e-9 / 6000.0])
+    assert abs(r["kappa"] - k) < 3.5 * r["kappa_se"]
+    src = oracle.sources(m, g)
+    src1 = oracle.sources(m, W.film(1e-6))      # same box, same |grad T|: the same body source
+    assert src["E_tot"] == pytest.approx(src1["E_tot"], rel=1e-12)
+
+
+def test_film_in_plane_diagonal_gradient_fuchs_sondheimer():
+    m = W.gray(6000.0, 300e-9, C=1e6)
+    g = W.film(100e-9)
+    g.grad_T = (-1e6 * 0.6, -1e6 * 0.8, 0.0)
+    run = W.SteadyRun(n=300_000, seed=44, tally_axis=0, n_scat_max=10, max_events=10 ** 7)
+    r = oracle.run_steady(m, g, run)
+    fs = cf.fuchs_sondheimer([1e6], [6000.0], [300e-9 / 6000.0], 100e-9)
+    assert abs(r["kappa"] - fs) < 3.5 * r["kappa_se"]
+
+
 @pytest.mark.parametrize("d", [10e-9, 100e-9, 1e-6])
 def test_fuchs_sondheimer_films_bvk(d):
     m = W.bvk_holland()
