@@ -115,8 +115,9 @@ mcbte_status mcbte_material_tables(const mcbte_material* m, double* C, double* p
  * the box length, spatially varying control, Eq. periodic_lin_final).
  * Optional cylindrical pore parallel to z at (cx, cy) with radius r and
  * specularity p_pore (boundary ID 7).  grad_T is the uniform control
- * gradient of Sec. 2.5 (Eq. lin_spatial); it adds the body source of
- * Eq. grad_flux.  At most one component may be non-zero.  gauss adds an
+ * gradient of Sec. 2.5 (Eq. lin_spatial), in any direction; it adds the body
+ * source of Eq. grad_flux with |grad T|, particles Lambertian about
+ * -+grad T / |grad T| (Sec. 3.2.3).  gauss adds an
  * initial-condition source dT exp(-|x-c|^2 / 2 sigma^2) (transient only).
  * Internal walls (Sec. 4.2, In_bnd.txt): up to MCBTE_MAX_INNER adiabatic
  * segments (x1, y1, x2, y2) in the x-y plane running through the thickness,
@@ -128,9 +129,8 @@ mcbte_status mcbte_material_tables(const mcbte_material* m, double* C, double* p
  * (mcbte_material_desc.spec_bin; the run fails with MCBTE_ERR_INVALID_ARG if
  * the material has none).
  * Errors: L <= 0, periodic faces not paired on an axis, p above 1,
- * pore not inside the cell (r >= min(Lx,Ly)/2 or centre off), more than one
- * gradient component, walls outside the box or normals not of unit length
- * -> MCBTE_ERR_INVALID_ARG. */
+ * pore not inside the cell (r >= min(Lx,Ly)/2 or centre off), walls outside
+ * the box or normals not of unit length -> MCBTE_ERR_INVALID_ARG. */
 enum { MCBTE_FACE_ISOTHERMAL = 0, MCBTE_FACE_ADIABATIC = 1, MCBTE_FACE_PERIODIC = 2 };
 #define MCBTE_MAX_INNER 16
 

@@ -246,7 +246,7 @@ mcbte_status mcbte_geometry_create(const mcbte_geometry_desc* d, mcbte_geometry*
     if (!std::isfinite(d->grad_T[a])) return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: grad_T not finite");
     if (d->grad_T[a] != 0.0) ++ng;
   }
-  if (ng > 1) return fail(MCBTE_ERR_INVALID_ARG, "geometry_create: at most one grad_T component");
+  (void)ng;   // any direction (Sec. 3.2.3); a single component keeps the axis-aligned emission
   if (d->pore) {
     const double r = d->pore_r, cx = d->pore_c[0], cy = d->pore_c[1];
     if (!finite_pos(r) || !(cx - r > 0.0) || !(cx + r < d->L[0]) || !(cy - r > 0.0) || !(cy + r < d->L[1]))
@@ -308,6 +308,14 @@ bool uses_spec_bin(const mcbte_geometry_desc& d) {
   for (int k = 0; k < d.n_inner; ++k)
     if (d.inner_p[k] < 0.0) return true;
   return false;
+}
+
+// The run needs the tracers' extended paths: a two-phonon clock, internal
+// walls, per-bin specularity or a control gradient off the axes.
+bool uses_ext(const mcbte_material* m, const mcbte_geometry_desc& d) {
+  int nz = 0;
+  for (int a = 0; a < 3; ++a) nz += d.grad_T[a] != 0.0;
+  return m->view.imp || d.n_inner > 0 || uses_spec_bin(d) || nz > 1;
 }
 
 bool has_gradient(const mcbte_geometry_desc& d) {
@@ -494,6 +502,8 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   C.seed_dev = reinterpret_cast<const unsigned long long*>(p->seed_device);
   C.refill_min = p->refill_threshold;
   C.cell_flux_axis = p->cell_flux_axis ? 1 : 0;
+  C.ext = 0;
+  for (int g = 0; g < G; ++g) C.ext |= uses_ext(m, geoms[g]->host) ? 1 : 0;
   Acc A{};
   A.cellP = w.cellP;
   A.cellD = w.cellD;
@@ -777,6 +787,7 @@ mcbte_status mcbte_run_transient(const mcbte_material* m, const mcbte_geometry* 
   C.t0 = w.t0;
   C.budget_ns = (uint64_t)((p->time_budget_s > 0 ? p->time_budget_s : 120.0) * 1e9);
   C.t_max_ps = p->t_max * 1e12;
+  C.ext = uses_ext(m, g->host) ? 1 : 0;
   C.n_times = p->n_times;
   C.t_meas_ps = w.t_meas_ps;
   for (int k = 0; k < 3; ++k) C.grid[k] = p->grid[k];

@@ -54,6 +54,9 @@ struct GeoRun {
   double face_sign[6];         // sign of T_b - T_eq of isothermal faces
   int grad_axis;
   double grad_sign;
+  int grad_general;            // gradient with several components: Lambertian about -+grad T
+  double gframe[2][9];         // frames {n, b1, b2} about -grad T/|grad T| ([0]) and +grad T/|grad T| ([1])
+  float gframef[2][9];
   double gauss_c[3];
   double gauss_sigma;
   double gauss_sign;
@@ -254,9 +257,35 @@ __device__ __forceinline__ void dir_about_axis(R u[3], int a, R sgn, R mu, uint3
   put3_cyclic<R>(u, a, sgn * mu, s * cs, s * sn);
 }
 
+// Orthonormal frame {n, b1, b2} of n = sgn gv (gv a unit vector) by the
+// branchless construction of Duff et al., "Building an Orthonormal Basis,
+// Revisited" (JCGT 2017); f = {n, b1, b2} (9 values).
+__host__ __device__ __forceinline__ void frame_about(const double gv[3], double sgn, double f[9]) {
+  const double n0 = sgn * gv[0], n1 = sgn * gv[1], n2 = sgn * gv[2];
+  const double sg = n2 >= 0.0 ? 1.0 : -1.0;
+  const double a = -1.0 / (sg + n2);
+  const double b = (n0 * n1) * a;
+  f[0] = n0; f[1] = n1; f[2] = n2;
+  f[3] = 1.0 + ((sg * n0) * n0) * a; f[4] = sg * b; f[5] = -sg * n0;
+  f[6] = b; f[7] = sg + (n1 * n1) * a; f[8] = -n1;
+}
+
+// Direction with polar cosine mu about the frame's n:
+// u = mu n + s cos(phi) b1 + s sin(phi) b2, phi = 2 pi co(wphi).
+template <typename R>
+__device__ __forceinline__ void dir_about_frame(R u[3], const R* f, R mu, uint32_t wphi) {
+  const R s = Num<R>::sqrt_(Num<R>::fmax_(R(0), R(1) - mu * mu));
+  R sn, cs;
+  Num<R>::sincos2pi(Num<R>::co(wphi), &sn, &cs);
+  const R sc = s * cs, ss = s * sn;
+  u[0] = (mu * f[0] + sc * f[3]) + ss * f[6];
+  u[1] = (mu * f[1] + sc * f[4]) + ss * f[7];
+  u[2] = (mu * f[2] + sc * f[5]) + ss * f[8];
+}
+
 // First boundary along the ray (faces in the direction of travel, then the
 // pore cylinder); ties go to the lowest paper boundary ID.
-template <typename R>
+template <typename R, bool EXT = true>
 __device__ __forceinline__ void first_hit(const GeoRun& g, const R x[3], const R u[3], R* dist, int* face) {
   R best = Num<R>::big();
   int bf = 7;
@@ -291,7 +320,7 @@ __device__ __forceinline__ void first_hit(const GeoRun& g, const R x[3], const R
   // internal walls (faces 7, 8, ...), met only from their solid side; a
   // particle behind a wall's line by more than rounding is beyond the hole
   const R tol = sizeof(R) == 8 ? R(1e-9) : R(1e-4);
-  for (int k = 0; k < g.n_inner; ++k) {
+  for (int k = 0; k < (EXT ? g.n_inner : 0); ++k) {
     const R nx = sizeof(R) == 8 ? (R)g.snx[k] : (R)g.snxf[k];
     const R ny = sizeof(R) == 8 ? (R)g.sny[k] : (R)g.snyf[k];
     const R un = u[0] * nx + u[1] * ny;

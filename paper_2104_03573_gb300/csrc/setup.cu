@@ -93,13 +93,34 @@ __global__ void k_setup(SetupArgs a, int G, MatView M, int transient, double t_m
   }
   r.grad_axis = 0;
   r.grad_sign = 0.0;
+  r.grad_general = 0;
+  int nz = 0;
   for (int k = 0; k < 3; ++k)
     if (d.grad_T[k] != 0.0) {
+      ++nz;
       r.grad_axis = k;
       r.grad_sign = d.grad_T[k] > 0.0 ? 1.0 : -1.0;
     }
-  if (r.grad_sign != 0.0) {
+  if (nz == 1) {
     E[ns] = ((0.5 * V) * fabs(d.grad_T[r.grad_axis])) * sum_Cv;
+    r.src_kind[ns] = 1;
+    r.src_face[ns] = -1;
+    ++ns;
+  } else if (nz > 1) {
+    // gradient in any direction: |grad T| for the source, Lambertian about
+    // +-grad T / |grad T| (Sec. 3.2.3)
+    const double gmag = sqrt((d.grad_T[0] * d.grad_T[0] + d.grad_T[1] * d.grad_T[1]) + d.grad_T[2] * d.grad_T[2]);
+    r.grad_general = 1;
+    r.grad_sign = 1.0;
+    double gv[3];
+    for (int k = 0; k < 3; ++k) gv[k] = d.grad_T[k] / gmag;
+    frame_about(gv, -1.0, r.gframe[0]);
+    frame_about(gv, 1.0, r.gframe[1]);
+    for (int k = 0; k < 9; ++k) {
+      r.gframef[0][k] = (float)r.gframe[0][k];
+      r.gframef[1][k] = (float)r.gframe[1][k];
+    }
+    E[ns] = ((0.5 * V) * gmag) * sum_Cv;
     r.src_kind[ns] = 1;
     r.src_face[ns] = -1;
     ++ns;

@@ -46,6 +46,7 @@ struct RunCfg {
   const double* t_meas_ps;
   int grid[3];
   int cell_flux_axis;   // FP32 cell tallies: T and the tally-axis flux only
+  int ext;              // extended physics in use (two-phonon clock, walls, per-bin d, general gradient)
   // FP32 transient time windows: this launch takes the snapshots with index
   // < win_end; the first window emits, later ones resume saved particles
   int win_first, win_last, win_end;
@@ -125,12 +126,16 @@ __device__ __forceinline__ R draw_d2(const Particle<R>& p, const MatView& M, con
 // mu = sqrt(R) about a face normal or the gradient (Lambertian, Eq. wall_dir)
 // or mu = 1 - 2R (isotropic, Eq. angle_gen), new relaxation distance
 // Lambda (-ln R) (Eq. time_to_scat).  w, w1 are the event's sub-blocks 0 and 1.
-template <typename R>
+// axis 3: Lambertian about the frame `fr` (control gradient in a general
+// direction; the frame already carries the sign).
+template <typename R, bool EXT = true>
 __device__ __forceinline__ void resample(Particle<R>& p, const MatView& M, const uint4* rec, const float4* binf,
-                                         uint4 w, uint4 w1, bool lambert, int axis, R sgn) {
+                                         uint4 w, uint4 w1, bool lambert, int axis, R sgn,
+                                         const R* fr = nullptr) {
   p.bin = alias_draw(rec, M.n, w.x, w.y, w1.x);
   const R mu = lambert ? Num<R>::sqrt_(Num<R>::oc(w.z)) : R(1) - R(2) * Num<R>::oc(w.z);
-  dir_about_axis<R>(p.u, axis, sgn, mu, w.w);
+  if (EXT && axis == 3) dir_about_frame<R>(p.u, fr, mu, w.w);
+  else dir_about_axis<R>(p.u, axis, sgn, mu, w.w);
   load_bin(p, M, binf);
   p.d_rel = p.lam * (-Num<R>::log_(Num<R>::oc53(w1.y, w1.z)));
 }
@@ -140,7 +145,7 @@ __device__ __forceinline__ void resample(Particle<R>& p, const MatView& M, const
 // further body-position attempts from sub 2 + j, Box-Muller from sub 3).
 // Returns the direction law for resample(): table (0 ~C v, 1 ~C), Lambertian
 // or isotropic, axis and sign.
-template <typename R>
+template <typename R, bool EXT = true>
 __device__ __forceinline__ void emit_prologue(Particle<R>& p, const GeoRun& g, uint32_t k0, uint32_t k1,
                                               bool transient, R t_max_ps, uint4 w1, int* table, bool* lambert,
                                               int* axis, R* sgn) {
@@ -168,7 +173,7 @@ __device__ __forceinline__ void emit_prologue(Particle<R>& p, const GeoRun& g, u
     p.s = (w2.w < 0x80000000u) ? R(1) : R(-1);
     *table = 0;
     *lambert = true;
-    *axis = g.grad_axis;
+    *axis = (EXT && g.grad_general) ? 3 : g.grad_axis;
     // positive particles travel down the control gradient, negative ones up it
     *sgn = (p.s > R(0)) ? (R)(-g.grad_sign) : (R)g.grad_sign;
     const R cx = sizeof(R) == 8 ? (R)g.cx : (R)g.cxf;
@@ -188,7 +193,7 @@ __device__ __forceinline__ void emit_prologue(Particle<R>& p, const GeoRun& g, u
         const R dx = p.x[0] - cx, dy = p.x[1] - cy;
         inside = dx * dx + dy * dy < r2;
       }
-      if (!inside && g.n_inner > 0) inside = in_hole<R>(g, p.x[0], p.x[1]);
+      if (EXT && !inside && g.n_inner > 0) inside = in_hole<R>(g, p.x[0], p.x[1]);
       if (!inside) break;
       if (j + 1 >= 64u) break;
     }
@@ -238,8 +243,10 @@ __device__ __forceinline__ void particle_reset_counters(Particle<double>& p) {
 
 // Emission of particle (pid, g) at event 0: the emission prologue, then the
 // shared resampling step with the source's bin law and direction law.
-// IMP: the material may have a two-phonon clock (else d2 is never drawn).
-template <typename R, bool IMP = true>
+// EXT: the run uses extended physics (a two-phonon clock, internal walls,
+// per-bin specularity, a control gradient off the axes); without it those
+// paths are compiled out.
+template <typename R, bool EXT = true>
 __device__ __forceinline__ void emit(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_emit,
                                      const uint4* rec_init, const float4* binf, uint32_t k0, uint32_t k1,
                                      bool transient, R t_max_ps) {
@@ -251,10 +258,14 @@ __device__ __forceinline__ void emit(Particle<R>& p, const GeoRun& g, const MatV
   bool lambert;
   int axis;
   R sgn;
-  emit_prologue<R>(p, g, k0, k1, transient, t_max_ps, w1, &table, &lambert, &axis, &sgn);
-  resample<R>(p, M, table ? rec_init : rec_emit, binf, w, w1, lambert, axis, sgn);
+  emit_prologue<R, EXT>(p, g, k0, k1, transient, t_max_ps, w1, &table, &lambert, &axis, &sgn);
+  const int fi = sgn > R(0) ? 1 : 0;
+  const R* fr = nullptr;
+  if constexpr (sizeof(R) == 8) fr = reinterpret_cast<const R*>(g.gframe[fi]);
+  else fr = reinterpret_cast<const R*>(g.gframef[fi]);
+  resample<R, EXT>(p, M, table ? rec_init : rec_emit, binf, w, w1, lambert, axis, sgn, fr);
   particle_reset_counters(p);
-  if constexpr (IMP) p.d2 = draw_d2(p, M, binf, k0, k1);
+  if constexpr (EXT) p.d2 = draw_d2(p, M, binf, k0, k1);
 }
 
 // ------------------------------------------------------------------ tally policies
@@ -574,7 +585,7 @@ enum { STEP_ALIVE = 0, STEP_ABSORBED = 1, STEP_DONE = 2, STEP_TRUNCATED = 3 };
 // to the opposite face; adiabatic / pore: specular with probability p, else
 // Lambertian about the inward normal).  The particle has already moved.
 // `Xnow` is the particle's tally so far (gradient bookkeeping only).
-template <typename R, class Grad, class Tally, bool IMP = true>
+template <typename R, class Grad, class Tally, bool EXT = true>
 __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_relax,
                                            const float4* binf, const RunCfg& C, uint32_t k0, uint32_t k1,
                                            bool relax, bool relax2, int face, R seg, const Tally& T, Grad& gr,
@@ -590,12 +601,12 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
     ctr.w = 1u;
     const uint4 w1 = philox(ctr, k0, k1);
     resample<R>(p, M, rec_relax, binf, w, w1, false, 2, R(1));
-    if constexpr (IMP) p.d2 = draw_d2(p, M, binf, k0, k1);   // both clocks restart in the new mode (Sec. 3.3 (i))
+    if constexpr (EXT) p.d2 = draw_d2(p, M, binf, k0, k1);   // both clocks restart in the new mode (Sec. 3.3 (i))
     if (Grad::on) gr.resampled(p.bin, Xnow);
     return STEP_ALIVE;
   }
   p.d_rel = p.d_rel - seg;
-  if constexpr (IMP) {
+  if constexpr (EXT) {
     if (relax2) {
       // two-phonon scattering (Sec. 3.5.1, Sec. 3.3 (ii)): same mode, new
       // isotropic direction, new two-phonon clock; the three-phonon clock runs on
@@ -621,7 +632,7 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
     }
     put3<R>(p.x, a, mx ? La : R(0));
     const uint4 w = philox(ctr, k0, k1);
-    if ((uint64_t)w.x < (((g.fbin >> face) & 1) ? M.spec_thr[p.bin] : g.pthr[face])) {
+    if ((uint64_t)w.x < ((EXT && ((g.fbin >> face) & 1)) ? M.spec_thr[p.bin] : g.pthr[face])) {
       put3<R>(p.u, a, -sel3(p.u, a));
     } else {
       dir_about_axis<R>(p.u, a, mx ? R(-1) : R(1), Num<R>::sqrt_(Num<R>::oc(w.z)), w.w);
@@ -631,7 +642,7 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
   R nx, ny;
   bool spec;
   const uint4 w = philox(ctr, k0, k1);
-  if (face >= 7) {
+  if (EXT && face >= 7) {
     // internal wall (Sec. 4.2): onto its line, then reflect about its normal
     const int k = face - 7;
     nx = sizeof(R) == 8 ? (R)g.snx[k] : (R)g.snxf[k];
@@ -674,18 +685,18 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
 // remaining relaxation distance (boundary wins ties, Sec. 3.3 case iii),
 // track-length tallies of the flight (Eqs. temp_steady, flux_x_steady), then
 // the event.
-template <typename R, class Grad, class Tally, bool IMP = true>
+template <typename R, class Grad, class Tally, bool EXT = true>
 __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_relax,
                                            const float4* binf, const RunCfg& C, uint32_t k0, uint32_t k1,
                                            const Tally& T, Grad& gr) {
   if (p.e + 1u >= C.max_events) return STEP_TRUNCATED;
   R db;
   int face;
-  first_hit<R>(g, p.x, p.u, &db, &face);
+  first_hit<R, EXT>(g, p.x, p.u, &db, &face);
   // nearest of the two scattering clocks and the boundary (Sec. 3.3): the
   // boundary wins ties, the three-phonon clock wins a tie with the two-phonon one
-  const bool relax = IMP ? (p.d_rel < db && p.d_rel <= p.d2) : p.d_rel < db;
-  const bool relax2 = IMP && !relax && p.d2 < db;
+  const bool relax = EXT ? (p.d_rel < db && p.d_rel <= p.d2) : p.d_rel < db;
+  const bool relax2 = EXT && !relax && p.d2 < db;
   const R seg = relax ? p.d_rel : (relax2 ? p.d2 : db);
   double Xb = 0.0;
   if (Grad::on) Xb = T.X(p);
@@ -693,7 +704,7 @@ __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, cons
   if (Grad::on) gr.flight(relax, (double)(seg / p.lam), Xb, c);
 #pragma unroll
   for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
-  return apply_event<R, Grad, Tally, IMP>(p, g, M, rec_relax, binf, C, k0, k1, relax, relax2, face, seg, T, gr,
+  return apply_event<R, Grad, Tally, EXT>(p, g, M, rec_relax, binf, C, k0, k1, relax, relax2, face, seg, T, gr,
                                             Grad::on ? T.X(p) : 0.0);
 }
 
@@ -704,7 +715,7 @@ __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, cons
 // `tmeas`: the measurement times in ps (FP64 path: the global array; FP32
 // path: a float copy in shared memory).  `cinv`: cells per nm along x, y, z
 // (FP32 path only; the FP64 path divides by the cell size, the CPU reference form).
-template <typename R, bool IMP = true>
+template <typename R, bool EXT = true>
 __device__ __forceinline__ int step_transient(Particle<R>& p, const GeoRun& g, const MatView& M,
                                               const uint4* rec_relax, const float4* binf, const RunCfg& C,
                                               uint32_t k0, uint32_t k1, double* snap, const R* tmeas,
@@ -712,15 +723,15 @@ __device__ __forceinline__ int step_transient(Particle<R>& p, const GeoRun& g, c
   if (p.e + 1u >= C.max_events) return STEP_TRUNCATED;
   R db;
   int face;
-  first_hit<R>(g, p.x, p.u, &db, &face);
+  first_hit<R, EXT>(g, p.x, p.u, &db, &face);
   const R v = p.v;
   const R tmax = (R)C.t_max_ps;
   const R d_end = (tmax - p.t) * v;
   bool fin = false, relax = false, relax2 = false;
   R seg;
-  if (d_end <= p.d_rel && d_end <= db && (!IMP || d_end <= p.d2)) { fin = true; seg = d_end; }
-  else if (p.d_rel < db && (!IMP || p.d_rel <= p.d2)) { relax = true; seg = p.d_rel; }
-  else if (IMP && p.d2 < db) { relax2 = true; seg = p.d2; }
+  if (d_end <= p.d_rel && d_end <= db && (!EXT || d_end <= p.d2)) { fin = true; seg = d_end; }
+  else if (p.d_rel < db && (!EXT || p.d_rel <= p.d2)) { relax = true; seg = p.d_rel; }
+  else if (EXT && p.d2 < db) { relax2 = true; seg = p.d2; }
   else { seg = db; }
   // the flight ended by t_max ends at t_max exactly (Sec. 3.5.6), so a
   // measurement at t_max samples every particle still alive
@@ -778,7 +789,7 @@ __device__ __forceinline__ int step_transient(Particle<R>& p, const GeoRun& g, c
   for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
   if (fin) return STEP_DONE;
   GradOff off;
-  return apply_event<R, GradOff, TallyNone, IMP>(p, g, M, rec_relax, binf, C, k0, k1, relax, relax2, face, seg, TallyNone(), off,
+  return apply_event<R, GradOff, TallyNone, EXT>(p, g, M, rec_relax, binf, C, k0, k1, relax, relax2, face, seg, TallyNone(), off,
                                             0.0);
 }
 

@@ -178,7 +178,7 @@ __device__ __forceinline__ void grad_finish_replay(GradReplay& gr, double X, int
 // only, and flags (bit 2) any particle whose replayed tally differs.
 // CELLS: 0 no cell tallies, 1 T and three flux components, 2 T and the
 // tally-axis flux only.
-template <int CELLS, bool GRAD, int TPB, bool IMP>
+template <int CELLS, bool GRAD, int TPB, bool EXT>
 __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict__ geos,
                                                        const uint64_t* __restrict__ offs, MatView M, RunCfg C,
                                                        Acc A, SmemPlan S) {
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
         G = &geos[g];
         p.pid = (uint32_t)(idx - offs[g]);
         p.g = g;
-        emit<float, IMP>(p, *G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, false, 0.0f);
+        emit<float, EXT>(p, *G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, false, 0.0f);
         if constexpr (GRAD) {
           gr.init(p.bin);
           gr.Xf = A.X_pp[idx];
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
       }
     }
     if (!alive) continue;
-    int out = step_steady<float, typename GradPick<GRAD, GradReplay>::type, decltype(T), IMP>(p, *G, M, relax, binf, C, key.x,
+    int out = step_steady<float, typename GradPick<GRAD, GradReplay>::type, decltype(T), EXT>(p, *G, M, relax, binf, C, key.x,
                                                                                   key.y, T, gr);
     if (out == STEP_ALIVE && (p.e & 255u) == 0u && globaltimer_ns() > deadline) {
       atomicOr(A.flags, 1);
@@ -449,11 +449,11 @@ cudaError_t launch_f64(const GeoRun* geos, const uint64_t* offs, const MatView& 
 #endif  // MCBTE_F64
 
 #if MCBTE_F32
-template <int CELLS, bool GRAD, int TPB, bool IMP>
+template <int CELLS, bool GRAD, int TPB, bool EXT>
 cudaError_t launch_f32_tpb(const GeoRun* geos, const uint64_t* offs, const MatView& M, const RunCfg& C,
                            const Acc& A, int bps, cudaStream_t s) {
   const SmemPlan S = plan_smem_f32(M.n, C.n_geoms, GRAD ? 0 : C.n_cells, GRAD ? 0 : C.per_bin, 200 * 1024);
-  auto kern = k_steady_f32<CELLS, GRAD, TPB, IMP>;
+  auto kern = k_steady_f32<CELLS, GRAD, TPB, EXT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.bytes);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -465,24 +465,24 @@ cudaError_t launch_f32_tpb(const GeoRun* geos, const uint64_t* offs, const MatVi
   return cudaGetLastError();
 }
 
-template <int CELLS, bool GRAD, bool IMP>
-cudaError_t launch_f32_imp(const GeoRun* geos, const uint64_t* offs, const MatView& M, const RunCfg& C, const Acc& A,
+template <int CELLS, bool GRAD, bool EXT>
+cudaError_t launch_f32_ext(const GeoRun* geos, const uint64_t* offs, const MatView& M, const RunCfg& C, const Acc& A,
                            int threads, int bps, cudaStream_t s) {
   switch (threads) {
-    case 256: return launch_f32_tpb<CELLS, GRAD, 256, IMP>(geos, offs, M, C, A, bps, s);
-    case 512: return launch_f32_tpb<CELLS, GRAD, 512, IMP>(geos, offs, M, C, A, bps, s);
-    case 768: return launch_f32_tpb<CELLS, GRAD, 768, IMP>(geos, offs, M, C, A, bps, s);
-    case 1024: return launch_f32_tpb<CELLS, GRAD, 1024, IMP>(geos, offs, M, C, A, bps, s);
+    case 256: return launch_f32_tpb<CELLS, GRAD, 256, EXT>(geos, offs, M, C, A, bps, s);
+    case 512: return launch_f32_tpb<CELLS, GRAD, 512, EXT>(geos, offs, M, C, A, bps, s);
+    case 768: return launch_f32_tpb<CELLS, GRAD, 768, EXT>(geos, offs, M, C, A, bps, s);
+    case 1024: return launch_f32_tpb<CELLS, GRAD, 1024, EXT>(geos, offs, M, C, A, bps, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-// The two-phonon clock is compiled in only for materials that have one.
+// The extended physics is compiled in only for runs that use it.
 template <int CELLS, bool GRAD>
 cudaError_t launch_f32(const GeoRun* geos, const uint64_t* offs, const MatView& M, const RunCfg& C, const Acc& A,
                        int threads, int bps, cudaStream_t s) {
-  return M.imp ? launch_f32_imp<CELLS, GRAD, true>(geos, offs, M, C, A, threads, bps, s)
-               : launch_f32_imp<CELLS, GRAD, false>(geos, offs, M, C, A, threads, bps, s);
+  return C.ext ? launch_f32_ext<CELLS, GRAD, true>(geos, offs, M, C, A, threads, bps, s)
+               : launch_f32_ext<CELLS, GRAD, false>(geos, offs, M, C, A, threads, bps, s);
 }
 #endif  // MCBTE_F32
 

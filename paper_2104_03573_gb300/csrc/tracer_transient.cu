@@ -119,7 +119,7 @@ __device__ __forceinline__ bool load_state(const uint4* st, uint64_t idx, Partic
 
 // Shared memory: the measurement times as float (always), then the relaxation
 // alias records and per-bin constants where the plan has room.
-template <int TPB, bool IMP>
+template <int TPB, bool EXT>
 __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restrict__ geos, MatView M, RunCfg C,
                                                           Acc A, SmemPlan S) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
         if (C.win_first) {
           p.pid = (uint32_t)idx;
           p.g = 0;
-          emit<float, IMP>(p, G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, true, (float)C.t_max_ps);
+          emit<float, EXT>(p, G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, true, (float)C.t_max_ps);
           transient_start(p, C);
           if (!C.win_last && p.mi >= C.win_end) {   // emitted after this window's last snapshot
             save_state(A.tstate, idx, p);
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
       }
     }
     if (!alive) continue;
-    int out = step_transient<float, IMP>(p, G, M, relax, binf, C, key.x, key.y, A.snap, tmeas, cinv);
+    int out = step_transient<float, EXT>(p, G, M, relax, binf, C, key.x, key.y, A.snap, tmeas, cinv);
     if (out == STEP_ALIVE && (p.e & 255u) == 0u && globaltimer_ns() > deadline) {
       atomicOr(A.flags, 1);
       out = STEP_TRUNCATED;
@@ -274,13 +274,13 @@ cudaError_t launch_transient(int precision, const GeoRun* geos, const MatView& M
 #endif  // MCBTE_F64
 #if MCBTE_F32
 namespace {
-template <int TPB, bool IMP>
+template <int TPB, bool EXT>
 cudaError_t launch_transient_tpb(const GeoRun* geos, const MatView& M, const RunCfg& C, const Acc& A, int bps,
                                  cudaStream_t s) {
   const size_t tm_bytes = ((size_t)C.n_times * sizeof(float) + 15) & ~(size_t)15;
   SmemPlan S = plan_smem_f32(M.n, 1, 0, 0, 200 * 1024 - tm_bytes);
   S.bytes += tm_bytes;
-  auto kern = k_transient_f32<TPB, IMP>;
+  auto kern = k_transient_f32<TPB, EXT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.bytes);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -295,7 +295,7 @@ cudaError_t launch_transient_tpb(const GeoRun* geos, const MatView& M, const Run
 
 cudaError_t launch_transient_f32(const GeoRun* geos, const MatView& M, const RunCfg& C, const Acc& A, int threads,
                                  int bps, cudaStream_t s) {
-  const bool imp = M.imp != 0;   // the two-phonon clock is compiled in only when present
+  const bool imp = C.ext != 0;   // the extended physics is compiled in only when used
   switch (threads) {
     case 256: return imp ? launch_transient_tpb<256, true>(geos, M, C, A, bps, s)
                          : launch_transient_tpb<256, false>(geos, M, C, A, bps, s);

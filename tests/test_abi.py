@@ -62,7 +62,7 @@ def test_geometry_validation_rejects_before_cuda(lib):
     p.pore_r = 60e-9
     assert lib.mcbte_geometry_create(C.byref(api.geometry_desc(p)), C.byref(h)) == _lib.ERR_INVALID_ARG
     g2 = W.film(10e-9)
-    g2.grad_T = (1.0, 1.0, 0.0)
+    g2.grad_T = (1.0, float("nan"), 0.0)            # any direction, but finite
     assert lib.mcbte_geometry_create(C.byref(api.geometry_desc(g2)), C.byref(h)) == _lib.ERR_INVALID_ARG
     g3 = W.film(10e-9, p=1.5)
     assert lib.mcbte_geometry_create(C.byref(api.geometry_desc(g3)), C.byref(h)) == _lib.ERR_INVALID_ARG

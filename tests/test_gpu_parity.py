@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import closed_forms as cf
 from inputs import workloads as W
 from gpu_helpers import batch_stats, gpu_steady, gpu_transient, rel_close, z_scores
 
@@ -181,6 +182,27 @@ def test_fp32_nanomesh_kappa_vs_oracle():
     gsp = gpu_steady(ms, [gs], [run.n], run, L.FP32_TRACE, seed=903)
     assert gsp["stats"][0][L.STAT_KAPPA] > s[L.STAT_KAPPA] + 4 * np.hypot(gsp["stats"][0][L.STAT_KAPPA_SE],
                                                                            s[L.STAT_KAPPA_SE])
+
+
+def test_fp64_and_fp32_diagonal_control_gradient():
+    # control gradient with several components (Lambertian frame about grad T)
+    wl = W.pore_film_c5(n=4000)
+    m, g, run = wl.material, wl.geometries[0], wl.run
+    g.grad_T = (-0.6e6, -0.8e6, 0.0)
+    run.max_events = 10 ** 8
+    gg = gpu_steady(m, [g], [run.n], run, L.FP64_PLAIN, per_particle=True)
+    ref = oracle.run_steady(m, g, run, per_particle=True)
+    _check_fp64({"events_pp": gg["events_pp"], "X_pp": gg["X_pp"], "q_bin": gg["q_bin"][0]}, ref,
+                tallies=("q_bin",))
+    mg = W.gray(6000.0, 100e-9, C=1e6)
+    gb = W.film(1e-6)
+    gb.face_type = [W.PERIODIC] * 6
+    gb.grad_T = (-1e6 / np.sqrt(2), -1e6 / np.sqrt(2), 0.0)
+    rb = W.SteadyRun(n=1_000_000, seed=45, tally_axis=0, n_scat_max=3)
+    g32 = gpu_steady(mg, [gb], [rb.n], rb, L.FP32_TRACE)
+    k = cf.kinetic_kappa([1e6], [6000.0], [100e-9 / 6000.0])
+    s32 = g32["stats"][0]
+    assert abs(s32[L.STAT_KAPPA] - k) < 3.5 * s32[L.STAT_KAPPA_SE]
 
 
 def test_fp64_film_batch_geometry_index_streams():
