@@ -189,6 +189,9 @@ class TransientRun:
     t_meas: np.ndarray
     grid: Sequence[int]
     max_events: int = 10 ** 9
+    # detector regions (Sec. 4.5): ((xmin, xmax, ymin, ymax, zmin, zmax) m, (nx, ny, nz));
+    # empty: the whole box split by `grid`
+    regions: Sequence = ()
 
 
 @dataclass

@@ -52,6 +52,7 @@ class _Params(C.Structure):
         ("n_scat_max", C.c_int), ("max_events", C.c_uint64),
         ("n_cells", C.c_int), ("cell_axis", C.c_int), ("tally_axis", C.c_int),
         ("t_max", C.c_double), ("n_times", C.c_int), ("t_meas", C.c_void_p), ("grid", C.c_int * 3),
+        ("n_regions", C.c_int), ("regions", C.c_void_p), ("region_grid", C.c_void_p),
         ("want_grad", C.c_int), ("n_dirs", C.c_int), ("dirs", C.c_void_p), ("n_threads", C.c_int),
     ]
 
@@ -368,7 +369,19 @@ def run_transient(material, geom, run, *, pid_begin: int = 0, pid_end: Optional[
                 tally_axis=2, n_threads=int(n_threads))
     P.grid[:] = [nx, ny, nz]
     nt = t_meas.shape[0]
-    snap = np.zeros((nt, nz, ny, nx, 4))
+    regions = list(getattr(run, "regions", ()) or ())
+    if regions:
+        boxes = keep.add(np.ascontiguousarray([r[0] for r in regions], dtype=np.float64))
+        grids = keep.add(np.ascontiguousarray([r[1] for r in regions], dtype=np.int32))
+        P.n_regions, P.regions, P.region_grid = len(regions), boxes.ctypes.data, grids.ctypes.data
+        n_det = int(sum(int(np.prod(r[1])) for r in regions))
+        snap = np.zeros((nt, n_det, 4))
+        v_det = np.concatenate([np.full(int(np.prod(r[1])),
+                                        np.prod(np.asarray(r[0])[1::2] - np.asarray(r[0])[0::2]) / np.prod(r[1]))
+                                for r in regions])
+    else:
+        snap = np.zeros((nt, nz, ny, nx, 4))
+        v_det = float(geom.L[0] * geom.L[1] * geom.L[2]) / (nx * ny * nz)
     npp = pe - int(pid_begin)
     ev = np.zeros(npp, dtype=np.uint32) if per_particle else None
     O = _Out()
@@ -379,9 +392,10 @@ def run_transient(material, geom, run, *, pid_begin: int = 0, pid_end: Optional[
         raise ValueError(f"oracle run failed ({rc})")
     sc = np.array(O.scal[:])
     E_eff = sc[ETOT] / N
-    Vc = float(geom.L[0] * geom.L[1] * geom.L[2]) / (nx * ny * nz)
+    Vc = v_det if regions else np.float64(v_det)
+    vb = Vc[None, :] if regions else Vc
     out = np.empty_like(snap)
-    out[..., 0] = (E_eff / (sc[CTOT] * Vc)) * snap[..., 0]
-    out[..., 1:] = (E_eff / Vc) * snap[..., 1:] * 1e3
+    out[..., 0] = (E_eff / (sc[CTOT] * vb)) * snap[..., 0]
+    out[..., 1:] = (E_eff / vb)[..., None] * snap[..., 1:] * 1e3 if regions else (E_eff / vb) * snap[..., 1:] * 1e3
     return {"raw": snap, "tally": out, "scal": sc, "events_pp": ev, "events": sc[EVENTS],
             "E_tot": sc[ETOT], "C_tot": sc[CTOT], "N": N, "V_cell": Vc}

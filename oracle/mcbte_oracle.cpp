@@ -255,6 +255,11 @@ typedef struct {
   int n_times;
   const double* t_meas;   // s
   int grid[3];
+  // detector regions (Sec. 4.5, Measure_region): axis-aligned cuboids, each
+  // split into nx x ny x nz detectors; none: the whole box with `grid`
+  int n_regions;
+  const double* regions;      // [n_regions][6] xmin, xmax, ymin, ymax, zmin, zmax (m)
+  const int* region_grid;     // [n_regions][3]
   int want_grad;
   int n_dirs;
   const double* dirs;     // [n_dirs][n_bins]
@@ -398,6 +403,14 @@ struct Setup {
   std::vector<double> t_meas_ps;
   double gauss_c[3], gauss_sigma;
   double dpi_dirs[64];
+  struct Region {
+    double lo[3], hi[3];   // nm
+    int n[3];
+    size_t off;            // first detector of the region
+    bool whole;            // the whole box (every position inside, clamped to the grid)
+  };
+  std::vector<Region> regs;
+  size_t n_det = 0;
 };
 
 int setup(const or_params* P, const Tables& t, Setup& S) {
@@ -488,6 +501,32 @@ int setup(const or_params* P, const Tables& t, Setup& S) {
   }
   S.t_max_ps = P->t_max * 1e12;
   for (int m = 0; m < P->n_times; ++m) S.t_meas_ps.push_back(P->t_meas[m] * 1e12);
+  if (P->transient) {
+    if (P->n_regions == 0) {
+      Setup::Region r;
+      for (int a = 0; a < 3; ++a) { r.lo[a] = 0.0; r.hi[a] = g.L[a]; r.n[a] = P->grid[a]; }
+      r.off = 0;
+      r.whole = true;
+      S.regs.push_back(r);
+      S.n_det = (size_t)P->grid[0] * P->grid[1] * P->grid[2];
+    } else {
+      size_t off = 0;
+      for (int k = 0; k < P->n_regions; ++k) {
+        Setup::Region r;
+        for (int a = 0; a < 3; ++a) {
+          r.lo[a] = P->regions[6 * k + 2 * a] * 1e9;
+          r.hi[a] = P->regions[6 * k + 2 * a + 1] * 1e9;
+          r.n[a] = P->region_grid[3 * k + a];
+          if (!(r.hi[a] > r.lo[a]) || r.n[a] < 1) return 6;
+        }
+        r.off = off;
+        r.whole = false;
+        off += (size_t)r.n[0] * r.n[1] * r.n[2];
+        S.regs.push_back(r);
+      }
+      S.n_det = off;
+    }
+  }
   if (P->want_grad) {
     if (P->n_dirs > 64) return 4;
     for (int k = 0; k < P->n_dirs; ++k) {
@@ -590,8 +629,6 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
   const int ta = P->tally_axis;
   const bool cells = P->n_cells > 0 && !P->transient;
   const double h_cell = cells ? g.L[P->cell_axis] / (double)P->n_cells : 0.0;
-  const int nx = P->grid[0], ny = P->grid[1], nzg = P->grid[2];
-  const int ncell_t = nx * ny * nzg;
   std::vector<Period> periods;
   for (uint64_t pid = p0; pid < p1; ++pid) {
     uint32_t ctr[4] = {(uint32_t)pid, P->batch_index, 0u, 0u};
@@ -726,17 +763,24 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
           double dist = v * (S.t_meas_ps[mi] - t_now);
           double pm[3];
           for (int a = 0; a < 3; ++a) pm[a] = x[a] + dist * u[a];
-          int ix = (int)std::floor(pm[0] / (g.L[0] / (double)nx));
-          int iy = (int)std::floor(pm[1] / (g.L[1] / (double)ny));
-          int iz = (int)std::floor(pm[2] / (g.L[2] / (double)nzg));
-          ix = std::min(std::max(ix, 0), nx - 1);
-          iy = std::min(std::max(iy, 0), ny - 1);
-          iz = std::min(std::max(iz, 0), nzg - 1);
-          size_t c = ((size_t)mi * ncell_t + ((size_t)iz * ny + iy) * nx + ix) * 4;
-          out.snap[c + 0] += s;
-          out.snap[c + 1] += (s * v) * u[0];
-          out.snap[c + 2] += (s * v) * u[1];
-          out.snap[c + 3] += (s * v) * u[2];
+          // every detector region containing the position (closed cuboids)
+          for (const Setup::Region& r : S.regs) {
+            if (!r.whole) {
+              bool in = true;
+              for (int a = 0; a < 3; ++a) in = in && pm[a] >= r.lo[a] && pm[a] <= r.hi[a];
+              if (!in) continue;
+            }
+            int i3[3];
+            for (int a = 0; a < 3; ++a) {
+              int ia = (int)std::floor((pm[a] - r.lo[a]) / ((r.hi[a] - r.lo[a]) / (double)r.n[a]));
+              i3[a] = std::min(std::max(ia, 0), r.n[a] - 1);
+            }
+            size_t c = ((size_t)mi * S.n_det + r.off + ((size_t)i3[2] * r.n[1] + i3[1]) * r.n[0] + i3[0]) * 4;
+            out.snap[c + 0] += s;
+            out.snap[c + 1] += (s * v) * u[0];
+            out.snap[c + 2] += (s * v) * u[1];
+            out.snap[c + 3] += (s * v) * u[2];
+          }
           ++mi;
         }
         t_now = t_end;
@@ -1018,7 +1062,7 @@ int or_run(const or_params* P, or_out* O) {
   int nt = P->n_threads > 0 ? P->n_threads : (int)std::thread::hardware_concurrency();
   if (nt < 1) nt = 1;
   if ((uint64_t)nt > total) nt = (int)std::max<uint64_t>(1, total);
-  const size_t ncell_t = (size_t)P->grid[0] * P->grid[1] * P->grid[2];
+  const size_t ncell_t = S.n_det;
   std::vector<Partial> parts(nt);
   for (auto& p : parts) {
     if (!P->transient && P->n_cells > 0) { p.T.assign(P->n_cells, 0.0); p.Q.assign((size_t)P->n_cells * 3, 0.0); }

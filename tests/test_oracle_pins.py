@@ -281,6 +281,45 @@ def test_kinetic_limit_bvk():
     assert abs(r["kappa"] - k) < 3.5 * r["kappa_se"]
 
 
+# ------------------------------------------------------------------ detector regions (Sec. 4.5)
+def _region_run(regions, n=20_000, n_times=12):
+    wl = W.transient_box_c3(n=n, grid=(8, 8, 4), n_times=n_times)
+    run = wl.run
+    run.regions = regions
+    return wl.material, wl.geometries[0], run
+
+
+def test_refined_region_sums_to_the_coarse_region():
+    # a region split into 2^(3n) detectors (n = 2) next to the same region
+    # unsplit: per time, the refined counts add up to the coarse count exactly
+    box = (0.5e-6, 1.5e-6, 0.4e-6, 1.7e-6, 0.3e-6, 1.0e-6)
+    m, g, run = _region_run([(box, (1, 1, 1)), (box, (4, 4, 4))])
+    r = oracle.run_transient(m, g, run)
+    raw = r["raw"]                     # [time][detector][4]
+    coarse = raw[:, 0, :]
+    fine = raw[:, 1:, :].sum(axis=1)
+    assert np.array_equal(coarse[:, 0], fine[:, 0])
+    np.testing.assert_allclose(fine[:, 1:], coarse[:, 1:], rtol=1e-12, atol=1e-9)
+    assert coarse[:, 0].max() > 1000
+    # volume-averaged temperature: the coarse value is the mean of the 64 fine ones
+    np.testing.assert_allclose(r["tally"][:, 1:, 0].mean(axis=1), r["tally"][:, 0, 0], rtol=1e-12)
+
+
+def test_regions_tiling_the_box_count_every_particle():
+    L = (2e-6, 2e-6, 1e-6)
+    halves = [((0.0, 1e-6, 0.0, L[1], 0.0, L[2]), (2, 3, 2)), ((1e-6, L[0], 0.0, L[1], 0.0, L[2]), (5, 1, 2))]
+    m, g, run = _region_run(halves)
+    r = oracle.run_transient(m, g, run)
+    per_time = r["raw"][:, :, 0].sum(axis=1)
+    assert np.all(per_time == run.n)    # every particle sits in the closed box, all signs +
+    # the whole-box grid of the same run sees the same snapshots
+    run.regions = ()
+    whole = oracle.run_transient(m, g, run)
+    assert np.all(whole["raw"][..., 0].sum(axis=(1, 2, 3)) == run.n)
+    np.testing.assert_allclose(r["raw"][:, :, 1:].sum(axis=1), whole["raw"][..., 1:].sum(axis=(1, 2, 3)),
+                               rtol=1e-9, atol=1e-6)
+
+
 # ------------------------------------------------------------------ two-phonon clock (Sec. 3.3)
 def _with_imp(m, tau_imp):
     from dataclasses import replace
