@@ -763,11 +763,14 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
           double dist = v * (S.t_meas_ps[mi] - t_now);
           double pm[3];
           for (int a = 0; a < 3; ++a) pm[a] = x[a] + dist * u[a];
-          // every detector region containing the position (closed cuboids)
+          // every detector region containing the position: half-open cuboids
+          // [lo, hi), closed on the box's upper faces, so that regions tiling
+          // the box partition it
           for (const Setup::Region& r : S.regs) {
             if (!r.whole) {
               bool in = true;
-              for (int a = 0; a < 3; ++a) in = in && pm[a] >= r.lo[a] && pm[a] <= r.hi[a];
+              for (int a = 0; a < 3; ++a)
+                in = in && pm[a] >= r.lo[a] && (pm[a] < r.hi[a] || (pm[a] == r.hi[a] && pm[a] >= g.L[a]));
               if (!in) continue;
             }
             int i3[3];
