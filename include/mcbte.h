@@ -278,10 +278,21 @@ typedef struct {
   int window_times;            /* FP32 path: measurement times per time window; 0 picks the
                                   largest window whose tally slice fits a third of the L2;
                                   >= n_times traces in one pass (no state buffer)           */
+  int n_regions;               /* detector regions (Sec. 4.5, Measure_region), 0..MCBTE_MAX_REGIONS;
+                                  0: the whole box split by grid                            */
+  const double* regions;       /* HOST [n_regions][6] xmin, xmax, ymin, ymax, zmin, zmax (m)  */
+  const int* region_grid;      /* HOST [n_regions][3] detectors per axis (2^n for the paper's
+                                  2^(3n) refinement); every region that contains a particle
+                                  tallies it; regions are half-open [min, max), closed on the
+                                  box's upper faces, so regions tiling the box partition it */
 } mcbte_transient_params;
 
+#define MCBTE_MAX_REGIONS 16
+
 typedef struct {
-  double* tally;        /* [n_times][nz][ny][nx][4]: T - T_eq (K), q_x, q_y, q_z (W/m^2), Eq. sampling */
+  double* tally;        /* [n_times][n_detectors][4]: T - T_eq (K), q_x, q_y, q_z (W/m^2),
+                           Eq. sampling; detectors region by region, x fastest (without
+                           regions: [n_times][nz][ny][nx][4])                            */
   double* stats;        /* [MCBTE_NSTATS]                                                */
   uint32_t* events_pp;  /* [n_particles] or NULL                                         */
   int on_host;

@@ -274,14 +274,23 @@ class TransientConfig:
     time_budget_s: float = 0.0
     trace_events: Optional[tuple] = None
     window_times: int = 0                    # measurement times per time window (0: sized to the L2)
+    regions: Sequence = ()                   # ((xmin, xmax, ymin, ymax, zmin, zmax) m, (nx, ny, nz)) per region
 
 
 class TransientOutputs:
-    def __init__(self, n_times: int, grid, n_particles: int, per_particle: bool = False, device=None):
+    """Device outputs of a transient run: tally [n_times][nz][ny][nx][4] for the
+    whole-box grid, or [n_times][n_detectors][4] when `regions` are given."""
+
+    def __init__(self, n_times: int, grid, n_particles: int, per_particle: bool = False, device=None,
+                 regions: Sequence = ()):
         import torch
         dev = device or torch.device("cuda")
         nx, ny, nz = (int(g) for g in grid)
-        self.tally = torch.zeros(n_times, nz, ny, nx, 4, dtype=torch.float64, device=dev)
+        if regions:
+            nd = sum(int(np.prod(r[1])) for r in regions)
+            self.tally = torch.zeros(n_times, nd, 4, dtype=torch.float64, device=dev)
+        else:
+            self.tally = torch.zeros(n_times, nz, ny, nx, 4, dtype=torch.float64, device=dev)
         self.stats = torch.zeros(L.NSTATS, dtype=torch.float64, device=dev)
         self.events_pp = torch.zeros(n_particles, dtype=torch.int32, device=dev) if per_particle else None
 
@@ -307,6 +316,12 @@ def transient_params(cfg: TransientConfig, n_particles: int, t_meas: np.ndarray)
     p.time_budget_s = float(cfg.time_budget_s)
     p.trace_event_start, p.trace_event_stop = _event_handles(cfg.trace_events)
     p.window_times = int(cfg.window_times)
+    regions = list(cfg.regions or ())
+    if regions:
+        boxes = np.ascontiguousarray([r[0] for r in regions], dtype=np.float64)
+        grids = np.ascontiguousarray([r[1] for r in regions], dtype=np.int32)
+        p._keep = (boxes, grids)            # host arrays read during the call
+        p.n_regions, p.regions, p.region_grid = len(regions), boxes.ctypes.data, grids.ctypes.data
     return p
 
 
@@ -315,7 +330,7 @@ def run_transient(material: Material, geom: Geometry, n_particles: int, cfg: Tra
                   stream=None) -> TransientOutputs:
     tm = _f64(cfg.t_meas)
     if out is None:
-        out = TransientOutputs(tm.shape[0], cfg.grid, n_particles, per_particle)
+        out = TransientOutputs(tm.shape[0], cfg.grid, n_particles, per_particle, regions=cfg.regions)
     p = transient_params(cfg, n_particles, tm)
     o = out.struct()
     ws_ptr, ws_bytes = (None, 0) if workspace is None else (workspace.data_ptr(), workspace.numel() * workspace.element_size())

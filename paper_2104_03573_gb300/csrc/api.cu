@@ -643,6 +643,7 @@ struct TransientWs {
   double* stats;
   uint32_t* events_pp;
   uint4* tstate;    // FP32 time windows: particle state between windows
+  DetRegion* regs;  // detector regions
   size_t bytes;
 };
 
@@ -650,6 +651,14 @@ struct TransientWs {
 // choice: the largest window whose [times][cells][4] x 8-byte slice of the
 // snapshot tally fits a third of the L2, so the snapshot atomics of a window
 // hit in L2 instead of read-modify-writing HBM.
+uint64_t transient_detectors(const mcbte_transient_params* p) {
+  if (p->n_regions == 0) return (uint64_t)p->grid[0] * p->grid[1] * p->grid[2];
+  uint64_t nd = 0;
+  for (int k = 0; k < p->n_regions; ++k)
+    nd += (uint64_t)p->region_grid[3 * k] * p->region_grid[3 * k + 1] * p->region_grid[3 * k + 2];
+  return nd;
+}
+
 int transient_window_times(const mcbte_transient_params* p) {
   if (p->precision != MCBTE_FP32_TRACE) return p->n_times;
   int wt = p->window_times;
@@ -658,7 +667,7 @@ int transient_window_times(const mcbte_transient_params* p) {
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess ||
         l2 <= 0)
       l2 = 96 << 20;
-    const size_t slice = (size_t)p->grid[0] * p->grid[1] * p->grid[2] * 4 * sizeof(long long);
+    const size_t slice = (size_t)transient_detectors(p) * 4 * sizeof(long long);
     const size_t fit = ((size_t)l2 / 3) / slice;
     wt = fit < 1 ? 1 : (fit > (size_t)p->n_times ? p->n_times : (int)fit);
   }
@@ -683,6 +692,7 @@ TransientWs layout_transient(char* base, size_t snap_len, int n_times, bool host
   w.zero_end = base ? base + c.off : nullptr;
   w.t_meas_ps = c.take<double>(n_times);
   w.tstate = windows ? c.take<uint4>(3 * total) : nullptr;
+  w.regs = c.take<DetRegion>(MCBTE_MAX_REGIONS);
   if (host_out) {
     w.snap = c.take<double>(snap_len);
     w.stats = c.take<double>(MCBTE_NSTATS);
@@ -707,6 +717,24 @@ mcbte_status check_transient(const mcbte_material* m, const mcbte_geometry* g, c
   }
   for (int a = 0; a < 3; ++a)
     if (p->grid[a] < 1 || p->grid[a] > 4096) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: grid in [1, 4096]");
+  if (p->n_regions < 0 || p->n_regions > MCBTE_MAX_REGIONS)
+    return fail(MCBTE_ERR_INVALID_ARG, "run_transient: n_regions in [0, MCBTE_MAX_REGIONS]");
+  if (p->n_regions > 0 && (!p->regions || !p->region_grid))
+    return fail(MCBTE_ERR_INVALID_ARG, "run_transient: regions and region_grid required");
+  uint64_t nd = 0;
+  for (int k = 0; k < p->n_regions; ++k) {
+    uint64_t cnt = 1;
+    for (int a = 0; a < 3; ++a) {
+      const double lo = p->regions[6 * k + 2 * a], hi = p->regions[6 * k + 2 * a + 1];
+      const int n = p->region_grid[3 * k + a];
+      if (!(std::isfinite(lo) && std::isfinite(hi) && hi > lo))
+        return fail(MCBTE_ERR_INVALID_ARG, "run_transient: region bounds must satisfy min < max");
+      if (n < 1 || n > 4096) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: region_grid in [1, 4096]");
+      cnt *= (uint64_t)n;
+    }
+    nd += cnt;
+  }
+  if (nd > (1ull << 28)) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: too many detectors");
   if (p->threads_per_block != 0 && p->threads_per_block != 256 && p->threads_per_block != 512 &&
       p->threads_per_block != 768 && p->threads_per_block != 1024)
     return fail(MCBTE_ERR_INVALID_ARG, "run_transient: threads_per_block must be 0, 256, 512, 768 or 1024");
@@ -739,7 +767,7 @@ mcbte_status mcbte_run_transient(const mcbte_material* m, const mcbte_geometry* 
   if (st != MCBTE_OK) return st;
   if (!out || !out->tally || !out->stats) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: tally and stats required");
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t ncell = (size_t)p->grid[0] * p->grid[1] * p->grid[2];
+  const size_t ncell = (size_t)transient_detectors(p);
   const size_t snap_len = (size_t)p->n_times * ncell * 4;
   const bool host_out = out->on_host != 0;
   const int wt = transient_window_times(p);
@@ -791,6 +819,35 @@ mcbte_status mcbte_run_transient(const mcbte_material* m, const mcbte_geometry* 
   C.n_times = p->n_times;
   C.t_meas_ps = w.t_meas_ps;
   for (int k = 0; k < 3; ++k) C.grid[k] = p->grid[k];
+  // detector regions, derived on the host with the CPU reference's arithmetic
+  C.n_regs = p->n_regions;
+  C.n_det = (uint32_t)ncell;
+  C.regs = w.regs;
+  if (p->n_regions > 0) {
+    std::vector<DetRegion> rg(p->n_regions);
+    uint32_t off = 0;
+    for (int k = 0; k < p->n_regions; ++k) {
+      DetRegion& r = rg[k];
+      double vol = 1.0;
+      int cnt = 1;
+      for (int a = 0; a < 3; ++a) {
+        const double lo_m = p->regions[6 * k + 2 * a], hi_m = p->regions[6 * k + 2 * a + 1];
+        r.n[a] = p->region_grid[3 * k + a];
+        r.lo[a] = lo_m * 1e9;
+        r.hi[a] = hi_m * 1e9;
+        r.h[a] = (r.hi[a] - r.lo[a]) / (double)r.n[a];
+        r.lof[a] = (float)r.lo[a];
+        r.hif[a] = (float)r.hi[a];
+        r.cinvf[a] = (float)((double)r.n[a] / (r.hi[a] - r.lo[a]));
+        vol = vol * (hi_m - lo_m);
+        cnt *= r.n[a];
+      }
+      r.v_det = vol / (double)cnt;
+      r.off = off;
+      off += (uint32_t)cnt;
+    }
+    RUN_TRY(cudaMemcpyAsync(w.regs, rg.data(), rg.size() * sizeof(DetRegion), cudaMemcpyHostToDevice, s));
+  }
   Acc A{};
   A.dsc = w.dsc;
   A.cnt = w.cnt;

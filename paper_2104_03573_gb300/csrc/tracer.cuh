@@ -47,9 +47,23 @@ struct RunCfg {
   int grid[3];
   int cell_flux_axis;   // FP32 cell tallies: T and the tally-axis flux only
   int ext;              // extended physics in use (two-phonon clock, walls, per-bin d, general gradient)
+  // transient detector regions (none: the whole box split by grid)
+  const struct DetRegion* regs;
+  int n_regs;
+  uint32_t n_det;
   // FP32 transient time windows: this launch takes the snapshots with index
   // < win_end; the first window emits, later ones resume saved particles
   int win_first, win_last, win_end;
+};
+
+// Transient detector region (Sec. 4.5): a closed axis-aligned cuboid split
+// into n[0] x n[1] x n[2] detectors numbered from `off`, x fastest.
+struct DetRegion {
+  double lo[3], hi[3], h[3];   // nm; h = (hi - lo) / n
+  float lof[3], hif[3], cinvf[3];
+  int n[3];
+  uint32_t off;
+  double v_det;                // m^3 per detector
 };
 
 // Raw accumulators of a run (device).
@@ -712,6 +726,25 @@ __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, cons
 // t_max (Sec. 3.5.6); every measurement time t_m inside the flight's
 // interval [t, t_end) (closed at t_max) adds the particle's snapshot to its
 // detector cell (Eq. sampling, Sec. 3.4).
+// One snapshot into tally entry c: FP64 atomics, or (FP32 path) the exact
+// signed count and the flux in 2^-20 nm/ps fixed point.
+template <typename R>
+__device__ __forceinline__ void snap_add(double* snap, size_t c, R s, R sv, const R u[3], R v) {
+  if constexpr (sizeof(R) == 8) {
+    atomicAdd(&snap[c + 0], (double)s);
+    atomicAdd(&snap[c + 1], (double)(sv * u[0]));
+    atomicAdd(&snap[c + 2], (double)(sv * u[1]));
+    atomicAdd(&snap[c + 3], (double)(sv * u[2]));
+  } else {
+    long long* q = reinterpret_cast<long long*>(snap) + c;
+    red_s64(q + 0, s > R(0) ? 1ll : -1ll);
+    red_s64(q + 1, fx((float)(sv * u[0])));
+    red_s64(q + 2, fx((float)(sv * u[1])));
+    red_s64(q + 3, fx((float)(sv * u[2])));
+  }
+  (void)v;
+}
+
 // `tmeas`: the measurement times in ps (FP64 path: the global array; FP32
 // path: a float copy in shared memory).  `cinv`: cells per nm along x, y, z
 // (FP32 path only; the FP64 path divides by the cell size, the CPU reference form).
@@ -758,8 +791,32 @@ __device__ __forceinline__ int step_transient(Particle<R>& p, const GeoRun& g, c
     ix = min(max(ix, 0), nx - 1);
     iy = min(max(iy, 0), ny - 1);
     iz = min(max(iz, 0), nz - 1);
-    const size_t c = ((size_t)p.mi * ncell + ((size_t)iz * ny + iy) * nx + ix) * 4;
     const R sv = p.s * v;
+    if (C.n_regs > 0) {
+      // detector regions: every half-open cuboid [lo, hi) containing the
+      // position (closed on the box's upper faces)
+      for (int k = 0; k < C.n_regs; ++k) {
+        const DetRegion& r = C.regs[k];
+        int i3[3];
+        bool in = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const R lo = sizeof(R) == 8 ? (R)r.lo[a] : (R)r.lof[a];
+          const R hi = sizeof(R) == 8 ? (R)r.hi[a] : (R)r.hif[a];
+          in = in && pm[a] >= lo && (pm[a] < hi || (pm[a] == hi && pm[a] >= geo_L<R>(g, a)));
+          int ia;
+          if constexpr (sizeof(R) == 8) ia = (int)floor((pm[a] - lo) / (R)r.h[a]);
+          else ia = (int)floorf((pm[a] - lo) * r.cinvf[a]);
+          i3[a] = min(max(ia, 0), r.n[a] - 1);
+        }
+        if (!in) continue;
+        const size_t c = ((size_t)p.mi * C.n_det + r.off + ((size_t)i3[2] * r.n[1] + i3[1]) * r.n[0] + i3[0]) * 4;
+        snap_add<R>(snap, c, p.s, sv, p.u, v);
+      }
+      ++p.mi;
+      continue;
+    }
+    const size_t c = ((size_t)p.mi * ncell + ((size_t)iz * ny + iy) * nx + ix) * 4;
     if (sizeof(R) == 8) {
       atomicAdd(&snap[c + 0], (double)p.s);
       atomicAdd(&snap[c + 1], (double)(sv * p.u[0]));

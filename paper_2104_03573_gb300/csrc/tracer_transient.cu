@@ -218,10 +218,17 @@ __global__ void k_finalize_transient(const GeoRun* geos, MatView M, RunCfg C, Ac
   const GeoRun& G = geos[0];
   const double E_eff = G.E_tot / (double)G.n;
   const double Vc = G.V_box / (double)((size_t)C.grid[0] * C.grid[1] * C.grid[2]);
-  const double kT = E_eff / (M.sums[0] * Vc);
-  const double kq = E_eff / Vc;
   const size_t total = (size_t)C.n_times * n_cells_total;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    // volume of this entry's detector (its region's split, or the grid cell)
+    double vd = Vc;
+    if (C.n_regs > 0) {
+      const uint32_t det = (uint32_t)(i % n_cells_total);
+      for (int k = 0; k < C.n_regs; ++k)
+        if (det >= C.regs[k].off) vd = C.regs[k].v_det;
+    }
+    const double kT = E_eff / (M.sums[0] * vd);
+    const double kq = E_eff / vd;
     const double* r = A.snap + i * 4;
     double* o = tally + i * 4;
     double a0, a1, a2, a3;

@@ -205,6 +205,29 @@ def test_fp64_and_fp32_diagonal_control_gradient():
     assert abs(s32[L.STAT_KAPPA] - k) < 3.5 * s32[L.STAT_KAPPA_SE]
 
 
+def test_detector_regions_fp64_parity_and_fp32_identities():
+    # Sec. 4.5 regions: a coarse region, the same region split 4 x 4 x 4, and
+    # two halves tiling the box
+    box = (0.5e-6, 1.5e-6, 0.4e-6, 1.7e-6, 0.3e-6, 1.0e-6)
+    halves = [((0.0, 1e-6, 0.0, 2e-6, 0.0, 1e-6), (2, 3, 2)), ((1e-6, 2e-6, 0.0, 2e-6, 0.0, 1e-6), (5, 1, 2))]
+    wl = W.transient_box_c3(n=3000, grid=(8, 8, 4), n_times=12)
+    m, g, run = wl.material, wl.geometries[0], wl.run
+    run.regions = [(box, (1, 1, 1)), (box, (4, 4, 4))] + halves
+    gg = gpu_transient(m, g, run, L.FP64_PLAIN, per_particle=True)
+    ref = oracle.run_transient(m, g, run, per_particle=True)
+    assert np.array_equal(gg["events_pp"], ref["events_pp"])
+    ok, err = rel_close(gg["tally"], ref["tally"], RTOL)
+    assert ok, err
+    run.n = 400_000
+    f32 = gpu_transient(m, g, run, L.FP32_TRACE)
+    T = f32["tally"][..., 0]
+    q = ref["V_cell"]                                 # per-detector volumes
+    quanta = f32["stats"][L.STAT_E_TOT] / run.n / (oracle.tables(m)["C_tot"] * q)
+    cnt = np.rint(T / quanta[None, :])
+    assert np.array_equal(cnt[:, 0], cnt[:, 1:65].sum(axis=1))       # refined = coarse, exactly
+    assert np.all(cnt[:, 65:].sum(axis=1) == run.n)                  # tiling halves count everyone
+
+
 def test_fp64_film_batch_geometry_index_streams():
     wl = W.film_batch_c4(n_films=6)
     mat = wl.material
