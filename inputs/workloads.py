@@ -192,6 +192,8 @@ class TransientRun:
     # detector regions (Sec. 4.5): ((xmin, xmax, ymin, ymax, zmin, zmax) m, (nx, ny, nz));
     # empty: the whole box split by `grid`
     regions: Sequence = ()
+    # False: snapshots at each t_m (Eq. sampling); True: averages over [t_{m-1}, t_m)
+    time_average: bool = False
 
 
 @dataclass

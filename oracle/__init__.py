@@ -52,7 +52,7 @@ class _Params(C.Structure):
         ("n_scat_max", C.c_int), ("max_events", C.c_uint64),
         ("n_cells", C.c_int), ("cell_axis", C.c_int), ("tally_axis", C.c_int),
         ("t_max", C.c_double), ("n_times", C.c_int), ("t_meas", C.c_void_p), ("grid", C.c_int * 3),
-        ("n_regions", C.c_int), ("regions", C.c_void_p), ("region_grid", C.c_void_p),
+        ("n_regions", C.c_int), ("regions", C.c_void_p), ("region_grid", C.c_void_p), ("time_average", C.c_int),
         ("want_grad", C.c_int), ("n_dirs", C.c_int), ("dirs", C.c_void_p), ("n_threads", C.c_int),
     ]
 
@@ -368,6 +368,7 @@ def run_transient(material, geom, run, *, pid_begin: int = 0, pid_end: Optional[
                 t_max=float(run.t_max), n_times=int(t_meas.shape[0]), t_meas=t_meas.ctypes.data,
                 tally_axis=2, n_threads=int(n_threads))
     P.grid[:] = [nx, ny, nz]
+    P.time_average = int(bool(getattr(run, "time_average", False)))
     nt = t_meas.shape[0]
     regions = list(getattr(run, "regions", ()) or ())
     if regions:

@@ -260,6 +260,7 @@ typedef struct {
   int n_regions;
   const double* regions;      // [n_regions][6] xmin, xmax, ymin, ymax, zmin, zmax (m)
   const int* region_grid;     // [n_regions][3]
+  int time_average;           // 0: snapshots at t_m (Eq. sampling); 1: averages over [t_{m-1}, t_m)
   int want_grad;
   int n_dirs;
   const double* dirs;     // [n_dirs][n_bins]
@@ -408,6 +409,7 @@ struct Setup {
     int n[3];
     size_t off;            // first detector of the region
     bool whole;            // the whole box (every position inside, clamped to the grid)
+    bool hi_closed[3];     // the upper face lies on (or beyond) the box's upper face
   };
   std::vector<Region> regs;
   size_t n_det = 0;
@@ -504,7 +506,7 @@ int setup(const or_params* P, const Tables& t, Setup& S) {
   if (P->transient) {
     if (P->n_regions == 0) {
       Setup::Region r;
-      for (int a = 0; a < 3; ++a) { r.lo[a] = 0.0; r.hi[a] = g.L[a]; r.n[a] = P->grid[a]; }
+      for (int a = 0; a < 3; ++a) { r.lo[a] = 0.0; r.hi[a] = g.L[a]; r.n[a] = P->grid[a]; r.hi_closed[a] = true; }
       r.off = 0;
       r.whole = true;
       S.regs.push_back(r);
@@ -517,6 +519,7 @@ int setup(const or_params* P, const Tables& t, Setup& S) {
           r.lo[a] = P->regions[6 * k + 2 * a] * 1e9;
           r.hi[a] = P->regions[6 * k + 2 * a + 1] * 1e9;
           r.n[a] = P->region_grid[3 * k + a];
+          r.hi_closed[a] = r.hi[a] >= g.L[a];
           if (!(r.hi[a] > r.lo[a]) || r.n[a] < 1) return 6;
         }
         r.off = off;
@@ -612,6 +615,62 @@ inline void dir_about_vector(double u[3], const double gv[3], double sgn, double
   double sn, cs;
   series_sincos2pi(co32(wphi), &sn, &cs);
   for (int k = 0; k < 3; ++k) u[k] = (mu * n[k] + (s * cs) * b1[k]) + (s * sn) * b2[k];
+}
+
+// Time the straight path x(tau) = x0 + w (tau - t0) spends in each detector
+// of region r between times ta < tb (w in nm/ps): clip [ta, tb) to the
+// region's box, then walk the detector grid from cell to cell in time order
+// (cell-crossing times from the grid planes; ties advance every axis that
+// crosses).  add(detector index within the region, duration).
+template <class Add>
+void region_track(const Setup::Region& r, const double x0[3], const double w[3], double t0, double ta, double tb,
+                  Add add) {
+  double t_in = ta, t_out = tb;
+  for (int a = 0; a < 3; ++a) {
+    const double p = x0[a] + w[a] * (ta - t0);
+    if (w[a] == 0.0) {
+      if (!(p >= r.lo[a] && (p < r.hi[a] || (r.hi_closed[a] && p <= r.hi[a])))) return;
+      continue;
+    }
+    double c0 = t0 + (r.lo[a] - x0[a]) / w[a];
+    double c1 = t0 + (r.hi[a] - x0[a]) / w[a];
+    if (c0 > c1) std::swap(c0, c1);
+    t_in = std::max(t_in, c0);
+    t_out = std::min(t_out, c1);
+  }
+  if (!(t_in < t_out)) return;
+  int i3[3];
+  double h[3];
+  for (int a = 0; a < 3; ++a) {
+    h[a] = (r.hi[a] - r.lo[a]) / (double)r.n[a];
+    const double p = x0[a] + w[a] * (t_in - t0);
+    int ia = (int)std::floor((p - r.lo[a]) / h[a]);
+    if (w[a] < 0.0 && ia * h[a] + r.lo[a] == p) ia = ia - 1;   // on a plane, moving down: the cell below
+    i3[a] = std::min(std::max(ia, 0), r.n[a] - 1);
+  }
+  double tau = t_in;
+  const int max_steps = r.n[0] + r.n[1] + r.n[2] + 3;
+  for (int step = 0; step < max_steps && tau < t_out; ++step) {
+    double tn = t_out;
+    double tc[3];
+    for (int a = 0; a < 3; ++a) {
+      tc[a] = INFINITY;
+      if (w[a] > 0.0) tc[a] = t0 + ((r.lo[a] + (i3[a] + 1) * h[a]) - x0[a]) / w[a];
+      else if (w[a] < 0.0) tc[a] = t0 + ((r.lo[a] + i3[a] * h[a]) - x0[a]) / w[a];
+      if (tc[a] < tn) tn = tc[a];
+    }
+    if (tn < tau) tn = tau;
+    add(((size_t)i3[2] * r.n[1] + i3[1]) * r.n[0] + i3[0], tn - tau);
+    tau = tn;
+    if (!(tau < t_out)) break;
+    bool out_of = false;
+    for (int a = 0; a < 3; ++a)
+      if (tc[a] <= tn) {
+        i3[a] += w[a] > 0.0 ? 1 : -1;
+        if (i3[a] < 0 || i3[a] >= r.n[a]) out_of = true;
+      }
+    if (out_of) break;
+  }
 }
 
 struct Partial {
@@ -728,7 +787,8 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
     double PA = 0.0, PB = 0.0;
     size_t mi = 0;
     if (P->transient) {
-      while (mi < S.t_meas_ps.size() && S.t_meas_ps[mi] < t_now) ++mi;
+      if (P->time_average) { while (mi < S.t_meas_ps.size() && S.t_meas_ps[mi] <= t_now) ++mi; }
+      else { while (mi < S.t_meas_ps.size() && S.t_meas_ps[mi] < t_now) ++mi; }
     }
     for (;;) {
       if ((uint64_t)e + 1 >= P->max_events) { truncated = true; break; }
@@ -758,6 +818,32 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
         // the flight ended by t_max ends at t_max exactly (its length was
         // derived from t_max; dividing it by v again could land an ulp short)
         double t_end = final_seg ? S.t_max_ps : t_now + seg / v;
+        if (P->time_average) {
+          // time-bin averages: the flight's time in each detector during each
+          // bin [t_{m-1}, t_m) it overlaps, over the bin's length
+          const double w3[3] = {v * u[0], v * u[1], v * u[2]};
+          while (mi < S.t_meas_ps.size()) {
+            const double b0 = mi == 0 ? 0.0 : S.t_meas_ps[mi - 1];
+            const double b1 = S.t_meas_ps[mi];
+            if (!(b0 < t_end)) break;
+            const double ta = std::max(t_now, b0), tb = std::min(t_end, b1);
+            if (ta < tb) {
+              const double wb = 1.0 / (b1 - b0);
+              for (const Setup::Region& r : S.regs)
+                region_track(r, x, w3, t_now, ta, tb, [&](size_t det, double dur) {
+                  const size_t c = ((size_t)mi * S.n_det + r.off + det) * 4;
+                  const double f = (s * dur) * wb;
+                  out.snap[c + 0] += f;
+                  out.snap[c + 1] += (f * v) * u[0];
+                  out.snap[c + 2] += (f * v) * u[1];
+                  out.snap[c + 3] += (f * v) * u[2];
+                });
+            }
+            if (b1 <= t_end) ++mi;
+            else break;
+          }
+          t_now = t_end;
+        } else
         while (mi < S.t_meas_ps.size() &&
                (S.t_meas_ps[mi] < t_end || (final_seg && S.t_meas_ps[mi] <= t_end))) {
           double dist = v * (S.t_meas_ps[mi] - t_now);
