@@ -285,6 +285,9 @@ typedef struct {
                                   2^(3n) refinement); every region that contains a particle
                                   tallies it; regions are half-open [min, max), closed on the
                                   box's upper faces, so regions tiling the box partition it */
+  int time_average;            /* 0: snapshots at each t_meas (Eq. sampling); 1: averages of T
+                                  and q over [t_{m-1}, t_m) (t_0 = 0), from the time each flight
+                                  spends in each detector                                  */
 } mcbte_transient_params;
 
 #define MCBTE_MAX_REGIONS 16

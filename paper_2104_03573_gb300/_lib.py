@@ -60,7 +60,8 @@ class TransientParams(C.Structure):
                 ("t_meas", C.c_void_p), ("grid", C.c_int * 3), ("threads_per_block", C.c_int),
                 ("blocks_per_sm", C.c_int), ("time_budget_s", C.c_double),
                 ("trace_event_start", C.c_void_p), ("trace_event_stop", C.c_void_p), ("window_times", C.c_int),
-                ("n_regions", C.c_int), ("regions", C.c_void_p), ("region_grid", C.c_void_p)]
+                ("n_regions", C.c_int), ("regions", C.c_void_p), ("region_grid", C.c_void_p),
+                ("time_average", C.c_int)]
 
 
 class TransientOut(C.Structure):

@@ -275,6 +275,7 @@ class TransientConfig:
     trace_events: Optional[tuple] = None
     window_times: int = 0                    # measurement times per time window (0: sized to the L2)
     regions: Sequence = ()                   # ((xmin, xmax, ymin, ymax, zmin, zmax) m, (nx, ny, nz)) per region
+    time_average: bool = False               # averages over [t_{m-1}, t_m) instead of snapshots at t_m
 
 
 class TransientOutputs:
@@ -316,6 +317,7 @@ def transient_params(cfg: TransientConfig, n_particles: int, t_meas: np.ndarray)
     p.time_budget_s = float(cfg.time_budget_s)
     p.trace_event_start, p.trace_event_stop = _event_handles(cfg.trace_events)
     p.window_times = int(cfg.window_times)
+    p.time_average = int(bool(cfg.time_average))
     regions = list(cfg.regions or ())
     if regions:
         boxes = np.ascontiguousarray([r[0] for r in regions], dtype=np.float64)

@@ -819,20 +819,25 @@ mcbte_status mcbte_run_transient(const mcbte_material* m, const mcbte_geometry* 
   C.n_times = p->n_times;
   C.t_meas_ps = w.t_meas_ps;
   for (int k = 0; k < 3; ++k) C.grid[k] = p->grid[k];
-  // detector regions, derived on the host with the CPU reference's arithmetic
-  C.n_regs = p->n_regions;
+  // detector regions, derived on the host with the CPU reference's arithmetic;
+  // bin averages over the whole box walk the box grid as one region
+  C.time_average = p->time_average ? 1 : 0;
+  const bool whole_region = p->time_average && p->n_regions == 0;
+  C.n_regs = whole_region ? 1 : p->n_regions;
   C.n_det = (uint32_t)ncell;
   C.regs = w.regs;
-  if (p->n_regions > 0) {
-    std::vector<DetRegion> rg(p->n_regions);
+  if (C.n_regs > 0) {
+    std::vector<DetRegion> rg(C.n_regs);
     uint32_t off = 0;
-    for (int k = 0; k < p->n_regions; ++k) {
+    for (int k = 0; k < C.n_regs; ++k) {
       DetRegion& r = rg[k];
       double vol = 1.0;
       int cnt = 1;
       for (int a = 0; a < 3; ++a) {
-        const double lo_m = p->regions[6 * k + 2 * a], hi_m = p->regions[6 * k + 2 * a + 1];
-        r.n[a] = p->region_grid[3 * k + a];
+        const double lo_m = whole_region ? 0.0 : p->regions[6 * k + 2 * a];
+        const double hi_m = whole_region ? g->host.L[a] : p->regions[6 * k + 2 * a + 1];
+        r.n[a] = whole_region ? p->grid[a] : p->region_grid[3 * k + a];
+        r.hi_closed[a] = (hi_m * 1e9) >= (g->host.L[a] * 1e9);
         r.lo[a] = lo_m * 1e9;
         r.hi[a] = hi_m * 1e9;
         r.h[a] = (r.hi[a] - r.lo[a]) / (double)r.n[a];

@@ -51,6 +51,7 @@ struct RunCfg {
   const struct DetRegion* regs;
   int n_regs;
   uint32_t n_det;
+  int time_average;     // bin averages over [t_{m-1}, t_m) instead of snapshots
   // FP32 transient time windows: this launch takes the snapshots with index
   // < win_end; the first window emits, later ones resume saved particles
   int win_first, win_last, win_end;
@@ -64,7 +65,79 @@ struct DetRegion {
   int n[3];
   uint32_t off;
   double v_det;                // m^3 per detector
+  int hi_closed[3];            // upper face on (or beyond) the box's upper face
 };
+
+// Time the path x(tau) = x0 + w (tau - t0) (w in nm/ps) spends in each
+// detector of region r between ta < tb: the interval clipped to the region's
+// box, then a cell-by-cell walk of the grid in time order (crossing times
+// from the grid planes; ties advance every axis that crosses); at most
+// nx + ny + nz + 3 steps.  add(detector index within the region, duration).
+template <typename R, class Add>
+__device__ __forceinline__ void region_track(const DetRegion& r, const R x0[3], const R w[3], R t0, R ta, R tb,
+                                             Add add) {
+  R lo[3], hi[3], h[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = sizeof(R) == 8 ? (R)r.lo[a] : (R)r.lof[a];
+    hi[a] = sizeof(R) == 8 ? (R)r.hi[a] : (R)r.hif[a];
+    h[a] = sizeof(R) == 8 ? (R)r.h[a] : (hi[a] - lo[a]) / (R)r.n[a];
+  }
+  R t_in = ta, t_out = tb;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const R p = x0[a] + w[a] * (ta - t0);
+    if (w[a] == R(0)) {
+      if (!(p >= lo[a] && (p < hi[a] || (r.hi_closed[a] && p <= hi[a])))) return;
+      continue;
+    }
+    R c0 = t0 + (lo[a] - x0[a]) / w[a];
+    R c1 = t0 + (hi[a] - x0[a]) / w[a];
+    if (c0 > c1) {
+      const R tmp = c0;
+      c0 = c1;
+      c1 = tmp;
+    }
+    t_in = t_in > c0 ? t_in : c0;
+    t_out = t_out < c1 ? t_out : c1;
+  }
+  if (!(t_in < t_out)) return;
+  int i3[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const R p = x0[a] + w[a] * (t_in - t0);
+    int ia;
+    if constexpr (sizeof(R) == 8) ia = (int)floor((p - lo[a]) / h[a]);
+    else ia = (int)floorf((p - lo[a]) / h[a]);
+    if (w[a] < R(0) && (R)ia * h[a] + lo[a] == p) ia = ia - 1;
+    i3[a] = min(max(ia, 0), r.n[a] - 1);
+  }
+  R tau = t_in;
+  const int max_steps = r.n[0] + r.n[1] + r.n[2] + 3;
+  for (int step = 0; step < max_steps && tau < t_out; ++step) {
+    R tn = t_out;
+    R tc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      tc[a] = Num<R>::inf();
+      if (w[a] > R(0)) tc[a] = t0 + ((lo[a] + (R)(i3[a] + 1) * h[a]) - x0[a]) / w[a];
+      else if (w[a] < R(0)) tc[a] = t0 + ((lo[a] + (R)i3[a] * h[a]) - x0[a]) / w[a];
+      if (tc[a] < tn) tn = tc[a];
+    }
+    if (tn < tau) tn = tau;
+    add(((uint32_t)i3[2] * (uint32_t)r.n[1] + (uint32_t)i3[1]) * (uint32_t)r.n[0] + (uint32_t)i3[0], tn - tau);
+    tau = tn;
+    if (!(tau < t_out)) break;
+    bool out_of = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (tc[a] <= tn) {
+        i3[a] += w[a] > R(0) ? 1 : -1;
+        if (i3[a] < 0 || i3[a] >= r.n[a]) out_of = true;
+      }
+    if (out_of) break;
+  }
+}
 
 // Raw accumulators of a run (device).
 struct Acc {
@@ -771,6 +844,44 @@ __device__ __forceinline__ int step_transient(Particle<R>& p, const GeoRun& g, c
   const R t_end = fin ? tmax : ((sizeof(R) == 8) ? p.t + seg / v : p.t + seg * p.inv_v);
   const int nx = C.grid[0], ny = C.grid[1], nz = C.grid[2];
   const size_t ncell = (size_t)nx * ny * nz;
+  if (C.time_average) {
+    // bin averages over [t_{m-1}, t_m): the flight's time in each detector
+    // during each bin it overlaps, over the bin's length
+    const R w3[3] = {v * p.u[0], v * p.u[1], v * p.u[2]};
+    while (p.mi < C.n_times) {
+      const R b0 = p.mi == 0 ? R(0) : tmeas[p.mi - 1];
+      const R b1 = tmeas[p.mi];
+      if (!(b0 < t_end)) break;
+      const R ta = p.t > b0 ? p.t : b0;
+      const R tb = t_end < b1 ? t_end : b1;
+      if (ta < tb) {
+        const R wb = R(1) / (b1 - b0);
+        for (int k = 0; k < C.n_regs; ++k) {
+          const DetRegion& r = C.regs[k];
+          const size_t base = (size_t)p.mi * C.n_det + r.off;
+          region_track<R>(r, p.x, w3, p.t, ta, tb, [&](uint32_t det, R dur) {
+            const size_t c = (base + det) * 4;
+            const R f = (p.s * dur) * wb;
+            if constexpr (sizeof(R) == 8) {
+              atomicAdd(&snap[c + 0], (double)f);
+              atomicAdd(&snap[c + 1], (double)((f * v) * p.u[0]));
+              atomicAdd(&snap[c + 2], (double)((f * v) * p.u[1]));
+              atomicAdd(&snap[c + 3], (double)((f * v) * p.u[2]));
+            } else {
+              // FP32 path: every component in 2^-20 fixed point (the weights are fractions)
+              long long* q = reinterpret_cast<long long*>(snap) + c;
+              red_s64(q + 0, fx((float)f));
+              red_s64(q + 1, fx((float)((f * v) * p.u[0])));
+              red_s64(q + 2, fx((float)((f * v) * p.u[1])));
+              red_s64(q + 3, fx((float)((f * v) * p.u[2])));
+            }
+          });
+        }
+      }
+      if (b1 <= t_end) ++p.mi;
+      else break;
+    }
+  } else
   while (p.mi < C.n_times) {
     const R tm = tmeas[p.mi];
     if (!(tm < t_end || (fin && tm <= t_end))) break;

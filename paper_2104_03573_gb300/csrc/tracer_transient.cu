@@ -17,10 +17,16 @@ namespace mcbte {
 
 namespace {
 
+// First measurement index still ahead of the particle: for snapshots the
+// first t_m >= t0, for bin averages the bin [t_{m-1}, t_m) containing t0.
 template <typename R>
 __device__ __forceinline__ void transient_start(Particle<R>& p, const RunCfg& C) {
   p.mi = 0;
-  while (p.mi < C.n_times && (R)C.t_meas_ps[p.mi] < p.t) ++p.mi;
+  if (C.time_average) {
+    while (p.mi < C.n_times && (R)C.t_meas_ps[p.mi] <= p.t) ++p.mi;
+  } else {
+    while (p.mi < C.n_times && (R)C.t_meas_ps[p.mi] < p.t) ++p.mi;
+  }
 }
 
 template <typename R>
@@ -234,7 +240,7 @@ __global__ void k_finalize_transient(const GeoRun* geos, MatView M, RunCfg C, Ac
     double a0, a1, a2, a3;
     if (fixed) {
       const long long* q = reinterpret_cast<const long long*>(r);
-      a0 = (double)q[0];
+      a0 = C.time_average ? (double)q[0] * kFxInv : (double)q[0];
       a1 = (double)q[1] * kFxInv;
       a2 = (double)q[2] * kFxInv;
       a3 = (double)q[3] * kFxInv;

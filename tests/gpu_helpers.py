@@ -41,7 +41,8 @@ def gpu_transient(mat, geom, run, precision, seed=None, per_particle=False, **kw
     G = api.Geometry(geom)
     cfg = api.TransientConfig(seed=run.seed if seed is None else seed, t_max=run.t_max, t_meas=run.t_meas,
                               grid=run.grid, precision=precision, max_events=run.max_events,
-                              regions=getattr(run, "regions", ()), **kw)
+                              regions=getattr(run, "regions", ()),
+                              time_average=bool(getattr(run, "time_average", False)), **kw)
     out = api.run_transient(M, G, run.n, cfg, per_particle=per_particle)
     torch.cuda.synchronize()
     r = {"tally": out.tally.cpu().numpy(), "stats": out.stats.cpu().numpy()}

@@ -228,6 +228,30 @@ def test_detector_regions_fp64_parity_and_fp32_identities():
     assert np.all(cnt[:, 65:].sum(axis=1) == run.n)                  # tiling halves count everyone
 
 
+@pytest.mark.parametrize("with_regions", [False, True])
+def test_time_bin_averages_fp64_parity_and_fp32_conservation(with_regions):
+    wl = W.transient_box_c3(n=3000, grid=(8, 8, 4), n_times=12)
+    m, g, run = wl.material, wl.geometries[0], wl.run
+    run.time_average = True
+    if with_regions:
+        box = (0.5e-6, 1.5e-6, 0.4e-6, 1.7e-6, 0.3e-6, 1.0e-6)
+        run.regions = [(box, (4, 4, 4)), ((0.0, 2e-6, 0.0, 2e-6, 0.0, 1e-6), (3, 5, 2))]
+    gg = gpu_transient(m, g, run, L.FP64_PLAIN, per_particle=True)
+    ref = oracle.run_transient(m, g, run, per_particle=True)
+    assert np.array_equal(gg["events_pp"], ref["events_pp"])
+    ok, err = rel_close(gg["tally"], ref["tally"], RTOL)
+    assert ok, err
+    run.n = 400_000
+    f32 = gpu_transient(m, g, run, L.FP32_TRACE)
+    assert f32["stats"][L.STAT_STATUS] == 0
+    T = f32["tally"][..., 0].reshape(len(run.t_meas), -1)
+    vd = np.broadcast_to(np.asarray(ref["V_cell"], dtype=np.float64), T.shape[1:])
+    quanta = f32["stats"][L.STAT_E_TOT] / run.n / (oracle.tables(m)["C_tot"] * vd)
+    cnt = T / quanta[None, :]
+    whole = cnt if not with_regions else cnt[:, 64:]
+    np.testing.assert_allclose(whole.sum(axis=1), run.n, rtol=1e-6)   # every particle, every whole bin
+
+
 def test_fp64_film_batch_geometry_index_streams():
     wl = W.film_batch_c4(n_films=6)
     mat = wl.material

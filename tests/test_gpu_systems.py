@@ -239,11 +239,14 @@ def test_fp32_gradient_forward_equals_plain_run_and_is_reproducible():
     assert torch.equal(g1.dkappa_dlogtau, g2.dkappa_dlogtau)
 
 
-@pytest.mark.parametrize("case", ["gauss_box", "walls", "two_phonon"])
+@pytest.mark.parametrize("case", ["gauss_box", "walls", "two_phonon", "bin_average"])
 def test_fp32_transient_time_windows_change_nothing(case):
     # windows hold whole flights and park particles at events, so any window
     # size reproduces the one-pass trajectories and integer tallies exactly
-    if case in ("gauss_box", "two_phonon"):
+    if case == "bin_average":
+        wl = W.transient_box_c3(n=300_000, grid=(16, 16, 8), n_times=23)
+        wl.run.time_average = True
+    elif case in ("gauss_box", "two_phonon"):
         wl = W.transient_box_c3(n=300_000, grid=(16, 16, 8), n_times=23)
         if case == "two_phonon":       # the parked state carries the two-phonon clock
             from dataclasses import replace
@@ -257,7 +260,7 @@ def test_fp32_transient_time_windows_change_nothing(case):
     outs = []
     for wt in (nt, 5, 1, 0):
         cfg = api.TransientConfig(seed=r.seed, t_max=r.t_max, t_meas=r.t_meas, grid=r.grid, precision=L.FP32_TRACE,
-                                  window_times=wt)
+                                  window_times=wt, time_average=bool(getattr(r, "time_average", False)))
         o = api.run_transient(M, G, r.n, cfg, per_particle=True)
         torch.cuda.synchronize()
         assert o.stats[L.STAT_STATUS].item() == 0
