@@ -47,6 +47,7 @@ METRIC = "particle-events/s and s to 1% std-err kappa_eff, batched FP32 vs plain
 UNIT = "particle-events/s"
 WORKLOADS = {"si_slab": "si_slab_L1um_3000bins", "si_slab_imp": "si_slab_L1um_3000bins_two_phonon_clock",
              "transient_box": "transient_box_2x2x1um_gauss",
+             "transient_box_avg": "transient_box_2x2x1um_gauss_bin_averages",
              "nanomesh": "nanomesh_W34nm_pore11nm_t22nm_timp",
              "film_batch": "film_batch_64_10nm_10um", "pore_grad": "pore_film_W100nm_phi0.25_t200nm_grad"}
 # Algorithmic thread-instructions per event of the tracer (one Philox4x32-10
@@ -308,13 +309,14 @@ def _workload_setup(name, args, seed_offset):
                     timer=tm, kernel="k_steady_f32 (64 geometries, graph)",
                     shape={"threads_per_block": gb.cfg.threads_per_block, "refill_threshold": gb.cfg.refill_threshold},
                     kappa=True, kind="batch")
-    if name == "transient_box":
+    if name in ("transient_box", "transient_box_avg"):
         wl = W.transient_box_c3(n=args.n_particles or 100_000_000)
         mat, geo, run = wl.material, wl.geometries[0], wl.run
+        run.time_average = name == "transient_box_avg"
         M, G = api.Material(mat), api.Geometry(geo)
         cfg = api.TransientConfig(seed=run.seed + seed_offset, t_max=run.t_max, t_meas=run.t_meas, grid=run.grid,
                                   precision=L.FP32_TRACE, threads_per_block=args.threads if args.threads in (0, 256, 512, 768, 1024) else 0,
-                                  trace_events=ev, time_budget_s=300)
+                                  trace_events=ev, time_budget_s=300, time_average=run.time_average)
         out = api.TransientOutputs(len(run.t_meas), run.grid, run.n)
 
         def step():
@@ -342,7 +344,8 @@ def _workload_setup(name, args, seed_offset):
             return st[None, :]
         nt = len(run.t_meas) * run.grid[0] * run.grid[1] * run.grid[2] * 4 * 8
         desc = ("transient 2x2x1 um diffuse adiabatic box, +1 K Gaussian sigma 100 nm at the top-face centre, "
-                "64x64x32 cells x 200 snapshots (10 ps), FP32 flights, FP64 L2-atomic snapshot tallies")
+                "64x64x32 cells x 200 " + ("10 ps bin averages" if run.time_average else "snapshots (10 ps)")
+                + ", FP32 flights, fixed-point tallies in L2-sized time windows")
         return dict(mat=mat, geo=geo, run=run, n=run.n, step=step, fp64=fp64, e2e=e2e, d2h=nt + 8 * L.NSTATS,
                     h2d=_material_bytes(mat) + ctypes.sizeof(L.GeometryDesc) + 8 * len(run.t_meas), desc=desc,
                     launches=3, timer=tm, kernel="k_transient_f32", shape={"threads_per_block": cfg.threads_per_block},
@@ -480,7 +483,8 @@ def cpu_baseline(wk, args, target_s=None):
     kind = wk["kind"]
     if kind == "transient":
         def go(n):
-            r = W.TransientRun(n=n, seed=run.seed, t_max=run.t_max, t_meas=run.t_meas, grid=run.grid)
+            r = W.TransientRun(n=n, seed=run.seed, t_max=run.t_max, t_meas=run.t_meas, grid=run.grid,
+                               time_average=bool(getattr(run, "time_average", False)))
             return oracle.run_transient(mat, wk["geo"], r, n_threads=4)
         probe_n = 5_000
         cores = 4

@@ -179,6 +179,8 @@ class SteadyRun:
     per_bin: bool = False
     n_scat_max: int = 0
     max_events: int = 10 ** 9
+    # steady detector regions (Sec. 4.5): ((xmin, xmax, ymin, ymax, zmin, zmax) m, (nx, ny, nz))
+    regions: Sequence = ()
 
 
 @dataclass

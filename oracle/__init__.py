@@ -308,12 +308,26 @@ def run_steady(material, geom, run, *, pid_begin: int = 0, pid_end: Optional[int
     O.events_pp = _ptr(ev); O.X_pp = _ptr(Xp); O.G = _ptr(G)
     O.dir_sum = ds.ctypes.data if nd else None
     O.dir_sum2 = ds2.ctypes.data if nd else None
+    regions = list(getattr(run, "regions", ()) or ())
+    det = None
+    if regions:
+        boxes = keep.add(np.ascontiguousarray([rg[0] for rg in regions], dtype=np.float64))
+        grids = keep.add(np.ascontiguousarray([rg[1] for rg in regions], dtype=np.int32))
+        P.n_regions, P.regions, P.region_grid = len(regions), boxes.ctypes.data, grids.ctypes.data
+        det = np.zeros((int(sum(int(np.prod(rg[1])) for rg in regions)), 4))
+        O.snap = det.ctypes.data
     rc = lib().or_run(C.byref(P), C.byref(O))
     if rc:
         raise ValueError(f"oracle run failed ({rc})")
     sc = np.array(O.scal[:])
     r = {"raw_T": T[:nc], "raw_Q": Q[:nc], "raw_qbin": qb, "scal": sc, "events_pp": ev, "X_pp": Xp,
          "N": N, "n_traced": npp}
+    if regions:
+        v_det = np.concatenate([np.full(int(np.prod(rg[1])),
+                                        np.prod(np.asarray(rg[0])[1::2] - np.asarray(rg[0])[0::2]) / np.prod(rg[1]))
+                                for rg in regions])
+        r["det_raw"] = det
+        r["det_V"] = v_det
     E_tot, C_tot, V = sc[ETOT], sc[CTOT], sc[VSOLID]
     E_eff = E_tot / N
     Vbox = float(geom.L[0] * geom.L[1] * geom.L[2])
@@ -322,6 +336,9 @@ def run_steady(material, geom, run, *, pid_begin: int = 0, pid_end: Optional[int
         r["T"] = (E_eff / (C_tot * Vc)) * T[:nc] * 1e-12
         r["q"] = (E_eff / Vc) * Q[:nc] * 1e-9
     r["q_bin"] = (E_eff / V) * qb * 1e-9
+    if regions:
+        r["det_T"] = (E_eff / (C_tot * r["det_V"])) * det[:, 0] * 1e-12
+        r["det_q"] = (E_eff / r["det_V"])[:, None] * det[:, 1:] * 1e-9
     sx, sx2 = sc[SUMX], sc[SUMX2]
     mean = sx / npp if npp else 0.0
     var = (sx2 - npp * mean * mean) / (npp - 1) if npp > 1 else 0.0

@@ -503,7 +503,7 @@ int setup(const or_params* P, const Tables& t, Setup& S) {
   }
   S.t_max_ps = P->t_max * 1e12;
   for (int m = 0; m < P->n_times; ++m) S.t_meas_ps.push_back(P->t_meas[m] * 1e12);
-  if (P->transient) {
+  if (P->transient || P->n_regions > 0) {
     if (P->n_regions == 0) {
       Setup::Region r;
       for (int a = 0; a < 3; ++a) { r.lo[a] = 0.0; r.hi[a] = g.L[a]; r.n[a] = P->grid[a]; r.hi_closed[a] = true; }
@@ -906,6 +906,20 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
             }
           }
         }
+        if (P->n_regions > 0) {
+          // steady detector regions (Sec. 4.5): track length in each detector,
+          // s dt for T (ps) and s v dt u for q (nm), dt the time spent there
+          const double w3[3] = {v * u[0], v * u[1], v * u[2]};
+          const double dt = seg / v;
+          for (const Setup::Region& r : S.regs)
+            region_track(r, x, w3, 0.0, 0.0, dt, [&](size_t det, double dur) {
+              const size_t c = (r.off + det) * 4;
+              out.snap[c + 0] += s * dur;
+              out.snap[c + 1] += ((s * v) * dur) * u[0];
+              out.snap[c + 2] += ((s * v) * dur) * u[1];
+              out.snap[c + 3] += ((s * v) * dur) * u[2];
+            });
+        }
         if (P->want_grad) {
           double score = seg / t.lam_nm[bin];
           if (relax) score = score - 1.0;
@@ -1157,6 +1171,7 @@ int or_run(const or_params* P, or_out* O) {
     if (!P->transient && P->n_cells > 0) { p.T.assign(P->n_cells, 0.0); p.Q.assign((size_t)P->n_cells * 3, 0.0); }
     if (O->qbin_sum) p.qbin.assign(P->n_bins, 0.0);
     if (P->transient) p.snap.assign((size_t)P->n_times * ncell_t * 4, 0.0);
+    else if (P->n_regions > 0) p.snap.assign(ncell_t * 4, 0.0);     // steady detector regions
     if (P->want_grad) { p.G.assign(P->n_bins, 0.0); p.dsum.assign(P->n_dirs, 0.0); p.dsum2.assign(P->n_dirs, 0.0); }
   }
   std::vector<std::thread> th;

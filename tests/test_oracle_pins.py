@@ -348,6 +348,23 @@ def test_time_bin_averages_conserve_and_match_dense_snapshots():
     np.testing.assert_allclose(rg[:, 1:, :].sum(axis=1), rg[:, 0, :], rtol=1e-9, atol=1e-9)
 
 
+def test_steady_regions_match_the_slab_cells():
+    # detector regions along the slab axis reproduce the 1-D cell tallies
+    # (the same track-length estimator, Eqs. temp_steady, flux_x_steady);
+    # a region split 2^(3n) ways sums to the unsplit region
+    wl = W.gray_slab_c1(n=20_000)
+    m, g, run = wl.material, wl.geometries[0], wl.run
+    L = g.L
+    slabs = ((0.0, L[0], 0.0, L[1], 0.0, L[2]), (1, 1, run.n_cells))
+    sub = ((0.1 * L[0], 0.7 * L[0], 0.0, L[1], 0.25 * L[2], 0.75 * L[2]), (1, 1, 1))
+    sub8 = (sub[0], (2, 2, 2))
+    r = oracle.run_steady(m, g, replace(run, regions=[slabs, sub, sub8]))
+    nc = run.n_cells
+    np.testing.assert_allclose(r["det_T"][:nc], r["T"], rtol=1e-9, atol=1e-12 * np.abs(r["T"]).max())
+    np.testing.assert_allclose(r["det_q"][:nc], r["q"], rtol=1e-9, atol=1e-9 * np.abs(r["q"]).max())
+    np.testing.assert_allclose(r["det_raw"][nc + 1:].sum(axis=0), r["det_raw"][nc], rtol=1e-12, atol=1e-9)
+
+
 # ------------------------------------------------------------------ two-phonon clock (Sec. 3.3)
 def _with_imp(m, tau_imp):
     from dataclasses import replace
