@@ -40,6 +40,9 @@ typedef struct CUstream_st* mcbte_stream; /* == cudaStream_t */
  * in shared memory (4 bytes each). */
 #define MCBTE_MAX_TIMES 16384
 
+/* Largest number of detector regions of a run (Sec. 4.5). */
+#define MCBTE_MAX_REGIONS 16
+
 typedef enum {
   MCBTE_OK = 0,
   MCBTE_ERR_INVALID_ARG = 1,   /* a descriptor or parameter is out of range  */
@@ -210,6 +213,11 @@ typedef struct {
                                   1 = T and the flux along tally_axis only (the other two
                                   components are returned as 0; Eq. flux_x_steady needs
                                   only that one)                                          */
+  int n_regions;               /* steady detector regions (Sec. 4.5), 0..MCBTE_MAX_REGIONS,
+                                  one geometry only; results in mcbte_steady_out.det       */
+  const double* regions;       /* HOST [n_regions][6] xmin, xmax, ymin, ymax, zmin, zmax (m)  */
+  const int* region_grid;      /* HOST [n_regions][3] detectors per axis (half-open cuboids
+                                  [min, max), closed on the box's upper faces)              */
 } mcbte_steady_params;
 
 typedef struct {
@@ -220,6 +228,9 @@ typedef struct {
   uint32_t* events_pp;  /* [sum n_particles] per-particle event counts, or NULL          */
   double* X_pp;         /* [sum n_particles] per-particle X_p (nm), or NULL              */
   int on_host;          /* 0: device pointers, 1: host pointers                          */
+  double* det;          /* [n_detectors][4] T - T_eq (K), q_x, q_y, q_z (W/m^2) per detector of
+                           the regions (track length in each, Eqs. temp_steady, flux_x_steady),
+                           detectors region by region, x fastest; or NULL                */
 } mcbte_steady_out;
 
 /* Device scratch a run needs.  Pass a buffer at least this large (256-byte
@@ -290,7 +301,6 @@ typedef struct {
                                   spends in each detector                                  */
 } mcbte_transient_params;
 
-#define MCBTE_MAX_REGIONS 16
 
 typedef struct {
   double* tally;        /* [n_times][n_detectors][4]: T - T_eq (K), q_x, q_y, q_z (W/m^2),

@@ -137,6 +137,7 @@ class SteadyConfig:
     seed_device: Optional[object] = None     # int64 device tensor holding the Philox key
     refill_threshold: int = 0
     cell_flux_axis: bool = False             # FP32 cell tallies: T and the tally-axis flux only
+    regions: Sequence = ()                   # detector regions ((xmin..zmax) m, (nx, ny, nz)), one geometry
 
 
 def _event_handles(pair):
@@ -166,6 +167,12 @@ def steady_params(cfg: SteadyConfig, n_particles: np.ndarray) -> "L.SteadyParams
     p.seed_device = None if cfg.seed_device is None else cfg.seed_device.data_ptr()
     p.refill_threshold = int(cfg.refill_threshold)
     p.cell_flux_axis = int(bool(cfg.cell_flux_axis))
+    regions = list(cfg.regions or ())
+    if regions:
+        boxes = np.ascontiguousarray([r[0] for r in regions], dtype=np.float64)
+        grids = np.ascontiguousarray([r[1] for r in regions], dtype=np.int32)
+        p._keep = (boxes, grids)            # host arrays read during the call
+        p.n_regions, p.regions, p.region_grid = len(regions), boxes.ctypes.data, grids.ctypes.data
     return p
 
 
@@ -173,10 +180,12 @@ class SteadyOutputs:
     """Caller-owned device outputs of a steady run (torch tensors)."""
 
     def __init__(self, n_geoms: int, n_bins: int, n_cells: int, per_bin: bool, total: int = 0,
-                 per_particle: bool = False, device=None):
+                 per_particle: bool = False, device=None, regions: Sequence = ()):
         import torch
         dev = device or torch.device("cuda")
         f = dict(dtype=torch.float64, device=dev)
+        nd = sum(int(np.prod(r[1])) for r in regions) if regions else 0
+        self.det = torch.zeros(nd, 4, **f) if nd else None   # T, q_x, q_y, q_z per detector
         self.T = torch.zeros(n_geoms, n_cells, **f) if n_cells > 0 else None
         self.q = torch.zeros(n_geoms, n_cells, 3, **f) if n_cells > 0 else None
         self.q_bin = torch.zeros(n_geoms, n_bins, **f) if per_bin else None
@@ -188,6 +197,7 @@ class SteadyOutputs:
         o = L.SteadyOut()
         o.T, o.q, o.q_bin, o.stats = _ptr(self.T), _ptr(self.q), _ptr(self.q_bin), _ptr(self.stats)
         o.events_pp, o.X_pp = _ptr(self.events_pp), _ptr(self.X_pp)
+        o.det = _ptr(self.det)
         o.on_host = 0
         return o
 
@@ -215,7 +225,8 @@ def run_steady(material: Material, geoms: Sequence[Geometry], n_particles, cfg: 
     """``mcbte_run_steady`` with device outputs (asynchronous on `stream`)."""
     n = np.ascontiguousarray(np.asarray(n_particles, dtype=np.uint64))
     if out is None:
-        out = SteadyOutputs(len(geoms), material.n_bins, cfg.n_cells, cfg.per_bin, int(n.sum()), per_particle)
+        out = SteadyOutputs(len(geoms), material.n_bins, cfg.n_cells, cfg.per_bin, int(n.sum()), per_particle,
+                            regions=cfg.regions)
     p = steady_params(cfg, n)
     o = out.struct()
     ws_ptr, ws_bytes = (None, 0) if workspace is None else (workspace.data_ptr(), workspace.numel() * workspace.element_size())

@@ -318,6 +318,64 @@ bool uses_ext(const mcbte_material* m, const mcbte_geometry_desc& d) {
   return m->view.imp || d.n_inner > 0 || uses_spec_bin(d) || nz > 1;
 }
 
+// Detector regions (Sec. 4.5): validation and the device records, derived
+// with the CPU reference's arithmetic.
+mcbte_status check_regions(int n, const double* regions, const int* grid, const char* who) {
+  if (n < 0 || n > MCBTE_MAX_REGIONS) return fail(MCBTE_ERR_INVALID_ARG, std::string(who) + ": n_regions in [0, 16]");
+  if (n > 0 && (!regions || !grid)) return fail(MCBTE_ERR_INVALID_ARG, std::string(who) + ": regions and region_grid required");
+  uint64_t nd = 0;
+  for (int k = 0; k < n; ++k) {
+    uint64_t cnt = 1;
+    for (int a = 0; a < 3; ++a) {
+      const double lo = regions[6 * k + 2 * a], hi = regions[6 * k + 2 * a + 1];
+      const int g = grid[3 * k + a];
+      if (!(std::isfinite(lo) && std::isfinite(hi) && hi > lo))
+        return fail(MCBTE_ERR_INVALID_ARG, std::string(who) + ": region bounds must satisfy min < max");
+      if (g < 1 || g > 4096) return fail(MCBTE_ERR_INVALID_ARG, std::string(who) + ": region_grid in [1, 4096]");
+      cnt *= (uint64_t)g;
+    }
+    nd += cnt;
+  }
+  if (nd > (1ull << 28)) return fail(MCBTE_ERR_INVALID_ARG, std::string(who) + ": too many detectors");
+  return MCBTE_OK;
+}
+
+uint64_t region_detectors(int n, const int* grid) {
+  uint64_t nd = 0;
+  for (int k = 0; k < n; ++k) nd += (uint64_t)grid[3 * k] * grid[3 * k + 1] * grid[3 * k + 2];
+  return nd;
+}
+
+// Records of n regions (whole: the box split by `grid` as one region).
+std::vector<DetRegion> build_regions(int n, const double* regions, const int* rgrid, bool whole, const int grid[3],
+                                     const double Lbox[3]) {
+  std::vector<DetRegion> rg(n);
+  uint32_t off = 0;
+  for (int k = 0; k < n; ++k) {
+    DetRegion& r = rg[k];
+    double vol = 1.0;
+    int cnt = 1;
+    for (int a = 0; a < 3; ++a) {
+      const double lo_m = whole ? 0.0 : regions[6 * k + 2 * a];
+      const double hi_m = whole ? Lbox[a] : regions[6 * k + 2 * a + 1];
+      r.n[a] = whole ? grid[a] : rgrid[3 * k + a];
+      r.hi_closed[a] = (hi_m * 1e9) >= (Lbox[a] * 1e9);
+      r.lo[a] = lo_m * 1e9;
+      r.hi[a] = hi_m * 1e9;
+      r.h[a] = (r.hi[a] - r.lo[a]) / (double)r.n[a];
+      r.lof[a] = (float)r.lo[a];
+      r.hif[a] = (float)r.hi[a];
+      r.cinvf[a] = (float)((double)r.n[a] / (r.hi[a] - r.lo[a]));
+      vol = vol * (hi_m - lo_m);
+      cnt *= r.n[a];
+    }
+    r.v_det = vol / (double)cnt;
+    r.off = off;
+    off += (uint32_t)cnt;
+  }
+  return rg;
+}
+
 bool has_gradient(const mcbte_geometry_desc& d) {
   return d.grad_T[0] != 0.0 || d.grad_T[1] != 0.0 || d.grad_T[2] != 0.0;
 }
@@ -349,11 +407,16 @@ struct SteadyWs {
   double* X_pp;
   double *dk, *dkp, *dkdir;
   double* xrep;   // FP32 gradient: final tally of every particle (forward -> replay)
+  DetRegion* regs;      // steady detector regions
+  double* det_raw;      // [n_det][4] FP64 path sums (zeroed)
+  long long* det_q;     // [n_det][4] FP32 path fixed-point sums (zeroed)
+  double* det;          // host staging of the outputs
   size_t bytes;
 };
 
 SteadyWs layout_steady(char* base, int G, int n, int nc, uint64_t total, bool grad, bool replay, int nd,
-                       bool host_out, bool want_ev, bool want_x, bool want_T, bool want_q, bool want_qbin) {
+                       bool host_out, bool want_ev, bool want_x, bool want_T, bool want_q, bool want_qbin,
+                       uint64_t n_det = 0) {
   Carve c;
   c.base = base;
   SteadyWs w{};
@@ -375,8 +438,12 @@ SteadyWs layout_steady(char* base, int G, int n, int nc, uint64_t total, bool gr
   w.work = c.take<unsigned long long>(1);
   w.flags = c.take<int>(2);
   w.t0 = c.take<unsigned long long>(1);
+  w.det_raw = n_det ? c.take<double>(4 * n_det) : nullptr;
+  w.det_q = n_det ? c.take<long long>(4 * n_det) : nullptr;
   c.off = (c.off + 255) & ~(size_t)255;
   w.zero_end = base ? base + c.off : nullptr;
+  w.regs = n_det ? c.take<DetRegion>(MCBTE_MAX_REGIONS) : nullptr;
+  w.det = (host_out && n_det) ? c.take<double>(4 * n_det) : nullptr;
   w.dirs = (grad && nd > 0) ? c.take<double>((size_t)nd * n) : nullptr;
   w.dpi = (grad && nd > 0) ? c.take<double>(nd) : nullptr;
   w.xrep = replay ? c.take<double>(total) : nullptr;
@@ -424,6 +491,11 @@ mcbte_status check_steady(const mcbte_material* m, const mcbte_geometry* const* 
     if (uses_spec_bin(d) && !m->view.spec_thr)
       return fail(MCBTE_ERR_INVALID_ARG, "run_steady: a per-bin specularity needs the material's spec_bin");
   }
+  {
+    const mcbte_status rs = check_regions(p->n_regions, p->regions, p->region_grid, "run_steady");
+    if (rs != MCBTE_OK) return rs;
+    if (p->n_regions > 0 && G != 1) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: detector regions need one geometry");
+  }
   if (t >= (1ull << 40)) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: too many particles");
   *total = t;
   return MCBTE_OK;
@@ -453,8 +525,9 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   }
   const bool host_out = out->on_host != 0;
   const bool replay = grad && p->precision == MCBTE_FP32_TRACE;
+  const uint64_t n_det = region_detectors(p->n_regions, p->region_grid);
   SteadyWs w = layout_steady(nullptr, G, n, nc, total, grad, replay, nd, host_out, out->events_pp, out->X_pp, out->T,
-                             out->q, out->q_bin);
+                             out->q, out->q_bin, n_det);
   const size_t need = w.bytes;
   char* base = static_cast<char*>(workspace);
   bool own = false;
@@ -466,7 +539,7 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   }
   char* aligned = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(base) + 255) & ~(uintptr_t)255);
   w = layout_steady(aligned, G, n, nc, total, grad, replay, nd, host_out, out->events_pp, out->X_pp, out->T, out->q,
-                    out->q_bin);
+                    out->q_bin, n_det);
   auto release = [&]() {
     if (own) cudaFreeAsync(base, s);
   };
@@ -502,8 +575,16 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   C.seed_dev = reinterpret_cast<const unsigned long long*>(p->seed_device);
   C.refill_min = p->refill_threshold;
   C.cell_flux_axis = p->cell_flux_axis ? 1 : 0;
-  C.ext = 0;
+  C.ext = p->n_regions > 0 ? 1 : 0;
   for (int g = 0; g < G; ++g) C.ext |= uses_ext(m, geoms[g]->host) ? 1 : 0;
+  C.n_regs = p->n_regions;
+  C.n_det = (uint32_t)n_det;
+  C.regs = w.regs;
+  if (p->n_regions > 0) {
+    const std::vector<DetRegion> rg =
+        build_regions(p->n_regions, p->regions, p->region_grid, false, nullptr, geoms[0]->host.L);
+    RUN_TRY(cudaMemcpyAsync(w.regs, rg.data(), rg.size() * sizeof(DetRegion), cudaMemcpyHostToDevice, s));
+  }
   Acc A{};
   A.cellP = w.cellP;
   A.cellD = w.cellD;
@@ -518,6 +599,8 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   A.dsum = w.dsum;
   A.work = w.work;
   A.flags = w.flags;
+  A.det_raw = w.det_raw;
+  A.det_q = w.det_q;
   A.events_pp = host_out ? w.events_pp : out->events_pp;
   A.X_pp = host_out ? w.X_pp : out->X_pp;
   if (grad && nd > 0) {
@@ -553,6 +636,7 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   O.q = host_out ? w.q : out->q;
   O.q_bin = host_out ? w.q_bin : out->q_bin;
   O.stats = host_out ? w.stats : out->stats;
+  O.det = host_out ? w.det : out->det;
   if (grad) {
     O.dk = host_out ? w.dk : gout->dkappa_dlogtau;
     O.dkp = host_out ? w.dkp : gout->dkappa_dp;
@@ -571,6 +655,7 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
     RUN_TRY(d2h(out->stats, w.stats, (size_t)G * MCBTE_NSTATS * sizeof(double)));
     RUN_TRY(d2h(out->events_pp, w.events_pp, total * sizeof(uint32_t)));
     RUN_TRY(d2h(out->X_pp, w.X_pp, total * sizeof(double)));
+    RUN_TRY(d2h(out->det, w.det, 4 * n_det * sizeof(double)));
     if (grad) {
       RUN_TRY(d2h(gout->dkappa_dlogtau, w.dk, (size_t)n * sizeof(double)));
       RUN_TRY(d2h(gout->dkappa_dp, w.dkp, 2 * sizeof(double)));
@@ -604,7 +689,7 @@ mcbte_status mcbte_steady_workspace_size(const mcbte_material* m, const mcbte_ge
   if (!bytes) return fail(MCBTE_ERR_INVALID_ARG, "workspace_size: null bytes");
   SteadyWs w = layout_steady(nullptr, n_geoms, m->n, p->n_cells, total, want_grad != 0,
                              want_grad != 0 && p->precision == MCBTE_FP32_TRACE, n_dirs, false, false, false, false,
-                             false, false);
+                             false, false, region_detectors(p->n_regions, p->region_grid));
   *bytes = w.bytes;
   return MCBTE_OK;
 }
@@ -717,24 +802,10 @@ mcbte_status check_transient(const mcbte_material* m, const mcbte_geometry* g, c
   }
   for (int a = 0; a < 3; ++a)
     if (p->grid[a] < 1 || p->grid[a] > 4096) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: grid in [1, 4096]");
-  if (p->n_regions < 0 || p->n_regions > MCBTE_MAX_REGIONS)
-    return fail(MCBTE_ERR_INVALID_ARG, "run_transient: n_regions in [0, MCBTE_MAX_REGIONS]");
-  if (p->n_regions > 0 && (!p->regions || !p->region_grid))
-    return fail(MCBTE_ERR_INVALID_ARG, "run_transient: regions and region_grid required");
-  uint64_t nd = 0;
-  for (int k = 0; k < p->n_regions; ++k) {
-    uint64_t cnt = 1;
-    for (int a = 0; a < 3; ++a) {
-      const double lo = p->regions[6 * k + 2 * a], hi = p->regions[6 * k + 2 * a + 1];
-      const int n = p->region_grid[3 * k + a];
-      if (!(std::isfinite(lo) && std::isfinite(hi) && hi > lo))
-        return fail(MCBTE_ERR_INVALID_ARG, "run_transient: region bounds must satisfy min < max");
-      if (n < 1 || n > 4096) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: region_grid in [1, 4096]");
-      cnt *= (uint64_t)n;
-    }
-    nd += cnt;
+  {
+    const mcbte_status rs = check_regions(p->n_regions, p->regions, p->region_grid, "run_transient");
+    if (rs != MCBTE_OK) return rs;
   }
-  if (nd > (1ull << 28)) return fail(MCBTE_ERR_INVALID_ARG, "run_transient: too many detectors");
   if (p->threads_per_block != 0 && p->threads_per_block != 256 && p->threads_per_block != 512 &&
       p->threads_per_block != 768 && p->threads_per_block != 1024)
     return fail(MCBTE_ERR_INVALID_ARG, "run_transient: threads_per_block must be 0, 256, 512, 768 or 1024");
@@ -827,30 +898,8 @@ mcbte_status mcbte_run_transient(const mcbte_material* m, const mcbte_geometry* 
   C.n_det = (uint32_t)ncell;
   C.regs = w.regs;
   if (C.n_regs > 0) {
-    std::vector<DetRegion> rg(C.n_regs);
-    uint32_t off = 0;
-    for (int k = 0; k < C.n_regs; ++k) {
-      DetRegion& r = rg[k];
-      double vol = 1.0;
-      int cnt = 1;
-      for (int a = 0; a < 3; ++a) {
-        const double lo_m = whole_region ? 0.0 : p->regions[6 * k + 2 * a];
-        const double hi_m = whole_region ? g->host.L[a] : p->regions[6 * k + 2 * a + 1];
-        r.n[a] = whole_region ? p->grid[a] : p->region_grid[3 * k + a];
-        r.hi_closed[a] = (hi_m * 1e9) >= (g->host.L[a] * 1e9);
-        r.lo[a] = lo_m * 1e9;
-        r.hi[a] = hi_m * 1e9;
-        r.h[a] = (r.hi[a] - r.lo[a]) / (double)r.n[a];
-        r.lof[a] = (float)r.lo[a];
-        r.hif[a] = (float)r.hi[a];
-        r.cinvf[a] = (float)((double)r.n[a] / (r.hi[a] - r.lo[a]));
-        vol = vol * (hi_m - lo_m);
-        cnt *= r.n[a];
-      }
-      r.v_det = vol / (double)cnt;
-      r.off = off;
-      off += (uint32_t)cnt;
-    }
+    const std::vector<DetRegion> rg =
+        build_regions(C.n_regs, p->regions, p->region_grid, whole_region, p->grid, g->host.L);
     RUN_TRY(cudaMemcpyAsync(w.regs, rg.data(), rg.size() * sizeof(DetRegion), cudaMemcpyHostToDevice, s));
   }
   Acc A{};

@@ -40,6 +40,7 @@ struct SteadyOutDev {
   double* dk;        // grad: [n_bins]
   double* dkp;       // grad: [2]
   double* dkdir;     // grad: [n_dirs][2]
+  double* det;       // detector regions: [n_det][4], or null
 };
 
 cudaError_t launch_steady_f32(bool grad, bool cells, const GeoRun* geos, const uint64_t* offs, const MatView& M,

@@ -154,6 +154,8 @@ struct Acc {
   double* dsum;               // [n_dirs][2]
   double* snap;               // [n_times][cells][4] transient
   uint4* tstate;              // [total][3] particle state between transient time windows, or null
+  double* det_raw;            // [n_det][4] steady detector sums (FP64 path)
+  long long* det_q;           // [n_det][4] the same in fixed point (FP32 path)
   uint32_t* events_pp;        // [total] or null
   double* X_pp;               // [total] or null
   unsigned long long* work;   // [1] persistent work counter
@@ -364,6 +366,15 @@ struct TallyPlain {
   double* qb;      // [n_bins], or null
   int nc, ca, ta;
   double h;
+  double* det = nullptr;   // [n_det][4] steady detector-region sums, or null
+
+  __device__ __forceinline__ bool has_det() const { return det != nullptr; }
+  __device__ __forceinline__ void det_add(size_t c, double a0, double a1, double a2, double a3) const {
+    atomicAdd(det + c + 0, a0);
+    atomicAdd(det + c + 1, a1);
+    atomicAdd(det + c + 2, a2);
+    atomicAdd(det + c + 3, a3);
+  }
 
   __device__ __forceinline__ double X(const Particle<double>& p) const { return p.X; }
 
@@ -472,6 +483,15 @@ struct TallyFxT {
   long long* qb;   // [n_bins], or null
   int nc, ca, ta;
   float h, inv_h;
+  long long* det = nullptr;   // [n_det][4] steady detector-region sums (fixed point), or null
+
+  __device__ __forceinline__ bool has_det() const { return det != nullptr; }
+  __device__ __forceinline__ void det_add(size_t c, float a0, float a1, float a2, float a3) const {
+    red_s64(det + c + 0, fx(a0));
+    red_s64(det + c + 1, fx(a1));
+    red_s64(det + c + 2, fx(a2));
+    red_s64(det + c + 3, fx(a3));
+  }
 
   __device__ __forceinline__ double X(const Particle<float>& p) const { return (double)p.Xq * kFxInv; }
 
@@ -768,6 +788,23 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
   return STEP_ALIVE;
 }
 
+// Steady detector regions (Sec. 4.5): the flight's track length in every
+// detector it crosses, s dt for T (ps) and s v dt u for q (nm), dt the time
+// spent in the detector (the time integral of Eqs. temp_steady, flux_x_steady).
+template <typename R, class Tally>
+__device__ __forceinline__ void region_steady(const Particle<R>& p, R seg, const RunCfg& C, const Tally& T) {
+  const R v = p.v;
+  const R w3[3] = {v * p.u[0], v * p.u[1], v * p.u[2]};
+  const R dt = sizeof(R) == 8 ? seg / v : seg * p.inv_v;
+  for (int k = 0; k < C.n_regs; ++k) {
+    const DetRegion& r = C.regs[k];
+    region_track<R>(r, p.x, w3, R(0), R(0), dt, [&](uint32_t d, R dur) {
+      T.det_add(((size_t)r.off + d) * 4, p.s * dur, ((p.s * v) * dur) * p.u[0], ((p.s * v) * dur) * p.u[1],
+                ((p.s * v) * dur) * p.u[2]);
+    });
+  }
+}
+
 // One flight + event of a steady (or gradient) particle: first hit vs the
 // remaining relaxation distance (boundary wins ties, Sec. 3.3 case iii),
 // track-length tallies of the flight (Eqs. temp_steady, flux_x_steady), then
@@ -788,6 +825,9 @@ __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, cons
   double Xb = 0.0;
   if (Grad::on) Xb = T.X(p);
   const auto c = T.segment(p, seg);
+  if constexpr (EXT) {
+    if (C.n_regs > 0 && T.has_det()) region_steady<R>(p, seg, C, T);
+  }
   if (Grad::on) gr.flight(relax, (double)(seg / p.lam), Xb, c);
 #pragma unroll
   for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];

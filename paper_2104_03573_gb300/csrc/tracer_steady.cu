@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(256) k_steady_fp64(const GeoRun* __restrict__ 
   T.ca = C.cell_axis;
   T.ta = C.tally_axis;
   T.h = CELLS ? G.L[C.cell_axis] / (double)C.n_cells : 1.0;
+  T.det = C.n_regs > 0 ? A.det_raw : nullptr;
   int out;
   for (;;) {
     out = step_steady<double, typename GradPick<GRAD, GradList>::type, TallyPlain>(p, G, M, M.rec_relax, nullptr, C,
@@ -233,6 +234,7 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
   T.ta = C.tally_axis;
   T.cP = T.cD = T.qb = nullptr;
   T.h = T.inv_h = 1.0f;
+  T.det = (C.n_regs > 0 && !GRAD) ? A.det_q : nullptr;
   bool alive = false;
   bool drained = false;   // no work left for this lane: it idles in the loop until its warp is drained
   uint64_t idx = 0;
@@ -373,6 +375,21 @@ __global__ void k_finalize_steady(const GeoRun* geos, MatView M, RunCfg C, Acc A
       if (O.T) O.T[(size_t)g * nc + c] = (kT * v[0]) * 1e-12;
       if (O.q)
         for (int b = 0; b < 3; ++b) O.q[((size_t)g * nc + c) * 3 + b] = (kq * v[1 + b]) * 1e-9;
+    }
+  }
+  if (O.det && C.n_regs > 0) {
+    // detector regions: volume-averaged T and q of each detector
+    const double C_tot_d = M.sums[0];
+    for (uint32_t d = threadIdx.x; d < C.n_det; d += blockDim.x) {
+      double vd = C.regs[0].v_det;
+      for (int k = 0; k < C.n_regs; ++k)
+        if (d >= C.regs[k].off) vd = C.regs[k].v_det;
+      const double kT = E_eff / (C_tot_d * vd);
+      const double kq = E_eff / vd;
+      double raw[4];
+      for (int b = 0; b < 4; ++b) raw[b] = A.det_raw[(size_t)d * 4 + b] + (double)A.det_q[(size_t)d * 4 + b] * kFxInv;
+      O.det[(size_t)d * 4 + 0] = (kT * raw[0]) * 1e-12;
+      for (int b = 1; b < 4; ++b) O.det[(size_t)d * 4 + b] = (kq * raw[b]) * 1e-9;
     }
   }
   if (O.q_bin && C.per_bin) {

@@ -252,6 +252,33 @@ def test_time_bin_averages_fp64_parity_and_fp32_conservation(with_regions):
     np.testing.assert_allclose(whole.sum(axis=1), run.n, rtol=1e-6)   # every particle, every whole bin
 
 
+def test_steady_detector_regions_fp64_parity_and_fp32():
+    wl = W.si_slab_c2(n=20_000)
+    m, g, run = wl.material, wl.geometries[0], wl.run
+    Lb = g.L
+    sub = ((0.1 * Lb[0], 0.7 * Lb[0], 0.0, Lb[1], 0.25 * Lb[2], 0.75 * Lb[2]), (2, 2, 4))
+    slabs = ((0.0, Lb[0], 0.0, Lb[1], 0.0, Lb[2]), (1, 1, run.n_cells))
+    run.regions = [slabs, sub]
+    M, G = api.Material(m), api.Geometry(g)
+    base = dict(seed=run.seed, n_cells=run.n_cells, cell_axis=2, tally_axis=2, per_bin=True,
+                max_events=run.max_events, regions=run.regions)
+    o = api.run_steady(M, [G], [run.n], api.SteadyConfig(precision=L.FP64_PLAIN, **base))
+    torch.cuda.synchronize()
+    ref = oracle.run_steady(m, g, run)
+    ok, err = rel_close(o.det[:, 0].cpu().numpy(), ref["det_T"], RTOL)
+    assert ok, err
+    ok, err = rel_close(o.det[:, 1:].cpu().numpy(), ref["det_q"], RTOL)
+    assert ok, err
+    # FP32: the slab slices of the region equal the 1-D cell tallies statistically
+    o32 = api.run_steady(M, [G], [1_000_000], api.SteadyConfig(precision=L.FP32_TRACE, **base))
+    torch.cuda.synchronize()
+    d = o32.det.cpu().numpy()
+    nc = run.n_cells
+    T1 = o32.T[0].cpu().numpy()
+    assert np.max(np.abs(d[:nc, 0] - T1)) < 1e-3 * np.max(np.abs(T1)) + 1e-6
+    assert abs(d[nc:, 0].mean() - ref["det_T"][nc:].mean()) < 0.1 * np.abs(ref["det_T"]).max()
+
+
 def test_fp64_film_batch_geometry_index_streams():
     wl = W.film_batch_c4(n_films=6)
     mat = wl.material
