@@ -53,7 +53,7 @@ class _Params(C.Structure):
         ("n_cells", C.c_int), ("cell_axis", C.c_int), ("tally_axis", C.c_int),
         ("t_max", C.c_double), ("n_times", C.c_int), ("t_meas", C.c_void_p), ("grid", C.c_int * 3),
         ("n_regions", C.c_int), ("regions", C.c_void_p), ("region_grid", C.c_void_p), ("time_average", C.c_int),
-        ("want_grad", C.c_int), ("n_dirs", C.c_int), ("dirs", C.c_void_p), ("n_threads", C.c_int),
+        ("want_grad", C.c_int), ("dp_mvd", C.c_int), ("n_dirs", C.c_int), ("dirs", C.c_void_p), ("n_threads", C.c_int),
     ]
 
 
@@ -275,11 +275,25 @@ def _kappa_gradient(geom, axis: int) -> float:
     return float("nan")
 
 
+def dp_mvd(geom, dp_estimator: int = 0) -> bool:
+    """Whether d kappa / d p_pore takes the measure-valued estimator."""
+    if not getattr(geom, "pore", False):
+        return False
+    p = float(geom.pore_p)
+    return dp_estimator == 2 or (dp_estimator == 0 and (p <= 0.0 or p >= 1.0))
+
+
 def run_steady(material, geom, run, *, pid_begin: int = 0, pid_end: Optional[int] = None,
                per_particle: bool = False, grad: bool = False, dirs: Optional[np.ndarray] = None,
-               n_threads: int = 0, batch_index: int = 0, n_total: Optional[int] = None) -> dict:
+               n_threads: int = 0, batch_index: int = 0, n_total: Optional[int] = None,
+               dp_estimator: int = 0) -> dict:
     """Trace particles [pid_begin, pid_end) of a steady run of N = run.n (or
-    n_total) particles and return raw sums plus the physical tallies."""
+    n_total) particles and return raw sums plus the physical tallies.
+
+    dp_estimator selects the estimator of d kappa / d p_pore when grad is set:
+    1 the likelihood ratio of the specular / diffuse draw, 2 the measure-valued
+    one (each particle's phantom trace with one pore hit's branch flipped),
+    0 the likelihood ratio for 0 < p < 1 and the measure-valued one at p = 0, 1."""
     N = int(n_total if n_total is not None else run.n)
     pe = N if pid_end is None else int(pid_end)
     keep = _Keep()
@@ -291,6 +305,7 @@ def run_steady(material, geom, run, *, pid_begin: int = 0, pid_end: Optional[int
                 n_particles=N, pid_begin=int(pid_begin), pid_end=pe, n_scat_max=int(run.n_scat_max),
                 max_events=int(run.max_events), n_cells=int(run.n_cells), cell_axis=int(run.cell_axis),
                 tally_axis=int(run.tally_axis), want_grad=int(grad),
+                dp_mvd=int(bool(grad) and dp_mvd(geom, dp_estimator)),
                 n_dirs=0 if dirs_a is None else dirs_a.shape[0],
                 dirs=_ptr(dirs_a), n_threads=int(n_threads))
     npp = pe - int(pid_begin)

@@ -22,6 +22,9 @@
 //   - transient snapshot tallies                                          Eq. sampling, Sec. 3.4
 //   - likelihood-ratio scores for d/d(log tau_i) and d/dp (no counterpart in the paper; derived
 //     from the exponential law of Eq. time_to_scat and the discrete draws of Eq. n_scatt / Eq. specular)
+//   - measure-valued d/dp of the pore specularity (the weak derivative of the specular / diffuse
+//     draw of Eq. specular: one pore hit per particle, chosen uniformly, traced again with the
+//     other branch)
 //
 // The random numbers are Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11,
 // "Parallel random numbers: as easy as 1, 2, 3"), implemented here from
@@ -262,6 +265,7 @@ typedef struct {
   const int* region_grid;     // [n_regions][3]
   int time_average;           // 0: snapshots at t_m (Eq. sampling); 1: averages over [t_{m-1}, t_m)
   int want_grad;
+  int dp_mvd;                 // 1: d kappa / d p_pore by the measure-valued estimator
   int n_dirs;
   const double* dirs;     // [n_dirs][n_bins]
   int n_threads;
@@ -680,8 +684,12 @@ struct Partial {
 
 struct Period { int bin; double A, B; };
 
+// The pore hit a particle's phantom trace flips: `sel` of its K pore hits,
+// and whether the nominal trajectory reflected specularly there.
+struct MvdPick { uint32_t K = 0, sel = 0; bool spec = false; };
+
 void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p0, uint64_t p1,
-                 Partial& out, or_out* O) {
+                 Partial& res, or_out* O) {
   const Geo& g = S.g;
   const int n = t.n;
   const uint32_t k0 = (uint32_t)P->seed, k1 = (uint32_t)(P->seed >> 32);
@@ -689,7 +697,16 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
   const bool cells = P->n_cells > 0 && !P->transient;
   const double h_cell = cells ? g.L[P->cell_axis] / (double)P->n_cells : 0.0;
   std::vector<Period> periods;
-  for (uint64_t pid = p0; pid < p1; ++pid) {
+  // tallies of phantom traces (discarded)
+  Partial scratch;
+  if (P->dp_mvd) scratch = res;
+  // One trajectory of particle pid.  flip = 0: the nominal trace, with all
+  // tallies; `pick` receives the reservoir choice of a pore hit.  flip = j > 0:
+  // the phantom trace of the measure-valued derivative: the same random words,
+  // but the j-th pore hit takes the other branch; only its X is used.
+  auto trace_one = [&](uint64_t pid, uint32_t flip, MvdPick* pick) -> double {
+    Partial& out = flip ? scratch : res;
+    uint32_t n_pore = 0;
     uint32_t ctr[4] = {(uint32_t)pid, P->batch_index, 0u, 0u};
     uint32_t w[4], w1[4], w2[4], w3[4];
     // ---- emission (event 0): sub-blocks 0 and 1 carry the bin, direction
@@ -1010,7 +1027,24 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
         ctr[2] = e;
         ctr[3] = 0; philox4x32_10(ctr, k0, k1, w);
         bool spec = (uint64_t)w[0] < g.pthr_pore;
-        if (P->want_grad) {
+        ++n_pore;
+        if (flip) {
+          if (n_pore == flip) spec = !spec;
+        } else if (P->want_grad && P->dp_mvd) {
+          // reservoir choice, uniform over the trajectory's pore hits: hit j
+          // takes the choice with probability 1/j, decided by the 64-bit word
+          // r of sub-block 257 of its event (r <= floor((2^64 - 1) / j) holds
+          // for exactly ceil(2^64 / j) of the 2^64 words)
+          uint32_t c5[4] = {(uint32_t)pid, P->batch_index, e, 257u};
+          uint32_t w5[4];
+          philox4x32_10(c5, k0, k1, w5);
+          const uint64_t r = (uint64_t)w5[0] | ((uint64_t)w5[1] << 32);
+          if (r <= UINT64_MAX / (uint64_t)n_pore) {
+            pick->sel = n_pore;
+            pick->spec = spec;
+          }
+          pick->K = n_pore;
+        } else if (P->want_grad) {
           double sc = spec ? 1.0 / g.p_pore : -1.0 / (1.0 - g.p_pore);
           PA += sc;
           PB += sc * X;
@@ -1037,15 +1071,18 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
     if (truncated) out.scal[OR_TRUNC] += 1.0;
     out.scal[OR_SUMX] += X;
     out.scal[OR_SUMX2] += X * X;
+    if (flip) return X;
     if (O->events_pp) O->events_pp[pid - P->pid_begin] = (uint32_t)std::min<uint64_t>(nev, 0xFFFFFFFFu);
     if (O->X_pp) O->X_pp[pid - P->pid_begin] = X;
     if (P->want_grad) {
       for (const Period& pr : periods) out.G[pr.bin] += pr.A * X - pr.B;
       double R = (double)n_res * X - sum_x_res;
       out.scal[OR_RSUM] += R;
-      double gp = PA * X - PB;
-      out.scal[OR_GP] += gp;
-      out.scal[OR_GP2] += gp * gp;
+      if (!P->dp_mvd) {
+        double gp = PA * X - PB;
+        out.scal[OR_GP] += gp;
+        out.scal[OR_GP2] += gp * gp;
+      }
       for (int kd = 0; kd < P->n_dirs; ++kd) {
         const double* d = P->dirs + (size_t)kd * n;
         double val = 0.0;
@@ -1054,6 +1091,23 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
         out.dsum[kd] += val;
         out.dsum2[kd] += val * val;
       }
+    }
+    return X;
+  };
+  for (uint64_t pid = p0; pid < p1; ++pid) {
+    MvdPick pick;
+    const double X = trace_one(pid, 0, &pick);
+    if (P->want_grad && P->dp_mvd) {
+      // measure-valued derivative of the specular / diffuse draw at the chosen
+      // hit: K (X with a specular reflection there - X with a diffuse one),
+      // whose mean over the uniform choice is the sum over all K hits
+      double D = 0.0;
+      if (pick.K > 0) {
+        const double Xph = trace_one(pid, pick.sel, nullptr);
+        D = (double)pick.K * (pick.spec ? X - Xph : Xph - X);
+      }
+      res.scal[OR_GP] += D;
+      res.scal[OR_GP2] += D * D;
     }
   }
 }

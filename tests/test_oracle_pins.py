@@ -719,3 +719,51 @@ def test_lr_gradient_matches_crn_finite_difference_specularity():
     se = math.hypot(fd_se, r["dkappa_dp_se"])
     assert r["dkappa_dp"] > 0           # specular pores conduct better
     assert abs(r["dkappa_dp"] - fd) < 4.0 * se
+
+
+def _gray_pore_run(n, seed):
+    m = W.gray(6000.0, 200e-9, C=1e6)
+    return m, W.SteadyRun(n=n, seed=seed, tally_axis=1, n_scat_max=4, max_events=10 ** 7)
+
+
+@pytest.mark.slow
+def test_measure_valued_specularity_gradient_agrees_with_likelihood_ratio():
+    # two unrelated unbiased estimators of d kappa / d p at p = 0.5: the score
+    # of the specular / diffuse draw (Eq. specular) and its weak derivative
+    # (each particle traced again with one pore hit's branch flipped)
+    m, run = _gray_pore_run(4_000_000, 41)
+    g = W.pore_lattice(100e-9, 0.25, 200e-9, p_pore=0.5)
+    rl = oracle.run_steady(m, g, run, grad=True, dp_estimator=1)
+    rv = oracle.run_steady(m, g, run, grad=True, dp_estimator=2)
+    # the phantom traces leave every nominal tally and the tau gradient alone
+    assert rv["kappa"] == rl["kappa"] and rv["events"] == rl["events"]
+    assert np.array_equal(rv["raw_G"], rl["raw_G"])
+    se = math.hypot(rl["dkappa_dp_se"], rv["dkappa_dp_se"])
+    assert rv["dkappa_dp"] > 0
+    assert abs(rv["dkappa_dp"] - rl["dkappa_dp"]) < 4.0 * se, (rv["dkappa_dp"], rl["dkappa_dp"], se)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("p0,side", [(0.0, 1.0), (1.0, -1.0)])
+def test_measure_valued_specularity_gradient_at_p0_and_p1(p0, side):
+    # at p = 0 (1) no pore hit is ever specular (diffuse), so the score of the
+    # draw misses the derivative; the measure-valued estimator matches the
+    # one-sided common-random-number difference quotient
+    m, run = _gray_pore_run(4_000_000, 32)
+    h = 0.05
+    g0 = W.pore_lattice(100e-9, 0.25, 200e-9, p_pore=p0)
+    g1 = W.pore_lattice(100e-9, 0.25, 200e-9, p_pore=p0 + side * h)
+    rv = oracle.run_steady(m, g0, run, grad=True)              # automatic choice: measure-valued here
+    r2 = oracle.run_steady(m, g0, run, grad=True, dp_estimator=2)
+    assert rv["dkappa_dp"] == r2["dkappa_dp"]
+    ra = oracle.run_steady(m, g0, run, per_particle=True)
+    rb = oracle.run_steady(m, g1, run, per_particle=True)
+    fd = side * (rb["kappa"] - ra["kappa"]) / h
+    dpp = (rb["X_pp"] - ra["X_pp"]) / h
+    fd_se = abs(ra["kappa"] / ra["X_pp"].sum()) * dpp.std(ddof=1) * math.sqrt(run.n)
+    se = math.hypot(fd_se, rv["dkappa_dp_se"])
+    assert abs(rv["dkappa_dp"] - fd) < 4.0 * se, (rv["dkappa_dp"], fd, se)
+    # the score estimator at the end point is not that derivative (at p = 1 it
+    # even has the wrong sign here)
+    rl = oracle.run_steady(m, g0, run, grad=True, dp_estimator=1)
+    assert abs(rl["dkappa_dp"] - fd) > 4.0 * math.hypot(fd_se, rl["dkappa_dp_se"])
