@@ -17,7 +17,8 @@ Other workloads (`--workload`), same line format:
   film_batch     64 films 10 nm..10 um in one persistent launch replayed as
                  a CUDA graph, 1.4e8 particles in total
   pore_grad      nanoporous film, 5e7 particles, forward + likelihood-ratio
-                 gradient over 3000 log-tau scales and the pore specularity
+                 gradient over 3000 log-tau scales + measure-valued derivative
+                 in the pore specularity at p = 0
 
 `--impl reference` times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload.  Multi-GPU (torchrun): every rank traces its own
@@ -261,8 +262,10 @@ def _workload_setup(name, args, seed_offset):
             f3, g3 = api.grad(Mh, Gh, run.n, replace(cfg, trace_events=None))
             return f3.stats.cpu().numpy(), g3.dkappa_dlogtau.cpu().numpy()
         desc = ("nanoporous film: 100 nm cell, cylindrical pore porosity 0.25, 200 nm thick, diffuse walls, "
-                "grad_T -1e6 K/m along y, N_scat_max 10; forward + LR gradient (3000 log-tau + pore p)")
-        return dict(mat=mat, geo=geo, run=run, n=run.n, step=step, fp64=fp64, e2e=e2e,
+                "grad_T -1e6 K/m along y, N_scat_max 10; forward + gradient: likelihood ratio over 3000 "
+                "log-tau scales, measure-valued d kappa / d p_pore at p = 0 (every particle that meets the "
+                "pore is traced once more with one pore hit specular)")
+        return dict(mat=mat, geo=geo, run=run, n=run.n, step=step, fp64=fp64, e2e=e2e, gout=go,
                     d2h=8 * (M.n_bins * 2 + 2 + L.NSTATS), h2d=_material_bytes(mat) + ctypes.sizeof(L.GeometryDesc) + 8,
                     desc=desc, launches=3, timer=tm, kernel="k_steady_f32 (grad)",
                     shape={"threads_per_block": cfg.threads_per_block, "refill_threshold": cfg.refill_threshold},
@@ -404,6 +407,7 @@ def run_ours(args):
             pooled = shard.allreduce_steady_stats(st[0])
             kappa, kse = pooled["kappa"], pooled["kappa_se"]
         t_1pct = float(t_step * np.max((se / np.abs(k) / 0.01) ** 2))
+    dkdp = [float(x) for x in wk["gout"].dkappa_dp.cpu().numpy()] if "gout" in wk else None
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -456,6 +460,7 @@ def run_ours(args):
                    "seed": wk["run"].seed, "launch": wk["shape"]},
         "s_to_1pct_se_kappa": t_1pct, "kappa_eff": kappa, "kappa_se": kse,
         "events_per_step": ev_step, "wall_s": wall_max,
+        **({"dkappa_dp_pore": dkdp} if dkdp is not None else {}),
         "fp64_plain": fp64,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
                      "frac": achieved / peak_tinst,

@@ -325,11 +325,15 @@ mcbte_status mcbte_run_transient(const mcbte_material* m, const mcbte_geometry* 
 typedef struct {
   double* dkappa_dlogtau;  /* [n_bins] d kappa / d log tau_i                              */
   double* dkappa_dp;       /* [2] value and standard error of d kappa / d p_pore; NaN
-                              when the geometry has no pore or p_pore is 0 or 1           */
+                              when the geometry has no pore, or for the likelihood ratio
+                              at p_pore = 0 or 1                                          */
   const double* dirs;      /* [n_dirs][n_bins] probe directions in log-tau space, or NULL */
   int n_dirs;              /* 0..16                                                        */
   double* dkappa_dir;      /* [n_dirs][2] value and SE of d kappa along each direction     */
   int on_host;             /* must equal the forward outputs' on_host                     */
+  int dp_estimator;        /* d kappa / d p_pore: 0 = likelihood ratio for 0 < p_pore < 1,
+                              measure-valued at p_pore = 0 or 1; 1 = likelihood ratio;
+                              2 = measure-valued (any p_pore)                              */
 } mcbte_grad_out;
 
 /* Steady run of one geometry that also returns the likelihood-ratio
@@ -340,6 +344,15 @@ typedef struct {
  * the resampling law ~ C/tau of Eq. n_scatt (-delta_ij + pi_j) and the
  * specular / diffuse draw of Sec. 3.5.3 (1/p, -1/(1-p)); each score
  * multiplies the tally still to come.  The paper itself has no gradient.
+ * The measure-valued estimator of d kappa / d p_pore differentiates the
+ * specular / diffuse draw itself (its weak derivative is the difference of
+ * the two branches): of a particle's K pore hits one is chosen uniformly (hit
+ * j replaces the choice when the 64-bit word of Philox sub-block 257 of its
+ * event is at most floor((2^64 - 1) / j)), the particle is traced a second
+ * time from its emission with the same random words and that hit's branch
+ * flipped, and its score is K (X with the hit specular - X with it diffuse).
+ * It stays valid at p_pore = 0 and 1, where the likelihood-ratio score does
+ * not; the second traces add to the run time, not to the tallies.
  * FP64_PLAIN keeps each particle's relaxation periods and requires
  * 1 <= n_scat_max <= 64.  FP32_TRACE runs two passes: the forward run, which
  * records every particle's final tally, then a pass that replays the same

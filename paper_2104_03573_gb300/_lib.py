@@ -12,6 +12,7 @@ LIB_PATH = os.path.join(HERE, "libmcbte.so")
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, WARN_TRUNCATED, ERR_WORKSPACE, ERR_REPLAY = range(8)
 FACE_ISOTHERMAL, FACE_ADIABATIC, FACE_PERIODIC = 0, 1, 2
 FP64_PLAIN, FP32_TRACE = 0, 1
+DP_AUTO, DP_LIKELIHOOD_RATIO, DP_MEASURE_VALUED = 0, 1, 2
 (STAT_KAPPA, STAT_KAPPA_SE, STAT_Q_MEAN, STAT_Q_SE, STAT_SUMX, STAT_SUMX2, STAT_EVENTS, STAT_TRUNCATED,
  STAT_E_TOT, STAT_MAX_EVENTS, STAT_KAPPA_CELL, STAT_SIGNED_EMITTED, STAT_SIGNED_ABSORBED, STAT_STATUS,
  STAT_N, STAT_ABSORBED) = range(16)
@@ -71,7 +72,8 @@ class TransientOut(C.Structure):
 
 class GradOut(C.Structure):
     _fields_ = [("dkappa_dlogtau", C.c_void_p), ("dkappa_dp", C.c_void_p), ("dirs", C.c_void_p),
-                ("n_dirs", C.c_int), ("dkappa_dir", C.c_void_p), ("on_host", C.c_int)]
+                ("n_dirs", C.c_int), ("dkappa_dir", C.c_void_p), ("on_host", C.c_int),
+                ("dp_estimator", C.c_int)]
 
 
 _lib = None

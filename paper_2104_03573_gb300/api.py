@@ -365,9 +365,11 @@ class GradOutputs:
 
 def grad(material: Material, geom: Geometry, n_particles: int, cfg: SteadyConfig, *, dirs=None,
          fwd: Optional[SteadyOutputs] = None, gout: Optional[GradOutputs] = None, workspace=None,
-         stream=None):
+         stream=None, dp_estimator: int = L.DP_AUTO):
     """``mcbte_grad``: forward tallies plus the likelihood-ratio gradient of
-    kappa with respect to per-bin log tau and the pore specularity."""
+    kappa with respect to per-bin log tau and the pore specularity (the
+    measure-valued estimator for the latter at p = 0, 1, or wherever
+    ``dp_estimator`` asks for it)."""
     import torch
     n = np.ascontiguousarray(np.asarray([n_particles], dtype=np.uint64))
     if fwd is None:
@@ -385,6 +387,7 @@ def grad(material: Material, geom: Geometry, n_particles: int, cfg: SteadyConfig
     g.n_dirs = nd
     g.dkappa_dir = gout.dkappa_dir.data_ptr()
     g.on_host = 0
+    g.dp_estimator = int(dp_estimator)
     p = steady_params(cfg, n)
     o = fwd.struct()
     ws_ptr, ws_bytes = (None, 0) if workspace is None else (workspace.data_ptr(), workspace.numel() * workspace.element_size())

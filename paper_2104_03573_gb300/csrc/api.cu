@@ -522,6 +522,8 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
     if (!gout->dkappa_dlogtau || !gout->dkappa_dp || (nd > 0 && !gout->dkappa_dir))
       return fail(MCBTE_ERR_INVALID_ARG, "grad: output pointers required");
     if (gout->on_host != out->on_host) return fail(MCBTE_ERR_INVALID_ARG, "grad: on_host must match");
+    if (gout->dp_estimator < 0 || gout->dp_estimator > 2)
+      return fail(MCBTE_ERR_INVALID_ARG, "grad: dp_estimator must be 0, 1 or 2");
   }
   const bool host_out = out->on_host != 0;
   const bool replay = grad && p->precision == MCBTE_FP32_TRACE;
@@ -580,6 +582,12 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   C.n_regs = p->n_regions;
   C.n_det = (uint32_t)n_det;
   C.regs = w.regs;
+  if (grad && geoms[0]->host.pore) {
+    // d kappa / d p_pore: the measure-valued estimator on request, and where
+    // the likelihood-ratio score is undefined
+    const double pp = geoms[0]->host.pore_p;
+    C.mvd = (gout->dp_estimator == 2 || (gout->dp_estimator == 0 && (pp <= 0.0 || pp >= 1.0))) ? 1 : 0;
+  }
   if (p->n_regions > 0) {
     const std::vector<DetRegion> rg =
         build_regions(p->n_regions, p->regions, p->region_grid, false, nullptr, geoms[0]->host.L);

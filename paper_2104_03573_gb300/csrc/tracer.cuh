@@ -55,6 +55,7 @@ struct RunCfg {
   // FP32 transient time windows: this launch takes the snapshots with index
   // < win_end; the first window emits, later ones resume saved particles
   int win_first, win_last, win_end;
+  int mvd;              // gradient: measure-valued d kappa / d p_pore (phantom traces)
 };
 
 // Transient detector region (Sec. 4.5): a closed axis-aligned cuboid split
@@ -557,6 +558,49 @@ struct TallyNone {
 // and relaxation period k (bin b_k): G[b_k] += A_k X - B_k with A_k the sum
 // of its scores and B_k the sum of score x tally-so-far; the dense pi_j part
 // is R pi_j with R = n_res X - sum of X at each resampling.
+//
+// Measure-valued alternative for the pore specularity: the weak derivative
+// of the Bernoulli(p) draw of Eq. specular is the difference of its two
+// branches.  In the nominal trace (phase 0) pore hit j of the particle takes
+// the choice with probability 1/j (reservoir draw: the 64-bit word of
+// sub-block 257 of its event is at most floor((2^64 - 1) / j)), so the chosen
+// hit is uniform over the K hits; the phantom trace (phase 1) is the same
+// particle from its emission with the chosen hit's branch flipped; the score
+// is K (X_spec - X_diff).
+struct MvdState {
+  uint32_t K;      // pore hits of this trace so far
+  uint32_t Kn;     // the nominal trace's K (phantom phase)
+  uint32_t sel;    // chosen hit (1-based), 0: none
+  bool sel_spec;   // the nominal branch at the chosen hit
+  bool phase;      // false: nominal trace, true: phantom trace
+
+  __device__ __forceinline__ void reset() {
+    K = Kn = sel = 0u;
+    sel_spec = false;
+    phase = false;
+  }
+  __device__ __forceinline__ bool branch(bool spec, uint4 ctr, uint32_t k0, uint32_t k1) {
+    ++K;
+    if (phase) return K == sel ? !spec : spec;
+    ctr.w = 257u;
+    const uint4 r = philox(ctr, k0, k1);
+    const unsigned long long v = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
+    if (v <= 0xFFFFFFFFFFFFFFFFull / (unsigned long long)K) {
+      sel = K;
+      sel_spec = spec;
+    }
+    return spec;
+  }
+  // the phantom trace starts; the nominal trace's K is kept
+  __device__ __forceinline__ void start_phantom() {
+    Kn = K;
+    K = 0u;
+    phase = true;
+  }
+  __device__ __forceinline__ double score(double X_nominal, double X_phantom) const {
+    return (double)Kn * (sel_spec ? X_nominal - X_phantom : X_phantom - X_nominal);
+  }
+};
 
 struct GradOff {
   static constexpr bool on = false;
@@ -564,7 +608,7 @@ struct GradOff {
   template <typename C>
   __device__ __forceinline__ void flight(bool, double, double, C) {}
   __device__ __forceinline__ void resampled(int, double) {}
-  __device__ __forceinline__ void pore_hit(bool, double, double) {}
+  __device__ __forceinline__ bool pore_branch(bool spec, double, double, uint4, uint32_t, uint32_t) { return spec; }
   __device__ __forceinline__ int periods() const { return 0; }
   __device__ __forceinline__ int period_bin(int) const { return 0; }
   __device__ __forceinline__ double period_value(int, double) const { return 0.0; }
@@ -583,8 +627,11 @@ struct GradList {
   int n_res;
   double sum_x_res;
   double PA, PB;
+  bool mvd;         // measure-valued d/dp (set by the kernel)
+  MvdState mv;
 
   __device__ __forceinline__ void init(int b) {
+    mv.reset();
     np = 1;
     bin[0] = b;
     A[0] = 0.0;
@@ -596,12 +643,14 @@ struct GradList {
   }
   // ratio = l / Lambda of the flight; Xb = tally before it
   __device__ __forceinline__ void flight(bool relax, double ratio, double Xb, double) {
+    if (mv.phase) return;
     double score = ratio;
     if (relax) score = score - 1.0;
     A[np - 1] += score;
     B[np - 1] += score * Xb;
   }
   __device__ __forceinline__ void resampled(int b, double Xnow) {
+    if (mv.phase) return;
     if (np < kMaxPeriods) {
       bin[np] = b;
       A[np] = -1.0;
@@ -611,10 +660,12 @@ struct GradList {
     n_res++;
     sum_x_res += Xnow;
   }
-  __device__ __forceinline__ void pore_hit(bool spec, double p, double Xnow) {
+  __device__ __forceinline__ bool pore_branch(bool spec, double p, double Xnow, uint4 ctr, uint32_t k0, uint32_t k1) {
+    if (mvd) return mv.branch(spec, ctr, k0, k1);
     const double sc = spec ? 1.0 / p : -1.0 / (1.0 - p);
     PA += sc;
     PB += sc * Xnow;
+    return spec;
   }
   __device__ __forceinline__ double period_value(int k, double X) const { return A[k] * X - B[k]; }
   __device__ __forceinline__ int periods() const { return np; }
@@ -641,8 +692,11 @@ struct GradReplay {
   int n_dirs, n_bins;
   const double* dirs;
   double dv[kMaxDirs];  // per direction: sum over closed periods of value x dirs[bin]
+  bool mvd;             // measure-valued d/dp (set by the kernel)
+  MvdState mv;
 
   __device__ __forceinline__ void init(int b) {
+    mv.reset();
     bin_cur = b;
     a = d = pa = pd = 0.0f;
     n_res = 0;
@@ -650,6 +704,7 @@ struct GradReplay {
     for (int k = 0; k < n_dirs; ++k) dv[k] = 0.0;
   }
   __device__ __forceinline__ void flight(bool relax, double ratio, double, float c) {
+    if (mv.phase) return;
     a += (float)ratio - (relax ? 1.0f : 0.0f);
     d = fmaf(a, c, d);
     pd = fmaf(pa, c, pd);
@@ -660,6 +715,7 @@ struct GradReplay {
     for (int k = 0; k < n_dirs; ++k) dv[k] += val * dirs[(size_t)k * n_bins + bin_cur];
   }
   __device__ __forceinline__ void resampled(int b, double Xnow) {
+    if (mv.phase) return;
     close_period(Xnow);
     bin_cur = b;
     a = -1.0f;
@@ -667,8 +723,10 @@ struct GradReplay {
     n_res++;
     sum_x_res += Xnow;
   }
-  __device__ __forceinline__ void pore_hit(bool spec, double p, double) {
+  __device__ __forceinline__ bool pore_branch(bool spec, double p, double, uint4 ctr, uint32_t k0, uint32_t k1) {
+    if (mvd) return mv.branch(spec, ctr, k0, k1);
     pa += spec ? (float)(1.0 / p) : (float)(-1.0 / (1.0 - p));
+    return spec;
   }
   __device__ __forceinline__ double resample_term(double X) const { return (double)n_res * X - sum_x_res; }
   __device__ __forceinline__ double spec_term(double) const { return (double)pd; }
@@ -769,7 +827,7 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
     nx = nx / len;
     ny = ny / len;
     spec = (uint64_t)w.x < g.pthr_pore;
-    if (Grad::on) gr.pore_hit(spec, g.p_pore, Xnow);
+    if (Grad::on) spec = gr.pore_branch(spec, g.p_pore, Xnow, ctr, k0, k1);
   }
   if (spec) {
     const R un = p.u[0] * nx + p.u[1] * ny;

@@ -38,9 +38,11 @@ __device__ __forceinline__ void grad_finish(const Grad& gr, double X, int g, con
   for (int k = 0; k < np; ++k) atomicAdd(&A.G[gr.period_bin(k)], gr.period_value(k, X));
   const double Rv = gr.resample_term(X);
   atomicAdd(&A.dsc[g * 8 + 4], Rv);
-  const double gp = gr.spec_term(X);
-  atomicAdd(&A.dsc[g * 8 + 5], gp);
-  atomicAdd(&A.dsc[g * 8 + 6], gp * gp);
+  if (!C.mvd) {   // the measure-valued score is added after the phantom trace
+    const double gp = gr.spec_term(X);
+    atomicAdd(&A.dsc[g * 8 + 5], gp);
+    atomicAdd(&A.dsc[g * 8 + 6], gp * gp);
+  }
   for (int kd = 0; kd < C.n_dirs; ++kd) {
     const double* dd = C.dirs + (size_t)kd * M.n;
     double val = 0.0;
@@ -76,6 +78,7 @@ __global__ void __launch_bounds__(256) k_steady_fp64(const GeoRun* __restrict__ 
   }
   emit<double>(p, G, M, M.rec_emit, M.rec_init, nullptr, key.x, key.y, false, 0.0);
   typename GradPick<GRAD, GradList>::type gr;
+  if constexpr (GRAD) gr.mvd = C.mvd != 0;
   if (GRAD) gr.init(p.bin);
   TallyPlain T;
   T.cP = CELLS ? A.cellP + (size_t)g * C.n_cells * 4 : nullptr;
@@ -111,7 +114,35 @@ __global__ void __launch_bounds__(256) k_steady_fp64(const GeoRun* __restrict__ 
   }
   if (A.events_pp) A.events_pp[idx] = (uint32_t)nev;
   if (A.X_pp) A.X_pp[idx] = p.X;
-  if (GRAD) grad_finish(gr, p.X, g, C, A, M);
+  if constexpr (GRAD) {
+    grad_finish(gr, p.X, g, C, A, M);
+    if (C.mvd && gr.mv.sel > 0u) {
+      // measure-valued d/dp_pore: the particle again from its emission, the
+      // chosen pore hit's branch flipped; nothing is tallied but its X
+      const double Xn = p.X;
+      gr.mv.start_phantom();
+      emit<double>(p, G, M, M.rec_emit, M.rec_init, nullptr, key.x, key.y, false, 0.0);
+      TallyPlain Tq;
+      Tq.cP = nullptr;
+      Tq.qb = nullptr;
+      Tq.nc = C.n_cells;
+      Tq.ca = C.cell_axis;
+      Tq.ta = C.tally_axis;
+      Tq.h = 1.0;
+      Tq.det = nullptr;
+      for (;;) {
+        const int o = step_steady<double, GradList, TallyPlain>(p, G, M, M.rec_relax, nullptr, C, key.x, key.y, Tq, gr);
+        if (o != STEP_ALIVE) break;
+        if ((p.e & 1023u) == 0u && globaltimer_ns() > deadline) {
+          atomicOr(A.flags, 1);
+          break;
+        }
+      }
+      const double D = gr.mv.score(Xn, p.X);
+      atomicAdd(&A.dsc[g * 8 + 5], D);
+      atomicAdd(&A.dsc[g * 8 + 6], D * D);
+    }
+  }
 }
 #endif  // MCBTE_F64
 
@@ -158,9 +189,11 @@ __device__ __forceinline__ void grad_finish_replay(GradReplay& gr, double X, int
   gr.close_period(X);
   const double Rv = gr.resample_term(X);
   atomicAdd(&A.dsc[g * 8 + 4], Rv);
-  const double gp = gr.spec_term(X);
-  atomicAdd(&A.dsc[g * 8 + 5], gp);
-  atomicAdd(&A.dsc[g * 8 + 6], gp * gp);
+  if (!C.mvd) {   // the measure-valued score is added after the phantom trace
+    const double gp = gr.spec_term(X);
+    atomicAdd(&A.dsc[g * 8 + 5], gp);
+    atomicAdd(&A.dsc[g * 8 + 6], gp * gp);
+  }
   for (int kd = 0; kd < C.n_dirs; ++kd) {
     const double val = gr.dv[kd] + Rv * C.dpi[kd];
     atomicAdd(&A.dsum[kd * 2 + 0], val);
@@ -176,7 +209,9 @@ __device__ __forceinline__ void grad_finish_replay(GradReplay& gr, double X, int
 // TPB is the block size the kernel is compiled for (register budget).
 // GRAD: the gradient pass, which replays the forward pass's particles with
 // their final tallies read from A.X_pp; it writes the gradient accumulators
-// only, and flags (bit 2) any particle whose replayed tally differs.
+// only, and flags (bit 2) any particle whose replayed tally differs.  With
+// the measure-valued d/dp_pore the lane then traces the same particle once
+// more (phantom phase, the chosen pore hit flipped) before it refills.
 // CELLS: 0 no cell tallies, 1 T and three flux components, 2 T and the
 // tally-axis flux only.
 template <int CELLS, bool GRAD, int TPB, bool EXT>
@@ -225,6 +260,7 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
     gr.n_dirs = C.n_dirs;
     gr.n_bins = n;
     gr.dirs = C.dirs;
+    gr.mvd = C.mvd != 0;
   }
   ThreadAcct acct;
   acct.reset(-1);
@@ -300,8 +336,23 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
     if (GRAD && out != STEP_ALIVE) {
       const double X = T.X(p);
       if constexpr (GRAD) {
-        if (X != gr.Xf) atomicOr(A.flags, 4);
-        grad_finish_replay(gr, X, p.g, C, A);
+        if (!gr.mv.phase) {
+          if (X != gr.Xf) atomicOr(A.flags, 4);
+          grad_finish_replay(gr, X, p.g, C, A);
+          if (C.mvd && gr.mv.sel > 0u) {
+            // measure-valued d/dp_pore: the same particle again from its
+            // emission, the chosen pore hit's branch flipped (Xf keeps the
+            // nominal tally)
+            gr.Xf = X;
+            gr.mv.start_phantom();
+            emit<float, EXT>(p, *G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, false, 0.0f);
+            continue;
+          }
+        } else {
+          const double D = gr.mv.score(gr.Xf, X);
+          atomicAdd(&A.dsc[p.g * 8 + 5], D);
+          atomicAdd(&A.dsc[p.g * 8 + 6], D * D);
+        }
       }
       alive = false;
     } else if (out != STEP_ALIVE) {
@@ -434,7 +485,7 @@ __global__ void k_finalize_steady(const GeoRun* geos, MatView M, RunCfg C, Acc A
       const double nt = (double)A.cnt[3];
       const double gm = A.dsc[5] / nt;
       const double gv = (A.dsc[6] - nt * gm * gm) / fmax(nt - 1.0, 1.0);
-      const bool ok = G.pore && G.p_pore > 0.0 && G.p_pore < 1.0;
+      const bool ok = G.pore && (C.mvd || (G.p_pore > 0.0 && G.p_pore < 1.0));
       const double nan = __longlong_as_double(0x7ff8000000000000ll);
       O.dkp[0] = ok ? scale * A.dsc[5] : nan;
       O.dkp[1] = ok ? fabs(scale) * sqrt(fmax(gv, 0.0) * nt) : nan;

@@ -548,3 +548,55 @@ def test_fp32_gradient_directional_vs_oracle():
         assert abs(gd[k, 0] - ref["dkappa_dir"][k]) < 4 * se
     gp = go.dkappa_dp.cpu().numpy()
     assert abs(gp[0] - ref["dkappa_dp"]) < 4 * np.hypot(gp[1], ref["dkappa_dp_se"])
+
+
+@pytest.mark.parametrize("p_pore,est", [(0.0, L.DP_AUTO), (0.3, L.DP_MEASURE_VALUED), (1.0, L.DP_AUTO)])
+def test_fp64_measure_valued_specularity_gradient_matches_oracle(p_pore, est):
+    wl = W.pore_film_c5(n=4000, p_pore=p_pore)
+    mat, g, run = wl.material, wl.geometries[0], wl.run
+    run.max_events = 2_000_000
+    M, G = api.Material(mat), api.Geometry(g)
+    cfg = api.SteadyConfig(seed=run.seed, precision=L.FP64_PLAIN, n_scat_max=run.n_scat_max,
+                           max_events=run.max_events, tally_axis=run.tally_axis, per_bin=True)
+    fwd, go = api.grad(M, G, run.n, cfg, dp_estimator=est)
+    torch.cuda.synchronize()
+    ref = oracle.run_steady(mat, g, run, grad=True, dp_estimator=est)
+    dp = go.dkappa_dp.cpu().numpy()
+    assert dp[0] == pytest.approx(ref["dkappa_dp"], rel=1e-9)
+    assert dp[1] == pytest.approx(ref["dkappa_dp_se"], rel=1e-9)
+    # the phantom traces change neither the forward tallies nor the tau gradient
+    ok, err = rel_close(go.dkappa_dlogtau.cpu().numpy(), ref["dkappa_dlogtau"], RTOL)
+    assert ok, err
+    assert fwd.stats[0, L.STAT_KAPPA].item() == pytest.approx(ref["kappa"], rel=RTOL)
+    assert fwd.stats[0, L.STAT_EVENTS].item() == ref["events"]
+    if p_pore in (0.0, 1.0):
+        # the likelihood ratio is undefined there: NaN on request
+        _, gl = api.grad(M, G, run.n, cfg, dp_estimator=L.DP_LIKELIHOOD_RATIO)
+        torch.cuda.synchronize()
+        assert np.isnan(gl.dkappa_dp.cpu().numpy()).all()
+
+
+def test_fp32_measure_valued_specularity_gradient_vs_oracle():
+    wl = W.pore_film_c5(n=100_000, p_pore=0.0)
+    mat, g, run = wl.material, wl.geometries[0], wl.run
+    run.max_events = 20_000_000
+    M, G = api.Material(mat), api.Geometry(g)
+    cfg = api.SteadyConfig(seed=810, precision=L.FP32_TRACE, n_scat_max=run.n_scat_max,
+                           max_events=run.max_events, tally_axis=run.tally_axis, per_bin=True)
+    fwd, go = api.grad(M, G, run.n, cfg)
+    torch.cuda.synchronize()
+    assert fwd.stats[0, L.STAT_STATUS].item() == 0      # no replay mismatch, no truncation
+    run.seed = 811
+    ref = oracle.run_steady(mat, g, run, grad=True)     # measure-valued at p = 0
+    gp = go.dkappa_dp.cpu().numpy()
+    assert np.isfinite(gp).all() and gp[1] > 0
+    assert abs(gp[0] - ref["dkappa_dp"]) < 4 * np.hypot(gp[1], ref["dkappa_dp_se"])
+
+
+def test_grad_rejects_unknown_dp_estimator():
+    wl = W.pore_film_c5(n=100)
+    M, G = api.Material(wl.material), api.Geometry(wl.geometries[0])
+    cfg = api.SteadyConfig(seed=1, precision=L.FP64_PLAIN, n_scat_max=4, tally_axis=1)
+    with pytest.raises(L.MCBTEError) as e:
+        api.grad(M, G, 100, cfg, dp_estimator=3)
+    assert e.value.status == L.ERR_INVALID_ARG
