@@ -53,7 +53,7 @@ class _Params(C.Structure):
         ("n_cells", C.c_int), ("cell_axis", C.c_int), ("tally_axis", C.c_int),
         ("t_max", C.c_double), ("n_times", C.c_int), ("t_meas", C.c_void_p), ("grid", C.c_int * 3),
         ("n_regions", C.c_int), ("regions", C.c_void_p), ("region_grid", C.c_void_p), ("time_average", C.c_int),
-        ("want_grad", C.c_int), ("dp_mvd", C.c_int), ("n_dirs", C.c_int), ("dirs", C.c_void_p), ("n_threads", C.c_int),
+        ("nscat_curve", C.c_int), ("want_grad", C.c_int), ("dp_mvd", C.c_int), ("n_dirs", C.c_int), ("dirs", C.c_void_p), ("n_threads", C.c_int),
     ]
 
 
@@ -61,7 +61,7 @@ class _Out(C.Structure):
     _fields_ = [
         ("T_sum", C.c_void_p), ("Q_sum", C.c_void_p), ("qbin_sum", C.c_void_p), ("snap", C.c_void_p),
         ("events_pp", C.c_void_p), ("X_pp", C.c_void_p), ("G", C.c_void_p),
-        ("dir_sum", C.c_void_p), ("dir_sum2", C.c_void_p), ("scal", C.c_double * 16),
+        ("dir_sum", C.c_void_p), ("dir_sum2", C.c_void_p), ("curve", C.c_void_p), ("scal", C.c_double * 16),
     ]
 
 
@@ -286,14 +286,16 @@ def dp_mvd(geom, dp_estimator: int = 0) -> bool:
 def run_steady(material, geom, run, *, pid_begin: int = 0, pid_end: Optional[int] = None,
                per_particle: bool = False, grad: bool = False, dirs: Optional[np.ndarray] = None,
                n_threads: int = 0, batch_index: int = 0, n_total: Optional[int] = None,
-               dp_estimator: int = 0) -> dict:
+               dp_estimator: int = 0, nscat_curve: bool = False) -> dict:
     """Trace particles [pid_begin, pid_end) of a steady run of N = run.n (or
     n_total) particles and return raw sums plus the physical tallies.
 
     dp_estimator selects the estimator of d kappa / d p_pore when grad is set:
     1 the likelihood ratio of the specular / diffuse draw, 2 the measure-valued
     one (each particle's phantom trace with one pore hit's branch flipped),
-    0 the likelihood ratio for 0 < p < 1 and the measure-valued one at p = 0, 1."""
+    0 the likelihood ratio for 0 < p < 1 and the measure-valued one at p = 0, 1.
+    nscat_curve adds "kappa_nscat" [n_scat_max][2]: kappa and its standard
+    error for every N_scat_max' = 1..n_scat_max, from the same trajectories."""
     N = int(n_total if n_total is not None else run.n)
     pe = N if pid_end is None else int(pid_end)
     keep = _Keep()
@@ -305,7 +307,7 @@ def run_steady(material, geom, run, *, pid_begin: int = 0, pid_end: Optional[int
                 n_particles=N, pid_begin=int(pid_begin), pid_end=pe, n_scat_max=int(run.n_scat_max),
                 max_events=int(run.max_events), n_cells=int(run.n_cells), cell_axis=int(run.cell_axis),
                 tally_axis=int(run.tally_axis), want_grad=int(grad),
-                dp_mvd=int(bool(grad) and dp_mvd(geom, dp_estimator)),
+                dp_mvd=int(bool(grad) and dp_mvd(geom, dp_estimator)), nscat_curve=int(bool(nscat_curve)),
                 n_dirs=0 if dirs_a is None else dirs_a.shape[0],
                 dirs=_ptr(dirs_a), n_threads=int(n_threads))
     npp = pe - int(pid_begin)
@@ -323,6 +325,8 @@ def run_steady(material, geom, run, *, pid_begin: int = 0, pid_end: Optional[int
     O.events_pp = _ptr(ev); O.X_pp = _ptr(Xp); O.G = _ptr(G)
     O.dir_sum = ds.ctypes.data if nd else None
     O.dir_sum2 = ds2.ctypes.data if nd else None
+    curve = np.zeros((max(int(run.n_scat_max), 1), 2)) if nscat_curve else None
+    O.curve = _ptr(curve)
     regions = list(getattr(run, "regions", ()) or ())
     det = None
     if regions:
@@ -364,6 +368,13 @@ def run_steady(material, geom, run, *, pid_begin: int = 0, pid_end: Optional[int
     r["kappa"] = -r["q_mean"] / gk
     r["kappa_se"] = r["q_se"] / abs(gk)
     r["kappa_cell"] = r["kappa"] * V / Vbox
+    if nscat_curve:
+        cm = curve[:, 0] / npp
+        cv = (curve[:, 1] - npp * cm * cm) / max(npp - 1, 1)
+        r["raw_curve"] = curve
+        r["kappa_nscat"] = np.stack([-((E_eff / V) * curve[:, 0] * 1e-9) / gk,
+                                     (E_tot / V) * 1e-9 * np.sqrt(np.maximum(cv, 0.0) / npp) * (npp / N) / abs(gk)],
+                                    axis=1)
     r["events"] = sc[EVENTS]
     r["truncated"] = sc[TRUNC]
     r["E_tot"] = E_tot

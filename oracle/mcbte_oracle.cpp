@@ -19,6 +19,7 @@
 //   - isothermal wall absorbs; periodic wall translates                   Secs. 3.5.4, 3.5.5 (Eq. periodic_lin_final)
 //   - termination: absorbed, t > t_max, or N_scat_max relaxations         Sec. 3.5.6
 //   - steady track-length tallies                                         Eqs. steady_estimate, temp_steady, flux_x_steady
+//   - N_scat_max convergence curve: X_p of every smaller N_scat_max       Sec. 3.5.6 (the study of N_scat_max)
 //   - transient snapshot tallies                                          Eq. sampling, Sec. 3.4
 //   - likelihood-ratio scores for d/d(log tau_i) and d/dp (no counterpart in the paper; derived
 //     from the exponential law of Eq. time_to_scat and the discrete draws of Eq. n_scatt / Eq. specular)
@@ -264,6 +265,7 @@ typedef struct {
   const double* regions;      // [n_regions][6] xmin, xmax, ymin, ymax, zmin, zmax (m)
   const int* region_grid;     // [n_regions][3]
   int time_average;           // 0: snapshots at t_m (Eq. sampling); 1: averages over [t_{m-1}, t_m)
+  int nscat_curve;            // 1: X sums for every N_scat_max' = 1..n_scat_max (steady)
   int want_grad;
   int dp_mvd;                 // 1: d kappa / d p_pore by the measure-valued estimator
   int n_dirs;
@@ -286,6 +288,7 @@ typedef struct {
   double* G;            // [n_bins]  sum over particles of the sparse LR part
   double* dir_sum;      // [n_dirs]
   double* dir_sum2;     // [n_dirs]
+  double* curve;        // [n_scat_max][2]  sum X_p(k), sum X_p(k)^2 for N_scat_max = k (nscat_curve)
   double scal[16];
 } or_out;
 
@@ -678,7 +681,7 @@ void region_track(const Setup::Region& r, const double x0[3], const double w[3],
 }
 
 struct Partial {
-  std::vector<double> T, Q, qbin, snap, G, dsum, dsum2;
+  std::vector<double> T, Q, qbin, snap, G, dsum, dsum2, curve;
   double scal[OR_NSCAL] = {0};
 };
 
@@ -697,6 +700,7 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
   const bool cells = P->n_cells > 0 && !P->transient;
   const double h_cell = cells ? g.L[P->cell_axis] / (double)P->n_cells : 0.0;
   std::vector<Period> periods;
+  std::vector<double> x_relax;   // X at each relaxation event (N_scat_max curve)
   // tallies of phantom traces (discarded)
   Partial scratch;
   if (P->dp_mvd) scratch = res;
@@ -802,6 +806,7 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
     int n_res = 0;
     double sum_x_res = 0.0;
     double PA = 0.0, PB = 0.0;
+    x_relax.clear();
     size_t mi = 0;
     if (P->transient) {
       if (P->time_average) { while (mi < S.t_meas_ps.size() && S.t_meas_ps[mi] <= t_now) ++mi; }
@@ -951,6 +956,7 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
       ++e;
       if (relax) {
         ++n_relax;
+        if (P->nscat_curve) x_relax.push_back(X);
         if (P->n_scat_max > 0 && n_relax >= P->n_scat_max) break;
         ctr[2] = e;
         ctr[3] = 0; philox4x32_10(ctr, k0, k1, w);
@@ -1072,6 +1078,16 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
     out.scal[OR_SUMX] += X;
     out.scal[OR_SUMX2] += X * X;
     if (flip) return X;
+    if (P->nscat_curve) {
+      // a run with N_scat_max = k ends this trajectory at its k-th
+      // relaxation (Sec. 3.5.6) with the tally it had there; a trajectory
+      // that ended earlier is the same in that run
+      for (int k = 1; k <= P->n_scat_max; ++k) {
+        const double Xk = (size_t)k <= x_relax.size() ? x_relax[(size_t)k - 1] : X;
+        out.curve[2 * (size_t)(k - 1) + 0] += Xk;
+        out.curve[2 * (size_t)(k - 1) + 1] += Xk * Xk;
+      }
+    }
     if (O->events_pp) O->events_pp[pid - P->pid_begin] = (uint32_t)std::min<uint64_t>(nev, 0xFFFFFFFFu);
     if (O->X_pp) O->X_pp[pid - P->pid_begin] = X;
     if (P->want_grad) {
@@ -1215,6 +1231,7 @@ int or_run(const or_params* P, or_out* O) {
   if (rc) return 10 + rc;
   if (P->transient && (P->grid[0] < 1 || P->grid[1] < 1 || P->grid[2] < 1)) return 20;
   if (P->want_grad && P->transient) return 21;
+  if (P->nscat_curve && (P->transient || P->n_scat_max < 1 || !O->curve)) return 22;
   const uint64_t total = P->pid_end - P->pid_begin;
   int nt = P->n_threads > 0 ? P->n_threads : (int)std::thread::hardware_concurrency();
   if (nt < 1) nt = 1;
@@ -1227,6 +1244,7 @@ int or_run(const or_params* P, or_out* O) {
     if (P->transient) p.snap.assign((size_t)P->n_times * ncell_t * 4, 0.0);
     else if (P->n_regions > 0) p.snap.assign(ncell_t * 4, 0.0);     // steady detector regions
     if (P->want_grad) { p.G.assign(P->n_bins, 0.0); p.dsum.assign(P->n_dirs, 0.0); p.dsum2.assign(P->n_dirs, 0.0); }
+    if (P->nscat_curve) p.curve.assign(2 * (size_t)P->n_scat_max, 0.0);
   }
   std::vector<std::thread> th;
   for (int i = 0; i < nt; ++i) {
@@ -1248,6 +1266,7 @@ int or_run(const or_params* P, or_out* O) {
     if (O->snap) for (size_t c = 0; c < p.snap.size(); ++c) O->snap[c] += p.snap[c];
     if (O->G) for (size_t c = 0; c < p.G.size(); ++c) O->G[c] += p.G[c];
     if (O->dir_sum) for (size_t c = 0; c < p.dsum.size(); ++c) { O->dir_sum[c] += p.dsum[c]; O->dir_sum2[c] += p.dsum2[c]; }
+    if (O->curve) for (size_t c = 0; c < p.curve.size(); ++c) O->curve[c] += p.curve[c];
   }
   O->scal[OR_ETOT] = S.E_tot;
   O->scal[OR_CTOT] = t.C_tot;
