@@ -19,6 +19,9 @@ Other workloads (`--workload`), same line format:
   pore_grad      nanoporous film, 5e7 particles, forward + likelihood-ratio
                  gradient over 3000 log-tau scales + measure-valued derivative
                  in the pore specularity at p = 0
+  pore_nscat     nanoporous cell without symmetry (off-centre pore, diagonal
+                 control gradient), 1e7 particles, kappa for every
+                 N_scat_max = 1..32 from one run (convergence study)
 
 `--impl reference` times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload.  Multi-GPU (torchrun): every rank traces its own
@@ -50,7 +53,8 @@ WORKLOADS = {"si_slab": "si_slab_L1um_3000bins", "si_slab_imp": "si_slab_L1um_30
              "transient_box": "transient_box_2x2x1um_gauss",
              "transient_box_avg": "transient_box_2x2x1um_gauss_bin_averages",
              "nanomesh": "nanomesh_W34nm_pore11nm_t22nm_timp",
-             "film_batch": "film_batch_64_10nm_10um", "pore_grad": "pore_film_W100nm_phi0.25_t200nm_grad"}
+             "film_batch": "film_batch_64_10nm_10um", "pore_grad": "pore_film_W100nm_phi0.25_t200nm_grad",
+             "pore_nscat": "pore_skew_W100nm_phi0.25_t200nm_nscat_curve_1_32"}
 # Algorithmic thread-instructions per event of the tracer (one Philox4x32-10
 # call, log + sqrt + sincos, six-plane first hit, alias draw, state update and
 # tallies); the issue-rate roofline is SMs x 4 x 32 lanes x f_clk / this.
@@ -237,6 +241,39 @@ def _workload_setup(name, args, seed_offset):
                     desc=desc, launches=3, timer=tm, kernel="k_steady_f32 (nanomesh)",
                     shape={"threads_per_block": cfg.threads_per_block, "refill_threshold": cfg.refill_threshold},
                     kappa=True, kind="steady")
+    if name == "pore_nscat":
+        n = args.n_particles or 10_000_000
+        mat, geo = W.bvk_holland(), W.pore_skew()
+        run = W.SteadyRun(n=n, seed=1007 + seed_offset, tally_axis=1, per_bin=True, n_scat_max=32)
+        M, G = api.Material(mat), api.Geometry(geo)
+        cfg = api.SteadyConfig(seed=run.seed, precision=L.FP32_TRACE, tally_axis=1, per_bin=True, n_scat_max=32,
+                               max_events=10 ** 9, threads_per_block=args.threads, refill_threshold=args.refill,
+                               time_budget_s=300, nscat_curve=True)
+        if args.threads == 0 and not args.no_autotune:
+            cfg = autotune.tune(M, [G], [n], cfg)
+        cfg = replace(cfg, trace_events=ev)
+        out = api.SteadyOutputs(1, M.n_bins, 0, True, nscat=32)
+
+        def step():
+            api.run_steady(M, [G], [n], cfg, out=out)
+            return lambda: out.stats.cpu().numpy()
+
+        def fp64(n64):
+            c = replace(cfg, precision=L.FP64_PLAIN, threads_per_block=0, refill_threshold=0)
+            o = api.SteadyOutputs(1, M.n_bins, 0, True, nscat=32)
+            return lambda: (api.run_steady(M, [G], [n64], c, out=o), (lambda: o.stats.cpu().numpy()))[1]
+
+        def e2e():
+            Mh, Gh = api.Material(mat), api.Geometry(geo)
+            return api.run_steady_host(Mh, [Gh], [n], replace(cfg, trace_events=None))["stats"]
+        desc = ("nanoporous cell without symmetry: 100 nm cell, cylindrical pore porosity 0.25 centred at "
+                "(30, 62) nm, 200 nm thick, diffuse walls, periodic x,y, grad_T (-0.5, -1, 0) x 1e6 K/m, "
+                "BvK 3x1000 bins + Holland tau; kappa and its SE for every N_scat_max = 1..32 from one run")
+        return dict(mat=mat, geo=geo, run=run, n=n, step=step, fp64=fp64, e2e=e2e, curve=out,
+                    d2h=8 * (M.n_bins + L.NSTATS + 64), h2d=_material_bytes(mat) + ctypes.sizeof(L.GeometryDesc) + 8,
+                    desc=desc, launches=3, timer=tm, kernel="k_steady_f32 (N_scat_max curve)",
+                    shape={"threads_per_block": cfg.threads_per_block, "refill_threshold": cfg.refill_threshold},
+                    kappa=True, kind="steady")
     if name == "pore_grad":
         wl = W.pore_film_c5(n=args.n_particles or 50_000_000)
         mat, geo, run = wl.material, wl.geometries[0], wl.run
@@ -408,6 +445,14 @@ def run_ours(args):
             kappa, kse = pooled["kappa"], pooled["kappa_se"]
         t_1pct = float(t_step * np.max((se / np.abs(k) / 0.01) ** 2))
     dkdp = [float(x) for x in wk["gout"].dkappa_dp.cpu().numpy()] if "gout" in wk else None
+    curve = None
+    if "curve" in wk:
+        kn = wk["curve"].kappa_nscat[0].cpu().numpy()
+        kfin, sfin = kn[-1]
+        # the smallest N_scat_max whose kappa is within two standard errors of the largest one's
+        conv = next(k + 1 for k in range(len(kn)) if abs(kn[k, 0] - kfin) <= 2.0 * np.hypot(kn[k, 1], sfin))
+        curve = {"n_scat_max": [1, 2, 4, 8, 16, 32], "kappa": [float(kn[k - 1, 0]) for k in (1, 2, 4, 8, 16, 32)],
+                 "kappa_se": [float(kn[k - 1, 1]) for k in (1, 2, 4, 8, 16, 32)], "converged_at": int(conv)}
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -461,6 +506,7 @@ def run_ours(args):
         "s_to_1pct_se_kappa": t_1pct, "kappa_eff": kappa, "kappa_se": kse,
         "events_per_step": ev_step, "wall_s": wall_max,
         **({"dkappa_dp_pore": dkdp} if dkdp is not None else {}),
+        **({"kappa_nscat": curve} if curve is not None else {}),
         "fp64_plain": fp64,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
                      "frac": achieved / peak_tinst,
@@ -512,7 +558,7 @@ def cpu_baseline(wk, args, target_s=None):
     else:
         def go(n):
             r = replace(run, n=n)
-            return oracle.run_steady(mat, wk["geo"], r, grad=(kind == "grad"))
+            return oracle.run_steady(mat, wk["geo"], r, grad=(kind == "grad"), nscat_curve="curve" in wk)
         probe_n = 50_000
         cores = os.cpu_count()
     t0 = time.perf_counter()

@@ -40,6 +40,10 @@ typedef struct CUstream_st* mcbte_stream; /* == cudaStream_t */
  * in shared memory (4 bytes each). */
 #define MCBTE_MAX_TIMES 16384
 
+/* Largest n_scat_max of a run that returns the N_scat_max convergence curve
+ * (Sec. 3.5.6 leaves N_scat_max to a convergence study). */
+#define MCBTE_MAX_NSCAT_CURVE 4096
+
 /* Largest number of detector regions of a run (Sec. 4.5). */
 #define MCBTE_MAX_REGIONS 16
 
@@ -218,6 +222,9 @@ typedef struct {
   const double* regions;       /* HOST [n_regions][6] xmin, xmax, ymin, ymax, zmin, zmax (m)  */
   const int* region_grid;      /* HOST [n_regions][3] detectors per axis (half-open cuboids
                                   [min, max), closed on the box's upper faces)              */
+  int nscat_curve;             /* 1: also kappa for every N_scat_max' = 1..n_scat_max from the
+                                  same trajectories (mcbte_steady_out.kappa_nscat); needs
+                                  1 <= n_scat_max <= MCBTE_MAX_NSCAT_CURVE; not with mcbte_grad */
 } mcbte_steady_params;
 
 typedef struct {
@@ -231,6 +238,8 @@ typedef struct {
   double* det;          /* [n_detectors][4] T - T_eq (K), q_x, q_y, q_z (W/m^2) per detector of
                            the regions (track length in each, Eqs. temp_steady, flux_x_steady),
                            detectors region by region, x fastest; or NULL                */
+  double* kappa_nscat;  /* [n_geoms][n_scat_max][2] kappa (W/m/K) and its standard error with
+                           N_scat_max' = k + 1 at index k (required with nscat_curve)       */
 } mcbte_steady_out;
 
 /* Device scratch a run needs.  Pass a buffer at least this large (256-byte

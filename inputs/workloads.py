@@ -152,6 +152,16 @@ def pore_lattice(W: float, porosity: float, thickness: float, p_pore: float = 0.
     return g
 
 
+def pore_skew(W: float = 100e-9, porosity: float = 0.25, thickness: float = 200e-9) -> Geometry:
+    """Nanoporous cell without symmetry: the pore off centre at (0.3 W, 0.62 W)
+    and the control gradient along (-0.5, -1, 0) x 1e6 K/m, diagonal in the
+    film plane."""
+    g = pore_lattice(W, porosity, thickness)
+    g.pore_c = (0.3 * W, 0.62 * W)
+    g.grad_T = (-0.5e6, -1.0e6, 0.0)
+    return g
+
+
 def nanomesh(W: float = 34e-9, pore: float = 11e-9, thickness: float = 22e-9, p_pore: float = 0.0,
              p_faces: float = 0.0, grad_y: float = -1.0e6, T_eq: float = 300.0) -> Geometry:
     """Square-pore nanomesh unit cell of Sec. 5.5: W x W, periodic in x and y,

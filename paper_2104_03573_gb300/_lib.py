@@ -48,12 +48,14 @@ class SteadyParams(C.Structure):
                 ("threads_per_block", C.c_int), ("blocks_per_sm", C.c_int), ("time_budget_s", C.c_double),
                 ("trace_event_start", C.c_void_p), ("trace_event_stop", C.c_void_p),
                 ("seed_device", C.c_void_p), ("refill_threshold", C.c_int), ("cell_flux_axis", C.c_int),
-                ("n_regions", C.c_int), ("regions", C.c_void_p), ("region_grid", C.c_void_p)]
+                ("n_regions", C.c_int), ("regions", C.c_void_p), ("region_grid", C.c_void_p),
+                ("nscat_curve", C.c_int)]
 
 
 class SteadyOut(C.Structure):
     _fields_ = [("T", C.c_void_p), ("q", C.c_void_p), ("q_bin", C.c_void_p), ("stats", C.c_void_p),
-                ("events_pp", C.c_void_p), ("X_pp", C.c_void_p), ("on_host", C.c_int), ("det", C.c_void_p)]
+                ("events_pp", C.c_void_p), ("X_pp", C.c_void_p), ("on_host", C.c_int), ("det", C.c_void_p),
+                ("kappa_nscat", C.c_void_p)]
 
 
 class TransientParams(C.Structure):

@@ -138,6 +138,7 @@ class SteadyConfig:
     refill_threshold: int = 0
     cell_flux_axis: bool = False             # FP32 cell tallies: T and the tally-axis flux only
     regions: Sequence = ()                   # detector regions ((xmin..zmax) m, (nx, ny, nz)), one geometry
+    nscat_curve: bool = False                # also kappa for every N_scat_max' <= n_scat_max (kappa_nscat)
 
 
 def _event_handles(pair):
@@ -167,6 +168,7 @@ def steady_params(cfg: SteadyConfig, n_particles: np.ndarray) -> "L.SteadyParams
     p.seed_device = None if cfg.seed_device is None else cfg.seed_device.data_ptr()
     p.refill_threshold = int(cfg.refill_threshold)
     p.cell_flux_axis = int(bool(cfg.cell_flux_axis))
+    p.nscat_curve = int(bool(cfg.nscat_curve))
     regions = list(cfg.regions or ())
     if regions:
         boxes = np.ascontiguousarray([r[0] for r in regions], dtype=np.float64)
@@ -180,7 +182,7 @@ class SteadyOutputs:
     """Caller-owned device outputs of a steady run (torch tensors)."""
 
     def __init__(self, n_geoms: int, n_bins: int, n_cells: int, per_bin: bool, total: int = 0,
-                 per_particle: bool = False, device=None, regions: Sequence = ()):
+                 per_particle: bool = False, device=None, regions: Sequence = (), nscat: int = 0):
         import torch
         dev = device or torch.device("cuda")
         f = dict(dtype=torch.float64, device=dev)
@@ -192,12 +194,15 @@ class SteadyOutputs:
         self.stats = torch.zeros(n_geoms, L.NSTATS, **f)
         self.events_pp = torch.zeros(total, dtype=torch.int32, device=dev) if per_particle else None
         self.X_pp = torch.zeros(total, **f) if per_particle else None
+        # kappa and its SE for N_scat_max = k + 1 at [g, k]
+        self.kappa_nscat = torch.zeros(n_geoms, nscat, 2, **f) if nscat > 0 else None
 
     def struct(self) -> "L.SteadyOut":
         o = L.SteadyOut()
         o.T, o.q, o.q_bin, o.stats = _ptr(self.T), _ptr(self.q), _ptr(self.q_bin), _ptr(self.stats)
         o.events_pp, o.X_pp = _ptr(self.events_pp), _ptr(self.X_pp)
         o.det = _ptr(self.det)
+        o.kappa_nscat = _ptr(self.kappa_nscat)
         o.on_host = 0
         return o
 
@@ -226,7 +231,7 @@ def run_steady(material: Material, geoms: Sequence[Geometry], n_particles, cfg: 
     n = np.ascontiguousarray(np.asarray(n_particles, dtype=np.uint64))
     if out is None:
         out = SteadyOutputs(len(geoms), material.n_bins, cfg.n_cells, cfg.per_bin, int(n.sum()), per_particle,
-                            regions=cfg.regions)
+                            regions=cfg.regions, nscat=cfg.n_scat_max if cfg.nscat_curve else 0)
     p = steady_params(cfg, n)
     o = out.struct()
     ws_ptr, ws_bytes = (None, 0) if workspace is None else (workspace.data_ptr(), workspace.numel() * workspace.element_size())
@@ -264,6 +269,9 @@ def run_steady_host(material: Material, geoms: Sequence[Geometry], n_particles, 
     o.T = res["T"].ctypes.data if nc > 0 else None
     o.q = res["q"].ctypes.data if nc > 0 else None
     o.q_bin = res["q_bin"].ctypes.data if cfg.per_bin else None
+    if cfg.nscat_curve:
+        res["kappa_nscat"] = np.zeros((G, int(cfg.n_scat_max), 2))
+        o.kappa_nscat = res["kappa_nscat"].ctypes.data
     o.on_host = 1
     p = steady_params(cfg, n)
     st = L.load().mcbte_run_steady(material.handle, _handles(geoms), G, C.byref(p), C.byref(o), None, 0, None)

@@ -34,7 +34,8 @@ class GraphBatch:
         self.cfg = replace(cfg, seed_device=self.seed)
         ws = api.steady_workspace_size(material, self.geoms, self.n, self.cfg)
         self.workspace = torch.empty(ws, dtype=torch.uint8, device="cuda")
-        self.out = api.SteadyOutputs(len(self.geoms), material.n_bins, cfg.n_cells, cfg.per_bin)
+        self.out = api.SteadyOutputs(len(self.geoms), material.n_bins, cfg.n_cells, cfg.per_bin, regions=cfg.regions,
+                                     nscat=cfg.n_scat_max if cfg.nscat_curve else 0)
         self.stream = torch.cuda.Stream()
         self.stream.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(self.stream):

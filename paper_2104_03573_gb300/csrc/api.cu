@@ -411,12 +411,14 @@ struct SteadyWs {
   double* det_raw;      // [n_det][4] FP64 path sums (zeroed)
   long long* det_q;     // [n_det][4] FP32 path fixed-point sums (zeroed)
   double* det;          // host staging of the outputs
+  double* nscat;        // [G][K + 1][4] N_scat_max curve sums (zeroed)
+  double* kn;           // host staging of the curve
   size_t bytes;
 };
 
 SteadyWs layout_steady(char* base, int G, int n, int nc, uint64_t total, bool grad, bool replay, int nd,
                        bool host_out, bool want_ev, bool want_x, bool want_T, bool want_q, bool want_qbin,
-                       uint64_t n_det = 0) {
+                       uint64_t n_det = 0, int nscat = 0) {
   Carve c;
   c.base = base;
   SteadyWs w{};
@@ -440,6 +442,7 @@ SteadyWs layout_steady(char* base, int G, int n, int nc, uint64_t total, bool gr
   w.t0 = c.take<unsigned long long>(1);
   w.det_raw = n_det ? c.take<double>(4 * n_det) : nullptr;
   w.det_q = n_det ? c.take<long long>(4 * n_det) : nullptr;
+  w.nscat = nscat ? c.take<double>((size_t)G * (size_t)(nscat + 1) * 4) : nullptr;
   c.off = (c.off + 255) & ~(size_t)255;
   w.zero_end = base ? base + c.off : nullptr;
   w.regs = n_det ? c.take<DetRegion>(MCBTE_MAX_REGIONS) : nullptr;
@@ -457,6 +460,7 @@ SteadyWs layout_steady(char* base, int G, int n, int nc, uint64_t total, bool gr
     w.dk = grad ? c.take<double>(n) : nullptr;
     w.dkp = grad ? c.take<double>(2) : nullptr;
     w.dkdir = (grad && nd > 0) ? c.take<double>(2 * (size_t)nd) : nullptr;
+    w.kn = nscat ? c.take<double>((size_t)G * (size_t)nscat * 2) : nullptr;
   }
   w.bytes = c.off + 256;
   return w;
@@ -496,6 +500,8 @@ mcbte_status check_steady(const mcbte_material* m, const mcbte_geometry* const* 
     if (rs != MCBTE_OK) return rs;
     if (p->n_regions > 0 && G != 1) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: detector regions need one geometry");
   }
+  if (p->nscat_curve && (p->n_scat_max < 1 || p->n_scat_max > MCBTE_MAX_NSCAT_CURVE))
+    return fail(MCBTE_ERR_INVALID_ARG, "run_steady: nscat_curve needs n_scat_max in [1, MCBTE_MAX_NSCAT_CURVE]");
   if (t >= (1ull << 40)) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: too many particles");
   *total = t;
   return MCBTE_OK;
@@ -524,12 +530,16 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
     if (gout->on_host != out->on_host) return fail(MCBTE_ERR_INVALID_ARG, "grad: on_host must match");
     if (gout->dp_estimator < 0 || gout->dp_estimator > 2)
       return fail(MCBTE_ERR_INVALID_ARG, "grad: dp_estimator must be 0, 1 or 2");
+    if (p->nscat_curve) return fail(MCBTE_ERR_INVALID_ARG, "grad: nscat_curve is an output of run_steady");
   }
+  if (p->nscat_curve && !out->kappa_nscat)
+    return fail(MCBTE_ERR_INVALID_ARG, "run_steady: nscat_curve needs out->kappa_nscat");
+  const int nscat = p->nscat_curve ? p->n_scat_max : 0;
   const bool host_out = out->on_host != 0;
   const bool replay = grad && p->precision == MCBTE_FP32_TRACE;
   const uint64_t n_det = region_detectors(p->n_regions, p->region_grid);
   SteadyWs w = layout_steady(nullptr, G, n, nc, total, grad, replay, nd, host_out, out->events_pp, out->X_pp, out->T,
-                             out->q, out->q_bin, n_det);
+                             out->q, out->q_bin, n_det, nscat);
   const size_t need = w.bytes;
   char* base = static_cast<char*>(workspace);
   bool own = false;
@@ -541,7 +551,7 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   }
   char* aligned = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(base) + 255) & ~(uintptr_t)255);
   w = layout_steady(aligned, G, n, nc, total, grad, replay, nd, host_out, out->events_pp, out->X_pp, out->T, out->q,
-                    out->q_bin, n_det);
+                    out->q_bin, n_det, nscat);
   auto release = [&]() {
     if (own) cudaFreeAsync(base, s);
   };
@@ -577,8 +587,9 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   C.seed_dev = reinterpret_cast<const unsigned long long*>(p->seed_device);
   C.refill_min = p->refill_threshold;
   C.cell_flux_axis = p->cell_flux_axis ? 1 : 0;
-  C.ext = p->n_regions > 0 ? 1 : 0;
+  C.ext = (p->n_regions > 0 || nscat > 0) ? 1 : 0;
   for (int g = 0; g < G; ++g) C.ext |= uses_ext(m, geoms[g]->host) ? 1 : 0;
+  C.nscat_acc = w.nscat;
   C.n_regs = p->n_regions;
   C.n_det = (uint32_t)n_det;
   C.regs = w.regs;
@@ -645,6 +656,7 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   O.q_bin = host_out ? w.q_bin : out->q_bin;
   O.stats = host_out ? w.stats : out->stats;
   O.det = host_out ? w.det : out->det;
+  O.kn = host_out ? w.kn : out->kappa_nscat;
   if (grad) {
     O.dk = host_out ? w.dk : gout->dkappa_dlogtau;
     O.dkp = host_out ? w.dkp : gout->dkappa_dp;
@@ -664,6 +676,7 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
     RUN_TRY(d2h(out->events_pp, w.events_pp, total * sizeof(uint32_t)));
     RUN_TRY(d2h(out->X_pp, w.X_pp, total * sizeof(double)));
     RUN_TRY(d2h(out->det, w.det, 4 * n_det * sizeof(double)));
+    RUN_TRY(d2h(out->kappa_nscat, w.kn, (size_t)G * (size_t)nscat * 2 * sizeof(double)));
     if (grad) {
       RUN_TRY(d2h(gout->dkappa_dlogtau, w.dk, (size_t)n * sizeof(double)));
       RUN_TRY(d2h(gout->dkappa_dp, w.dkp, 2 * sizeof(double)));
@@ -697,7 +710,8 @@ mcbte_status mcbte_steady_workspace_size(const mcbte_material* m, const mcbte_ge
   if (!bytes) return fail(MCBTE_ERR_INVALID_ARG, "workspace_size: null bytes");
   SteadyWs w = layout_steady(nullptr, n_geoms, m->n, p->n_cells, total, want_grad != 0,
                              want_grad != 0 && p->precision == MCBTE_FP32_TRACE, n_dirs, false, false, false, false,
-                             false, false, region_detectors(p->n_regions, p->region_grid));
+                             false, false, region_detectors(p->n_regions, p->region_grid),
+                             p->nscat_curve ? p->n_scat_max : 0);
   *bytes = w.bytes;
   return MCBTE_OK;
 }
@@ -981,7 +995,8 @@ mcbte_status mcbte_run_steady_noalloc(const mcbte_material* m, const mcbte_geome
   mcbte_status st = check_steady(m, geoms, n_geoms, p, &total);
   if (st != MCBTE_OK) return st;
   const SteadyWs w = layout_steady(nullptr, n_geoms, m->n, p->n_cells, total, false, false, 0, false, false, false,
-                                   false, false, false);
+                                   false, false, false, region_detectors(p->n_regions, p->region_grid),
+                                   p->nscat_curve ? p->n_scat_max : 0);
   if (w.bytes > kNoAllocScratchBytes)
     return fail(MCBTE_ERR_WORKSPACE, "run_steady_noalloc: this run needs " + std::to_string(w.bytes) +
                                          " bytes of scratch, above the fixed " +

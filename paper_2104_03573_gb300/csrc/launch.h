@@ -41,6 +41,7 @@ struct SteadyOutDev {
   double* dkp;       // grad: [2]
   double* dkdir;     // grad: [n_dirs][2]
   double* det;       // detector regions: [n_det][4], or null
+  double* kn;        // N_scat_max curve: [G][n_scat_max][2], or null
 };
 
 cudaError_t launch_steady_f32(bool grad, bool cells, const GeoRun* geos, const uint64_t* offs, const MatView& M,

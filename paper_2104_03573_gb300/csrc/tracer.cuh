@@ -56,6 +56,10 @@ struct RunCfg {
   // < win_end; the first window emits, later ones resume saved particles
   int win_first, win_last, win_end;
   int mvd;              // gradient: measure-valued d kappa / d p_pore (phantom traces)
+  // N_scat_max convergence curve, or null: per geometry and k = 1..n_scat_max,
+  // [0] sum of X at the k-th relaxation, [1] its square, [2] sum of the final
+  // X of trajectories with exactly k - 1 relaxations, [3] its square
+  double* nscat_acc;    // [G][n_scat_max + 1][4]
 };
 
 // Transient detector region (Sec. 4.5): a closed axis-aligned cuboid split
@@ -546,6 +550,8 @@ using TallyFx = TallyFxT<4>;
 struct TallyNone {
   template <typename R>
   __device__ __forceinline__ void period_end(Particle<R>&) const {}
+  template <typename R>
+  __device__ __forceinline__ double X(const Particle<R>&) const { return 0.0; }
 };
 
 // ------------------------------------------------------------------ likelihood-ratio policies
@@ -759,6 +765,15 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
   uint4 ctr = make_uint4(p.pid, (uint32_t)p.g, p.e, 0u);
   if (relax) {
     ++p.n_relax;
+    if constexpr (EXT) {
+      if (C.nscat_acc) {
+        // a run with N_scat_max = n_relax would end the particle here with this tally
+        const double x = T.X(p);
+        double* a = C.nscat_acc + ((size_t)p.g * (size_t)(C.n_scat_max + 1) + (size_t)p.n_relax) * 4;
+        atomicAdd(a + 0, x);
+        atomicAdd(a + 1, x * x);
+      }
+    }
     if (C.n_scat_max > 0 && p.n_relax >= C.n_scat_max) return STEP_DONE;
     // the relaxation period in this bin is over: frequency-resolved flux
     T.period_end(p);

@@ -28,6 +28,16 @@ __device__ __forceinline__ int find_geom(const uint64_t* offs, int G, uint64_t i
   return lo;
 }
 
+// N_scat_max curve: a trajectory that ended (absorbed, truncated) after m <
+// n_scat_max relaxations has the same final tally X in every run with
+// N_scat_max > m; it enters the difference array at m + 1.
+__device__ __forceinline__ void nscat_end(const RunCfg& C, int g, int m, double X) {
+  if (!C.nscat_acc || m >= C.n_scat_max) return;
+  double* a = C.nscat_acc + ((size_t)g * (size_t)(C.n_scat_max + 1) + (size_t)(m + 1)) * 4;
+  atomicAdd(a + 2, X);
+  atomicAdd(a + 3, X * X);
+}
+
 // Likelihood-ratio contributions of a finished particle with tally X: every
 // relaxation period's value into G[bin], the dense resampling term R, the
 // specularity score and the probe directions.
@@ -114,6 +124,7 @@ __global__ void __launch_bounds__(256) k_steady_fp64(const GeoRun* __restrict__ 
   }
   if (A.events_pp) A.events_pp[idx] = (uint32_t)nev;
   if (A.X_pp) A.X_pp[idx] = p.X;
+  nscat_end(C, g, p.n_relax, p.X);
   if constexpr (GRAD) {
     grad_finish(gr, p.X, g, C, A, M);
     if (C.mvd && gr.mv.sel > 0u) {
@@ -373,6 +384,7 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
       }
       if (A.events_pp) A.events_pp[idx] = nev;
       if (A.X_pp) A.X_pp[idx] = X;
+      if constexpr (EXT) nscat_end(C, p.g, p.n_relax, X);
       alive = false;
     }
   }
@@ -441,6 +453,26 @@ __global__ void k_finalize_steady(const GeoRun* geos, MatView M, RunCfg C, Acc A
       for (int b = 0; b < 4; ++b) raw[b] = A.det_raw[(size_t)d * 4 + b] + (double)A.det_q[(size_t)d * 4 + b] * kFxInv;
       O.det[(size_t)d * 4 + 0] = (kT * raw[0]) * 1e-12;
       for (int b = 1; b < 4; ++b) O.det[(size_t)d * 4 + b] = (kq * raw[b]) * 1e-9;
+    }
+  }
+  if (O.kn && C.nscat_acc && threadIdx.x == 0) {
+    // kappa and its standard error for N_scat_max = k: the tally at the k-th
+    // relaxation, or the final one of trajectories that ended before it
+    const int K = C.n_scat_max;
+    const double nt = (double)A.cnt[g * 4 + 3];
+    const double* a = C.nscat_acc + (size_t)g * (size_t)(K + 1) * 4;
+    double e1 = 0.0, e2 = 0.0;
+    for (int k = 1; k <= K; ++k) {
+      e1 += a[(size_t)k * 4 + 2];
+      e2 += a[(size_t)k * 4 + 3];
+      const double s1 = a[(size_t)k * 4 + 0] + e1;
+      const double s2 = a[(size_t)k * 4 + 1] + e2;
+      const double mean = s1 / nt;
+      const double var = nt > 1.0 ? (s2 - nt * mean * mean) / (nt - 1.0) : 0.0;
+      const double qm = (E_eff / G.V_solid) * s1 * 1e-9;
+      const double qs = (G.E_tot / G.V_solid) * 1e-9 * sqrt(fmax(var, 0.0) / nt);
+      O.kn[((size_t)g * K + (k - 1)) * 2 + 0] = -qm / G.kappa_grad;
+      O.kn[((size_t)g * K + (k - 1)) * 2 + 1] = qs / fabs(G.kappa_grad);
     }
   }
   if (O.q_bin && C.per_bin) {

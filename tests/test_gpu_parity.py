@@ -600,3 +600,54 @@ def test_grad_rejects_unknown_dp_estimator():
     with pytest.raises(L.MCBTEError) as e:
         api.grad(M, G, 100, cfg, dp_estimator=3)
     assert e.value.status == L.ERR_INVALID_ARG
+
+
+def test_nscat_curve_fp64_matches_oracle_and_fp32_statistics():
+    # kappa for every N_scat_max from one run (Sec. 3.5.6), off-centre pore
+    # with a diagonal control gradient
+    m = W.bvk_holland(n_per_branch=50)
+    g = W.pore_skew()
+    run = W.SteadyRun(n=20_000, seed=62, tally_axis=1, n_scat_max=16, max_events=10 ** 7)
+    ref = oracle.run_steady(m, g, run, nscat_curve=True)
+    M, G = api.Material(m), api.Geometry(g)
+    base = dict(n_scat_max=run.n_scat_max, max_events=run.max_events, tally_axis=1, nscat_curve=True)
+    o = api.run_steady(M, [G], [run.n], api.SteadyConfig(seed=run.seed, precision=L.FP64_PLAIN, **base))
+    torch.cuda.synchronize()
+    kn = o.kappa_nscat[0].cpu().numpy()
+    ok, err = rel_close(kn, ref["kappa_nscat"], 1e-9)
+    assert ok, err
+    assert kn[-1, 0] == pytest.approx(o.stats[0, L.STAT_KAPPA].item(), rel=1e-12)
+    # host outputs through the C ABI: the same curve
+    h = api.run_steady_host(M, [G], [run.n], api.SteadyConfig(seed=run.seed, precision=L.FP64_PLAIN, **base))
+    ok, err = rel_close(h["kappa_nscat"][0], ref["kappa_nscat"], 1e-9)
+    assert ok, err
+    # FP32: an independent sample, every point within 4 combined SE; the last
+    # point is the run's own kappa, which a plain run reproduces
+    n32 = 400_000
+    c32 = api.SteadyConfig(seed=63, precision=L.FP32_TRACE, **base)
+    o32 = api.run_steady(M, [G], [n32], c32)
+    plain = api.run_steady(M, [G], [n32], replace(c32, nscat_curve=False))
+    torch.cuda.synchronize()
+    k32 = o32.kappa_nscat[0].cpu().numpy()
+    assert o32.stats[0, L.STAT_STATUS].item() == 0
+    assert o32.stats[0, L.STAT_KAPPA].item() == pytest.approx(plain.stats[0, L.STAT_KAPPA].item(), rel=1e-3)
+    assert k32[-1, 0] == pytest.approx(o32.stats[0, L.STAT_KAPPA].item(), rel=1e-9)
+    ref2 = oracle.run_steady(m, g, replace(run, n=200_000, seed=64), nscat_curve=True)
+    z = (k32[:, 0] - ref2["kappa_nscat"][:, 0]) / np.hypot(k32[:, 1], ref2["kappa_nscat"][:, 1])
+    assert np.all(np.abs(z) < 4.0), z
+
+
+def test_nscat_curve_rejected_with_gradient_and_without_output():
+    wl = W.pore_film_c5(n=100)
+    M, G = api.Material(wl.material), api.Geometry(wl.geometries[0])
+    cfg = api.SteadyConfig(seed=1, precision=L.FP64_PLAIN, n_scat_max=4, tally_axis=1, nscat_curve=True)
+    with pytest.raises(L.MCBTEError) as e:
+        api.grad(M, G, 100, cfg)
+    assert e.value.status == L.ERR_INVALID_ARG
+    out = api.SteadyOutputs(1, M.n_bins, 0, False)          # no kappa_nscat buffer
+    with pytest.raises(L.MCBTEError) as e:
+        api.run_steady(M, [G], [100], cfg, out=out)
+    assert e.value.status == L.ERR_INVALID_ARG
+    with pytest.raises(L.MCBTEError) as e:
+        api.run_steady(M, [G], [100], replace(cfg, n_scat_max=0))
+    assert e.value.status == L.ERR_INVALID_ARG

@@ -769,21 +769,12 @@ def test_measure_valued_specularity_gradient_at_p0_and_p1(p0, side):
     assert abs(rl["dkappa_dp"] - fd) > 4.0 * math.hypot(fd_se, rl["dkappa_dp_se"])
 
 
-def _skewed_pore_film(W_=100e-9):
-    """Non-symmetric nanoporous cell: off-centre pore, control gradient along
-    the diagonal of the x-y plane."""
-    g = W.pore_lattice(W_, 0.25, 200e-9)
-    g.pore_c = (0.3 * W_, 0.62 * W_)
-    g.grad_T = (-0.5e6, -1e6, 0.0)
-    return g
-
-
 def test_nscat_curve_equals_separate_runs():
     # a run with N_scat_max = k stops each trajectory at its k-th relaxation
     # (Sec. 3.5.6) and draws nothing else differently, so one run with the
     # largest N_scat_max yields kappa for every smaller one
     m = W.bvk_holland(n_per_branch=20)
-    g = _skewed_pore_film()
+    g = W.pore_skew()
     run = W.SteadyRun(n=20_000, seed=61, tally_axis=1, n_scat_max=12, max_events=10 ** 7)
     r = oracle.run_steady(m, g, run, nscat_curve=True, n_threads=4)
     curve = r["kappa_nscat"]
