@@ -53,6 +53,7 @@ class _Params(C.Structure):
         ("n_cells", C.c_int), ("cell_axis", C.c_int), ("tally_axis", C.c_int),
         ("t_max", C.c_double), ("n_times", C.c_int), ("t_meas", C.c_void_p), ("grid", C.c_int * 3),
         ("n_regions", C.c_int), ("regions", C.c_void_p), ("region_grid", C.c_void_p), ("time_average", C.c_int),
+        ("det_per_bin", C.c_int),
         ("nscat_curve", C.c_int), ("want_grad", C.c_int), ("dp_mvd", C.c_int), ("n_dirs", C.c_int), ("dirs", C.c_void_p), ("n_threads", C.c_int),
     ]
 
@@ -286,7 +287,7 @@ def dp_mvd(geom, dp_estimator: int = 0) -> bool:
 def run_steady(material, geom, run, *, pid_begin: int = 0, pid_end: Optional[int] = None,
                per_particle: bool = False, grad: bool = False, dirs: Optional[np.ndarray] = None,
                n_threads: int = 0, batch_index: int = 0, n_total: Optional[int] = None,
-               dp_estimator: int = 0, nscat_curve: bool = False) -> dict:
+               dp_estimator: int = 0, nscat_curve: bool = False, det_per_bin: bool = False) -> dict:
     """Trace particles [pid_begin, pid_end) of a steady run of N = run.n (or
     n_total) particles and return raw sums plus the physical tallies.
 
@@ -295,7 +296,9 @@ def run_steady(material, geom, run, *, pid_begin: int = 0, pid_end: Optional[int
     one (each particle's phantom trace with one pore hit's branch flipped),
     0 the likelihood ratio for 0 < p < 1 and the measure-valued one at p = 0, 1.
     nscat_curve adds "kappa_nscat" [n_scat_max][2]: kappa and its standard
-    error for every N_scat_max' = 1..n_scat_max, from the same trajectories."""
+    error for every N_scat_max' = 1..n_scat_max, from the same trajectories.
+    det_per_bin splits the detector-region outputs by frequency bin
+    (det_T [n_det][n_bins], det_q [n_det][n_bins][3])."""
     N = int(n_total if n_total is not None else run.n)
     pe = N if pid_end is None else int(pid_end)
     keep = _Keep()
@@ -333,7 +336,9 @@ def run_steady(material, geom, run, *, pid_begin: int = 0, pid_end: Optional[int
         boxes = keep.add(np.ascontiguousarray([rg[0] for rg in regions], dtype=np.float64))
         grids = keep.add(np.ascontiguousarray([rg[1] for rg in regions], dtype=np.int32))
         P.n_regions, P.regions, P.region_grid = len(regions), boxes.ctypes.data, grids.ctypes.data
-        det = np.zeros((int(sum(int(np.prod(rg[1])) for rg in regions)), 4))
+        P.det_per_bin = int(bool(det_per_bin))
+        nd_ = int(sum(int(np.prod(rg[1])) for rg in regions))
+        det = np.zeros((nd_, n, 4) if det_per_bin else (nd_, 4))
         O.snap = det.ctypes.data
     rc = lib().or_run(C.byref(P), C.byref(O))
     if rc:
@@ -356,8 +361,9 @@ def run_steady(material, geom, run, *, pid_begin: int = 0, pid_end: Optional[int
         r["q"] = (E_eff / Vc) * Q[:nc] * 1e-9
     r["q_bin"] = (E_eff / V) * qb * 1e-9
     if regions:
-        r["det_T"] = (E_eff / (C_tot * r["det_V"])) * det[:, 0] * 1e-12
-        r["det_q"] = (E_eff / r["det_V"])[:, None] * det[:, 1:] * 1e-9
+        vol = r["det_V"][:, None] if det_per_bin else r["det_V"]
+        r["det_T"] = (E_eff / (C_tot * vol)) * det[..., 0] * 1e-12
+        r["det_q"] = (E_eff / vol)[..., None] * det[..., 1:] * 1e-9
     sx, sx2 = sc[SUMX], sc[SUMX2]
     mean = sx / npp if npp else 0.0
     var = (sx2 - npp * mean * mean) / (npp - 1) if npp > 1 else 0.0

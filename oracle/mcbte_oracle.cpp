@@ -265,6 +265,7 @@ typedef struct {
   const double* regions;      // [n_regions][6] xmin, xmax, ymin, ymax, zmin, zmax (m)
   const int* region_grid;     // [n_regions][3]
   int time_average;           // 0: snapshots at t_m (Eq. sampling); 1: averages over [t_{m-1}, t_m)
+  int det_per_bin;            // steady regions: one T, q per detector and frequency bin (Sec. 4.5)
   int nscat_curve;            // 1: X sums for every N_scat_max' = 1..n_scat_max (steady)
   int want_grad;
   int dp_mvd;                 // 1: d kappa / d p_pore by the measure-valued estimator
@@ -935,7 +936,8 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
           const double dt = seg / v;
           for (const Setup::Region& r : S.regs)
             region_track(r, x, w3, 0.0, 0.0, dt, [&](size_t det, double dur) {
-              const size_t c = (r.off + det) * 4;
+              // per detector, or per detector and the particle's bin
+              const size_t c = P->det_per_bin ? ((r.off + det) * (size_t)n + (size_t)bin) * 4 : (r.off + det) * 4;
               out.snap[c + 0] += s * dur;
               out.snap[c + 1] += ((s * v) * dur) * u[0];
               out.snap[c + 2] += ((s * v) * dur) * u[1];
@@ -1242,7 +1244,8 @@ int or_run(const or_params* P, or_out* O) {
     if (!P->transient && P->n_cells > 0) { p.T.assign(P->n_cells, 0.0); p.Q.assign((size_t)P->n_cells * 3, 0.0); }
     if (O->qbin_sum) p.qbin.assign(P->n_bins, 0.0);
     if (P->transient) p.snap.assign((size_t)P->n_times * ncell_t * 4, 0.0);
-    else if (P->n_regions > 0) p.snap.assign(ncell_t * 4, 0.0);     // steady detector regions
+    else if (P->n_regions > 0)                                      // steady detector regions
+      p.snap.assign(ncell_t * 4 * (P->det_per_bin ? (size_t)P->n_bins : 1), 0.0);
     if (P->want_grad) { p.G.assign(P->n_bins, 0.0); p.dsum.assign(P->n_dirs, 0.0); p.dsum2.assign(P->n_dirs, 0.0); }
     if (P->nscat_curve) p.curve.assign(2 * (size_t)P->n_scat_max, 0.0);
   }

@@ -365,6 +365,28 @@ def test_steady_regions_match_the_slab_cells():
     np.testing.assert_allclose(r["det_raw"][nc + 1:].sum(axis=0), r["det_raw"][nc], rtol=1e-12, atol=1e-9)
 
 
+def test_steady_regions_per_frequency_bin():
+    # the steady output of Sec. 4.5 lists every detector per frequency bin:
+    # the bins of a detector sum to its total, and detectors tiling the box
+    # give back the frequency-resolved flux of Sec. 4.6 (volume-weighted)
+    m = W.bvk_holland(n_per_branch=10)
+    wl = W.si_slab_c2(n=20_000, material=m)
+    g, run = wl.geometries[0], wl.run
+    L = g.L
+    tiles = ((0.0, L[0], 0.0, L[1], 0.0, L[2]), (2, 2, 4))
+    sub = ((0.1 * L[0], 0.7 * L[0], 0.0, L[1], 0.25 * L[2], 0.75 * L[2]), (2, 1, 3))
+    run = replace(run, regions=[tiles, sub])
+    tot = oracle.run_steady(m, g, run)
+    pb = oracle.run_steady(m, g, run, det_per_bin=True)
+    assert pb["det_T"].shape == (16 + 6, m.n_bins) and pb["det_q"].shape == (16 + 6, m.n_bins, 3)
+    sc = np.abs(tot["det_raw"]).max(axis=0)
+    np.testing.assert_allclose(pb["det_raw"].sum(axis=1), tot["det_raw"], rtol=1e-9, atol=1e-12 * sc.max())
+    assert tot["kappa"] == pb["kappa"]
+    ta = run.tally_axis
+    q_tiles = (pb["det_V"][:16, None] * pb["det_q"][:16, :, ta]).sum(axis=0) / float(np.prod(L))
+    np.testing.assert_allclose(q_tiles, pb["q_bin"], rtol=1e-9, atol=1e-12 * np.abs(pb["q_bin"]).max())
+
+
 # ------------------------------------------------------------------ two-phonon clock (Sec. 3.3)
 def _with_imp(m, tau_imp):
     from dataclasses import replace
