@@ -225,6 +225,8 @@ typedef struct {
   int nscat_curve;             /* 1: also kappa for every N_scat_max' = 1..n_scat_max from the
                                   same trajectories (mcbte_steady_out.kappa_nscat); needs
                                   1 <= n_scat_max <= MCBTE_MAX_NSCAT_CURVE; not with mcbte_grad */
+  int det_per_bin;             /* 1: the detector outputs per frequency bin (Sec. 4.5 lists the
+                                  steady output of each detector per bin); needs n_regions > 0 */
 } mcbte_steady_params;
 
 typedef struct {
@@ -237,7 +239,8 @@ typedef struct {
   int on_host;          /* 0: device pointers, 1: host pointers                          */
   double* det;          /* [n_detectors][4] T - T_eq (K), q_x, q_y, q_z (W/m^2) per detector of
                            the regions (track length in each, Eqs. temp_steady, flux_x_steady),
-                           detectors region by region, x fastest; or NULL                */
+                           detectors region by region, x fastest; with det_per_bin
+                           [n_detectors][n_bins][4], the contribution of each bin; or NULL */
   double* kappa_nscat;  /* [n_geoms][n_scat_max][2] kappa (W/m/K) and its standard error with
                            N_scat_max' = k + 1 at index k (required with nscat_curve)       */
 } mcbte_steady_out;

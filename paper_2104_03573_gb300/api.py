@@ -139,6 +139,7 @@ class SteadyConfig:
     cell_flux_axis: bool = False             # FP32 cell tallies: T and the tally-axis flux only
     regions: Sequence = ()                   # detector regions ((xmin..zmax) m, (nx, ny, nz)), one geometry
     nscat_curve: bool = False                # also kappa for every N_scat_max' <= n_scat_max (kappa_nscat)
+    det_per_bin: bool = False                # detector outputs per frequency bin (det: [n_det][n_bins][4])
 
 
 def _event_handles(pair):
@@ -169,6 +170,7 @@ def steady_params(cfg: SteadyConfig, n_particles: np.ndarray) -> "L.SteadyParams
     p.refill_threshold = int(cfg.refill_threshold)
     p.cell_flux_axis = int(bool(cfg.cell_flux_axis))
     p.nscat_curve = int(bool(cfg.nscat_curve))
+    p.det_per_bin = int(bool(cfg.det_per_bin))
     regions = list(cfg.regions or ())
     if regions:
         boxes = np.ascontiguousarray([r[0] for r in regions], dtype=np.float64)
@@ -182,12 +184,14 @@ class SteadyOutputs:
     """Caller-owned device outputs of a steady run (torch tensors)."""
 
     def __init__(self, n_geoms: int, n_bins: int, n_cells: int, per_bin: bool, total: int = 0,
-                 per_particle: bool = False, device=None, regions: Sequence = (), nscat: int = 0):
+                 per_particle: bool = False, device=None, regions: Sequence = (), nscat: int = 0,
+                 det_per_bin: bool = False):
         import torch
         dev = device or torch.device("cuda")
         f = dict(dtype=torch.float64, device=dev)
         nd = sum(int(np.prod(r[1])) for r in regions) if regions else 0
-        self.det = torch.zeros(nd, 4, **f) if nd else None   # T, q_x, q_y, q_z per detector
+        # T, q_x, q_y, q_z per detector (and bin)
+        self.det = (torch.zeros(nd, n_bins, 4, **f) if det_per_bin else torch.zeros(nd, 4, **f)) if nd else None
         self.T = torch.zeros(n_geoms, n_cells, **f) if n_cells > 0 else None
         self.q = torch.zeros(n_geoms, n_cells, 3, **f) if n_cells > 0 else None
         self.q_bin = torch.zeros(n_geoms, n_bins, **f) if per_bin else None
@@ -231,7 +235,8 @@ def run_steady(material: Material, geoms: Sequence[Geometry], n_particles, cfg: 
     n = np.ascontiguousarray(np.asarray(n_particles, dtype=np.uint64))
     if out is None:
         out = SteadyOutputs(len(geoms), material.n_bins, cfg.n_cells, cfg.per_bin, int(n.sum()), per_particle,
-                            regions=cfg.regions, nscat=cfg.n_scat_max if cfg.nscat_curve else 0)
+                            regions=cfg.regions, nscat=cfg.n_scat_max if cfg.nscat_curve else 0,
+                            det_per_bin=cfg.det_per_bin)
     p = steady_params(cfg, n)
     o = out.struct()
     ws_ptr, ws_bytes = (None, 0) if workspace is None else (workspace.data_ptr(), workspace.numel() * workspace.element_size())
@@ -272,6 +277,10 @@ def run_steady_host(material: Material, geoms: Sequence[Geometry], n_particles, 
     if cfg.nscat_curve:
         res["kappa_nscat"] = np.zeros((G, int(cfg.n_scat_max), 2))
         o.kappa_nscat = res["kappa_nscat"].ctypes.data
+    nd = sum(int(np.prod(r[1])) for r in cfg.regions) if cfg.regions else 0
+    if nd:
+        res["det"] = np.zeros((nd, nb, 4) if cfg.det_per_bin else (nd, 4))
+        o.det = res["det"].ctypes.data
     o.on_host = 1
     p = steady_params(cfg, n)
     st = L.load().mcbte_run_steady(material.handle, _handles(geoms), G, C.byref(p), C.byref(o), None, 0, None)

@@ -53,7 +53,7 @@ def tune(material: api.Material, geoms: Sequence[api.Geometry], n_particles, cfg
         c = replace(cfg, threads_per_block=threads, blocks_per_sm=bps, refill_threshold=refill, trace_events=None,
                     seed_device=None)
         out = api.SteadyOutputs(len(geoms), material.n_bins, c.n_cells, c.per_bin, regions=c.regions,
-                                nscat=c.n_scat_max if c.nscat_curve else 0)
+                                nscat=c.n_scat_max if c.nscat_curve else 0, det_per_bin=c.det_per_bin)
         api.run_steady(material, geoms, sample, c, out=out)        # warm-up / first-launch costs
         times = []
         for _ in range(repeats):

@@ -35,7 +35,7 @@ class GraphBatch:
         ws = api.steady_workspace_size(material, self.geoms, self.n, self.cfg)
         self.workspace = torch.empty(ws, dtype=torch.uint8, device="cuda")
         self.out = api.SteadyOutputs(len(self.geoms), material.n_bins, cfg.n_cells, cfg.per_bin, regions=cfg.regions,
-                                     nscat=cfg.n_scat_max if cfg.nscat_curve else 0)
+                                     nscat=cfg.n_scat_max if cfg.nscat_curve else 0, det_per_bin=cfg.det_per_bin)
         self.stream = torch.cuda.Stream()
         self.stream.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(self.stream):

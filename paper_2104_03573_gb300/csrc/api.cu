@@ -346,6 +346,11 @@ uint64_t region_detectors(int n, const int* grid) {
   return nd;
 }
 
+// Steady detector sums: one per detector, or one per detector and bin.
+uint64_t steady_det_slots(const mcbte_steady_params* p, int n_bins) {
+  return region_detectors(p->n_regions, p->region_grid) * (p->det_per_bin ? (uint64_t)n_bins : 1ull);
+}
+
 // Records of n regions (whole: the box split by `grid` as one region).
 std::vector<DetRegion> build_regions(int n, const double* regions, const int* rgrid, bool whole, const int grid[3],
                                      const double Lbox[3]) {
@@ -500,6 +505,8 @@ mcbte_status check_steady(const mcbte_material* m, const mcbte_geometry* const* 
     if (rs != MCBTE_OK) return rs;
     if (p->n_regions > 0 && G != 1) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: detector regions need one geometry");
   }
+  if (p->det_per_bin && p->n_regions < 1)
+    return fail(MCBTE_ERR_INVALID_ARG, "run_steady: det_per_bin needs detector regions");
   if (p->nscat_curve && (p->n_scat_max < 1 || p->n_scat_max > MCBTE_MAX_NSCAT_CURVE))
     return fail(MCBTE_ERR_INVALID_ARG, "run_steady: nscat_curve needs n_scat_max in [1, MCBTE_MAX_NSCAT_CURVE]");
   if (t >= (1ull << 40)) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: too many particles");
@@ -538,8 +545,9 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   const bool host_out = out->on_host != 0;
   const bool replay = grad && p->precision == MCBTE_FP32_TRACE;
   const uint64_t n_det = region_detectors(p->n_regions, p->region_grid);
+  const uint64_t det_slots = steady_det_slots(p, n);
   SteadyWs w = layout_steady(nullptr, G, n, nc, total, grad, replay, nd, host_out, out->events_pp, out->X_pp, out->T,
-                             out->q, out->q_bin, n_det, nscat);
+                             out->q, out->q_bin, det_slots, nscat);
   const size_t need = w.bytes;
   char* base = static_cast<char*>(workspace);
   bool own = false;
@@ -551,7 +559,7 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   }
   char* aligned = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(base) + 255) & ~(uintptr_t)255);
   w = layout_steady(aligned, G, n, nc, total, grad, replay, nd, host_out, out->events_pp, out->X_pp, out->T, out->q,
-                    out->q_bin, n_det, nscat);
+                    out->q_bin, det_slots, nscat);
   auto release = [&]() {
     if (own) cudaFreeAsync(base, s);
   };
@@ -592,6 +600,7 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   C.nscat_acc = w.nscat;
   C.n_regs = p->n_regions;
   C.n_det = (uint32_t)n_det;
+  C.det_nb = p->det_per_bin ? n : 1;
   C.regs = w.regs;
   if (grad && geoms[0]->host.pore) {
     // d kappa / d p_pore: the measure-valued estimator on request, and where
@@ -675,7 +684,7 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
     RUN_TRY(d2h(out->stats, w.stats, (size_t)G * MCBTE_NSTATS * sizeof(double)));
     RUN_TRY(d2h(out->events_pp, w.events_pp, total * sizeof(uint32_t)));
     RUN_TRY(d2h(out->X_pp, w.X_pp, total * sizeof(double)));
-    RUN_TRY(d2h(out->det, w.det, 4 * n_det * sizeof(double)));
+    RUN_TRY(d2h(out->det, w.det, 4 * det_slots * sizeof(double)));
     RUN_TRY(d2h(out->kappa_nscat, w.kn, (size_t)G * (size_t)nscat * 2 * sizeof(double)));
     if (grad) {
       RUN_TRY(d2h(gout->dkappa_dlogtau, w.dk, (size_t)n * sizeof(double)));
@@ -710,8 +719,7 @@ mcbte_status mcbte_steady_workspace_size(const mcbte_material* m, const mcbte_ge
   if (!bytes) return fail(MCBTE_ERR_INVALID_ARG, "workspace_size: null bytes");
   SteadyWs w = layout_steady(nullptr, n_geoms, m->n, p->n_cells, total, want_grad != 0,
                              want_grad != 0 && p->precision == MCBTE_FP32_TRACE, n_dirs, false, false, false, false,
-                             false, false, region_detectors(p->n_regions, p->region_grid),
-                             p->nscat_curve ? p->n_scat_max : 0);
+                             false, false, steady_det_slots(p, m->n), p->nscat_curve ? p->n_scat_max : 0);
   *bytes = w.bytes;
   return MCBTE_OK;
 }
@@ -995,7 +1003,7 @@ mcbte_status mcbte_run_steady_noalloc(const mcbte_material* m, const mcbte_geome
   mcbte_status st = check_steady(m, geoms, n_geoms, p, &total);
   if (st != MCBTE_OK) return st;
   const SteadyWs w = layout_steady(nullptr, n_geoms, m->n, p->n_cells, total, false, false, 0, false, false, false,
-                                   false, false, false, region_detectors(p->n_regions, p->region_grid),
+                                   false, false, false, steady_det_slots(p, m->n),
                                    p->nscat_curve ? p->n_scat_max : 0);
   if (w.bytes > kNoAllocScratchBytes)
     return fail(MCBTE_ERR_WORKSPACE, "run_steady_noalloc: this run needs " + std::to_string(w.bytes) +

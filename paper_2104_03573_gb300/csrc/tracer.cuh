@@ -60,6 +60,7 @@ struct RunCfg {
   // [0] sum of X at the k-th relaxation, [1] its square, [2] sum of the final
   // X of trajectories with exactly k - 1 relaxations, [3] its square
   double* nscat_acc;    // [G][n_scat_max + 1][4]
+  int det_nb;           // steady detector sums per detector (1) or per detector and bin (n_bins)
 };
 
 // Transient detector region (Sec. 4.5): a closed axis-aligned cuboid split
@@ -872,7 +873,7 @@ __device__ __forceinline__ void region_steady(const Particle<R>& p, R seg, const
   for (int k = 0; k < C.n_regs; ++k) {
     const DetRegion& r = C.regs[k];
     region_track<R>(r, p.x, w3, R(0), R(0), dt, [&](uint32_t d, R dur) {
-      T.det_add(((size_t)r.off + d) * 4, p.s * dur, ((p.s * v) * dur) * p.u[0], ((p.s * v) * dur) * p.u[1],
+      T.det_add((((size_t)r.off + d) * (size_t)C.det_nb + (C.det_nb > 1 ? (size_t)p.bin : 0)) * 4, p.s * dur, ((p.s * v) * dur) * p.u[0], ((p.s * v) * dur) * p.u[1],
                 ((p.s * v) * dur) * p.u[2]);
     });
   }

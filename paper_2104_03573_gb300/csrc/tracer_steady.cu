@@ -441,18 +441,20 @@ __global__ void k_finalize_steady(const GeoRun* geos, MatView M, RunCfg C, Acc A
     }
   }
   if (O.det && C.n_regs > 0) {
-    // detector regions: volume-averaged T and q of each detector
+    // detector regions: volume-averaged T and q of each detector (and bin)
     const double C_tot_d = M.sums[0];
-    for (uint32_t d = threadIdx.x; d < C.n_det; d += blockDim.x) {
+    const size_t nb = C.det_nb > 1 ? (size_t)C.det_nb : 1;
+    for (size_t s = threadIdx.x; s < (size_t)C.n_det * nb; s += blockDim.x) {
+      const uint32_t d = (uint32_t)(s / nb);
       double vd = C.regs[0].v_det;
       for (int k = 0; k < C.n_regs; ++k)
         if (d >= C.regs[k].off) vd = C.regs[k].v_det;
       const double kT = E_eff / (C_tot_d * vd);
       const double kq = E_eff / vd;
       double raw[4];
-      for (int b = 0; b < 4; ++b) raw[b] = A.det_raw[(size_t)d * 4 + b] + (double)A.det_q[(size_t)d * 4 + b] * kFxInv;
-      O.det[(size_t)d * 4 + 0] = (kT * raw[0]) * 1e-12;
-      for (int b = 1; b < 4; ++b) O.det[(size_t)d * 4 + b] = (kq * raw[b]) * 1e-9;
+      for (int b = 0; b < 4; ++b) raw[b] = A.det_raw[s * 4 + b] + (double)A.det_q[s * 4 + b] * kFxInv;
+      O.det[s * 4 + 0] = (kT * raw[0]) * 1e-12;
+      for (int b = 1; b < 4; ++b) O.det[s * 4 + b] = (kq * raw[b]) * 1e-9;
     }
   }
   if (O.kn && C.nscat_acc && threadIdx.x == 0) {

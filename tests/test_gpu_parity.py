@@ -651,3 +651,52 @@ def test_nscat_curve_rejected_with_gradient_and_without_output():
     with pytest.raises(L.MCBTEError) as e:
         api.run_steady(M, [G], [100], replace(cfg, n_scat_max=0))
     assert e.value.status == L.ERR_INVALID_ARG
+
+
+def test_steady_detectors_per_frequency_bin():
+    m = W.bvk_holland(n_per_branch=20)
+    wl = W.si_slab_c2(n=20_000, material=m)
+    g, run = wl.geometries[0], wl.run
+    Lb = g.L
+    tiles = ((0.0, Lb[0], 0.0, Lb[1], 0.0, Lb[2]), (2, 2, 4))
+    sub = ((0.1 * Lb[0], 0.7 * Lb[0], 0.0, Lb[1], 0.25 * Lb[2], 0.75 * Lb[2]), (2, 1, 3))
+    run = replace(run, regions=[tiles, sub])
+    M, G = api.Material(m), api.Geometry(g)
+    base = dict(seed=run.seed, n_cells=run.n_cells, cell_axis=2, tally_axis=2, per_bin=True,
+                max_events=run.max_events, regions=run.regions, det_per_bin=True)
+    o = api.run_steady(M, [G], [run.n], api.SteadyConfig(precision=L.FP64_PLAIN, **base))
+    torch.cuda.synchronize()
+    ref = oracle.run_steady(m, g, run, det_per_bin=True)
+    d = o.det.cpu().numpy()
+    assert d.shape == (22, m.n_bins, 4)
+    ok, err = rel_close(d[..., 0], ref["det_T"], RTOL)
+    assert ok, err
+    ok, err = rel_close(d[..., 1:], ref["det_q"], RTOL)
+    assert ok, err
+    # host outputs through the C ABI carry the same array
+    h = api.run_steady_host(M, [G], [run.n], api.SteadyConfig(precision=L.FP64_PLAIN, **base))
+    assert h["stats"][0, L.STAT_KAPPA] == pytest.approx(o.stats[0, L.STAT_KAPPA].item(), rel=1e-12)
+    ok, err = rel_close(h["det"], d, RTOL)
+    assert ok, err
+    # FP32: the bins of each detector sum to the detector total of a run
+    # without the split (exact fixed-point sums, same trajectories)
+    c32 = api.SteadyConfig(precision=L.FP32_TRACE, **base)
+    o32 = api.run_steady(M, [G], [500_000], c32)
+    t32 = api.run_steady(M, [G], [500_000], replace(c32, det_per_bin=False))
+    torch.cuda.synchronize()
+    s = o32.det.sum(dim=1).cpu().numpy()
+    t = t32.det.cpu().numpy()
+    np.testing.assert_allclose(s, t, rtol=1e-9, atol=1e-12 * np.abs(t).max())
+    # and the tiles give back the frequency-resolved flux
+    vd = float(np.prod(Lb)) / 16
+    q_tiles = (vd * o32.det[:16, :, 3]).sum(dim=0).cpu().numpy() / float(np.prod(Lb))
+    qb = o32.q_bin[0].cpu().numpy()
+    np.testing.assert_allclose(q_tiles, qb, rtol=1e-6, atol=1e-9 * np.abs(qb).max())
+
+
+def test_det_per_bin_needs_regions():
+    wl = W.si_slab_c2(n=100)
+    M, G = api.Material(wl.material), api.Geometry(wl.geometries[0])
+    with pytest.raises(L.MCBTEError) as e:
+        api.run_steady(M, [G], [100], api.SteadyConfig(seed=1, precision=L.FP64_PLAIN, tally_axis=2, det_per_bin=True))
+    assert e.value.status == L.ERR_INVALID_ARG
