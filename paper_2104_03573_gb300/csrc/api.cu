@@ -153,12 +153,17 @@ mcbte_status mcbte_material_create(const mcbte_material_desc* d, mcbte_material*
   layout(probe);
   const size_t bytes = c.off;
   void* block = nullptr;
-  CUDA_TRY(cudaMalloc(&block, bytes));
+  // stream-ordered pool allocation (a plain cudaMalloc costs far more than
+  // the table build for a few thousand bins)
+  CUDA_TRY(cudaMallocAsync(&block, bytes, 0));
   c.off = 0;
   c.base = static_cast<char*>(block);
   MatBuild b{};
   layout(b);
-  auto cleanup = [&]() { cudaFree(block); };
+  auto cleanup = [&]() {
+    cudaFreeAsync(block, 0);
+    cudaStreamSynchronize(0);
+  };
   const size_t nb = (size_t)n * sizeof(double);
   cudaError_t e = cudaMemcpy((void*)b.omega, d->omega, nb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy((void*)b.v, d->v, nb, cudaMemcpyHostToDevice);
@@ -204,7 +209,10 @@ mcbte_status mcbte_material_create(const mcbte_material_desc* d, mcbte_material*
 
 void mcbte_material_destroy(mcbte_material* m) {
   if (!m) return;
-  cudaFree(m->block);
+  // the block returns to the pool once the work queued before this call is done
+  cudaDeviceSynchronize();
+  cudaFreeAsync(m->block, 0);
+  cudaStreamSynchronize(0);
   delete m;
 }
 

@@ -185,6 +185,7 @@ template <> struct Num<double> {
   static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
   static __device__ __forceinline__ void sincos2pi(double r, double* s, double* c) { series_sincos2pi(r, s, c); }
   static __device__ __forceinline__ double fmax_(double a, double b) { return fmax(a, b); }
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
   static __device__ __forceinline__ double big() { return 1.0e300; }
   static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
 };
@@ -203,6 +204,9 @@ template <> struct Num<float> {
     __sincosf(6.28318530717958647f * r, s, c);
   }
   static __device__ __forceinline__ float fmax_(float a, float b) { return fmaxf(a, b); }
+  // distances for the first hit: the 2-ulp hardware quotient (the particle
+  // is set onto the face it hits, so the quotient's last bits move nothing)
+  static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
   static __device__ __forceinline__ float big() { return 3.0e38f; }
   static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
 };
@@ -294,8 +298,8 @@ __device__ __forceinline__ void first_hit(const GeoRun& g, const R x[3], const R
     R d;
     int f;
     const R La = geo_L<R>(g, a);
-    if (u[a] > R(0)) { d = (La - x[a]) / u[a]; f = axis_max_face(a); }
-    else if (u[a] < R(0)) { d = (R(0) - x[a]) / u[a]; f = axis_min_face(a); }
+    if (u[a] > R(0)) { d = Num<R>::div(La - x[a], u[a]); f = axis_max_face(a); }
+    else if (u[a] < R(0)) { d = Num<R>::div(R(0) - x[a], u[a]); f = axis_min_face(a); }
     else continue;
     if (d < R(0)) d = R(0);
     if (d < best || (d == best && f < bf)) { best = d; bf = f; }

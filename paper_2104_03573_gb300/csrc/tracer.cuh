@@ -11,6 +11,8 @@
 //                       sub 3+k {position attempt k; Gaussian: Box-Muller words}
 //   relaxation event  : sub 0 {alias column, threshold lo, mu, phi}
 //                       sub 1 {threshold hi, flight -ln R lo, hi}
+//                       FP32 path with at most kOneBlockBins bins: sub 0 only,
+//                       {alias column and its 32-bit test word, flight -ln R, mu, phi}
 //   adiabatic / pore  : sub 0 {specular test, -, mu, phi}
 //   isothermal / periodic walls draw nothing.
 #pragma once
@@ -233,6 +235,25 @@ __device__ __forceinline__ void resample(Particle<R>& p, const MatView& M, const
   else dir_about_axis<R>(p.u, axis, sgn, mu, w.w);
   load_bin(p, M, binf);
   p.d_rel = p.lam * (-Num<R>::log_(Num<R>::oc53(w1.y, w1.z)));
+}
+
+// FP32 relaxation from one Philox block (tables of at most kOneBlockBins
+// bins): word 0 times n gives the alias column (high half) and a 32-bit
+// uniform for its test (low half, compared with the threshold's high word:
+// the acceptance is off by at most n / 2^32), word 1 the flight, words 2 and
+// 3 the isotropic direction.  A 24-bit flight uniform is all FP32 resolves.
+constexpr int kOneBlockBins = 65536;
+
+template <typename R>
+__device__ __forceinline__ void resample_relax1(Particle<R>& p, const MatView& M, const uint4* rec, const float4* binf,
+                                                uint4 w) {
+  const uint64_t m = (uint64_t)w.x * (uint64_t)M.n;
+  const int col = (int)(m >> 32);
+  const uint4 a = rec[col];
+  p.bin = ((uint32_t)m < a.y) ? col : (int)a.z;
+  dir_about_axis<R>(p.u, 2, R(1), R(1) - R(2) * Num<R>::oc(w.z), w.w);
+  load_bin(p, M, binf);
+  p.d_rel = p.lam * (-Num<R>::log_(Num<R>::oc(w.y)));
 }
 
 // Emission-only part of event 0 (Sec. 3.2: source by cumulative energy,
@@ -779,9 +800,13 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
     // the relaxation period in this bin is over: frequency-resolved flux
     T.period_end(p);
     const uint4 w = philox(ctr, k0, k1);
-    ctr.w = 1u;
-    const uint4 w1 = philox(ctr, k0, k1);
-    resample<R>(p, M, rec_relax, binf, w, w1, false, 2, R(1));
+    if (sizeof(R) == 4 && M.n <= kOneBlockBins) {
+      resample_relax1<R>(p, M, rec_relax, binf, w);
+    } else {
+      ctr.w = 1u;
+      const uint4 w1 = philox(ctr, k0, k1);
+      resample<R>(p, M, rec_relax, binf, w, w1, false, 2, R(1));
+    }
     if constexpr (EXT) p.d2 = draw_d2(p, M, binf, k0, k1);   // both clocks restart in the new mode (Sec. 3.3 (i))
     if (Grad::on) gr.resampled(p.bin, Xnow);
     return STEP_ALIVE;

@@ -159,13 +159,18 @@ def test_pore_grad_full_size_replay_and_crn_differences():
     torch.cuda.synchronize()
     assert fwd.stats[0, L.STAT_STATUS].item() == 0       # every replayed particle reproduced its tally
     d, d_se = go.dkappa_dir[0].cpu().numpy()
-    # common random numbers: kappa(tau e^{+h}) - kappa(tau e^{-h}) over 2h
+    # common random numbers: kappa(tau e^{+h}) - kappa(tau e^{-h}) over 2h,
+    # with its own standard error from the per-particle differences (the two
+    # runs share their random words but not every trajectory)
     h = 0.05
-    ks = []
+    ks, xs = [], []
     for sgn in (1.0, -1.0):
         m2 = replace(mat, tau=mat.tau * np.exp(sgn * h))
-        o = api.run_steady(api.Material(m2), [G], [run.n], cfg)
+        o = api.run_steady(api.Material(m2), [G], [run.n], cfg, per_particle=True)
         torch.cuda.synchronize()
         ks.append(o.stats[0, L.STAT_KAPPA].item())
+        xs.append(o.X_pp)
     fd = (ks[0] - ks[1]) / (2 * h)
-    assert abs(d - fd) < 4 * d_se + 0.01 * abs(fd), (d, d_se, fd)
+    dpp = (xs[0] - xs[1]) / (2 * h)
+    fd_se = abs(ks[0] / xs[0].sum().item()) * dpp.std().item() * np.sqrt(run.n)
+    assert abs(d - fd) < 4 * np.hypot(d_se, fd_se) + 0.002 * abs(fd), (d, d_se, fd, fd_se)
