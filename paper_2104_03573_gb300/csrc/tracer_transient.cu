@@ -123,6 +123,69 @@ __device__ __forceinline__ bool load_state(const uint4* st, uint64_t idx, Partic
   return true;
 }
 
+// Snapshots of a warp's flights, shared out over its 32 lanes.  Lane i
+// takes k_i snapshots this step (measurement indices p.mi .. p.mi + k_i - 1
+// of the flight that starts at p.x at time p.t); a lane's count depends on
+// its flight's length, so a per-lane loop would leave most lanes idle while
+// the longest flights sample.  Here the warp's k_1 + ... + k_32 snapshots are
+// taken 32 at a time: each lane finds the owner of its snapshot by a binary
+// search of the inclusive prefix sums and reads the owner's state by
+// shuffles.  Every lane of the warp must call this (k = 0 for idle lanes).
+// The arithmetic per snapshot is the per-lane loop's (Eq. sampling, Sec. 3.4).
+__device__ __forceinline__ void warp_snapshots(int k, const Particle<float>& p, const float* tmeas, const float* cinv,
+                                               const RunCfg& C, double* snap) {
+  constexpr unsigned kAll = 0xffffffffu;
+  const int lane = (int)(threadIdx.x & 31u);
+  int incl = k;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kAll, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(kAll, incl, 31);
+  const int nx = C.grid[0], ny = C.grid[1], nz = C.grid[2];
+  const size_t ncell = (size_t)nx * ny * nz;
+  for (int base = 0; base < total; base += 32) {
+    const int j = base + lane;
+    // owner: the first lane whose inclusive sum exceeds j (always in 0..31)
+    int own = 0;
+#pragma unroll
+    for (int st = 16; st >= 1; st >>= 1) {
+      const int v = __shfl_sync(kAll, incl, own + st - 1);
+      if (v <= j) own += st;
+    }
+    const int first = __shfl_sync(kAll, incl - k, own);
+    const int mi0 = __shfl_sync(kAll, p.mi, own);
+    const float x0 = __shfl_sync(kAll, p.x[0], own), x1 = __shfl_sync(kAll, p.x[1], own),
+                x2 = __shfl_sync(kAll, p.x[2], own);
+    const float u0 = __shfl_sync(kAll, p.u[0], own), u1 = __shfl_sync(kAll, p.u[1], own),
+                u2 = __shfl_sync(kAll, p.u[2], own);
+    const float t0 = __shfl_sync(kAll, p.t, own), v = __shfl_sync(kAll, p.v, own),
+                s = __shfl_sync(kAll, p.s, own);
+    if (j < total) {
+      const int m = mi0 + (j - first);
+      const float dist = v * (tmeas[m] - t0);
+      const float pm0 = x0 + dist * u0, pm1 = x1 + dist * u1, pm2 = x2 + dist * u2;
+      const int ix = min(max((int)floorf(pm0 * cinv[0]), 0), nx - 1);
+      const int iy = min(max((int)floorf(pm1 * cinv[1]), 0), ny - 1);
+      const int iz = min(max((int)floorf(pm2 * cinv[2]), 0), nz - 1);
+      const size_t c = ((size_t)m * ncell + ((size_t)iz * ny + iy) * nx + ix) * 4;
+      long long* q = reinterpret_cast<long long*>(snap) + c;
+      const float sv = s * v;
+      red_s64(q + 0, s > 0.0f ? 1ll : -1ll);
+      if (v < 1024.0f) {
+        red_s64(q + 1, (long long)__float2int_rn((sv * u0) * kFx));
+        red_s64(q + 2, (long long)__float2int_rn((sv * u1) * kFx));
+        red_s64(q + 3, (long long)__float2int_rn((sv * u2) * kFx));
+      } else {
+        red_s64(q + 1, fx(sv * u0));
+        red_s64(q + 2, fx(sv * u1));
+        red_s64(q + 3, fx(sv * u2));
+      }
+    }
+  }
+}
+
 // Shared memory: the measurement times as float (always), then the relaxation
 // alias records and per-bin constants where the plan has room.
 template <int TPB, bool EXT>
@@ -160,6 +223,98 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
   bool drained = false;   // as in the steady tracer: idle lanes stay until the warp is drained
   uint64_t idx = 0;
   constexpr unsigned kAll = 0xffffffffu;
+  if (C.n_regs == 0 && !C.time_average) {
+    // Snapshots on the whole-box grid: every lane of a warp runs every step
+    // (no lane skips ahead to the next refill), so that the warp can share
+    // out its snapshots (warp_snapshots).  Flight and event as in
+    // step_transient.
+    for (;;) {
+      if (__all_sync(kAll, drained)) break;
+      const unsigned need = __ballot_sync(kAll, !alive && !drained);
+      if (need) {
+        const int leader = __ffs(need) - 1;
+        unsigned long long base = 0;
+        if ((int)lane == leader) {
+          base = atomicAdd(A.work, (unsigned long long)__popc(need));
+          if (((base + (unsigned long long)__popc(need)) >> 12) != (base >> 12) && globaltimer_ns() > deadline)
+            atomicOr(A.flags, 1);
+        }
+        base = __shfl_sync(kAll, base, leader);
+        if (!alive && !drained) {
+          idx = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
+          if (idx >= C.total || (*(volatile int*)A.flags & 1)) {
+            drained = true;
+          } else if (C.win_first) {
+            p.pid = (uint32_t)idx;
+            p.g = 0;
+            emit<float, EXT>(p, G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, true, (float)C.t_max_ps);
+            transient_start(p, C);
+            if (!C.win_last && p.mi >= C.win_end) save_state(A.tstate, idx, p);   // emitted after this window
+            else alive = true;
+          } else if (load_state(A.tstate, idx, p, M, binf, C)) {
+            alive = true;
+          }
+        }
+      }
+      // the flight: nearest of t_max, the clocks and the boundary (Sec. 3.3,
+      // Sec. 3.5.6), and how many measurement times it covers
+      int out = STEP_ALIVE, k = 0, face = 0;
+      bool fin = false, rlx = false, rlx2 = false;
+      float seg = 0.0f, t_end = 0.0f;
+      if (alive) {
+        if (p.e + 1u >= C.max_events) {
+          out = STEP_TRUNCATED;
+        } else {
+          float db;
+          first_hit<float, EXT>(G, p.x, p.u, &db, &face);
+          const float tmax = (float)C.t_max_ps;
+          const float d_end = (tmax - p.t) * p.v;
+          if (d_end <= p.d_rel && d_end <= db && (!EXT || d_end <= p.d2)) { fin = true; seg = d_end; }
+          else if (p.d_rel < db && (!EXT || p.d_rel <= p.d2)) { rlx = true; seg = p.d_rel; }
+          else if (EXT && p.d2 < db) { rlx2 = true; seg = p.d2; }
+          else { seg = db; }
+          t_end = fin ? tmax : p.t + seg * p.inv_v;
+          // the measurement times in [t, t_end) (closed at t_max): the first
+          // index from p.mi on that is not covered, by bisection
+          int lo = p.mi, hi = C.n_times;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            const bool cov = fin ? (tmeas[mid] <= t_end) : (tmeas[mid] < t_end);
+            if (cov) lo = mid + 1; else hi = mid;
+          }
+          k = lo - p.mi;
+        }
+      }
+      warp_snapshots(k, p, tmeas, cinv, C, A.snap);
+      if (!alive) continue;
+      if (out == STEP_ALIVE) {
+        p.mi += k;
+        p.t = t_end;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
+        if (fin) {
+          out = STEP_DONE;
+        } else {
+          GradOff off;
+          out = apply_event<float, GradOff, TallyNone, EXT>(p, G, M, relax, binf, C, key.x, key.y, rlx, rlx2, face, seg,
+                                                            TallyNone(), off, 0.0);
+        }
+      }
+      if (out == STEP_ALIVE && (p.e & 255u) == 0u && globaltimer_ns() > deadline) {
+        atomicOr(A.flags, 1);
+        out = STEP_TRUNCATED;
+      }
+      if (out != STEP_ALIVE) {
+        transient_finish(p, out, idx, A);
+        if (!C.win_last) mark_done(A.tstate, idx);
+        alive = false;
+      } else if (!C.win_last && p.mi >= C.win_end) {
+        save_state(A.tstate, idx, p);
+        alive = false;
+      }
+    }
+    return;
+  }
   for (;;) {
     if (__all_sync(kAll, drained)) break;
     const unsigned need = __ballot_sync(kAll, !alive && !drained);
