@@ -299,11 +299,19 @@ def _workload_setup(name, args, seed_offset):
             Mh, Gh = api.Material(mat), api.Geometry(geo)
             f3, g3 = api.grad(Mh, Gh, run.n, replace(cfg, trace_events=None))
             return f3.stats.cpu().numpy(), g3.dkappa_dlogtau.cpu().numpy()
+        def nscat_check():
+            # N_scat_max convergence check of this workload (the pore lattice's
+            # truncation biases kappa): one run with N_scat_max = 40, kappa at 10/20/40
+            c = replace(cfg, n_scat_max=40, nscat_curve=True, trace_events=None)
+            o = api.run_steady(M, [G], [run.n], c)
+            kn = o.kappa_nscat[0].cpu().numpy()
+            return {"n_scat_max": [10, 20, 40], "kappa": [float(kn[k - 1, 0]) for k in (10, 20, 40)],
+                    "kappa_se": [float(kn[k - 1, 1]) for k in (10, 20, 40)], "particles": int(run.n)}
         desc = ("nanoporous film: 100 nm cell, cylindrical pore porosity 0.25, 200 nm thick, diffuse walls, "
                 "grad_T -1e6 K/m along y, N_scat_max 10; forward + gradient: likelihood ratio over 3000 "
                 "log-tau scales, measure-valued d kappa / d p_pore at p = 0 (every particle that meets the "
                 "pore is traced once more with one pore hit specular)")
-        return dict(mat=mat, geo=geo, run=run, n=run.n, step=step, fp64=fp64, e2e=e2e, gout=go,
+        return dict(mat=mat, geo=geo, run=run, n=run.n, step=step, fp64=fp64, e2e=e2e, gout=go, check=nscat_check,
                     d2h=8 * (M.n_bins * 2 + 2 + L.NSTATS), h2d=_material_bytes(mat) + ctypes.sizeof(L.GeometryDesc) + 8,
                     desc=desc, launches=3, timer=tm, kernel="k_steady_f32 (grad)",
                     shape={"threads_per_block": cfg.threads_per_block, "refill_threshold": cfg.refill_threshold},
@@ -384,13 +392,22 @@ def _workload_setup(name, args, seed_offset):
                                                    None), allow=(LL.OK, LL.WARN_TRUNCATED))
             return st[None, :]
         nt = len(run.t_meas) * run.grid[0] * run.grid[1] * run.grid[2] * 4 * 8
+        # time windows of the FP32 run (the library's automatic choice: the
+        # largest window whose tally slice fits a third of the L2)
+        slice_b = run.grid[0] * run.grid[1] * run.grid[2] * 4 * 8
+        l2 = int(getattr(torch.cuda.get_device_properties(torch.cuda.current_device()), "L2_cache_size", 96 << 20))
+        wt = max(1, min(len(run.t_meas), (l2 // 3) // slice_b))
+        windows = -(-len(run.t_meas) // wt)
         desc = ("transient 2x2x1 um diffuse adiabatic box, +1 K Gaussian sigma 100 nm at the top-face centre, "
                 "64x64x32 cells x 200 " + ("10 ps bin averages" if run.time_average else "snapshots (10 ps)")
                 + ", FP32 flights, fixed-point tallies in L2-sized time windows")
         return dict(mat=mat, geo=geo, run=run, n=run.n, step=step, fp64=fp64, e2e=e2e, d2h=nt + 8 * L.NSTATS,
                     h2d=_material_bytes(mat) + ctypes.sizeof(L.GeometryDesc) + 8 * len(run.t_meas), desc=desc,
-                    launches=3, timer=tm, kernel="k_transient_f32", shape={"threads_per_block": cfg.threads_per_block},
-                    kappa=False, kind="transient")
+                    launches=2 + windows, timer=tm, kernel="k_transient_f32",
+                    shape={"threads_per_block": cfg.threads_per_block, "time_windows": windows},
+                    kappa=False, kind="transient",
+                    # adiabatic box: every particle lives to t_max, so it is sampled at all n_times
+                    tally_ops=run.n * len(run.t_meas), l2_slice_words=wt * slice_b // 8)
     raise ValueError(name)
 
 
@@ -447,6 +464,8 @@ def run_ours(args):
         t_1pct = float(t_step * np.max((se / np.abs(k) / 0.01) ** 2))
     dkdp = [float(x) for x in wk["gout"].dkappa_dp.cpu().numpy()] if "gout" in wk else None
     curve = None
+    check = wk["check"]() if "check" in wk else None
+    l2 = l2_reduction_roofline(wk, t_kern_probe(kern_ms)) if "tally_ops" in wk else None
     if "curve" in wk:
         kn = wk["curve"].kappa_nscat[0].cpu().numpy()
         kfin, sfin = kn[-1]
@@ -508,6 +527,11 @@ def run_ours(args):
         "events_per_step": ev_step, "wall_s": wall_max,
         **({"dkappa_dp_pore": dkdp} if dkdp is not None else {}),
         **({"kappa_nscat": curve} if curve is not None else {}),
+        **({"nscat_check": check} if check is not None else {}),
+        **({"l2_reductions": l2} if l2 is not None else {}),
+        **({"tally_ops_per_s": {"value": wk["tally_ops"] * args.steps * ws / t_ranks,
+                                "what": "snapshot tallies (4 atomics each) per second"}}
+           if "tally_ops" in wk else {}),
         "fp64_plain": fp64,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
                      "frac": achieved / peak_tinst,
@@ -524,6 +548,39 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def t_kern_probe(kern_ms):
+    return sum(kern_ms) / len(kern_ms) / 1e3
+
+
+def l2_reduction_roofline(wk, t_kern):
+    """Snapshot-bound transient runs: the 64-bit L2 reductions the tracing
+    kernels issue per second (4 per snapshot) against the rate the library's
+    probe reaches in the same pattern on an array the size of one time
+    window's tally slice (best of 3 timed launches)."""
+    import torch
+    from paper_2104_03573_gb300 import _lib as L
+    words = int(wk["l2_slice_words"]) // 4 * 4
+    slots = torch.zeros(words, dtype=torch.int64, device="cuda")
+    groups = 1 << 28
+    lib = L.load()
+    s = torch.cuda.current_stream()
+    L.check(lib.mcbte_l2_reduction_probe(slots.data_ptr(), words, groups // 16, ctypes.c_void_p(s.cuda_stream)))
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        L.check(lib.mcbte_l2_reduction_probe(slots.data_ptr(), words, groups, ctypes.c_void_p(s.cuda_stream)))
+        e1.record(s)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        best = t if best is None else min(best, t)
+    peak = 4.0 * groups / best / 1e9
+    achieved = 4.0 * wk["tally_ops"] / t_kern / 1e9
+    return {"achieved": achieved, "peak": peak, "unit": "G reductions/s", "frac": achieved / peak,
+            "peak_basis": f"mcbte_l2_reduction_probe: 2^28 groups of 4 64-bit reductions into a "
+                          f"{words * 8 / 2**20:.0f} MiB array (one time window's tally slice), best of 3"}
 
 
 def cpu_baseline(wk, args, target_s=None):

@@ -738,6 +738,15 @@ mcbte_status mcbte_run_steady(const mcbte_material* m, const mcbte_geometry* con
   return steady_impl(m, geoms, n_geoms, p, out, nullptr, workspace, workspace_bytes, (cudaStream_t)stream);
 }
 
+mcbte_status mcbte_l2_reduction_probe(long long* slots, uint64_t n_slots, uint64_t n_groups, mcbte_stream stream) {
+  if (!slots || n_slots < 4 || (n_slots & 3u) != 0)
+    return fail(MCBTE_ERR_INVALID_ARG, "l2_reduction_probe: n_slots must be a positive multiple of 4");
+  if (n_groups == 0) return MCBTE_OK;
+  CUDA_TRY(launch_l2_reduction_probe(reinterpret_cast<unsigned long long*>(slots), n_slots / 4, n_groups,
+                                     (cudaStream_t)stream));
+  return MCBTE_OK;
+}
+
 mcbte_status mcbte_grad(const mcbte_material* m, const mcbte_geometry* g, const mcbte_steady_params* p,
                         const mcbte_steady_out* fwd, const mcbte_grad_out* grad, void* workspace,
                         size_t workspace_bytes, mcbte_stream stream) {

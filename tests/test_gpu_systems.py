@@ -10,6 +10,7 @@
   central finite differences under common random numbers.
 """
 import math
+import ctypes
 
 import numpy as np
 import pytest
@@ -287,3 +288,15 @@ def test_fp32_axis_only_cell_tallies_equal_the_full_ones():
     assert torch.count_nonzero(axis.q[..., :2]) == 0
     assert torch.equal(axis.q_bin, full.q_bin)
     assert torch.equal(axis.stats[:, L.STAT_SUMX], full.stats[:, L.STAT_SUMX])
+
+
+def test_l2_reduction_probe_adds_exactly():
+    slots = torch.zeros(4096, dtype=torch.int64, device="cuda")
+    lib = L.load()
+    s = torch.cuda.current_stream()
+    L.check(lib.mcbte_l2_reduction_probe(slots.data_ptr(), 4096, 100_003, ctypes.c_void_p(s.cuda_stream)))
+    torch.cuda.synchronize()
+    assert int(slots.sum().item()) == 4 * 100_003
+    r = slots.view(-1, 4)
+    assert torch.equal(r[:, 0], r[:, 3])          # the four words of a record move together
+    assert int((r[:, 0] > 0).sum().item()) > 900   # the groups spread over the records
