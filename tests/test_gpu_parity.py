@@ -700,3 +700,41 @@ def test_det_per_bin_needs_regions():
     with pytest.raises(L.MCBTEError) as e:
         api.run_steady(M, [G], [100], api.SteadyConfig(seed=1, precision=L.FP64_PLAIN, tally_axis=2, det_per_bin=True))
     assert e.value.status == L.ERR_INVALID_ARG
+
+
+def test_nscat_curve_per_geometry_in_a_batch():
+    # the curve's accumulators are kept per geometry: three films of one
+    # batched launch, each against the oracle run of that film alone
+    wl = W.film_batch_c4(n_films=3)
+    mat, run = wl.material, wl.run
+    run.max_events = 2_000_000
+    ns = [700, 257, 1000]
+    M = api.Material(mat)
+    Gs = [api.Geometry(g) for g in wl.geometries]
+    cfg = api.SteadyConfig(seed=run.seed, precision=L.FP64_PLAIN, tally_axis=run.tally_axis,
+                           n_scat_max=run.n_scat_max, max_events=run.max_events, nscat_curve=True)
+    o = api.run_steady(M, Gs, ns, cfg)
+    torch.cuda.synchronize()
+    kn = o.kappa_nscat.cpu().numpy()
+    assert kn.shape == (3, run.n_scat_max, 2)
+    for f in range(3):
+        ref = oracle.run_steady(mat, wl.geometries[f], run, n_total=ns[f], batch_index=f, nscat_curve=True)
+        ok, err = rel_close(kn[f], ref["kappa_nscat"], RTOL)
+        assert ok, (f, err)
+
+
+def test_fp32_measure_valued_specularity_gradient_at_p1():
+    wl = W.pore_film_c5(n=100_000, p_pore=1.0)
+    mat, g, run = wl.material, wl.geometries[0], wl.run
+    run.max_events = 20_000_000
+    M, G = api.Material(mat), api.Geometry(g)
+    cfg = api.SteadyConfig(seed=820, precision=L.FP32_TRACE, n_scat_max=run.n_scat_max,
+                           max_events=run.max_events, tally_axis=run.tally_axis, per_bin=True)
+    fwd, go = api.grad(M, G, run.n, cfg)
+    torch.cuda.synchronize()
+    assert fwd.stats[0, L.STAT_STATUS].item() == 0
+    run.seed = 821
+    ref = oracle.run_steady(mat, g, run, grad=True)     # measure-valued at p = 1
+    gp = go.dkappa_dp.cpu().numpy()
+    assert np.isfinite(gp).all() and gp[1] > 0
+    assert abs(gp[0] - ref["dkappa_dp"]) < 4 * np.hypot(gp[1], ref["dkappa_dp_se"])
