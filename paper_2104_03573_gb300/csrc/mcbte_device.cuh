@@ -293,16 +293,32 @@ template <typename R, bool EXT = true>
 __device__ __forceinline__ void first_hit(const GeoRun& g, const R x[3], const R u[3], R* dist, int* face) {
   R best = Num<R>::big();
   int bf = 7;
+  if constexpr (sizeof(R) == 4) {
+    // FP32: the three face distances without branches (the quotients are
+    // independent, so their latencies overlap); the same candidates and ties
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    R d;
-    int f;
-    const R La = geo_L<R>(g, a);
-    if (u[a] > R(0)) { d = Num<R>::div(La - x[a], u[a]); f = axis_max_face(a); }
-    else if (u[a] < R(0)) { d = Num<R>::div(R(0) - x[a], u[a]); f = axis_min_face(a); }
-    else continue;
-    if (d < R(0)) d = R(0);
-    if (d < best || (d == best && f < bf)) { best = d; bf = f; }
+    for (int a = 0; a < 3; ++a) {
+      const R ua = u[a];
+      const bool up = ua > R(0);
+      const R d0 = Num<R>::div((up ? geo_L<R>(g, a) : R(0)) - x[a], ua);
+      const R d = d0 < R(0) ? R(0) : d0;
+      const int f = up ? axis_max_face(a) : axis_min_face(a);
+      const bool take = ua != R(0) && (d < best || (d == best && f < bf));
+      best = take ? d : best;
+      bf = take ? f : bf;
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      R d;
+      int f;
+      const R La = geo_L<R>(g, a);
+      if (u[a] > R(0)) { d = Num<R>::div(La - x[a], u[a]); f = axis_max_face(a); }
+      else if (u[a] < R(0)) { d = Num<R>::div(R(0) - x[a], u[a]); f = axis_min_face(a); }
+      else continue;
+      if (d < R(0)) d = R(0);
+      if (d < best || (d == best && f < bf)) { best = d; bf = f; }
+    }
   }
   if (g.pore) {
     const R cx = sizeof(R) == 8 ? (R)g.cx : (R)g.cxf;
