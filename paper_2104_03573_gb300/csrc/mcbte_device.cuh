@@ -327,7 +327,17 @@ __device__ __forceinline__ void first_hit(const GeoRun& g, const R x[3], const R
     const R dx = x[0] - cx, dy = x[1] - cy;
     const R a = u[0] * u[0] + u[1] * u[1];
     const R b = dx * u[0] + dy * u[1];
-    if (a > R(0) && b < R(0)) {
+    if constexpr (sizeof(R) == 4) {
+      // FP32: the same test and root with selects instead of branches
+      const R c = (dx * dx + dy * dy) - r2;
+      const R disc = b * b - a * c;
+      const bool hit = a > R(0) && b < R(0) && disc >= R(0);
+      const R d0 = Num<R>::div(c, Num<R>::sqrt_(Num<R>::fmax_(disc, R(0))) - b);
+      const R d = d0 < R(0) ? R(0) : d0;
+      const bool take = hit && d < best;
+      best = take ? d : best;
+      bf = take ? 6 : bf;
+    } else if (a > R(0) && b < R(0)) {
       const R c = (dx * dx + dy * dy) - r2;
       const R disc = b * b - a * c;
       if (disc >= R(0)) {

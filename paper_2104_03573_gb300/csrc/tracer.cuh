@@ -838,7 +838,15 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
     }
     put3<R>(p.x, a, mx ? La : R(0));
     const uint4 w = philox(ctr, k0, k1);
-    if ((uint64_t)w.x < ((EXT && ((g.fbin >> face) & 1)) ? M.spec_thr[p.bin] : g.pthr[face])) {
+    const bool spec_f = (uint64_t)w.x < ((EXT && ((g.fbin >> face) & 1)) ? M.spec_thr[p.bin] : g.pthr[face]);
+    if constexpr (sizeof(R) == 4) {
+      // FP32: both outcomes, then a select (no branch on the draw)
+      R ud[3];
+      dir_about_axis<R>(ud, a, mx ? R(-1) : R(1), Num<R>::sqrt_(Num<R>::oc(w.z)), w.w);
+      const R flip = -sel3(p.u, a);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) p.u[b] = spec_f ? (b == a ? flip : p.u[b]) : ud[b];
+    } else if (spec_f) {
       put3<R>(p.u, a, -sel3(p.u, a));
     } else {
       dir_about_axis<R>(p.u, a, mx ? R(-1) : R(1), Num<R>::sqrt_(Num<R>::oc(w.z)), w.w);
@@ -870,7 +878,19 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
     spec = (uint64_t)w.x < g.pthr_pore;
     if (Grad::on) spec = gr.pore_branch(spec, g.p_pore, Xnow, ctr, k0, k1);
   }
-  if (spec) {
+  if constexpr (sizeof(R) == 4) {
+    // FP32: both outcomes, then a select (no branch on the draw)
+    const R un = p.u[0] * nx + p.u[1] * ny;
+    const R mu = Num<R>::sqrt_(Num<R>::oc(w.z));
+    const R sn = Num<R>::sqrt_(Num<R>::fmax_(R(0), R(1) - mu * mu));
+    R sphi, cphi;
+    Num<R>::sincos2pi(Num<R>::co(w.w), &sphi, &cphi);
+    const R sc = sn * cphi;
+    const R s0 = p.u[0] - (R(2) * un) * nx, s1 = p.u[1] - (R(2) * un) * ny;
+    p.u[0] = spec ? s0 : mu * nx - sc * ny;
+    p.u[1] = spec ? s1 : mu * ny + sc * nx;
+    p.u[2] = spec ? p.u[2] : sn * sphi;
+  } else if (spec) {
     const R un = p.u[0] * nx + p.u[1] * ny;
     p.u[0] = p.u[0] - (R(2) * un) * nx;
     p.u[1] = p.u[1] - (R(2) * un) * ny;
