@@ -354,10 +354,22 @@ __device__ __forceinline__ void first_hit(const GeoRun& g, const R x[3], const R
     const R nx = sizeof(R) == 8 ? (R)g.snx[k] : (R)g.snxf[k];
     const R ny = sizeof(R) == 8 ? (R)g.sny[k] : (R)g.snyf[k];
     const R un = u[0] * nx + u[1] * ny;
-    if (!(un < R(0))) continue;
     const R x1 = sizeof(R) == 8 ? (R)g.sx1[k] : (R)g.sx1f[k];
     const R y1 = sizeof(R) == 8 ? (R)g.sy1[k] : (R)g.sy1f[k];
     const R dn = (x[0] - x1) * nx + (x[1] - y1) * ny;
+    if constexpr (sizeof(R) == 4) {
+      // FP32: every wall's candidate computed, the valid nearest selected
+      const R d0 = Num<R>::div(dn, -un);
+      const R d = d0 < R(0) ? R(0) : d0;
+      const R tx = g.sx2f[k] - x1;
+      const R ty = g.sy2f[k] - y1;
+      const R hs = ((x[0] + d * u[0]) - x1) * tx + ((x[1] + d * u[1]) - y1) * ty;
+      const bool take = un < R(0) && !(dn < -tol) && !(hs < R(0) || hs > tx * tx + ty * ty) && d < best;
+      best = take ? d : best;
+      bf = take ? 7 + k : bf;
+      continue;
+    }
+    if (!(un < R(0))) continue;
     if (dn < -tol) continue;
     R d = dn / (-un);
     if (d < R(0)) d = R(0);
