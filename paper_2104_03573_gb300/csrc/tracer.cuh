@@ -541,11 +541,10 @@ struct TallyFxT {
     const int chi = min(max((int)(zhi * inv_h), 0), nc - 1);
     const float k = copysignf(__frcp_rn(fabsf(uz)), p.s);   // s / |u_z| exactly (s = +-1): per unit axial length
     const float f0 = k * p.inv_v, f1 = k * p.u[0], f2 = k * p.u[1], f3 = k * p.u[2];
-    if (clo == chi) {
-      add(cP + clo * 4, f0, f1, f2, f3, zhi - zlo);
-      return contrib;
-    }
-    add(cP + clo * 4, f0, f1, f2, f3, (float)(clo + 1) * h - zlo);
+    // the lower end's partial cell always (the whole flight when it stays in
+    // one cell); the upper end's and the run of full cells only when needed
+    add(cP + clo * 4, f0, f1, f2, f3, (clo == chi ? zhi : (float)(clo + 1) * h) - zlo);
+    if (clo == chi) return contrib;
     add(cP + chi * 4, f0, f1, f2, f3, zhi - (float)chi * h);
     if (chi > clo + 1) {
       add(cD + (clo + 1) * 4, f0, f1, f2, f3, h);

@@ -292,9 +292,11 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
   // the warp-wide votes below reconverge the warp at every event step.
   constexpr unsigned kAll = 0xffffffffu;
   for (;;) {
-    if (__all_sync(kAll, drained)) break;
-    const unsigned need = __ballot_sync(kAll, !alive && !drained);
+    // two votes per step: the drained lanes and the busy ones
+    const unsigned dry = __ballot_sync(kAll, drained);
+    if (dry == kAll) break;
     const unsigned live = __ballot_sync(kAll, alive);
+    const unsigned need = ~(dry | live);
     // refill once enough lanes are idle (or no lane is busy)
     if (need && (__popc(need) >= refill_min || live == 0u)) {
       const int leader = __ffs(need) - 1;
