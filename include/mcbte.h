@@ -186,7 +186,7 @@ enum {
   MCBTE_STAT_KAPPA_CELL,      /* kappa normalised by the full cell volume                 */
   MCBTE_STAT_SIGNED_EMITTED,  /* sum of emitted signs                                     */
   MCBTE_STAT_SIGNED_ABSORBED, /* sum of signs absorbed at isothermal walls                */
-  MCBTE_STAT_STATUS,          /* 0 ok, 4 timeout, 5 truncated                              */
+  MCBTE_STAT_STATUS,          /* 0 ok, 4 timeout, 5 truncated, 7 gradient replay mismatch  */
   MCBTE_STAT_N,               /* particles traced                                         */
   MCBTE_STAT_ABSORBED,        /* particles absorbed at isothermal walls                   */
   MCBTE_NSTATS = 16

@@ -186,6 +186,66 @@ __device__ __forceinline__ void warp_snapshots(int k, const Particle<float>& p, 
   }
 }
 
+// Time-bin averages of a warp's flights, shared out over its 32 lanes in the
+// same way: lane i contributes to the k_i bins m = p.mi .. p.mi + k_i - 1
+// that its flight [p.t, t_end) overlaps; each (flight, bin) pair is one item,
+// and the warp takes its items 32 at a time, every lane walking its item's
+// piece of flight through the detector grids (region_track) with the
+// owner's state read by shuffles.  Every lane of the warp must call this.
+// The arithmetic per item is the per-lane loop's in step_transient.
+__device__ __forceinline__ void warp_bin_averages(int k, float t_end, const Particle<float>& p, const float* tmeas,
+                                                  const RunCfg& C, double* snap) {
+  constexpr unsigned kAll = 0xffffffffu;
+  const int lane = (int)(threadIdx.x & 31u);
+  int incl = k;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kAll, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(kAll, incl, 31);
+  for (int base = 0; base < total; base += 32) {
+    const int j = base + lane;
+    int own = 0;
+#pragma unroll
+    for (int st = 16; st >= 1; st >>= 1) {
+      const int v = __shfl_sync(kAll, incl, own + st - 1);
+      if (v <= j) own += st;
+    }
+    const int first = __shfl_sync(kAll, incl - k, own);
+    const int mi0 = __shfl_sync(kAll, p.mi, own);
+    const float x[3] = {__shfl_sync(kAll, p.x[0], own), __shfl_sync(kAll, p.x[1], own),
+                        __shfl_sync(kAll, p.x[2], own)};
+    const float u0 = __shfl_sync(kAll, p.u[0], own), u1 = __shfl_sync(kAll, p.u[1], own),
+                u2 = __shfl_sync(kAll, p.u[2], own);
+    const float t0 = __shfl_sync(kAll, p.t, own), te = __shfl_sync(kAll, t_end, own),
+                v = __shfl_sync(kAll, p.v, own), s = __shfl_sync(kAll, p.s, own);
+    if (j < total) {
+      const int m = mi0 + (j - first);
+      const float b0 = m == 0 ? 0.0f : tmeas[m - 1];
+      const float b1 = tmeas[m];
+      const float ta = t0 > b0 ? t0 : b0;
+      const float tb = te < b1 ? te : b1;
+      if (ta < tb) {
+        const float wb = 1.0f / (b1 - b0);
+        const float w3[3] = {v * u0, v * u1, v * u2};
+        for (int r = 0; r < C.n_regs; ++r) {
+          const DetRegion& reg = C.regs[r];
+          const size_t base_c = (size_t)m * C.n_det + reg.off;
+          region_track<float>(reg, x, w3, t0, ta, tb, [&](uint32_t det, float dur) {
+            long long* q = reinterpret_cast<long long*>(snap) + (base_c + det) * 4;
+            const float f = (s * dur) * wb;
+            red_s64(q + 0, fx(f));
+            red_s64(q + 1, fx((f * v) * u0));
+            red_s64(q + 2, fx((f * v) * u1));
+            red_s64(q + 3, fx((f * v) * u2));
+          });
+        }
+      }
+    }
+  }
+}
+
 // Shared memory: the measurement times as float (always), then the relaxation
 // alias records and per-bin constants where the plan has room.
 template <int TPB, bool EXT>
@@ -223,7 +283,7 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
   bool drained = false;   // as in the steady tracer: idle lanes stay until the warp is drained
   uint64_t idx = 0;
   constexpr unsigned kAll = 0xffffffffu;
-  if (C.n_regs == 0 && !C.time_average) {
+  if (C.time_average || C.n_regs == 0) {
     // Snapshots on the whole-box grid: every lane of a warp runs every step
     // (no lane skips ahead to the next refill), so that the warp can share
     // out its snapshots (warp_snapshots).  Flight and event as in
@@ -258,7 +318,7 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
       }
       // the flight: nearest of t_max, the clocks and the boundary (Sec. 3.3,
       // Sec. 3.5.6), and how many measurement times it covers
-      int out = STEP_ALIVE, k = 0, face = 0;
+      int out = STEP_ALIVE, k = 0, face = 0, mi_next = 0;
       bool fin = false, rlx = false, rlx2 = false;
       float seg = 0.0f, t_end = 0.0f;
       if (alive) {
@@ -274,21 +334,36 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
           else if (EXT && p.d2 < db) { rlx2 = true; seg = p.d2; }
           else { seg = db; }
           t_end = fin ? tmax : p.t + seg * p.inv_v;
-          // the measurement times in [t, t_end) (closed at t_max): the first
-          // index from p.mi on that is not covered, by bisection
-          int lo = p.mi, hi = C.n_times;
-          while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            const bool cov = fin ? (tmeas[mid] <= t_end) : (tmeas[mid] < t_end);
-            if (cov) lo = mid + 1; else hi = mid;
+          if (C.time_average) {
+            // the bins [t_{m-1}, t_m) the flight overlaps: m = p.mi up to the
+            // first m whose end t_m lies beyond t_end (the flight's last bin,
+            // where the particle stays), by bisection
+            int lo = p.mi, hi = C.n_times;
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (tmeas[mid] <= t_end) lo = mid + 1; else hi = mid;
+            }
+            mi_next = lo;
+            k = p.mi < C.n_times ? (lo < C.n_times ? lo : C.n_times - 1) - p.mi + 1 : 0;
+          } else {
+            // the measurement times in [t, t_end) (closed at t_max): the first
+            // index from p.mi on that is not covered, by bisection
+            int lo = p.mi, hi = C.n_times;
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              const bool cov = fin ? (tmeas[mid] <= t_end) : (tmeas[mid] < t_end);
+              if (cov) lo = mid + 1; else hi = mid;
+            }
+            k = lo - p.mi;
+            mi_next = lo;
           }
-          k = lo - p.mi;
         }
       }
-      warp_snapshots(k, p, tmeas, cinv, C, A.snap);
+      if (C.time_average) warp_bin_averages(k, t_end, p, tmeas, C, A.snap);
+      else warp_snapshots(k, p, tmeas, cinv, C, A.snap);
       if (!alive) continue;
       if (out == STEP_ALIVE) {
-        p.mi += k;
+        p.mi = mi_next;
         p.t = t_end;
 #pragma unroll
         for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
