@@ -248,7 +248,9 @@ __device__ __forceinline__ void warp_bin_averages(int k, float t_end, const Part
 
 // Shared memory: the measurement times as float (always), then the relaxation
 // alias records and per-bin constants where the plan has room.
-template <int TPB, bool EXT>
+// TAVG: the run tallies time-bin averages (compiled apart, so that the
+// snapshot variant carries none of that code).
+template <int TPB, bool EXT, bool TAVG>
 __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restrict__ geos, MatView M, RunCfg C,
                                                           Acc A, SmemPlan S) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -283,7 +285,7 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
   bool drained = false;   // as in the steady tracer: idle lanes stay until the warp is drained
   uint64_t idx = 0;
   constexpr unsigned kAll = 0xffffffffu;
-  if (C.time_average || C.n_regs == 0) {
+  if (TAVG || C.n_regs == 0) {
     // Snapshots on the whole-box grid: every lane of a warp runs every step
     // (no lane skips ahead to the next refill), so that the warp can share
     // out its snapshots (warp_snapshots).  Flight and event as in
@@ -334,7 +336,7 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
           else if (EXT && p.d2 < db) { rlx2 = true; seg = p.d2; }
           else { seg = db; }
           t_end = fin ? tmax : p.t + seg * p.inv_v;
-          if (C.time_average) {
+          if constexpr (TAVG) {
             // the bins [t_{m-1}, t_m) the flight overlaps: m = p.mi up to the
             // first m whose end t_m lies beyond t_end (the flight's last bin,
             // where the particle stays), by bisection
@@ -355,15 +357,15 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
               if (cov) lo = mid + 1; else hi = mid;
             }
             k = lo - p.mi;
-            mi_next = lo;
           }
         }
       }
-      if (C.time_average) warp_bin_averages(k, t_end, p, tmeas, C, A.snap);
+      if constexpr (TAVG) warp_bin_averages(k, t_end, p, tmeas, C, A.snap);
       else warp_snapshots(k, p, tmeas, cinv, C, A.snap);
       if (!alive) continue;
       if (out == STEP_ALIVE) {
-        p.mi = mi_next;
+        if constexpr (TAVG) p.mi = mi_next;
+        else p.mi += k;
         p.t = t_end;
 #pragma unroll
         for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
@@ -517,13 +519,13 @@ cudaError_t launch_transient(int precision, const GeoRun* geos, const MatView& M
 #endif  // MCBTE_F64
 #if MCBTE_F32
 namespace {
-template <int TPB, bool EXT>
-cudaError_t launch_transient_tpb(const GeoRun* geos, const MatView& M, const RunCfg& C, const Acc& A, int bps,
+template <int TPB, bool EXT, bool TAVG>
+cudaError_t launch_transient_tav(const GeoRun* geos, const MatView& M, const RunCfg& C, const Acc& A, int bps,
                                  cudaStream_t s) {
   const size_t tm_bytes = ((size_t)C.n_times * sizeof(float) + 15) & ~(size_t)15;
   SmemPlan S = plan_smem_f32(M.n, 1, 0, 0, 200 * 1024 - tm_bytes);
   S.bytes += tm_bytes;
-  auto kern = k_transient_f32<TPB, EXT>;
+  auto kern = k_transient_f32<TPB, EXT, TAVG>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.bytes);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -533,6 +535,12 @@ cudaError_t launch_transient_tpb(const GeoRun* geos, const MatView& M, const Run
   const int b = (bps > 0 && bps < occ) ? bps : occ;
   kern<<<sm_count() * b, TPB, S.bytes, s>>>(geos, M, C, A, S);
   return cudaGetLastError();
+}
+template <int TPB, bool EXT>
+cudaError_t launch_transient_tpb(const GeoRun* geos, const MatView& M, const RunCfg& C, const Acc& A, int bps,
+                                 cudaStream_t s) {
+  return C.time_average ? launch_transient_tav<TPB, EXT, true>(geos, M, C, A, bps, s)
+                        : launch_transient_tav<TPB, EXT, false>(geos, M, C, A, bps, s);
 }
 }  // namespace
 
