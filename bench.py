@@ -62,7 +62,7 @@ INSTR_PER_EVENT = 200.0
 # DRAM bytes per launch of the FP32 steady tracing kernel on the default
 # workload, from the ncu capture summarised in profiles/ (None until a capture
 # of the current kernel exists).
-TRACE_DRAM_BYTES_PER_LAUNCH = 983_808 + 305_152
+TRACE_DRAM_BYTES_PER_LAUNCH = 1_175_808 + 315_392
 
 
 def _dist():

@@ -524,7 +524,7 @@ struct TallyFxT {
 
   __device__ __forceinline__ float segment(Particle<float>& p, float seg) const {
     const float contrib = (p.s * seg) * sel3(p.u, ta);
-    p.Xq += fx(contrib);
+    p.Xq += __float2ll_rn(contrib * kFx);   // fx(contrib) without its range branch (same rounding)
     if (!cP) return contrib;
     const float z0 = sel3(p.x, ca);
     const float uz = sel3(p.u, ca);
