@@ -12,8 +12,16 @@ standard error on kappa_eff (t_step * (SE_rel / 0.01)^2), with the plain FP64
 tracer timed beside it on the same inputs.
 
 Other workloads (`--workload`), same line format:
+  si_slab_imp    the default slab with a separate two-phonon (impurity) clock,
+                 tau_imp^-1 = 2e-44 omega^4
+  nanomesh       the paper's square-pore nanomesh (four internal walls), 1e6
+                 particles, N_scat_max 10, separate two-phonon clock
   transient_box  2x2x1 um diffuse box, +1 K Gaussian hot spot, 1e8 particles,
-                 64x64x32 cells x 200 snapshot times (FP64 L2 atomics)
+                 64x64x32 cells x 200 snapshot times (fixed-point L2 reductions
+                 in L2-sized time windows); also reports the reductions' rate
+                 against the library's L2 reduction probe
+  transient_box_avg  the same box with 200 time-bin averages instead of
+                 snapshots
   film_batch     64 films 10 nm..10 um in one persistent launch replayed as
                  a CUDA graph, 1.4e8 particles in total
   pore_grad      nanoporous film, 5e7 particles, forward + likelihood-ratio
