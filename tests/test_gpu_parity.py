@@ -738,3 +738,32 @@ def test_fp32_measure_valued_specularity_gradient_at_p1():
     gp = go.dkappa_dp.cpu().numpy()
     assert np.isfinite(gp).all() and gp[1] > 0
     assert abs(gp[0] - ref["dkappa_dp"]) < 4 * np.hypot(gp[1], ref["dkappa_dp_se"])
+
+
+def test_large_tables_global_memory_paths():
+    # 12 000 bins: the alias build works in global scratch (beyond its
+    # shared-memory size), the FP32 tracer keeps the per-bin constants out
+    # of shared memory; tables bit-identical, FP64 run identical per
+    # particle, FP32 kappa within the combined standard error
+    rng = np.random.default_rng(12)
+    n = 12_000
+    m = W.Material(omega=np.linspace(1e12, 7e13, n), v=rng.uniform(1e3, 9e3, n), tau=10 ** rng.uniform(-12, -10, n),
+                   C=rng.exponential(size=n) * 1e3, T_lin=300.0)
+    M = api.Material(m)
+    t_g, t_o = M.tables(), oracle.tables(m)
+    for k in ("C", "alias", "thr", "prob"):
+        assert np.array_equal(t_g[k], t_o[k]), k
+    wl = W.gray_slab_c1(n=3000)
+    g, run = wl.geometries[0], wl.run
+    run.n_cells = 10
+    gg = gpu_steady(m, [g], [run.n], run, L.FP64_PLAIN, per_particle=True)
+    ref = oracle.run_steady(m, g, run, per_particle=True)
+    _check_fp64({"events_pp": gg["events_pp"], "X_pp": gg["X_pp"], "T": gg["T"][0], "q": gg["q"][0]}, ref)
+    G = api.Geometry(g)
+    o32 = api.run_steady(M, [G], [200_000], api.SteadyConfig(seed=77, precision=L.FP32_TRACE, n_cells=10,
+                                                             cell_axis=2, tally_axis=2, per_bin=True))
+    torch.cuda.synchronize()
+    s32 = o32.stats[0].cpu().numpy()
+    assert s32[L.STAT_STATUS] == 0
+    ref2 = oracle.run_steady(m, g, replace(run, n=200_000, seed=78))
+    assert abs(s32[L.STAT_KAPPA] - ref2["kappa"]) < 4 * np.hypot(s32[L.STAT_KAPPA_SE], ref2["kappa_se"])
