@@ -767,3 +767,27 @@ def test_large_tables_global_memory_paths():
     assert s32[L.STAT_STATUS] == 0
     ref2 = oracle.run_steady(m, g, replace(run, n=200_000, seed=78))
     assert abs(s32[L.STAT_KAPPA] - ref2["kappa"]) < 4 * np.hypot(s32[L.STAT_KAPPA_SE], ref2["kappa_se"])
+
+
+def test_fp32_two_block_relaxation_draw_beyond_65536_bins():
+    # more bins than the one-block FP32 relaxation draw serves: the FP32
+    # tracer takes the two-block draw of the FP64 path (64-bit threshold)
+    rng = np.random.default_rng(13)
+    n = 70_000
+    m = W.Material(omega=np.linspace(1e12, 7e13, n), v=rng.uniform(1e3, 9e3, n), tau=10 ** rng.uniform(-12, -10, n),
+                   C=rng.exponential(size=n) * 1e3, T_lin=300.0)
+    M = api.Material(m)
+    wl = W.gray_slab_c1(n=2000)
+    g, run = wl.geometries[0], wl.run
+    run.n_cells = 10
+    gg = gpu_steady(m, [g], [run.n], run, L.FP64_PLAIN, per_particle=True, M=M)
+    ref = oracle.run_steady(m, g, run, per_particle=True)
+    _check_fp64({"events_pp": gg["events_pp"], "X_pp": gg["X_pp"], "T": gg["T"][0], "q": gg["q"][0]}, ref)
+    G = api.Geometry(g)
+    o32 = api.run_steady(M, [G], [200_000], api.SteadyConfig(seed=79, precision=L.FP32_TRACE, n_cells=10,
+                                                             cell_axis=2, tally_axis=2))
+    torch.cuda.synchronize()
+    s32 = o32.stats[0].cpu().numpy()
+    assert s32[L.STAT_STATUS] == 0
+    ref2 = oracle.run_steady(m, g, replace(run, n=200_000, seed=80))
+    assert abs(s32[L.STAT_KAPPA] - ref2["kappa"]) < 4 * np.hypot(s32[L.STAT_KAPPA_SE], ref2["kappa_se"])
