@@ -2,6 +2,7 @@
 // workspace layout and the launch sequence of every run.  No numerical step
 // of the method runs here; this file only validates, lays out memory and
 // launches kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -407,7 +408,7 @@ struct SteadyWs {
   unsigned long long* cnt;
   double* G;
   long long* Gq;
-  double* dsum;
+  double* gsum;
   unsigned long long* work;
   int* flags;
   unsigned long long* t0;
@@ -424,10 +425,22 @@ struct SteadyWs {
   double* det_raw;      // [n_det][4] FP64 path sums (zeroed)
   long long* det_q;     // [n_det][4] FP32 path fixed-point sums (zeroed)
   double* det;          // host staging of the outputs
-  double* nscat;        // [G][K + 1][4] N_scat_max curve sums (zeroed)
+  double* nscat;        // [R][G][K + 1][4] N_scat_max curve sums, R = nscat_replicas (zeroed)
   double* kn;           // host staging of the curve
   size_t bytes;
 };
+
+// Copies of the N_scat_max curve sums: every relaxation adds to one of K + 1
+// slots per geometry, and one copy for the whole grid serialises those
+// same-address atomics in a few L2 slices.  Up to 64 copies (a power of
+// two), fewer where the curve is long or the batch large, so that they stay
+// within 8 MiB.
+int nscat_replicas(int G, int K) {
+  const size_t per = (size_t)G * (size_t)(K + 1) * 4 * sizeof(double);
+  int r = 64;
+  while (r > 1 && (size_t)r * per > ((size_t)8 << 20)) r >>= 1;
+  return r;
+}
 
 SteadyWs layout_steady(char* base, int G, int n, int nc, uint64_t total, bool grad, bool replay, int nd,
                        bool host_out, bool want_ev, bool want_x, bool want_T, bool want_q, bool want_qbin,
@@ -449,13 +462,13 @@ SteadyWs layout_steady(char* base, int G, int n, int nc, uint64_t total, bool gr
   w.cnt = c.take<unsigned long long>((size_t)G * 4);
   w.G = grad ? c.take<double>(n) : nullptr;
   w.Gq = grad ? c.take<long long>(n) : nullptr;
-  w.dsum = grad ? c.take<double>(2 * (size_t)(nd > 0 ? nd : 1)) : nullptr;
+  w.gsum = grad ? c.take<double>((size_t)kSumCopies * kGradStride) : nullptr;
   w.work = c.take<unsigned long long>(1);
   w.flags = c.take<int>(2);
   w.t0 = c.take<unsigned long long>(1);
   w.det_raw = n_det ? c.take<double>(4 * n_det) : nullptr;
   w.det_q = n_det ? c.take<long long>(4 * n_det) : nullptr;
-  w.nscat = nscat ? c.take<double>((size_t)G * (size_t)(nscat + 1) * 4) : nullptr;
+  w.nscat = nscat ? c.take<double>((size_t)nscat_replicas(G, nscat) * G * (size_t)(nscat + 1) * 4) : nullptr;
   c.off = (c.off + 255) & ~(size_t)255;
   w.zero_end = base ? base + c.off : nullptr;
   w.regs = n_det ? c.take<DetRegion>(MCBTE_MAX_REGIONS) : nullptr;
@@ -606,6 +619,7 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   C.ext = (p->n_regions > 0 || nscat > 0) ? 1 : 0;
   for (int g = 0; g < G; ++g) C.ext |= uses_ext(m, geoms[g]->host) ? 1 : 0;
   C.nscat_acc = w.nscat;
+  C.nscat_rep = nscat ? nscat_replicas(G, nscat) : 1;
   C.n_regs = p->n_regions;
   C.n_det = (uint32_t)n_det;
   C.det_nb = p->det_per_bin ? n : 1;
@@ -632,7 +646,7 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   A.cnt = w.cnt;
   A.G = w.G;
   A.Gq = w.Gq;
-  A.dsum = w.dsum;
+  A.gsum = w.gsum;
   A.work = w.work;
   A.flags = w.flags;
   A.det_raw = w.det_raw;
@@ -815,8 +829,8 @@ TransientWs layout_transient(char* base, size_t snap_len, int n_times, bool host
   w.offs = c.take<uint64_t>(2);
   c.off = (c.off + 255) & ~(size_t)255;
   w.zero_begin = base ? base + c.off : nullptr;
-  w.dsc = c.take<double>(8);
-  w.cnt = c.take<unsigned long long>(4);
+  w.dsc = c.take<double>(8 * (size_t)kSumCopies);
+  w.cnt = c.take<unsigned long long>(4 * (size_t)kSumCopies);
   w.work = c.take<unsigned long long>(1);
   w.flags = c.take<int>(2);
   w.t0 = c.take<unsigned long long>(1);

@@ -60,8 +60,10 @@ struct RunCfg {
   int mvd;              // gradient: measure-valued d kappa / d p_pore (phantom traces)
   // N_scat_max convergence curve, or null: per geometry and k = 1..n_scat_max,
   // [0] sum of X at the k-th relaxation, [1] its square, [2] sum of the final
-  // X of trajectories with exactly k - 1 relaxations, [3] its square
-  double* nscat_acc;    // [G][n_scat_max + 1][4]
+  // X of trajectories with exactly k - 1 relaxations, [3] its square; in
+  // nscat_rep copies (a power of two), block b adding to copy b % nscat_rep
+  double* nscat_acc;    // [nscat_rep][G][n_scat_max + 1][4]
+  int nscat_rep;
   int det_nb;           // steady detector sums per detector (1) or per detector and bin (n_bins)
 };
 
@@ -148,6 +150,16 @@ __device__ __forceinline__ void region_track(const DetRegion& r, const R x0[3], 
 }
 
 // Raw accumulators of a run (device).
+// Sums that every particle adds to (the gradient sums, a transient run's
+// counters) are kept in kSumCopies copies, block b adding to copy
+// b % kSumCopies, so that those same-address atomics do not serialise in one
+// L2 slice; the finalising kernel folds the copies.
+constexpr int kSumCopies = 64;
+// Gradient sums of one run (one geometry): [0] the resampling term R, [1] the
+// d kappa / d p_pore score, [2] its square, [3] unused, [4 + 2k] the value
+// along probe direction k, [5 + 2k] its square.
+constexpr int kGradStride = 4 + 2 * kMaxDirs;
+
 struct Acc {
   double* cellP;              // [G][nc][4]   per-cell direct / partial-cell sums (FP64 path)
   double* cellD;              // [G][nc+1][4] difference array of full-cell sums (FP64 path)
@@ -155,11 +167,12 @@ struct Acc {
   long long* cellPq;          // [G][nc][4]   fixed-point counterparts (FP32 path)
   long long* cellDq;          // [G][nc+1][4]
   long long* qbinq;           // [G][n_bins]
-  double* dsc;                // [G][8]: sumX, sumX2, signed emitted, signed absorbed, R, Gp, Gp^2, absorbed
-  unsigned long long* cnt;    // [G][4]: events, truncated, max events, traced
+  double* dsc;                // [G][8] (transient: [kSumCopies][8]): sumX, sumX2, signed emitted,
+                              // signed absorbed, -, -, -, absorbed
+  unsigned long long* cnt;    // [G][4] (transient: [kSumCopies][4]): events, truncated, max events, traced
   double* G;                  // [n_bins] sparse part of the LR gradient (FP64 path)
   long long* Gq;              // [n_bins] its fixed-point counterpart (FP32 gradient pass)
-  double* dsum;               // [n_dirs][2]
+  double* gsum;               // [kSumCopies][kGradStride] gradient sums
   double* snap;               // [n_times][cells][4] transient
   uint4* tstate;              // [total][3] particle state between transient time windows, or null
   double* det_raw;            // [n_det][4] steady detector sums (FP64 path)
@@ -169,6 +182,10 @@ struct Acc {
   unsigned long long* work;   // [1] persistent work counter
   int* flags;                 // [1] bit 0: time budget hit
 };
+
+__device__ __forceinline__ size_t sum_copy() { return (size_t)(blockIdx.x & (unsigned)(kSumCopies - 1)); }
+
+__device__ __forceinline__ double* grad_copy(const Acc& A) { return A.gsum + sum_copy() * kGradStride; }
 
 template <typename R>
 struct Particle {
@@ -777,6 +794,12 @@ enum { STEP_ALIVE = 0, STEP_ABSORBED = 1, STEP_DONE = 2, STEP_TRUNCATED = 3 };
 // to the opposite face; adiabatic / pore: specular with probability p, else
 // Lambertian about the inward normal).  The particle has already moved.
 // `Xnow` is the particle's tally so far (gradient bookkeeping only).
+// Slot k of geometry g's N_scat_max curve sums in this block's copy.
+__device__ __forceinline__ double* nscat_slot(const RunCfg& C, int g, int k) {
+  const size_t rep = (size_t)(blockIdx.x & (unsigned)(C.nscat_rep - 1));
+  return C.nscat_acc + ((rep * (size_t)C.n_geoms + (size_t)g) * (size_t)(C.n_scat_max + 1) + (size_t)k) * 4;
+}
+
 template <typename R, class Grad, class Tally, bool EXT = true>
 __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_relax,
                                            const float4* binf, const RunCfg& C, uint32_t k0, uint32_t k1,
@@ -790,7 +813,7 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
       if (C.nscat_acc) {
         // a run with N_scat_max = n_relax would end the particle here with this tally
         const double x = T.X(p);
-        double* a = C.nscat_acc + ((size_t)p.g * (size_t)(C.n_scat_max + 1) + (size_t)p.n_relax) * 4;
+        double* a = nscat_slot(C, p.g, p.n_relax);
         atomicAdd(a + 0, x);
         atomicAdd(a + 1, x * x);
       }

@@ -33,7 +33,7 @@ __device__ __forceinline__ int find_geom(const uint64_t* offs, int G, uint64_t i
 // N_scat_max > m; it enters the difference array at m + 1.
 __device__ __forceinline__ void nscat_end(const RunCfg& C, int g, int m, double X) {
   if (!C.nscat_acc || m >= C.n_scat_max) return;
-  double* a = C.nscat_acc + ((size_t)g * (size_t)(C.n_scat_max + 1) + (size_t)(m + 1)) * 4;
+  double* a = nscat_slot(C, g, m + 1);
   atomicAdd(a + 2, X);
   atomicAdd(a + 3, X * X);
 }
@@ -47,19 +47,20 @@ __device__ __forceinline__ void grad_finish(const Grad& gr, double X, int g, con
   const int np = gr.periods();
   for (int k = 0; k < np; ++k) atomicAdd(&A.G[gr.period_bin(k)], gr.period_value(k, X));
   const double Rv = gr.resample_term(X);
-  atomicAdd(&A.dsc[g * 8 + 4], Rv);
+  double* gs = grad_copy(A);
+  atomicAdd(gs + 0, Rv);
   if (!C.mvd) {   // the measure-valued score is added after the phantom trace
     const double gp = gr.spec_term(X);
-    atomicAdd(&A.dsc[g * 8 + 5], gp);
-    atomicAdd(&A.dsc[g * 8 + 6], gp * gp);
+    atomicAdd(gs + 1, gp);
+    atomicAdd(gs + 2, gp * gp);
   }
   for (int kd = 0; kd < C.n_dirs; ++kd) {
     const double* dd = C.dirs + (size_t)kd * M.n;
     double val = 0.0;
     for (int k = 0; k < np; ++k) val += gr.period_value(k, X) * dd[gr.period_bin(k)];
     val += Rv * C.dpi[kd];
-    atomicAdd(&A.dsum[kd * 2 + 0], val);
-    atomicAdd(&A.dsum[kd * 2 + 1], val * val);
+    atomicAdd(gs + 4 + 2 * kd, val);
+    atomicAdd(gs + 5 + 2 * kd, val * val);
   }
 }
 
@@ -150,8 +151,9 @@ __global__ void __launch_bounds__(256) k_steady_fp64(const GeoRun* __restrict__ 
         }
       }
       const double D = gr.mv.score(Xn, p.X);
-      atomicAdd(&A.dsc[g * 8 + 5], D);
-      atomicAdd(&A.dsc[g * 8 + 6], D * D);
+      double* gs = grad_copy(A);
+      atomicAdd(gs + 1, D);
+      atomicAdd(gs + 2, D * D);
     }
   }
 }
@@ -199,16 +201,17 @@ struct ThreadAcct {
 __device__ __forceinline__ void grad_finish_replay(GradReplay& gr, double X, int g, const RunCfg& C, const Acc& A) {
   gr.close_period(X);
   const double Rv = gr.resample_term(X);
-  atomicAdd(&A.dsc[g * 8 + 4], Rv);
+  double* gs = grad_copy(A);
+  atomicAdd(gs + 0, Rv);
   if (!C.mvd) {   // the measure-valued score is added after the phantom trace
     const double gp = gr.spec_term(X);
-    atomicAdd(&A.dsc[g * 8 + 5], gp);
-    atomicAdd(&A.dsc[g * 8 + 6], gp * gp);
+    atomicAdd(gs + 1, gp);
+    atomicAdd(gs + 2, gp * gp);
   }
   for (int kd = 0; kd < C.n_dirs; ++kd) {
     const double val = gr.dv[kd] + Rv * C.dpi[kd];
-    atomicAdd(&A.dsum[kd * 2 + 0], val);
-    atomicAdd(&A.dsum[kd * 2 + 1], val * val);
+    atomicAdd(gs + 4 + 2 * kd, val);
+    atomicAdd(gs + 5 + 2 * kd, val * val);
   }
 }
 
@@ -363,8 +366,9 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
           }
         } else {
           const double D = gr.mv.score(gr.Xf, X);
-          atomicAdd(&A.dsc[p.g * 8 + 5], D);
-          atomicAdd(&A.dsc[p.g * 8 + 6], D * D);
+          double* gs = grad_copy(A);
+          atomicAdd(gs + 1, D);
+          atomicAdd(gs + 2, D * D);
         }
       }
       alive = false;
@@ -459,6 +463,18 @@ __global__ void k_finalize_steady(const GeoRun* geos, MatView M, RunCfg C, Acc A
       for (int b = 1; b < 4; ++b) O.det[s * 4 + b] = (kq * raw[b]) * 1e-9;
     }
   }
+  if (O.kn && C.nscat_acc) {
+    // fold the copies of the curve sums into the first
+    const size_t per = (size_t)(C.n_scat_max + 1) * 4;
+    const size_t stride = (size_t)C.n_geoms * per;
+    double* a0 = C.nscat_acc + (size_t)g * per;
+    for (size_t i = threadIdx.x; i < per; i += blockDim.x) {
+      double v = a0[i];
+      for (int r = 1; r < C.nscat_rep; ++r) v += a0[(size_t)r * stride + i];
+      a0[i] = v;
+    }
+    __syncthreads();
+  }
   if (O.kn && C.nscat_acc && threadIdx.x == 0) {
     // kappa and its standard error for N_scat_max = k: the tally at the k-th
     // relaxation, or the final one of trajectories that ended before it
@@ -514,21 +530,29 @@ __global__ void k_finalize_steady(const GeoRun* geos, MatView M, RunCfg C, Acc A
     st[MCBTE_STAT_ABSORBED] = A.dsc[g * 8 + 7];
   }
   if (grad && g == 0) {
+    // fold the copies of the gradient sums into the first
+    double* gs = A.gsum;
+    for (int i = threadIdx.x; i < kGradStride; i += blockDim.x) {
+      double v = gs[i];
+      for (int r = 1; r < kSumCopies; ++r) v += gs[(size_t)r * kGradStride + i];
+      gs[i] = v;
+    }
+    __syncthreads();
     const double scale = -(E_eff / G.V_solid) * 1e-9 / G.kappa_grad;
-    const double Rs = A.dsc[4];
+    const double Rs = gs[0];
     for (int i = threadIdx.x; i < n; i += blockDim.x) O.dk[i] = scale * ((A.G[i] + (double)A.Gq[i] * kFxInv) + Rs * M.pi[i]);
     if (threadIdx.x == 0) {
       const double nt = (double)A.cnt[3];
-      const double gm = A.dsc[5] / nt;
-      const double gv = (A.dsc[6] - nt * gm * gm) / fmax(nt - 1.0, 1.0);
+      const double gm = gs[1] / nt;
+      const double gv = (gs[2] - nt * gm * gm) / fmax(nt - 1.0, 1.0);
       const bool ok = G.pore && (C.mvd || (G.p_pore > 0.0 && G.p_pore < 1.0));
       const double nan = __longlong_as_double(0x7ff8000000000000ll);
-      O.dkp[0] = ok ? scale * A.dsc[5] : nan;
+      O.dkp[0] = ok ? scale * gs[1] : nan;
       O.dkp[1] = ok ? fabs(scale) * sqrt(fmax(gv, 0.0) * nt) : nan;
       for (int k = 0; k < C.n_dirs; ++k) {
-        const double dm = A.dsum[k * 2] / nt;
-        const double dv = (A.dsum[k * 2 + 1] - nt * dm * dm) / fmax(nt - 1.0, 1.0);
-        O.dkdir[k * 2 + 0] = scale * A.dsum[k * 2];
+        const double dm = gs[4 + 2 * k] / nt;
+        const double dv = (gs[5 + 2 * k] - nt * dm * dm) / fmax(nt - 1.0, 1.0);
+        O.dkdir[k * 2 + 0] = scale * gs[4 + 2 * k];
         O.dkdir[k * 2 + 1] = fabs(scale) * sqrt(fmax(dv, 0.0) * nt);
       }
     }

@@ -32,14 +32,16 @@ __device__ __forceinline__ void transient_start(Particle<R>& p, const RunCfg& C)
 template <typename R>
 __device__ __forceinline__ void transient_finish(const Particle<R>& p, int out, uint64_t idx, const Acc& A) {
   const unsigned long long nev = (unsigned long long)p.e + 1ull;
-  atomicAdd(&A.cnt[0], nev);
-  if (out == STEP_TRUNCATED) atomicAdd(&A.cnt[1], 1ull);
-  atomicMax(&A.cnt[2], nev);
-  atomicAdd(&A.cnt[3], 1ull);
-  atomicAdd(&A.dsc[2], (double)p.s);
+  unsigned long long* cnt = A.cnt + sum_copy() * 4;
+  double* dsc = A.dsc + sum_copy() * 8;
+  atomicAdd(cnt + 0, nev);
+  if (out == STEP_TRUNCATED) atomicAdd(cnt + 1, 1ull);
+  atomicMax(cnt + 2, nev);
+  atomicAdd(cnt + 3, 1ull);
+  atomicAdd(dsc + 2, (double)p.s);
   if (out == STEP_ABSORBED) {
-    atomicAdd(&A.dsc[3], (double)p.s);
-    atomicAdd(&A.dsc[7], 1.0);
+    atomicAdd(dsc + 3, (double)p.s);
+    atomicAdd(dsc + 7, 1.0);
   }
   if (A.events_pp) A.events_pp[idx] = (uint32_t)nev;
 }
@@ -488,17 +490,27 @@ __global__ void k_finalize_transient(const GeoRun* geos, MatView M, RunCfg C, Ac
     o[3] = (kq * a3) * 1e3;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // fold the copies of the run counters
+    unsigned long long c[4] = {0ull, 0ull, 0ull, 0ull};
+    double d[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int r = 0; r < kSumCopies; ++r) {
+      c[0] += A.cnt[r * 4 + 0];
+      c[1] += A.cnt[r * 4 + 1];
+      c[2] = c[2] > A.cnt[r * 4 + 2] ? c[2] : A.cnt[r * 4 + 2];
+      c[3] += A.cnt[r * 4 + 3];
+      for (int k = 0; k < 8; ++k) d[k] += A.dsc[r * 8 + k];
+    }
     for (int k = 0; k < MCBTE_NSTATS; ++k) stats[k] = 0.0;
-    stats[MCBTE_STAT_EVENTS] = (double)A.cnt[0];
-    stats[MCBTE_STAT_TRUNCATED] = (double)A.cnt[1];
-    stats[MCBTE_STAT_MAX_EVENTS] = (double)A.cnt[2];
-    stats[MCBTE_STAT_N] = (double)A.cnt[3];
+    stats[MCBTE_STAT_EVENTS] = (double)c[0];
+    stats[MCBTE_STAT_TRUNCATED] = (double)c[1];
+    stats[MCBTE_STAT_MAX_EVENTS] = (double)c[2];
+    stats[MCBTE_STAT_N] = (double)c[3];
     stats[MCBTE_STAT_E_TOT] = G.E_tot;
-    stats[MCBTE_STAT_SIGNED_EMITTED] = A.dsc[2];
-    stats[MCBTE_STAT_SIGNED_ABSORBED] = A.dsc[3];
-    stats[MCBTE_STAT_ABSORBED] = A.dsc[7];
+    stats[MCBTE_STAT_SIGNED_EMITTED] = d[2];
+    stats[MCBTE_STAT_SIGNED_ABSORBED] = d[3];
+    stats[MCBTE_STAT_ABSORBED] = d[7];
     stats[MCBTE_STAT_STATUS] = (A.flags[0] & 1) ? (double)MCBTE_ERR_TIMEOUT
-                                                : (A.cnt[1] ? (double)MCBTE_WARN_TRUNCATED : 0.0);
+                                                : (c[1] ? (double)MCBTE_WARN_TRUNCATED : 0.0);
   }
 }
 

@@ -723,6 +723,26 @@ def test_nscat_curve_per_geometry_in_a_batch():
         assert ok, (f, err)
 
 
+def test_nscat_curve_4096_points_matches_a_short_run():
+    # the longest curve (its sums kept in fewer copies than a short curve's):
+    # on the same trajectories, the point at k = 16 is the kappa of a run with
+    # N_scat_max = 16, and the last point the run's own kappa
+    m = W.bvk_holland(n_per_branch=20)
+    wl = W.si_slab_c2(n=300_000, material=m)
+    M, G = api.Material(m), api.Geometry(wl.geometries[0])
+    c = api.SteadyConfig(seed=71, precision=L.FP32_TRACE, tally_axis=2, n_scat_max=4096, nscat_curve=True,
+                         max_events=10 ** 7)
+    o = api.run_steady(M, [G], [wl.run.n], c)
+    s16 = api.run_steady(M, [G], [wl.run.n], replace(c, n_scat_max=16, nscat_curve=False))
+    torch.cuda.synchronize()
+    kn = o.kappa_nscat[0].cpu().numpy()
+    assert kn.shape == (4096, 2)
+    assert o.stats[0, L.STAT_STATUS].item() == 0 and s16.stats[0, L.STAT_STATUS].item() == 0
+    assert kn[-1, 0] == pytest.approx(o.stats[0, L.STAT_KAPPA].item(), rel=1e-9)
+    assert kn[15, 0] == pytest.approx(s16.stats[0, L.STAT_KAPPA].item(), rel=1e-9)
+    assert kn[15, 1] == pytest.approx(s16.stats[0, L.STAT_KAPPA_SE].item(), rel=1e-6)
+
+
 def test_fp32_measure_valued_specularity_gradient_at_p1():
     wl = W.pore_film_c5(n=100_000, p_pore=1.0)
     mat, g, run = wl.material, wl.geometries[0], wl.run
