@@ -394,56 +394,59 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
     }
     return;
   }
-  for (;;) {
-    if (__all_sync(kAll, drained)) break;
-    const unsigned need = __ballot_sync(kAll, !alive && !drained);
-    if (need) {
-      const int leader = __ffs(need) - 1;
-      unsigned long long base = 0;
-      if ((int)lane == leader) {
-        base = atomicAdd(A.work, (unsigned long long)__popc(need));
-        // the time budget is also checked each time the handed-out count
-        // crosses a multiple of 4096 (particles shorter than the per-event
-        // check interval would otherwise never look)
-        if (((base + (unsigned long long)__popc(need)) >> 12) != (base >> 12) && globaltimer_ns() > deadline)
-          atomicOr(A.flags, 1);
-      }
-      base = __shfl_sync(kAll, base, leader);
-      if (!alive && !drained) {
-        idx = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
-        if (idx >= C.total || (*(volatile int*)A.flags & 1)) {
-          drained = true;
-          continue;
+  // snapshots into detector regions: the per-lane loop
+  if constexpr (!TAVG) {
+    for (;;) {
+      if (__all_sync(kAll, drained)) break;
+      const unsigned need = __ballot_sync(kAll, !alive && !drained);
+      if (need) {
+        const int leader = __ffs(need) - 1;
+        unsigned long long base = 0;
+        if ((int)lane == leader) {
+          base = atomicAdd(A.work, (unsigned long long)__popc(need));
+          // the time budget is also checked each time the handed-out count
+          // crosses a multiple of 4096 (particles shorter than the per-event
+          // check interval would otherwise never look)
+          if (((base + (unsigned long long)__popc(need)) >> 12) != (base >> 12) && globaltimer_ns() > deadline)
+            atomicOr(A.flags, 1);
         }
-        if (C.win_first) {
-          p.pid = (uint32_t)idx;
-          p.g = 0;
-          emit<float, EXT>(p, G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, true, (float)C.t_max_ps);
-          transient_start(p, C);
-          if (!C.win_last && p.mi >= C.win_end) {   // emitted after this window's last snapshot
-            save_state(A.tstate, idx, p);
+        base = __shfl_sync(kAll, base, leader);
+        if (!alive && !drained) {
+          idx = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
+          if (idx >= C.total || (*(volatile int*)A.flags & 1)) {
+            drained = true;
             continue;
           }
-        } else if (!load_state(A.tstate, idx, p, M, binf, C)) {
-          continue;
+          if (C.win_first) {
+            p.pid = (uint32_t)idx;
+            p.g = 0;
+            emit<float, EXT>(p, G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, true, (float)C.t_max_ps);
+            transient_start(p, C);
+            if (!C.win_last && p.mi >= C.win_end) {   // emitted after this window's last snapshot
+              save_state(A.tstate, idx, p);
+              continue;
+            }
+          } else if (!load_state(A.tstate, idx, p, M, binf, C)) {
+            continue;
+          }
+          alive = true;
         }
-        alive = true;
       }
-    }
-    if (!alive) continue;
-    int out = step_transient<float, EXT>(p, G, M, relax, binf, C, key.x, key.y, A.snap, tmeas, cinv);
-    if (out == STEP_ALIVE && (p.e & 255u) == 0u && globaltimer_ns() > deadline) {
-      atomicOr(A.flags, 1);
-      out = STEP_TRUNCATED;
-    }
-    if (out != STEP_ALIVE) {
-      transient_finish(p, out, idx, A);
-      if (!C.win_last) mark_done(A.tstate, idx);
-      alive = false;
-    } else if (!C.win_last && p.mi >= C.win_end) {
-      // this window's snapshots are taken: park the particle at its event
-      save_state(A.tstate, idx, p);
-      alive = false;
+      if (!alive) continue;
+      int out = step_transient<float, EXT>(p, G, M, relax, binf, C, key.x, key.y, A.snap, tmeas, cinv);
+      if (out == STEP_ALIVE && (p.e & 255u) == 0u && globaltimer_ns() > deadline) {
+        atomicOr(A.flags, 1);
+        out = STEP_TRUNCATED;
+      }
+      if (out != STEP_ALIVE) {
+        transient_finish(p, out, idx, A);
+        if (!C.win_last) mark_done(A.tstate, idx);
+        alive = false;
+      } else if (!C.win_last && p.mi >= C.win_end) {
+        // this window's snapshots are taken: park the particle at its event
+        save_state(A.tstate, idx, p);
+        alive = false;
+      }
     }
   }
 }
