@@ -12,6 +12,10 @@ numpy / scipy library primitives (the exponential integrals E_n come from
                           the E1 kernel, solved by product integration; the
                           heat flux Psi = 1 - 2 int phi E2
 * ``gray_slab_ordinates`` the same slab by discrete ordinates (independent)
+* ``nongray_slab``        frequency-dependent slab between black walls: the
+                          multi-group integral equation for the local
+                          temperature (relaxation weights C_i / tau_i of
+                          Eq. n_scatt), per-bin flux and energy temperature
 * ``ballistic_transient`` the paper's Eq. Analytical_T (Sec. 5.1)
 * ``gaussian_fourier``    long-time Fourier solution of a Gaussian hot spot
                           against an adiabatic plane (image method)
@@ -120,6 +124,132 @@ def gray_slab_nystrom(tau0: float, n: int = 801):
     m1 = xa * e3a - xb * e3b + e4a - e4b
     integ = np.sum(phi[:-1] * (xb * m0 - m1) / h + phi[1:] * (m1 - xa * m0) / h)
     return t, phi, 1.0 - 2.0 * integ
+
+
+def _hat_weights(n_nodes: int, h: float, n: int):
+    """Product-integration weights of the kernel E_n on a uniform grid of
+    spacing h (optical units).  For the interval whose near end lies at
+    distance m h and far end at (m + 1) h from the evaluation point, a[m] and
+    b[m] are the weights of its near and far node in int f(t') E_n(|t' - s|) dt'
+    with f linear on the interval (moments int E_n = -E_{n+1},
+    int x E_n = -x E_{n+1} - E_{n+2})."""
+    m = np.arange(n_nodes - 1, dtype=np.float64)
+    xa, xb = m * h, (m + 1.0) * h
+    ea1, eb1 = E(n + 1, xa), E(n + 1, xb)
+    m0 = ea1 - eb1
+    m1 = xa * ea1 - xb * eb1 + E(n + 2, xa) - E(n + 2, xb)
+    return (xb * m0 - m1) / h, (m1 - xa * m0) / h
+
+
+def _kernel_matrix(a, b):
+    """K[i, k] = weight of node k in int f(t') E_n(|t' - t_i|) dt' over the
+    whole grid, from the per-interval weights of _hat_weights."""
+    n = a.shape[0] + 1
+    ap, bp = np.append(a, 0.0), np.append(b, 0.0)
+    i = np.arange(n)[:, None]
+    k = np.arange(n)[None, :]
+    o = np.abs(k - i)
+    prev = bp[np.maximum(o - 1, 0)]
+    K = np.where(k > i, ap[o] * (k <= n - 2) + prev, 0.0)
+    K += np.where(k < i, ap[o] * (k >= 1) + prev, 0.0)
+    K += np.where(k == i, a[0] * ((i <= n - 2).astype(np.float64) + (i >= 1)), 0.0)
+    return K
+
+
+def _side_rows(a, b, s: int):
+    """Rows (right, left) of node weights in int_{t' > t_s} f E_n(t' - t_s) dt'
+    and int_{t' < t_s} f E_n(t_s - t') dt'."""
+    n = a.shape[0] + 1
+    ap, bp = np.append(a, 0.0), np.append(b, 0.0)
+    k = np.arange(n)
+    o = np.abs(k - s)
+    prev = bp[np.maximum(o - 1, 0)]
+    right = np.where(k > s, ap[o] * (k <= n - 2) + prev, 0.0)
+    right += np.where(k == s, a[0] * (s <= n - 2), 0.0)
+    left = np.where(k < s, ap[o] * (k >= 1) + prev, 0.0)
+    left += np.where(k == s, a[0] * (s >= 1), 0.0)
+    return right, left
+
+
+def nongray_slab(C, v, tau, L: float, dT_hot: float, dT_cold: float, n_cells: int,
+                 n_nodes: int = 801, relax_weights=None) -> dict:
+    """Frequency-dependent slab 0 <= z <= L between black walls (deviational
+    temperatures dT_hot at z = 0, dT_cold at z = L), linearised RTA with one
+    relaxation time per bin.
+
+    With t = z / Lambda_i (Lambda_i = v_i tau_i) the pseudo-temperature of
+    bin i (its energy density over C_i) is
+        T_i(t) = 1/2 [dT_hot E2(t) + dT_cold E2(tau0_i - t)
+                      + g_i int_0^tau0_i T_loc(t') E1(|t - t'|) dt']
+    and the local temperature balances the relaxed energy,
+        T_loc = sum_i w_i T_i,   w_i = (C_i / tau_i) / sum_j (C_j / tau_j).
+    g_i = 1 when relaxed energy is re-emitted in proportion to C_i / tau_i
+    (Eq. n_scatt); a re-emission law w'_i (relax_weights, normalised here)
+    gives g_i = w'_i / w_i.  T_loc is piecewise linear on n_nodes uniform
+    nodes and every kernel is integrated exactly against it (product
+    integration); (n_nodes - 1) must be a multiple of n_cells.
+
+    Returns the nodes z, T_loc at the nodes, the cell averages of the energy
+    temperature sum_i C_i T_i / sum_i C_i ("T_cells", the track-length
+    temperature of Eq. temp_steady), the slab-averaged flux of every bin
+    (1/L) int q_i dz with q_i = (C_i v_i / 2)[dT_hot E3(t) - dT_cold E3(tau0 - t)
+    + g_i int T_loc(t') sgn(t - t') E2(|t - t'|) dt'] ("q_bin", the per-bin
+    flux of Eq. flux_x_steady), and their sum ("q")."""
+    C, v, tau = (np.asarray(x, dtype=np.float64) for x in (C, v, tau))
+    nb = C.shape[0]
+    if (n_nodes - 1) % n_cells:
+        raise ValueError("n_nodes - 1 must be a multiple of n_cells")
+    lam = v * tau
+    u = C / tau
+    w = u / u.sum()
+    wr = u if relax_weights is None else np.asarray(relax_weights, dtype=np.float64)
+    g = (wr / wr.sum()) / w
+    z = np.linspace(0.0, L, n_nodes)
+    A = np.eye(n_nodes)
+    rhs = np.zeros(n_nodes)
+    groups = []
+    for i in range(nb):
+        tau0 = L / lam[i]
+        h = tau0 / (n_nodes - 1)
+        t = z / lam[i]
+        a1, b1 = _hat_weights(n_nodes, h, 1)
+        A -= (0.5 * w[i] * g[i]) * _kernel_matrix(a1, b1)
+        rhs += (0.5 * w[i]) * (dT_hot * E(2, t) + dT_cold * E(2, tau0 - t))
+        groups.append((tau0, h, t))
+    f = np.linalg.solve(A, rhs)
+    per = (n_nodes - 1) // n_cells
+    edges = np.arange(0, n_nodes, per)
+    T_bins = np.zeros((nb, n_cells))
+    q_bin = np.zeros(nb)
+    for i, (tau0, h, t) in enumerate(groups):
+        a2, b2 = _hat_weights(n_nodes, h, 2)
+        J = np.zeros(edges.shape[0])
+        for c, s in enumerate(edges):
+            r, l = _side_rows(a2, b2, int(s))
+            J[c] = (r - l) @ f
+        ta, tb = t[edges[:-1]], t[edges[1:]]
+        inner = np.array([h * (0.5 * f[s] + f[s + 1:s + per].sum() + 0.5 * f[s + per]) for s in edges[:-1]])
+        wall = dT_hot * (E(3, ta) - E(3, tb)) + dT_cold * (E(3, tau0 - tb) - E(3, tau0 - ta))
+        T_bins[i] = (0.5 * wall + 0.5 * g[i] * (2.0 * inner + J[1:] - J[:-1])) / (tb - ta)
+        a3, b3 = _hat_weights(n_nodes, h, 3)
+        r0, _ = _side_rows(a3, b3, 0)
+        _, lN = _side_rows(a3, b3, n_nodes - 1)
+        vol = (r0 - lN) @ f
+        q_bin[i] = C[i] * v[i] / (2.0 * tau0) * ((dT_hot - dT_cold) * (1.0 / 3.0 - E(4, tau0)) + g[i] * vol)
+    T_cells = (C[:, None] * T_bins).sum(axis=0) / C.sum()
+    return {"z": z, "T_loc": f, "T_cells": T_cells, "T_bins": T_bins, "q_bin": q_bin, "q": float(q_bin.sum())}
+
+
+def nongray_slab_extrapolated(C, v, tau, L: float, dT_hot: float, dT_cold: float, n_cells: int,
+                              relax_weights=None) -> dict:
+    """nongray_slab on 401 and 801 nodes with Richardson extrapolation (O(h^2))."""
+    r1 = nongray_slab(C, v, tau, L, dT_hot, dT_cold, n_cells, 401, relax_weights)
+    r2 = nongray_slab(C, v, tau, L, dT_hot, dT_cold, n_cells, 801, relax_weights)
+    out = dict(r2)
+    for k in ("T_cells", "q_bin"):
+        out[k] = r2[k] + (r2[k] - r1[k]) / 3.0
+    out["q"] = float(out["q_bin"].sum())
+    return out
 
 
 def gray_slab_psi(tau0: float) -> float:

@@ -252,6 +252,56 @@ def test_gray_slab_flux_and_temperature():
     assert np.mean(z ** 2) < 2.0
 
 
+def test_nongray_slab_solve_reduces_to_the_gray_one():
+    """One bin: the multi-group solve is the gray integral equation."""
+    r = cf.nongray_slab([1e6], [6000.0], [100e-9 / 6000.0], 100e-9, 0.5, -0.5, 50, 801)
+    _, phi, psi = cf.gray_slab_nystrom(1.0, 801)
+    assert np.max(np.abs(r["T_loc"] - (phi - 0.5))) < 1e-12
+    assert r["q"] / (1e6 * 6000.0 / 4.0) == pytest.approx(psi, abs=2e-6)
+
+
+def _bvk30_format2():
+    """30-bin silicon-like material (10 midpoint bins per branch) with its
+    per-bin heat capacity given directly (format 2), so the slab below tests
+    transport and relaxation only."""
+    m = W.bvk_holland(n_per_branch=10)
+    x = HBAR * m.omega / (KB * 300.0)
+    Cb = m.D * KB * (x / 2.0) ** 2 / np.sinh(x / 2.0) ** 2 * m.domega
+    return W.Material(omega=m.omega, v=m.v, tau=m.tau, C=Cb, T_lin=300.0, name="bvk30")
+
+
+def test_nongray_slab_relaxation_law():
+    """Eq. n_scatt (Sec. 3.5.2): relaxed energy is re-emitted in proportion to
+    C_i / tau_i.  In a slab between isothermal walls that law decides how the
+    energy of short-lived modes is handed to long-lived ones, so the per-bin
+    flux and the temperature profile depend on it (unlike in the
+    translation-invariant films and the periodic bulk).  The oracle's cell
+    temperatures and per-bin fluxes (1e6 particles, 16 batch means) are
+    compared with the multi-group Nystrom solution of the same slab; the
+    solutions for re-emission in proportion to C_i or C_i v_i are rejected by
+    the same data, so a wrong relaxation table cannot pass.  Bonferroni over
+    the 80 compared values: max |z| < 4.5 has a false-alarm rate below 1e-3."""
+    mat = _bvk30_format2()
+    L = 1e-6
+    g = W.slab_z(L, 300.5, 299.5, lateral=1e-6)
+    run = W.SteadyRun(n=1_000_000, seed=77, n_cells=50, cell_axis=2, tally_axis=2, per_bin=True)
+
+    def f(a, e):
+        r = oracle.run_steady(mat, g, run, pid_begin=a, pid_end=e)
+        return np.concatenate([r["T"], r["q_bin"]]) * (run.n / (e - a))
+    m, se = _batches(f, run.n, nb=16)
+    Tm, qm, Tse, qse = m[:50], m[50:], se[:50], se[50:]
+    det = cf.nongray_slab_extrapolated(mat.C, mat.v, mat.tau, L, 0.5, -0.5, 50)
+    zT = (Tm - det["T_cells"]) / Tse
+    zq = (qm - det["q_bin"]) / qse
+    assert np.max(np.abs(zT)) < 4.5 and np.mean(zT ** 2) < 2.0
+    assert np.max(np.abs(zq)) < 4.5 and np.mean(zq ** 2) < 2.0
+    for wr in (mat.C, mat.C * mat.v):
+        alt = cf.nongray_slab_extrapolated(mat.C, mat.v, mat.tau, L, 0.5, -0.5, 50, relax_weights=wr)
+        assert np.max(np.abs((qm - alt["q_bin"]) / qse)) > 20.0
+        assert np.max(np.abs((Tm - alt["T_cells"]) / Tse)) > 20.0
+
+
 def test_signed_energy_conservation_slab():
     wl = W.gray_slab_c1(n=20_000)
     r = oracle.run_steady(wl.material, wl.geometries[0], wl.run)
