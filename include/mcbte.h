@@ -227,6 +227,11 @@ typedef struct {
                                   1 <= n_scat_max <= MCBTE_MAX_NSCAT_CURVE; not with mcbte_grad */
   int det_per_bin;             /* 1: the detector outputs per frequency bin (Sec. 4.5 lists the
                                   steady output of each detector per bin); needs n_regions > 0 */
+  int tail_lanes;              /* FP32 tracer, tail of the run: once no particle is left to hand
+                                  out, a warp with at most this many particles in flight draws
+                                  the random words of their next events on all 32 lanes at once
+                                  and then traces them (same results, shorter dependent chain
+                                  per event); 0 = default (8), -1 = off, at most 32 */
 } mcbte_steady_params;
 
 typedef struct {

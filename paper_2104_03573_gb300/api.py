@@ -140,6 +140,7 @@ class SteadyConfig:
     regions: Sequence = ()                   # detector regions ((xmin..zmax) m, (nx, ny, nz)), one geometry
     nscat_curve: bool = False                # also kappa for every N_scat_max' <= n_scat_max (kappa_nscat)
     det_per_bin: bool = False                # detector outputs per frequency bin (det: [n_det][n_bins][4])
+    tail_lanes: int = 0                      # FP32 tail: warps with <= this many particles left draw ahead (0: 8, -1: off)
 
 
 def _event_handles(pair):
@@ -171,6 +172,7 @@ def steady_params(cfg: SteadyConfig, n_particles: np.ndarray) -> "L.SteadyParams
     p.cell_flux_axis = int(bool(cfg.cell_flux_axis))
     p.nscat_curve = int(bool(cfg.nscat_curve))
     p.det_per_bin = int(bool(cfg.det_per_bin))
+    p.tail_lanes = int(cfg.tail_lanes)
     regions = list(cfg.regions or ())
     if regions:
         boxes = np.ascontiguousarray([r[0] for r in regions], dtype=np.float64)

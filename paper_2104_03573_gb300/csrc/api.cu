@@ -412,6 +412,8 @@ struct SteadyWs {
   unsigned long long* work;
   int* flags;
   unsigned long long* t0;
+  unsigned long long* park_n;   // FP32 tail: particles parked, and taken by the tail kernel
+  unsigned long long* park_rd;
   char* zero_end;
   double* dirs;
   double* dpi;
@@ -427,8 +429,20 @@ struct SteadyWs {
   double* det;          // host staging of the outputs
   double* nscat;        // [R][G][K + 1][4] N_scat_max curve sums, R = nscat_replicas (zeroed)
   double* kn;           // host staging of the curve
+  unsigned char* park;  // FP32 tail: park_cap records of park_record_bytes() (last, not zeroed)
+  uint64_t park_cap;
   size_t bytes;
 };
+
+// Records the FP32 steady tracer can park for its tail kernel: at most
+// tail_max per resident warp of the main kernel (64 warps per SM), and never
+// more than the run's particles.
+uint64_t park_capacity(const mcbte_steady_params* p, uint64_t total) {
+  if (p->precision != MCBTE_FP32_TRACE || p->tail_lanes < 0) return 0;
+  const uint64_t tail = p->tail_lanes == 0 ? 8 : (uint64_t)p->tail_lanes;
+  const uint64_t cap = (uint64_t)sm_count() * 64ull * tail;
+  return cap < total ? cap : total;
+}
 
 // Copies of the N_scat_max curve sums: every relaxation adds to one of K + 1
 // slots per geometry, and one copy for the whole grid serialises those
@@ -444,7 +458,7 @@ int nscat_replicas(int G, int K) {
 
 SteadyWs layout_steady(char* base, int G, int n, int nc, uint64_t total, bool grad, bool replay, int nd,
                        bool host_out, bool want_ev, bool want_x, bool want_T, bool want_q, bool want_qbin,
-                       uint64_t n_det = 0, int nscat = 0) {
+                       uint64_t n_det = 0, int nscat = 0, uint64_t park_cap = 0) {
   Carve c;
   c.base = base;
   SteadyWs w{};
@@ -466,6 +480,8 @@ SteadyWs layout_steady(char* base, int G, int n, int nc, uint64_t total, bool gr
   w.work = c.take<unsigned long long>(1);
   w.flags = c.take<int>(2);
   w.t0 = c.take<unsigned long long>(1);
+  w.park_n = c.take<unsigned long long>(1);
+  w.park_rd = c.take<unsigned long long>(1);
   w.det_raw = n_det ? c.take<double>(4 * n_det) : nullptr;
   w.det_q = n_det ? c.take<long long>(4 * n_det) : nullptr;
   w.nscat = nscat ? c.take<double>((size_t)nscat_replicas(G, nscat) * G * (size_t)(nscat + 1) * 4) : nullptr;
@@ -488,6 +504,8 @@ SteadyWs layout_steady(char* base, int G, int n, int nc, uint64_t total, bool gr
     w.dkdir = (grad && nd > 0) ? c.take<double>(2 * (size_t)nd) : nullptr;
     w.kn = nscat ? c.take<double>((size_t)G * (size_t)nscat * 2) : nullptr;
   }
+  w.park_cap = park_cap;
+  w.park = park_cap ? c.take<unsigned char>(park_cap * park_record_bytes()) : nullptr;
   w.bytes = c.off + 256;
   return w;
 }
@@ -505,6 +523,8 @@ mcbte_status check_steady(const mcbte_material* m, const mcbte_geometry* const* 
   if (p->n_scat_max < 0) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: n_scat_max < 0");
   if (p->refill_threshold < 0 || p->refill_threshold > 32)
     return fail(MCBTE_ERR_INVALID_ARG, "run_steady: refill_threshold in [0, 32]");
+  if (p->tail_lanes < -1 || p->tail_lanes > 32)
+    return fail(MCBTE_ERR_INVALID_ARG, "run_steady: tail_lanes in [-1, 32]");
   if (p->threads_per_block != 0 && p->threads_per_block != 256 && p->threads_per_block != 512 &&
       p->threads_per_block != 768 && p->threads_per_block != 1024)
     return fail(MCBTE_ERR_INVALID_ARG, "run_steady: threads_per_block must be 0, 256, 512, 768 or 1024");
@@ -567,10 +587,18 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   const bool replay = grad && p->precision == MCBTE_FP32_TRACE;
   const uint64_t n_det = region_detectors(p->n_regions, p->region_grid);
   const uint64_t det_slots = steady_det_slots(p, n);
+  // the tail kernel's park buffer when the workspace has room for it (a
+  // caller's workspace sized without it still runs, without the tail kernel)
+  uint64_t park_cap = park_capacity(p, total);
   SteadyWs w = layout_steady(nullptr, G, n, nc, total, grad, replay, nd, host_out, out->events_pp, out->X_pp, out->T,
-                             out->q, out->q_bin, det_slots, nscat);
-  const size_t need = w.bytes;
+                             out->q, out->q_bin, det_slots, nscat, park_cap);
   char* base = static_cast<char*>(workspace);
+  if (base && ws_bytes < w.bytes && park_cap) {
+    park_cap = 0;
+    w = layout_steady(nullptr, G, n, nc, total, grad, replay, nd, host_out, out->events_pp, out->X_pp, out->T, out->q,
+                      out->q_bin, det_slots, nscat, 0);
+  }
+  const size_t need = w.bytes;
   bool own = false;
   if (!base) {
     CUDA_TRY(cudaMallocAsync((void**)&base, need, s));
@@ -580,7 +608,7 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   }
   char* aligned = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(base) + 255) & ~(uintptr_t)255);
   w = layout_steady(aligned, G, n, nc, total, grad, replay, nd, host_out, out->events_pp, out->X_pp, out->T, out->q,
-                    out->q_bin, det_slots, nscat);
+                    out->q_bin, det_slots, nscat, park_cap);
   auto release = [&]() {
     if (own) cudaFreeAsync(base, s);
   };
@@ -615,6 +643,7 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   C.budget_ns = (uint64_t)((p->time_budget_s > 0 ? p->time_budget_s : 120.0) * 1e9);
   C.seed_dev = reinterpret_cast<const unsigned long long*>(p->seed_device);
   C.refill_min = p->refill_threshold;
+  C.tail_max = p->tail_lanes == 0 ? 8 : (p->tail_lanes < 0 ? 0 : p->tail_lanes);
   C.cell_flux_axis = p->cell_flux_axis ? 1 : 0;
   C.ext = (p->n_regions > 0 || nscat > 0) ? 1 : 0;
   for (int g = 0; g < G; ++g) C.ext |= uses_ext(m, geoms[g]->host) ? 1 : 0;
@@ -651,6 +680,11 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   A.flags = w.flags;
   A.det_raw = w.det_raw;
   A.det_q = w.det_q;
+  A.park = w.park;
+  A.park_n = w.park_n;
+  A.park_rd = w.park_rd;
+  A.park_stride = park_record_bytes();
+  A.park_cap = w.park_cap;
   A.events_pp = host_out ? w.events_pp : out->events_pp;
   A.X_pp = host_out ? w.X_pp : out->X_pp;
   if (grad && nd > 0) {
@@ -670,6 +704,8 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
     RUN_TRY(launch_steady(p->precision, false, w.geos, w.offs, m->view, C, A1, p->threads_per_block,
                           p->blocks_per_sm, s));
     RUN_TRY(cudaMemsetAsync(w.work, 0, sizeof(unsigned long long), s));
+    RUN_TRY(cudaMemsetAsync(w.park_n, 0, sizeof(unsigned long long), s));
+    RUN_TRY(cudaMemsetAsync(w.park_rd, 0, sizeof(unsigned long long), s));
     Acc A2 = A;
     A2.X_pp = w.xrep;
     A2.events_pp = nullptr;
@@ -741,7 +777,8 @@ mcbte_status mcbte_steady_workspace_size(const mcbte_material* m, const mcbte_ge
   if (!bytes) return fail(MCBTE_ERR_INVALID_ARG, "workspace_size: null bytes");
   SteadyWs w = layout_steady(nullptr, n_geoms, m->n, p->n_cells, total, want_grad != 0,
                              want_grad != 0 && p->precision == MCBTE_FP32_TRACE, n_dirs, false, false, false, false,
-                             false, false, steady_det_slots(p, m->n), p->nscat_curve ? p->n_scat_max : 0);
+                             false, false, steady_det_slots(p, m->n), p->nscat_curve ? p->n_scat_max : 0,
+                             park_capacity(p, total));
   *bytes = w.bytes;
   return MCBTE_OK;
 }
@@ -1033,6 +1070,7 @@ mcbte_status mcbte_run_steady_noalloc(const mcbte_material* m, const mcbte_geome
   uint64_t total = 0;
   mcbte_status st = check_steady(m, geoms, n_geoms, p, &total);
   if (st != MCBTE_OK) return st;
+  // (the tail kernel's park buffer is used only when it fits as well)
   const SteadyWs w = layout_steady(nullptr, n_geoms, m->n, p->n_cells, total, false, false, 0, false, false, false,
                                    false, false, false, steady_det_slots(p, m->n),
                                    p->nscat_curve ? p->n_scat_max : 0);

@@ -21,10 +21,11 @@ struct SmemPlan {
   int binf_in_smem;    // per-bin {v, 1/v, Lambda} in shared memory
   int qbin_in_smem;    // frequency-resolved flux privatised per block
   int cells_in_smem;   // cell tallies privatised per block
+  int tail_slots;      // the tail's per-thread draw slots (first in the layout)
   size_t bytes;
 };
 
-SmemPlan plan_smem_f32(int n_bins, int n_geoms, int n_cells, int per_bin, size_t budget);
+SmemPlan plan_smem_f32(int n_bins, int n_geoms, int n_cells, int per_bin, size_t budget, int tail_threads = 0);
 
 cudaError_t launch_setup(const SetupArgs& a, int n_geoms, const MatView& M, int transient, double t_max_s,
                          int tally_axis, GeoRun* geos, uint64_t* offs, unsigned long long* t0, cudaStream_t s);
@@ -46,6 +47,9 @@ struct SteadyOutDev {
 
 cudaError_t launch_steady_f32(bool grad, bool cells, const GeoRun* geos, const uint64_t* offs, const MatView& M,
                               const RunCfg& C, const Acc& A, int threads, int bps, cudaStream_t s);
+// the same with the main kernel that parks its tail and the tail kernel
+cudaError_t launch_steady_f32_tail(bool grad, bool cells, const GeoRun* geos, const uint64_t* offs, const MatView& M,
+                                   const RunCfg& C, const Acc& A, int threads, int bps, cudaStream_t s);
 cudaError_t launch_transient_f32(const GeoRun* geos, const MatView& M, const RunCfg& C, const Acc& A, int threads,
                                  int bps, cudaStream_t s);
 
@@ -84,6 +88,8 @@ struct MatBuild {
 cudaError_t launch_material_build(const MatBuild& b, cudaStream_t s);
 
 int sm_count();
+// bytes of one parked particle of the FP32 steady tracer's tail (both passes)
+size_t park_record_bytes();
 // n_groups groups of four 64-bit reductions into records of `slots` (the
 // measurement utility mcbte_l2_reduction_probe)
 cudaError_t launch_l2_reduction_probe(unsigned long long* slots, uint64_t n_rec, uint64_t n_groups, cudaStream_t s);

@@ -6,6 +6,7 @@
 // Internal units: length nm, time ps, velocity nm/ps.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -31,19 +32,22 @@ __host__ __device__ __forceinline__ uint64_t spec_threshold(double p) {
 // Geometry as the tracer sees it, derived on the device by the setup kernel
 // from the caller's SI descriptor (lengths in nm, specularities as 32-bit
 // integer thresholds, isothermal faces and sources resolved).
-struct GeoRun {
-  double L[3];
-  double cx, cy, r2;
+struct alignas(128) GeoRun {
+  // What the FP32 event step reads at every event, together in the record's
+  // first 128 bytes (one L1 line: a batch of many geometries keeps every
+  // geometry's line cached); the rest is read at emission or by the FP64 path.
   float Lf[3];
   float cxf, cyf, r2f;
-  uint64_t pthr[6];
-  uint64_t pthr_pore;
-  int type[6];
   int pore;
-  // internal walls (Sec. 4.2), nm, oriented as given; normal into the solid
   int n_inner;
   int fbin;                    // bit f: face f takes the per-bin specularity
   int sbin;                    // bit k: wall k takes the per-bin specularity
+  int type[6];
+  uint64_t pthr[6];
+  uint64_t pthr_pore;
+  double L[3];
+  double cx, cy, r2;
+  // internal walls (Sec. 4.2), nm, oriented as given; normal into the solid
   double sx1[kMaxInner], sy1[kMaxInner], sx2[kMaxInner], sy2[kMaxInner], snx[kMaxInner], sny[kMaxInner];
   float sx1f[kMaxInner], sy1f[kMaxInner], sx2f[kMaxInner], sy2f[kMaxInner], snxf[kMaxInner], snyf[kMaxInner];
   uint64_t sthr[kMaxInner];
@@ -68,6 +72,7 @@ struct GeoRun {
   uint64_t n;                  // particles of this geometry
   uint64_t offset;             // first flattened particle index
 };
+static_assert(offsetof(GeoRun, pthr_pore) + sizeof(uint64_t) <= 128, "FP32 per-event fields within one line");
 
 // Material as the tracer sees it (device pointers).
 struct MatView {

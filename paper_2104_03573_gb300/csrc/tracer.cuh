@@ -65,6 +65,8 @@ struct RunCfg {
   double* nscat_acc;    // [nscat_rep][G][n_scat_max + 1][4]
   int nscat_rep;
   int det_nb;           // steady detector sums per detector (1) or per detector and bin (n_bins)
+  int tail_max;         // FP32 steady tracer: the tail's draw slots serve warps with at most
+                        // this many particles in flight once the work counter has run out (0: off)
 };
 
 // Transient detector region (Sec. 4.5): a closed axis-aligned cuboid split
@@ -181,6 +183,14 @@ struct Acc {
   double* X_pp;               // [total] or null
   unsigned long long* work;   // [1] persistent work counter
   int* flags;                 // [1] bit 0: time budget hit
+  // FP32 steady tracer's tail: particles the main kernel hands to the tail
+  // kernel (records of park_stride bytes), how many it parked, how many the
+  // tail kernel has taken
+  unsigned char* park;
+  unsigned long long* park_n;
+  unsigned long long* park_rd;
+  size_t park_stride;
+  uint64_t park_cap;          // records the buffer holds (0: no tail kernel)
 };
 
 __device__ __forceinline__ size_t sum_copy() { return (size_t)(blockIdx.x & (unsigned)(kSumCopies - 1)); }
@@ -221,19 +231,6 @@ __device__ __forceinline__ void load_bin(Particle<R>& p, const MatView& M, const
   }
 }
 
-// Two-phonon clock (Sec. 3.3): a new exponential distance with the current
-// bin's mean free path v tau_imp, from sub-block 256 of the particle's
-// current event; +inf without impurity scattering.
-template <typename R>
-__device__ __forceinline__ R draw_d2(const Particle<R>& p, const MatView& M, const float4* binf, uint32_t k0,
-                                     uint32_t k1) {
-  if (!M.imp) return Num<R>::inf();
-  const R lam2 = sizeof(R) == 8 ? (R)M.lam2_d[p.bin] : (R)binf[p.bin].w;
-  if (isinf(lam2)) return Num<R>::inf();
-  const uint4 w = philox(make_uint4(p.pid, (uint32_t)p.g, p.e, 256u), k0, k1);
-  return lam2 * (-Num<R>::log_(Num<R>::oc53(w.x, w.y)));
-}
-
 // Shared resampling step of emissions and relaxations: bin from an alias
 // table (~C v or ~C at emission, Eqs. iso_flux / grad_flux_sim / Nbin;
 // ~C/tau at relaxation, Eq. n_scatt), direction with polar cosine
@@ -255,22 +252,104 @@ __device__ __forceinline__ void resample(Particle<R>& p, const MatView& M, const
 }
 
 // FP32 relaxation from one Philox block (tables of at most kOneBlockBins
-// bins): word 0 times n gives the alias column (high half) and a 32-bit
-// uniform for its test (low half, compared with the threshold's high word:
-// the acceptance is off by at most n / 2^32), word 1 the flight, words 2 and
-// 3 the isotropic direction.  A 24-bit flight uniform is all FP32 resolves.
+// bins, draw_words): word 0 times n gives the alias column (high half) and a
+// 32-bit uniform for its test (low half, compared with the threshold's high
+// word: the acceptance is off by at most n / 2^32), word 1 the flight, words
+// 2 and 3 the isotropic direction.  A 24-bit flight uniform is all FP32
+// resolves.
 constexpr int kOneBlockBins = 65536;
 
-template <typename R>
-__device__ __forceinline__ void resample_relax1(Particle<R>& p, const MatView& M, const uint4* rec, const float4* binf,
-                                                uint4 w) {
-  const uint64_t m = (uint64_t)w.x * (uint64_t)M.n;
+// ------------------------------------------------------------------ FP32 event draws
+// What the words of one event decide whatever the particle's state (FP32
+// path, tables of at most kOneBlockBins bins): from sub-block 0 the test
+// word, the relaxation's bin (alias draw ~ C/tau, Eq. n_scatt), its flight
+// factor -ln R (Eq. time_to_scat) and isotropic direction (Eq. angle_gen),
+// and the Lambertian direction about a surface normal in the normal's frame
+// (mu = sqrt(R), Eq. wall_dir); the two-phonon factor -ln R2 from sub-block
+// 256 and the measure-valued reservoir word from sub-block 257 when those are
+// in use.  12 words, stored as three 16-byte vectors.
+struct __align__(16) Draw32 {
+  uint32_t wx;             // sub 0 word 0: specular / alias test word
+  int bin;                 // relaxation bin
+  float E;                 // -ln R of the relaxation flight
+  float iso[3];            // isotropic unit vector
+  float lam[3];            // (mu, s cos phi, s sin phi), s = sqrt(1 - mu^2)
+  float E2;                // -ln R2 (sub-block 256)
+  uint32_t mv_lo, mv_hi;   // sub-block 257 words 0 and 1
+};
+
+// Sub-block 0 of an event: one Philox block, one alias lookup, ln, two square
+// roots and one sincos.  Products that meet a sum are written with explicit
+// roundings so every caller computes the same bits.
+__device__ __forceinline__ void draw_words(Draw32& d, uint4 w, const uint4* rec, int n) {
+  d.wx = w.x;
+  const uint64_t m = (uint64_t)w.x * (uint64_t)n;
   const int col = (int)(m >> 32);
   const uint4 a = rec[col];
-  p.bin = ((uint32_t)m < a.y) ? col : (int)a.z;
-  dir_about_axis<R>(p.u, 2, R(1), R(1) - R(2) * Num<R>::oc(w.z), w.w);
-  load_bin(p, M, binf);
-  p.d_rel = p.lam * (-Num<R>::log_(Num<R>::oc(w.y)));
+  d.bin = ((uint32_t)m < a.y) ? col : (int)a.z;
+  d.E = -Num<float>::log_(Num<float>::oc(w.y));
+  float sn, cs;
+  Num<float>::sincos2pi(Num<float>::co(w.w), &sn, &cs);
+  const float mi = 1.0f - 2.0f * Num<float>::oc(w.z);      // exact
+  const float si = sqrtf(fmaxf(0.0f, __fmaf_rn(-mi, mi, 1.0f)));
+  d.iso[0] = __fmul_rn(si, cs);
+  d.iso[1] = __fmul_rn(si, sn);
+  d.iso[2] = mi;
+  const float ml = sqrtf(Num<float>::oc(w.z));
+  const float sl = sqrtf(fmaxf(0.0f, __fmaf_rn(-ml, ml, 1.0f)));
+  d.lam[0] = ml;
+  d.lam[1] = __fmul_rn(sl, cs);
+  d.lam[2] = __fmul_rn(sl, sn);
+}
+
+// Two-phonon factor -ln R2 from the words of sub-block 256.
+__device__ __forceinline__ float draw_e2(uint4 w) { return -Num<float>::log_(Num<float>::oc53(w.x, w.y)); }
+
+// Where an FP32 event takes its draws.  DrawInline computes them from the
+// event's Philox blocks when the event needs them; DrawSlot reads the ones a
+// warp computed beforehand for this event (the same functions, so the same
+// bits).  ctr is (particle, geometry, event, 0).
+struct DrawInline {
+  __device__ __forceinline__ Draw32 sub0(uint4 ctr, uint32_t k0, uint32_t k1, const uint4* rec, int n) const {
+    Draw32 d;
+    draw_words(d, philox(ctr, k0, k1), rec, n);
+    return d;
+  }
+  __device__ __forceinline__ float e2(uint4 ctr, uint32_t k0, uint32_t k1) const {
+    ctr.w = 256u;
+    return draw_e2(philox(ctr, k0, k1));
+  }
+  __device__ __forceinline__ unsigned long long mv(uint4 ctr, uint32_t k0, uint32_t k1) const {
+    ctr.w = 257u;
+    const uint4 r = philox(ctr, k0, k1);
+    return (unsigned long long)r.x | ((unsigned long long)r.y << 32);
+  }
+};
+
+struct DrawSlot {
+  const Draw32* s;   // this event's draws (shared memory)
+  __device__ __forceinline__ Draw32 sub0(uint4, uint32_t, uint32_t, const uint4*, int) const { return *s; }
+  __device__ __forceinline__ float e2(uint4, uint32_t, uint32_t) const { return s->E2; }
+  __device__ __forceinline__ unsigned long long mv(uint4, uint32_t, uint32_t) const {
+    return (unsigned long long)s->mv_lo | ((unsigned long long)s->mv_hi << 32);
+  }
+};
+
+// Two-phonon clock (Sec. 3.3): a new exponential distance with the current
+// bin's mean free path v tau_imp, from sub-block 256 of the particle's
+// current event; +inf without impurity scattering.
+template <typename R, class Src = DrawInline>
+__device__ __forceinline__ R draw_d2(const Particle<R>& p, const MatView& M, const float4* binf, uint32_t k0,
+                                     uint32_t k1, const Src& src = Src()) {
+  if (!M.imp) return Num<R>::inf();
+  const R lam2 = sizeof(R) == 8 ? (R)M.lam2_d[p.bin] : (R)binf[p.bin].w;
+  if (isinf(lam2)) return Num<R>::inf();
+  if constexpr (sizeof(R) == 4) {
+    return lam2 * src.e2(make_uint4(p.pid, (uint32_t)p.g, p.e, 0u), k0, k1);
+  } else {
+    const uint4 w = philox(make_uint4(p.pid, (uint32_t)p.g, p.e, 256u), k0, k1);
+    return lam2 * (-Num<R>::log_(Num<R>::oc53(w.x, w.y)));
+  }
 }
 
 // Emission-only part of event 0 (Sec. 3.2: source by cumulative energy,
@@ -623,12 +702,13 @@ struct MvdState {
     sel_spec = false;
     phase = false;
   }
-  __device__ __forceinline__ bool branch(bool spec, uint4 ctr, uint32_t k0, uint32_t k1) {
+  // word(): the 64-bit reservoir word of this event (sub-block 257), drawn
+  // only in the nominal trace
+  template <class Word>
+  __device__ __forceinline__ bool branch(bool spec, Word word) {
     ++K;
     if (phase) return K == sel ? !spec : spec;
-    ctr.w = 257u;
-    const uint4 r = philox(ctr, k0, k1);
-    const unsigned long long v = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
+    const unsigned long long v = word();
     if (v <= 0xFFFFFFFFFFFFFFFFull / (unsigned long long)K) {
       sel = K;
       sel_spec = spec;
@@ -652,7 +732,8 @@ struct GradOff {
   template <typename C>
   __device__ __forceinline__ void flight(bool, double, double, C) {}
   __device__ __forceinline__ void resampled(int, double) {}
-  __device__ __forceinline__ bool pore_branch(bool spec, double, double, uint4, uint32_t, uint32_t) { return spec; }
+  template <class Word>
+  __device__ __forceinline__ bool pore_branch(bool spec, double, double, Word) { return spec; }
   __device__ __forceinline__ int periods() const { return 0; }
   __device__ __forceinline__ int period_bin(int) const { return 0; }
   __device__ __forceinline__ double period_value(int, double) const { return 0.0; }
@@ -704,8 +785,9 @@ struct GradList {
     n_res++;
     sum_x_res += Xnow;
   }
-  __device__ __forceinline__ bool pore_branch(bool spec, double p, double Xnow, uint4 ctr, uint32_t k0, uint32_t k1) {
-    if (mvd) return mv.branch(spec, ctr, k0, k1);
+  template <class Word>
+  __device__ __forceinline__ bool pore_branch(bool spec, double p, double Xnow, Word word) {
+    if (mvd) return mv.branch(spec, word);
     const double sc = spec ? 1.0 / p : -1.0 / (1.0 - p);
     PA += sc;
     PB += sc * Xnow;
@@ -767,8 +849,9 @@ struct GradReplay {
     n_res++;
     sum_x_res += Xnow;
   }
-  __device__ __forceinline__ bool pore_branch(bool spec, double p, double, uint4 ctr, uint32_t k0, uint32_t k1) {
-    if (mvd) return mv.branch(spec, ctr, k0, k1);
+  template <class Word>
+  __device__ __forceinline__ bool pore_branch(bool spec, double p, double, Word word) {
+    if (mvd) return mv.branch(spec, word);
     pa += spec ? (float)(1.0 / p) : (float)(-1.0 / (1.0 - p));
     return spec;
   }
@@ -800,11 +883,11 @@ __device__ __forceinline__ double* nscat_slot(const RunCfg& C, int g, int k) {
   return C.nscat_acc + ((rep * (size_t)C.n_geoms + (size_t)g) * (size_t)(C.n_scat_max + 1) + (size_t)k) * 4;
 }
 
-template <typename R, class Grad, class Tally, bool EXT = true>
+template <typename R, class Grad, class Tally, bool EXT = true, class Src = DrawInline>
 __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_relax,
                                            const float4* binf, const RunCfg& C, uint32_t k0, uint32_t k1,
                                            bool relax, bool relax2, int face, R seg, const Tally& T, Grad& gr,
-                                           double Xnow) {
+                                           double Xnow, const Src& src = Src()) {
   ++p.e;
   uint4 ctr = make_uint4(p.pid, (uint32_t)p.g, p.e, 0u);
   if (relax) {
@@ -821,15 +904,20 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
     if (C.n_scat_max > 0 && p.n_relax >= C.n_scat_max) return STEP_DONE;
     // the relaxation period in this bin is over: frequency-resolved flux
     T.period_end(p);
-    const uint4 w = philox(ctr, k0, k1);
     if (sizeof(R) == 4 && M.n <= kOneBlockBins) {
-      resample_relax1<R>(p, M, rec_relax, binf, w);
+      const Draw32 d = src.sub0(ctr, k0, k1, rec_relax, M.n);
+      p.bin = d.bin;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) p.u[b] = (R)d.iso[b];
+      load_bin(p, M, binf);
+      p.d_rel = p.lam * (R)d.E;
     } else {
+      const uint4 w = philox(ctr, k0, k1);
       ctr.w = 1u;
       const uint4 w1 = philox(ctr, k0, k1);
       resample<R>(p, M, rec_relax, binf, w, w1, false, 2, R(1));
     }
-    if constexpr (EXT) p.d2 = draw_d2(p, M, binf, k0, k1);   // both clocks restart in the new mode (Sec. 3.3 (i))
+    if constexpr (EXT) p.d2 = draw_d2(p, M, binf, k0, k1, src);   // both clocks restart in the new mode (Sec. 3.3 (i))
     if (Grad::on) gr.resampled(p.bin, Xnow);
     return STEP_ALIVE;
   }
@@ -838,9 +926,15 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
     if (relax2) {
       // two-phonon scattering (Sec. 3.5.1, Sec. 3.3 (ii)): same mode, new
       // isotropic direction, new two-phonon clock; the three-phonon clock runs on
-      const uint4 w = philox(ctr, k0, k1);
-      dir_about_axis<R>(p.u, 2, R(1), R(1) - R(2) * Num<R>::oc(w.z), w.w);
-      p.d2 = draw_d2(p, M, binf, k0, k1);
+      if constexpr (sizeof(R) == 4) {
+        const Draw32 d = src.sub0(ctr, k0, k1, rec_relax, M.n);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) p.u[b] = (R)d.iso[b];
+      } else {
+        const uint4 w = philox(ctr, k0, k1);
+        dir_about_axis<R>(p.u, 2, R(1), R(1) - R(2) * Num<R>::oc(w.z), w.w);
+      }
+      p.d2 = draw_d2(p, M, binf, k0, k1, src);
       return STEP_ALIVE;
     }
     p.d2 = p.d2 - seg;
@@ -859,74 +953,96 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
       return STEP_ALIVE;
     }
     put3<R>(p.x, a, mx ? La : R(0));
-    const uint4 w = philox(ctr, k0, k1);
-    const bool spec_f = (uint64_t)w.x < ((EXT && ((g.fbin >> face) & 1)) ? M.spec_thr[p.bin] : g.pthr[face]);
     if constexpr (sizeof(R) == 4) {
       // FP32: both outcomes, then a select (no branch on the draw)
+      const Draw32 d = src.sub0(ctr, k0, k1, rec_relax, M.n);
+      const bool spec_f = (uint64_t)d.wx < ((EXT && ((g.fbin >> face) & 1)) ? M.spec_thr[p.bin] : g.pthr[face]);
       R ud[3];
-      dir_about_axis<R>(ud, a, mx ? R(-1) : R(1), Num<R>::sqrt_(Num<R>::oc(w.z)), w.w);
+      put3_cyclic<R>(ud, a, mx ? -d.lam[0] : d.lam[0], d.lam[1], d.lam[2]);
       const R flip = -sel3(p.u, a);
 #pragma unroll
       for (int b = 0; b < 3; ++b) p.u[b] = spec_f ? (b == a ? flip : p.u[b]) : ud[b];
-    } else if (spec_f) {
-      put3<R>(p.u, a, -sel3(p.u, a));
     } else {
-      dir_about_axis<R>(p.u, a, mx ? R(-1) : R(1), Num<R>::sqrt_(Num<R>::oc(w.z)), w.w);
+      const uint4 w = philox(ctr, k0, k1);
+      const bool spec_f = (uint64_t)w.x < ((EXT && ((g.fbin >> face) & 1)) ? M.spec_thr[p.bin] : g.pthr[face]);
+      if (spec_f) put3<R>(p.u, a, -sel3(p.u, a));
+      else dir_about_axis<R>(p.u, a, mx ? R(-1) : R(1), Num<R>::sqrt_(Num<R>::oc(w.z)), w.w);
     }
     return STEP_ALIVE;
   }
-  R nx, ny;
-  bool spec;
-  const uint4 w = philox(ctr, k0, k1);
-  if (EXT && face >= 7) {
-    // internal wall (Sec. 4.2): onto its line, then reflect about its normal
-    const int k = face - 7;
-    nx = sizeof(R) == 8 ? (R)g.snx[k] : (R)g.snxf[k];
-    ny = sizeof(R) == 8 ? (R)g.sny[k] : (R)g.snyf[k];
-    const R dn = (p.x[0] - (sizeof(R) == 8 ? (R)g.sx1[k] : (R)g.sx1f[k])) * nx +
-                 (p.x[1] - (sizeof(R) == 8 ? (R)g.sy1[k] : (R)g.sy1f[k])) * ny;
-    p.x[0] = p.x[0] - dn * nx;
-    p.x[1] = p.x[1] - dn * ny;
-    spec = (uint64_t)w.x < (((g.sbin >> k) & 1) ? M.spec_thr[p.bin] : g.sthr[k]);
-  } else {
-    // pore wall: the cylinder's outward normal points into the solid
-    const R cx = sizeof(R) == 8 ? (R)g.cx : (R)g.cxf;
-    const R cy = sizeof(R) == 8 ? (R)g.cy : (R)g.cyf;
-    nx = p.x[0] - cx;
-    ny = p.x[1] - cy;
-    const R len = Num<R>::sqrt_(nx * nx + ny * ny);
-    nx = nx / len;
-    ny = ny / len;
-    spec = (uint64_t)w.x < g.pthr_pore;
-    if (Grad::on) spec = gr.pore_branch(spec, g.p_pore, Xnow, ctr, k0, k1);
-  }
   if constexpr (sizeof(R) == 4) {
-    // FP32: both outcomes, then a select (no branch on the draw)
-    const R un = p.u[0] * nx + p.u[1] * ny;
-    const R mu = Num<R>::sqrt_(Num<R>::oc(w.z));
-    const R sn = Num<R>::sqrt_(Num<R>::fmax_(R(0), R(1) - mu * mu));
-    R sphi, cphi;
-    Num<R>::sincos2pi(Num<R>::co(w.w), &sphi, &cphi);
-    const R sc = sn * cphi;
-    const R s0 = p.u[0] - (R(2) * un) * nx, s1 = p.u[1] - (R(2) * un) * ny;
-    p.u[0] = spec ? s0 : mu * nx - sc * ny;
-    p.u[1] = spec ? s1 : mu * ny + sc * nx;
-    p.u[2] = spec ? p.u[2] : sn * sphi;
-  } else if (spec) {
-    const R un = p.u[0] * nx + p.u[1] * ny;
-    p.u[0] = p.u[0] - (R(2) * un) * nx;
-    p.u[1] = p.u[1] - (R(2) * un) * ny;
+    // FP32 pore or internal wall: both outcomes, then a select (no branch on
+    // the draw); explicit roundings keep every draw source's bits equal
+    const Draw32 d = src.sub0(ctr, k0, k1, rec_relax, M.n);
+    float nx, ny;
+    bool spec;
+    if (EXT && face >= 7) {
+      // internal wall (Sec. 4.2): onto its line, then reflect about its normal
+      const int k = face - 7;
+      nx = g.snxf[k];
+      ny = g.snyf[k];
+      const float dn = __fmaf_rn(p.x[0] - g.sx1f[k], nx, __fmul_rn(p.x[1] - g.sy1f[k], ny));
+      p.x[0] = __fmaf_rn(-dn, nx, p.x[0]);
+      p.x[1] = __fmaf_rn(-dn, ny, p.x[1]);
+      spec = (uint64_t)d.wx < (((g.sbin >> k) & 1) ? M.spec_thr[p.bin] : g.sthr[k]);
+    } else {
+      // pore wall: the cylinder's outward normal points into the solid
+      nx = p.x[0] - g.cxf;
+      ny = p.x[1] - g.cyf;
+      const float len = sqrtf(__fmaf_rn(nx, nx, __fmul_rn(ny, ny)));
+      nx = nx / len;
+      ny = ny / len;
+      spec = (uint64_t)d.wx < g.pthr_pore;
+      if (Grad::on) spec = gr.pore_branch(spec, g.p_pore, Xnow, [&] { return src.mv(ctr, k0, k1); });
+    }
+    const float two_un = 2.0f * __fmaf_rn(p.u[0], nx, __fmul_rn(p.u[1], ny));
+    const float s0 = __fmaf_rn(-two_un, nx, p.u[0]);
+    const float s1 = __fmaf_rn(-two_un, ny, p.u[1]);
+    const float l0 = __fmaf_rn(d.lam[0], nx, -__fmul_rn(d.lam[1], ny));
+    const float l1 = __fmaf_rn(d.lam[0], ny, __fmul_rn(d.lam[1], nx));
+    p.u[0] = spec ? s0 : l0;
+    p.u[1] = spec ? s1 : l1;
+    p.u[2] = spec ? p.u[2] : d.lam[2];
+    return STEP_ALIVE;
   } else {
-    const R mu = Num<R>::sqrt_(Num<R>::oc(w.z));
-    const R sn = Num<R>::sqrt_(Num<R>::fmax_(R(0), R(1) - mu * mu));
-    R sphi, cphi;
-    Num<R>::sincos2pi(Num<R>::co(w.w), &sphi, &cphi);
-    const R sc = sn * cphi;
-    p.u[0] = mu * nx - sc * ny;
-    p.u[1] = mu * ny + sc * nx;
-    p.u[2] = sn * sphi;
+    R nx, ny;
+    bool spec;
+    const uint4 w = philox(ctr, k0, k1);
+    if (EXT && face >= 7) {
+      // internal wall (Sec. 4.2): onto its line, then reflect about its normal
+      const int k = face - 7;
+      nx = (R)g.snx[k];
+      ny = (R)g.sny[k];
+      const R dn = (p.x[0] - (R)g.sx1[k]) * nx + (p.x[1] - (R)g.sy1[k]) * ny;
+      p.x[0] = p.x[0] - dn * nx;
+      p.x[1] = p.x[1] - dn * ny;
+      spec = (uint64_t)w.x < (((g.sbin >> k) & 1) ? M.spec_thr[p.bin] : g.sthr[k]);
+    } else {
+      // pore wall: the cylinder's outward normal points into the solid
+      nx = p.x[0] - (R)g.cx;
+      ny = p.x[1] - (R)g.cy;
+      const R len = Num<R>::sqrt_(nx * nx + ny * ny);
+      nx = nx / len;
+      ny = ny / len;
+      spec = (uint64_t)w.x < g.pthr_pore;
+      if (Grad::on) spec = gr.pore_branch(spec, g.p_pore, Xnow, [&] { return DrawInline().mv(ctr, k0, k1); });
+    }
+    if (spec) {
+      const R un = p.u[0] * nx + p.u[1] * ny;
+      p.u[0] = p.u[0] - (R(2) * un) * nx;
+      p.u[1] = p.u[1] - (R(2) * un) * ny;
+    } else {
+      const R mu = Num<R>::sqrt_(Num<R>::oc(w.z));
+      const R sn = Num<R>::sqrt_(Num<R>::fmax_(R(0), R(1) - mu * mu));
+      R sphi, cphi;
+      Num<R>::sincos2pi(Num<R>::co(w.w), &sphi, &cphi);
+      const R sc = sn * cphi;
+      p.u[0] = mu * nx - sc * ny;
+      p.u[1] = mu * ny + sc * nx;
+      p.u[2] = sn * sphi;
+    }
+    return STEP_ALIVE;
   }
-  return STEP_ALIVE;
 }
 
 // Steady detector regions (Sec. 4.5): the flight's track length in every
@@ -950,10 +1066,10 @@ __device__ __forceinline__ void region_steady(const Particle<R>& p, R seg, const
 // remaining relaxation distance (boundary wins ties, Sec. 3.3 case iii),
 // track-length tallies of the flight (Eqs. temp_steady, flux_x_steady), then
 // the event.
-template <typename R, class Grad, class Tally, bool EXT = true>
+template <typename R, class Grad, class Tally, bool EXT = true, class Src = DrawInline>
 __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_relax,
                                            const float4* binf, const RunCfg& C, uint32_t k0, uint32_t k1,
-                                           const Tally& T, Grad& gr) {
+                                           const Tally& T, Grad& gr, const Src& src = Src()) {
   if (p.e + 1u >= C.max_events) return STEP_TRUNCATED;
   R db;
   int face;
@@ -972,8 +1088,8 @@ __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, cons
   if (Grad::on) gr.flight(relax, (double)(seg / p.lam), Xb, c);
 #pragma unroll
   for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
-  return apply_event<R, Grad, Tally, EXT>(p, g, M, rec_relax, binf, C, k0, k1, relax, relax2, face, seg, T, gr,
-                                            Grad::on ? T.X(p) : 0.0);
+  return apply_event<R, Grad, Tally, EXT, Src>(p, g, M, rec_relax, binf, C, k0, k1, relax, relax2, face, seg, T, gr,
+                                                 Grad::on ? T.X(p) : 0.0, src);
 }
 
 // One flight + event of a transient particle: the flight also ends at

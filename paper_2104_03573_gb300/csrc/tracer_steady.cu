@@ -4,8 +4,12 @@
 // memory, reduced to FP64; per-lane refill from a warp-aggregated work
 // counter; alias tables in shared memory), plus the finalisation kernel.
 //
-// This file is compiled twice: with MCBTE_F64 (FP64 kernels, no fused
-// multiply-add) and with MCBTE_F32 (FP32 kernel).
+// This file is compiled three times: with MCBTE_F64 (FP64 kernels, no fused
+// multiply-add) and with MCBTE_F32 twice, MCBTE_F32_PART 0 (the FP32 kernels
+// of runs without the tail kernel, and the launch dispatch) and 1 (the FP32
+// kernels that park their tail, and the tail kernels), built in parallel.
+#include <atomic>
+
 #include "launch.h"
 
 #ifndef MCBTE_F64
@@ -13,6 +17,9 @@
 #endif
 #ifndef MCBTE_F32
 #define MCBTE_F32 0
+#endif
+#ifndef MCBTE_F32_PART
+#define MCBTE_F32_PART 0
 #endif
 
 namespace mcbte {
@@ -215,6 +222,99 @@ __device__ __forceinline__ void grad_finish_replay(GradReplay& gr, double X, int
   }
 }
 
+// A particle the main FP32 kernel hands to the tail kernel: the state the
+// FP32 steady step carries (v, 1/v and Lambda are the bin's, reloaded), its
+// index in the run and, in the gradient pass, the replay bookkeeping.  Only
+// these fields are stored, so parking keeps nothing else alive in the loop.
+struct ParkRec {
+  float x[3], u[3], d_rel, d2, s;
+  int bin, n_relax, g;
+  uint32_t e, pid;
+  long long Xq, Xqper;
+  uint64_t idx;
+  // gradient pass
+  double Xf, sum_x_res;
+  float a, d, pa, pd;
+  int bin_cur, n_res;
+  uint32_t mK, mKn, msel;
+  int mflags;   // bit 0 sel_spec, bit 1 phase
+  double dv[kMaxDirs];
+};
+
+template <bool GRAD, class GradT>
+__device__ __forceinline__ void park_store(ParkRec* r, const Particle<float>& p, uint64_t idx, const GradT& gr,
+                                           int n_dirs) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    r->x[a] = p.x[a];
+    r->u[a] = p.u[a];
+  }
+  r->d_rel = p.d_rel;
+  r->d2 = p.d2;
+  r->s = p.s;
+  r->bin = p.bin;
+  r->n_relax = p.n_relax;
+  r->g = p.g;
+  r->e = p.e;
+  r->pid = p.pid;
+  r->Xq = p.Xq;
+  r->Xqper = p.Xqper;
+  r->idx = idx;
+  if constexpr (GRAD) {
+    r->Xf = gr.Xf;
+    r->sum_x_res = gr.sum_x_res;
+    r->a = gr.a;
+    r->d = gr.d;
+    r->pa = gr.pa;
+    r->pd = gr.pd;
+    r->bin_cur = gr.bin_cur;
+    r->n_res = gr.n_res;
+    r->mK = gr.mv.K;
+    r->mKn = gr.mv.Kn;
+    r->msel = gr.mv.sel;
+    r->mflags = (gr.mv.sel_spec ? 1 : 0) | (gr.mv.phase ? 2 : 0);
+    for (int k = 0; k < n_dirs; ++k) r->dv[k] = gr.dv[k];
+  }
+}
+
+template <bool GRAD, class GradT>
+__device__ __forceinline__ void park_load(const ParkRec* r, Particle<float>& p, uint64_t& idx, GradT& gr, int n_dirs,
+                                          const MatView& M, const float4* binf) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    p.x[a] = r->x[a];
+    p.u[a] = r->u[a];
+  }
+  p.d_rel = r->d_rel;
+  p.d2 = r->d2;
+  p.s = r->s;
+  p.bin = r->bin;
+  p.n_relax = r->n_relax;
+  p.g = r->g;
+  p.e = r->e;
+  p.pid = r->pid;
+  p.Xq = r->Xq;
+  p.Xqper = r->Xqper;
+  idx = r->idx;
+  load_bin(p, M, binf);
+  if constexpr (GRAD) {
+    gr.Xf = r->Xf;
+    gr.sum_x_res = r->sum_x_res;
+    gr.a = r->a;
+    gr.d = r->d;
+    gr.pa = r->pa;
+    gr.pd = r->pd;
+    gr.bin_cur = r->bin_cur;
+    gr.n_res = r->n_res;
+    gr.mv.K = r->mK;
+    gr.mv.Kn = r->mKn;
+    gr.mv.sel = r->msel;
+    gr.mv.sel_spec = (r->mflags & 1) != 0;
+    gr.mv.phase = (r->mflags & 2) != 0;
+    for (int k = 0; k < n_dirs; ++k) gr.dv[k] = r->dv[k];
+  }
+}
+
 // Every lane owns one particle at a time.  When its particle terminates the
 // lane refills from a global work counter; the refills of a warp are
 // aggregated into one atomicAdd (ballot of the empty lanes, leader adds the
@@ -228,10 +328,26 @@ __device__ __forceinline__ void grad_finish_replay(GradReplay& gr, double X, int
 // more (phantom phase, the chosen pore hit flipped) before it refills.
 // CELLS: 0 no cell tallies, 1 T and three flux components, 2 T and the
 // tally-axis flux only.
-template <int CELLS, bool GRAD, int TPB, bool EXT>
+//
+// MODE 0: the main kernel of a run without the tail kernel.  The run's tail
+// (MODE 1 and 2): once the work counter has run out, a warp of the main
+// kernel (MODE 1) with at most C.tail_max particles in flight parks them
+// (ParkRec, A.park) and retires, so no warp idles most of its lanes for the
+// rest of the run.  The tail kernel (MODE 2, launched next on the same
+// stream) takes the parked particles instead of emitting new ones; once none
+// is left, a warp with at most C.tail_max particles in flight computes the
+// draws of their next events on all 32 lanes at once (one Draw32 per lane,
+// the warp's 32 slots shared out over its live particles, 32 / 2^ceil(log2
+// live) events each) and every live lane traces that many events reading its
+// slots (DrawSlot), so its dependent chain per event holds the geometry and
+// the tallies only.  The draws are the inline path's, the parked state is
+// resumed as it was: trajectories and tallies are bit for bit those of a
+// single kernel.
+template <int CELLS, bool GRAD, int TPB, bool EXT, int MODE>
 __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict__ geos,
                                                        const uint64_t* __restrict__ offs, MatView M, RunCfg C,
                                                        Acc A, SmemPlan S) {
+  constexpr bool TK = MODE == 2;
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* sp = smem;
   const int n = M.n;
@@ -241,6 +357,12 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
   long long* s_qbin = nullptr;
   long long* s_cP = nullptr;
   long long* s_cD = nullptr;
+  // the tail kernel's per-warp draw slots come first (16-byte aligned), 32 per warp
+  Draw32* slots = nullptr;
+  if (TK && S.tail_slots) {
+    slots = reinterpret_cast<Draw32*>(sp) + (threadIdx.x & ~31u);
+    sp += (size_t)TPB * sizeof(Draw32);
+  }
   if (S.relax_in_smem) {
     uint4* t = reinterpret_cast<uint4*>(sp);
     for (int i = threadIdx.x; i < n; i += blockDim.x) t[i] = M.rec_relax[i];
@@ -268,7 +390,8 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
   const unsigned lane = threadIdx.x & 31u;
   const uint64_t deadline = *C.t0 + C.budget_ns;
   Particle<float> p;
-  typename GradPick<GRAD, GradReplay>::type gr;
+  using GradT = typename GradPick<GRAD, GradReplay>::type;
+  GradT gr;
   if constexpr (GRAD) {
     gr.G = A.Gq;
     gr.n_dirs = C.n_dirs;
@@ -290,7 +413,26 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
   uint64_t idx = 0;
   const GeoRun* G = geos;
   const uint2 key = run_key(C);
-  const int refill_min = C.refill_min > 1 ? C.refill_min : 1;
+  const int refill_min = (C.refill_min > 1 && !TK) ? C.refill_min : 1;
+  // the tail: parking (main kernel) or the draws ahead (tail kernel)
+  const int tail_max = (TK ? (slots != nullptr && n <= kOneBlockBins) : (MODE == 1 && A.park_cap > 0)) ? C.tail_max : 0;
+  const uint64_t n_parked = TK ? min(*(volatile unsigned long long*)A.park_n, (unsigned long long)A.park_cap) : 0;
+  bool pool_dry = false;   // the same in every lane: nothing left to hand out
+  // the tallies of the lane's geometry
+  auto bind = [&](int g) {
+    if (g != acct.g) {
+      acct.flush(A);
+      acct.reset(g);
+    }
+    G = &geos[g];
+    if (CELLS) {
+      T.cP = S.cells_in_smem ? s_cP : A.cellPq + (size_t)g * nc * 4;
+      T.cD = S.cells_in_smem ? s_cD : A.cellDq + (size_t)g * (nc + 1) * 4;
+      T.h = G->Lf[C.cell_axis] / (float)nc;
+      T.inv_h = (float)nc / G->Lf[C.cell_axis];
+    }
+    T.qb = (C.per_bin && !GRAD) ? (S.qbin_in_smem ? s_qbin : A.qbinq + (size_t)g * n) : nullptr;
+  };
   // All 32 lanes stay in the loop until every lane of the warp is drained, so
   // the warp-wide votes below reconverge the warp at every event step.
   constexpr unsigned kAll = 0xffffffffu;
@@ -299,57 +441,122 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
     const unsigned dry = __ballot_sync(kAll, drained);
     if (dry == kAll) break;
     const unsigned live = __ballot_sync(kAll, alive);
-    const unsigned need = ~(dry | live);
-    // refill once enough lanes are idle (or no lane is busy)
-    if (need && (__popc(need) >= refill_min || live == 0u)) {
-      const int leader = __ffs(need) - 1;
-      unsigned long long base = 0;
-      if ((int)lane == leader) {
-        base = atomicAdd(A.work, (unsigned long long)__popc(need));
-        // the time budget is also checked each time the handed-out count
-        // crosses a multiple of 4096 (particles shorter than the per-event
-        // check interval would otherwise never look)
-        if (((base + (unsigned long long)__popc(need)) >> 12) != (base >> 12) && globaltimer_ns() > deadline)
-          atomicOr(A.flags, 1);
+    const int nlive = __popc(live);
+    int out = STEP_ALIVE;
+    if (MODE != 0 && pool_dry && nlive > 0 && nlive <= tail_max) {
+      if constexpr (MODE == 1) {
+        // park the warp's last particles for the tail kernel
+        const int leader = __ffs(live) - 1;
+        unsigned long long base = 0;
+        if ((int)lane == leader) base = atomicAdd(A.park_n, (unsigned long long)nlive);
+        base = __shfl_sync(kAll, base, leader);
+        if (alive) {
+          const unsigned long long slot = base + (unsigned long long)__popc(live & ((1u << lane) - 1u));
+          if (slot < A.park_cap) {
+            park_store<GRAD>(reinterpret_cast<ParkRec*>(A.park + slot * A.park_stride), p, idx, gr, C.n_dirs);
+            alive = false;
+            drained = true;
+          }
+        }
+        continue;   // lanes the buffer could not take trace on with the next votes (park_cap reached)
+      } else {
+        // log2 of the slots per particle: 5 - ceil(log2(nlive)), so nlive << sh <= 32
+        const int sh = 5 - (32 - __clz(nlive - 1));
+        const int r = (int)(lane >> sh);                                        // the live particle this lane draws for
+        unsigned mm = live;
+        for (int i = 0; i < r && mm; ++i) mm &= mm - 1u;
+        const int owner = mm ? __ffs(mm) - 1 : 0;
+        const uint32_t e_o = __shfl_sync(kAll, p.e, owner);
+        const uint32_t pid_o = __shfl_sync(kAll, p.pid, owner);
+        const int g_o = __shfl_sync(kAll, p.g, owner);
+        if (r < nlive) {
+          Draw32 d;
+          uint4 ctr = make_uint4(pid_o, (uint32_t)g_o, e_o + 1u + (lane & ((1u << sh) - 1u)), 0u);
+          draw_words(d, philox(ctr, key.x, key.y), relax, n);
+          d.E2 = 0.0f;
+          d.mv_lo = d.mv_hi = 0u;
+          if (EXT && M.imp) {
+            ctr.w = 256u;
+            d.E2 = draw_e2(philox(ctr, key.x, key.y));
+          }
+          if (GRAD && C.mvd) {
+            ctr.w = 257u;
+            const uint4 w7 = philox(ctr, key.x, key.y);
+            d.mv_lo = w7.x;
+            d.mv_hi = w7.y;
+          }
+          slots[lane] = d;
+        }
+        __syncwarp();
+        if (alive) {
+          const Draw32* mine = slots + (__popc(live & ((1u << lane) - 1u)) << sh);
+          for (int j = 0; j < (1 << sh); ++j) {
+            out = step_steady<float, GradT, decltype(T), EXT, DrawSlot>(p, *G, M, relax, binf, C, key.x, key.y, T,
+                                                                         gr, DrawSlot{mine + j});
+            if (out == STEP_ALIVE && (p.e & 255u) == 0u && globaltimer_ns() > deadline) {
+              atomicOr(A.flags, 1);
+              out = STEP_TRUNCATED;
+            }
+            if (out != STEP_ALIVE) break;
+          }
+        }
+        __syncwarp();   // the slots are rewritten in the next round
       }
-      base = __shfl_sync(kAll, base, leader);
-      if (!alive && !drained) {
-        idx = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
-        if (idx >= C.total || (*(volatile int*)A.flags & 1)) {
-          drained = true;
-          continue;
+    } else {
+      const unsigned need = ~(dry | live);
+      // refill once enough lanes are idle (or no lane is busy)
+      if (need && !pool_dry && (__popc(need) >= refill_min || live == 0u)) {
+        const int leader = __ffs(need) - 1;
+        unsigned long long base = 0;
+        if ((int)lane == leader) {
+          base = atomicAdd(TK ? A.park_rd : A.work, (unsigned long long)__popc(need));
+          // the time budget is also checked each time the handed-out count
+          // crosses a multiple of 4096 (particles shorter than the per-event
+          // check interval would otherwise never look)
+          if (((base + (unsigned long long)__popc(need)) >> 12) != (base >> 12) && globaltimer_ns() > deadline)
+            atomicOr(A.flags, 1);
         }
-        const int g = find_geom(offs, C.n_geoms, idx);
-        if (g != acct.g) {
-          acct.flush(A);
-          acct.reset(g);
+        base = __shfl_sync(kAll, base, leader);
+        const uint64_t avail = TK ? n_parked : C.total;
+        if (base + (unsigned long long)__popc(need) >= avail) pool_dry = true;
+        if (!alive && !drained) {
+          const uint64_t k = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
+          if (k >= avail || (*(volatile int*)A.flags & 1)) {
+            drained = true;
+            continue;
+          }
+          if constexpr (TK) {
+            // a parked particle, exactly as the main kernel left it
+            park_load<GRAD>(reinterpret_cast<const ParkRec*>(A.park + k * A.park_stride), p, idx, gr, C.n_dirs, M,
+                            binf);
+            bind(p.g);
+          } else {
+            idx = k;
+            const int g = find_geom(offs, C.n_geoms, idx);
+            bind(g);
+            p.pid = (uint32_t)(idx - offs[g]);
+            p.g = g;
+            emit<float, EXT>(p, *G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, false, 0.0f);
+            if constexpr (GRAD) {
+              gr.init(p.bin);
+              gr.Xf = A.X_pp[idx];
+            }
+          }
+          alive = true;
         }
-        G = &geos[g];
-        p.pid = (uint32_t)(idx - offs[g]);
-        p.g = g;
-        emit<float, EXT>(p, *G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, false, 0.0f);
-        if constexpr (GRAD) {
-          gr.init(p.bin);
-          gr.Xf = A.X_pp[idx];
-        }
-        if (CELLS) {
-          T.cP = S.cells_in_smem ? s_cP : A.cellPq + (size_t)g * nc * 4;
-          T.cD = S.cells_in_smem ? s_cD : A.cellDq + (size_t)g * (nc + 1) * 4;
-          T.h = G->Lf[C.cell_axis] / (float)nc;
-          T.inv_h = (float)nc / G->Lf[C.cell_axis];
-        }
-        T.qb = (C.per_bin && !GRAD) ? (S.qbin_in_smem ? s_qbin : A.qbinq + (size_t)g * n) : nullptr;
-        alive = true;
+      }
+      if (!alive) {
+        drained = drained || pool_dry;   // nothing left to hand out
+        continue;
+      }
+      out = step_steady<float, GradT, decltype(T), EXT>(p, *G, M, relax, binf, C, key.x, key.y, T, gr);
+      if (out == STEP_ALIVE && (p.e & 255u) == 0u && globaltimer_ns() > deadline) {
+        atomicOr(A.flags, 1);
+        out = STEP_TRUNCATED;
       }
     }
-    if (!alive) continue;
-    int out = step_steady<float, typename GradPick<GRAD, GradReplay>::type, decltype(T), EXT>(p, *G, M, relax, binf, C, key.x,
-                                                                                  key.y, T, gr);
-    if (out == STEP_ALIVE && (p.e & 255u) == 0u && globaltimer_ns() > deadline) {
-      atomicOr(A.flags, 1);
-      out = STEP_TRUNCATED;
-    }
-    if (GRAD && out != STEP_ALIVE) {
+    if (!alive || out == STEP_ALIVE) continue;
+    if (GRAD) {
       const double X = T.X(p);
       if constexpr (GRAD) {
         if (!gr.mv.phase) {
@@ -371,8 +578,7 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
           atomicAdd(gs + 2, D * D);
         }
       }
-      alive = false;
-    } else if (out != STEP_ALIVE) {
+    } else {
       T.period_end(p);
       const double X = T.X(p);
       const unsigned nev = p.e + 1u;
@@ -391,8 +597,9 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
       if (A.events_pp) A.events_pp[idx] = nev;
       if (A.X_pp) A.X_pp[idx] = X;
       if constexpr (EXT) nscat_end(C, p.g, p.n_relax, X);
-      alive = false;
     }
+    alive = false;
+    drained = pool_dry;
   }
   if (!GRAD) acct.flush(A);
   __syncthreads();
@@ -577,11 +784,13 @@ cudaError_t launch_f64(const GeoRun* geos, const uint64_t* offs, const MatView& 
 #endif  // MCBTE_F64
 
 #if MCBTE_F32
-template <int CELLS, bool GRAD, int TPB, bool EXT>
-cudaError_t launch_f32_tpb(const GeoRun* geos, const uint64_t* offs, const MatView& M, const RunCfg& C,
-                           const Acc& A, int bps, cudaStream_t s) {
-  const SmemPlan S = plan_smem_f32(M.n, C.n_geoms, GRAD ? 0 : C.n_cells, GRAD ? 0 : C.per_bin, 200 * 1024);
-  auto kern = k_steady_f32<CELLS, GRAD, TPB, EXT>;
+// One persistent launch: SMs x resident blocks (or fewer on request).
+template <int CELLS, bool GRAD, int TPB, bool EXT, int MODE>
+cudaError_t launch_f32_kernel(const GeoRun* geos, const uint64_t* offs, const MatView& M, const RunCfg& C,
+                              const Acc& A, int bps, cudaStream_t s) {
+  const SmemPlan S = plan_smem_f32(M.n, C.n_geoms, GRAD ? 0 : C.n_cells, GRAD ? 0 : C.per_bin, 200 * 1024,
+                                   MODE == 2 ? TPB : 0);
+  auto kern = k_steady_f32<CELLS, GRAD, TPB, EXT, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.bytes);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -591,6 +800,22 @@ cudaError_t launch_f32_tpb(const GeoRun* geos, const uint64_t* offs, const MatVi
   const int b = (bps > 0 && bps < occ) ? bps : occ;
   kern<<<sm_count() * b, TPB, S.bytes, s>>>(geos, offs, M, C, A, S);
   return cudaGetLastError();
+}
+
+// Part 0: the main kernel alone.  Part 1: the main kernel that parks its
+// tail, then the tail kernel over the parked particles (256-thread blocks).
+constexpr int kTailThreads = 256;
+
+template <int CELLS, bool GRAD, int TPB, bool EXT>
+cudaError_t launch_f32_tpb(const GeoRun* geos, const uint64_t* offs, const MatView& M, const RunCfg& C,
+                           const Acc& A, int bps, cudaStream_t s) {
+#if MCBTE_F32_PART == 0
+  return launch_f32_kernel<CELLS, GRAD, TPB, EXT, 0>(geos, offs, M, C, A, bps, s);
+#else
+  cudaError_t e = launch_f32_kernel<CELLS, GRAD, TPB, EXT, 1>(geos, offs, M, C, A, bps, s);
+  if (e != cudaSuccess) return e;
+  return launch_f32_kernel<CELLS, GRAD, kTailThreads, EXT, 2>(geos, offs, M, C, A, 0, s);
+#endif
 }
 
 template <int CELLS, bool GRAD, bool EXT>
@@ -612,16 +837,26 @@ cudaError_t launch_f32(const GeoRun* geos, const uint64_t* offs, const MatView& 
   return C.ext ? launch_f32_ext<CELLS, GRAD, true>(geos, offs, M, C, A, threads, bps, s)
                : launch_f32_ext<CELLS, GRAD, false>(geos, offs, M, C, A, threads, bps, s);
 }
+
+cudaError_t launch_f32_variants(bool grad, bool cells, const GeoRun* geos, const uint64_t* offs, const MatView& M,
+                                const RunCfg& C, const Acc& A, int threads, int bps, cudaStream_t s) {
+  // the gradient pass keeps no cell or per-bin tallies
+  if (grad) return launch_f32<0, true>(geos, offs, M, C, A, threads, bps, s);
+  if (!cells) return launch_f32<0, false>(geos, offs, M, C, A, threads, bps, s);
+  return C.cell_flux_axis ? launch_f32<2, false>(geos, offs, M, C, A, threads, bps, s)
+                          : launch_f32<1, false>(geos, offs, M, C, A, threads, bps, s);
+}
 #endif  // MCBTE_F32
 
 }  // namespace
 
 #if MCBTE_F64
-SmemPlan plan_smem_f32(int n_bins, int n_geoms, int n_cells, int per_bin, size_t budget) {
+SmemPlan plan_smem_f32(int n_bins, int n_geoms, int n_cells, int per_bin, size_t budget, int tail_threads) {
   // By use per event: the relaxation alias records and the per-bin
   // constants (every relaxation), the cell tallies (every flight), the
-  // per-bin flux (every relaxation period); each is placed while room remains.
-  SmemPlan S{0, 0, 0, 0, 0};
+  // per-bin flux (every relaxation period); each is placed while room
+  // remains, then the tail's draw slots (one Draw32 per thread).
+  SmemPlan S{0, 0, 0, 0, 0, 0};
   size_t used = 0;
   if (used + (size_t)n_bins * 16 <= budget) {
     S.relax_in_smem = 1;
@@ -640,19 +875,30 @@ SmemPlan plan_smem_f32(int n_bins, int n_geoms, int n_cells, int per_bin, size_t
     S.qbin_in_smem = 1;
     used += (size_t)n_bins * 8;
   }
+  if (tail_threads > 0 && n_bins <= kOneBlockBins && used + (size_t)tail_threads * sizeof(Draw32) <= budget) {
+    S.tail_slots = 1;
+    used += (size_t)tail_threads * sizeof(Draw32);
+  }
   S.bytes = used;
   return S;
 }
 
+// SM count of the current device, cached per device ordinal (grids are sized
+// for the device the launch goes to).
 int sm_count() {
-  static int cached = 0;
-  if (cached == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
-    if (cached < 1) cached = 1;
+  constexpr int kDevices = 64;
+  static std::atomic<int> cached[kDevices];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < kDevices) {
+    const int c = cached[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
   }
-  return cached;
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+  if (v < 1) v = 1;
+  if (dev >= 0 && dev < kDevices) cached[dev].store(v, std::memory_order_relaxed);
+  return v;
 }
 
 cudaError_t launch_steady(int precision, bool grad, const GeoRun* geos, const uint64_t* offs, const MatView& M,
@@ -678,14 +924,23 @@ cudaError_t launch_dirs_dot_pi(const double* dirs, int n_dirs, const MatView& M,
 }
 #endif  // MCBTE_F64
 
-#if MCBTE_F32
+#if MCBTE_F32 && MCBTE_F32_PART == 1
+cudaError_t launch_steady_f32_tail(bool grad, bool cells, const GeoRun* geos, const uint64_t* offs, const MatView& M,
+                                   const RunCfg& C, const Acc& A, int threads, int bps, cudaStream_t s) {
+  return launch_f32_variants(grad, cells, geos, offs, M, C, A, threads, bps, s);
+}
+#endif
+
+#if MCBTE_F32 && MCBTE_F32_PART == 0
+size_t park_record_bytes() { return (sizeof(ParkRec) + 15) & ~(size_t)15; }
+
+// Runs that can park their tail (a park buffer and a threshold) take the
+// kernels of part 1, the others the plain main kernel.
 cudaError_t launch_steady_f32(bool grad, bool cells, const GeoRun* geos, const uint64_t* offs, const MatView& M,
                               const RunCfg& C, const Acc& A, int threads, int bps, cudaStream_t s) {
-  // the gradient pass keeps no cell or per-bin tallies
-  if (grad) return launch_f32<0, true>(geos, offs, M, C, A, threads, bps, s);
-  if (!cells) return launch_f32<0, false>(geos, offs, M, C, A, threads, bps, s);
-  return C.cell_flux_axis ? launch_f32<2, false>(geos, offs, M, C, A, threads, bps, s)
-                          : launch_f32<1, false>(geos, offs, M, C, A, threads, bps, s);
+  if (A.park_cap > 0 && C.tail_max > 0)
+    return launch_steady_f32_tail(grad, cells, geos, offs, M, C, A, threads, bps, s);
+  return launch_f32_variants(grad, cells, geos, offs, M, C, A, threads, bps, s);
 }
 #endif  // MCBTE_F32
 

@@ -83,8 +83,8 @@ def test_si_slab_full_size_sampled_particles():
     ranges = _ranges(run.n, 24, 16, 11)
     ev, X = _oracle_sample(mat, geo, run, run.n, ranges)
     assert np.array_equal(_take(o.events_pp.cpu().numpy().astype(np.uint32), ranges), ev)
-    ok, err = rel_close(_take(o.X_pp.cpu().numpy(), ranges), X, RTOL)
-    assert ok, err
+    # X_p bit for bit: one thread's sum of the same IEEE operations on both sides
+    assert np.array_equal(_take(o.X_pp.cpu().numpy(), ranges).view(np.int64), X.view(np.int64))
 
 
 def test_transient_box_full_size_counts_and_windows():
@@ -134,8 +134,7 @@ def test_film_batch_full_size_sampled_particles_and_fp32_batch():
         ev, X = _oracle_sample(mat, wl.geometries[f], run, ns[f], rr, batch_index=f)
         glob = [(a + off[f], b + off[f]) for a, b in rr]
         assert np.array_equal(_take(ev_all, glob), ev), f
-        ok, err = rel_close(_take(X_all, glob), X, RTOL)
-        assert ok, (f, err)
+        assert np.array_equal(_take(X_all, glob).view(np.int64), X.view(np.int64)), f
     # FP32: the bench's batched launch (CUDA graph, device-resident key)
     gb = batch.GraphBatch(M, Gs, ns, api.SteadyConfig(seed=run.seed, precision=L.FP32_TRACE, **base), tune=True)
     o = gb.replay(seed=run.seed)

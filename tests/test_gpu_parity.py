@@ -1,9 +1,10 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-FP64 plain mode: per-particle event counts identical, per-particle X_p and
-every tally within 1e-9 of the oracle relative to the tally's largest
-magnitude (the two sides run the same IEEE operations; atomics reorder
-sums and libm's log / sin / cos may differ by an ulp).  FP32 mode: every
+FP64 plain mode: per-particle event counts identical; per-particle X_p bit
+for bit (each is one thread's sum of the same IEEE operations in the same
+order on both sides); every tally within 1e-9 of the oracle relative to the
+tally's largest magnitude (tallies are sums of atomics whose order differs
+run to run, and a signed sum can cancel below its terms).  FP32 mode: every
 compared tally within 3 combined standard errors of the oracle on
 independent seeds, kappa within 0.5 %.
 """
@@ -33,8 +34,10 @@ def _check_fp64(g, ref, mask_events=True, tallies=("T", "q")):
     ev_ok = np.array_equal(g["events_pp"], ref["events_pp"])
     n_bad = int(np.sum(g["events_pp"] != ref["events_pp"]))
     assert ev_ok, f"{n_bad} particles with different event counts"
-    ok, err = rel_close(g["X_pp"], ref["X_pp"], RTOL)
-    assert ok, f"X_p rel err {err}"
+    a = np.ascontiguousarray(g["X_pp"], dtype=np.float64)
+    b = np.ascontiguousarray(ref["X_pp"], dtype=np.float64)
+    n_diff = int(np.sum(a.view(np.int64) != b.view(np.int64)))
+    assert n_diff == 0, f"{n_diff} particles whose X_p differs from the oracle's in some bit"
     for k in tallies:
         if k in ref and k in g:
             ok, err = rel_close(g[k].reshape(ref[k].shape), ref[k], RTOL)
@@ -411,6 +414,9 @@ def test_host_output_path_matches_device_path():
 
 # ------------------------------------------------------------------ FP32 statistical parity
 def test_fp32_gray_slab_tallies_within_3se():
+    """Cell tallies at the workload's size (1e5 particles per run); kappa on
+    larger runs so that 3 combined standard errors are below 0.5 % and both
+    bounds of the FP32 contract bind."""
     wl = W.gray_slab_c1()
     mat, g, run = wl.material, wl.geometries[0], wl.run
     M = api.Material(mat)
@@ -429,10 +435,18 @@ def test_fp32_gray_slab_tallies_within_3se():
         z = z_scores(m1, s1, m2, s2)
         assert np.max(np.abs(z)) < 4.0
         assert np.mean(z ** 2) < 2.0
+    gk, ok_ = [], []
+    for s in range(8):
+        gk.append(gpu_steady(mat, [g], [2_000_000], run, L.FP32_TRACE, seed=150 + s, M=M)["stats"][0][L.STAT_KAPPA])
+    big = W.SteadyRun(n=500_000, seed=0, n_cells=0, cell_axis=2, tally_axis=2)
+    for s in range(8):
+        big.seed = 250 + s
+        ok_.append(oracle.run_steady(mat, g, big)["kappa"])
     m1, s1 = batch_stats(gk)
     m2, s2 = batch_stats(ok_)
-    assert abs(m1 - m2) < 3 * np.hypot(s1, s2)
-    assert abs(m1 - m2) < 0.005 * m2 + 3 * np.hypot(s1, s2)
+    se = np.hypot(s1, s2)
+    assert 3 * se < 0.005 * m2
+    assert abs(m1 - m2) < 3 * se and abs(m1 - m2) < 0.005 * m2, (m1, m2, se)
 
 
 def test_fp32_bvk_slab_kappa_and_spectrum():

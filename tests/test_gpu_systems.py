@@ -11,6 +11,7 @@
 """
 import math
 import ctypes
+from dataclasses import replace
 
 import numpy as np
 import pytest
@@ -50,6 +51,66 @@ def test_fp32_results_independent_of_launch_shape():
             continue
         for k in cur:
             assert np.array_equal(cur[k], base[k]), (threads, refill, k)
+
+
+def _exact_outputs(o):
+    return [o.events_pp.cpu().numpy(), o.X_pp.cpu().numpy().view(np.int64), o.q_bin.cpu().numpy()]
+
+
+def test_tail_draws_change_no_result():
+    """The run's tail (warps with few particles left draw the next events of
+    all of them at once) traces with the draws the inline path computes, so
+    per-particle event counts, X_p and the fixed-point tallies are bit for bit
+    those of runs without it, for every threshold and launch shape; with the
+    two-phonon clock and internal walls (sub-block 256 draws) as well."""
+    wl = W.film_batch_c4(scale=0.01)
+    M = api.Material(wl.material)
+    Gs = [api.Geometry(g) for g in wl.geometries]
+    base = None
+    for tail in (-1, 0, 3, 16, 32):
+        for threads, refill in ((256, 1), (1024, 4)):
+            cfg = api.SteadyConfig(seed=41, precision=L.FP32_TRACE, tally_axis=1, per_bin=True, n_scat_max=10,
+                                   max_events=10 ** 8, threads_per_block=threads, refill_threshold=refill,
+                                   tail_lanes=tail)
+            o = _run(M, Gs, wl.n_per_geom, cfg, per_particle=True)
+            assert np.all(o.stats[:, L.STAT_STATUS].cpu().numpy() == 0)
+            cur = _exact_outputs(o)
+            if base is None:
+                base = cur
+                continue
+            for a, b in zip(cur, base):
+                assert np.array_equal(a, b), (tail, threads)
+    m = W.bvk_holland()
+    m = replace(m, tau_imp=1.0 / (2e-44 * m.omega ** 4))
+    M2, G2 = api.Material(m), api.Geometry(W.nanomesh())
+    outs = []
+    for tail in (-1, 8):
+        cfg = api.SteadyConfig(seed=43, precision=L.FP32_TRACE, tally_axis=1, per_bin=True, n_scat_max=10,
+                               max_events=10 ** 8, threads_per_block=512, tail_lanes=tail)
+        outs.append(_exact_outputs(_run(M2, [G2], [200_000], cfg, per_particle=True)))
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+def test_tail_draws_change_no_gradient():
+    """The gradient's replay pass with the measure-valued d/dp_pore (its
+    reservoir words come from the tail's draws too) gives the same gradient
+    with and without the tail draws."""
+    wl = W.pore_film_c5(n=300_000)
+    M, G = api.Material(wl.material), api.Geometry(wl.geometries[0])
+    res = []
+    for tail in (-1, 0):
+        cfg = api.SteadyConfig(seed=44, precision=L.FP32_TRACE, tally_axis=1, per_bin=True, n_scat_max=10,
+                               max_events=10 ** 8, threads_per_block=768, refill_threshold=4, tail_lanes=tail)
+        fwd, go = api.grad(M, G, wl.run.n, cfg)
+        torch.cuda.synchronize()
+        assert fwd.stats[0, L.STAT_STATUS].item() == 0
+        res.append((fwd.q_bin.cpu().numpy(), go.dkappa_dlogtau.cpu().numpy(), go.dkappa_dp.cpu().numpy()))
+    (q0, d0, p0), (q1, d1, p1) = res
+    assert np.array_equal(q0, q1)
+    # the resampling and specularity sums are FP64 atomics (order-dependent rounding)
+    np.testing.assert_allclose(d1, d0, rtol=1e-12, atol=1e-12 * np.abs(d0).max())
+    np.testing.assert_allclose(p1, p0, rtol=1e-9)
 
 
 def test_graph_batch_replays_and_matches_direct_run():
