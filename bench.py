@@ -63,14 +63,47 @@ WORKLOADS = {"si_slab": "si_slab_L1um_3000bins", "si_slab_imp": "si_slab_L1um_30
              "nanomesh": "nanomesh_W34nm_pore11nm_t22nm_timp",
              "film_batch": "film_batch_64_10nm_10um", "pore_grad": "pore_film_W100nm_phi0.25_t200nm_grad",
              "pore_nscat": "pore_skew_W100nm_phi0.25_t200nm_nscat_curve_1_32"}
-# Algorithmic thread-instructions per event of the tracer (one Philox4x32-10
-# call, log + sqrt + sincos, six-plane first hit, alias draw, state update and
-# tallies); the issue-rate roofline is SMs x 4 x 32 lanes x f_clk / this.
+# Issue-rate roofline of the FP32 steady tracer: SMs x 4 schedulers x 32
+# lanes x f_clk thread-instructions per second, against the instructions one
+# event costs, taken from ncu's instruction counters of the bench's own launch
+# (smsp__thread_inst_executed.sum and smsp__inst_executed.sum over the tracing
+# kernels of one step, divided by the step's events; the capture and its
+# command are summarised in profiles/k_steady_f32_si_slab.md).  Workloads
+# without such a capture fall back to the count of the work one event needs
+# (one Philox4x32-10 call, log + sqrt + sincos, six-plane first hit, alias
+# draw, state update and tallies: 200 thread-instructions).
 INSTR_PER_EVENT = 200.0
+NCU_INSTR_PER_EVENT = {   # workload: (thread-instructions, warp-instructions) per event
+    "si_slab": (388.2, 19.59),    # 2.570e11 / 1.297e10 instructions over 6.619e8 events
+}
 # DRAM bytes per launch of the FP32 steady tracing kernel on the default
 # workload, from the ncu capture summarised in profiles/ (None until a capture
 # of the current kernel exists).
 TRACE_DRAM_BYTES_PER_LAUNCH = 1_175_808 + 315_392
+
+
+PROBE_SRC = os.path.join(ROOT, "bench_l2_probe.cu")
+PROBE_LIB = os.path.join(ROOT, "bench_l2_probe.so")
+
+
+def build_probe(force: bool = False) -> str:
+    """Compile the bench's L2 reduction probe (bench_l2_probe.cu, not part of
+    the library) for sm_103a beside this file."""
+    if not force and os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(PROBE_SRC):
+        return PROBE_LIB
+    nvcc = "nvcc" if subprocess.run(["which", "nvcc"], capture_output=True).returncode == 0 else "/usr/local/cuda/bin/nvcc"
+    subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-shared",
+                           "-Xcompiler", "-fPIC", PROBE_SRC, "-o", PROBE_LIB + ".tmp"])
+    os.replace(PROBE_LIB + ".tmp", PROBE_LIB)
+    return PROBE_LIB
+
+
+def load_probe():
+    build_probe()
+    lib = ctypes.CDLL(PROBE_LIB)
+    lib.bench_l2_reduction_probe.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p]
+    lib.bench_l2_reduction_probe.restype = ctypes.c_int
+    return lib
 
 
 def _dist():
@@ -168,6 +201,13 @@ class Timer:
         return step_ms, kern_ms, results
 
 
+def _tail_kernel(cfg) -> int:
+    """1 when the FP32 run hands its last particles to the tail kernel (a
+    second launch), else 0."""
+    from paper_2104_03573_gb300 import _lib as L
+    return int(cfg.precision == L.FP32_TRACE and cfg.tail_lanes >= 0)
+
+
 def _workload_setup(name, args, seed_offset):
     """Build (material, geometries, step factory, description, counters)."""
     from paper_2104_03573_gb300 import api, _lib as L, batch, autotune
@@ -182,7 +222,7 @@ def _workload_setup(name, args, seed_offset):
         M, G = api.Material(mat), api.Geometry(geo)
         cfg = api.SteadyConfig(seed=run.seed + seed_offset, precision=L.FP32_TRACE, n_cells=run.n_cells,
                                cell_axis=2, tally_axis=2, per_bin=True, threads_per_block=args.threads,
-                               blocks_per_sm=args.blocks_per_sm, refill_threshold=args.refill,
+                               blocks_per_sm=args.blocks_per_sm, refill_threshold=args.refill, tail_lanes=args.tail,
                                cell_flux_axis=True)
         if args.threads == 0 and not args.no_autotune:
             # on the whole workload: a smaller sample ranks the shapes by their drain tail
@@ -209,8 +249,9 @@ def _workload_setup(name, args, seed_offset):
         desc = ("steady cross-plane Si-like film L=1um (1um cube, periodic x,y), BvK 3x1000 bins + Holland tau "
                 "at 300 K, walls 300+-0.5 K, 50 cells x {T, q_z} + per-bin q_z; FP32 tracing, fixed-point FP64-exact tallies"
                 + ("; separate two-phonon clock, tau_imp^-1 = 2e-44 omega^4" if name == "si_slab_imp" else ""))
-        launches = 3
-        shape = {"threads_per_block": cfg.threads_per_block, "refill_threshold": cfg.refill_threshold}
+        launches = 3 + _tail_kernel(cfg)       # setup, tracer (+ tail kernel), finaliser
+        shape = {"threads_per_block": cfg.threads_per_block, "refill_threshold": cfg.refill_threshold,
+                 "tail_lanes": cfg.tail_lanes}
         return dict(mat=mat, geo=geo, run=run, n=run.n, step=step, fp64=fp64, e2e=e2e, d2h=d2h, h2d=h2d, desc=desc,
                     launches=launches, timer=tm, kernel="k_steady_f32", shape=shape, kappa=True, kind="steady")
     if name == "nanomesh":
@@ -224,7 +265,7 @@ def _workload_setup(name, args, seed_offset):
         M, G = api.Material(mat), api.Geometry(geo)
         cfg = api.SteadyConfig(seed=run.seed, precision=L.FP32_TRACE, tally_axis=1, per_bin=True, n_scat_max=10,
                                max_events=10 ** 9, threads_per_block=args.threads, refill_threshold=args.refill,
-                               time_budget_s=300)
+                               time_budget_s=300, tail_lanes=args.tail)
         if args.threads == 0 and not args.no_autotune:
             cfg = autotune.tune(M, [G], [n], cfg)
         cfg = replace(cfg, trace_events=ev)
@@ -247,8 +288,9 @@ def _workload_setup(name, args, seed_offset):
                 "separate impurity clock tau_imp^-1 = 2e-44 omega^4, N_scat_max 10")
         return dict(mat=mat, geo=geo, run=run, n=n, step=step, fp64=fp64, e2e=e2e,
                     d2h=8 * (M.n_bins + L.NSTATS), h2d=_material_bytes(mat) + ctypes.sizeof(L.GeometryDesc) + 8,
-                    desc=desc, launches=3, timer=tm, kernel="k_steady_f32 (nanomesh)",
-                    shape={"threads_per_block": cfg.threads_per_block, "refill_threshold": cfg.refill_threshold},
+                    desc=desc, launches=3 + _tail_kernel(cfg), timer=tm, kernel="k_steady_f32 (nanomesh)",
+                    shape={"threads_per_block": cfg.threads_per_block, "refill_threshold": cfg.refill_threshold,
+                           "tail_lanes": cfg.tail_lanes},
                     kappa=True, kind="steady")
     if name == "pore_nscat":
         n = args.n_particles or 10_000_000
@@ -257,7 +299,7 @@ def _workload_setup(name, args, seed_offset):
         M, G = api.Material(mat), api.Geometry(geo)
         cfg = api.SteadyConfig(seed=run.seed, precision=L.FP32_TRACE, tally_axis=1, per_bin=True, n_scat_max=32,
                                max_events=10 ** 9, threads_per_block=args.threads, refill_threshold=args.refill,
-                               time_budget_s=300, nscat_curve=True)
+                               time_budget_s=300, nscat_curve=True, tail_lanes=args.tail)
         if args.threads == 0 and not args.no_autotune:
             cfg = autotune.tune(M, [G], [n], cfg)
         cfg = replace(cfg, trace_events=ev)
@@ -280,8 +322,9 @@ def _workload_setup(name, args, seed_offset):
                 "BvK 3x1000 bins + Holland tau; kappa and its SE for every N_scat_max = 1..32 from one run")
         return dict(mat=mat, geo=geo, run=run, n=n, step=step, fp64=fp64, e2e=e2e, curve=out,
                     d2h=8 * (M.n_bins + L.NSTATS + 64), h2d=_material_bytes(mat) + ctypes.sizeof(L.GeometryDesc) + 8,
-                    desc=desc, launches=3, timer=tm, kernel="k_steady_f32 (N_scat_max curve)",
-                    shape={"threads_per_block": cfg.threads_per_block, "refill_threshold": cfg.refill_threshold},
+                    desc=desc, launches=3 + _tail_kernel(cfg), timer=tm, kernel="k_steady_f32 (N_scat_max curve)",
+                    shape={"threads_per_block": cfg.threads_per_block, "refill_threshold": cfg.refill_threshold,
+                           "tail_lanes": cfg.tail_lanes},
                     kappa=True, kind="steady")
     if name == "pore_grad":
         wl = W.pore_film_c5(n=args.n_particles or 50_000_000)
@@ -289,7 +332,8 @@ def _workload_setup(name, args, seed_offset):
         M, G = api.Material(mat), api.Geometry(geo)
         cfg = api.SteadyConfig(seed=run.seed + seed_offset, precision=L.FP32_TRACE, tally_axis=1, per_bin=True,
                                n_scat_max=10, max_events=10 ** 9, threads_per_block=args.threads or 768,
-                               refill_threshold=args.refill or 4, trace_events=ev, time_budget_s=300)
+                               refill_threshold=args.refill or 4, trace_events=ev, time_budget_s=300,
+                               tail_lanes=args.tail)
         fwd = api.SteadyOutputs(1, M.n_bins, 0, True)
         go = api.GradOutputs(M.n_bins)
 
@@ -321,8 +365,10 @@ def _workload_setup(name, args, seed_offset):
                 "pore is traced once more with one pore hit specular)")
         return dict(mat=mat, geo=geo, run=run, n=run.n, step=step, fp64=fp64, e2e=e2e, gout=go, check=nscat_check,
                     d2h=8 * (M.n_bins * 2 + 2 + L.NSTATS), h2d=_material_bytes(mat) + ctypes.sizeof(L.GeometryDesc) + 8,
-                    desc=desc, launches=3, timer=tm, kernel="k_steady_f32 (grad)",
-                    shape={"threads_per_block": cfg.threads_per_block, "refill_threshold": cfg.refill_threshold},
+                    # setup, forward (+ tail), replay (+ tail), finaliser
+                    desc=desc, launches=2 + 2 * (1 + _tail_kernel(cfg)), timer=tm, kernel="k_steady_f32 (grad)",
+                    shape={"threads_per_block": cfg.threads_per_block, "refill_threshold": cfg.refill_threshold,
+                           "tail_lanes": cfg.tail_lanes},
                     kappa=True, kind="grad")
     if name == "film_batch":
         scale = (args.n_particles / 1.4e8) if args.n_particles else 1.0
@@ -332,7 +378,8 @@ def _workload_setup(name, args, seed_offset):
         Gs = [api.Geometry(g) for g in wl.geometries]
         cfg = api.SteadyConfig(seed=run.seed + seed_offset, precision=L.FP32_TRACE, tally_axis=1, per_bin=True,
                                n_scat_max=10, max_events=10 ** 9, threads_per_block=args.threads,
-                               refill_threshold=args.refill, trace_events=ev, time_budget_s=300)
+                               refill_threshold=args.refill, trace_events=ev, time_budget_s=300,
+                               tail_lanes=args.tail)
         gb = batch.GraphBatch(M, Gs, wl.n_per_geom, cfg, tune=(args.threads == 0 and not args.no_autotune))
 
         def step():
@@ -362,9 +409,11 @@ def _workload_setup(name, args, seed_offset):
                 "N_f = 1e5*100^u_f, N_scat_max 10; one persistent launch replayed as a CUDA graph")
         return dict(mat=mat, geo=None, run=run, n=int(sum(wl.n_per_geom)), step=step, fp64=fp64, e2e=e2e,
                     d2h=8 * 64 * (M.n_bins + L.NSTATS),
-                    h2d=_material_bytes(mat) + 64 * (ctypes.sizeof(L.GeometryDesc) + 8), desc=desc, launches=3,
+                    h2d=_material_bytes(mat) + 64 * (ctypes.sizeof(L.GeometryDesc) + 8), desc=desc,
+                    launches=3 + _tail_kernel(gb.cfg),
                     timer=tm, kernel="k_steady_f32 (64 geometries, graph)",
-                    shape={"threads_per_block": gb.cfg.threads_per_block, "refill_threshold": gb.cfg.refill_threshold},
+                    shape={"threads_per_block": gb.cfg.threads_per_block, "refill_threshold": gb.cfg.refill_threshold,
+                           "tail_lanes": gb.cfg.tail_lanes},
                     kappa=True, kind="batch")
     if name in ("transient_box", "transient_box_avg"):
         wl = W.transient_box_c3(n=args.n_particles or 100_000_000)
@@ -521,7 +570,10 @@ def run_ours(args):
     f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     peak_tinst = n_sm * 4 * 32 * f_max / 1e12
     t_kern = sum(kern_ms) / len(kern_ms) / 1e3
-    achieved = ev_step * INSTR_PER_EVENT / t_kern / 1e12
+    roof = _roofline(args.workload, ev_step, t_kern, n_sm, f_max, peak_kind)
+    roof.update({"traffic": TRACE_DRAM_BYTES_PER_LAUNCH if args.workload == "si_slab" else None,
+                 "kernel": wk["kernel"], "kernel_ms": t_kern * 1e3})
+    subs = _sub_records(args, lrank) if (ws == 1 and args.workload == "si_slab" and args.sub_steps > 0) else None
     cpu = cpu_baseline(wk, args) if (ws == 1 and not args.no_cpu) else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -541,12 +593,8 @@ def run_ours(args):
                                 "what": "snapshot tallies (4 atomics each) per second"}}
            if "tally_ops" in wk else {}),
         "fp64_plain": fp64,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
-                     "frac": achieved / peak_tinst,
-                     "traffic": TRACE_DRAM_BYTES_PER_LAUNCH if args.workload == "si_slab" else None,
-                     "kernel": wk["kernel"], "kernel_ms": t_kern * 1e3,
-                     "peak_basis": f"{n_sm} SMs x 4 x 32 lanes x {f_max / 1e6:.0f} MHz ({peak_kind} sm_max_mhz); "
-                                   f"{INSTR_PER_EVENT:.0f} algorithmic thread-instructions per event"},
+        "roofline": roof,
+        **({"workloads": subs} if subs else {}),
         "e2e": {"value": ev_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(wk["h2d"]),
                 "d2h_bytes_per_step": int(wk["d2h"]), "s_per_step": t_e2e},
         "gpu_launches": wk["launches"] * args.steps,
@@ -558,28 +606,99 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _roofline(workload, ev_step, t_kern, n_sm, f_max, peak_kind):
+    """Issue-rate roofline of the tracing kernels of one step: achieved
+    thread-instructions per second (events x instructions per event / kernel
+    time) against SMs x 4 x 32 x f_max; issue_frac is the same with warp
+    instructions against SMs x 4 x f_max, simt_eff the mean active lanes per
+    warp instruction over 32."""
+    peak = n_sm * 4 * 32 * f_max / 1e12
+    if workload in NCU_INSTR_PER_EVENT:
+        ti, wi = NCU_INSTR_PER_EVENT[workload]
+        achieved = ev_step * ti / t_kern / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s", "frac": achieved / peak,
+                "issue_frac": ev_step * wi / t_kern / (n_sm * 4 * f_max), "simt_eff": ti / (32.0 * wi),
+                "thread_inst_per_event": ti, "warp_inst_per_event": wi,
+                "frac_200_algorithmic": ev_step * INSTR_PER_EVENT / t_kern / 1e12 / peak,
+                "peak_basis": f"{n_sm} SMs x 4 x 32 lanes x {f_max / 1e6:.0f} MHz ({peak_kind} sm_max_mhz); "
+                              f"{ti:.1f} thread- / {wi:.2f} warp-instructions per event from ncu instruction "
+                              f"counters of this launch"}
+    achieved = ev_step * INSTR_PER_EVENT / t_kern / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s", "frac": achieved / peak,
+            "peak_basis": f"{n_sm} SMs x 4 x 32 lanes x {f_max / 1e6:.0f} MHz ({peak_kind} sm_max_mhz); "
+                          f"{INSTR_PER_EVENT:.0f} thread-instructions per event (work count; no ncu count of "
+                          f"this workload)"}
+
+
+def _sub_records(args, dev):
+    """The default run's extra lines: the film batch under a CUDA graph, the
+    transient box and the pore-film gradient, each W = 3 warm-up and
+    args.sub_steps timed steps (L2 flushed between steps, CUDA events, clocks
+    sampled), in the same units as the main line."""
+    import numpy as np
+    import torch
+    from paper_2104_03573_gb300 import _lib as L
+    out = {}
+    for name in ("film_batch", "transient_box", "pore_grad"):
+        sa = argparse.Namespace(**vars(args))
+        sa.n_particles, sa.threads, sa.blocks_per_sm, sa.refill, sa.workload = 0, 0, 0, 0, name
+        wk = _workload_setup(name, sa, 0)
+        tm = wk["timer"]
+        for _ in range(3):
+            wk["step"]()()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(dev)
+        sampler.start()
+        step_ms, kern_ms, stats = tm.run(wk["step"], args.sub_steps)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        for st in stats:
+            assert np.all(st[:, L.STAT_STATUS] == 0), f"{name}: run status {st[:, L.STAT_STATUS]}"
+        t_step = sum(step_ms) / len(step_ms) / 1e3
+        t_kern = sum(kern_ms) / len(kern_ms) / 1e3
+        ev = float(np.mean([st[:, L.STAT_EVENTS].sum() for st in stats]))
+        rec = {"workload": WORKLOADS[name], "description": wk["desc"], "value": ev / t_step, "unit": UNIT,
+               "ms_per_step": t_step * 1e3, "kernel_ms": t_kern * 1e3, "steps": args.sub_steps, "warmup": 3,
+               "events_per_step": ev, "n_particles": wk["n"], "launch": wk["shape"],
+               "ms_per_step_each": [round(x, 3) for x in step_ms], "clocks": clocks}
+        st = stats[-1]
+        if wk["kappa"]:
+            k, se = st[:, L.STAT_KAPPA], st[:, L.STAT_KAPPA_SE]
+            rec["s_to_1pct_se_kappa"] = float(t_step * np.max((se / np.abs(k) / 0.01) ** 2))
+            rec["kappa_eff"] = float(k[0]) if k.size == 1 else [round(float(x), 4) for x in k]
+        if "gout" in wk:
+            rec["dkappa_dp_pore"] = [float(x) for x in wk["gout"].dkappa_dp.cpu().numpy()]
+        if "tally_ops" in wk:
+            rec["l2_reductions"] = l2_reduction_roofline(wk, t_kern)
+            rec["tally_ops_per_s"] = wk["tally_ops"] / t_step
+        out[name] = rec
+        del wk
+        torch.cuda.empty_cache()
+    return out
+
+
 def t_kern_probe(kern_ms):
     return sum(kern_ms) / len(kern_ms) / 1e3
 
 
 def l2_reduction_roofline(wk, t_kern):
     """Snapshot-bound transient runs: the 64-bit L2 reductions the tracing
-    kernels issue per second (4 per snapshot) against the rate the library's
-    probe reaches in the same pattern on an array the size of one time
+    kernels issue per second (4 per snapshot) against the rate the bench's
+    probe (bench_l2_probe.cu) reaches in the same pattern on an array the size of one time
     window's tally slice (best of 3 timed launches)."""
     import torch
     from paper_2104_03573_gb300 import _lib as L
     words = int(wk["l2_slice_words"]) // 4 * 4
     slots = torch.zeros(words, dtype=torch.int64, device="cuda")
     groups = 1 << 28
-    lib = L.load()
+    lib = load_probe()
     s = torch.cuda.current_stream()
-    L.check(lib.mcbte_l2_reduction_probe(slots.data_ptr(), words, groups // 16, ctypes.c_void_p(s.cuda_stream)))
+    assert lib.bench_l2_reduction_probe(slots.data_ptr(), words, groups // 16, ctypes.c_void_p(s.cuda_stream)) == 0
     best = None
     for _ in range(3):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
-        L.check(lib.mcbte_l2_reduction_probe(slots.data_ptr(), words, groups, ctypes.c_void_p(s.cuda_stream)))
+        assert lib.bench_l2_reduction_probe(slots.data_ptr(), words, groups, ctypes.c_void_p(s.cuda_stream)) == 0
         e1.record(s)
         e1.synchronize()
         t = e0.elapsed_time(e1) / 1e3
@@ -587,7 +706,7 @@ def l2_reduction_roofline(wk, t_kern):
     peak = 4.0 * groups / best / 1e9
     achieved = 4.0 * wk["tally_ops"] / t_kern / 1e9
     return {"achieved": achieved, "peak": peak, "unit": "G reductions/s", "frac": achieved / peak,
-            "peak_basis": f"mcbte_l2_reduction_probe: 2^28 groups of 4 64-bit reductions into a "
+            "peak_basis": f"bench_l2_probe.cu: 2^28 groups of 4 64-bit reductions into a "
                           f"{words * 8 / 2**20:.0f} MiB array (one time window's tally slice), best of 3"}
 
 
@@ -682,6 +801,10 @@ def main():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--refill", type=int, default=0)
+    ap.add_argument("--tail", type=int, default=0,
+                    help="tail_lanes of the FP32 steady runs: 0 default / autotuned, -1 no tail kernel")
+    ap.add_argument("--sub-steps", type=int, default=3,
+                    help="timed steps of each extra workload line of the default run (0: none)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-fp64", action="store_true")

@@ -281,6 +281,10 @@ mcbte_status mcbte_run_steady(const mcbte_material* m, const mcbte_geometry* con
  *     cells) return MCBTE_ERR_WORKSPACE with the size needed.
  *   - The first call on a device looks up the array's device address (with
  *     that device current); make that first call before any stream capture.
+ *     With CUDA's lazy module loading that first call, or the first one that
+ *     launches a given kernel variant, may load the library's device code,
+ *     which itself takes device memory: make one call of each kind of run at
+ *     start-up, after which calls allocate nothing.
  *   - Every call shares the one array, which keeps the last call's contents
  *     (each call clears what must start at zero): calls whose GPU work
  *     overlaps, on any streams or host threads, race and corrupt each
@@ -380,16 +384,6 @@ typedef struct {
 mcbte_status mcbte_grad(const mcbte_material* m, const mcbte_geometry* g, const mcbte_steady_params* p,
                         const mcbte_steady_out* fwd, const mcbte_grad_out* grad,
                         void* workspace, size_t workspace_bytes, mcbte_stream stream);
-
-/* Measurement utility (no counterpart in the paper; the method does not use
- * it): n_groups groups of four 64-bit integer reductions (+1 each), each group
- * into one 32-byte record of `slots` (DEVICE, n_slots 64-bit words, a
- * positive multiple of 4) picked by a hash of the group index -- the access
- * pattern of the FP32 transient snapshots.  Timed by the caller on `stream`,
- * it gives the GPU's L2 reduction rate, the ceiling of snapshot-bound
- * transient runs.  Asynchronous; afterwards the slots hold 4 n_groups in
- * total on top of what they held. */
-mcbte_status mcbte_l2_reduction_probe(long long* slots, uint64_t n_slots, uint64_t n_groups, mcbte_stream stream);
 
 #ifdef __cplusplus
 }

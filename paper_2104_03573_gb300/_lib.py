@@ -22,7 +22,7 @@ EXPORTS = [
     "mcbte_last_error", "mcbte_version", "mcbte_material_create", "mcbte_material_destroy",
     "mcbte_material_n_bins", "mcbte_material_tables", "mcbte_geometry_create", "mcbte_geometry_destroy",
     "mcbte_steady_workspace_size", "mcbte_run_steady", "mcbte_transient_workspace_size",
-    "mcbte_run_transient", "mcbte_grad", "mcbte_run_steady_noalloc", "mcbte_l2_reduction_probe",
+    "mcbte_run_transient", "mcbte_grad", "mcbte_run_steady_noalloc",
 ]
 
 
@@ -110,10 +110,9 @@ def load(path: str = LIB_PATH):
     L.mcbte_grad.argtypes = [vp, vp, C.POINTER(SteadyParams), C.POINTER(SteadyOut), C.POINTER(GradOut), vp,
                              C.c_size_t, vp]
     L.mcbte_run_steady_noalloc.argtypes = [vp, vp, C.c_int, C.POINTER(SteadyParams), C.POINTER(SteadyOut), vp]
-    L.mcbte_l2_reduction_probe.argtypes = [vp, C.c_uint64, C.c_uint64, vp]
     for name in ("mcbte_material_create", "mcbte_material_tables", "mcbte_geometry_create",
                  "mcbte_steady_workspace_size", "mcbte_run_steady", "mcbte_transient_workspace_size",
-                 "mcbte_run_transient", "mcbte_grad", "mcbte_run_steady_noalloc", "mcbte_l2_reduction_probe"):
+                 "mcbte_run_transient", "mcbte_grad", "mcbte_run_steady_noalloc"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

@@ -50,6 +50,10 @@ class Material:
         L.check(lib.mcbte_material_create(C.byref(d), C.byref(h)))
         self.handle = h
         self.n_bins = d.n_bins
+        # what decides the tracer's kernel variant and load balance (the
+        # autotuner's cache key): size, optional columns, the tables' content
+        self.features = (d.n_bins, d.tau_imp is not None, d.spec_bin is not None,
+                         hash(b"".join(a.tobytes() for a in self._keep)))
         self._keep = None
 
     def tables(self) -> Dict[str, np.ndarray]:
@@ -101,6 +105,7 @@ class Geometry:
         h = C.c_void_p()
         L.check(L.load().mcbte_geometry_create(C.byref(d), C.byref(h)))
         self.handle = h
+        self.features = hash(bytes(d))   # the whole descriptor (autotuner cache key)
 
     def __del__(self):
         h = getattr(self, "handle", None)

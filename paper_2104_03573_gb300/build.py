@@ -31,7 +31,6 @@ UNITS = [
     ("tracer_steady.cu", ["-DMCBTE_F32=1", "-DMCBTE_F32_PART=1"], True),
     ("tracer_transient.cu", ["-DMCBTE_F64=1"], False),
     ("tracer_transient.cu", ["-DMCBTE_F32=1"], True),
-    ("probe_l2.cu", [], True),
 ]
 
 

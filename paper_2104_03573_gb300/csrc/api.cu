@@ -61,6 +61,34 @@ struct Carve {
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
+// Small host data (detector regions, measurement times) reaches the device
+// as kernel parameters, 4000 bytes per launch: the parameters are copied
+// when the launch is issued, so the host buffer may go away at once, and a
+// stream capture records the bytes themselves (a copy from host memory would
+// record the host address, read again at every replay).
+constexpr unsigned kParamChunk = 4000;
+struct ParamChunk {
+  unsigned char b[kParamChunk];
+};
+
+__global__ void k_param_copy(unsigned char* dst, ParamChunk c, unsigned n) {
+  for (unsigned i = threadIdx.x; i < n; i += blockDim.x) dst[i] = c.b[i];
+}
+
+cudaError_t param_upload(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  const unsigned char* from = static_cast<const unsigned char*>(src);
+  unsigned char* to = static_cast<unsigned char*>(dst);
+  for (size_t off = 0; off < bytes; off += kParamChunk) {
+    const unsigned n = (unsigned)std::min<size_t>(kParamChunk, bytes - off);
+    ParamChunk c;
+    std::memcpy(c.b, from + off, n);
+    k_param_copy<<<1, 256, 0, s>>>(to + off, c, n);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace
 
 struct mcbte_material {
@@ -662,7 +690,7 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   if (p->n_regions > 0) {
     const std::vector<DetRegion> rg =
         build_regions(p->n_regions, p->regions, p->region_grid, false, nullptr, geoms[0]->host.L);
-    RUN_TRY(cudaMemcpyAsync(w.regs, rg.data(), rg.size() * sizeof(DetRegion), cudaMemcpyHostToDevice, s));
+    RUN_TRY(param_upload(w.regs, rg.data(), rg.size() * sizeof(DetRegion), s));
   }
   Acc A{};
   A.cellP = w.cellP;
@@ -787,15 +815,6 @@ mcbte_status mcbte_run_steady(const mcbte_material* m, const mcbte_geometry* con
                               const mcbte_steady_params* p, const mcbte_steady_out* out, void* workspace,
                               size_t workspace_bytes, mcbte_stream stream) {
   return steady_impl(m, geoms, n_geoms, p, out, nullptr, workspace, workspace_bytes, (cudaStream_t)stream);
-}
-
-mcbte_status mcbte_l2_reduction_probe(long long* slots, uint64_t n_slots, uint64_t n_groups, mcbte_stream stream) {
-  if (!slots || n_slots < 4 || (n_slots & 3u) != 0)
-    return fail(MCBTE_ERR_INVALID_ARG, "l2_reduction_probe: n_slots must be a positive multiple of 4");
-  if (n_groups == 0) return MCBTE_OK;
-  CUDA_TRY(launch_l2_reduction_probe(reinterpret_cast<unsigned long long*>(slots), n_slots / 4, n_groups,
-                                     (cudaStream_t)stream));
-  return MCBTE_OK;
 }
 
 mcbte_status mcbte_grad(const mcbte_material* m, const mcbte_geometry* g, const mcbte_steady_params* p,
@@ -968,7 +987,7 @@ mcbte_status mcbte_run_transient(const mcbte_material* m, const mcbte_geometry* 
   RUN_TRY(cudaMemsetAsync(snap, 0, snap_len * sizeof(double), s));
   std::vector<double> tm(p->n_times);
   for (int k = 0; k < p->n_times; ++k) tm[k] = p->t_meas[k] * 1e12;
-  RUN_TRY(cudaMemcpyAsync(w.t_meas_ps, tm.data(), tm.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  RUN_TRY(param_upload(w.t_meas_ps, tm.data(), tm.size() * sizeof(double), s));
   SetupArgs a;
   std::memset(&a, 0, sizeof(a));
   a.desc[0] = g->dev;
@@ -998,7 +1017,7 @@ mcbte_status mcbte_run_transient(const mcbte_material* m, const mcbte_geometry* 
   if (C.n_regs > 0) {
     const std::vector<DetRegion> rg =
         build_regions(C.n_regs, p->regions, p->region_grid, whole_region, p->grid, g->host.L);
-    RUN_TRY(cudaMemcpyAsync(w.regs, rg.data(), rg.size() * sizeof(DetRegion), cudaMemcpyHostToDevice, s));
+    RUN_TRY(param_upload(w.regs, rg.data(), rg.size() * sizeof(DetRegion), s));
   }
   Acc A{};
   A.dsc = w.dsc;

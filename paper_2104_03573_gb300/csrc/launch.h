@@ -90,8 +90,5 @@ cudaError_t launch_material_build(const MatBuild& b, cudaStream_t s);
 int sm_count();
 // bytes of one parked particle of the FP32 steady tracer's tail (both passes)
 size_t park_record_bytes();
-// n_groups groups of four 64-bit reductions into records of `slots` (the
-// measurement utility mcbte_l2_reduction_probe)
-cudaError_t launch_l2_reduction_probe(unsigned long long* slots, uint64_t n_rec, uint64_t n_groups, cudaStream_t s);
 
 }  // namespace mcbte

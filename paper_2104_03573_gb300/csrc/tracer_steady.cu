@@ -315,6 +315,57 @@ __device__ __forceinline__ void park_load(const ParkRec* r, Particle<float>& p, 
   }
 }
 
+// The tail kernel's events of one live particle from its precomputed draws:
+// slot0 holds the draws of event p.e + 1, and the slots end with event
+// e_last.  A flight that ends on a periodic face draws nothing, so it is
+// handled here without the event dispatch (the same operations as
+// apply_event's periodic branch: ++e, the clocks run down, the particle moves
+// to the opposite face); any other event goes through apply_event with its
+// slot.  Returns at the particle's end, or ALIVE once the slots are used up.
+template <class Grad, class Tally, bool EXT>
+__device__ __forceinline__ int trace_slots(Particle<float>& p, const GeoRun& g, const MatView& M, const uint4* relax_tab,
+                                           const float4* binf, const RunCfg& C, uint32_t k0, uint32_t k1,
+                                           const Tally& T, Grad& gr, const Draw32* slot0, uint32_t e_last,
+                                           uint64_t deadline, int* flags) {
+  const uint32_t e0 = p.e;
+  for (;;) {
+    if (p.e + 1u >= C.max_events) return STEP_TRUNCATED;
+    float db;
+    int face;
+    first_hit<float, EXT>(g, p.x, p.u, &db, &face);
+    const bool relax = EXT ? (p.d_rel < db && p.d_rel <= p.d2) : p.d_rel < db;
+    const bool relax2 = EXT && !relax && p.d2 < db;
+    const float seg = relax ? p.d_rel : (relax2 ? p.d2 : db);
+    double Xb = 0.0;
+    if (Grad::on) Xb = T.X(p);
+    const auto c = T.segment(p, seg);
+    if constexpr (EXT) {
+      if (C.n_regs > 0 && T.has_det()) region_steady<float>(p, seg, C, T);
+    }
+    if (Grad::on) gr.flight(relax, (double)(seg / p.lam), Xb, c);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
+    int out = STEP_ALIVE;
+    if (!relax && !relax2 && face < 6 && g.type[face] == MCBTE_FACE_PERIODIC) {
+      ++p.e;
+      p.d_rel = p.d_rel - seg;
+      if constexpr (EXT) p.d2 = p.d2 - seg;
+      const int a = face_axis(face);
+      put3<float>(p.x, a, face_is_max(face) ? 0.0f : geo_L<float>(g, a));
+    } else {
+      out = apply_event<float, Grad, Tally, EXT, DrawSlot>(p, g, M, relax_tab, binf, C, k0, k1, relax, relax2, face,
+                                                           seg, T, gr, Grad::on ? T.X(p) : 0.0,
+                                                           DrawSlot{slot0 + (p.e - e0)});
+      if (out != STEP_ALIVE) return out;
+    }
+    if ((p.e & 255u) == 0u && globaltimer_ns() > deadline) {
+      atomicOr(flags, 1);
+      return STEP_TRUNCATED;
+    }
+    if (p.e >= e_last) return STEP_ALIVE;
+  }
+}
+
 // Every lane owns one particle at a time.  When its particle terminates the
 // lane refills from a global work counter; the refills of a warp are
 // aggregated into one atomicAdd (ballot of the empty lanes, leader adds the
@@ -488,18 +539,10 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
           slots[lane] = d;
         }
         __syncwarp();
-        if (alive) {
-          const Draw32* mine = slots + (__popc(live & ((1u << lane) - 1u)) << sh);
-          for (int j = 0; j < (1 << sh); ++j) {
-            out = step_steady<float, GradT, decltype(T), EXT, DrawSlot>(p, *G, M, relax, binf, C, key.x, key.y, T,
-                                                                         gr, DrawSlot{mine + j});
-            if (out == STEP_ALIVE && (p.e & 255u) == 0u && globaltimer_ns() > deadline) {
-              atomicOr(A.flags, 1);
-              out = STEP_TRUNCATED;
-            }
-            if (out != STEP_ALIVE) break;
-          }
-        }
+        if (alive)
+          out = trace_slots<GradT, decltype(T), EXT>(p, *G, M, relax, binf, C, key.x, key.y, T, gr,
+                                                      slots + (__popc(live & ((1u << lane) - 1u)) << sh),
+                                                      p.e + (1u << sh), deadline, A.flags);
         __syncwarp();   // the slots are rewritten in the next round
       }
     } else {

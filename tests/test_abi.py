@@ -137,8 +137,10 @@ def test_product_package_does_not_import_oracle():
                 assert "oracle" not in src.lower().replace("oracle-free", ""), f
 
 
-def test_l2_probe_rejects_bad_sizes_before_cuda(lib):
-    from paper_2104_03573_gb300 import _lib
-    assert lib.mcbte_l2_reduction_probe(None, 16, 10, None) == _lib.ERR_INVALID_ARG
-    assert lib.mcbte_l2_reduction_probe(C.c_void_p(256), 6, 10, None) == _lib.ERR_INVALID_ARG
-    assert lib.mcbte_l2_reduction_probe(C.c_void_p(256), 0, 10, None) == _lib.ERR_INVALID_ARG
+def test_bench_l2_probe_builds_apart_and_rejects_bad_sizes_before_cuda(lib):
+    import bench
+    probe = bench.load_probe()
+    assert probe.bench_l2_reduction_probe(None, 16, 10, None) == 1
+    assert probe.bench_l2_reduction_probe(C.c_void_p(256), 6, 10, None) == 1
+    assert probe.bench_l2_reduction_probe(C.c_void_p(256), 0, 10, None) == 1
+    assert not hasattr(lib, "mcbte_l2_reduction_probe")      # a measurement of the bench, not a library call

@@ -140,6 +140,27 @@ def test_graph_batch_replays_and_matches_direct_run():
     assert (sa[:, L.STAT_N].cpu().numpy() == np.array(ns)).all()
 
 
+def test_graph_batch_with_detector_regions_matches_direct_run():
+    """Detector regions reach the device as launch parameters, so a captured
+    graph holds their bytes: replays (after the host list is gone) give the
+    direct run's detector tallies bit for bit."""
+    wl = W.si_slab_c2(n=50_000)
+    mat, geo, run = wl.material, wl.geometries[0], wl.run
+    M, G = api.Material(mat), api.Geometry(geo)
+    Lb = geo.L
+    regions = [((0.1 * Lb[0], 0.7 * Lb[0], 0.0, Lb[1], 0.25 * Lb[2], 0.75 * Lb[2]), (2, 2, 4)),
+               ((0.0, Lb[0], 0.0, Lb[1], 0.0, Lb[2]), (1, 1, 8))]
+    cfg = api.SteadyConfig(seed=5, precision=L.FP32_TRACE, tally_axis=2, per_bin=True, regions=regions)
+    gb = batch.GraphBatch(M, [G], [run.n], cfg, tune=False)
+    gb.replay(seed=777)
+    gb.replay(seed=777)
+    torch.cuda.synchronize()
+    det_g, qb_g = gb.out.det.clone(), gb.out.q_bin.clone()
+    d = _run(M, [G], [run.n], replace(cfg, seed=777))
+    assert torch.equal(d.det, det_g) and torch.equal(d.q_bin, qb_g)
+    assert torch.count_nonzero(det_g) > 0
+
+
 def test_autotune_returns_a_valid_shape_with_the_same_physics():
     wl = W.si_slab_c2(n=200_000)
     mat, geo, run = wl.material, wl.geometries[0], wl.run
@@ -147,11 +168,23 @@ def test_autotune_returns_a_valid_shape_with_the_same_physics():
     cfg = api.SteadyConfig(seed=run.seed, precision=L.FP32_TRACE, n_cells=run.n_cells, tally_axis=2, per_bin=True)
     autotune.clear_cache()
     tuned = autotune.tune(M, [G], [run.n], cfg)
-    assert tuned.threads_per_block in (256, 512, 768, 1024)
+    assert tuned.threads_per_block in (256, 512, 768, 1024) and tuned.tail_lanes in (-1, 0)
     a = _run(M, [G], [run.n], cfg)
     b = _run(M, [G], [run.n], tuned)
     assert torch.equal(a.T, b.T) and torch.equal(a.q_bin, b.q_bin)
     assert autotune.tune(M, [G], [run.n], cfg) == tuned       # cached
+    # the cache key holds what picks the kernel and its load: another
+    # geometry, the two-phonon clock or the axis-only cell tallies are new keys
+    key = autotune._key(M, [G], [run.n], cfg)
+    geo2 = W.si_slab_c2(n=10).geometries[0]
+    geo2.L = (2e-6, 2e-6, 1e-6)
+    assert autotune._key(M, [api.Geometry(geo2)], [run.n], cfg) != key
+    M2 = api.Material(replace(mat, tau_imp=1.0 / (2e-44 * mat.omega ** 4)))
+    assert autotune._key(M2, [G], [run.n], cfg) != key
+    assert autotune._key(M, [G], [run.n], replace(cfg, cell_flux_axis=True)) != key
+    assert autotune._key(M, [G], [run.n], replace(cfg, nscat_curve=True)) != key
+    # a tail threshold the caller set is kept
+    assert autotune.tune(M, [G], [run.n], replace(cfg, tail_lanes=4)).tail_lanes == 4
 
 
 def test_films_batched_kappa_vs_fuchs_sondheimer():
@@ -352,10 +385,11 @@ def test_fp32_axis_only_cell_tallies_equal_the_full_ones():
 
 
 def test_l2_reduction_probe_adds_exactly():
+    import bench
     slots = torch.zeros(4096, dtype=torch.int64, device="cuda")
-    lib = L.load()
+    probe = bench.load_probe()
     s = torch.cuda.current_stream()
-    L.check(lib.mcbte_l2_reduction_probe(slots.data_ptr(), 4096, 100_003, ctypes.c_void_p(s.cuda_stream)))
+    assert probe.bench_l2_reduction_probe(slots.data_ptr(), 4096, 100_003, ctypes.c_void_p(s.cuda_stream)) == 0
     torch.cuda.synchronize()
     assert int(slots.sum().item()) == 4 * 100_003
     r = slots.view(-1, 4)

@@ -5,9 +5,11 @@ memory, must give the same results as the regular steady run.
 inside the library instead of a caller workspace or cudaMallocAsync.  It is
 called here twice in a row through the C ABI: the second call reuses the
 array left behind by the first, so it also checks that everything that must
-start at zero is cleared on each call.  The tolerance is the one the other
-parity tests use (1e-9 of the tally's largest magnitude; per-particle
-event counts identical).  This file is collected last on purpose.
+start at zero is cleared on each call, and that the second call leaves the
+device's free memory unchanged (the first may still load device code).  The
+tolerance is the one the other parity tests use (1e-9 of the tally's largest
+magnitude; per-particle event counts and X_p identical).  This file is
+collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -42,12 +44,16 @@ def test_noalloc_matches_regular_steady_run_twice(precision):
                            per_bin=True)
     ref = api.run_steady(M, [G], [run.n], cfg, per_particle=True)
     torch.cuda.synchronize()
-    for _ in range(2):
+    for call in range(2):
         out = api.SteadyOutputs(1, M.n_bins, run.n_cells, True, run.n, per_particle=True)
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         api.run_steady_noalloc(M, [G], [run.n], cfg, out)
         torch.cuda.synchronize()
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] == free_before
         assert torch.equal(out.events_pp, ref.events_pp)
-        assert _close(out.X_pp.cpu().numpy(), ref.X_pp.cpu().numpy())
+        assert torch.equal(out.X_pp, ref.X_pp)
         assert _close(out.T.cpu().numpy(), ref.T.cpu().numpy())
         assert _close(out.q.cpu().numpy(), ref.q.cpu().numpy())
         assert _close(out.q_bin.cpu().numpy(), ref.q_bin.cpu().numpy())
