@@ -102,6 +102,8 @@ def lib():
         L.or_alias.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.or_alias_draw.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32]
         L.or_alias_draw.restype = C.c_int
+        L.or_set_libm.argtypes = [C.c_int]
+        L.or_set_libm.restype = None
         _lib = L
     return _lib
 
@@ -170,6 +172,20 @@ def _params(material, geom, keep: _Keep, **kw) -> _Params:
     for k, val in kw.items():
         setattr(P, k, val)
     return P
+
+
+class libm_mode:
+    """Context manager: inside it the tracer evaluates ln, sin and cos with
+    the C library instead of its fixed series (shows what that choice
+    changes per particle; the default series mode is the reference)."""
+
+    def __enter__(self):
+        lib().or_set_libm(1)
+        return self
+
+    def __exit__(self, *exc):
+        lib().or_set_libm(0)
+        return False
 
 
 def philox(ctr: Sequence[int], key: Sequence[int]) -> np.ndarray:

@@ -147,6 +147,25 @@ void series_sincos2pi(double r, double* sn, double* cs) {
   }
 }
 
+// The tracer's ln and sincos(2 pi r): the series above by default; the C
+// library's std::log, std::sin, std::cos after or_set_libm(1).  The libm mode
+// exists to show what the choice changes (a particle whose trajectory turns
+// on a last-bit difference: a near-tie between two distances); results are
+// compared with the CUDA path in the series mode.
+static int g_use_libm = 0;
+
+double ln_(double x) { return g_use_libm ? std::log(x) : series_log(x); }
+
+void sincos2pi_(double r, double* sn, double* cs) {
+  if (g_use_libm) {
+    const double a = 6.283185307179586 * r;
+    *sn = std::sin(a);
+    *cs = std::cos(a);
+  } else {
+    series_sincos2pi(r, sn, cs);
+  }
+}
+
 // ---------------------------------------------------------------- tables
 struct Alias {
   std::vector<double> prob;
@@ -602,7 +621,7 @@ inline void first_hit(const Geo& g, const double x[3], const double u[3], double
 inline void dir_about_axis(double u[3], int a, double sgn, double mu, uint32_t wphi) {
   double s = std::sqrt(std::max(0.0, 1.0 - mu * mu));
   double sn, cs;
-  series_sincos2pi(co32(wphi), &sn, &cs);
+  sincos2pi_(co32(wphi), &sn, &cs);
   u[a] = sgn * mu;
   u[(a + 1) % 3] = s * cs;
   u[(a + 2) % 3] = s * sn;
@@ -621,7 +640,7 @@ inline void dir_about_vector(double u[3], const double gv[3], double sgn, double
   const double b2[3] = {b, sg + (n[1] * n[1]) * a, -n[1]};
   double s = std::sqrt(std::max(0.0, 1.0 - mu * mu));
   double sn, cs;
-  series_sincos2pi(co32(wphi), &sn, &cs);
+  sincos2pi_(co32(wphi), &sn, &cs);
   for (int k = 0; k < 3; ++k) u[k] = (mu * n[k] + (s * cs) * b1[k]) + (s * sn) * b2[k];
 }
 
@@ -770,11 +789,11 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
       double mu = 1.0 - 2.0 * oc32(w[2]);
       dir_about_axis(u, 2, 1.0, mu, w[3]);
       ctr[3] = 3; philox4x32_10(ctr, k0, k1, w3);
-      double m1 = std::sqrt(-2.0 * series_log(oc32(w3[0])));
-      double m2 = std::sqrt(-2.0 * series_log(oc32(w3[2])));
+      double m1 = std::sqrt(-2.0 * ln_(oc32(w3[0])));
+      double m2 = std::sqrt(-2.0 * ln_(oc32(w3[2])));
       double s1, c1, s2, c2;
-      series_sincos2pi(co32(w3[1]), &s1, &c1);
-      series_sincos2pi(co32(w3[3]), &s2, &c2);
+      sincos2pi_(co32(w3[1]), &s1, &c1);
+      sincos2pi_(co32(w3[3]), &s2, &c2);
       double nrm[3] = {m1 * c1, m1 * s1, m2 * c2};
       for (int a = 0; a < 3; ++a) {
         double c = S.gauss_c[a] + S.gauss_sigma * nrm[a];
@@ -785,7 +804,7 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
         x[a] = c;
       }
     }
-    double d_rel = t.lam_nm[bin] * (-series_log(oc53(w1[1], w1[2])));
+    double d_rel = t.lam_nm[bin] * (-ln_(oc53(w1[1], w1[2])));
     // two-phonon clock (Sec. 3.3): its own exponential distance, drawn from
     // sub-block 256 of the event that (re)starts it
     auto draw_d2 = [&](uint32_t ev) -> double {
@@ -793,7 +812,7 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
       uint32_t c4[4] = {(uint32_t)pid, P->batch_index, ev, 256u};
       uint32_t w4[4];
       philox4x32_10(c4, k0, k1, w4);
-      return t.lam2_nm[bin] * (-series_log(oc53(w4[0], w4[1])));
+      return t.lam2_nm[bin] * (-ln_(oc53(w4[0], w4[1])));
     };
     double d2 = draw_d2(0);
     out.scal[OR_SIGNED_EMIT] += s;
@@ -965,7 +984,7 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
         ctr[3] = 1; philox4x32_10(ctr, k0, k1, w1);
         bin = alias_draw(t.relax, n, w[0], w[1], w1[0]);
         dir_about_axis(u, 2, 1.0, 1.0 - 2.0 * oc32(w[2]), w[3]);
-        d_rel = t.lam_nm[bin] * (-series_log(oc53(w1[1], w1[2])));
+        d_rel = t.lam_nm[bin] * (-ln_(oc53(w1[1], w1[2])));
         d2 = draw_d2(e);
         if (P->want_grad) {
           periods.push_back({bin, -1.0, -X});
@@ -1020,7 +1039,7 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
           double mu = std::sqrt(oc32(w[2]));
           double sn = std::sqrt(std::max(0.0, 1.0 - mu * mu));
           double sphi, cphi;
-          series_sincos2pi(co32(w[3]), &sphi, &cphi);
+          sincos2pi_(co32(w[3]), &sphi, &cphi);
           double sc = sn * cphi;
           u[0] = mu * nx0 - sc * ny0;
           u[1] = mu * ny0 + sc * nx0;
@@ -1065,7 +1084,7 @@ void trace_range(const or_params* P, const Tables& t, const Setup& S, uint64_t p
           double mu = std::sqrt(oc32(w[2]));
           double sn = std::sqrt(std::max(0.0, 1.0 - mu * mu));
           double sphi, cphi;
-          series_sincos2pi(co32(w[3]), &sphi, &cphi);
+          sincos2pi_(co32(w[3]), &sphi, &cphi);
           double sc = sn * cphi;
           u[0] = mu * nx0 - sc * ny0;
           u[1] = mu * ny0 + sc * nx0;
@@ -1141,6 +1160,8 @@ void or_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
 double or_dEdT(double omega, double T) { return dEdT(omega, T); }
 
 double or_log(double x) { return series_log(x); }
+
+void or_set_libm(int on) { g_use_libm = on ? 1 : 0; }
 
 void or_sincos2pi(double r, double* s, double* c) { series_sincos2pi(r, s, c); }
 
