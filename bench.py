@@ -208,7 +208,16 @@ def _tail_kernel(cfg) -> int:
     return int(cfg.precision == L.FP32_TRACE and cfg.tail_lanes >= 0)
 
 
-def _workload_setup(name, args, seed_offset):
+def _split(cfg, n_per_geom, rank, world):
+    """Steady runs on several GPUs: rank r traces particles [r n, (r+1) n) of
+    a run of world x n particles per geometry (weak scaling, per-GPU work
+    fixed; the ranks together trace exactly the particles of that run)."""
+    if world <= 1:
+        return cfg
+    return replace(cfg, pid_begin=[rank * int(n) for n in n_per_geom], n_total=[world * int(n) for n in n_per_geom])
+
+
+def _workload_setup(name, args, seed_offset, rank=0, world=1):
     """Build (material, geometries, step factory, description, counters)."""
     from paper_2104_03573_gb300 import api, _lib as L, batch, autotune
     import torch
@@ -227,7 +236,7 @@ def _workload_setup(name, args, seed_offset):
         if args.threads == 0 and not args.no_autotune:
             # on the whole workload: a smaller sample ranks the shapes by their drain tail
             cfg = autotune.tune(M, [G], [run.n], cfg, fraction=1.0)
-        cfg = replace(cfg, trace_events=ev)
+        cfg = _split(replace(cfg, trace_events=ev), [run.n], rank, world)
         ws = torch.empty(api.steady_workspace_size(M, [G], [run.n], cfg), dtype=torch.uint8, device="cuda")
         out = api.SteadyOutputs(1, M.n_bins, run.n_cells, True)
 
@@ -236,7 +245,7 @@ def _workload_setup(name, args, seed_offset):
             return lambda: out.stats.cpu().numpy()
 
         def fp64(n64):
-            c = replace(cfg, precision=L.FP64_PLAIN, threads_per_block=0, refill_threshold=0)
+            c = replace(cfg, precision=L.FP64_PLAIN, pid_begin=(), n_total=(), threads_per_block=0, refill_threshold=0)
             o = api.SteadyOutputs(1, M.n_bins, run.n_cells, True)
             return lambda: (api.run_steady(M, [G], [n64], c, out=o), (lambda: o.stats.cpu().numpy()))[1]
 
@@ -268,7 +277,7 @@ def _workload_setup(name, args, seed_offset):
                                time_budget_s=300, tail_lanes=args.tail)
         if args.threads == 0 and not args.no_autotune:
             cfg = autotune.tune(M, [G], [n], cfg)
-        cfg = replace(cfg, trace_events=ev)
+        cfg = _split(replace(cfg, trace_events=ev), [n], rank, world)
         out = api.SteadyOutputs(1, M.n_bins, 0, True)
 
         def step():
@@ -276,7 +285,7 @@ def _workload_setup(name, args, seed_offset):
             return lambda: out.stats.cpu().numpy()
 
         def fp64(n64):
-            c = replace(cfg, precision=L.FP64_PLAIN, threads_per_block=0, refill_threshold=0)
+            c = replace(cfg, precision=L.FP64_PLAIN, pid_begin=(), n_total=(), threads_per_block=0, refill_threshold=0)
             o = api.SteadyOutputs(1, M.n_bins, 0, True)
             return lambda: (api.run_steady(M, [G], [n64], c, out=o), (lambda: o.stats.cpu().numpy()))[1]
 
@@ -302,7 +311,7 @@ def _workload_setup(name, args, seed_offset):
                                time_budget_s=300, nscat_curve=True, tail_lanes=args.tail)
         if args.threads == 0 and not args.no_autotune:
             cfg = autotune.tune(M, [G], [n], cfg)
-        cfg = replace(cfg, trace_events=ev)
+        cfg = _split(replace(cfg, trace_events=ev), [n], rank, world)
         out = api.SteadyOutputs(1, M.n_bins, 0, True, nscat=32)
 
         def step():
@@ -310,7 +319,7 @@ def _workload_setup(name, args, seed_offset):
             return lambda: out.stats.cpu().numpy()
 
         def fp64(n64):
-            c = replace(cfg, precision=L.FP64_PLAIN, threads_per_block=0, refill_threshold=0)
+            c = replace(cfg, precision=L.FP64_PLAIN, pid_begin=(), n_total=(), threads_per_block=0, refill_threshold=0)
             o = api.SteadyOutputs(1, M.n_bins, 0, True, nscat=32)
             return lambda: (api.run_steady(M, [G], [n64], c, out=o), (lambda: o.stats.cpu().numpy()))[1]
 
@@ -334,6 +343,7 @@ def _workload_setup(name, args, seed_offset):
                                n_scat_max=10, max_events=10 ** 9, threads_per_block=args.threads or 768,
                                refill_threshold=args.refill or 4, trace_events=ev, time_budget_s=300,
                                tail_lanes=args.tail)
+        cfg = _split(cfg, [run.n], rank, world)
         fwd = api.SteadyOutputs(1, M.n_bins, 0, True)
         go = api.GradOutputs(M.n_bins)
 
@@ -342,7 +352,7 @@ def _workload_setup(name, args, seed_offset):
             return lambda: fwd.stats.cpu().numpy()
 
         def fp64(n64):
-            c = replace(cfg, precision=L.FP64_PLAIN)
+            c = replace(cfg, precision=L.FP64_PLAIN, pid_begin=(), n_total=())
             f2, g2 = api.SteadyOutputs(1, M.n_bins, 0, True), api.GradOutputs(M.n_bins)
             return lambda: (api.grad(M, G, n64, c, fwd=f2, gout=g2), (lambda: f2.stats.cpu().numpy()))[1]
 
@@ -380,6 +390,7 @@ def _workload_setup(name, args, seed_offset):
                                n_scat_max=10, max_events=10 ** 9, threads_per_block=args.threads,
                                refill_threshold=args.refill, trace_events=ev, time_budget_s=300,
                                tail_lanes=args.tail)
+        cfg = _split(cfg, wl.n_per_geom, rank, world)
         gb = batch.GraphBatch(M, Gs, wl.n_per_geom, cfg, tune=(args.threads == 0 and not args.no_autotune))
 
         def step():
@@ -389,7 +400,7 @@ def _workload_setup(name, args, seed_offset):
         def fp64(n64):
             fr = n64 / sum(wl.n_per_geom)
             ns = [max(1, int(x * fr)) for x in wl.n_per_geom]
-            c = replace(cfg, precision=L.FP64_PLAIN, trace_events=ev)
+            c = replace(cfg, precision=L.FP64_PLAIN, pid_begin=(), n_total=(), trace_events=ev)
             o = api.SteadyOutputs(len(Gs), M.n_bins, 0, True)
             return lambda: (api.run_steady(M, Gs, ns, c, out=o), (lambda: o.stats.cpu().numpy()))[1]
 
@@ -481,7 +492,10 @@ def run_ours(args):
     from paper_2104_03573_gb300 import build, _lib as L
     build.build()
     from paper_2104_03573_gb300 import shard
-    wk = _workload_setup(args.workload, args, shard.rank_key(0, rank))
+    # steady workloads: rank r traces its own range of a world x n particle run
+    # under the one key; the transient box (no range split) takes a key per rank
+    wk = _workload_setup(args.workload, args, shard.rank_key(0, rank) if args.workload.startswith("transient") else 0,
+                         rank, ws)
     tm = wk["timer"]
     for _ in range(args.warmup):
         wk["step"]()()
@@ -516,7 +530,7 @@ def run_ours(args):
         se = st[:, L.STAT_KAPPA_SE]
         kappa, kse = float(k[0]), float(se[0])
         if dist:                                        # pooled over the ranks' independent samples
-            pooled = shard.allreduce_steady_stats(st[0])
+            pooled = shard.pooled_kappa(shard.allreduce_stats(st)[0])
             kappa, kse = pooled["kappa"], pooled["kappa_se"]
         t_1pct = float(t_step * np.max((se / np.abs(k) / 0.01) ** 2))
     dkdp = [float(x) for x in wk["gout"].dkappa_dp.cpu().numpy()] if "gout" in wk else None

@@ -232,6 +232,15 @@ typedef struct {
                                   the random words of their next events on all 32 lanes at once
                                   and then traces them (same results, shorter dependent chain
                                   per event); 0 = default (8), -1 = off, at most 32 */
+  const uint64_t* pid_begin;   /* HOST [n_geoms] or NULL (0): this call traces particles
+                                  pid_begin .. pid_begin + n_particles - 1 of each geometry's
+                                  run (their own Philox streams, so a run split over calls or
+                                  GPUs gives the particles of the whole run, Sec. 6)        */
+  const uint64_t* n_total;     /* HOST [n_geoms] or NULL (n_particles): particles of each
+                                  geometry's whole run; E_eff = E_tot / n_total scales this
+                                  call's tallies, so the tallies of calls covering the run
+                                  add up to the run's (kappa and q_mean too; standard errors
+                                  combine through SUMX, SUMX2 and N)                          */
 } mcbte_steady_params;
 
 typedef struct {

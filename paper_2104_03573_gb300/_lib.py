@@ -49,7 +49,8 @@ class SteadyParams(C.Structure):
                 ("trace_event_start", C.c_void_p), ("trace_event_stop", C.c_void_p),
                 ("seed_device", C.c_void_p), ("refill_threshold", C.c_int), ("cell_flux_axis", C.c_int),
                 ("n_regions", C.c_int), ("regions", C.c_void_p), ("region_grid", C.c_void_p),
-                ("nscat_curve", C.c_int), ("det_per_bin", C.c_int), ("tail_lanes", C.c_int)]
+                ("nscat_curve", C.c_int), ("det_per_bin", C.c_int), ("tail_lanes", C.c_int),
+                ("pid_begin", C.c_void_p), ("n_total", C.c_void_p)]
 
 
 class SteadyOut(C.Structure):

@@ -146,6 +146,8 @@ class SteadyConfig:
     nscat_curve: bool = False                # also kappa for every N_scat_max' <= n_scat_max (kappa_nscat)
     det_per_bin: bool = False                # detector outputs per frequency bin (det: [n_det][n_bins][4])
     tail_lanes: int = 0                      # FP32 tail: warps with <= this many particles left draw ahead (0: 8, -1: off)
+    pid_begin: Sequence = ()                 # per geometry: index of this call's first particle in the run
+    n_total: Sequence = ()                   # per geometry: particles of the whole run (E_eff normalisation)
 
 
 def _event_handles(pair):
@@ -178,6 +180,16 @@ def steady_params(cfg: SteadyConfig, n_particles: np.ndarray) -> "L.SteadyParams
     p.nscat_curve = int(bool(cfg.nscat_curve))
     p.det_per_bin = int(bool(cfg.det_per_bin))
     p.tail_lanes = int(cfg.tail_lanes)
+    keep = []
+    if len(cfg.pid_begin):
+        pb = np.ascontiguousarray(cfg.pid_begin, dtype=np.uint64)
+        keep.append(pb)
+        p.pid_begin = pb.ctypes.data
+    if len(cfg.n_total):
+        nt = np.ascontiguousarray(cfg.n_total, dtype=np.uint64)
+        keep.append(nt)
+        p.n_total = nt.ctypes.data
+    p._keep_split = keep                    # host arrays read during the call
     regions = list(cfg.regions or ())
     if regions:
         boxes = np.ascontiguousarray([r[0] for r in regions], dtype=np.float64)

@@ -561,6 +561,10 @@ mcbte_status check_steady(const mcbte_material* m, const mcbte_geometry* const* 
     if (!geoms[g]) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: null geometry");
     const uint64_t ng = p->n_particles[g];
     if (ng < 1 || ng >= (1ull << 32)) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: n_particles in [1, 2^32)");
+    const uint64_t b = p->pid_begin ? p->pid_begin[g] : 0;
+    const uint64_t nt = p->n_total ? p->n_total[g] : ng;
+    if (b + ng > (1ull << 32) || b + ng > nt)
+      return fail(MCBTE_ERR_INVALID_ARG, "run_steady: pid_begin + n_particles must be <= n_total and <= 2^32");
     t += ng;
     const mcbte_geometry_desc& d = geoms[g]->host;
     if (d.gauss) return fail(MCBTE_ERR_INVALID_ARG, "run_steady: an initial condition needs a transient run");
@@ -654,6 +658,8 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   for (int g = 0; g < G; ++g) {
     a.desc[g] = geoms[g]->dev;
     a.n[g] = p->n_particles[g];
+    a.pid0[g] = p->pid_begin ? p->pid_begin[g] : 0;
+    a.n_norm[g] = p->n_total ? p->n_total[g] : p->n_particles[g];
   }
   RUN_TRY(launch_setup(a, G, m->view, 0, 0.0, p->tally_axis, w.geos, w.offs, w.t0, s));
   RunCfg C{};

@@ -9,10 +9,14 @@
 
 namespace mcbte {
 
-// Per-geometry inputs of the setup kernel, passed by value (<= 2 KB).
+// Per-geometry inputs of the setup kernel, passed by value (4 KB): the
+// descriptor, the particles of this call, the index of the first one, and
+// the particles of the whole run that normalise E_eff = E_tot / N.
 struct SetupArgs {
   const mcbte_geometry_desc* desc[kMaxGeoms];
   uint64_t n[kMaxGeoms];
+  uint64_t pid0[kMaxGeoms];
+  uint64_t n_norm[kMaxGeoms];
 };
 
 // Shared-memory plan of the persistent FP32 tracer.

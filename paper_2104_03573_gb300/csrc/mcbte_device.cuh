@@ -69,8 +69,10 @@ struct alignas(128) GeoRun {
   double V_solid;              // m^3
   double V_box;                // m^3
   double kappa_grad;           // K/m that defines kappa along the tally axis
-  uint64_t n;                  // particles of this geometry
+  uint64_t n;                  // particles of this geometry in this call
   uint64_t offset;             // first flattened particle index
+  uint64_t pid0;               // index of this call's first particle within the geometry's run
+  uint64_t n_norm;             // particles of the geometry's whole run (E_eff = E_tot / n_norm)
 };
 static_assert(offsetof(GeoRun, pthr_pore) + sizeof(uint64_t) <= 128, "FP32 per-event fields within one line");
 

@@ -161,6 +161,8 @@ __global__ void k_setup(SetupArgs a, int G, MatView M, int transient, double t_m
   r.kappa_grad = kg;
   r.n = a.n[gi];
   r.offset = 0;
+  r.pid0 = a.pid0[gi];
+  r.n_norm = a.n_norm[gi] ? a.n_norm[gi] : a.n[gi];
   geos[gi] = r;
 }
 

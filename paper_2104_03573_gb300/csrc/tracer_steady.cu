@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) k_steady_fp64(const GeoRun* __restrict__ 
   const GeoRun& G = geos[g];
   const uint64_t deadline = *C.t0 + C.budget_ns;
   Particle<double> p;
-  p.pid = (uint32_t)(idx - offs[g]);
+  p.pid = (uint32_t)(idx - offs[g] + G.pid0);
   p.g = g;
   const uint2 key = run_key(C);
   if (globaltimer_ns() > deadline) {   // over budget before this particle started
@@ -577,7 +577,7 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
             idx = k;
             const int g = find_geom(offs, C.n_geoms, idx);
             bind(g);
-            p.pid = (uint32_t)(idx - offs[g]);
+            p.pid = (uint32_t)(idx - offs[g] + G->pid0);
             p.g = g;
             emit<float, EXT>(p, *G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, false, 0.0f);
             if constexpr (GRAD) {
@@ -671,7 +671,7 @@ __global__ void k_finalize_steady(const GeoRun* geos, MatView M, RunCfg C, Acc A
   const GeoRun& G = geos[g];
   const int nc = C.n_cells;
   const int n = M.n;
-  const double N = (double)G.n;
+  const double N = (double)G.n_norm;
   const double E_eff = G.E_tot / N;
   const double C_tot = M.sums[0];
   if (nc > 0 && threadIdx.x == 0) {
@@ -740,7 +740,7 @@ __global__ void k_finalize_steady(const GeoRun* geos, MatView M, RunCfg C, Acc A
       const double mean = s1 / nt;
       const double var = nt > 1.0 ? (s2 - nt * mean * mean) / (nt - 1.0) : 0.0;
       const double qm = (E_eff / G.V_solid) * s1 * 1e-9;
-      const double qs = (G.E_tot / G.V_solid) * 1e-9 * sqrt(fmax(var, 0.0) / nt);
+      const double qs = (E_eff / G.V_solid) * 1e-9 * sqrt(fmax(var, 0.0) * nt);
       O.kn[((size_t)g * K + (k - 1)) * 2 + 0] = -qm / G.kappa_grad;
       O.kn[((size_t)g * K + (k - 1)) * 2 + 1] = qs / fabs(G.kappa_grad);
     }
@@ -758,7 +758,7 @@ __global__ void k_finalize_steady(const GeoRun* geos, MatView M, RunCfg C, Acc A
     const double mean = sx / nt;
     const double var = nt > 1.0 ? (sx2 - nt * mean * mean) / (nt - 1.0) : 0.0;
     const double q_mean = (E_eff / G.V_solid) * sx * 1e-9;
-    const double q_se = (G.E_tot / G.V_solid) * 1e-9 * sqrt(fmax(var, 0.0) / nt);
+    const double q_se = (E_eff / G.V_solid) * 1e-9 * sqrt(fmax(var, 0.0) * nt);
     double* st = O.stats + (size_t)g * MCBTE_NSTATS;
     st[MCBTE_STAT_KAPPA] = -q_mean / G.kappa_grad;
     st[MCBTE_STAT_KAPPA_SE] = q_se / fabs(G.kappa_grad);

@@ -53,6 +53,39 @@ def test_fp32_results_independent_of_launch_shape():
             assert np.array_equal(cur[k], base[k]), (threads, refill, k)
 
 
+@pytest.mark.parametrize("precision", [L.FP64_PLAIN, L.FP32_TRACE])
+def test_run_split_by_particle_ranges_equals_the_whole_run(precision):
+    """pid_begin / n_total: three calls that cover a run's particle indices
+    trace exactly its particles (per-particle results bit for bit), their
+    tallies add up to the run's, and the pooled statistics (shard.combine_stats)
+    give the run's kappa and standard error."""
+    from paper_2104_03573_gb300 import shard
+    wl = W.si_slab_c2(n=90_001)
+    mat, geo, run = wl.material, wl.geometries[0], wl.run
+    M, G = api.Material(mat), api.Geometry(geo)
+    cfg = api.SteadyConfig(seed=run.seed, precision=precision, n_cells=run.n_cells, cell_axis=2, tally_axis=2,
+                           per_bin=True)
+    full = _run(M, [G], [run.n], cfg, per_particle=True)
+    parts = []
+    for r in range(3):
+        c, ns = shard.rank_config(cfg, [run.n], r, 3)
+        parts.append(_run(M, [G], ns, c, per_particle=True))
+    ev = torch.cat([o.events_pp for o in parts])
+    X = torch.cat([o.X_pp for o in parts])
+    assert torch.equal(ev, full.events_pp) and torch.equal(X, full.X_pp)
+    for k in ("T", "q", "q_bin"):
+        tot = sum(getattr(o, k) for o in parts)
+        ref = getattr(full, k)
+        assert torch.allclose(tot, ref, rtol=1e-12, atol=1e-12 * ref.abs().max().item()), k
+    pooled = shard.combine_stats([o.stats[0].cpu().numpy() for o in parts])
+    st = full.stats[0].cpu().numpy()
+    assert pooled[L.STAT_N] == run.n and pooled[L.STAT_EVENTS] == st[L.STAT_EVENTS]
+    assert pooled[L.STAT_KAPPA] == pytest.approx(st[L.STAT_KAPPA], rel=1e-12)
+    assert pooled[L.STAT_KAPPA_SE] == pytest.approx(st[L.STAT_KAPPA_SE], rel=1e-9)
+    with pytest.raises(L.MCBTEError):
+        _run(M, [G], [10], replace(cfg, pid_begin=[run.n - 5], n_total=[run.n]))
+
+
 def _exact_outputs(o):
     return [o.events_pp.cpu().numpy(), o.X_pp.cpu().numpy().view(np.int64), o.q_bin.cpu().numpy()]
 

@@ -1,6 +1,10 @@
-"""Multi-rank path on CPU: two gloo ranks, each tracing its own independent
-sample (the oracle stands in for the GPU tracer), pool the kappa estimator's
-accumulators and take the maximum of their timings."""
+"""Multi-rank path on CPU: two gloo ranks each trace a contiguous range of
+one run's particles under the run's single key (the oracle stands in for
+the GPU tracer), then the shard module sums the tallies and pools the
+statistics.  The result is the single-process run of all the particles:
+per-particle event counts and X_p bit for bit, tallies and kappa to the
+rounding of a different summation order, standard errors from the pooled
+sums."""
 import json
 import os
 import socket
@@ -25,49 +29,38 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _row(r, n):
-    row = np.zeros(L.NSTATS)
-    row[L.STAT_N] = n
-    row[L.STAT_SUMX] = r["scal"][oracle.SUMX]
-    row[L.STAT_SUMX2] = r["scal"][oracle.SUMX2]
-    row[L.STAT_EVENTS] = r["events"]
-    row[L.STAT_KAPPA] = r["kappa"]
-    return row
+def test_shard_ranges_cover_the_run():
+    for n, world in ((10, 3), (1_000_003, 8), (5, 8)):
+        ranges = [shard.shard_range(n, r, world) for r in range(world)]
+        assert sum(c for _, c in ranges) == n
+        assert all(ranges[r][0] + ranges[r][1] == ranges[r + 1][0] for r in range(world - 1))
 
 
 def test_rank_keys_are_distinct():
-    keys = {shard.rank_key(1001, r) for r in range(64)}
-    assert len(keys) == 64
+    assert len({shard.rank_key(1001, r) for r in range(64)}) == 64
 
 
-def test_two_gloo_ranks_pool_the_estimator(tmp_path):
-    n = 20_000
+def test_two_gloo_ranks_equal_the_single_run(tmp_path):
+    n = 30_001
     port = _free_port()
-    out = tmp_path / "rank0.json"
     env = dict(os.environ, MASTER_ADDR="127.0.0.1", GLOO_SOCKET_IFNAME=os.environ.get("GLOO_SOCKET_IFNAME", "lo"))
-    procs = [subprocess.Popen([sys.executable, os.path.join(HERE, "shard_worker.py"), str(r), "2", str(port), str(out),
-                               str(n)], env=env) for r in range(2)]
-    rcs = [p.wait(timeout=300) for p in procs]
-    assert rcs == [0, 0]
-    got = json.loads(out.read_text())
+    procs = [subprocess.Popen([sys.executable, os.path.join(HERE, "shard_worker.py"), str(r), "2", str(port),
+                               str(tmp_path), str(n)], env=env) for r in range(2)]
+    assert [p.wait(timeout=300) for p in procs] == [0, 0]
+    got = json.loads((tmp_path / "rank0.json").read_text())
+    pooled = np.array(got["stats"])
+    tall = np.load(tmp_path / "tallies.npy")
+    pp = np.concatenate([np.load(tmp_path / f"pp{r}.npy") for r in range(2)], axis=1)
 
-    # the same two samples pooled in one process
-    wl = W.gray_slab_c1(n=n)
-    rows, ks = [], []
-    for r in range(2):
-        run = wl.run
-        run.seed = shard.rank_key(1001, r)
-        res = oracle.run_steady(wl.material, wl.geometries[0], run, n_threads=2)
-        rows.append(_row(res, n))
-        ks.append(res["kappa"])
-    ref = shard.combine_steady_stats(rows)
-    for k in ("n", "events", "kappa", "kappa_se"):
-        assert got["pooled"][k] == pytest.approx(ref[k], rel=1e-12, abs=0), k
-    assert got["pooled"]["n"] == 2 * n
-    assert got["events"] == pytest.approx(rows[0][L.STAT_EVENTS] + rows[1][L.STAT_EVENTS], rel=0, abs=0)
+    wl = W.si_slab_c2(n=n, material=W.bvk_holland(n_per_branch=20))
+    ref = oracle.run_steady(wl.material, wl.geometries[0], wl.run, per_particle=True, n_threads=2)
+    assert np.array_equal(pp[0], ref["events_pp"].astype(np.float64))
+    assert np.array_equal(pp[1].view(np.int64), ref["X_pp"].view(np.int64))
+    want = np.concatenate([ref["T"].ravel(), ref["q"].ravel(), ref["q_bin"].ravel()])
+    np.testing.assert_allclose(tall, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+    assert pooled[L.STAT_N] == n and pooled[L.STAT_EVENTS] == ref["events"]
+    assert pooled[L.STAT_KAPPA] == pytest.approx(ref["kappa"], rel=1e-12)
+    assert pooled[L.STAT_Q_MEAN] == pytest.approx(ref["q_mean"], rel=1e-12)
+    assert pooled[L.STAT_KAPPA_SE] == pytest.approx(ref["kappa_se"], rel=1e-9)
+    assert pooled[L.STAT_SIGNED_ABSORBED] == pooled[L.STAT_SIGNED_EMITTED]
     assert got["t_max"] == 2.0
-    # the pooled estimate is the particle-weighted mean of the ranks' estimates,
-    # with a standard error about 1/sqrt(2) of one rank's
-    assert ref["kappa"] == pytest.approx(0.5 * (ks[0] + ks[1]), rel=1e-12)
-    se1 = [shard.combine_steady_stats([r])["kappa_se"] for r in rows]
-    assert ref["kappa_se"] == pytest.approx(np.mean(se1) / np.sqrt(2), rel=0.05)
