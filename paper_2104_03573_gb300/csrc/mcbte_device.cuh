@@ -302,18 +302,27 @@ __device__ __forceinline__ void first_hit(const GeoRun& g, const R x[3], const R
   int bf = 7;
   if constexpr (sizeof(R) == 4) {
     // FP32: the three face distances without branches (the quotients are
-    // independent, so their latencies overlap); the same candidates and ties
+    // independent, so their latencies overlap), then their minimum and the
+    // lowest paper face ID among the axes that reach it: the same result as
+    // scanning the axes with "nearer, or as near with a lower ID", with a
+    // short dependent chain (a lone particle's event waits on it)
+    R c[3];
+    int fa[3];
+    bool ok[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const R ua = u[a];
       const bool up = ua > R(0);
       const R d0 = Num<R>::div((up ? geo_L<R>(g, a) : R(0)) - x[a], ua);
-      const R d = d0 < R(0) ? R(0) : d0;
-      const int f = up ? axis_max_face(a) : axis_min_face(a);
-      const bool take = ua != R(0) && (d < best || (d == best && f < bf));
-      best = take ? d : best;
-      bf = take ? f : bf;
+      ok[a] = ua != R(0);
+      c[a] = ok[a] ? (d0 < R(0) ? R(0) : d0) : Num<R>::big();
+      fa[a] = up ? axis_max_face(a) : axis_min_face(a);
     }
+    best = fminf(fminf(c[0], c[1]), c[2]);
+    const int f0 = (ok[0] && c[0] == best) ? fa[0] : 7;
+    const int f1 = (ok[1] && c[1] == best) ? fa[1] : 7;
+    const int f2 = (ok[2] && c[2] == best) ? fa[2] : 7;
+    bf = min(min(f0, f1), f2);
   } else {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
