@@ -294,6 +294,75 @@ __device__ __forceinline__ void dir_about_frame(R u[3], const R* f, R mu, uint32
   u[2] = (mu * f[2] + sc * f[5]) + ss * f[8];
 }
 
+// FP32 box faces and pore cylinder of a geometry record (GeoRun, or the
+// register copy GeoLean with the same member names): the three face
+// distances without branches (the quotients are independent, so their
+// latencies overlap), then their minimum and the lowest paper face ID among
+// the axes that reach it (the same result as scanning the axes with "nearer,
+// or as near with a lower ID", with a short dependent chain: a lone
+// particle's event waits on it); then the pore by the same test and root
+// with selects instead of branches.  One function for both records, so both
+// compute the same bits.
+template <class Geo>
+__device__ __forceinline__ void hit_box_pore_f32(const Geo& g, const float x[3], const float u[3], float* dist,
+                                                 int* face) {
+  float c[3];
+  int fa[3];
+  bool ok[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float ua = u[a];
+    const bool up = ua > 0.0f;
+    const float d0 = Num<float>::div((up ? g.Lf[a] : 0.0f) - x[a], ua);
+    ok[a] = ua != 0.0f;
+    c[a] = ok[a] ? (d0 < 0.0f ? 0.0f : d0) : Num<float>::big();
+    fa[a] = up ? axis_max_face(a) : axis_min_face(a);
+  }
+  float best = fminf(fminf(c[0], c[1]), c[2]);
+  const int f0 = (ok[0] && c[0] == best) ? fa[0] : 7;
+  const int f1 = (ok[1] && c[1] == best) ? fa[1] : 7;
+  const int f2 = (ok[2] && c[2] == best) ? fa[2] : 7;
+  int bf = min(min(f0, f1), f2);
+  if (g.pore) {
+    const float dx = x[0] - g.cxf, dy = x[1] - g.cyf;
+    const float a = u[0] * u[0] + u[1] * u[1];
+    const float b = dx * u[0] + dy * u[1];
+    const float cc = (dx * dx + dy * dy) - g.r2f;
+    const float disc = b * b - a * cc;
+    const bool hit = a > 0.0f && b < 0.0f && disc >= 0.0f;
+    const float d0 = Num<float>::div(cc, Num<float>::sqrt_(Num<float>::fmax_(disc, 0.0f)) - b);
+    const float d = d0 < 0.0f ? 0.0f : d0;
+    const bool take = hit && d < best;
+    best = take ? d : best;
+    bf = take ? 6 : bf;
+  }
+  *dist = best;
+  *face = bf;
+}
+
+// The FP32 event step's geometry in registers (the tail kernel's particles):
+// the box, the pore, the face types packed two bits per face.
+struct GeoLean {
+  float Lf[3];
+  float cxf, cyf, r2f;
+  int pore;
+  unsigned tmask;   // bits 2f..2f+1: MCBTE_FACE_* type of face f
+
+  __device__ __forceinline__ void load(const GeoRun& g) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Lf[a] = g.Lf[a];
+    cxf = g.cxf;
+    cyf = g.cyf;
+    r2f = g.r2f;
+    pore = g.pore;
+    tmask = 0u;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) tmask |= ((unsigned)g.type[f] & 3u) << (2 * f);
+  }
+  __device__ __forceinline__ int type(int f) const { return (int)((tmask >> (2 * f)) & 3u); }
+  __device__ __forceinline__ float L(int a) const { return a == 0 ? Lf[0] : (a == 1 ? Lf[1] : Lf[2]); }
+};
+
 // First boundary along the ray (faces in the direction of travel, then the
 // pore cylinder); ties go to the lowest paper boundary ID.
 template <typename R, bool EXT = true>
@@ -301,28 +370,7 @@ __device__ __forceinline__ void first_hit(const GeoRun& g, const R x[3], const R
   R best = Num<R>::big();
   int bf = 7;
   if constexpr (sizeof(R) == 4) {
-    // FP32: the three face distances without branches (the quotients are
-    // independent, so their latencies overlap), then their minimum and the
-    // lowest paper face ID among the axes that reach it: the same result as
-    // scanning the axes with "nearer, or as near with a lower ID", with a
-    // short dependent chain (a lone particle's event waits on it)
-    R c[3];
-    int fa[3];
-    bool ok[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const R ua = u[a];
-      const bool up = ua > R(0);
-      const R d0 = Num<R>::div((up ? geo_L<R>(g, a) : R(0)) - x[a], ua);
-      ok[a] = ua != R(0);
-      c[a] = ok[a] ? (d0 < R(0) ? R(0) : d0) : Num<R>::big();
-      fa[a] = up ? axis_max_face(a) : axis_min_face(a);
-    }
-    best = fminf(fminf(c[0], c[1]), c[2]);
-    const int f0 = (ok[0] && c[0] == best) ? fa[0] : 7;
-    const int f1 = (ok[1] && c[1] == best) ? fa[1] : 7;
-    const int f2 = (ok[2] && c[2] == best) ? fa[2] : 7;
-    bf = min(min(f0, f1), f2);
+    hit_box_pore_f32(g, x, u, &best, &bf);
   } else {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -335,31 +383,21 @@ __device__ __forceinline__ void first_hit(const GeoRun& g, const R x[3], const R
       if (d < R(0)) d = R(0);
       if (d < best || (d == best && f < bf)) { best = d; bf = f; }
     }
-  }
-  if (g.pore) {
-    const R cx = sizeof(R) == 8 ? (R)g.cx : (R)g.cxf;
-    const R cy = sizeof(R) == 8 ? (R)g.cy : (R)g.cyf;
-    const R r2 = sizeof(R) == 8 ? (R)g.r2 : (R)g.r2f;
-    const R dx = x[0] - cx, dy = x[1] - cy;
-    const R a = u[0] * u[0] + u[1] * u[1];
-    const R b = dx * u[0] + dy * u[1];
-    if constexpr (sizeof(R) == 4) {
-      // FP32: the same test and root with selects instead of branches
-      const R c = (dx * dx + dy * dy) - r2;
-      const R disc = b * b - a * c;
-      const bool hit = a > R(0) && b < R(0) && disc >= R(0);
-      const R d0 = Num<R>::div(c, Num<R>::sqrt_(Num<R>::fmax_(disc, R(0))) - b);
-      const R d = d0 < R(0) ? R(0) : d0;
-      const bool take = hit && d < best;
-      best = take ? d : best;
-      bf = take ? 6 : bf;
-    } else if (a > R(0) && b < R(0)) {
-      const R c = (dx * dx + dy * dy) - r2;
-      const R disc = b * b - a * c;
-      if (disc >= R(0)) {
-        R d = c / (Num<R>::sqrt_(disc) - b);
-        if (d < R(0)) d = R(0);
-        if (d < best) { best = d; bf = 6; }
+    if (g.pore) {
+      const R cx = (R)g.cx;
+      const R cy = (R)g.cy;
+      const R r2 = (R)g.r2;
+      const R dx = x[0] - cx, dy = x[1] - cy;
+      const R a = u[0] * u[0] + u[1] * u[1];
+      const R b = dx * u[0] + dy * u[1];
+      if (a > R(0) && b < R(0)) {
+        const R c = (dx * dx + dy * dy) - r2;
+        const R disc = b * b - a * c;
+        if (disc >= R(0)) {
+          R d = c / (Num<R>::sqrt_(disc) - b);
+          if (d < R(0)) d = R(0);
+          if (d < best) { best = d; bf = 6; }
+        }
       }
     }
   }

@@ -320,19 +320,27 @@ __device__ __forceinline__ void park_load(const ParkRec* r, Particle<float>& p, 
 // e_last.  A flight that ends on a periodic face draws nothing, so it is
 // handled here without the event dispatch (the same operations as
 // apply_event's periodic branch: ++e, the clocks run down, the particle moves
-// to the opposite face); any other event goes through apply_event with its
-// slot.  Returns at the particle's end, or ALIVE once the slots are used up.
+// to the opposite face).  Without the extended physics the box and the pore
+// are read once into registers (GeoLean: the per-event geometry then costs no
+// load on the particle's dependent chain) and a flight that ends on a box
+// face takes apply_event's FP32 face branch here, from the register copy;
+// relaxations, pore hits and, with the extended physics, every non-periodic
+// event go through apply_event with their slot.  Returns at the particle's
+// end, or ALIVE once the slots are used up.
 template <class Grad, class Tally, bool EXT>
 __device__ __forceinline__ int trace_slots(Particle<float>& p, const GeoRun& g, const MatView& M, const uint4* relax_tab,
                                            const float4* binf, const RunCfg& C, uint32_t k0, uint32_t k1,
                                            const Tally& T, Grad& gr, const Draw32* slot0, uint32_t e_last,
                                            uint64_t deadline, int* flags) {
   const uint32_t e0 = p.e;
+  GeoLean gl;
+  if constexpr (!EXT) gl.load(g);
   for (;;) {
     if (p.e + 1u >= C.max_events) return STEP_TRUNCATED;
     float db;
     int face;
-    first_hit<float, EXT>(g, p.x, p.u, &db, &face);
+    if constexpr (EXT) first_hit<float, EXT>(g, p.x, p.u, &db, &face);
+    else hit_box_pore_f32(gl, p.x, p.u, &db, &face);
     const bool relax = EXT ? (p.d_rel < db && p.d_rel <= p.d2) : p.d_rel < db;
     const bool relax2 = EXT && !relax && p.d2 < db;
     const float seg = relax ? p.d_rel : (relax2 ? p.d2 : db);
@@ -345,13 +353,31 @@ __device__ __forceinline__ int trace_slots(Particle<float>& p, const GeoRun& g, 
     if (Grad::on) gr.flight(relax, (double)(seg / p.lam), Xb, c);
 #pragma unroll
     for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
+    const bool box = !relax && !relax2 && face < 6;
+    const int ty = box ? (EXT ? g.type[face] : gl.type(face)) : -1;
     int out = STEP_ALIVE;
-    if (!relax && !relax2 && face < 6 && g.type[face] == MCBTE_FACE_PERIODIC) {
+    if (ty == MCBTE_FACE_PERIODIC) {
       ++p.e;
       p.d_rel = p.d_rel - seg;
       if constexpr (EXT) p.d2 = p.d2 - seg;
       const int a = face_axis(face);
-      put3<float>(p.x, a, face_is_max(face) ? 0.0f : geo_L<float>(g, a));
+      put3<float>(p.x, a, face_is_max(face) ? 0.0f : (EXT ? geo_L<float>(g, a) : gl.L(a)));
+    } else if (!EXT && box) {
+      // apply_event's FP32 face branch (isothermal: absorbed; adiabatic:
+      // specular or Lambertian by the slot's draws, then a select)
+      ++p.e;
+      p.d_rel = p.d_rel - seg;
+      const int a = face_axis(face);
+      const int mx = face_is_max(face);
+      put3<float>(p.x, a, mx ? gl.L(a) : 0.0f);
+      if (ty == MCBTE_FACE_ISOTHERMAL) return STEP_ABSORBED;
+      const Draw32& d = slot0[p.e - 1u - e0];
+      const bool spec_f = (uint64_t)d.wx < g.pthr[face];
+      float ud[3];
+      put3_cyclic<float>(ud, a, mx ? -d.lam[0] : d.lam[0], d.lam[1], d.lam[2]);
+      const float flip = -sel3(p.u, a);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) p.u[b] = spec_f ? (b == a ? flip : p.u[b]) : ud[b];
     } else {
       out = apply_event<float, Grad, Tally, EXT, DrawSlot>(p, g, M, relax_tab, binf, C, k0, k1, relax, relax2, face,
                                                            seg, T, gr, Grad::on ? T.X(p) : 0.0,
