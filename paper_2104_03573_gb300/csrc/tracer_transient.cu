@@ -528,7 +528,11 @@ cudaError_t launch_transient(int precision, const GeoRun* geos, const MatView& M
     k_transient_fp64<<<(unsigned)blocks, 256, 0, s>>>(geos, M, C, A);
     return cudaGetLastError();
   }
-  return launch_transient_f32(geos, M, C, A, threads > 0 ? threads : 1024, bps, s);
+  // default block: 512 threads for whole-grid snapshots (no register
+  // spills; they are bound by their tally reductions, not by warps in
+  // flight), 1024 for time-bin averages and detector regions
+  const int dflt = (!C.time_average && C.n_regs == 0) ? 512 : 1024;
+  return launch_transient_f32(geos, M, C, A, threads > 0 ? threads : dflt, bps, s);
 }
 
 #endif  // MCBTE_F64
