@@ -340,7 +340,7 @@ def _workload_setup(name, args, seed_offset, rank=0, world=1):
         mat, geo, run = wl.material, wl.geometries[0], wl.run
         M, G = api.Material(mat), api.Geometry(geo)
         cfg = api.SteadyConfig(seed=run.seed + seed_offset, precision=L.FP32_TRACE, tally_axis=1, per_bin=True,
-                               n_scat_max=10, max_events=10 ** 9, threads_per_block=args.threads or 768,
+                               n_scat_max=10, max_events=10 ** 9, threads_per_block=args.threads or 512,
                                refill_threshold=args.refill or 4, trace_events=ev, time_budget_s=300,
                                tail_lanes=args.tail)
         cfg = _split(cfg, [run.n], rank, world)

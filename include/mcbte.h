@@ -385,12 +385,15 @@ typedef struct {
  * It stays valid at p_pore = 0 and 1, where the likelihood-ratio score does
  * not; the second traces add to the run time, not to the tallies.
  * FP64_PLAIN keeps each particle's relaxation periods and requires
- * 1 <= n_scat_max <= 64.  FP32_TRACE runs two passes: the forward run, which
- * records every particle's final tally, then a pass that replays the same
- * particles (same random words) and adds each period's term as it closes;
- * it requires n_scat_max >= 1, needs 8 more workspace bytes per particle,
- * and returns MCBTE_ERR_REPLAY in the status statistic should a replayed
- * tally differ from the recorded one. */
+ * 1 <= n_scat_max <= 64.  FP32_TRACE requires n_scat_max >= 1.  With
+ * n_scat_max <= 16, no cells (n_cells = 0) and no detector regions it runs
+ * one pass: the forward tallies and the gradient together, each particle
+ * listing its relaxation periods' score sums until its final tally is known.
+ * Otherwise it runs two passes: the forward run, which records every
+ * particle's final tally, then a pass that replays the same particles (same
+ * random words) and adds each period's term as it closes; that needs 8 more
+ * workspace bytes per particle, and returns MCBTE_ERR_REPLAY in the status
+ * statistic should a replayed tally differ from the recorded one. */
 mcbte_status mcbte_grad(const mcbte_material* m, const mcbte_geometry* g, const mcbte_steady_params* p,
                         const mcbte_steady_out* fwd, const mcbte_grad_out* grad,
                         void* workspace, size_t workspace_bytes, mcbte_stream stream);

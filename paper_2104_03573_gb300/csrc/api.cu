@@ -587,6 +587,15 @@ mcbte_status check_steady(const mcbte_material* m, const mcbte_geometry* const* 
   return MCBTE_OK;
 }
 
+// An FP32 gradient run is one pass (forward tallies and gradient together,
+// GradReplay's fused mode) when every particle's relaxation periods fit its
+// list and the run keeps no cell or detector tallies; otherwise a forward
+// pass stores every particle's final tally and a second pass replays it.
+bool grad_fused(const mcbte_steady_params* p) {
+  return p->precision == MCBTE_FP32_TRACE && p->n_scat_max >= 1 && p->n_scat_max <= kFusedPeriods &&
+         p->n_cells == 0 && p->n_regions == 0 && !p->nscat_curve;
+}
+
 mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* geoms, int G,
                          const mcbte_steady_params* p, const mcbte_steady_out* out, const mcbte_grad_out* gout,
                          void* workspace, size_t ws_bytes, cudaStream_t s) {
@@ -616,7 +625,8 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
     return fail(MCBTE_ERR_INVALID_ARG, "run_steady: nscat_curve needs out->kappa_nscat");
   const int nscat = p->nscat_curve ? p->n_scat_max : 0;
   const bool host_out = out->on_host != 0;
-  const bool replay = grad && p->precision == MCBTE_FP32_TRACE;
+  const bool fused = grad && grad_fused(p);
+  const bool replay = grad && p->precision == MCBTE_FP32_TRACE && !fused;
   const uint64_t n_det = region_detectors(p->n_regions, p->region_grid);
   const uint64_t det_slots = steady_det_slots(p, n);
   // the tail kernel's park buffer when the workspace has room for it (a
@@ -678,6 +688,7 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   C.seed_dev = reinterpret_cast<const unsigned long long*>(p->seed_device);
   C.refill_min = p->refill_threshold;
   C.tail_max = p->tail_lanes == 0 ? 8 : (p->tail_lanes < 0 ? 0 : p->tail_lanes);
+  C.fused = fused ? 1 : 0;
   C.cell_flux_axis = p->cell_flux_axis ? 1 : 0;
   C.ext = (p->n_regions > 0 || nscat > 0) ? 1 : 0;
   for (int g = 0; g < G; ++g) C.ext |= uses_ext(m, geoms[g]->host) ? 1 : 0;
@@ -810,7 +821,8 @@ mcbte_status mcbte_steady_workspace_size(const mcbte_material* m, const mcbte_ge
   if (st != MCBTE_OK) return st;
   if (!bytes) return fail(MCBTE_ERR_INVALID_ARG, "workspace_size: null bytes");
   SteadyWs w = layout_steady(nullptr, n_geoms, m->n, p->n_cells, total, want_grad != 0,
-                             want_grad != 0 && p->precision == MCBTE_FP32_TRACE, n_dirs, false, false, false, false,
+                             want_grad != 0 && p->precision == MCBTE_FP32_TRACE && !grad_fused(p), n_dirs, false,
+                             false, false, false,
                              false, false, steady_det_slots(p, m->n), p->nscat_curve ? p->n_scat_max : 0,
                              park_capacity(p, total));
   *bytes = w.bytes;

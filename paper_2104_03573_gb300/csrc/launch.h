@@ -26,10 +26,13 @@ struct SmemPlan {
   int qbin_in_smem;    // frequency-resolved flux privatised per block
   int cells_in_smem;   // cell tallies privatised per block
   int tail_slots;      // the tail's per-thread draw slots (first in the layout)
+  int grad_in_smem;    // the gradient accumulator privatised per block
+  int snap_in_smem;    // a pore-hit snapshot per thread (measure-valued d/dp; after the tail slots)
   size_t bytes;
 };
 
-SmemPlan plan_smem_f32(int n_bins, int n_geoms, int n_cells, int per_bin, size_t budget, int tail_threads = 0);
+SmemPlan plan_smem_f32(int n_bins, int n_geoms, int n_cells, int per_bin, size_t budget, int tail_threads = 0,
+                       int grad_acc = 0, int snap_threads = 0);
 
 cudaError_t launch_setup(const SetupArgs& a, int n_geoms, const MatView& M, int transient, double t_max_s,
                          int tally_axis, GeoRun* geos, uint64_t* offs, unsigned long long* t0, cudaStream_t s);

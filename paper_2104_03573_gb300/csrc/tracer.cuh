@@ -67,6 +67,7 @@ struct RunCfg {
   int det_nb;           // steady detector sums per detector (1) or per detector and bin (n_bins)
   int tail_max;         // FP32 steady tracer: the tail's draw slots serve warps with at most
                         // this many particles in flight once the work counter has run out (0: off)
+  int fused;            // FP32 gradient: the forward tallies and the gradient in one pass
 };
 
 // Transient detector region (Sec. 4.5): a closed axis-aligned cuboid split
@@ -709,7 +710,9 @@ struct MvdState {
     ++K;
     if (phase) return K == sel ? !spec : spec;
     const unsigned long long v = word();
-    if (v <= 0xFFFFFFFFFFFFFFFFull / (unsigned long long)K) {
+    // v <= floor((2^64 - 1) / K) exactly when the product v K is below
+    // 2^64, i.e. when its high 64 bits are zero (no 64-bit division)
+    if (__umul64hi(v, (unsigned long long)K) == 0ull) {
       sel = K;
       sel_spec = spec;
     }
@@ -734,6 +737,8 @@ struct GradOff {
   __device__ __forceinline__ void resampled(int, double) {}
   template <class Word>
   __device__ __forceinline__ bool pore_branch(bool spec, double, double, Word) { return spec; }
+  template <typename R>
+  __device__ __forceinline__ void pore_hit(const Particle<R>&) {}
   __device__ __forceinline__ int periods() const { return 0; }
   __device__ __forceinline__ int period_bin(int) const { return 0; }
   __device__ __forceinline__ double period_value(int, double) const { return 0.0; }
@@ -798,18 +803,29 @@ struct GradList {
   __device__ __forceinline__ int period_bin(int k) const { return bin[k]; }
   __device__ __forceinline__ double resample_term(double X) const { return (double)n_res * X - sum_x_res; }
   __device__ __forceinline__ double spec_term(double X) const { return PA * X - PB; }
+  template <typename R>
+  __device__ __forceinline__ void pore_hit(const Particle<R>&) {}
 };
 
-// FP32 path, second pass.  The forward pass stored every particle's final
-// tally X_f; this pass traces the same particle again (same random words,
-// same fixed-point tally, so the same trajectory) and adds each relaxation
-// period's term A_k X_f - B_k = a (X_f - X_end) + d to the gradient the moment
-// the period closes.  Nothing is stored per period: a is the period's score
-// sum, d the running sum of (score so far) x (segment tally) (FP32 registers).
+// Relaxation periods a particle of the one-pass FP32 gradient can list
+// (runs with N_scat_max up to this many).
+constexpr int kFusedPeriods = 16;
+
+// FP32 path.  Each relaxation period k adds A_k X_f - B_k = a (X_f - X_k) + d
+// to the gradient of its bin, a being the period's score sum, d the running
+// sum of (score so far) x (segment tally) (FP32 registers) and X_k the tally
+// when the period closes.
+// Replay (second pass): the forward pass stored every particle's final tally
+// X_f; this pass traces the same particle again (same random words, same
+// fixed-point tally, so the same trajectory) and adds the whole term the
+// moment the period closes.  Nothing is stored per period.
+// Fused (one pass, N_scat_max <= kFusedPeriods): X_f is known only at the
+// particle's end, so a closing period adds d - a X_k at once and lists
+// (bin, a); the end adds a X_f for every listed period.
 struct GradReplay {
   static constexpr bool on = true;
   double Xf;
-  long long* G;         // [n_bins] gradient accumulator (global, 2^-20 fixed point: order-free sums)
+  long long* G;         // [n_bins] gradient accumulator (shared or global memory, 2^-20 fixed point: order-free sums)
   int bin_cur;
   float a, d;
   float pa, pd;
@@ -817,8 +833,21 @@ struct GradReplay {
   double sum_x_res;
   int n_dirs, n_bins;
   const double* dirs;
-  double dv[kMaxDirs];  // per direction: sum over closed periods of value x dirs[bin]
+  // The arrays live outside the struct (the kernel's own local arrays): a
+  // struct holding a dynamically indexed array stays in local memory as a
+  // whole, and the per-flight scalars above would go with it.
+  double* dv;           // [kMaxDirs] per direction: sum over closed periods of value x dirs[bin]
   bool mvd;             // measure-valued d/dp (set by the kernel)
+  bool fused;           // one pass (set by the kernel)
+  int np;               // fused: listed periods
+  int* lb;              // [kFusedPeriods] fused: their bins
+  float* la;            // [kFusedPeriods] fused: their score sums
+  // Measure-valued d/dp: the particle as it reached the chosen pore hit
+  // (position on the wall, incoming direction, clocks, tally, counters), so
+  // the phantom trace resumes there instead of tracing again from the
+  // emission: the same state, hence the same bits.  Null: no snapshot.
+  int4* snap;           // [4] this lane's record (shared memory)
+  bool snap_ok;
   MvdState mv;
 
   __device__ __forceinline__ void init(int b) {
@@ -827,7 +856,43 @@ struct GradReplay {
     a = d = pa = pd = 0.0f;
     n_res = 0;
     sum_x_res = 0.0;
+    np = 0;
+    snap_ok = false;
     for (int k = 0; k < n_dirs; ++k) dv[k] = 0.0;
+  }
+  // after the pore branch of a hit: the hit just chosen (nominal trace) is
+  // recorded; p has reached the wall and not yet turned
+  template <typename R>
+  __device__ __forceinline__ void pore_hit(const Particle<R>& p) {
+    if constexpr (sizeof(R) == 4) {
+      if (!mvd || mv.phase || mv.sel != mv.K || snap == nullptr) return;
+      snap[0] = make_int4(__float_as_int(p.x[0]), __float_as_int(p.x[1]), __float_as_int(p.x[2]),
+                          __float_as_int(p.u[0]));
+      snap[1] = make_int4(__float_as_int(p.u[1]), __float_as_int(p.u[2]), __float_as_int(p.d_rel),
+                          __float_as_int(p.d2));
+      snap[2] = make_int4((int)(unsigned)p.Xq, (int)(p.Xq >> 32), (int)(unsigned)p.Xqper, (int)(p.Xqper >> 32));
+      snap[3] = make_int4((int)p.e, p.bin, p.n_relax, __float_as_int(p.s));
+      snap_ok = true;
+    }
+  }
+  // the particle back at the chosen hit, its event not yet applied (e one
+  // less); the caller reloads the bin's constants and applies the event
+  __device__ __forceinline__ void restore(Particle<float>& p) const {
+    const int4 a = snap[0], b = snap[1], c = snap[2], d = snap[3];
+    p.x[0] = __int_as_float(a.x);
+    p.x[1] = __int_as_float(a.y);
+    p.x[2] = __int_as_float(a.z);
+    p.u[0] = __int_as_float(a.w);
+    p.u[1] = __int_as_float(b.x);
+    p.u[2] = __int_as_float(b.y);
+    p.d_rel = __int_as_float(b.z);
+    p.d2 = __int_as_float(b.w);
+    p.Xq = (long long)(((unsigned long long)(unsigned)c.y << 32) | (unsigned)c.x);
+    p.Xqper = (long long)(((unsigned long long)(unsigned)c.w << 32) | (unsigned)c.z);
+    p.e = (uint32_t)d.x - 1u;
+    p.bin = d.y;
+    p.n_relax = d.z;
+    p.s = __int_as_float(d.w);
   }
   __device__ __forceinline__ void flight(bool relax, double ratio, double, float c) {
     if (mv.phase) return;
@@ -835,10 +900,31 @@ struct GradReplay {
     d = fmaf(a, c, d);
     pd = fmaf(pa, c, pd);
   }
+  __device__ __forceinline__ void add(int b, double val) {
+    red_s64(&G[b], __double2ll_rn(val * kFx));
+    for (int k = 0; k < n_dirs; ++k) dv[k] += val * dirs[(size_t)k * n_bins + b];
+  }
   __device__ __forceinline__ void close_period(double Xnow) {
-    const double val = (double)a * (Xf - Xnow) + (double)d;
-    red_s64(&G[bin_cur], __double2ll_rn(val * kFx));
-    for (int k = 0; k < n_dirs; ++k) dv[k] += val * dirs[(size_t)k * n_bins + bin_cur];
+    if (fused) {
+      add(bin_cur, (double)d - (double)a * Xnow);
+      if (np < kFusedPeriods) {   // always: the host runs this pass only for N_scat_max <= kFusedPeriods
+        lb[np] = bin_cur;
+        la[np] = a;
+        ++np;
+      }
+    } else {
+      add(bin_cur, (double)a * (Xf - Xnow) + (double)d);
+    }
+  }
+  // the particle's end, X its final tally: the open period (X_k = X_f: its
+  // term is d), and in a fused pass the listed periods' a X_f
+  __device__ __forceinline__ void finish(double X) {
+    if (!fused) {
+      close_period(X);
+      return;
+    }
+    add(bin_cur, (double)d);
+    for (int k = 0; k < np; ++k) add(lb[k], (double)la[k] * X);
   }
   __device__ __forceinline__ void resampled(int b, double Xnow) {
     if (mv.phase) return;
@@ -993,7 +1079,10 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
       nx = nx / len;
       ny = ny / len;
       spec = (uint64_t)d.wx < g.pthr_pore;
-      if (Grad::on) spec = gr.pore_branch(spec, g.p_pore, Xnow, [&] { return src.mv(ctr, k0, k1); });
+      if (Grad::on) {
+        spec = gr.pore_branch(spec, g.p_pore, Xnow, [&] { return src.mv(ctr, k0, k1); });
+        gr.pore_hit(p);
+      }
     }
     const float two_un = 2.0f * __fmaf_rn(p.u[0], nx, __fmul_rn(p.u[1], ny));
     const float s0 = __fmaf_rn(-two_un, nx, p.u[0]);
@@ -1085,7 +1174,7 @@ __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, cons
   if constexpr (EXT) {
     if (C.n_regs > 0 && T.has_det()) region_steady<R>(p, seg, C, T);
   }
-  if (Grad::on) gr.flight(relax, (double)(seg / p.lam), Xb, c);
+  if (Grad::on) gr.flight(relax, (double)Num<R>::div(seg, p.lam), Xb, c);
 #pragma unroll
   for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
   return apply_event<R, Grad, Tally, EXT, Src>(p, g, M, rec_relax, binf, C, k0, k1, relax, relax2, face, seg, T, gr,

@@ -203,10 +203,11 @@ struct ThreadAcct {
   }
 };
 
-// Gradient pass: the open period closes at the particle's end (X = X_f),
-// then the resampling and specularity terms and the directional values.
+// Gradient pass: the open period closes at the particle's end (X = X_f; a
+// fused pass adds its listed periods' a X_f too), then the resampling and
+// specularity terms and the directional values.
 __device__ __forceinline__ void grad_finish_replay(GradReplay& gr, double X, int g, const RunCfg& C, const Acc& A) {
-  gr.close_period(X);
+  gr.finish(X);
   const double Rv = gr.resample_term(X);
   double* gs = grad_copy(A);
   atomicAdd(gs + 0, Rv);
@@ -224,9 +225,10 @@ __device__ __forceinline__ void grad_finish_replay(GradReplay& gr, double X, int
 
 // A particle the main FP32 kernel hands to the tail kernel: the state the
 // FP32 steady step carries (v, 1/v and Lambda are the bin's, reloaded), its
-// index in the run and, in the gradient pass, the replay bookkeeping.  Only
+// index in the run and, in the gradient pass, the gradient bookkeeping.  Only
 // these fields are stored, so parking keeps nothing else alive in the loop.
 struct ParkRec {
+  int4 snap[4];   // gradient pass: the pore-hit snapshot (snap_ok)
   float x[3], u[3], d_rel, d2, s;
   int bin, n_relax, g;
   uint32_t e, pid;
@@ -239,6 +241,10 @@ struct ParkRec {
   uint32_t mK, mKn, msel;
   int mflags;   // bit 0 sel_spec, bit 1 phase
   double dv[kMaxDirs];
+  int np;       // fused gradient pass: the listed periods
+  int lb[kFusedPeriods];
+  float la[kFusedPeriods];
+  int snap_ok;
 };
 
 template <bool GRAD, class GradT>
@@ -274,6 +280,16 @@ __device__ __forceinline__ void park_store(ParkRec* r, const Particle<float>& p,
     r->msel = gr.mv.sel;
     r->mflags = (gr.mv.sel_spec ? 1 : 0) | (gr.mv.phase ? 2 : 0);
     for (int k = 0; k < n_dirs; ++k) r->dv[k] = gr.dv[k];
+    r->np = gr.np;
+    for (int k = 0; k < gr.np; ++k) {
+      r->lb[k] = gr.lb[k];
+      r->la[k] = gr.la[k];
+    }
+    r->snap_ok = gr.snap_ok ? 1 : 0;
+    if (gr.snap_ok) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) r->snap[k] = gr.snap[k];
+    }
   }
 }
 
@@ -312,6 +328,17 @@ __device__ __forceinline__ void park_load(const ParkRec* r, Particle<float>& p, 
     gr.mv.sel_spec = (r->mflags & 1) != 0;
     gr.mv.phase = (r->mflags & 2) != 0;
     for (int k = 0; k < n_dirs; ++k) gr.dv[k] = r->dv[k];
+    gr.np = r->np;
+    for (int k = 0; k < gr.np; ++k) {
+      gr.lb[k] = r->lb[k];
+      gr.la[k] = r->la[k];
+    }
+    // without a snapshot here the phantom trace starts from the emission
+    gr.snap_ok = r->snap_ok != 0 && gr.snap != nullptr;
+    if (gr.snap_ok) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) gr.snap[k] = r->snap[k];
+    }
   }
 }
 
@@ -350,7 +377,7 @@ __device__ __forceinline__ int trace_slots(Particle<float>& p, const GeoRun& g, 
     if constexpr (EXT) {
       if (C.n_regs > 0 && T.has_det()) region_steady<float>(p, seg, C, T);
     }
-    if (Grad::on) gr.flight(relax, (double)(seg / p.lam), Xb, c);
+    if (Grad::on) gr.flight(relax, (double)Num<float>::div(seg, p.lam), Xb, c);
 #pragma unroll
     for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
     const bool box = !relax && !relax2 && face < 6;
@@ -440,6 +467,12 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
     slots = reinterpret_cast<Draw32*>(sp) + (threadIdx.x & ~31u);
     sp += (size_t)TPB * sizeof(Draw32);
   }
+  // then the pore-hit snapshots (16-byte aligned), four int4 per thread
+  int4* snaps = nullptr;
+  if (S.snap_in_smem) {
+    snaps = reinterpret_cast<int4*>(sp) + (size_t)threadIdx.x * 4;
+    sp += (size_t)TPB * 4 * sizeof(int4);
+  }
   if (S.relax_in_smem) {
     uint4* t = reinterpret_cast<uint4*>(sp);
     for (int i = threadIdx.x; i < n; i += blockDim.x) t[i] = M.rec_relax[i];
@@ -457,6 +490,12 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
     for (int i = threadIdx.x; i < n; i += blockDim.x) s_qbin[i] = 0;
     sp += (size_t)n * sizeof(long long);
   }
+  long long* s_grad = nullptr;
+  if (S.grad_in_smem) {
+    s_grad = reinterpret_cast<long long*>(sp);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s_grad[i] = 0;
+    sp += (size_t)n * sizeof(long long);
+  }
   if (S.cells_in_smem) {
     s_cP = reinterpret_cast<long long*>(sp);
     s_cD = s_cP + (size_t)nc * 4;
@@ -469,8 +508,16 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
   Particle<float> p;
   using GradT = typename GradPick<GRAD, GradReplay>::type;
   GradT gr;
+  double gr_dv[GRAD ? kMaxDirs : 1];
+  int gr_lb[GRAD ? kFusedPeriods : 1];
+  float gr_la[GRAD ? kFusedPeriods : 1];
   if constexpr (GRAD) {
-    gr.G = A.Gq;
+    gr.dv = gr_dv;
+    gr.lb = gr_lb;
+    gr.la = gr_la;
+    gr.snap = snaps;
+    gr.G = S.grad_in_smem ? s_grad : A.Gq;
+    gr.fused = C.fused != 0;
     gr.n_dirs = C.n_dirs;
     gr.n_bins = n;
     gr.dirs = C.dirs;
@@ -485,6 +532,12 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
   T.cP = T.cD = T.qb = nullptr;
   T.h = T.inv_h = 1.0f;
   T.det = (C.n_regs > 0 && !GRAD) ? A.det_q : nullptr;
+  // the per-bin flux of the particle's geometry (a gradient pass tallies
+  // only when fused, and never in a phantom trace)
+  auto qbin_of = [&](int g) -> long long* {
+    if (!C.per_bin || (GRAD && !C.fused)) return nullptr;
+    return S.qbin_in_smem ? s_qbin : A.qbinq + (size_t)g * n;
+  };
   bool alive = false;
   bool drained = false;   // no work left for this lane: it idles in the loop until its warp is drained
   uint64_t idx = 0;
@@ -508,7 +561,7 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
       T.h = G->Lf[C.cell_axis] / (float)nc;
       T.inv_h = (float)nc / G->Lf[C.cell_axis];
     }
-    T.qb = (C.per_bin && !GRAD) ? (S.qbin_in_smem ? s_qbin : A.qbinq + (size_t)g * n) : nullptr;
+    T.qb = qbin_of(g);
   };
   // All 32 lanes stay in the loop until every lane of the warp is drained, so
   // the warp-wide votes below reconverge the warp at every event step.
@@ -599,6 +652,9 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
             park_load<GRAD>(reinterpret_cast<const ParkRec*>(A.park + k * A.park_stride), p, idx, gr, C.n_dirs, M,
                             binf);
             bind(p.g);
+            if constexpr (GRAD) {
+              if (gr.mv.phase) T.qb = nullptr;   // a phantom trace tallies only its own X
+            }
           } else {
             idx = k;
             const int g = find_geom(offs, C.n_geoms, idx);
@@ -608,7 +664,7 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
             emit<float, EXT>(p, *G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, false, 0.0f);
             if constexpr (GRAD) {
               gr.init(p.bin);
-              gr.Xf = A.X_pp[idx];
+              if (!C.fused) gr.Xf = A.X_pp[idx];
             }
           }
           alive = true;
@@ -625,31 +681,10 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
       }
     }
     if (!alive || out == STEP_ALIVE) continue;
-    if (GRAD) {
-      const double X = T.X(p);
-      if constexpr (GRAD) {
-        if (!gr.mv.phase) {
-          if (X != gr.Xf) atomicOr(A.flags, 4);
-          grad_finish_replay(gr, X, p.g, C, A);
-          if (C.mvd && gr.mv.sel > 0u) {
-            // measure-valued d/dp_pore: the same particle again from its
-            // emission, the chosen pore hit's branch flipped (Xf keeps the
-            // nominal tally)
-            gr.Xf = X;
-            gr.mv.start_phantom();
-            emit<float, EXT>(p, *G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, false, 0.0f);
-            continue;
-          }
-        } else {
-          const double D = gr.mv.score(gr.Xf, X);
-          double* gs = grad_copy(A);
-          atomicAdd(gs + 1, D);
-          atomicAdd(gs + 2, D * D);
-        }
-      }
-    } else {
+    // the forward run's part of a finished (nominal) trace: the last period's
+    // per-bin flux, the run's counters and sums, the per-particle outputs
+    auto account = [&](double X) {
       T.period_end(p);
-      const double X = T.X(p);
       const unsigned nev = p.e + 1u;
       acct.ev += nev;
       acct.trunc += (out == STEP_TRUNCATED) ? 1u : 0u;
@@ -666,15 +701,56 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
       if (A.events_pp) A.events_pp[idx] = nev;
       if (A.X_pp) A.X_pp[idx] = X;
       if constexpr (EXT) nscat_end(C, p.g, p.n_relax, X);
+    };
+    if (GRAD) {
+      const double X = T.X(p);
+      if constexpr (GRAD) {
+        if (!gr.mv.phase) {
+          if (C.fused) account(X);
+          else if (X != gr.Xf) atomicOr(A.flags, 4);
+          grad_finish_replay(gr, X, p.g, C, A);
+          if (C.mvd && gr.mv.sel > 0u) {
+            // measure-valued d/dp_pore: the same particle again from its
+            // emission, the chosen pore hit's branch flipped (Xf keeps the
+            // nominal tally; the phantom tallies only its own X)
+            gr.Xf = X;
+            gr.mv.start_phantom();
+            T.qb = nullptr;
+            if (gr.snap_ok) {
+              // resume at the chosen hit (the state the trace from the
+              // emission would reach) and apply it with its branch flipped
+              gr.restore(p);
+              load_bin(p, M, binf);
+              gr.mv.K = gr.mv.sel - 1u;
+              apply_event<float, GradT, decltype(T), EXT>(p, *G, M, relax, binf, C, key.x, key.y, false, false, 6,
+                                                          0.0f, T, gr, T.X(p));
+            } else {
+              emit<float, EXT>(p, *G, M, M.rec_emit, M.rec_init, binf, key.x, key.y, false, 0.0f);
+            }
+            continue;
+          }
+        } else {
+          const double D = gr.mv.score(gr.Xf, X);
+          double* gs = grad_copy(A);
+          atomicAdd(gs + 1, D);
+          atomicAdd(gs + 2, D * D);
+        }
+      }
+    } else {
+      account(T.X(p));
     }
     alive = false;
     drained = pool_dry;
   }
-  if (!GRAD) acct.flush(A);
+  if (!GRAD || C.fused) acct.flush(A);
   __syncthreads();
   if (S.qbin_in_smem) {
     for (int i = threadIdx.x; i < n; i += blockDim.x)
       if (s_qbin[i] != 0) atomicAdd(reinterpret_cast<unsigned long long*>(&A.qbinq[i]), (unsigned long long)s_qbin[i]);
+  }
+  if (S.grad_in_smem) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (s_grad[i] != 0) atomicAdd(reinterpret_cast<unsigned long long*>(&A.Gq[i]), (unsigned long long)s_grad[i]);
   }
   if (S.cells_in_smem) {
     for (int i = threadIdx.x; i < nc * 4; i += blockDim.x)
@@ -857,8 +933,10 @@ cudaError_t launch_f64(const GeoRun* geos, const uint64_t* offs, const MatView& 
 template <int CELLS, bool GRAD, int TPB, bool EXT, int MODE>
 cudaError_t launch_f32_kernel(const GeoRun* geos, const uint64_t* offs, const MatView& M, const RunCfg& C,
                               const Acc& A, int bps, cudaStream_t s) {
-  const SmemPlan S = plan_smem_f32(M.n, C.n_geoms, GRAD ? 0 : C.n_cells, GRAD ? 0 : C.per_bin, 200 * 1024,
-                                   MODE == 2 ? TPB : 0);
+  // the gradient kernel keeps no cell tallies, and the per-bin flux only in
+  // a fused pass
+  const SmemPlan S = plan_smem_f32(M.n, C.n_geoms, GRAD ? 0 : C.n_cells, (GRAD && !C.fused) ? 0 : C.per_bin,
+                                   200 * 1024, MODE == 2 ? TPB : 0, GRAD ? 1 : 0, (GRAD && C.mvd) ? TPB : 0);
   auto kern = k_steady_f32<CELLS, GRAD, TPB, EXT, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.bytes);
   if (e != cudaSuccess) return e;
@@ -873,7 +951,9 @@ cudaError_t launch_f32_kernel(const GeoRun* geos, const uint64_t* offs, const Ma
 
 // Part 0: the main kernel alone.  Part 1: the main kernel that parks its
 // tail, then the tail kernel over the parked particles (256-thread blocks).
+#if MCBTE_F32_PART == 1
 constexpr int kTailThreads = 256;
+#endif
 
 template <int CELLS, bool GRAD, int TPB, bool EXT>
 cudaError_t launch_f32_tpb(const GeoRun* geos, const uint64_t* offs, const MatView& M, const RunCfg& C,
@@ -920,12 +1000,15 @@ cudaError_t launch_f32_variants(bool grad, bool cells, const GeoRun* geos, const
 }  // namespace
 
 #if MCBTE_F64
-SmemPlan plan_smem_f32(int n_bins, int n_geoms, int n_cells, int per_bin, size_t budget, int tail_threads) {
+SmemPlan plan_smem_f32(int n_bins, int n_geoms, int n_cells, int per_bin, size_t budget, int tail_threads,
+                       int grad_acc, int snap_threads) {
   // By use per event: the relaxation alias records and the per-bin
   // constants (every relaxation), the cell tallies (every flight), the
-  // per-bin flux (every relaxation period); each is placed while room
-  // remains, then the tail's draw slots (one Draw32 per thread).
-  SmemPlan S{0, 0, 0, 0, 0, 0};
+  // per-bin flux (every relaxation period), the gradient accumulator (every
+  // period of a gradient pass); each is placed while room remains, then the
+  // tail's draw slots (one Draw32 per thread), then the pore-hit snapshots
+  // of the measure-valued d/dp (64 bytes per thread).
+  SmemPlan S{0, 0, 0, 0, 0, 0, 0, 0};
   size_t used = 0;
   if (used + (size_t)n_bins * 16 <= budget) {
     S.relax_in_smem = 1;
@@ -944,9 +1027,17 @@ SmemPlan plan_smem_f32(int n_bins, int n_geoms, int n_cells, int per_bin, size_t
     S.qbin_in_smem = 1;
     used += (size_t)n_bins * 8;
   }
+  if (grad_acc && used + (size_t)n_bins * 8 <= budget) {
+    S.grad_in_smem = 1;
+    used += (size_t)n_bins * 8;
+  }
   if (tail_threads > 0 && n_bins <= kOneBlockBins && used + (size_t)tail_threads * sizeof(Draw32) <= budget) {
     S.tail_slots = 1;
     used += (size_t)tail_threads * sizeof(Draw32);
+  }
+  if (snap_threads > 0 && used + (size_t)snap_threads * 4 * sizeof(int4) <= budget) {
+    S.snap_in_smem = 1;
+    used += (size_t)snap_threads * 4 * sizeof(int4);
   }
   S.bytes = used;
   return S;
@@ -977,7 +1068,9 @@ cudaError_t launch_steady(int precision, bool grad, const GeoRun* geos, const ui
     if (grad) return cells ? launch_f64<true, true>(geos, offs, M, C, A, s) : launch_f64<false, true>(geos, offs, M, C, A, s);
     return cells ? launch_f64<true, false>(geos, offs, M, C, A, s) : launch_f64<false, false>(geos, offs, M, C, A, s);
   }
-  return launch_steady_f32(grad, cells, geos, offs, M, C, A, threads > 0 ? threads : 768, bps, s);
+  // default block: 768 threads, 512 for the gradient (its estimator state
+  // takes ~128 registers per thread)
+  return launch_steady_f32(grad, cells, geos, offs, M, C, A, threads > 0 ? threads : (grad ? 512 : 768), bps, s);
 }
 
 cudaError_t launch_finalize_steady(const GeoRun* geos, const MatView& M, const RunCfg& C, const Acc& A,
