@@ -42,6 +42,7 @@ struct alignas(128) GeoRun {
   int n_inner;
   int fbin;                    // bit f: face f takes the per-bin specularity
   int sbin;                    // bit k: wall k takes the per-bin specularity
+  int unfold;                  // bit a: axis a is periodic and the box holds no pore or wall
   int type[6];
   uint64_t pthr[6];
   uint64_t pthr_pore;
@@ -303,9 +304,12 @@ __device__ __forceinline__ void dir_about_frame(R u[3], const R* f, R mu, uint32
 // particle's event waits on it); then the pore by the same test and root
 // with selects instead of branches.  One function for both records, so both
 // compute the same bits.
+//
+// Axes in the mask `skip` (unfolded periodic axes) take no part: the flight
+// runs through their faces.
 template <class Geo>
 __device__ __forceinline__ void hit_box_pore_f32(const Geo& g, const float x[3], const float u[3], float* dist,
-                                                 int* face) {
+                                                 int* face, unsigned skip = 0u) {
   float c[3];
   int fa[3];
   bool ok[3];
@@ -314,7 +318,7 @@ __device__ __forceinline__ void hit_box_pore_f32(const Geo& g, const float x[3],
     const float ua = u[a];
     const bool up = ua > 0.0f;
     const float d0 = Num<float>::div((up ? g.Lf[a] : 0.0f) - x[a], ua);
-    ok[a] = ua != 0.0f;
+    ok[a] = ua != 0.0f && ((skip >> a) & 1u) == 0u;
     c[a] = ok[a] ? (d0 < 0.0f ? 0.0f : d0) : Num<float>::big();
     fa[a] = up ? axis_max_face(a) : axis_min_face(a);
   }
@@ -338,6 +342,34 @@ __device__ __forceinline__ void hit_box_pore_f32(const Geo& g, const float x[3],
   }
   *dist = best;
   *face = bf;
+}
+
+// The unfolded periodic axes (bits of um) folded back into [0, L) after a
+// flight that ran through their faces; returns the faces crossed, each of
+// them the event (a translation to the opposite face) a flight stopped at
+// every face would have counted.
+__device__ __forceinline__ uint32_t fold_periodic(float x[3], const float L[3], unsigned um) {
+  uint32_t n = 0u;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (((um >> a) & 1u) == 0u) continue;
+    const float La = L[a];
+    if (x[a] >= 0.0f && x[a] < La) continue;   // no face crossed on this axis
+    float k = floorf(__fdividef(x[a], La));
+    float r = fmaf(-k, La, x[a]);
+    // the quotient's rounding can leave r just outside [0, L)
+    if (r < 0.0f) {
+      r += La;
+      k -= 1.0f;
+    }
+    if (r >= La) {
+      r -= La;
+      k += 1.0f;
+    }
+    x[a] = r;
+    n += (uint32_t)fabsf(k);
+  }
+  return n;
 }
 
 // The FP32 event step's geometry in registers (the tail kernel's particles):

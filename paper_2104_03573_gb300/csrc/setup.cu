@@ -63,6 +63,12 @@ __global__ void k_setup(SetupArgs a, int G, MatView M, int transient, double t_m
     if (d.inner_p[k] < 0.0) r.sbin |= 1 << k;
   }
   r.pore = d.pore;
+  // periodic axes a flight may cross without stopping (no pore and no walls
+  // inside the box: crossing a periodic face changes nothing but the position)
+  r.unfold = 0;
+  if (!d.pore && d.n_inner == 0)
+    for (int a = 0; a < 3; ++a)
+      if (r.type[axis_min_face(a)] == MCBTE_FACE_PERIODIC) r.unfold |= 1 << a;
   r.cx = d.pore_c[0] * 1e9;
   r.cy = d.pore_c[1] * 1e9;
   const double rr = d.pore_r * 1e9;

@@ -336,6 +336,21 @@ struct DrawSlot {
   }
 };
 
+// The slot when the event has one (s non-null), else the inline draws: an
+// unfolded flight can end on an event past the slots computed for it.
+struct DrawSlotOr {
+  const Draw32* s;
+  __device__ __forceinline__ Draw32 sub0(uint4 ctr, uint32_t k0, uint32_t k1, const uint4* rec, int n) const {
+    return s ? *s : DrawInline().sub0(ctr, k0, k1, rec, n);
+  }
+  __device__ __forceinline__ float e2(uint4 ctr, uint32_t k0, uint32_t k1) const {
+    return s ? s->E2 : DrawInline().e2(ctr, k0, k1);
+  }
+  __device__ __forceinline__ unsigned long long mv(uint4 ctr, uint32_t k0, uint32_t k1) const {
+    return s ? DrawSlot{s}.mv(ctr, k0, k1) : DrawInline().mv(ctr, k0, k1);
+  }
+};
+
 // Two-phonon clock (Sec. 3.3): a new exponential distance with the current
 // bin's mean free path v tau_imp, from sub-block 256 of the particle's
 // current event; +inf without impurity scattering.
@@ -1155,11 +1170,48 @@ __device__ __forceinline__ void region_steady(const Particle<R>& p, R seg, const
 // remaining relaxation distance (boundary wins ties, Sec. 3.3 case iii),
 // track-length tallies of the flight (Eqs. temp_steady, flux_x_steady), then
 // the event.
-template <typename R, class Grad, class Tally, bool EXT = true, class Src = DrawInline>
+// Periodic axes an FP32 forward flight runs through (no extended physics,
+// no pore, no walls; never the cell axis, whose tallies follow the position).
+// A gradient pass keeps stopping at them: its causal scores depend on where
+// flights are cut.
+template <class Grad>
+__device__ __forceinline__ unsigned unfold_mask(const GeoRun& g, const RunCfg& C) {
+  if (Grad::on) return 0u;
+  return (unsigned)g.unfold & ~(C.n_cells > 0 ? (1u << C.cell_axis) : 0u);
+}
+
+// UNF: the kernel compiles the unfolded flight in (FP32 kernels without
+// cell tallies; the others keep their registers for the tallies).
+template <typename R, class Grad, class Tally, bool EXT = true, class Src = DrawInline, bool UNF = false>
 __device__ __forceinline__ int step_steady(Particle<R>& p, const GeoRun& g, const MatView& M, const uint4* rec_relax,
                                            const float4* binf, const RunCfg& C, uint32_t k0, uint32_t k1,
                                            const Tally& T, Grad& gr, const Src& src = Src()) {
   if (p.e + 1u >= C.max_events) return STEP_TRUNCATED;
+  if constexpr (UNF && sizeof(R) == 4 && !EXT && !Grad::on) {
+    const unsigned um = unfold_mask<Grad>(g, C);
+    if (um) {
+      // the flight runs to the nearest face off the periodic axes (or the
+      // relaxation), crossing periodic faces on its way; the crossings are
+      // counted as the events they are, so the event that ends the flight
+      // keeps its number and its random words
+      float db;
+      int face;
+      hit_box_pore_f32(g, p.x, p.u, &db, &face, um);
+      const bool relax = p.d_rel < db;
+      const float seg = relax ? p.d_rel : db;
+      T.segment(p, seg);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
+      const uint32_t n = fold_periodic(p.x, g.Lf, um);
+      if (n >= C.max_events - 1u - p.e) {
+        p.e = C.max_events - 1u;
+        return STEP_TRUNCATED;
+      }
+      p.e += n;
+      return apply_event<R, Grad, Tally, EXT, Src>(p, g, M, rec_relax, binf, C, k0, k1, relax, false, face, seg, T,
+                                                   gr, 0.0, src);
+    }
+  }
   R db;
   int face;
   first_hit<R, EXT>(g, p.x, p.u, &db, &face);

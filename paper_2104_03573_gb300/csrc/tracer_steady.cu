@@ -419,6 +419,136 @@ __device__ __forceinline__ int trace_slots(Particle<float>& p, const GeoRun& g, 
   }
 }
 
+// The tail loop of a particle whose flights run through unfolded periodic
+// axes (forward run without cell tallies or extended physics; a box with no
+// pore and no walls): trace_slots with step_steady's unfolded flight.  The
+// crossings advance the event number, so the event that ends a flight may
+// lie past the slots and then takes its draws inline (the same bits).
+template <class Tally>
+__device__ __forceinline__ int trace_unfolded(Particle<float>& p, const GeoRun& g, const MatView& M,
+                                              const uint4* relax_tab, const float4* binf, const RunCfg& C, uint32_t k0,
+                                              uint32_t k1, const Tally& T, const Draw32* slot0, uint32_t e_last,
+                                              uint64_t deadline, int* flags, unsigned um) {
+  const uint32_t e0 = p.e;
+  const uint32_t nslots = e_last - e0;
+  GeoLean gl;
+  gl.load(g);
+  GradOff off;
+  for (;;) {
+    if (p.e + 1u >= C.max_events) return STEP_TRUNCATED;
+    float db;
+    int face;
+    hit_box_pore_f32(gl, p.x, p.u, &db, &face, um);
+    const bool relax = p.d_rel < db;
+    const float seg = relax ? p.d_rel : db;
+    T.segment(p, seg);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
+    const uint32_t n = fold_periodic(p.x, gl.Lf, um);
+    if (n >= C.max_events - 1u - p.e) {
+      p.e = C.max_events - 1u;
+      return STEP_TRUNCATED;
+    }
+    p.e += n;
+    const uint32_t si = p.e - e0;
+    const Draw32* slot = si < nslots ? slot0 + si : nullptr;
+    if (!relax && face < 6) {
+      // apply_event's FP32 face branch (every periodic axis is unfolded, so
+      // the face is isothermal: absorbed, or adiabatic: specular or
+      // Lambertian by the event's draws, then a select)
+      ++p.e;
+      p.d_rel = p.d_rel - seg;
+      const int a = face_axis(face);
+      const int mx = face_is_max(face);
+      put3<float>(p.x, a, mx ? gl.L(a) : 0.0f);
+      if (gl.type(face) == MCBTE_FACE_ISOTHERMAL) return STEP_ABSORBED;
+      const Draw32 d = DrawSlotOr{slot}.sub0(make_uint4(p.pid, (uint32_t)p.g, p.e, 0u), k0, k1, relax_tab, M.n);
+      const bool spec_f = (uint64_t)d.wx < g.pthr[face];
+      float ud[3];
+      put3_cyclic<float>(ud, a, mx ? -d.lam[0] : d.lam[0], d.lam[1], d.lam[2]);
+      const float flip = -sel3(p.u, a);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) p.u[b] = spec_f ? (b == a ? flip : p.u[b]) : ud[b];
+    } else {
+      const int out = apply_event<float, GradOff, Tally, false, DrawSlotOr>(p, g, M, relax_tab, binf, C, k0, k1,
+                                                                            relax, false, face, seg, T, off, 0.0,
+                                                                            DrawSlotOr{slot});
+      if (out != STEP_ALIVE) return out;
+    }
+    if ((p.e & 255u) == 0u && globaltimer_ns() > deadline) {
+      atomicOr(flags, 1);
+      return STEP_TRUNCATED;
+    }
+    if (p.e >= e_last) return STEP_ALIVE;
+  }
+}
+
+// trace_unfolded for a box whose only faces left are the pair across axis W
+// (the other two axes unfolded: a film): the flight's first hit is that
+// pair's, and the pair's types and specular thresholds sit in registers.
+// The same operations as hit_box_pore_f32 with those axes skipped and as
+// apply_event's face branch, hence the same bits as step_steady.
+template <int W, class Tally>
+__device__ __forceinline__ int trace_film(Particle<float>& p, const GeoRun& g, const MatView& M,
+                                          const uint4* relax_tab, const float4* binf, const RunCfg& C, uint32_t k0,
+                                          uint32_t k1, const Tally& T, const Draw32* slot0, uint32_t e_last,
+                                          uint64_t deadline, int* flags, unsigned um) {
+  const uint32_t e0 = p.e;
+  const uint32_t nslots = e_last - e0;
+  float Lf[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) Lf[a] = g.Lf[a];
+  const int f_lo = axis_min_face(W), f_hi = axis_max_face(W);
+  const bool iso_lo = g.type[f_lo] == MCBTE_FACE_ISOTHERMAL, iso_hi = g.type[f_hi] == MCBTE_FACE_ISOTHERMAL;
+  const uint64_t th_lo = g.pthr[f_lo], th_hi = g.pthr[f_hi];
+  GradOff off;
+  for (;;) {
+    if (p.e + 1u >= C.max_events) return STEP_TRUNCATED;
+    const float uw = p.u[W];
+    const bool up = uw > 0.0f;
+    const bool ok = uw != 0.0f;
+    const float d0 = Num<float>::div((up ? Lf[W] : 0.0f) - p.x[W], uw);
+    const float db = ok ? (d0 < 0.0f ? 0.0f : d0) : Num<float>::big();
+    const bool relax = p.d_rel < db;
+    const float seg = relax ? p.d_rel : db;
+    T.segment(p, seg);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) p.x[a] = p.x[a] + seg * p.u[a];
+    const uint32_t n = fold_periodic(p.x, Lf, um);
+    if (n >= C.max_events - 1u - p.e) {
+      p.e = C.max_events - 1u;
+      return STEP_TRUNCATED;
+    }
+    p.e += n;
+    const uint32_t si = p.e - e0;
+    const Draw32* slot = si < nslots ? slot0 + si : nullptr;
+    if (!relax && ok) {
+      // a wall of the pair
+      ++p.e;
+      p.d_rel = p.d_rel - seg;
+      p.x[W] = up ? Lf[W] : 0.0f;
+      if (up ? iso_hi : iso_lo) return STEP_ABSORBED;
+      const Draw32 d = DrawSlotOr{slot}.sub0(make_uint4(p.pid, (uint32_t)p.g, p.e, 0u), k0, k1, relax_tab, M.n);
+      const bool spec_f = (uint64_t)d.wx < (up ? th_hi : th_lo);
+      float ud[3];
+      put3_cyclic<float>(ud, W, up ? -d.lam[0] : d.lam[0], d.lam[1], d.lam[2]);
+      const float flip = -p.u[W];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) p.u[b] = spec_f ? (b == W ? flip : p.u[b]) : ud[b];
+    } else {
+      const int out = apply_event<float, GradOff, Tally, false, DrawSlotOr>(p, g, M, relax_tab, binf, C, k0, k1,
+                                                                            relax, false, ok ? (up ? f_hi : f_lo) : 7,
+                                                                            seg, T, off, 0.0, DrawSlotOr{slot});
+      if (out != STEP_ALIVE) return out;
+    }
+    if ((p.e & 255u) == 0u && globaltimer_ns() > deadline) {
+      atomicOr(flags, 1);
+      return STEP_TRUNCATED;
+    }
+    if (p.e >= e_last) return STEP_ALIVE;
+  }
+}
+
 // Every lane owns one particle at a time.  When its particle terminates the
 // lane refills from a global work counter; the refills of a warp are
 // aggregated into one atomicAdd (ballot of the empty lanes, leader adds the
@@ -452,6 +582,8 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
                                                        const uint64_t* __restrict__ offs, MatView M, RunCfg C,
                                                        Acc A, SmemPlan S) {
   constexpr bool TK = MODE == 2;
+  // flights through the unfolded periodic axes (step_steady)
+  constexpr bool UNF = CELLS == 0 && !GRAD && !EXT;
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* sp = smem;
   const int n = M.n;
@@ -618,10 +750,22 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
           slots[lane] = d;
         }
         __syncwarp();
-        if (alive)
-          out = trace_slots<GradT, decltype(T), EXT>(p, *G, M, relax, binf, C, key.x, key.y, T, gr,
-                                                      slots + (__popc(live & ((1u << lane) - 1u)) << sh),
-                                                      p.e + (1u << sh), deadline, A.flags);
+        if (alive) {
+          const Draw32* s0 = slots + (__popc(live & ((1u << lane) - 1u)) << sh);
+          const unsigned um = UNF ? unfold_mask<GradT>(*G, C) : 0u;
+          const uint32_t e_l = p.e + (1u << sh);
+          if (UNF && um == 3u)
+            out = trace_film<2>(p, *G, M, relax, binf, C, key.x, key.y, T, s0, e_l, deadline, A.flags, um);
+          else if (UNF && um == 5u)
+            out = trace_film<1>(p, *G, M, relax, binf, C, key.x, key.y, T, s0, e_l, deadline, A.flags, um);
+          else if (UNF && um == 6u)
+            out = trace_film<0>(p, *G, M, relax, binf, C, key.x, key.y, T, s0, e_l, deadline, A.flags, um);
+          else if (UNF && um)
+            out = trace_unfolded(p, *G, M, relax, binf, C, key.x, key.y, T, s0, e_l, deadline, A.flags, um);
+          else
+            out = trace_slots<GradT, decltype(T), EXT>(p, *G, M, relax, binf, C, key.x, key.y, T, gr, s0,
+                                                        p.e + (1u << sh), deadline, A.flags);
+        }
         __syncwarp();   // the slots are rewritten in the next round
       }
     } else {
@@ -674,7 +818,8 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
         drained = drained || pool_dry;   // nothing left to hand out
         continue;
       }
-      out = step_steady<float, GradT, decltype(T), EXT>(p, *G, M, relax, binf, C, key.x, key.y, T, gr);
+      out = step_steady<float, GradT, decltype(T), EXT, DrawInline, UNF>(p, *G, M, relax, binf, C, key.x, key.y, T,
+                                                                          gr);
       if (out == STEP_ALIVE && (p.e & 255u) == 0u && globaltimer_ns() > deadline) {
         atomicOr(A.flags, 1);
         out = STEP_TRUNCATED;
