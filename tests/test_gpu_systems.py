@@ -428,3 +428,57 @@ def test_l2_reduction_probe_adds_exactly():
     r = slots.view(-1, 4)
     assert torch.equal(r[:, 0], r[:, 3])          # the four words of a record move together
     assert int((r[:, 0] > 0).sum().item()) > 900   # the groups spread over the records
+
+
+def test_fused_gradient_pass_equals_the_two_pass_replay():
+    """With N_scat_max <= 16 and no cell tallies the FP32 gradient is one pass
+    (each particle lists its periods' score sums until its final tally is
+    known); asking for cell tallies makes it a forward pass plus a replay.
+    Same particles, same trajectories: the forward tallies agree bit for bit,
+    the gradient to the rounding of its split fixed-point terms, and the
+    measure-valued d/dp (the same phantom tallies) to the order of its sums."""
+    wl = W.pore_film_c5(n=200_000)
+    mat, geo, run = wl.material, wl.geometries[0], wl.run
+    M, G = api.Material(mat), api.Geometry(geo)
+    base = api.SteadyConfig(seed=47, precision=L.FP32_TRACE, tally_axis=1, per_bin=True, n_scat_max=10,
+                            max_events=10 ** 8, threads_per_block=512, refill_threshold=4)
+    ones = np.ones((1, mat.n_bins))
+    res = []
+    for n_cells in (0, 4):
+        fwd, go = api.grad(M, G, run.n, replace(base, n_cells=n_cells, cell_axis=2), dirs=ones)
+        torch.cuda.synchronize()
+        assert fwd.stats[0, L.STAT_STATUS].item() == 0
+        res.append((fwd.q_bin.cpu().numpy(), fwd.stats[0].cpu().numpy(), go.dkappa_dlogtau.cpu().numpy(),
+                    go.dkappa_dp.cpu().numpy(), go.dkappa_dir.cpu().numpy()))
+    (q0, s0, d0, p0, r0), (q1, s1, d1, p1, r1) = res
+    assert np.array_equal(q0, q1)
+    assert s0[L.STAT_EVENTS] == s1[L.STAT_EVENTS]
+    assert s0[L.STAT_KAPPA] == pytest.approx(s1[L.STAT_KAPPA], rel=1e-12)
+    np.testing.assert_allclose(d0, d1, rtol=0, atol=1e-6 * np.abs(d1).max())
+    assert d0.sum() == pytest.approx(d1.sum(), rel=1e-6)
+    assert r0[0, 0] == pytest.approx(r1[0, 0], rel=1e-6)
+    assert p0[0] == pytest.approx(p1[0], rel=1e-12) and p0[1] == pytest.approx(p1[1], rel=1e-9)
+
+
+def test_unfolded_periodic_flights_keep_event_counts():
+    """A forward flight without cell tallies runs through periodic faces and
+    counts the crossings; with a cell tally the kernel stops at every face.
+    The event counts agree particle by particle (a rare position that rounds
+    onto a face may move one crossing), the tallies to rounding, kappa well
+    within its standard error."""
+    wl = W.film_batch_c4(n_films=8, scale=0.02)
+    M = api.Material(wl.material)
+    Gs = [api.Geometry(g) for g in wl.geometries]
+    base = api.SteadyConfig(seed=53, precision=L.FP32_TRACE, tally_axis=1, per_bin=True, n_scat_max=10,
+                            max_events=10 ** 8, threads_per_block=512, refill_threshold=4)
+    unf = _run(M, Gs, wl.n_per_geom, base, per_particle=True)
+    stp = _run(M, Gs, wl.n_per_geom, replace(base, n_cells=1, cell_axis=2), per_particle=True)
+    e_u, e_s = unf.events_pp.cpu().numpy(), stp.events_pp.cpu().numpy()
+    assert e_u.size == sum(wl.n_per_geom) and np.mean(e_u != e_s) < 1e-3
+    same = e_u == e_s
+    x_u, x_s = unf.X_pp.cpu().numpy(), stp.X_pp.cpu().numpy()
+    assert np.max(np.abs(x_u[same] - x_s[same])) < 1e-3 * max(1.0, np.abs(x_s).max())
+    su, ss = unf.stats.cpu().numpy(), stp.stats.cpu().numpy()
+    assert np.all(su[:, L.STAT_STATUS] == 0) and np.all(ss[:, L.STAT_STATUS] == 0)
+    z = (su[:, L.STAT_KAPPA] - ss[:, L.STAT_KAPPA]) / ss[:, L.STAT_KAPPA_SE]
+    assert np.all(np.abs(z) < 0.5), z
