@@ -960,6 +960,43 @@ struct GradReplay {
   __device__ __forceinline__ double spec_term(double) const { return (double)pd; }
 };
 
+// A warp's run of particle indices [cb, ce), taken kTakeChunk at a time
+// from the run's work counter: one returning atomic on that single address
+// per kTakeChunk particles instead of one per warp refill.  take() (called by
+// the whole warp) returns this lane's index among the lanes in `need` (the
+// others' values are meaningless) and checks the time budget at every take
+// of the counter (particles shorter than the per-event check interval would
+// otherwise never look).  dry: the counter has run out; with cb >= ce the
+// warp has nothing left to hand out.
+constexpr unsigned kTakeChunk = 256;
+struct WarpRun {
+  uint64_t cb = 0, ce = 0;
+  bool dry = false;
+  __device__ __forceinline__ uint64_t take(unsigned need, unsigned lane, unsigned long long* work, uint64_t total,
+                                           uint64_t deadline, int* flags) {
+    const unsigned cnt = __popc(need);
+    const unsigned rank = __popc(need & ((1u << lane) - 1u));
+    const uint64_t left = cb < ce ? ce - cb : 0;
+    if (left >= cnt) {
+      const uint64_t k = cb + rank;
+      cb += cnt;
+      return k;
+    }
+    unsigned long long nb = 0;
+    if (lane == 0) {
+      nb = atomicAdd(work, (unsigned long long)kTakeChunk);
+      if (globaltimer_ns() > deadline) atomicOr(flags, 1);
+    }
+    nb = __shfl_sync(0xffffffffu, nb, 0);
+    const uint64_t k = rank < left ? cb + rank : nb + (rank - left);
+    cb = nb + (cnt - left);
+    ce = nb + kTakeChunk < total ? nb + kTakeChunk : total;
+    if (nb + kTakeChunk >= total) dry = true;
+    return k;
+  }
+  __device__ __forceinline__ bool empty() const { return dry && cb >= ce; }
+};
+
 // Philox key of the run: the host seed, or the device-resident one.
 __device__ __forceinline__ uint2 run_key(const RunCfg& C) {
   if (C.seed_dev) {

@@ -168,9 +168,6 @@ __global__ void __launch_bounds__(256) k_steady_fp64(const GeoRun* __restrict__ 
 
 #if MCBTE_F32
 // ------------------------------------------------------------------ FP32 persistent
-// Particle indices a warp of the main kernel takes from the work counter at once.
-constexpr unsigned kChunk = 256;
-
 // Per-thread book-keeping of finished particles (integer / fixed-point
 // fields, few registers), flushed to the geometry's global accumulators when
 // the thread moves to another geometry and at exit.
@@ -683,8 +680,7 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
   const int tail_max = (TK ? (slots != nullptr && n <= kOneBlockBins) : (MODE == 1 && A.park_cap > 0)) ? C.tail_max : 0;
   const uint64_t n_parked = TK ? min(*(volatile unsigned long long*)A.park_n, (unsigned long long)A.park_cap) : 0;
   bool pool_dry = false;   // the same in every lane: nothing left to hand out
-  uint64_t cb = 0, ce = 0;  // main kernel: the warp's run of particle indices not yet handed out
-  bool work_dry = false;    // the work counter has run out
+  WarpRun run;              // main kernel: the warp's particle indices not yet handed out
   // the tallies of the lane's geometry
   auto bind = [&](int g) {
     if (g != acct.g) {
@@ -790,30 +786,9 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
           if (base + cnt >= avail) pool_dry = true;
           k = base + rank;
         } else {
-          // the warp's own run of indices [cb, ce), taken kChunk at a time
-          // from the work counter (one returning atomic per kChunk particles,
-          // not per refill); the time budget is checked at every take
-          // (particles shorter than the per-event check interval would
-          // otherwise never look)
-          const uint64_t left = cb < ce ? ce - cb : 0;
-          unsigned long long nb = 0;
-          if (left < cnt) {
-            if (lane == 0) {
-              nb = atomicAdd(A.work, (unsigned long long)kChunk);
-              if (globaltimer_ns() > deadline) atomicOr(A.flags, 1);
-            }
-            nb = __shfl_sync(kAll, nb, 0);
-          }
-          k = rank < left ? cb + rank : nb + (rank - left);
-          if (left < cnt) {
-            cb = nb + (cnt - left);
-            ce = nb + kChunk < C.total ? nb + kChunk : C.total;
-            if (nb + kChunk >= C.total) work_dry = true;
-          } else {
-            cb += cnt;
-          }
+          k = run.take(need, lane, A.work, C.total, deadline, A.flags);
           avail = C.total;
-          if (work_dry && cb >= ce) pool_dry = true;
+          if (run.empty()) pool_dry = true;
         }
         if (!alive && !drained) {
           if (k >= avail || (*(volatile int*)A.flags & 1)) {

@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
   const uint64_t deadline = *C.t0 + C.budget_ns;
   const unsigned lane = threadIdx.x & 31u;
   const uint2 key = run_key(C);
+  WarpRun run;   // the warp's particle indices not yet handed out
   Particle<float> p;
   bool alive = false;
   bool drained = false;   // as in the steady tracer: idle lanes stay until the warp is drained
@@ -296,16 +297,9 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
       if (__all_sync(kAll, drained)) break;
       const unsigned need = __ballot_sync(kAll, !alive && !drained);
       if (need) {
-        const int leader = __ffs(need) - 1;
-        unsigned long long base = 0;
-        if ((int)lane == leader) {
-          base = atomicAdd(A.work, (unsigned long long)__popc(need));
-          if (((base + (unsigned long long)__popc(need)) >> 12) != (base >> 12) && globaltimer_ns() > deadline)
-            atomicOr(A.flags, 1);
-        }
-        base = __shfl_sync(kAll, base, leader);
+        const uint64_t k = run.take(need, lane, A.work, C.total, deadline, A.flags);
         if (!alive && !drained) {
-          idx = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
+          idx = k;
           if (idx >= C.total || (*(volatile int*)A.flags & 1)) {
             drained = true;
           } else if (C.win_first) {
@@ -400,19 +394,9 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
       if (__all_sync(kAll, drained)) break;
       const unsigned need = __ballot_sync(kAll, !alive && !drained);
       if (need) {
-        const int leader = __ffs(need) - 1;
-        unsigned long long base = 0;
-        if ((int)lane == leader) {
-          base = atomicAdd(A.work, (unsigned long long)__popc(need));
-          // the time budget is also checked each time the handed-out count
-          // crosses a multiple of 4096 (particles shorter than the per-event
-          // check interval would otherwise never look)
-          if (((base + (unsigned long long)__popc(need)) >> 12) != (base >> 12) && globaltimer_ns() > deadline)
-            atomicOr(A.flags, 1);
-        }
-        base = __shfl_sync(kAll, base, leader);
+        const uint64_t k = run.take(need, lane, A.work, C.total, deadline, A.flags);
         if (!alive && !drained) {
-          idx = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
+          idx = k;
           if (idx >= C.total || (*(volatile int*)A.flags & 1)) {
             drained = true;
             continue;
