@@ -311,8 +311,7 @@ typedef struct {
   int n_times;                 /* measurement times (Sec. 3.4), 1..MCBTE_MAX_TIMES       */
   const double* t_meas;        /* HOST [n_times] s, ascending, in (0, t_max]             */
   int grid[3];                 /* nx, ny, nz detector cells over the box                 */
-  int threads_per_block;        /* 0 (default: 512 for whole-grid snapshots, else 1024),   */
-                                /* 256, 512, 768 or 1024 (FP32 path)                      */
+  int threads_per_block;        /* 0 (default 1024), 256, 512, 768 or 1024 (FP32 path)    */
   int blocks_per_sm;
   double time_budget_s;
   void* trace_event_start;     /* optional cudaEvent_t pair around the tracing kernel     */

@@ -689,6 +689,7 @@ mcbte_status steady_impl(const mcbte_material* m, const mcbte_geometry* const* g
   C.refill_min = p->refill_threshold;
   C.tail_max = p->tail_lanes == 0 ? 8 : (p->tail_lanes < 0 ? 0 : p->tail_lanes);
   C.fused = fused ? 1 : 0;
+  C.take_chunk = G > 1 ? 1024u : 256u;
   C.cell_flux_axis = p->cell_flux_axis ? 1 : 0;
   C.ext = (p->n_regions > 0 || nscat > 0) ? 1 : 0;
   for (int g = 0; g < G; ++g) C.ext |= uses_ext(m, geoms[g]->host) ? 1 : 0;
@@ -1018,6 +1019,7 @@ mcbte_status mcbte_run_transient(const mcbte_material* m, const mcbte_geometry* 
   C.max_events = (p->max_events == 0 || p->max_events > 0xFFFFFFFFull) ? 0xFFFFFFFFu : (uint32_t)p->max_events;
   C.n_geoms = 1;
   C.total = p->n_particles;
+  C.take_chunk = 256u;
   C.t0 = w.t0;
   C.budget_ns = (uint64_t)((p->time_budget_s > 0 ? p->time_budget_s : 120.0) * 1e9);
   C.t_max_ps = p->t_max * 1e12;

@@ -68,6 +68,10 @@ struct RunCfg {
   int tail_max;         // FP32 steady tracer: the tail's draw slots serve warps with at most
                         // this many particles in flight once the work counter has run out (0: off)
   int fused;            // FP32 gradient: the forward tallies and the gradient in one pass
+  // particle indices a warp takes from the work counter at once (WarpRun):
+  // 1024 for a batch of geometries (a warp stays on one geometry longer),
+  // 256 otherwise (a shorter drain); 0 counts as 32
+  unsigned take_chunk;
 };
 
 // Transient detector region (Sec. 4.5): a closed axis-aligned cuboid split
@@ -960,20 +964,19 @@ struct GradReplay {
   __device__ __forceinline__ double spec_term(double) const { return (double)pd; }
 };
 
-// A warp's run of particle indices [cb, ce), taken kTakeChunk at a time
-// from the run's work counter: one returning atomic on that single address
-// per kTakeChunk particles instead of one per warp refill.  take() (called by
-// the whole warp) returns this lane's index among the lanes in `need` (the
-// others' values are meaningless) and checks the time budget at every take
-// of the counter (particles shorter than the per-event check interval would
-// otherwise never look).  dry: the counter has run out; with cb >= ce the
-// warp has nothing left to hand out.
-constexpr unsigned kTakeChunk = 256;
+// A warp's run of particle indices [cb, ce), taken from the run's work
+// counter `chunk` at a time (RunCfg::take_chunk): one returning atomic on
+// that single address per chunk instead of one per warp refill.  take()
+// (called by the whole warp) returns this lane's index among the lanes in
+// `need` (the others' values are meaningless) and checks the time budget at
+// every take of the counter (particles shorter than the per-event check
+// interval would otherwise never look).  dry: the counter has run out; with
+// cb >= ce the warp has nothing left to hand out.
 struct WarpRun {
   uint64_t cb = 0, ce = 0;
   bool dry = false;
   __device__ __forceinline__ uint64_t take(unsigned need, unsigned lane, unsigned long long* work, uint64_t total,
-                                           uint64_t deadline, int* flags) {
+                                           unsigned chunk, uint64_t deadline, int* flags) {
     const unsigned cnt = __popc(need);
     const unsigned rank = __popc(need & ((1u << lane) - 1u));
     const uint64_t left = cb < ce ? ce - cb : 0;
@@ -982,16 +985,17 @@ struct WarpRun {
       cb += cnt;
       return k;
     }
+    chunk = chunk < 32u ? 32u : chunk;   // at least a warp's refill
     unsigned long long nb = 0;
     if (lane == 0) {
-      nb = atomicAdd(work, (unsigned long long)kTakeChunk);
+      nb = atomicAdd(work, (unsigned long long)chunk);
       if (globaltimer_ns() > deadline) atomicOr(flags, 1);
     }
     nb = __shfl_sync(0xffffffffu, nb, 0);
     const uint64_t k = rank < left ? cb + rank : nb + (rank - left);
     cb = nb + (cnt - left);
-    ce = nb + kTakeChunk < total ? nb + kTakeChunk : total;
-    if (nb + kTakeChunk >= total) dry = true;
+    ce = nb + chunk < total ? nb + chunk : total;
+    if (nb + chunk >= total) dry = true;
     return k;
   }
   __device__ __forceinline__ bool empty() const { return dry && cb >= ce; }

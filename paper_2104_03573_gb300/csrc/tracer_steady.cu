@@ -786,7 +786,7 @@ __global__ void __launch_bounds__(TPB, 1) k_steady_f32(const GeoRun* __restrict_
           if (base + cnt >= avail) pool_dry = true;
           k = base + rank;
         } else {
-          k = run.take(need, lane, A.work, C.total, deadline, A.flags);
+          k = run.take(need, lane, A.work, C.total, C.take_chunk, deadline, A.flags);
           avail = C.total;
           if (run.empty()) pool_dry = true;
         }

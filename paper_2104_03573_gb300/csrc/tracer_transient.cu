@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
       if (__all_sync(kAll, drained)) break;
       const unsigned need = __ballot_sync(kAll, !alive && !drained);
       if (need) {
-        const uint64_t k = run.take(need, lane, A.work, C.total, deadline, A.flags);
+        const uint64_t k = run.take(need, lane, A.work, C.total, C.take_chunk, deadline, A.flags);
         if (!alive && !drained) {
           idx = k;
           if (idx >= C.total || (*(volatile int*)A.flags & 1)) {
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(TPB, 1) k_transient_f32(const GeoRun* __restri
       if (__all_sync(kAll, drained)) break;
       const unsigned need = __ballot_sync(kAll, !alive && !drained);
       if (need) {
-        const uint64_t k = run.take(need, lane, A.work, C.total, deadline, A.flags);
+        const uint64_t k = run.take(need, lane, A.work, C.total, C.take_chunk, deadline, A.flags);
         if (!alive && !drained) {
           idx = k;
           if (idx >= C.total || (*(volatile int*)A.flags & 1)) {
@@ -512,11 +512,7 @@ cudaError_t launch_transient(int precision, const GeoRun* geos, const MatView& M
     k_transient_fp64<<<(unsigned)blocks, 256, 0, s>>>(geos, M, C, A);
     return cudaGetLastError();
   }
-  // default block: 512 threads for whole-grid snapshots (no register
-  // spills; they are bound by their tally reductions, not by warps in
-  // flight), 1024 for time-bin averages and detector regions
-  const int dflt = (!C.time_average && C.n_regs == 0) ? 512 : 1024;
-  return launch_transient_f32(geos, M, C, A, threads > 0 ? threads : dflt, bps, s);
+  return launch_transient_f32(geos, M, C, A, threads > 0 ? threads : 1024, bps, s);
 }
 
 #endif  // MCBTE_F64
