@@ -555,11 +555,17 @@ __device__ __forceinline__ int trace_film(Particle<float>& p, const GeoRun& g, c
 // popcount, lanes take consecutive indices).  Lanes therefore never idle
 // while work remains, whatever the event-count spread between particles.
 // TPB is the block size the kernel is compiled for (register budget).
-// GRAD: the gradient pass, which replays the forward pass's particles with
-// their final tallies read from A.X_pp; it writes the gradient accumulators
-// only, and flags (bit 2) any particle whose replayed tally differs.  With
-// the measure-valued d/dp_pore the lane then traces the same particle once
-// more (phantom phase, the chosen pore hit flipped) before it refills.
+// GRAD: the gradient pass.  Fused (C.fused): the forward run's tallies,
+// counters and per-particle outputs and the gradient in one pass, each
+// particle listing its periods until its final tally is known.  Otherwise
+// the replay of the forward pass's particles with their final tallies read
+// from A.X_pp: it writes the gradient accumulators only, and flags (bit 2)
+// any particle whose replayed tally differs.  With the measure-valued
+// d/dp_pore the lane then traces the same particle once more (phantom
+// phase, the chosen pore hit flipped, resumed from the lane's snapshot of
+// that hit where it has one) before it refills.
+// UNF (no cell tallies, no extended physics, no gradient): flights run
+// through the periodic faces of a box without pore or walls (step_steady).
 // CELLS: 0 no cell tallies, 1 T and three flux components, 2 T and the
 // tally-axis flux only.
 //
