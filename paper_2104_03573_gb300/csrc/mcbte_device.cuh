@@ -295,6 +295,15 @@ __device__ __forceinline__ void dir_about_frame(R u[3], const R* f, R mu, uint32
   u[2] = (mu * f[2] + sc * f[5]) + ss * f[8];
 }
 
+// The hardware's approximate square root (PTX sqrt.approx, a few ulp): the
+// FP32 pore hit's root, where a correctly rounded root's longer instruction
+// sequence sat on a lone particle's dependent chain.
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // FP32 box faces and pore cylinder of a geometry record (GeoRun, or the
 // register copy GeoLean with the same member names): the three face
 // distances without branches (the quotients are independent, so their
@@ -334,7 +343,7 @@ __device__ __forceinline__ void hit_box_pore_f32(const Geo& g, const float x[3],
     const float cc = (dx * dx + dy * dy) - g.r2f;
     const float disc = b * b - a * cc;
     const bool hit = a > 0.0f && b < 0.0f && disc >= 0.0f;
-    const float d0 = Num<float>::div(cc, Num<float>::sqrt_(Num<float>::fmax_(disc, 0.0f)) - b);
+    const float d0 = Num<float>::div(cc, sqrt_approx(Num<float>::fmax_(disc, 0.0f)) - b);
     const float d = d0 < 0.0f ? 0.0f : d0;
     const bool take = hit && d < best;
     best = take ? d : best;

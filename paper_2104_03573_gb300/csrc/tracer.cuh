@@ -1131,9 +1131,11 @@ __device__ __forceinline__ int apply_event(Particle<R>& p, const GeoRun& g, cons
       // pore wall: the cylinder's outward normal points into the solid
       nx = p.x[0] - g.cxf;
       ny = p.x[1] - g.cyf;
-      const float len = sqrtf(__fmaf_rn(nx, nx, __fmul_rn(ny, ny)));
-      nx = nx / len;
-      ny = ny / len;
+      // unit normal by the hardware reciprocal square root (the two
+      // quotients of a correctly rounded normalisation sat on the chain)
+      const float il = rsqrtf(__fmaf_rn(nx, nx, __fmul_rn(ny, ny)));
+      nx = nx * il;
+      ny = ny * il;
       spec = (uint64_t)d.wx < g.pthr_pore;
       if (Grad::on) {
         spec = gr.pore_branch(spec, g.p_pore, Xnow, [&] { return src.mv(ctr, k0, k1); });
