@@ -68,18 +68,18 @@ WORKLOADS = {"si_slab": "si_slab_L1um_3000bins", "si_slab_imp": "si_slab_L1um_30
 # event costs, taken from ncu's instruction counters of the bench's own launch
 # (smsp__thread_inst_executed.sum and smsp__inst_executed.sum over the tracing
 # kernels of one step, divided by the step's events; the capture and its
-# command are summarised in profiles/k_steady_f32_si_slab.md).  Workloads
+# command are summarised under profiles/).  Workloads
 # without such a capture fall back to the count of the work one event needs
 # (one Philox4x32-10 call, log + sqrt + sincos, six-plane first hit, alias
 # draw, state update and tallies: 200 thread-instructions).
 INSTR_PER_EVENT = 200.0
 NCU_INSTR_PER_EVENT = {   # workload: (thread-instructions, warp-instructions) per event
-    "si_slab": (388.2, 19.59),    # 2.570e11 / 1.297e10 instructions over 6.619e8 events
+    "si_slab": (375.9, 19.06),    # 2.488e11 / 1.261e10 instructions over 6.619e8 events
 }
 # DRAM bytes per launch of the FP32 steady tracing kernel on the default
 # workload, from the ncu capture summarised in profiles/ (None until a capture
 # of the current kernel exists).
-TRACE_DRAM_BYTES_PER_LAUNCH = 1_175_808 + 315_392
+TRACE_DRAM_BYTES_PER_LAUNCH = 1_713_152 + 40_448
 
 
 PROBE_SRC = os.path.join(ROOT, "bench_l2_probe.cu")
