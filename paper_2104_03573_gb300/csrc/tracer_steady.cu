@@ -550,10 +550,11 @@ __device__ __forceinline__ int trace_film(Particle<float>& p, const GeoRun& g, c
 }
 
 // Every lane owns one particle at a time.  When its particle terminates the
-// lane refills from a global work counter; the refills of a warp are
-// aggregated into one atomicAdd (ballot of the empty lanes, leader adds the
-// popcount, lanes take consecutive indices).  Lanes therefore never idle
-// while work remains, whatever the event-count spread between particles.
+// lane refills from its warp's run of particle indices (WarpRun: a ballot of
+// the empty lanes, which take consecutive indices of the run; the run is
+// refilled from the global work counter a chunk at a time, one atomic per
+// chunk).  Lanes therefore never idle while work remains, whatever the
+// event-count spread between particles.
 // TPB is the block size the kernel is compiled for (register budget).
 // GRAD: the gradient pass.  Fused (C.fused): the forward run's tallies,
 // counters and per-particle outputs and the gradient in one pass, each
